@@ -1,0 +1,214 @@
+/*
+ * vgicp.h -- C ABI of the B300 voxelised-GICP factor library.
+ *
+ * Operations (Koide et al., "Globally Consistent 3D LiDAR Mapping with
+ * GPU-accelerated GICP Matching Cost Factors", RA-L 2021):
+ *   - voxelmap build: Sec. III-A, voxel data association (a voxel holds the
+ *     mean of its points' means and the mean of their covariances);
+ *   - factor linearisation: Eq. 1-6 (cost, 12x12 Gauss-Newton H, 12-vector b);
+ *   - overlap: Eq. 7-8;
+ *   - per-point covariance estimation from k neighbours: Sec. III (overview).
+ *
+ * Conventions used by every call:
+ *   - Poses are 12 doubles, row-major 3x4 [R | t], world-from-frame.
+ *   - A factor has a target B (owner of the voxelmap) and a source A (whose
+ *     points are summed over); source points are mapped into the target frame
+ *     by T_BA = T_B^-1 T_A, computed in float64 as
+ *     R_BA[i][j] = sum_k R_B[k][i] R_A[k][j], t_BA[i] = sum_k R_B[k][i] (t_A[k] - t_B[k]),
+ *     k = 0, 1, 2, every product and sum separately rounded.
+ *   - Tangent: right perturbation T <- T Exp(xi), xi = (omega, v), rotation
+ *     first; the 12-vector is [xi_B ; xi_A].  H is the full symmetric 12x12
+ *     matrix, row-major, H = sum J^T Omega J, b = sum J^T Omega e, cost =
+ *     sum e^T Omega e with e = mu_B - T_BA p and Omega = (C_B + R C_A R^T)^-1
+ *     (no factor 1/2, no weighting by voxel point count).
+ *   - Voxel coordinate of a point x (target frame): k = floor(x * (1/r)),
+ *     x formed in float64 as fma(R0, px, fma(R1, py, fma(R2, pz, t))); valid
+ *     iff -2^20 <= k <= 2^20 - 1 on every axis and x is finite.  A source point
+ *     corresponds to the one target voxel containing it, or to none.
+ *   - Points: n x 3 float32 (x, y, z).  Covariances: n x 6 float32
+ *     (c00, c01, c02, c11, c12, c22), symmetric positive definite.
+ *
+ * Memory: mem_kind / out_kind say where a caller pointer lives.  HOST
+ * pointers may be pageable; DEVICE pointers are read on the context stream and
+ * copied into library-owned device memory before the call returns control of
+ * the stream.  Handles own their device memory until vgicp_release() or
+ * vgicp_destroy().  Output buffers are always caller-owned.
+ *
+ * Synchronisation: every call is ordered on the context's CUDA stream.  Calls
+ * with HOST outputs return after the results are in host memory; calls with
+ * DEVICE outputs return once the work is enqueued.
+ *
+ * Errors: every call returns a vgicp_status; nothing throws across the ABI.
+ * On error, vgicp_last_error() describes the first failure of the last call.
+ * A context is used from one host thread at a time.
+ */
+#ifndef VGICP_H
+#define VGICP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VGICP_OK = 0,
+    VGICP_ERR_INVALID_ARG = 1,  /* null pointer, negative size, bad handle, r <= 0 or non-finite */
+    VGICP_ERR_OOM = 2,          /* device or pinned host allocation failed */
+    VGICP_ERR_NOT_FOUND = 3,    /* handle does not exist (released or never created) */
+    VGICP_ERR_EMPTY = 4,        /* overlap of a source with zero points (Eq. 8 undefined) */
+    VGICP_ERR_CUDA = 5,         /* a CUDA runtime call failed; see vgicp_last_error() */
+    VGICP_ERR_TIMEOUT = 6,      /* a bounded device wait ran out */
+    VGICP_ERR_BUDGET = 7        /* admission would exceed the context's device-memory budget */
+} vgicp_status;
+
+enum { VGICP_MEM_HOST = 0, VGICP_MEM_DEVICE = 1 };
+
+/* Linearisation precision (vgicp_options.precision). */
+enum {
+    /* Batched path: one persistent launch over all factors; per-point transform,
+     * inverse and Jacobian products in float32 (voxel index and residual taken
+     * from an error-free float32-pair transform, with a float64 fallback at voxel
+     * faces); per-chunk sums in float64; 12x12 expansion in float64. */
+    VGICP_PREC_F32 = 0,
+    /* Plain path: one launch per factor; everything in float64 with the literal
+     * 3x12 Jacobian and all 78 unique entries of J^T Omega J per point. */
+    VGICP_PREC_F64 = 1
+};
+
+typedef struct vgicp_ctx vgicp_ctx;
+typedef int64_t vgicp_map_t;    /* voxelmap handle */
+typedef int64_t vgicp_frame_t;  /* source-frame handle (points + covariances resident on device) */
+
+/* One VGICP matching-cost factor (Eq. 1, 3): target voxelmap B, source frame A,
+ * and the indices of T_B and T_A in the poses array passed to vgicp_linearize(). */
+typedef struct {
+    vgicp_map_t target;
+    vgicp_frame_t source;
+    int32_t target_pose;
+    int32_t source_pose;
+} vgicp_factor;
+
+typedef struct {
+    int32_t precision;        /* VGICP_PREC_F32 (default) or VGICP_PREC_F64 */
+    int32_t chunk_points;     /* points per work item of the batched path (multiple of 32; 0 = default 2048) */
+    int32_t block_threads;    /* threads per block of the batched path (multiple of 32, <= 1024; 0 = default 256) */
+    int32_t blocks_per_sm;    /* persistent grid = SMs x this (0 = default from occupancy) */
+    int64_t hbm_budget_bytes; /* device bytes handles may hold in total (0 = unlimited) */
+} vgicp_options;
+
+/* Fill *opt with the defaults above. */
+vgicp_status vgicp_options_default(vgicp_options *opt);
+
+/* Create a context on the current CUDA device.  opt may be NULL (defaults).
+ * cuda_stream is a cudaStream_t to order work on, or NULL for a stream the
+ * context creates and owns. */
+vgicp_status vgicp_create(vgicp_ctx **ctx, const vgicp_options *opt, void *cuda_stream);
+
+/* Destroy a context: synchronises its stream and frees every handle. */
+vgicp_status vgicp_destroy(vgicp_ctx *ctx);
+
+/* Replace the options of a live context (takes effect on the next call). */
+vgicp_status vgicp_set_options(vgicp_ctx *ctx, const vgicp_options *opt);
+
+/* Order subsequent work on another stream (NULL = the context's own stream). */
+vgicp_status vgicp_set_stream(vgicp_ctx *ctx, void *cuda_stream);
+
+/* Block until all work enqueued by the context has finished. */
+vgicp_status vgicp_synchronize(vgicp_ctx *ctx);
+
+/* Register a point cloud with per-point covariances as a source frame (its
+ * points p_k and covariances C_k of Eq. 2).  The data are copied into a
+ * coalesced device layout owned by the handle.  n may be 0. */
+vgicp_status vgicp_add_frame(vgicp_ctx *ctx, const float *points, const float *covs, int64_t n,
+                             int mem_kind, vgicp_frame_t *out);
+
+/* Number of points of a frame. */
+vgicp_status vgicp_frame_size(vgicp_ctx *ctx, vgicp_frame_t frame, int64_t *n);
+
+/* Build the voxelmap of a cloud (in its own frame) at resolution r (Sec. III-A):
+ * an open-addressing hash on the device from voxel coordinate to (point count,
+ * mean, covariance).  Points with invalid voxel coordinates are skipped. */
+vgicp_status vgicp_build_voxelmap(vgicp_ctx *ctx, const float *points, const float *covs, int64_t n,
+                                  double resolution, int mem_kind, vgicp_map_t *out);
+
+/* Build voxelmaps of n registered frames at resolution r in one batched pass.
+ * maps[i] < 0 on input creates a new handle; maps[i] >= 0 rebuilds that map in
+ * place (its device memory is reused when large enough). */
+vgicp_status vgicp_build_voxelmaps(vgicp_ctx *ctx, const vgicp_frame_t *frames, int64_t n,
+                                   double resolution, vgicp_map_t *maps);
+
+/* Number of voxels of a map. */
+vgicp_status vgicp_voxelmap_size(vgicp_ctx *ctx, vgicp_map_t map, int64_t *n_voxels);
+
+/* Linearise n_f factors (Eq. 3-6) at the poses given (n_poses x 12 doubles,
+ * host memory).
+ * Outputs (caller-owned, n_f entries each, in out_kind memory):
+ *   H  n_f x 144 doubles (full symmetric 12x12, [xi_B ; xi_A] order),
+ *   b  n_f x 12 doubles, cost n_f doubles, inliers n_f int64 (nullable):
+ *   the number of source points that found a target voxel.
+ * Precision follows the context options (VGICP_PREC_*).  Factors whose
+ * indices or handles are invalid make the whole call fail with INVALID_ARG or
+ * NOT_FOUND before any work is enqueued. */
+vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f,
+                             const double *poses, int64_t n_poses,
+                             double *H, double *b, double *cost, int64_t *inliers, int out_kind);
+
+/* Overlap of a source frame with a target voxelmap (Eq. 8) under the relative
+ * pose T_target_source (12 doubles, host): fraction = count / N.  count is
+ * optional (nullable).  N = 0 returns VGICP_ERR_EMPTY. */
+vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t target,
+                           const double *T_target_source, double *fraction, int64_t *count);
+
+/* Overlap counts of every (source, target) pair (Eq. 7-8 numerators):
+ * counts[s * n_tgt + t] = #{k : voxel(T_t^-1 T_s p_k) in map t}, poses_src
+ * n_src x 12 and poses_tgt n_tgt x 12 (world-from-frame, host).  counts is
+ * caller-owned int64 in out_kind memory. */
+vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, int64_t n_src,
+                                  const vgicp_map_t *targets, int64_t n_tgt,
+                                  const double *poses_src, const double *poses_tgt,
+                                  int64_t *counts, int out_kind);
+
+/* Per-point voxel association of a source against a target (debug / parity):
+ * keys (n x 3 int64, host) receives each point's voxel coordinate under
+ * T_target_source (INT64_MIN on every axis when invalid), hit (n int32, host)
+ * 1 if that voxel exists in the map.  Either output may be NULL. */
+vgicp_status vgicp_debug_correspondences(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t target,
+                                         const double *T_target_source, int64_t *keys, int32_t *hit);
+
+/* Copy a voxelmap to host, sorted by (kx, ky, kz).  *n_voxels is the capacity of
+ * the outputs on input and the number of voxels on output (outputs may all be
+ * NULL to query the size).  keys V x 3 int64, counts V int64, mu V x 3 doubles
+ * (absolute coordinates), cov V x 6 doubles. */
+vgicp_status vgicp_export_voxelmap(vgicp_ctx *ctx, vgicp_map_t map, int64_t *keys, int64_t *counts,
+                                   double *mu, double *cov, int64_t *n_voxels);
+
+/* Per-point covariances from the k nearest neighbours of each point (Sec. III:
+ * estimated from k neighbouring points; the point itself counts, ties go to the
+ * lower index), regularised to eigenvalues (1, 1, eps): the direction of least
+ * spread receives eps.  points n x 3 and covs_out n x 6 float32, both in
+ * mem_kind memory.  1 <= k <= 32.  Points with fewer than k finite neighbours
+ * get the identity. */
+vgicp_status vgicp_estimate_covariances(vgicp_ctx *ctx, const float *points, int64_t n, int32_t k,
+                                        double eps, float *covs_out, int mem_kind);
+
+/* Release a map or frame handle and its device memory. */
+vgicp_status vgicp_release(vgicp_ctx *ctx, int64_t handle);
+
+/* Device bytes currently held by handles of this context. */
+vgicp_status vgicp_memory_in_use(vgicp_ctx *ctx, int64_t *bytes);
+
+/* Number of kernels this context has launched since creation. */
+vgicp_status vgicp_kernel_launches(vgicp_ctx *ctx, int64_t *count);
+
+/* Text of the last error of this context ("" if none).  Valid until the next call. */
+const char *vgicp_last_error(const vgicp_ctx *ctx);
+
+/* Human-readable name of a status code. */
+const char *vgicp_status_string(vgicp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VGICP_H */

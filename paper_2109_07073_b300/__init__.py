@@ -1,0 +1,351 @@
+"""Python binding of the B300 VGICP library (libvgicp.so).
+
+Argument marshalling only: every call goes through the C ABI declared in
+include/vgicp.h, whose kernels do all the arithmetic.  numpy arrays are passed
+as host memory; torch CUDA tensors are passed as device memory (their data
+pointers), so PyTorch serves for device memory and streams.  There is no CPU
+fallback: loading fails loudly if the library has not been built.
+
+Functions keep the C names (vgicp_create, vgicp_add_frame, vgicp_build_voxelmap,
+vgicp_build_voxelmaps, vgicp_linearize, vgicp_overlap, vgicp_overlap_matrix,
+vgicp_debug_correspondences, vgicp_export_voxelmap, vgicp_estimate_covariances,
+vgicp_release, ...); `Context` bundles them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvgicp.so")
+
+VGICP_OK = 0
+STATUS = {0: "VGICP_OK", 1: "VGICP_ERR_INVALID_ARG", 2: "VGICP_ERR_OOM", 3: "VGICP_ERR_NOT_FOUND",
+          4: "VGICP_ERR_EMPTY", 5: "VGICP_ERR_CUDA", 6: "VGICP_ERR_TIMEOUT", 7: "VGICP_ERR_BUDGET"}
+VGICP_MEM_HOST, VGICP_MEM_DEVICE = 0, 1
+VGICP_PREC_F32, VGICP_PREC_F64 = 0, 1
+
+EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_options", "vgicp_set_stream",
+           "vgicp_synchronize", "vgicp_add_frame", "vgicp_frame_size", "vgicp_build_voxelmap",
+           "vgicp_build_voxelmaps", "vgicp_voxelmap_size", "vgicp_linearize", "vgicp_overlap",
+           "vgicp_overlap_matrix", "vgicp_debug_correspondences", "vgicp_export_voxelmap",
+           "vgicp_estimate_covariances", "vgicp_release", "vgicp_memory_in_use", "vgicp_kernel_launches",
+           "vgicp_last_error", "vgicp_status_string"]
+
+
+class VgicpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("chunk_points", C.c_int32), ("block_threads", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+
+
+class Factor(C.Structure):
+    _fields_ = [("target", C.c_int64), ("source", C.c_int64), ("target_pose", C.c_int32),
+                ("source_pose", C.c_int32)]
+
+
+FACTOR_DTYPE = np.dtype([("target", np.int64), ("source", np.int64), ("target_pose", np.int32),
+                         ("source_pose", np.int32)])
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libvgicp.so (build it first with paper_2109_07073_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2109_07073_b300.build`")
+    lib = C.CDLL(path)
+    vp, i64, i32, f64 = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    sig = {
+        "vgicp_options_default": [C.POINTER(Options)],
+        "vgicp_create": [C.POINTER(vp), C.POINTER(Options), vp],
+        "vgicp_destroy": [vp],
+        "vgicp_set_options": [vp, C.POINTER(Options)],
+        "vgicp_set_stream": [vp, vp],
+        "vgicp_synchronize": [vp],
+        "vgicp_add_frame": [vp, vp, vp, i64, C.c_int, C.POINTER(i64)],
+        "vgicp_frame_size": [vp, i64, C.POINTER(i64)],
+        "vgicp_build_voxelmap": [vp, vp, vp, i64, f64, C.c_int, C.POINTER(i64)],
+        "vgicp_build_voxelmaps": [vp, vp, i64, f64, vp],
+        "vgicp_voxelmap_size": [vp, i64, C.POINTER(i64)],
+        "vgicp_linearize": [vp, vp, i64, vp, i64, vp, vp, vp, vp, C.c_int],
+        "vgicp_overlap": [vp, i64, i64, vp, C.POINTER(f64), C.POINTER(i64)],
+        "vgicp_overlap_matrix": [vp, vp, i64, vp, i64, vp, vp, vp, C.c_int],
+        "vgicp_debug_correspondences": [vp, i64, i64, vp, vp, vp],
+        "vgicp_export_voxelmap": [vp, i64, vp, vp, vp, vp, C.POINTER(i64)],
+        "vgicp_estimate_covariances": [vp, vp, i64, i32, f64, vp, C.c_int],
+        "vgicp_release": [vp, i64],
+        "vgicp_memory_in_use": [vp, C.POINTER(i64)],
+        "vgicp_kernel_launches": [vp, C.POINTER(i64)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.vgicp_last_error.argtypes = [vp]
+    lib.vgicp_last_error.restype = C.c_char_p
+    lib.vgicp_status_string.argtypes = [C.c_int]
+    lib.vgicp_status_string.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status: int):
+    if status != VGICP_OK:
+        msg = load().vgicp_last_error(ctx).decode() if ctx else ""
+        raise VgicpError(status, msg)
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _host(a, dtype, cols=None):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if cols is not None:
+        a = a.reshape(-1, cols)
+    return a
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch_cuda(a):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _cloud(points, covs=None):
+    """(points, covs, n, mem_kind) with both in the same memory and the C layout."""
+    if _is_torch_cuda(points):
+        import torch
+        p = points.to(torch.float32).contiguous().reshape(-1, 3)
+        c = None if covs is None else covs.to(device=p.device, dtype=torch.float32).contiguous().reshape(-1, 6)
+        return p, c, int(p.shape[0]), VGICP_MEM_DEVICE
+    p = _host(points, np.float32, 3)
+    c = None if covs is None else _host(covs, np.float32, 6)
+    return p, c, int(p.shape[0]), VGICP_MEM_HOST
+
+
+def _pose12(T):
+    return _host(np.asarray(T, dtype=np.float64).reshape(-1, 12), np.float64)
+
+
+# ----------------------------------------------------------------- the ABI --
+
+def vgicp_options_default() -> Options:
+    o = Options()
+    _check(None, load().vgicp_options_default(C.byref(o)))
+    return o
+
+
+def vgicp_create(options: Options = None, stream=None):
+    """New context; stream is a torch.cuda.Stream, a raw cudaStream_t int, or None (own stream)."""
+    ctx = C.c_void_p()
+    s = getattr(stream, "cuda_stream", stream)
+    _check(None, load().vgicp_create(C.byref(ctx), C.byref(options) if options is not None else None,
+                                     C.c_void_p(s) if s else None))
+    return ctx
+
+
+def vgicp_destroy(ctx):
+    _check(ctx, load().vgicp_destroy(ctx))
+
+
+def vgicp_set_options(ctx, options: Options):
+    _check(ctx, load().vgicp_set_options(ctx, C.byref(options)))
+
+
+def vgicp_set_stream(ctx, stream=None):
+    s = getattr(stream, "cuda_stream", stream)
+    _check(ctx, load().vgicp_set_stream(ctx, C.c_void_p(s) if s else None))
+
+
+def vgicp_synchronize(ctx):
+    _check(ctx, load().vgicp_synchronize(ctx))
+
+
+def vgicp_add_frame(ctx, points, covs) -> int:
+    p, c, n, kind = _cloud(points, covs)
+    h = C.c_int64()
+    _check(ctx, load().vgicp_add_frame(ctx, _ptr(p), _ptr(c), n, kind, C.byref(h)))
+    return h.value
+
+
+def vgicp_frame_size(ctx, frame: int) -> int:
+    n = C.c_int64()
+    _check(ctx, load().vgicp_frame_size(ctx, frame, C.byref(n)))
+    return n.value
+
+
+def vgicp_build_voxelmap(ctx, points, covs, resolution: float) -> int:
+    p, c, n, kind = _cloud(points, covs)
+    h = C.c_int64()
+    _check(ctx, load().vgicp_build_voxelmap(ctx, _ptr(p), _ptr(c), n, float(resolution), kind, C.byref(h)))
+    return h.value
+
+
+def vgicp_build_voxelmaps(ctx, frames, resolution: float, maps=None) -> np.ndarray:
+    f = _host(frames, np.int64)
+    m = np.full(f.shape[0], -1, np.int64) if maps is None else _host(maps, np.int64).copy()
+    _check(ctx, load().vgicp_build_voxelmaps(ctx, _ptr(f), f.shape[0], float(resolution), _ptr(m)))
+    return m
+
+
+def vgicp_voxelmap_size(ctx, vmap: int) -> int:
+    n = C.c_int64()
+    _check(ctx, load().vgicp_voxelmap_size(ctx, vmap, C.byref(n)))
+    return n.value
+
+
+def make_factors(targets, sources, target_poses, source_poses) -> np.ndarray:
+    f = np.zeros(len(targets), FACTOR_DTYPE)
+    f["target"], f["source"] = targets, sources
+    f["target_pose"], f["source_pose"] = target_poses, source_poses
+    return f
+
+
+def vgicp_linearize(ctx, factors, poses, out=None):
+    """Eq. 3-6 for every factor.  Returns (H (n,12,12), b (n,12), cost (n,), inliers (n,)).
+
+    out: optional tuple of preallocated outputs; torch CUDA tensors make the call
+    write device memory (asynchronously), numpy arrays host memory."""
+    f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
+    P = _pose12(poses)
+    nf = f.shape[0]
+    if out is None:
+        out = (np.zeros((nf, 12, 12)), np.zeros((nf, 12)), np.zeros(nf), np.zeros(nf, np.int64))
+    H, b, cost, inl = out
+    kind = VGICP_MEM_DEVICE if _is_torch_cuda(H) else VGICP_MEM_HOST
+    _check(ctx, load().vgicp_linearize(ctx, _ptr(f), nf, _ptr(P), P.shape[0], _ptr(H), _ptr(b), _ptr(cost),
+                                       _ptr(inl), kind))
+    return H, b, cost, inl
+
+
+def vgicp_overlap(ctx, source: int, target: int, T_target_source):
+    """Eq. 8: (fraction, count)."""
+    T = _pose12(T_target_source)
+    fr, cnt = C.c_double(), C.c_int64()
+    _check(ctx, load().vgicp_overlap(ctx, source, target, _ptr(T), C.byref(fr), C.byref(cnt)))
+    return fr.value, cnt.value
+
+
+def vgicp_overlap_matrix(ctx, sources, targets, poses_src, poses_tgt, out=None) -> np.ndarray:
+    """counts (n_src, n_tgt) int64: hits of source s in target t under T_t^-1 T_s."""
+    s = _host(sources, np.int64)
+    t = _host(targets, np.int64)
+    ps, pt = _pose12(poses_src), _pose12(poses_tgt)
+    if out is None:
+        out = np.zeros((s.shape[0], t.shape[0]), np.int64)
+    kind = VGICP_MEM_DEVICE if _is_torch_cuda(out) else VGICP_MEM_HOST
+    _check(ctx, load().vgicp_overlap_matrix(ctx, _ptr(s), s.shape[0], _ptr(t), t.shape[0], _ptr(ps), _ptr(pt),
+                                            _ptr(out), kind))
+    return out
+
+
+def vgicp_debug_correspondences(ctx, source: int, target: int, T_target_source):
+    """(keys (n, 3) int64 with INT64_MIN rows for invalid points, hit (n,) bool)."""
+    n = vgicp_frame_size(ctx, source)
+    keys = np.zeros((max(n, 1), 3), np.int64)
+    hit = np.zeros(max(n, 1), np.int32)
+    T = _pose12(T_target_source)
+    _check(ctx, load().vgicp_debug_correspondences(ctx, source, target, _ptr(T), _ptr(keys), _ptr(hit)))
+    return keys[:n], hit[:n].astype(bool)
+
+
+def vgicp_export_voxelmap(ctx, vmap: int):
+    """(keys (V, 3) int64, counts (V,), mu (V, 3) float64, cov (V, 6) float64), sorted by key."""
+    nv = C.c_int64(0)
+    _check(ctx, load().vgicp_export_voxelmap(ctx, vmap, None, None, None, None, C.byref(nv)))
+    V = nv.value
+    keys = np.zeros((max(V, 1), 3), np.int64)
+    counts = np.zeros(max(V, 1), np.int64)
+    mu = np.zeros((max(V, 1), 3))
+    cov = np.zeros((max(V, 1), 6))
+    nv = C.c_int64(max(V, 1))
+    _check(ctx, load().vgicp_export_voxelmap(ctx, vmap, _ptr(keys), _ptr(counts), _ptr(mu), _ptr(cov), C.byref(nv)))
+    V = nv.value
+    return keys[:V], counts[:V], mu[:V], cov[:V]
+
+
+def vgicp_estimate_covariances(ctx, points, k: int = 10, eps: float = 1e-3, out=None):
+    """Per-point covariances (n, 6) float32 from k neighbours, eigenvalues (1, 1, eps)."""
+    p, _, n, kind = _cloud(points)
+    if out is None:
+        if kind == VGICP_MEM_DEVICE:
+            import torch
+            out = torch.empty((n, 6), dtype=torch.float32, device=p.device)
+        else:
+            out = np.zeros((n, 6), np.float32)
+    _check(ctx, load().vgicp_estimate_covariances(ctx, _ptr(p), n, int(k), float(eps), _ptr(out), kind))
+    return out
+
+
+def vgicp_release(ctx, handle: int):
+    _check(ctx, load().vgicp_release(ctx, handle))
+
+
+def vgicp_memory_in_use(ctx) -> int:
+    v = C.c_int64()
+    _check(ctx, load().vgicp_memory_in_use(ctx, C.byref(v)))
+    return v.value
+
+
+def vgicp_kernel_launches(ctx) -> int:
+    v = C.c_int64()
+    _check(ctx, load().vgicp_kernel_launches(ctx, C.byref(v)))
+    return v.value
+
+
+def vgicp_last_error(ctx) -> str:
+    return load().vgicp_last_error(ctx).decode()
+
+
+class Context:
+    """A vgicp_ctx with the calls bound as methods (names without the vgicp_ prefix)."""
+
+    def __init__(self, precision: int = VGICP_PREC_F32, stream=None, **opts):
+        o = vgicp_options_default()
+        o.precision = precision
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.options = o
+        self.ctx = vgicp_create(o, stream)
+
+    def close(self):
+        if self.ctx:
+            vgicp_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **opts):
+        for k, v in opts.items():
+            setattr(self.options, k, v)
+        vgicp_set_options(self.ctx, self.options)
+
+    def __getattr__(self, name):
+        fn = globals().get("vgicp_" + name)
+        if fn is None or name.startswith("_"):
+            raise AttributeError(name)
+        return lambda *a, **k: fn(self.ctx, *a, **k)

@@ -1,0 +1,1008 @@
+// C ABI of the VGICP library: contexts, handles, device memory and the host
+// side of every call declared in include/vgicp.h.  All arithmetic of the
+// method runs in the kernels; this file validates arguments, owns memory,
+// builds work lists and orders launches on the context stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "vgicp.h"
+
+using namespace vg;
+
+namespace {
+
+struct Obj {
+    enum Kind { FREE = 0, FRAME = 1, MAP = 2 } kind = FREE;
+    uint32_t gen = 0;
+    // frame
+    int64_t n = 0;
+    void *frame_mem = nullptr;
+    size_t frame_bytes = 0;
+    // map
+    void *map_mem = nullptr;
+    size_t map_bytes = 0;
+    uint32_t cap = 0;
+    double r = 0.0;
+};
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// A cached work list for a factor set: device copies of the per-factor indices,
+// the chunk items and each factor's first item.
+struct Plan {
+    std::vector<vgicp_factor> key;
+    std::vector<int64_t> frame_n;
+    int chunk = 0;
+    int n_items = 0;
+    Buf idx, items, item_begin;
+};
+
+}  // namespace
+
+struct vgicp_ctx {
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    int device = 0;
+    int num_sms = 148;
+    vgicp_options opt{};
+    std::string err;
+    std::vector<Obj> objs;
+    std::vector<uint32_t> free_idx;
+    int64_t bytes_in_use = 0;
+    int64_t launches = 0;
+    // descriptor tables (device) and host mirrors
+    MapDesc *d_maps = nullptr;
+    FrameDesc *d_frames = nullptr;
+    std::vector<MapDesc> h_maps;
+    std::vector<FrameDesc> h_frames;
+    size_t tab_cap = 0;
+    // workspaces
+    Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
+    Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
+    Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter;
+    Plan plan;
+};
+
+namespace {
+
+
+vgicp_status fail(vgicp_ctx *c, vgicp_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CU(call)                                                                                            \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess)                                                                              \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? VGICP_ERR_OOM : VGICP_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                                 \
+    } while (0)
+
+#define CHECK_LAUNCH()                                                                                      \
+    do {                                                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                                                \
+        if (e_ != cudaSuccess)                                                                              \
+            return fail(ctx, VGICP_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__,  \
+                        __LINE__);                                                                          \
+    } while (0)
+
+#define TRY(expr)                               \
+    do {                                        \
+        vgicp_status s_ = (expr);               \
+        if (s_ != VGICP_OK) return s_;          \
+    } while (0)
+
+vgicp_status ensure(vgicp_ctx *ctx, Buf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return VGICP_OK;
+    if (b.p) CU(cudaFreeAsync(b.p, ctx->stream));
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t nb = std::max(bytes, b.bytes * 3 / 2);
+    CU(cudaMallocAsync(&b.p, nb, ctx->stream));
+    b.bytes = nb;
+    return VGICP_OK;
+}
+
+void free_buf(vgicp_ctx *ctx, Buf &b)
+{
+    if (b.p) cudaFreeAsync(b.p, ctx->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+template <class T>
+vgicp_status upload(vgicp_ctx *ctx, Buf &b, const T *src, size_t count)
+{
+    TRY(ensure(ctx, b, count * sizeof(T)));
+    if (count) CU(cudaMemcpyAsync(b.p, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return VGICP_OK;
+}
+
+inline int64_t make_handle(uint32_t idx, uint32_t gen) { return ((int64_t)gen << 32) | (int64_t)idx; }
+
+Obj *lookup(vgicp_ctx *ctx, int64_t h, Obj::Kind kind, uint32_t *idx_out = nullptr)
+{
+    if (h < 0) return nullptr;
+    const uint32_t idx = (uint32_t)(h & 0xffffffff), gen = (uint32_t)(h >> 32);
+    if (idx >= ctx->objs.size()) return nullptr;
+    Obj &o = ctx->objs[idx];
+    if (o.kind != kind || o.gen != gen) return nullptr;
+    if (idx_out) *idx_out = idx;
+    return &o;
+}
+
+vgicp_status grow_tables(vgicp_ctx *ctx, size_t need)
+{
+    if (need <= ctx->tab_cap) return VGICP_OK;
+    size_t cap = std::max<size_t>(64, ctx->tab_cap);
+    while (cap < need) cap *= 2;
+    MapDesc *nm = nullptr;
+    FrameDesc *nf = nullptr;
+    CU(cudaMallocAsync((void **)&nm, cap * sizeof(MapDesc), ctx->stream));
+    CU(cudaMallocAsync((void **)&nf, cap * sizeof(FrameDesc), ctx->stream));
+    CU(cudaMemsetAsync(nm, 0, cap * sizeof(MapDesc), ctx->stream));
+    CU(cudaMemsetAsync(nf, 0, cap * sizeof(FrameDesc), ctx->stream));
+    if (ctx->tab_cap) {
+        CU(cudaMemcpyAsync(nm, ctx->d_maps, ctx->tab_cap * sizeof(MapDesc), cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(nf, ctx->d_frames, ctx->tab_cap * sizeof(FrameDesc), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CU(cudaFreeAsync(ctx->d_maps, ctx->stream));
+        CU(cudaFreeAsync(ctx->d_frames, ctx->stream));
+    }
+    ctx->d_maps = nm;
+    ctx->d_frames = nf;
+    ctx->tab_cap = cap;
+    ctx->h_maps.resize(cap);
+    ctx->h_frames.resize(cap);
+    return VGICP_OK;
+}
+
+vgicp_status new_obj(vgicp_ctx *ctx, Obj::Kind kind, uint32_t *idx)
+{
+    uint32_t i;
+    if (!ctx->free_idx.empty()) {
+        i = ctx->free_idx.back();
+        ctx->free_idx.pop_back();
+    } else {
+        i = (uint32_t)ctx->objs.size();
+        ctx->objs.emplace_back();
+    }
+    TRY(grow_tables(ctx, ctx->objs.size()));
+    Obj &o = ctx->objs[i];
+    o.kind = kind;
+    o.gen += 1;
+    *idx = i;
+    return VGICP_OK;
+}
+
+vgicp_status budget_check(vgicp_ctx *ctx, int64_t extra)
+{
+    if (ctx->opt.hbm_budget_bytes > 0 && ctx->bytes_in_use + extra > ctx->opt.hbm_budget_bytes)
+        return fail(ctx, VGICP_ERR_BUDGET, "device budget %lld B exceeded (in use %lld B, requested %lld B)",
+                    (long long)ctx->opt.hbm_budget_bytes, (long long)ctx->bytes_in_use, (long long)extra);
+    return VGICP_OK;
+}
+
+vgicp_status put_frame_desc(vgicp_ctx *ctx, uint32_t idx)
+{
+    CU(cudaMemcpyAsync(ctx->d_frames + idx, &ctx->h_frames[idx], sizeof(FrameDesc), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return VGICP_OK;
+}
+
+vgicp_status put_map_desc(vgicp_ctx *ctx, uint32_t idx)
+{
+    CU(cudaMemcpyAsync(ctx->d_maps + idx, &ctx->h_maps[idx], sizeof(MapDesc), cudaMemcpyHostToDevice, ctx->stream));
+    return VGICP_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Allocate and fill a frame from device-resident points / covariances.
+vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, int64_t n, uint32_t *out_idx)
+{
+    const size_t o_pb = align256((size_t)n * 16), o_pc = o_pb + align256((size_t)n * 16);
+    const size_t o_cm = o_pc + align256((size_t)n * 4), bytes = o_cm + 256;
+    TRY(budget_check(ctx, (int64_t)bytes));
+    uint32_t idx;
+    TRY(new_obj(ctx, Obj::FRAME, &idx));
+    Obj &o = ctx->objs[idx];
+    char *base = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&base, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        o.kind = Obj::FREE;
+        ctx->free_idx.push_back(idx);
+        return fail(ctx, VGICP_ERR_OOM, "frame allocation of %zu B failed: %s", bytes, cudaGetErrorString(e));
+    }
+    o.n = n;
+    o.frame_mem = base;
+    o.frame_bytes = bytes;
+    ctx->bytes_in_use += (int64_t)bytes;
+    FrameDesc &f = ctx->h_frames[idx];
+    f.pa = (const float4 *)base;
+    f.pb = (const float4 *)(base + o_pb);
+    f.pc = (const float *)(base + o_pc);
+    f.cmax = (const float *)(base + o_cm);
+    f.n = n;
+    CU(cudaMemsetAsync(base + o_cm, 0, 4, ctx->stream));
+    launch_frame_pack(d_pts, d_cov, n, (float4 *)f.pa, (float4 *)f.pb, (float *)f.pc, (float *)f.cmax, ctx->stream);
+    ctx->launches += n > 0;
+    CHECK_LAUNCH();
+    TRY(put_frame_desc(ctx, idx));
+    *out_idx = idx;
+    return VGICP_OK;
+}
+
+uint32_t map_capacity(int64_t n)
+{
+    int64_t want = std::max<int64_t>(16, n + n / 2 + 1);
+    uint32_t cap = 16;
+    while ((int64_t)cap < want) cap <<= 1;
+    return cap;
+}
+
+bool is_pow2_res(double r)
+{
+    int e;
+    return std::frexp(r, &e) == 0.5;
+}
+
+void fill_map_desc(MapDesc &m, char *base, uint32_t cap, double r)
+{
+    m.keys = (uint64_t *)base;
+    m.rec = (VoxelRec *)(base + align256((size_t)cap * 8));
+    m.mask = cap - 1;
+    uint32_t l = 0;
+    while ((1u << l) < cap) ++l;
+    m.log2cap = l;
+    m.r = r;
+    m.inv_r = 1.0 / r;
+    m.r_h = (float)r;
+    m.r_l = (float)(r - (double)m.r_h);
+    m.inv_rf = (float)m.inv_r;
+    m.pow2 = is_pow2_res(r) ? 1 : 0;
+}
+
+size_t map_bytes(uint32_t cap) { return align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)) + 256; }
+
+uint32_t *map_nvox_ptr(const Obj &o) { return (uint32_t *)((char *)o.map_mem + o.map_bytes - 256); }
+
+// Build voxelmaps for frame indices fidx[] into map indices midx[] (already allocated).
+vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const std::vector<uint32_t> &midx)
+{
+    const int nu = (int)fidx.size();
+    std::vector<BuildUnit> units(nu);
+    std::vector<int64_t> prefix(nu + 1, 0);
+    std::vector<WorkItem> items;
+    int64_t pts = 0;
+    const int chunk = 2048;
+    for (int u = 0; u < nu; ++u) {
+        const Obj &fo = ctx->objs[fidx[u]];
+        const Obj &mo = ctx->objs[midx[u]];
+        units[u].map = (int32_t)midx[u];
+        units[u].frame = (int32_t)fidx[u];
+        units[u].point_base = pts;
+        units[u].slot_base = prefix[u];
+        units[u].n_voxels = map_nvox_ptr(mo);
+        units[u].pad = 0;
+        prefix[u + 1] = prefix[u] + mo.cap;
+        for (int64_t s = 0; s < fo.n; s += chunk) {
+            WorkItem w;
+            w.unit = u;
+            w.start = s;
+            w.count = (int32_t)std::min<int64_t>(chunk, fo.n - s);
+            items.push_back(w);
+        }
+        pts += fo.n;
+    }
+    TRY(upload(ctx, ctx->ws_bunits, units.data(), units.size()));
+    TRY(upload(ctx, ctx->ws_bprefix, prefix.data(), prefix.size()));
+    TRY(upload(ctx, ctx->ws_bitems, items.data(), items.size()));
+    TRY(ensure(ctx, ctx->ws_slot_of_point, (size_t)pts * 4));
+    TRY(ensure(ctx, ctx->ws_acc, (size_t)pts * 80));
+    TRY(ensure(ctx, ctx->ws_vid_of_slot, (size_t)prefix[nu] * 4));
+    TRY(ensure(ctx, ctx->ws_slot_of_vid, (size_t)pts * 4));
+    BuildScratch scr;
+    scr.slot_of_point = (int32_t *)ctx->ws_slot_of_point.p;
+    scr.acc = (int64_t *)ctx->ws_acc.p;
+    scr.vid_of_slot = (int32_t *)ctx->ws_vid_of_slot.p;
+    scr.slot_of_vid = (int32_t *)ctx->ws_slot_of_vid.p;
+    const int grid = std::max(1, std::min<int>((int)items.size(), ctx->num_sms * 8));
+    launch_voxelmap_build(ctx->d_maps, ctx->d_frames, (const BuildUnit *)ctx->ws_bunits.p, nu,
+                          (const WorkItem *)ctx->ws_bitems.p, (int)items.size(), (const int64_t *)ctx->ws_bprefix.p,
+                          scr, grid, ctx->stream);
+    ctx->launches += 1 + (items.empty() ? 0 : 3);
+    CHECK_LAUNCH();
+    return VGICP_OK;
+}
+
+// Make sure map object idx has capacity for n points at resolution r.
+vgicp_status prepare_map(vgicp_ctx *ctx, uint32_t idx, int64_t n, double r)
+{
+    Obj &o = ctx->objs[idx];
+    const uint32_t cap = map_capacity(n);
+    if (o.map_mem == nullptr || o.cap < cap) {
+        const size_t bytes = map_bytes(cap);
+        TRY(budget_check(ctx, (int64_t)bytes - (int64_t)o.map_bytes));
+        if (o.map_mem) {
+            CU(cudaFreeAsync(o.map_mem, ctx->stream));
+            ctx->bytes_in_use -= (int64_t)o.map_bytes;
+            o.map_mem = nullptr;
+        }
+        CU(cudaMallocAsync(&o.map_mem, bytes, ctx->stream));
+        o.map_bytes = bytes;
+        o.cap = cap;
+        ctx->bytes_in_use += (int64_t)bytes;
+    }
+    o.r = r;
+    fill_map_desc(ctx->h_maps[idx], (char *)o.map_mem, o.cap, r);
+    TRY(put_map_desc(ctx, idx));
+    return VGICP_OK;
+}
+
+bool valid_res(double r) { return std::isfinite(r) && r > 0.0 && r < 1e30; }
+
+void split_host(const double *T, PoseParam &p)
+{
+    for (int i = 0; i < 12; ++i) p.T[i] = T[i];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            const double v = T[4 * i + j];
+            const float h = (float)v;
+            p.Rh[3 * i + j] = h;
+            p.Rl[3 * i + j] = (float)(v - (double)h);
+        }
+        const double v = T[4 * i + 3];
+        const float h = (float)v;
+        p.th[i] = h;
+        p.tl[i] = (float)(v - (double)h);
+    }
+    p.pad0 = p.pad1 = 0;
+}
+
+bool finite_pose(const double *T)
+{
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(T[i])) return false;
+    return true;
+}
+
+vgicp_status read_nvox(vgicp_ctx *ctx, const Obj &o, int64_t *n)
+{
+    uint32_t v = 0;
+    CU(cudaMemcpyAsync(&v, map_nvox_ptr(o), 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *n = v;
+    return VGICP_OK;
+}
+
+int default_chunk(const vgicp_options &o) { return o.chunk_points > 0 ? o.chunk_points : 2048; }
+int default_block(const vgicp_options &o) { return o.block_threads > 0 ? o.block_threads : 256; }
+
+// Work list for a factor set (cached while the set and the chunk size stay the same).
+vgicp_status get_plan(vgicp_ctx *ctx, const vgicp_factor *f, int64_t n_f, const std::vector<int32_t> &idx)
+{
+    Plan &P = ctx->plan;
+    const int chunk = default_chunk(ctx->opt);
+    bool same = P.chunk == chunk && (int64_t)P.key.size() == n_f &&
+                std::memcmp(P.key.data(), f, sizeof(vgicp_factor) * (size_t)n_f) == 0;
+    if (same) {
+        for (int64_t i = 0; i < n_f && same; ++i) same = P.frame_n[i] == ctx->objs[idx[4 * i + 1]].n;
+    }
+    if (same) {
+        // descriptor indices are embedded in the cached idx array; handles are
+        // validated by the caller, so the cached copy is still exact
+        return VGICP_OK;
+    }
+    std::vector<WorkItem> items;
+    std::vector<int32_t> begin(n_f + 1, 0);
+    P.frame_n.resize(n_f);
+    for (int64_t i = 0; i < n_f; ++i) {
+        const int64_t n = ctx->objs[idx[4 * i + 1]].n;
+        P.frame_n[i] = n;
+        begin[i] = (int32_t)items.size();
+        for (int64_t s = 0; s < n; s += chunk) {
+            WorkItem w;
+            w.unit = (int32_t)i;
+            w.start = s;
+            w.count = (int32_t)std::min<int64_t>(chunk, n - s);
+            items.push_back(w);
+        }
+    }
+    begin[n_f] = (int32_t)items.size();
+    TRY(upload(ctx, P.idx, idx.data(), idx.size()));
+    TRY(upload(ctx, P.items, items.data(), items.size()));
+    TRY(upload(ctx, P.item_begin, begin.data(), begin.size()));
+    P.key.assign(f, f + n_f);
+    P.chunk = chunk;
+    P.n_items = (int)items.size();
+    return VGICP_OK;
+}
+
+int occupancy_grid(vgicp_ctx *ctx, int block)
+{
+    int per_sm = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : std::max(1, 2048 / block);
+    return ctx->num_sms * per_sm;
+}
+
+}  // namespace
+
+extern "C" {
+
+vgicp_status vgicp_options_default(vgicp_options *opt)
+{
+    if (!opt) return VGICP_ERR_INVALID_ARG;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = VGICP_PREC_F32;
+    opt->chunk_points = 2048;
+    opt->block_threads = 256;
+    opt->blocks_per_sm = 0;
+    opt->hbm_budget_bytes = 0;
+    return VGICP_OK;
+}
+
+static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
+{
+    if (o->precision != VGICP_PREC_F32 && o->precision != VGICP_PREC_F64)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "precision must be VGICP_PREC_F32 or VGICP_PREC_F64");
+    if (o->chunk_points < 0 || (o->chunk_points % 32) != 0)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "chunk_points must be a non-negative multiple of 32");
+    if (o->block_threads != 0 && o->block_threads != 128 && o->block_threads != 256 && o->block_threads != 512)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "block_threads must be 0, 128, 256 or 512");
+    if (o->blocks_per_sm < 0 || o->hbm_budget_bytes < 0)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_create(vgicp_ctx **out, const vgicp_options *opt, void *cuda_stream)
+{
+    if (!out) return VGICP_ERR_INVALID_ARG;
+    *out = nullptr;
+    vgicp_ctx *ctx = new vgicp_ctx();
+    vgicp_options_default(&ctx->opt);
+    if (opt) {
+        vgicp_status s = check_options(ctx, opt);
+        if (s != VGICP_OK) { delete ctx; return s; }
+        ctx->opt = *opt;
+    }
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess && !cuda_stream) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        cudaMemPool_t pool;
+        e = cudaDeviceGetDefaultMemPool(&pool, ctx->device);
+        if (e == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
+    if (e != cudaSuccess) {
+        delete ctx;
+        return VGICP_ERR_CUDA;
+    }
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+    *out = ctx;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_destroy(vgicp_ctx *ctx)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    for (Obj &o : ctx->objs) {
+        if (o.frame_mem) cudaFreeAsync(o.frame_mem, ctx->stream);
+        if (o.map_mem) cudaFreeAsync(o.map_mem, ctx->stream);
+    }
+    Buf *bufs[] = {&ctx->ws_poses, &ctx->ws_params, &ctx->ws_partials, &ctx->ws_inl, &ctx->ws_out, &ctx->ws_f64,
+                   &ctx->ws_ticket, &ctx->ws_counts, &ctx->ws_stage, &ctx->ws_bunits, &ctx->ws_bitems,
+                   &ctx->ws_bprefix, &ctx->ws_slot_of_point, &ctx->ws_acc, &ctx->ws_vid_of_slot,
+                   &ctx->ws_slot_of_vid, &ctx->ws_pairs, &ctx->ws_fidx, &ctx->ws_midx, &ctx->ws_chunks,
+                   &ctx->ws_export_keys, &ctx->ws_export_rec, &ctx->ws_counter, &ctx->plan.idx,
+                   &ctx->plan.items, &ctx->plan.item_begin};
+    for (Buf *b : bufs) free_buf(ctx, *b);
+    if (ctx->d_maps) cudaFreeAsync(ctx->d_maps, ctx->stream);
+    if (ctx->d_frames) cudaFreeAsync(ctx->d_frames, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return e == cudaSuccess ? VGICP_OK : VGICP_ERR_CUDA;
+}
+
+vgicp_status vgicp_set_options(vgicp_ctx *ctx, const vgicp_options *opt)
+{
+    if (!ctx || !opt) return VGICP_ERR_INVALID_ARG;
+    TRY(check_options(ctx, opt));
+    ctx->opt = *opt;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_set_stream(vgicp_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+    if (!ctx->stream) {
+        CU(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+        ctx->stream = ctx->own_stream;
+    }
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_synchronize(vgicp_ctx *ctx)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return VGICP_OK;
+}
+
+// Stage host or device points / covariances in device memory (covs nullable).
+static vgicp_status stage_inputs(vgicp_ctx *ctx, const float *points, const float *covs, int64_t n, int mem_kind,
+                                 const float **d_pts, const float **d_cov)
+{
+    if (mem_kind == VGICP_MEM_DEVICE) {
+        *d_pts = points;
+        if (d_cov) *d_cov = covs;
+        return VGICP_OK;
+    }
+    const size_t pb = align256((size_t)n * 12), cb = covs ? (size_t)n * 24 : 0;
+    TRY(ensure(ctx, ctx->ws_stage, pb + cb));
+    char *base = (char *)ctx->ws_stage.p;
+    if (n) CU(cudaMemcpyAsync(base, points, (size_t)n * 12, cudaMemcpyHostToDevice, ctx->stream));
+    if (covs && n) CU(cudaMemcpyAsync(base + pb, covs, (size_t)n * 24, cudaMemcpyHostToDevice, ctx->stream));
+    *d_pts = (const float *)base;
+    if (d_cov) *d_cov = covs ? (const float *)(base + pb) : nullptr;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_add_frame(vgicp_ctx *ctx, const float *points, const float *covs, int64_t n, int mem_kind,
+                             vgicp_frame_t *out)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (!out || n < 0 || (n > 0 && (!points || !covs)))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frame: null pointer or negative size");
+    if (mem_kind != VGICP_MEM_HOST && mem_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frame: bad mem_kind %d", mem_kind);
+    if (n > ((int64_t)1 << 31) - 1) return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frame: n >= 2^31");
+    const float *dp, *dc;
+    TRY(stage_inputs(ctx, points, covs, n, mem_kind, &dp, &dc));
+    uint32_t idx;
+    TRY(make_frame(ctx, dp, dc, n, &idx));
+    *out = make_handle(idx, ctx->objs[idx].gen);
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_frame_size(vgicp_ctx *ctx, vgicp_frame_t frame, int64_t *n)
+{
+    if (!ctx || !n) return VGICP_ERR_INVALID_ARG;
+    Obj *o = lookup(ctx, frame, Obj::FRAME);
+    if (!o) return fail(ctx, VGICP_ERR_NOT_FOUND, "frame handle %lld not found", (long long)frame);
+    *n = o->n;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_build_voxelmaps(vgicp_ctx *ctx, const vgicp_frame_t *frames, int64_t n, double resolution,
+                                   vgicp_map_t *maps)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!frames || !maps))) return fail(ctx, VGICP_ERR_INVALID_ARG, "build_voxelmaps: bad arguments");
+    if (!valid_res(resolution)) return fail(ctx, VGICP_ERR_INVALID_ARG, "resolution must be finite and > 0");
+    std::vector<uint32_t> fidx(n), midx(n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!lookup(ctx, frames[i], Obj::FRAME, &fidx[i]))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "frame handle %lld not found", (long long)frames[i]);
+        if (maps[i] >= 0 && !lookup(ctx, maps[i], Obj::MAP, &midx[i]))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)maps[i]);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (maps[i] < 0) {
+            TRY(new_obj(ctx, Obj::MAP, &midx[i]));
+            maps[i] = make_handle(midx[i], ctx->objs[midx[i]].gen);
+        }
+        TRY(prepare_map(ctx, midx[i], ctx->objs[fidx[i]].n, resolution));
+    }
+    if (n == 0) return VGICP_OK;
+    return run_build(ctx, fidx, midx);
+}
+
+vgicp_status vgicp_build_voxelmap(vgicp_ctx *ctx, const float *points, const float *covs, int64_t n,
+                                  double resolution, int mem_kind, vgicp_map_t *out)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (!out || n < 0 || (n > 0 && (!points || !covs)))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "build_voxelmap: null pointer or negative size");
+    if (!valid_res(resolution)) return fail(ctx, VGICP_ERR_INVALID_ARG, "resolution must be finite and > 0");
+    vgicp_frame_t fr;
+    TRY(vgicp_add_frame(ctx, points, covs, n, mem_kind, &fr));
+    vgicp_map_t m = -1;
+    vgicp_status s = vgicp_build_voxelmaps(ctx, &fr, 1, resolution, &m);
+    vgicp_release(ctx, fr);
+    if (s != VGICP_OK) return s;
+    *out = m;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_voxelmap_size(vgicp_ctx *ctx, vgicp_map_t map, int64_t *n_voxels)
+{
+    if (!ctx || !n_voxels) return VGICP_ERR_INVALID_ARG;
+    Obj *o = lookup(ctx, map, Obj::MAP);
+    if (!o) return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)map);
+    return read_nvox(ctx, *o, n_voxels);
+}
+
+vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
+                             int64_t n_poses, double *H, double *b, double *cost, int64_t *inliers, int out_kind)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n_f < 0 || n_poses < 0 || (n_f > 0 && (!factors || !H || !b || !cost)) || (n_poses > 0 && !poses))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: null pointer or negative size");
+    if (out_kind != VGICP_MEM_HOST && out_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: bad out_kind %d", out_kind);
+    if (n_f == 0) return VGICP_OK;
+    if (n_f > (1 << 30)) return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: too many factors");
+    std::vector<int32_t> idx((size_t)n_f * 4);
+    for (int64_t i = 0; i < n_f; ++i) {
+        uint32_t mi, fi;
+        if (!lookup(ctx, factors[i].target, Obj::MAP, &mi))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "factor %lld: map handle %lld not found", (long long)i,
+                        (long long)factors[i].target);
+        if (!lookup(ctx, factors[i].source, Obj::FRAME, &fi))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "factor %lld: frame handle %lld not found", (long long)i,
+                        (long long)factors[i].source);
+        if (factors[i].target_pose < 0 || factors[i].target_pose >= n_poses || factors[i].source_pose < 0 ||
+            factors[i].source_pose >= n_poses)
+            return fail(ctx, VGICP_ERR_INVALID_ARG, "factor %lld: pose index out of range", (long long)i);
+        idx[4 * i + 0] = (int32_t)mi;
+        idx[4 * i + 1] = (int32_t)fi;
+        idx[4 * i + 2] = factors[i].target_pose;
+        idx[4 * i + 3] = factors[i].source_pose;
+    }
+    for (int64_t i = 0; i < n_poses * 12; ++i)
+        if (!std::isfinite(poses[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: non-finite pose entry");
+    TRY(upload(ctx, ctx->ws_poses, poses, (size_t)n_poses * 12));
+    TRY(get_plan(ctx, factors, n_f, idx));
+    Plan &P = ctx->plan;
+    TRY(ensure(ctx, ctx->ws_params, (size_t)n_f * sizeof(PoseParam)));
+    PoseParam *d_params = (PoseParam *)ctx->ws_params.p;
+    launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)ctx->ws_poses.p, d_params, ctx->stream);
+    ctx->launches += 1;
+    CHECK_LAUNCH();
+    // outputs: caller's device buffers, or a device workspace copied back to the host
+    double *dH = H, *db = b, *dc = cost;
+    int64_t *di = inliers;
+    const size_t out_bytes = (size_t)n_f * (144 + 12 + 1) * 8 + (size_t)n_f * 8;
+    if (out_kind == VGICP_MEM_HOST) {
+        TRY(ensure(ctx, ctx->ws_out, out_bytes));
+        dH = (double *)ctx->ws_out.p;
+        db = dH + n_f * 144;
+        dc = db + n_f * 12;
+        di = (int64_t *)(dc + n_f);
+    }
+    if (ctx->opt.precision == VGICP_PREC_F64) {
+        const int blk = linearize_f64_block();
+        int max_grid = ctx->num_sms * 16;
+        TRY(ensure(ctx, ctx->ws_f64, (size_t)max_grid * 92 * 8));
+        TRY(ensure(ctx, ctx->ws_ticket, 4));
+        CU(cudaMemsetAsync(ctx->ws_ticket.p, 0, 4, ctx->stream));
+        for (int64_t i = 0; i < n_f; ++i) {
+            const int64_t n = ctx->objs[idx[4 * i + 1]].n;
+            int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, (n + blk - 1) / blk));
+            launch_linearize_f64(d_params + i, ctx->d_maps, ctx->d_frames, n, (double *)ctx->ws_f64.p,
+                                 (unsigned int *)ctx->ws_ticket.p, dH + 144 * i, db + 12 * i, dc + i,
+                                 di ? di + i : nullptr, grid, ctx->stream);
+        }
+        ctx->launches += n_f;
+        CHECK_LAUNCH();
+    } else {
+        const int block = default_block(ctx->opt);
+        TRY(ensure(ctx, ctx->ws_partials, (size_t)std::max(1, P.n_items) * 28 * 8));
+        TRY(ensure(ctx, ctx->ws_inl, (size_t)std::max(1, P.n_items) * 8));
+        const int grid = std::max(1, std::min(P.n_items, occupancy_grid(ctx, block)));
+        launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
+                             (double *)ctx->ws_partials.p, (int64_t *)ctx->ws_inl.p, block, grid, ctx->stream);
+        launch_reduce_finalize(d_params, (const int32_t *)P.item_begin.p, (int)n_f, (const double *)ctx->ws_partials.p,
+                               (const int64_t *)ctx->ws_inl.p, dH, db, dc, di, ctx->stream);
+        ctx->launches += (P.n_items > 0) + 1;
+        CHECK_LAUNCH();
+    }
+    if (out_kind == VGICP_MEM_HOST) {
+        CU(cudaMemcpyAsync(H, dH, (size_t)n_f * 144 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(b, db, (size_t)n_f * 12 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(cost, dc, (size_t)n_f * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        if (inliers) CU(cudaMemcpyAsync(inliers, di, (size_t)n_f * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t target, const double *T, double *fraction,
+                           int64_t *count)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (!T || !fraction) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap: null pointer");
+    uint32_t fi, mi;
+    Obj *fo = lookup(ctx, source, Obj::FRAME, &fi);
+    if (!fo) return fail(ctx, VGICP_ERR_NOT_FOUND, "frame handle %lld not found", (long long)source);
+    if (!lookup(ctx, target, Obj::MAP, &mi))
+        return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)target);
+    if (!finite_pose(T)) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap: non-finite pose");
+    const int64_t n = fo->n;
+    if (n == 0) return fail(ctx, VGICP_ERR_EMPTY, "overlap of an empty source is undefined (Eq. 8)");
+    PoseParam p;
+    split_host(T, p);
+    p.map = (int32_t)mi;
+    p.frame = (int32_t)fi;
+    std::vector<WorkItem> items;
+    for (int64_t s = 0; s < n; s += 4096) {
+        WorkItem w;
+        w.unit = 0;
+        w.start = s;
+        w.count = (int32_t)std::min<int64_t>(4096, n - s);
+        items.push_back(w);
+    }
+    TRY(upload(ctx, ctx->ws_pairs, &p, 1));
+    TRY(upload(ctx, ctx->ws_chunks, items.data(), items.size()));
+    TRY(ensure(ctx, ctx->ws_counts, 8));
+    CU(cudaMemsetAsync(ctx->ws_counts.p, 0, 8, ctx->stream));
+    const int grid = std::max(1, std::min((int)items.size(), ctx->num_sms * 8));
+    launch_overlap((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames, (const WorkItem *)ctx->ws_chunks.p,
+                   (int)items.size(), (unsigned long long *)ctx->ws_counts.p, grid, ctx->stream);
+    ctx->launches += 1;
+    CHECK_LAUNCH();
+    unsigned long long c = 0;
+    CU(cudaMemcpyAsync(&c, ctx->ws_counts.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (count) *count = (int64_t)c;
+    *fraction = (double)c / (double)n;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, int64_t n_src,
+                                  const vgicp_map_t *targets, int64_t n_tgt, const double *poses_src,
+                                  const double *poses_tgt, int64_t *counts, int out_kind)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n_src < 0 || n_tgt < 0 || (n_src > 0 && (!sources || !poses_src)) || (n_tgt > 0 && (!targets || !poses_tgt)) ||
+        (n_src * n_tgt > 0 && !counts))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: null pointer or negative size");
+    if (out_kind != VGICP_MEM_HOST && out_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: bad out_kind %d", out_kind);
+    const int64_t n_pairs = n_src * n_tgt;
+    if (n_pairs == 0) return VGICP_OK;
+    if (n_pairs > (int64_t)1 << 30) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: too many pairs");
+    std::vector<int32_t> fidx(n_src), midx(n_tgt);
+    std::vector<int64_t> nsrc(n_src);
+    for (int64_t i = 0; i < n_src; ++i) {
+        uint32_t k;
+        Obj *o = lookup(ctx, sources[i], Obj::FRAME, &k);
+        if (!o) return fail(ctx, VGICP_ERR_NOT_FOUND, "frame handle %lld not found", (long long)sources[i]);
+        fidx[i] = (int32_t)k;
+        nsrc[i] = o->n;
+    }
+    for (int64_t i = 0; i < n_tgt; ++i) {
+        uint32_t k;
+        if (!lookup(ctx, targets[i], Obj::MAP, &k))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)targets[i]);
+        midx[i] = (int32_t)k;
+    }
+    for (int64_t i = 0; i < n_src * 12; ++i)
+        if (!std::isfinite(poses_src[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
+    for (int64_t i = 0; i < n_tgt * 12; ++i)
+        if (!std::isfinite(poses_tgt[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
+    // source chunks; the kernel enumerates (target tile, chunk, target) so the
+    // CTAs in flight share a few target tables and a few source chunks
+    const int chunk = 4096, tile = 16;
+    std::vector<WorkItem> chunks;
+    for (int64_t s = 0; s < n_src; ++s)
+        for (int64_t o = 0; o < nsrc[s]; o += chunk) {
+            WorkItem w;
+            w.unit = (int32_t)s;
+            w.start = o;
+            w.count = (int32_t)std::min<int64_t>(chunk, nsrc[s] - o);
+            chunks.push_back(w);
+        }
+    TRY(upload(ctx, ctx->ws_poses, poses_src, (size_t)n_src * 12));
+    TRY(ensure(ctx, ctx->ws_stage, (size_t)n_tgt * 12 * 8));
+    CU(cudaMemcpyAsync(ctx->ws_stage.p, poses_tgt, (size_t)n_tgt * 12 * 8, cudaMemcpyHostToDevice, ctx->stream));
+    TRY(upload(ctx, ctx->ws_fidx, fidx.data(), fidx.size()));
+    TRY(upload(ctx, ctx->ws_midx, midx.data(), midx.size()));
+    TRY(upload(ctx, ctx->ws_chunks, chunks.data(), chunks.size()));
+    TRY(ensure(ctx, ctx->ws_pairs, (size_t)n_pairs * sizeof(PoseParam)));
+    launch_prepare_pairs((const double *)ctx->ws_poses.p, (const double *)ctx->ws_stage.p,
+                         (const int32_t *)ctx->ws_fidx.p, (const int32_t *)ctx->ws_midx.p, (int)n_src, (int)n_tgt,
+                         (PoseParam *)ctx->ws_pairs.p, ctx->stream);
+    unsigned long long *dcounts = (unsigned long long *)counts;
+    if (out_kind == VGICP_MEM_HOST) {
+        TRY(ensure(ctx, ctx->ws_counts, (size_t)n_pairs * 8));
+        dcounts = (unsigned long long *)ctx->ws_counts.p;
+    }
+    CU(cudaMemsetAsync(dcounts, 0, (size_t)n_pairs * 8, ctx->stream));
+    const int grid = ctx->num_sms * 8;
+    launch_overlap_matrix((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames,
+                          (const WorkItem *)ctx->ws_chunks.p, (int)chunks.size(), (int)n_tgt, tile, dcounts, grid,
+                          ctx->stream);
+    ctx->launches += 2;
+    CHECK_LAUNCH();
+    if (out_kind == VGICP_MEM_HOST) {
+        CU(cudaMemcpyAsync(counts, dcounts, (size_t)n_pairs * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_debug_correspondences(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t target, const double *T,
+                                         int64_t *keys, int32_t *hit)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (!T) return fail(ctx, VGICP_ERR_INVALID_ARG, "debug_correspondences: null pose");
+    uint32_t fi, mi;
+    Obj *fo = lookup(ctx, source, Obj::FRAME, &fi);
+    if (!fo) return fail(ctx, VGICP_ERR_NOT_FOUND, "frame handle %lld not found", (long long)source);
+    if (!lookup(ctx, target, Obj::MAP, &mi))
+        return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)target);
+    const int64_t n = fo->n;
+    if (n == 0) return VGICP_OK;
+    PoseParam p;
+    split_host(T, p);
+    p.map = (int32_t)mi;
+    p.frame = (int32_t)fi;
+    TRY(upload(ctx, ctx->ws_pairs, &p, 1));
+    TRY(ensure(ctx, ctx->ws_out, (size_t)n * (24 + 4)));
+    int64_t *dk = (int64_t *)ctx->ws_out.p;
+    int32_t *dh = (int32_t *)(dk + 3 * n);
+    launch_correspondences((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames, n, dk, dh, ctx->stream);
+    ctx->launches += 1;
+    CHECK_LAUNCH();
+    if (keys) CU(cudaMemcpyAsync(keys, dk, (size_t)n * 24, cudaMemcpyDeviceToHost, ctx->stream));
+    if (hit) CU(cudaMemcpyAsync(hit, dh, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_export_voxelmap(vgicp_ctx *ctx, vgicp_map_t map, int64_t *keys, int64_t *counts, double *mu,
+                                   double *cov, int64_t *n_voxels)
+{
+    if (!ctx || !n_voxels) return VGICP_ERR_INVALID_ARG;
+    uint32_t mi;
+    Obj *o = lookup(ctx, map, Obj::MAP, &mi);
+    if (!o) return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)map);
+    int64_t nv;
+    TRY(read_nvox(ctx, *o, &nv));
+    const int64_t capacity = *n_voxels;
+    *n_voxels = nv;
+    if (!keys && !counts && !mu && !cov) return VGICP_OK;
+    if (capacity < nv) return fail(ctx, VGICP_ERR_INVALID_ARG, "export: capacity %lld < %lld voxels",
+                                   (long long)capacity, (long long)nv);
+    TRY(ensure(ctx, ctx->ws_export_keys, (size_t)std::max<int64_t>(nv, 1) * 8));
+    TRY(ensure(ctx, ctx->ws_export_rec, (size_t)std::max<int64_t>(nv, 1) * sizeof(VoxelRec)));
+    TRY(ensure(ctx, ctx->ws_counter, 4));
+    CU(cudaMemsetAsync(ctx->ws_counter.p, 0, 4, ctx->stream));
+    launch_export_voxels(ctx->d_maps + mi, o->cap, (uint32_t *)ctx->ws_counter.p, (uint64_t *)ctx->ws_export_keys.p,
+                         (VoxelRec *)ctx->ws_export_rec.p, ctx->stream);
+    ctx->launches += 1;
+    CHECK_LAUNCH();
+    std::vector<uint64_t> hk(nv);
+    std::vector<VoxelRec> hr(nv);
+    if (nv) {
+        CU(cudaMemcpyAsync(hk.data(), ctx->ws_export_keys.p, (size_t)nv * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(hr.data(), ctx->ws_export_rec.p, (size_t)nv * sizeof(VoxelRec), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    std::vector<int64_t> order(nv);
+    for (int64_t i = 0; i < nv; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return hk[a] < hk[b]; });
+    const double r = o->r;
+    for (int64_t j = 0; j < nv; ++j) {
+        const uint64_t k = hk[order[j]];
+        const VoxelRec &v = hr[order[j]];
+        const int64_t kk[3] = {(int64_t)((k >> 42) & 0x1FFFFF) - kKeyOffset, (int64_t)((k >> 21) & 0x1FFFFF) - kKeyOffset,
+                               (int64_t)(k & 0x1FFFFF) - kKeyOffset};
+        if (keys) for (int a = 0; a < 3; ++a) keys[3 * j + a] = kk[a];
+        uint32_t cnt;
+        std::memcpy(&cnt, &v.c.y, 4);
+        if (counts) counts[j] = cnt;
+        if (mu) {
+            mu[3 * j + 0] = (double)kk[0] * r + (double)v.a.x;
+            mu[3 * j + 1] = (double)kk[1] * r + (double)v.a.y;
+            mu[3 * j + 2] = (double)kk[2] * r + (double)v.a.z;
+        }
+        if (cov) {
+            cov[6 * j + 0] = v.a.w; cov[6 * j + 1] = v.b.x; cov[6 * j + 2] = v.b.y;
+            cov[6 * j + 3] = v.b.z; cov[6 * j + 4] = v.b.w; cov[6 * j + 5] = v.c.x;
+        }
+    }
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_estimate_covariances(vgicp_ctx *ctx, const float *points, int64_t n, int32_t k, double eps,
+                                        float *covs_out, int mem_kind)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!points || !covs_out)) || k < 1 || k > 32 || !std::isfinite(eps))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "estimate_covariances: bad arguments");
+    if (mem_kind != VGICP_MEM_HOST && mem_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "estimate_covariances: bad mem_kind");
+    if (n == 0) return VGICP_OK;
+    const float *dp;
+    TRY(stage_inputs(ctx, points, nullptr, n, mem_kind, &dp, nullptr));
+    float *dc = covs_out;
+    if (mem_kind == VGICP_MEM_HOST) {
+        TRY(ensure(ctx, ctx->ws_out, (size_t)n * 24));
+        dc = (float *)ctx->ws_out.p;
+    }
+    launch_knn_covariances(dp, n, k, eps, dc, ctx->stream);
+    ctx->launches += 1;
+    CHECK_LAUNCH();
+    if (mem_kind == VGICP_MEM_HOST) {
+        CU(cudaMemcpyAsync(covs_out, dc, (size_t)n * 24, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_release(vgicp_ctx *ctx, int64_t handle)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    uint32_t idx;
+    Obj *o = lookup(ctx, handle, Obj::FRAME, &idx);
+    if (!o) o = lookup(ctx, handle, Obj::MAP, &idx);
+    if (!o) return fail(ctx, VGICP_ERR_NOT_FOUND, "handle %lld not found", (long long)handle);
+    if (o->frame_mem) CU(cudaFreeAsync(o->frame_mem, ctx->stream));
+    if (o->map_mem) CU(cudaFreeAsync(o->map_mem, ctx->stream));
+    ctx->bytes_in_use -= (int64_t)(o->frame_bytes + o->map_bytes);
+    const uint32_t gen = o->gen;
+    *o = Obj();
+    o->gen = gen;
+    ctx->free_idx.push_back(idx);
+    ctx->plan.key.clear();   // a cached work list may name this handle
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_memory_in_use(vgicp_ctx *ctx, int64_t *bytes)
+{
+    if (!ctx || !bytes) return VGICP_ERR_INVALID_ARG;
+    *bytes = ctx->bytes_in_use;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_kernel_launches(vgicp_ctx *ctx, int64_t *count)
+{
+    if (!ctx || !count) return VGICP_ERR_INVALID_ARG;
+    *count = ctx->launches;
+    return VGICP_OK;
+}
+
+const char *vgicp_last_error(const vgicp_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+const char *vgicp_status_string(vgicp_status s)
+{
+    switch (s) {
+    case VGICP_OK: return "VGICP_OK";
+    case VGICP_ERR_INVALID_ARG: return "VGICP_ERR_INVALID_ARG";
+    case VGICP_ERR_OOM: return "VGICP_ERR_OOM";
+    case VGICP_ERR_NOT_FOUND: return "VGICP_ERR_NOT_FOUND";
+    case VGICP_ERR_EMPTY: return "VGICP_ERR_EMPTY";
+    case VGICP_ERR_CUDA: return "VGICP_ERR_CUDA";
+    case VGICP_ERR_TIMEOUT: return "VGICP_ERR_TIMEOUT";
+    case VGICP_ERR_BUDGET: return "VGICP_ERR_BUDGET";
+    }
+    return "unknown";
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Host-side launchers of the VGICP kernels (declarations shared by the .cu files).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vgicp_internal.cuh"
+
+namespace vg {
+
+// A work item: `count` consecutive points of one unit (a map being built, a
+// factor, or an overlap pair) starting at point `start` of that unit's frame.
+struct __align__(16) WorkItem {
+    int32_t unit;
+    int32_t count;
+    int64_t start;
+};
+
+// ----------------------------------------------------------- frames ------
+// Re-lay n points (n x 3) and covariances (n x 6) into the three frame streams
+// and compute the frame's max |covariance entry| (cmax must be zeroed).
+void launch_frame_pack(const float *points, const float *covs, int64_t n, float4 *pa, float4 *pb, float *pc,
+                       float *cmax, cudaStream_t st);
+
+// ----------------------------------------------------------- voxelmaps ---
+// Scratch of a batched build: per point the slot it went to; per voxel the
+// exact fixed-point sums; per map the voxel counter.
+struct BuildScratch {
+    int32_t *slot_of_point;   // total points
+    int64_t *acc;             // 10 x total points (worst case: every point its own voxel)
+    int32_t *vid_of_slot;     // total capacity
+    int32_t *slot_of_vid;     // total points
+};
+
+struct BuildUnit {
+    int32_t map;         // index into the MapDesc table
+    int32_t frame;       // index into the FrameDesc table
+    int64_t point_base;  // offset of this unit's points in the scratch arrays
+    int64_t slot_base;   // offset of this unit's slots in vid_of_slot
+    uint32_t *n_voxels;  // the map's voxel counter (in the map's own allocation)
+    int64_t pad;
+};
+
+void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const BuildUnit *units, int n_units,
+                           const WorkItem *items, int n_items, const int64_t *slot_items /* n_units+1 prefix */,
+                           BuildScratch scr, int grid, cudaStream_t st);
+
+// ----------------------------------------------------------- linearise ---
+// Relative poses T_BA = T_B^-1 T_A for every factor, in the forms the kernels use.
+void launch_prepare_factors(const int32_t *factor_idx /* n_f x 4: map, frame, pose_t, pose_s */, int n_f,
+                            const double *poses, PoseParam *out, cudaStream_t st);
+
+// Batched float32 path: one persistent launch over all work items; each item
+// writes 28 float64 partial sums and an inlier count.
+void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
+                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
+                          int block, int grid, cudaStream_t st);
+
+// Per-factor fixed-order float64 reduction of the item partials and expansion
+// to the 12x12 H, b, cost.  item_begin has n_f + 1 entries.
+void launch_reduce_finalize(const PoseParam *params, const int32_t *item_begin, int n_f, const double *partials,
+                            const int64_t *inl_partials, double *H, double *b, double *cost, int64_t *inliers,
+                            cudaStream_t st);
+
+// Plain float64 path for one factor (literal Jacobians, 78 unique H entries).
+// scratch holds grid x 92 doubles; ticket is one zeroed int (reset by the kernel).
+void launch_linearize_f64(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,
+                          double *scratch, unsigned int *ticket, double *H, double *b, double *cost,
+                          int64_t *inliers, int grid, cudaStream_t st);
+int linearize_f64_block();
+
+// ----------------------------------------------------------- overlap -----
+// counts[unit] += #hits of the unit's points (counts must be zeroed).
+void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
+                    int n_items, unsigned long long *counts, int grid, cudaStream_t st);
+
+// Overlap matrix: counts[s * n_tgt + t] += hits of source s against target t.
+// chunks lists every source's point chunks (unit = source index); the items are
+// implied: target tiles outermost, then chunks, then the targets of the tile.
+void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames,
+                           const WorkItem *chunks, int n_chunks, int n_tgt, int tile, unsigned long long *counts,
+                           int grid, cudaStream_t st);
+
+// Pair parameters of an overlap matrix: pair (s, t) -> T_t^-1 T_s.
+void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, const int32_t *frame_idx,
+                          const int32_t *map_idx, int n_src, int n_tgt, PoseParam *out, cudaStream_t st);
+
+// Per-point association (debug / parity): keys n x 3 (INT64_MIN if invalid), hit n.
+void launch_correspondences(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,
+                            int64_t *keys, int32_t *hit, cudaStream_t st);
+
+// Export: gather the occupied slots of a map (compacted, unordered).
+void launch_export_voxels(const MapDesc *map_dev, uint32_t cap, uint32_t *counter, uint64_t *keys_out,
+                          VoxelRec *rec_out, cudaStream_t st);
+
+// ----------------------------------------------------------- covariances --
+void launch_knn_covariances(const float *points, int64_t n, int k, double eps, float *covs, cudaStream_t st);
+
+}  // namespace vg

@@ -1,0 +1,534 @@
+// Linearisation of VGICP matching-cost factors (Eq. 3-6).
+//
+// Batched float32 path (one persistent launch for all factors)
+//   With a = R p (the source point rotated into the target frame) and
+//   J^t = [-[a]x, I], the paper's Jacobians factor as
+//       J_B = J^t S,  S = [[I, 0], [-[t]x, I]],
+//       J_A = -J^t D, D = blkdiag(R, R)
+//   (q = a + t; R[p]x = [a]x R).  So every point only adds to
+//       H^t = sum J^t' Omega J^t   (21 unique entries)
+//       b^t = sum J^t' Omega e     (6)
+//       cost = sum e' Omega e      (1)
+//   and the per-factor 12x12 system is exactly
+//       H = [[S' H^t S, -S' H^t D], [-D' H^t S, D' H^t D]],  b = [S' b^t ; -D' b^t],
+//   formed once per factor in float64.  Accumulating about the translation
+//   (lever arm a instead of q) keeps the float32 sums free of |t|-sized terms.
+//   Per-point work is float32; the voxel floor and the residual offset inside
+//   the voxel come from an error-free float32-pair transform (float64 fallback at
+//   faces).  Each work item (a chunk of one factor's points) writes its 28 sums
+//   as float64; a second kernel adds a factor's item sums in fixed order.
+//
+// Plain float64 path (one launch per factor)
+//   Literal 3x12 Jacobian J = [-[q]x, I | R[p]x, -R], all 78 unique entries of
+//   J' Omega J, 12 of J' Omega e and the cost, per point, in float64.
+#include "kernels.cuh"
+
+namespace vg {
+
+namespace {
+
+constexpr int kNT = 28;   // accumulated values per point (batched path)
+
+__device__ __forceinline__ void rel_pose(const double *__restrict__ TB, const double *__restrict__ TA, double *T)
+{
+    // T_BA = T_B^-1 T_A; every product and sum separately rounded, k = 0, 1, 2.
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s = __dadd_rn(s, __dmul_rn(TB[4 * k + i], TA[4 * k + j]));
+            T[4 * i + j] = s;
+        }
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s = __dadd_rn(s, __dmul_rn(TB[4 * k + i], __dsub_rn(TA[4 * k + 3], TB[4 * k + 3])));
+        T[4 * i + 3] = s;
+    }
+}
+
+__device__ __forceinline__ void split_pose(const double *T, PoseParam &p)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double v = T[4 * i + j];
+            const float h = __double2float_rn(v);
+            p.Rh[3 * i + j] = h;
+            p.Rl[3 * i + j] = __double2float_rn(v - (double)h);
+        }
+        const double v = T[4 * i + 3];
+        const float h = __double2float_rn(v);
+        p.th[i] = h;
+        p.tl[i] = __double2float_rn(v - (double)h);
+    }
+}
+
+__global__ void k_prepare_factors(const int32_t *__restrict__ idx, int n_f, const double *__restrict__ poses,
+                                  PoseParam *__restrict__ out)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n_f) return;
+    PoseParam p;
+    rel_pose(poses + 12 * (int64_t)idx[4 * f + 2], poses + 12 * (int64_t)idx[4 * f + 3], p.T);
+    split_pose(p.T, p);
+    p.map = idx[4 * f + 0];
+    p.frame = idx[4 * f + 1];
+    p.pad0 = p.pad1 = 0;
+    out[f] = p;
+}
+
+__global__ void k_prepare_pairs(const double *__restrict__ ps, const double *__restrict__ pt,
+                                const int32_t *__restrict__ fidx, const int32_t *__restrict__ midx, int n_src,
+                                int n_tgt, PoseParam *__restrict__ out)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)n_src * n_tgt) return;
+    const int s = (int)(g / n_tgt), t = (int)(g % n_tgt);
+    PoseParam p;
+    rel_pose(pt + 12 * (int64_t)t, ps + 12 * (int64_t)s, p.T);
+    split_pose(p.T, p);
+    p.map = midx[t];
+    p.frame = fidx[s];
+    p.pad0 = p.pad1 = 0;
+    out[g] = p;
+}
+
+// Voxel coordinate and in-voxel offset of one point (batched path).
+__device__ __forceinline__ bool point_key_ff(const PoseParam &P, const MapDesc &m, float px, float py, float pz,
+                                             int k[3], float d[3])
+{
+    bool decided = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        decided &= axis_key_ff(P.Rh + 3 * a, P.Rl + 3 * a, P.th[a], P.tl[a], px, py, pz, m.r_h, m.r_l, m.inv_rf,
+                               k[a], d[a]);
+    if (decided) return k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN;
+    double q[3];
+    if (!key_f64(P.T, px, py, pz, m.inv_r, k, q)) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = __double2float_rn(q[a] - (double)k[a] * m.r);
+    return true;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_linearize_f32(const PoseParam *__restrict__ params,
+                                                         const MapDesc *__restrict__ maps,
+                                                         const FrameDesc *__restrict__ frames,
+                                                         const WorkItem *__restrict__ items, int n_items,
+                                                         double *__restrict__ partials,
+                                                         int64_t *__restrict__ inl_partials)
+{
+    constexpr int NW = BLOCK / 32;
+    __shared__ PoseParam sP;
+    __shared__ MapDesc sM;
+    __shared__ FrameDesc sF;
+    __shared__ float sRed[NW][kNT];
+    __shared__ int sInl[NW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        __syncthreads();   // previous item's readers of sP/sM/sF are done
+        if (threadIdx.x == 0) {
+            sP = params[w.unit];
+            sM = maps[sP.map];
+            sF = frames[sP.frame];
+        }
+        __syncthreads();
+        const PoseParam &P = sP;
+        const MapDesc m = sM;
+        const float R0 = P.Rh[0], R1 = P.Rh[1], R2 = P.Rh[2], R3 = P.Rh[3], R4 = P.Rh[4], R5 = P.Rh[5],
+                    R6 = P.Rh[6], R7 = P.Rh[7], R8 = P.Rh[8];
+        float acc[kNT];
+#pragma unroll
+        for (int j = 0; j < kNT; ++j) acc[j] = 0.f;
+        int inl = 0;
+        const float4 *__restrict__ pa = sF.pa;
+        const float4 *__restrict__ pb = sF.pb;
+        const float *__restrict__ pc = sF.pc;
+        const int64_t end = w.start + w.count;
+        for (int64_t i = w.start + threadIdx.x; i < end; i += BLOCK) {
+            const float4 A = __ldg(pa + i);
+            const float4 B = __ldg(pb + i);
+            const float C22 = __ldg(pc + i);
+            int k[3];
+            float d[3];
+            if (!point_key_ff(P, m, A.x, A.y, A.z, k, d)) continue;
+            const int slot = probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2]));
+            if (slot < 0) continue;
+            const VoxelRec v = m.rec[slot];
+            // residual e = mu_B - q, both relative to the voxel's lower corner
+            const float e0 = v.a.x - d[0], e1 = v.a.y - d[1], e2 = v.a.z - d[2];
+            // R C_A (C_A symmetric: c00 c01 c02 / c11 c12 / c22)
+            const float a00 = A.w, a01 = B.x, a02 = B.y, a11 = B.z, a12 = B.w, a22 = C22;
+            const float T00 = R0 * a00 + R1 * a01 + R2 * a02, T01 = R0 * a01 + R1 * a11 + R2 * a12,
+                        T02 = R0 * a02 + R1 * a12 + R2 * a22;
+            const float T10 = R3 * a00 + R4 * a01 + R5 * a02, T11 = R3 * a01 + R4 * a11 + R5 * a12,
+                        T12 = R3 * a02 + R4 * a12 + R5 * a22;
+            const float T20 = R6 * a00 + R7 * a01 + R8 * a02, T21 = R6 * a01 + R7 * a11 + R8 * a12,
+                        T22 = R6 * a02 + R7 * a12 + R8 * a22;
+            // M = C_B + (R C_A) R^T
+            const float m00 = v.a.w + T00 * R0 + T01 * R1 + T02 * R2;
+            const float m01 = v.b.x + T00 * R3 + T01 * R4 + T02 * R5;
+            const float m02 = v.b.y + T00 * R6 + T01 * R7 + T02 * R8;
+            const float m11 = v.b.z + T10 * R3 + T11 * R4 + T12 * R5;
+            const float m12 = v.b.w + T10 * R6 + T11 * R7 + T12 * R8;
+            const float m22 = v.c.x + T20 * R6 + T21 * R7 + T22 * R8;
+            // Omega = M^-1 by the adjugate
+            const float c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+            const float c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
+            const float det = m00 * c00 + m01 * c01 + m02 * c02;
+            if (!(det > 0.f)) continue;
+            const float id = 1.f / det;
+            const float o00 = c00 * id, o01 = c01 * id, o02 = c02 * id, o11 = c11 * id, o12 = c12 * id,
+                        o22 = c22 * id;
+            // w = Omega e, cost = e . w
+            const float w0 = o00 * e0 + o01 * e1 + o02 * e2;
+            const float w1 = o01 * e0 + o11 * e1 + o12 * e2;
+            const float w2 = o02 * e0 + o12 * e1 + o22 * e2;
+            // lever arm a = R p
+            const float x0 = R0 * A.x + R1 * A.y + R2 * A.z;
+            const float x1 = R3 * A.x + R4 * A.y + R5 * A.z;
+            const float x2 = R6 * A.x + R7 * A.y + R8 * A.z;
+            // P = [a]x Omega  (= H_wv contribution)
+            const float P00 = x1 * o02 - x2 * o01, P01 = x1 * o12 - x2 * o11, P02 = x1 * o22 - x2 * o12;
+            const float P10 = x2 * o00 - x0 * o02, P11 = x2 * o01 - x0 * o12, P12 = x2 * o02 - x0 * o22;
+            const float P20 = x0 * o01 - x1 * o00, P21 = x0 * o11 - x1 * o01, P22 = x0 * o12 - x1 * o02;
+            // H_ww = -[a]x Omega [a]x = -P [a]x (upper triangle)
+            acc[0] += P02 * x1 - P01 * x2;
+            acc[1] += P00 * x2 - P02 * x0;
+            acc[2] += P01 * x0 - P00 * x1;
+            acc[3] += P10 * x2 - P12 * x0;
+            acc[4] += P11 * x0 - P10 * x1;
+            acc[5] += P21 * x0 - P20 * x1;
+            acc[6] += P00; acc[7] += P01; acc[8] += P02;
+            acc[9] += P10; acc[10] += P11; acc[11] += P12;
+            acc[12] += P20; acc[13] += P21; acc[14] += P22;
+            acc[15] += o00; acc[16] += o01; acc[17] += o02; acc[18] += o11; acc[19] += o12; acc[20] += o22;
+            // b_w = a x w, b_v = w
+            acc[21] += x1 * w2 - x2 * w1;
+            acc[22] += x2 * w0 - x0 * w2;
+            acc[23] += x0 * w1 - x1 * w0;
+            acc[24] += w0; acc[25] += w1; acc[26] += w2;
+            acc[27] += e0 * w0 + e1 * w1 + e2 * w2;
+            ++inl;
+        }
+        // warp shuffle, then the block's warps in fixed order (float64)
+#pragma unroll
+        for (int j = 0; j < kNT; ++j) {
+            float x = acc[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            acc[j] = x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) inl += __shfl_xor_sync(0xffffffffu, inl, o);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < kNT; ++j) sRed[warp][j] = acc[j];
+            sInl[warp] = inl;
+        }
+        __syncthreads();
+        if (threadIdx.x < kNT) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < NW; ++q) s += (double)sRed[q][threadIdx.x];
+            partials[(int64_t)it * kNT + threadIdx.x] = s;
+        } else if (threadIdx.x == kNT) {
+            int64_t s = 0;
+#pragma unroll
+            for (int q = 0; q < NW; ++q) s += sInl[q];
+            inl_partials[it] = s;
+        }
+    }
+}
+
+// One warp per factor: fixed-order float64 sum of the factor's item partials,
+// then H = L H^t L', b = L b^t with L = [S' ; -D'] (12 x 6).
+__global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const int32_t *__restrict__ item_begin,
+                                  int n_f, const double *__restrict__ partials, const int64_t *__restrict__ inl_p,
+                                  double *__restrict__ H, double *__restrict__ b, double *__restrict__ cost,
+                                  int64_t *__restrict__ inliers)
+{
+    constexpr int WPB = 4;
+    __shared__ double sHt[WPB][36], sbt[WPB][6], sL[WPB][72], sG[WPB][72];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int f = blockIdx.x * WPB + warp;
+    if (f >= n_f) return;
+    const int i0 = item_begin[f], i1 = item_begin[f + 1];
+    double s = 0.0;
+    if (lane < kNT)
+        for (int i = i0; i < i1; ++i) s += partials[(int64_t)i * kNT + lane];
+    int64_t ni = 0;
+    if (lane == 0)
+        for (int i = i0; i < i1; ++i) ni += inl_p[i];
+    // scatter the 28 sums into H^t (6x6) and b^t
+    double *Ht = sHt[warp], *bt = sbt[warp], *L = sL[warp], *G = sG[warp];
+    if (lane < 6) {
+        const int ww[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+        Ht[6 * ww[lane][0] + ww[lane][1]] = s;
+        Ht[6 * ww[lane][1] + ww[lane][0]] = s;
+    } else if (lane < 15) {
+        const int r = (lane - 6) / 3, c = (lane - 6) % 3;
+        Ht[6 * r + 3 + c] = s;
+        Ht[6 * (3 + c) + r] = s;
+    } else if (lane < 21) {
+        const int vv[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+        const int l = lane - 15;
+        Ht[6 * (3 + vv[l][0]) + 3 + vv[l][1]] = s;
+        Ht[6 * (3 + vv[l][1]) + 3 + vv[l][0]] = s;
+    } else if (lane < 27) {
+        bt[lane - 21] = s;
+    } else if (lane == 27) {
+        cost[f] = s;
+    }
+    // L rows 0..5 = S' = [[I, [t]x], [0, I]]; rows 6..11 = -D' = -blkdiag(R', R')
+    const double *T = params[f].T;
+    for (int e = lane; e < 72; e += 32) {
+        const int r = e / 6, c = e % 6;
+        double v = 0.0;
+        if (r < 6) {
+            if (r == c) v = 1.0;
+            else if (r < 3 && c >= 3) {
+                const double tx = T[3], ty = T[7], tz = T[11];
+                const double K[3][3] = {{0, -tz, ty}, {tz, 0, -tx}, {-ty, tx, 0}};
+                v = K[r][c - 3];
+            }
+        } else {
+            const int rr = r - 6;
+            if ((rr < 3) == (c < 3)) v = -T[4 * (c % 3) + (rr % 3)];
+        }
+        L[e] = v;
+    }
+    __syncwarp();
+    for (int e = lane; e < 72; e += 32) {   // G = L H^t
+        const int r = e / 6, c = e % 6;
+        double x = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x += L[6 * r + k] * Ht[6 * k + c];
+        G[e] = x;
+    }
+    __syncwarp();
+    double *Hf = H + (int64_t)f * 144;
+    for (int e = lane; e < 144; e += 32) {  // H = G L'
+        const int r = e / 12, c = e % 12;
+        if (c < r) continue;
+        double x = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x += G[6 * r + k] * L[6 * c + k];
+        Hf[12 * r + c] = x;
+        Hf[12 * c + r] = x;
+    }
+    if (lane < 12) {
+        double x = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x += L[6 * lane + k] * bt[k];
+        b[(int64_t)f * 12 + lane] = x;
+    }
+    if (lane == 0 && inliers) inliers[f] = ni;
+}
+
+// ------------------------------------------------------------------ f64 ----
+
+constexpr int kF64Block = 64;
+constexpr int kF64Terms = 91;   // 78 upper-triangle H, 12 b, 1 cost
+
+__global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__restrict__ prm,
+                                                             const MapDesc *__restrict__ maps,
+                                                             const FrameDesc *__restrict__ frames, int64_t n,
+                                                             double *__restrict__ scratch, unsigned int *ticket,
+                                                             double *__restrict__ H, double *__restrict__ b,
+                                                             double *__restrict__ cost, int64_t *__restrict__ inliers)
+{
+    __shared__ double sT[kF64Terms][kF64Block];
+    __shared__ int sInl[kF64Block];
+    __shared__ bool amLast;
+    const int tid = threadIdx.x;
+    const PoseParam P = *prm;
+    const MapDesc m = maps[P.map];
+    const FrameDesc F = frames[P.frame];
+    double run0 = 0.0, run1 = 0.0;
+    int inl = 0;
+    for (int64_t base = (int64_t)blockIdx.x * kF64Block; base < n; base += (int64_t)gridDim.x * kF64Block) {
+        const int64_t i = base + tid;
+        bool have = false;
+        double J[3][12], e[3], Om[3][3];
+        if (i < n) {
+            const float4 A = F.pa[i], B = F.pb[i];
+            const float C22 = F.pc[i];
+            int k[3];
+            double q[3];
+            if (key_f64(P.T, A.x, A.y, A.z, m.inv_r, k, q)) {
+                const int slot = probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2]));
+                if (slot >= 0) {
+                    const VoxelRec v = m.rec[slot];
+                    double R[3][3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) R[r][c] = P.T[4 * r + c];
+                    const double CA[3][3] = {{A.w, B.x, B.y}, {B.x, B.z, B.w}, {B.y, B.w, C22}};
+                    const double CB[3][3] = {{v.a.w, v.b.x, v.b.y}, {v.b.x, v.b.z, v.b.w}, {v.b.y, v.b.w, v.c.x}};
+                    double RC[3][3], M[3][3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) RC[r][c] = R[r][0] * CA[0][c] + R[r][1] * CA[1][c] + R[r][2] * CA[2][c];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            M[r][c] = CB[r][c] + RC[r][0] * R[c][0] + RC[r][1] * R[c][1] + RC[r][2] * R[c][2];
+                    // symmetric inverse by the adjugate (M is symmetric positive definite)
+                    const double c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+                    const double c01 = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+                    const double c02 = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+                    const double c11 = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+                    const double c12 = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+                    const double c22 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+                    const double det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
+                    if (det > 0.0) {
+                        const double id = 1.0 / det;
+                        Om[0][0] = c00 * id; Om[0][1] = c01 * id; Om[0][2] = c02 * id;
+                        Om[1][0] = c01 * id; Om[1][1] = c11 * id; Om[1][2] = c12 * id;
+                        Om[2][0] = c02 * id; Om[2][1] = c12 * id; Om[2][2] = c22 * id;
+                        // mean relative to the voxel corner back to absolute target coordinates
+                        const double mu[3] = {(double)k[0] * m.r + (double)v.a.x, (double)k[1] * m.r + (double)v.a.y,
+                                              (double)k[2] * m.r + (double)v.a.z};
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) e[r] = mu[r] - q[r];
+                        const double px = A.x, py = A.y, pz = A.z;
+                        const double Pm[3][3] = {{0, -pz, py}, {pz, 0, -px}, {-py, px, 0}};
+                        const double Qm[3][3] = {{0, -q[2], q[1]}, {q[2], 0, -q[0]}, {-q[1], q[0], 0}};
+#pragma unroll
+                        for (int r = 0; r < 3; ++r)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                J[r][c] = -Qm[r][c];
+                                J[r][3 + c] = (r == c) ? 1.0 : 0.0;
+                                J[r][6 + c] = R[r][0] * Pm[0][c] + R[r][1] * Pm[1][c] + R[r][2] * Pm[2][c];
+                                J[r][9 + c] = -R[r][c];
+                            }
+                        have = true;
+                    }
+                }
+            }
+        }
+        if (have) {
+            ++inl;
+            double W[3][12], Oe[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) W[r][c] = Om[r][0] * J[0][c] + Om[r][1] * J[1][c] + Om[r][2] * J[2][c];
+                Oe[r] = Om[r][0] * e[0] + Om[r][1] * e[1] + Om[r][2] * e[2];
+            }
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < 12; ++a)
+#pragma unroll
+                for (int c = a; c < 12; ++c) sT[t++][tid] = J[0][a] * W[0][c] + J[1][a] * W[1][c] + J[2][a] * W[2][c];
+#pragma unroll
+            for (int a = 0; a < 12; ++a) sT[78 + a][tid] = J[0][a] * Oe[0] + J[1][a] * Oe[1] + J[2][a] * Oe[2];
+            sT[90][tid] = e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];
+        } else {
+#pragma unroll
+            for (int t = 0; t < kF64Terms; ++t) sT[t][tid] = 0.0;
+        }
+        __syncthreads();
+        for (int c = 0; c < kF64Block; ++c) {
+            run0 += sT[tid][c];
+            if (tid + kF64Block < kF64Terms) run1 += sT[tid + kF64Block][c];
+        }
+        __syncthreads();
+    }
+    // this block's partial
+    sInl[tid] = inl;
+    __syncthreads();
+    double *mine = scratch + (int64_t)blockIdx.x * (kF64Terms + 1);
+    mine[tid] = run0;
+    if (tid + kF64Block < kF64Terms) mine[tid + kF64Block] = run1;
+    if (tid == 0) {
+        int64_t s = 0;
+        for (int c = 0; c < kF64Block; ++c) s += sInl[c];
+        mine[kF64Terms] = (double)s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) amLast = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!amLast) return;
+    __threadfence();
+    // last block: fixed-order sum over blocks
+    for (int t = tid; t <= kF64Terms; t += kF64Block) {
+        double s = 0.0;
+        for (int q = 0; q < (int)gridDim.x; ++q) s += __ldcg(scratch + (int64_t)q * (kF64Terms + 1) + t);
+        if (t < 78) {
+            // upper-triangle index t -> (a, c)
+            int a = 0, rem = t;
+            while (rem >= 12 - a) { rem -= 12 - a; ++a; }
+            const int c = a + rem;
+            H[12 * a + c] = s;
+            H[12 * c + a] = s;
+        } else if (t < 90) {
+            b[t - 78] = s;
+        } else if (t == 90) {
+            *cost = s;
+        } else if (inliers) {
+            *inliers = (int64_t)s;
+        }
+    }
+    if (tid == 0) *ticket = 0u;
+}
+
+}  // namespace
+
+void launch_prepare_factors(const int32_t *factor_idx, int n_f, const double *poses, PoseParam *out, cudaStream_t st)
+{
+    if (n_f <= 0) return;
+    k_prepare_factors<<<(n_f + 127) / 128, 128, 0, st>>>(factor_idx, n_f, poses, out);
+}
+
+void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, const int32_t *frame_idx,
+                          const int32_t *map_idx, int n_src, int n_tgt, PoseParam *out, cudaStream_t st)
+{
+    const int64_t n = (int64_t)n_src * n_tgt;
+    if (n <= 0) return;
+    k_prepare_pairs<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(poses_src, poses_tgt, frame_idx, map_idx, n_src,
+                                                               n_tgt, out);
+}
+
+void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
+                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials, int block,
+                          int grid, cudaStream_t st)
+{
+    if (n_items <= 0) return;
+    switch (block) {
+    case 128: k_linearize_f32<128><<<grid, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials); break;
+    case 512: k_linearize_f32<512><<<grid, 512, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials); break;
+    default: k_linearize_f32<256><<<grid, 256, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials); break;
+    }
+}
+
+void launch_reduce_finalize(const PoseParam *params, const int32_t *item_begin, int n_f, const double *partials,
+                            const int64_t *inl_partials, double *H, double *b, double *cost, int64_t *inliers,
+                            cudaStream_t st)
+{
+    if (n_f <= 0) return;
+    k_reduce_finalize<<<(n_f + 3) / 4, 128, 0, st>>>(params, item_begin, n_f, partials, inl_partials, H, b, cost,
+                                                    inliers);
+}
+
+int linearize_f64_block() { return kF64Block; }
+
+void launch_linearize_f64(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,
+                          double *scratch, unsigned int *ticket, double *H, double *b, double *cost,
+                          int64_t *inliers, int grid, cudaStream_t st)
+{
+    k_linearize_f64<<<grid, kF64Block, 0, st>>>(param, maps, frames, n, scratch, ticket, H, b, cost, inliers);
+}
+
+}  // namespace vg

@@ -1,0 +1,205 @@
+// Internal device layouts and helpers of the VGICP library (sm_103a).
+//
+// Data layout in HBM
+//   frame  : three coalesced streams per point, 36 B/pt in total
+//              pa[i] = (x, y, z, c00)       float4
+//              pb[i] = (c01, c02, c11, c12) float4
+//              pc[i] = c22                  float
+//   voxelmap: open-addressing hash, capacity a power of two
+//              keys[cap]  uint64 packed voxel coordinate (EMPTY = all ones)
+//              rec[cap]   48 B record per slot: mean relative to the voxel's
+//                         lower corner k*r (so residuals never cancel against
+//                         large absolute coordinates), covariance, count
+//
+// Voxel coordinate (Sec. III-A, voxel data association): the reference
+// definition is k = floor(fl64(x * inv_r)) with x = fma(R0,px,fma(R1,py,fma(R2,pz,t)))
+// in float64.  B300 has little float64 throughput, so the kernels evaluate x in
+// float32 arithmetic with a proven error bound and fall back to that float64
+// definition only for the points whose floor the bound cannot decide.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vg {
+
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr int kKeyOffset = 1 << 20;   // 21-bit two's-complement range [-2^20, 2^20 - 1]
+constexpr double kKeyMin = -1048576.0;
+constexpr double kKeyMax = 1048575.0;
+
+struct __align__(16) VoxelRec {
+    float4 a;   // mu_rel.x, mu_rel.y, mu_rel.z, c00
+    float4 b;   // c01, c02, c11, c12
+    float4 c;   // c22, count (uint32 bits), unused, unused
+};
+
+struct MapDesc {
+    uint64_t *keys;
+    VoxelRec *rec;
+    uint32_t mask;       // cap - 1
+    uint32_t log2cap;    // >= 4
+    double r, inv_r;     // resolution and fl64(1 / r)
+    float r_h, r_l;      // r = r_h + r_l (float32 pair)
+    float inv_rf;        // fl32(inv_r)
+    int32_t pow2;        // r is a power of two
+};
+
+struct FrameDesc {
+    const float4 *pa;
+    const float4 *pb;
+    const float *pc;
+    int64_t n;
+    const float *cmax;   // device scalar: max |covariance entry| of the frame
+};
+
+// Per-factor (or per-pair) transform in the forms the kernels use.
+struct __align__(16) PoseParam {
+    double T[12];        // T_BA exactly as defined (float64)
+    float Rh[9], Rl[9];  // R = Rh + Rl (float32 pairs), row-major
+    float th[3], tl[3];  // t = th + tl
+    int32_t map, frame;  // descriptor-table indices
+    int32_t pad0, pad1;
+};
+
+// ---------------------------------------------------------------- keys ----
+
+__device__ __forceinline__ uint64_t pack_key(int kx, int ky, int kz)
+{
+    return ((uint64_t)(uint32_t)(kx + kKeyOffset) << 42) | ((uint64_t)(uint32_t)(ky + kKeyOffset) << 21) |
+           (uint64_t)(uint32_t)(kz + kKeyOffset);
+}
+
+__device__ __forceinline__ void unpack_key(uint64_t key, int &kx, int &ky, int &kz)
+{
+    kx = (int)((key >> 42) & 0x1FFFFF) - kKeyOffset;
+    ky = (int)((key >> 21) & 0x1FFFFF) - kKeyOffset;
+    kz = (int)(key & 0x1FFFFF) - kKeyOffset;
+}
+
+// Multiplicative (Fibonacci) hashing: top log2cap bits of key * 2^64/phi.
+__device__ __forceinline__ uint32_t hash_slot(uint64_t key, uint32_t log2cap)
+{
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - log2cap));
+}
+
+// Slot of key in the map, or -1.  Linear probing; the table always holds an
+// empty slot (load <= 2/3), so the loop ends at the first empty slot.
+__device__ __forceinline__ int probe(const uint64_t *__restrict__ keys, uint32_t mask, uint32_t log2cap,
+                                     uint64_t key)
+{
+    uint32_t s = hash_slot(key, log2cap);
+    for (uint32_t i = 0; i <= mask; ++i) {
+        const uint64_t k = __ldg(keys + s);
+        if (k == key) return (int)s;
+        if (k == kEmptyKey) return -1;
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
+// Reference voxel coordinate in float64: x = fma(R0,px,fma(R1,py,fma(R2,pz,t))),
+// k = floor(x * inv_r).  Returns false if any axis is out of range or not finite.
+__device__ __forceinline__ bool key_f64(const double *T, float px, float py, float pz, double inv_r,
+                                        int k[3], double q[3])
+{
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        q[i] = __fma_rn(T[4 * i], (double)px, __fma_rn(T[4 * i + 1], (double)py,
+                        __fma_rn(T[4 * i + 2], (double)pz, T[4 * i + 3])));
+        const double f = floor(__dmul_rn(q[i], inv_r));
+        ok = ok && (f >= kKeyMin && f <= kKeyMax);
+        k[i] = ok ? (int)f : 0;
+    }
+    return ok;
+}
+
+// Error-free sum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// x - k*r with r = r_h + r_l, as an unevaluated sum x = s + lo: rounding error
+// relative to the result itself (a few float32 ulps of |x - k r|).
+__device__ __forceinline__ float face_dist(float s, float lo, float k, float r_h, float r_l)
+{
+    float g = __fmaf_rn(-k, r_h, s);
+    g = __fmaf_rn(-k, r_l, g);
+    return __fadd_rn(g, lo);
+}
+
+// One axis of the voxel coordinate from a float32-pair transform.
+//
+// x = Rh.p + th + (Rl.p + tl) is formed as an unevaluated pair (s, lo) with
+// error-free products and sums, accurate to ~2^-45 of X = sum |Rh_j p_j| + |th|.
+// The float64 reference differs from the exact value by < 2^-50 X (three fmas,
+// one multiply by inv_r).  Returns false when x is within 2^-40 X of a voxel
+// face (or not finite); the caller then evaluates the float64 reference.
+// On success: k is the reference floor and d = x - k r in [0, r).
+__device__ __forceinline__ bool axis_key_ff(const float *Rh, const float *Rl, float th, float tl, float px,
+                                            float py, float pz, float r_h, float r_l, float inv_rf, int &k,
+                                            float &d)
+{
+    const float h0 = __fmul_rn(Rh[0], px), l0 = __fmaf_rn(Rh[0], px, -h0);
+    const float h1 = __fmul_rn(Rh[1], py), l1 = __fmaf_rn(Rh[1], py, -h1);
+    const float h2 = __fmul_rn(Rh[2], pz), l2 = __fmaf_rn(Rh[2], pz, -h2);
+    float s, e1, e2, e3;
+    two_sum(h0, h1, s, e1);
+    two_sum(s, h2, s, e2);
+    two_sum(s, th, s, e3);
+    float lo = __fadd_rn(__fadd_rn(l0, l1), __fadd_rn(l2, e1));
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(e2, e3), tl));
+    lo = __fmaf_rn(Rl[0], px, lo);
+    lo = __fmaf_rn(Rl[1], py, lo);
+    lo = __fmaf_rn(Rl[2], pz, lo);
+    const float X = fabsf(h0) + fabsf(h1) + fabsf(h2) + fabsf(th);
+    const float m = fmaxf(X * 0x1p-40f, 0x1p-100f);
+    float kf = floorf(__fmul_rn(__fadd_rn(s, lo), inv_rf));
+    float g0 = face_dist(s, lo, kf, r_h, r_l);
+    float g1 = face_dist(s, lo, kf + 1.f, r_h, r_l);
+    if (g0 < 0.f) {
+        kf -= 1.f;
+        g1 = g0;
+        g0 = face_dist(s, lo, kf, r_h, r_l);
+    } else if (g1 >= 0.f) {
+        kf += 1.f;
+        g0 = g1;
+        g1 = face_dist(s, lo, kf + 1.f, r_h, r_l);
+    }
+    if (!(g0 >= m && g1 <= -m)) return false;   // also catches NaN / inf
+    if (!(kf >= (float)kKeyMin && kf <= (float)kKeyMax)) {
+        k = INT32_MIN;                            // decided: out of range
+        return true;
+    }
+    k = (int)kf;
+    d = g0;
+    return true;
+}
+
+// One axis from a plain float32 fma chain with the error bound
+// |x32 - x| <= 2^-20 X (four roundings of at most 2^-24 X each, with margin).
+// Returns false when the bound straddles a voxel face.  k = INT32_MIN marks a
+// decided out-of-range coordinate.
+__device__ __forceinline__ bool axis_key_f32(const float *Rh, float th, float px, float py, float pz, float r_h,
+                                             float r_l, float inv_rf, int &k)
+{
+    const float x = __fmaf_rn(Rh[0], px, __fmaf_rn(Rh[1], py, __fmaf_rn(Rh[2], pz, th)));
+    const float X = fabsf(Rh[0] * px) + fabsf(Rh[1] * py) + fabsf(Rh[2] * pz) + fabsf(th);
+    const float kf = floorf(__fmul_rn(x, inv_rf));
+    const float tol = X * 0x1p-20f + fabsf(kf * r_l) * 2.f + 0x1p-100f;
+    const float d0 = __fmaf_rn(-kf, r_h, x);          // ~ x - kf r, error ~ 2^-24 |d0|
+    const float d1 = __fmaf_rn(-(kf + 1.f), r_h, x);  // ~ x - (kf+1) r
+    if (!(d0 >= tol * 1.0001f && d1 <= -tol * 1.0001f)) return false;
+    if (!(kf >= (float)kKeyMin && kf <= (float)kKeyMax)) {
+        k = INT32_MIN;
+        return true;
+    }
+    k = (int)kf;
+    return true;
+}
+
+}  // namespace vg

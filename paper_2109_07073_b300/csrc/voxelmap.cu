@@ -1,0 +1,242 @@
+// Frame packing and the batched voxelmap build (Sec. III-A: a voxel's
+// distribution aggregates the distributions of the points that fall in it:
+// mean of the point means and mean of the point covariances).
+//
+// Build of all maps of a batch in four launches:
+//   clear      keys <- EMPTY, voxel counters <- 0
+//   insert     per point: voxel key, atomicCAS into the map's open-addressing
+//              table; the thread that claims a slot takes a dense voxel id and
+//              zeroes that voxel's accumulators
+//   accumulate per point: exact fixed-point sums (int64 atomics, so the result
+//              does not depend on the order the GPU runs the points in)
+//   finalize   per voxel: mean relative to the voxel's lower corner, mean
+//              covariance, count -> the slot's 48 B record
+#include "kernels.cuh"
+
+namespace vg {
+
+namespace {
+
+constexpr int kAcc = 10;   // count, 3 mean sums, 6 covariance sums
+
+__global__ void k_frame_pack(const float *__restrict__ pts, const float *__restrict__ cov, int64_t n,
+                             float4 *__restrict__ pa, float4 *__restrict__ pb, float *__restrict__ pc,
+                             unsigned int *cmax_bits)
+{
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float *p = pts + 3 * i, *c = cov + 6 * i;
+        pa[i] = make_float4(p[0], p[1], p[2], c[0]);
+        pb[i] = make_float4(c[1], c[2], c[3], c[4]);
+        pc[i] = c[5];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) m = fmaxf(m, fabsf(c[j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(cmax_bits, __float_as_uint(m));
+}
+
+__device__ __forceinline__ int find_unit(const int64_t *prefix, int n_units, int64_t g)
+{
+    int lo = 0, hi = n_units - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_build_clear(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units, int n_units,
+                              const int64_t *__restrict__ slot_prefix, int32_t *__restrict__ vid_of_slot)
+{
+    const int64_t total = slot_prefix[n_units];
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int u = find_unit(slot_prefix, n_units, g);
+        const int64_t s = g - slot_prefix[u];
+        maps[units[u].map].keys[s] = kEmptyKey;
+        vid_of_slot[g] = -1;
+        if (s == 0) *units[u].n_voxels = 0;
+    }
+}
+
+// Voxel coordinate of a point of the map's own frame (identity pose).
+// Power-of-two resolutions: p * inv_r and floor are exact in float32.
+// Otherwise: the float64 reference floor(p * inv_r).
+__device__ __forceinline__ bool own_key(const MapDesc &m, float px, float py, float pz, int k[3])
+{
+    if (m.pow2) {
+        const float f[3] = {floorf(px * m.inv_rf), floorf(py * m.inv_rf), floorf(pz * m.inv_rf)};
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ok = ok && (f[i] >= (float)kKeyMin && f[i] <= (float)kKeyMax);
+            k[i] = ok ? (int)f[i] : 0;
+        }
+        return ok;
+    }
+    const double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    double q[3];
+    return key_f64(T, px, py, pz, m.inv_r, k, q);
+}
+
+__global__ void k_build_insert(const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
+                               const BuildUnit *__restrict__ units, const WorkItem *__restrict__ items, int n_items,
+                               BuildScratch scr)
+{
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const BuildUnit u = units[w.unit];
+        const MapDesc m = maps[u.map];
+        const FrameDesc f = frames[u.frame];
+        for (int64_t i = w.start + threadIdx.x; i < w.start + w.count; i += blockDim.x) {
+            const float4 a = __ldg(f.pa + i);
+            int k[3];
+            int32_t slot = -1;
+            if (own_key(m, a.x, a.y, a.z, k)) {
+                const uint64_t key = pack_key(k[0], k[1], k[2]);
+                uint32_t s = hash_slot(key, m.log2cap);
+                for (uint32_t t = 0; t <= m.mask; ++t) {
+                    const unsigned long long old =
+                        atomicCAS((unsigned long long *)(m.keys + s), (unsigned long long)kEmptyKey,
+                                  (unsigned long long)key);
+                    if (old == kEmptyKey) {          // claimed: this thread owns the new voxel
+                        const int32_t vid = (int32_t)atomicAdd(u.n_voxels, 1u);
+                        scr.vid_of_slot[u.slot_base + s] = vid;
+                        scr.slot_of_vid[u.point_base + vid] = (int32_t)s;
+                        int64_t *acc = scr.acc + (u.point_base + vid) * kAcc;
+#pragma unroll
+                        for (int j = 0; j < kAcc; ++j) acc[j] = 0;
+                        slot = (int32_t)s;
+                        break;
+                    }
+                    if (old == key) { slot = (int32_t)s; break; }
+                    s = (s + 1) & m.mask;
+                }
+            }
+            scr.slot_of_point[u.point_base + i] = slot;
+        }
+    }
+}
+
+__device__ __forceinline__ float cov_scale(const float *cmax)
+{
+    const float c = *cmax;
+    if (!(c > 0.f)) return 1.f;
+    int e;
+    frexpf(c, &e);                 // c < 2^e
+    return ldexpf(1.f, 40 - e);    // |entry| * scale < 2^40
+}
+
+__device__ __forceinline__ float mean_scale(const MapDesc &m) { return m.inv_rf * 0x1p32f; }
+
+__global__ void k_build_accumulate(const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
+                                   const BuildUnit *__restrict__ units, const WorkItem *__restrict__ items,
+                                   int n_items, BuildScratch scr)
+{
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const BuildUnit u = units[w.unit];
+        const MapDesc m = maps[u.map];
+        const FrameDesc f = frames[u.frame];
+        const float sc = cov_scale(f.cmax), sm = mean_scale(m);
+        for (int64_t i = w.start + threadIdx.x; i < w.start + w.count; i += blockDim.x) {
+            const int32_t slot = scr.slot_of_point[u.point_base + i];
+            if (slot < 0) continue;
+            const int32_t vid = scr.vid_of_slot[u.slot_base + slot];
+            const float4 a = __ldg(f.pa + i), b = __ldg(f.pb + i);
+            const float c22 = __ldg(f.pc + i);
+            int kx, ky, kz;
+            unpack_key(m.keys[slot], kx, ky, kz);
+            // offset from the voxel's lower corner k r, r = r_h + r_l
+            const float dx = __fmaf_rn(-(float)kx, m.r_l, __fmaf_rn(-(float)kx, m.r_h, a.x));
+            const float dy = __fmaf_rn(-(float)ky, m.r_l, __fmaf_rn(-(float)ky, m.r_h, a.y));
+            const float dz = __fmaf_rn(-(float)kz, m.r_l, __fmaf_rn(-(float)kz, m.r_h, a.z));
+            unsigned long long *acc = (unsigned long long *)(scr.acc + (u.point_base + vid) * kAcc);
+            atomicAdd(acc + 0, 1ull);
+            atomicAdd(acc + 1, (unsigned long long)__float2ll_rn(dx * sm));
+            atomicAdd(acc + 2, (unsigned long long)__float2ll_rn(dy * sm));
+            atomicAdd(acc + 3, (unsigned long long)__float2ll_rn(dz * sm));
+            atomicAdd(acc + 4, (unsigned long long)__float2ll_rn(a.w * sc));
+            atomicAdd(acc + 5, (unsigned long long)__float2ll_rn(b.x * sc));
+            atomicAdd(acc + 6, (unsigned long long)__float2ll_rn(b.y * sc));
+            atomicAdd(acc + 7, (unsigned long long)__float2ll_rn(b.z * sc));
+            atomicAdd(acc + 8, (unsigned long long)__float2ll_rn(b.w * sc));
+            atomicAdd(acc + 9, (unsigned long long)__float2ll_rn(c22 * sc));
+        }
+    }
+}
+
+__global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
+                                 const BuildUnit *__restrict__ units, const WorkItem *__restrict__ items,
+                                 int n_items, BuildScratch scr)
+{
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const BuildUnit u = units[w.unit];
+        const MapDesc m = maps[u.map];
+        const FrameDesc f = frames[u.frame];
+        const uint32_t nv = *u.n_voxels;
+        const float isc = 1.f / cov_scale(f.cmax), ism = 1.f / mean_scale(m);
+        for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
+            if (v >= (int64_t)nv) break;
+            const int64_t *acc = scr.acc + (u.point_base + v) * kAcc;
+            const int32_t slot = scr.slot_of_vid[u.point_base + v];
+            const float n = (float)acc[0], in = 1.f / n;
+            VoxelRec r;
+            r.a = make_float4(__ll2float_rn(acc[1]) * ism * in, __ll2float_rn(acc[2]) * ism * in,
+                              __ll2float_rn(acc[3]) * ism * in, __ll2float_rn(acc[4]) * isc * in);
+            r.b = make_float4(__ll2float_rn(acc[5]) * isc * in, __ll2float_rn(acc[6]) * isc * in,
+                              __ll2float_rn(acc[7]) * isc * in, __ll2float_rn(acc[8]) * isc * in);
+            r.c = make_float4(__ll2float_rn(acc[9]) * isc * in, __uint_as_float((uint32_t)acc[0]), 0.f, 0.f);
+            m.rec[slot] = r;
+        }
+    }
+}
+
+__global__ void k_export(const MapDesc *__restrict__ mp, uint32_t cap, uint32_t *counter, uint64_t *keys_out,
+                         VoxelRec *rec_out)
+{
+    const MapDesc m = *mp;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += gridDim.x * blockDim.x) {
+        const uint64_t k = m.keys[s];
+        if (k == kEmptyKey) continue;
+        const uint32_t i = atomicAdd(counter, 1u);
+        keys_out[i] = k;
+        rec_out[i] = m.rec[s];
+    }
+}
+
+}  // namespace
+
+void launch_frame_pack(const float *points, const float *covs, int64_t n, float4 *pa, float4 *pb, float *pc,
+                       float *cmax, cudaStream_t st)
+{
+    if (n <= 0) return;
+    const int block = 256;
+    int grid = (int)((n + block - 1) / block);
+    if (grid > 148 * 16) grid = 148 * 16;
+    k_frame_pack<<<grid, block, 0, st>>>(points, covs, n, pa, pb, pc, (unsigned int *)cmax);
+}
+
+void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const BuildUnit *units, int n_units,
+                           const WorkItem *items, int n_items, const int64_t *slot_prefix, BuildScratch scr,
+                           int grid, cudaStream_t st)
+{
+    if (n_units <= 0) return;
+    k_build_clear<<<148 * 8, 256, 0, st>>>(maps, units, n_units, slot_prefix, scr.vid_of_slot);
+    if (n_items <= 0) return;
+    k_build_insert<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
+    k_build_accumulate<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
+    k_build_finalize<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
+}
+
+void launch_export_voxels(const MapDesc *map_dev, uint32_t cap, uint32_t *counter, uint64_t *keys_out,
+                          VoxelRec *rec_out, cudaStream_t st)
+{
+    int grid = (int)((cap + 255) / 256);
+    if (grid > 148 * 8) grid = 148 * 8;
+    k_export<<<grid, 256, 0, st>>>(map_dev, cap, counter, keys_out, rec_out);
+}
+
+}  // namespace vg

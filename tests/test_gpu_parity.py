@@ -1,0 +1,292 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bit-exact: voxel keys and counts, per-point correspondences, overlap counts,
+inlier counts, kNN neighbour-dependent identity cases.  Floating point: voxel
+means within 1e-6 r and covariances within 1e-6 of their scale; cost, H and b
+within err(X) = max_i |X_i - X_i^ref| / S_i <= 1e-5 (float64 path) and
+<= 1e-4 (float32 path), S_i the sum of absolute per-point contributions.
+"""
+import numpy as np
+import pytest
+
+import datagen as dg
+import oracle
+import paper_2109_07073_b300 as vg
+from util import err_metric
+
+pytestmark = pytest.mark.gpu
+
+TOL = {vg.VGICP_PREC_F32: 1e-4, vg.VGICP_PREC_F64: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    vg.load()
+    c = vg.Context()
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def single():
+    w = dg.single_factor_workload()
+    cb = oracle.covariances(w.points_target)
+    ca = oracle.covariances(w.points_source)
+    return w, cb, ca
+
+
+def check_voxelmap(ctx, h, pts, covs, r):
+    ref = oracle.voxelmap(pts, covs, r)
+    keys, counts, mu, cov = ctx.export_voxelmap(h)
+    assert keys.shape == ref.keys.shape
+    assert np.array_equal(keys, ref.keys)
+    assert np.array_equal(counts, ref.counts)
+    assert np.max(np.abs(mu - ref.mu)) <= 1e-6 * r
+    scale = max(1e-30, float(np.abs(ref.cov).max()))
+    assert np.max(np.abs(cov - ref.cov)) <= 1e-6 * scale
+    assert ctx.voxelmap_size(h) == ref.n_voxels
+
+
+@pytest.mark.parametrize("r", [1.0, 0.25, 2.0, 0.3])
+def test_voxelmap_build(ctx, single, r):
+    w, cb, _ = single
+    h = ctx.build_voxelmap(w.points_target, cb, r)
+    check_voxelmap(ctx, h, w.points_target, cb, r)
+    ctx.release(h)
+
+
+def test_voxelmap_faces_negative_and_out_of_range(ctx):
+    rng = dg.Stream(21)
+    r = 0.5
+    face = (np.round(rng.uniform(1500, -40, 40)) * r).reshape(-1, 3)
+    free = rng.uniform(1500, -30, 30).reshape(-1, 3)
+    far = np.array([[2 ** 20 * r, 0, 0], [-(2 ** 20) * r - 1, 0, 0], [np.nan, 1, 1]])
+    pts = np.concatenate([face, free, far]).astype(np.float32)
+    cov = rng.uniform(pts.shape[0] * 6, -1, 1).astype(np.float32).reshape(-1, 6)
+    h = ctx.build_voxelmap(pts, cov, r)
+    check_voxelmap(ctx, h, pts, cov, r)
+    ctx.release(h)
+
+
+def test_batched_build_equals_single_builds(ctx, single):
+    w, cb, ca = single
+    fr = [ctx.add_frame(w.points_target, cb), ctx.add_frame(w.points_source, ca),
+          ctx.add_frame(w.points_target[:333], cb[:333])]
+    maps = ctx.build_voxelmaps(fr, 1.0)
+    check_voxelmap(ctx, int(maps[0]), w.points_target, cb, 1.0)
+    check_voxelmap(ctx, int(maps[1]), w.points_source, ca, 1.0)
+    check_voxelmap(ctx, int(maps[2]), w.points_target[:333], cb[:333], 1.0)
+    # rebuild in place at another resolution
+    maps2 = ctx.build_voxelmaps(fr, 0.5, maps)
+    assert np.array_equal(maps2, maps)
+    check_voxelmap(ctx, int(maps[1]), w.points_source, ca, 0.5)
+    for h in list(maps) + fr:
+        ctx.release(int(h))
+
+
+def _face_cloud(seed, n, r):
+    """Points exactly on voxel faces and corners in the target frame (after T = identity rotation)."""
+    rng = dg.Stream(seed)
+    return (np.round(rng.uniform(3 * n, -20, 20)) * r * 0.5).reshape(-1, 3).astype(np.float32)
+
+
+@pytest.mark.parametrize("r", [1.0, 0.5, 0.3])
+def test_correspondences_bit_exact(ctx, single, r):
+    w, cb, ca = single
+    hm = ctx.build_voxelmap(w.points_target, cb, r)
+    vm = oracle.voxelmap(w.points_target, cb, r)
+    rng = dg.Stream(31)
+    clouds = [w.points_source, _face_cloud(5, 3000, r)]
+    poses = [oracle.relative_pose(w.T_target, w.T_source), dg.identity_pose(),
+             dg.random_pose(rng, 60, 3.0)]
+    T = dg.identity_pose()
+    T[:, 3] = [r * 3, -r * 2, r]          # integer voxel shift: faces stay on faces
+    poses.append(T)
+    for pts in clouds:
+        hf = ctx.add_frame(pts, np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (pts.shape[0], 1)))
+        for P in poses:
+            keys, hit = ctx.debug_correspondences(hf, hm, P)
+            corr, rkeys = oracle.correspondences(vm, pts, P)
+            assert np.array_equal(keys, rkeys)
+            assert np.array_equal(hit, corr >= 0)
+            frac, count = ctx.overlap(hf, hm, P)
+            assert count == int((corr >= 0).sum()) == oracle.overlap_count(vm, pts, P)
+            assert frac == count / pts.shape[0]
+        ctx.release(hf)
+    ctx.release(hm)
+
+
+def test_overlap_empty_source_is_an_error(ctx, single):
+    w, cb, _ = single
+    hm = ctx.build_voxelmap(w.points_target, cb, 1.0)
+    he = ctx.add_frame(np.zeros((0, 3), np.float32), np.zeros((0, 6), np.float32))
+    with pytest.raises(vg.VgicpError) as e:
+        ctx.overlap(he, hm, dg.identity_pose())
+    assert e.value.status == 4
+    ctx.release(he)
+    ctx.release(hm)
+
+
+@pytest.fixture(scope="module")
+def loop_frames():
+    """Eight consecutive frames of the urban loop (64 x 1024 LiDAR, 20,000 points each)."""
+    ids = list(range(10, 18))
+    g = dg.graph_workload(frame_ids=ids)
+    pts = [g.points[i] for i in ids]
+    covs = [oracle.covariances(p) for p in pts]
+    return g, ids, pts, covs
+
+
+def test_overlap_matrix_bit_exact(ctx, loop_frames):
+    g, ids, pts, covs = loop_frames
+    fr = [ctx.add_frame(p, c) for p, c in zip(pts, covs)]
+    maps = ctx.build_voxelmaps(fr, g.resolution)
+    P = g.poses[ids]
+    counts = ctx.overlap_matrix(fr, maps, P, P)
+    vms = [oracle.voxelmap(p, c, g.resolution) for p, c in zip(pts, covs)]
+    for s in range(len(ids)):
+        for t in range(len(ids)):
+            T = oracle.relative_pose(P[t], P[s])
+            assert counts[s, t] == oracle.overlap_count(vms[t], pts[s], T), (s, t)
+    assert all(counts[i, i] == pts[i].shape[0] for i in range(len(ids)))
+    for h in list(maps) + fr:
+        ctx.release(int(h))
+
+
+def _ragged_case(seed=41):
+    """Several targets, sources of 0, 1, 31, 2047, 2048, 2049, 5000 and 12345 points."""
+    rng = dg.Stream(seed)
+    tg = [dg.sample_small_scene(rng, 3000) for _ in range(3)]
+    sizes = [0, 1, 31, 2047, 2048, 2049, 5000, 12345]
+    src = [dg.sample_small_scene(rng, n) for n in sizes]
+    tcov = [oracle.covariances(p) for p in tg]
+    scov = [oracle.covariances(p) if p.shape[0] else np.zeros((0, 6), np.float32) for p in src]
+    poses = np.stack([dg.identity_pose()] + [dg.random_pose(rng, 5, 0.5) for _ in range(len(src) + 2)])
+    factors = []
+    for i in range(len(src)):
+        factors.append((i % 3, i, (i + 1) % 3, 3 + i))
+    return tg, tcov, src, scov, poses, factors
+
+
+def _oracle_factor(vm, pts, covs, TB, TA):
+    return oracle.linearize(vm, pts, covs, oracle.relative_pose(TB, TA))
+
+
+@pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64])
+def test_linearize_single_factor(ctx, single, prec):
+    w, cb, ca = single
+    ctx.set_options(precision=prec)
+    hm = ctx.build_voxelmap(w.points_target, cb, w.resolution)
+    hf = ctx.add_frame(w.points_source, ca)
+    poses = np.stack([w.T_target, w.T_source])
+    f = vg.make_factors([hm], [hf], [0], [1])
+    H, b, cost, inl = ctx.linearize(f, poses)
+    vm = oracle.voxelmap(w.points_target, cb, w.resolution)
+    L = _oracle_factor(vm, w.points_source, ca, w.T_target, w.T_source)
+    assert inl[0] == L.inliers
+    assert err_metric(H[0], L.H, L.SH) <= TOL[prec]
+    assert err_metric(b[0], L.b, L.Sb) <= TOL[prec]
+    assert abs(cost[0] - L.cost) <= TOL[prec] * L.Scost
+    assert np.array_equal(H[0], H[0].T)
+    ctx.set_options(precision=vg.VGICP_PREC_F32)
+    ctx.release(hm)
+    ctx.release(hf)
+
+
+@pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64])
+@pytest.mark.parametrize("chunk", [64, 2048])
+def test_linearize_ragged_batch(ctx, prec, chunk):
+    tg, tcov, src, scov, poses, factors = _ragged_case()
+    ctx.set_options(precision=prec, chunk_points=chunk)
+    hm = [ctx.build_voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
+    hf = [ctx.add_frame(p, c) for p, c in zip(src, scov)]
+    f = vg.make_factors([hm[t] for t, _, _, _ in factors], [hf[s] for _, s, _, _ in factors],
+                        [a for _, _, a, _ in factors], [b for _, _, _, b in factors])
+    H, b, cost, inl = ctx.linearize(f, poses)
+    vms = [oracle.voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
+    for i, (t, s, pt, ps) in enumerate(factors):
+        L = _oracle_factor(vms[t], src[s], scov[s], poses[pt], poses[ps])
+        assert inl[i] == L.inliers, i
+        if L.inliers == 0:
+            assert not H[i].any() and not b[i].any() and cost[i] == 0.0
+            continue
+        assert err_metric(H[i], L.H, L.SH) <= TOL[prec], i
+        assert err_metric(b[i], L.b, L.Sb) <= TOL[prec], i
+        assert abs(cost[i] - L.cost) <= TOL[prec] * L.Scost, i
+    ctx.set_options(precision=vg.VGICP_PREC_F32, chunk_points=2048)
+    for h in hm + hf:
+        ctx.release(h)
+
+
+def test_factor_alone_equals_factor_in_batch(ctx):
+    tg, tcov, src, scov, poses, factors = _ragged_case(seed=43)
+    hm = [ctx.build_voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
+    hf = [ctx.add_frame(p, c) for p, c in zip(src, scov)]
+    f = vg.make_factors([hm[t] for t, _, _, _ in factors], [hf[s] for _, s, _, _ in factors],
+                        [a for _, _, a, _ in factors], [b for _, _, _, b in factors])
+    H, b, cost, inl = ctx.linearize(f, poses)
+    for i in range(len(factors)):
+        H1, b1, c1, i1 = ctx.linearize(f[i:i + 1], poses)
+        assert np.array_equal(H1[0], H[i]) and np.array_equal(b1[0], b[i])
+        assert c1[0] == cost[i] and i1[0] == inl[i]
+    for h in hm + hf:
+        ctx.release(h)
+
+
+def test_linearize_device_outputs_match_host_outputs(ctx, single):
+    import torch
+    w, cb, ca = single
+    hm = ctx.build_voxelmap(w.points_target, cb, w.resolution)
+    hf = ctx.add_frame(torch.from_numpy(w.points_source).cuda(), torch.from_numpy(ca).cuda())
+    poses = np.stack([w.T_target, w.T_source])
+    f = vg.make_factors([hm, hm], [hf, hf], [0, 1], [1, 0])
+    Hh, bh, ch, ih = ctx.linearize(f, poses)
+    out = (torch.zeros((2, 12, 12), dtype=torch.float64, device="cuda"),
+           torch.zeros((2, 12), dtype=torch.float64, device="cuda"),
+           torch.zeros(2, dtype=torch.float64, device="cuda"), torch.zeros(2, dtype=torch.int64, device="cuda"))
+    ctx.linearize(f, poses, out=out)
+    ctx.synchronize()
+    assert np.array_equal(out[0].cpu().numpy(), Hh) and np.array_equal(out[1].cpu().numpy(), bh)
+    assert np.array_equal(out[2].cpu().numpy(), ch) and np.array_equal(out[3].cpu().numpy(), ih)
+    ctx.release(hm)
+    ctx.release(hf)
+
+
+def test_invalid_arguments_fail_cleanly(ctx, single):
+    w, cb, ca = single
+    hm = ctx.build_voxelmap(w.points_target, cb, 1.0)
+    hf = ctx.add_frame(w.points_source, ca)
+    poses = np.stack([w.T_target, w.T_source])
+    with pytest.raises(vg.VgicpError) as e:
+        ctx.linearize(vg.make_factors([hm], [hf], [0], [2]), poses)
+    assert e.value.status == 1
+    with pytest.raises(vg.VgicpError) as e:
+        ctx.linearize(vg.make_factors([hf], [hf], [0], [1]), poses)
+    assert e.value.status == 3
+    with pytest.raises(vg.VgicpError) as e:
+        ctx.build_voxelmap(w.points_target, cb, -1.0)
+    assert e.value.status == 1
+    with pytest.raises(vg.VgicpError) as e:
+        ctx.build_voxelmap(w.points_target, cb, float("nan"))
+    assert e.value.status == 1
+    ctx.release(hm)
+    with pytest.raises(vg.VgicpError) as e:
+        ctx.release(hm)
+    assert e.value.status == 3
+    ctx.release(hf)
+
+
+def test_knn_covariances_match_oracle(ctx, single):
+    w, cb, _ = single
+    g = ctx.estimate_covariances(w.points_target, 10, 1e-3)
+    assert np.max(np.abs(g - cb)) <= 2e-6
+    tiny = w.points_target[:5]
+    assert np.array_equal(ctx.estimate_covariances(tiny, 10, 1e-3), oracle.covariances(tiny))
+
+
+def test_kernel_launch_counter_moves(ctx, single):
+    w, cb, _ = single
+    before = ctx.kernel_launches()
+    h = ctx.build_voxelmap(w.points_target, cb, 1.0)
+    assert ctx.kernel_launches() > before
+    ctx.release(h)
