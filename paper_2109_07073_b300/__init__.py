@@ -149,12 +149,25 @@ def vgicp_options_default() -> Options:
     return o
 
 
+CUDA_STREAM_LEGACY = 0x1
+
+
+def _stream_arg(stream):
+    """None -> the context's own stream; a torch stream or raw handle otherwise.
+
+    torch's default stream has handle 0, the legacy default stream, which the C
+    ABI reads as "no stream given"; it is passed as cudaStreamLegacy instead."""
+    if stream is None:
+        return None
+    s = getattr(stream, "cuda_stream", stream)
+    return C.c_void_p(s if s else CUDA_STREAM_LEGACY)
+
+
 def vgicp_create(options: Options = None, stream=None):
     """New context; stream is a torch.cuda.Stream, a raw cudaStream_t int, or None (own stream)."""
     ctx = C.c_void_p()
-    s = getattr(stream, "cuda_stream", stream)
     _check(None, load().vgicp_create(C.byref(ctx), C.byref(options) if options is not None else None,
-                                     C.c_void_p(s) if s else None))
+                                     _stream_arg(stream)))
     return ctx
 
 
@@ -167,8 +180,7 @@ def vgicp_set_options(ctx, options: Options):
 
 
 def vgicp_set_stream(ctx, stream=None):
-    s = getattr(stream, "cuda_stream", stream)
-    _check(ctx, load().vgicp_set_stream(ctx, C.c_void_p(s) if s else None))
+    _check(ctx, load().vgicp_set_stream(ctx, _stream_arg(stream)))
 
 
 def vgicp_synchronize(ctx):

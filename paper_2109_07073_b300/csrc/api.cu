@@ -68,7 +68,7 @@ struct vgicp_ctx {
     // workspaces
     Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
     Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
-    Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter;
+    Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs;
     Plan plan;
 };
 
@@ -208,12 +208,6 @@ vgicp_status put_frame_desc(vgicp_ctx *ctx, uint32_t idx)
     return VGICP_OK;
 }
 
-vgicp_status put_map_desc(vgicp_ctx *ctx, uint32_t idx)
-{
-    CU(cudaMemcpyAsync(ctx->d_maps + idx, &ctx->h_maps[idx], sizeof(MapDesc), cudaMemcpyHostToDevice, ctx->stream));
-    return VGICP_OK;
-}
-
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Allocate and fill a frame from device-resident points / covariances.
@@ -334,8 +328,9 @@ vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const 
     return VGICP_OK;
 }
 
-// Make sure map object idx has capacity for n points at resolution r.
-vgicp_status prepare_map(vgicp_ctx *ctx, uint32_t idx, int64_t n, double r)
+// Make sure map object idx has capacity for n points at resolution r; *changed
+// says whether its descriptor differs from the one in the device table.
+vgicp_status prepare_map(vgicp_ctx *ctx, uint32_t idx, int64_t n, double r, bool *changed)
 {
     Obj &o = ctx->objs[idx];
     const uint32_t cap = map_capacity(n);
@@ -353,8 +348,10 @@ vgicp_status prepare_map(vgicp_ctx *ctx, uint32_t idx, int64_t n, double r)
         ctx->bytes_in_use += (int64_t)bytes;
     }
     o.r = r;
-    fill_map_desc(ctx->h_maps[idx], (char *)o.map_mem, o.cap, r);
-    TRY(put_map_desc(ctx, idx));
+    MapDesc d{};
+    fill_map_desc(d, (char *)o.map_mem, o.cap, r);
+    *changed = std::memcmp(&d, &ctx->h_maps[idx], sizeof(MapDesc)) != 0;
+    ctx->h_maps[idx] = d;
     return VGICP_OK;
 }
 
@@ -514,7 +511,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
                    &ctx->ws_ticket, &ctx->ws_counts, &ctx->ws_stage, &ctx->ws_bunits, &ctx->ws_bitems,
                    &ctx->ws_bprefix, &ctx->ws_slot_of_point, &ctx->ws_acc, &ctx->ws_vid_of_slot,
                    &ctx->ws_slot_of_vid, &ctx->ws_pairs, &ctx->ws_fidx, &ctx->ws_midx, &ctx->ws_chunks,
-                   &ctx->ws_export_keys, &ctx->ws_export_rec, &ctx->ws_counter, &ctx->plan.idx,
+                   &ctx->ws_export_keys, &ctx->ws_export_rec, &ctx->ws_counter, &ctx->ws_descs, &ctx->plan.idx,
                    &ctx->plan.items, &ctx->plan.item_begin};
     for (Buf *b : bufs) free_buf(ctx, *b);
     if (ctx->d_maps) cudaFreeAsync(ctx->d_maps, ctx->stream);
@@ -609,14 +606,33 @@ vgicp_status vgicp_build_voxelmaps(vgicp_ctx *ctx, const vgicp_frame_t *frames, 
         if (maps[i] >= 0 && !lookup(ctx, maps[i], Obj::MAP, &midx[i]))
             return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)maps[i]);
     }
+    std::vector<uint32_t> upd_idx;
+    std::vector<MapDesc> upd;
     for (int64_t i = 0; i < n; ++i) {
         if (maps[i] < 0) {
             TRY(new_obj(ctx, Obj::MAP, &midx[i]));
             maps[i] = make_handle(midx[i], ctx->objs[midx[i]].gen);
         }
-        TRY(prepare_map(ctx, midx[i], ctx->objs[fidx[i]].n, resolution));
+        bool changed = false;
+        TRY(prepare_map(ctx, midx[i], ctx->objs[fidx[i]].n, resolution, &changed));
+        if (changed) {
+            upd_idx.push_back(midx[i]);
+            upd.push_back(ctx->h_maps[midx[i]]);
+        }
     }
     if (n == 0) return VGICP_OK;
+    if (!upd.empty()) {
+        // one upload and one scatter for every descriptor that changed
+        const size_t o_d = align256(upd_idx.size() * 4);
+        std::vector<char> host(o_d + upd.size() * sizeof(MapDesc));
+        std::memcpy(host.data(), upd_idx.data(), upd_idx.size() * 4);
+        std::memcpy(host.data() + o_d, upd.data(), upd.size() * sizeof(MapDesc));
+        TRY(upload(ctx, ctx->ws_descs, host.data(), host.size()));
+        launch_scatter_map_descs((const uint32_t *)ctx->ws_descs.p, (const MapDesc *)((char *)ctx->ws_descs.p + o_d),
+                                 (int)upd.size(), ctx->d_maps, ctx->stream);
+        ctx->launches += 1;
+        CHECK_LAUNCH();
+    }
     return run_build(ctx, fidx, midx);
 }
 

@@ -22,6 +22,9 @@ struct __align__(16) WorkItem {
 void launch_frame_pack(const float *points, const float *covs, int64_t n, float4 *pa, float4 *pb, float *pc,
                        float *cmax, cudaStream_t st);
 
+// Write n map descriptors into the device table: table[idx[i]] = src[i].
+void launch_scatter_map_descs(const uint32_t *idx, const MapDesc *src, int n, MapDesc *table, cudaStream_t st);
+
 // ----------------------------------------------------------- voxelmaps ---
 // Scratch of a batched build: per point the slot it went to; per voxel the
 // exact fixed-point sums; per map the voxel counter.

@@ -194,6 +194,13 @@ __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDe
     }
 }
 
+__global__ void k_scatter_map_descs(const uint32_t *__restrict__ idx, const MapDesc *__restrict__ src, int n,
+                                    MapDesc *__restrict__ table)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) table[idx[i]] = src[i];
+}
+
 __global__ void k_export(const MapDesc *__restrict__ mp, uint32_t cap, uint32_t *counter, uint64_t *keys_out,
                          VoxelRec *rec_out)
 {
@@ -229,6 +236,12 @@ void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const B
     k_build_insert<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
     k_build_accumulate<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
     k_build_finalize<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
+}
+
+void launch_scatter_map_descs(const uint32_t *idx, const MapDesc *src, int n, MapDesc *table, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_scatter_map_descs<<<(n + 127) / 128, 128, 0, st>>>(idx, src, n, table);
 }
 
 void launch_export_voxels(const MapDesc *map_dev, uint32_t cap, uint32_t *counter, uint64_t *keys_out,

