@@ -154,6 +154,36 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
                              const double *poses, int64_t n_poses,
                              double *H, double *b, double *cost, int64_t *inliers, int out_kind);
 
+/* Size limits of vgicp_linearize_noalloc() (its fixed scratch is sized for them). */
+#define VGICP_NOALLOC_MAX_FACTORS 1024
+#define VGICP_NOALLOC_MAX_POSES 2048
+#define VGICP_NOALLOC_MAX_ITEMS 16384   /* sum over factors of ceil(source points / chunk_points) */
+
+/* vgicp_linearize() without any allocation.  The paper has no counterpart:
+ * this serves callers that must not allocate device memory when they
+ * linearise, for example a mapping loop that fixes its device-memory footprint
+ * at start-up so an optimiser iteration cannot fail for lack of memory, or an
+ * application whose own allocator owns all device memory.  They create the
+ * context, frames and voxelmaps beforehand and pass their own outputs.
+ *
+ * Same results as vgicp_linearize() with VGICP_PREC_F32 and the context's
+ * chunk_points / block_threads (the same kernels run over the same chunks).
+ * factors and poses are host arrays copied on the context stream (a pinned
+ * buffer must stay valid until the stream passes the copy); H (n_f x 144),
+ * b (n_f x 12), cost (n_f) and inliers (n_f, nullable) are DEVICE memory,
+ * written asynchronously.  Sizes beyond VGICP_NOALLOC_MAX_FACTORS,
+ * VGICP_NOALLOC_MAX_POSES or VGICP_NOALLOC_MAX_ITEMS return
+ * VGICP_ERR_INVALID_ARG; unknown handles VGICP_ERR_NOT_FOUND.
+ *
+ * All intermediate data lives in one fixed device array of about 4.5 MB that
+ * every GPU loading the library holds until the process exits.  The first call
+ * on a device looks up that array's device address (the device must be
+ * current); make that first call before any stream capture.  Every call
+ * reuses the array: calls whose work overlaps on the GPU race on it. */
+vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f,
+                                     const double *poses, int64_t n_poses,
+                                     double *H, double *b, double *cost, int64_t *inliers);
+
 /* Overlap of a source frame with a target voxelmap (Eq. 8) under the relative
  * pose T_target_source (12 doubles, host): fraction = count / N.  count is
  * optional (nullable).  N = 0 returns VGICP_ERR_EMPTY. */

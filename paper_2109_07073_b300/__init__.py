@@ -32,7 +32,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_build_voxelmaps", "vgicp_voxelmap_size", "vgicp_linearize", "vgicp_overlap",
            "vgicp_overlap_matrix", "vgicp_debug_correspondences", "vgicp_export_voxelmap",
            "vgicp_estimate_covariances", "vgicp_release", "vgicp_memory_in_use", "vgicp_kernel_launches",
-           "vgicp_last_error", "vgicp_status_string"]
+           "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc"]
 
 
 class VgicpError(RuntimeError):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_build_voxelmaps": [vp, vp, i64, f64, vp],
         "vgicp_voxelmap_size": [vp, i64, C.POINTER(i64)],
         "vgicp_linearize": [vp, vp, i64, vp, i64, vp, vp, vp, vp, C.c_int],
+        "vgicp_linearize_noalloc": [vp, vp, i64, vp, i64, vp, vp, vp, vp],
         "vgicp_overlap": [vp, i64, i64, vp, C.POINTER(f64), C.POINTER(i64)],
         "vgicp_overlap_matrix": [vp, vp, i64, vp, i64, vp, vp, vp, C.c_int],
         "vgicp_debug_correspondences": [vp, i64, i64, vp, vp, vp],
@@ -241,6 +242,20 @@ def vgicp_linearize(ctx, factors, poses, out=None):
     kind = VGICP_MEM_DEVICE if _is_torch_cuda(H) else VGICP_MEM_HOST
     _check(ctx, load().vgicp_linearize(ctx, _ptr(f), nf, _ptr(P), P.shape[0], _ptr(H), _ptr(b), _ptr(cost),
                                        _ptr(inl), kind))
+    return H, b, cost, inl
+
+
+def vgicp_linearize_noalloc(ctx, factors, poses, out):
+    """vgicp_linearize without allocating: out = (H, b, cost, inliers) torch CUDA tensors
+    (n,12,12) float64, (n,12) float64, (n,) float64, (n,) int64, written asynchronously on the
+    context stream.  For callers that must not allocate device memory at call time."""
+    f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
+    P = _pose12(poses)
+    H, b, cost, inl = out
+    if not all(_is_torch_cuda(x) for x in (H, b, cost)) or (inl is not None and not _is_torch_cuda(inl)):
+        raise ValueError("vgicp_linearize_noalloc writes device outputs: pass torch CUDA tensors")
+    _check(ctx, load().vgicp_linearize_noalloc(ctx, _ptr(f), f.shape[0], _ptr(P), P.shape[0], _ptr(H), _ptr(b),
+                                               _ptr(cost), _ptr(inl)))
     return H, b, cost, inl
 
 

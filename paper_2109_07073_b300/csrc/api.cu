@@ -1022,3 +1022,38 @@ const char *vgicp_status_string(vgicp_status s)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Read-only access to a context for entry points in other translation units.
+// ---------------------------------------------------------------------------
+namespace vg {
+
+bool ctx_view(vgicp_ctx *ctx, CtxView *v)
+{
+    if (!ctx || !v) return false;
+    v->stream = ctx->stream;
+    v->device = ctx->device;
+    v->num_sms = ctx->num_sms;
+    v->chunk = default_chunk(ctx->opt);
+    v->block = default_block(ctx->opt);
+    v->blocks_per_sm = ctx->opt.blocks_per_sm;
+    v->d_maps = ctx->d_maps;
+    v->d_frames = ctx->d_frames;
+    return true;
+}
+
+bool ctx_is_map(vgicp_ctx *ctx, int64_t handle) { return lookup(ctx, handle, Obj::MAP) != nullptr; }
+
+bool ctx_frame_size(vgicp_ctx *ctx, int64_t handle, int64_t *n)
+{
+    Obj *o = lookup(ctx, handle, Obj::FRAME);
+    if (!o) return false;
+    *n = o->n;
+    return true;
+}
+
+vgicp_status ctx_fail(vgicp_ctx *ctx, vgicp_status s, const char *msg) { return fail(ctx, s, "%s", msg); }
+
+void ctx_count_launches(vgicp_ctx *ctx, int n) { ctx->launches += n; }
+
+}  // namespace vg

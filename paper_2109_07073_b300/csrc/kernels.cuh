@@ -100,3 +100,23 @@ void launch_export_voxels(const MapDesc *map_dev, uint32_t cap, uint32_t *counte
 void launch_knn_covariances(const float *points, int64_t n, int k, double eps, float *covs, cudaStream_t st);
 
 }  // namespace vg
+
+// --------------------------------------------------- context access -------
+struct vgicp_ctx;
+
+
+namespace vg {
+
+struct CtxView {
+    cudaStream_t stream;
+    int device, num_sms, chunk, block, blocks_per_sm;
+    MapDesc *d_maps;
+    FrameDesc *d_frames;
+};
+
+bool ctx_view(::vgicp_ctx *ctx, CtxView *v);
+bool ctx_is_map(::vgicp_ctx *ctx, int64_t handle);
+bool ctx_frame_size(::vgicp_ctx *ctx, int64_t handle, int64_t *n);
+void ctx_count_launches(::vgicp_ctx *ctx, int n);
+
+}  // namespace vg
