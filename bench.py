@@ -217,9 +217,12 @@ def run_ours(a):
         step()
     torch.cuda.synchronize()
     if a.profile_only:
+        # only the timed steps are profiled (ncu --profile-from-start off)
+        torch.cuda.profiler.start()
         for _ in range(a.steps):
             step()
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         return
     launches0 = ctx.kernel_launches()
     phase_ev = []
@@ -241,6 +244,21 @@ def run_ours(a):
     ph_mean = ph.mean(0)
     # parity spot-check of this run's outputs is in the tests; here only sanity
     inl = out[3].cpu().numpy()
+
+    # the overlap matrix with every point looked up (pair culling off), for reference
+    ctx.set_options(overlap_cull=0)
+    ctx.overlap_matrix(frames, maps, poses, poses, out=d_counts)
+    torch.cuda.synchronize()
+    bf_ev = []
+    for _ in range(2):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        ctx.overlap_matrix(frames, maps, poses, poses, out=d_counts)
+        e1.record(stream)
+        bf_ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ctx.set_options(overlap_cull=1)
+    bf_ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in bf_ev]))
 
     # plain float64 arm: the same step with the linearisation on the plain path
     ctx.set_options(precision=vg.VGICP_PREC_F64)
@@ -332,6 +350,9 @@ def run_ours(a):
         "plain_f64": {"value": corr_units * world / (f64_step / 1e3), "unit": UNIT, "ms_per_step": f64_step,
                       "linearize_ms": f64_lin, "linearize_only_value": corr_units / (f64_lin / 1e3),
                       "factors_per_s": n_f / (f64_lin / 1e3)},
+        "overlap_all_points": {"ms": bf_ms, "lookups": int(n_src.sum()) * n_frames,
+                               "lookups_per_s": int(n_src.sum()) * n_frames / (bf_ms / 1e3),
+                               "note": "overlap matrix with pair culling off (every point of every pair looked up)"},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -95,6 +95,12 @@ typedef struct {
     int32_t block_threads;    /* threads per block of the batched path (multiple of 32, <= 1024; 0 = default 256) */
     int32_t blocks_per_sm;    /* persistent grid = SMs x this (0 = default from occupancy) */
     int64_t hbm_budget_bytes; /* device bytes handles may hold in total (0 = unlimited) */
+    /* 1 (default): overlap pairs whose source bounding box, moved by the pair's
+     * pose and grown by a margin far above float64 rounding, misses the target's
+     * voxel bounding box are answered 0 without visiting their points (exact:
+     * such a pair has no correspondence).  0: every point is looked up. */
+    int32_t overlap_cull;
+    int32_t reserved;
 } vgicp_options;
 
 /* Fill *opt with the defaults above. */

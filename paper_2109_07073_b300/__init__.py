@@ -43,7 +43,8 @@ class VgicpError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("chunk_points", C.c_int32), ("block_threads", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+                ("blocks_per_sm", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("overlap_cull", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Factor(C.Structure):

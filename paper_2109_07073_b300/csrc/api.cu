@@ -214,7 +214,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, int64_t n, uint32_t *out_idx)
 {
     const size_t o_pb = align256((size_t)n * 16), o_pc = o_pb + align256((size_t)n * 16);
-    const size_t o_cm = o_pc + align256((size_t)n * 4), bytes = o_cm + 256;
+    const size_t o_st = o_pc + align256((size_t)n * 4), bytes = o_st + 256;
     TRY(budget_check(ctx, (int64_t)bytes));
     uint32_t idx;
     TRY(new_obj(ctx, Obj::FRAME, &idx));
@@ -234,10 +234,13 @@ vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, 
     f.pa = (const float4 *)base;
     f.pb = (const float4 *)(base + o_pb);
     f.pc = (const float *)(base + o_pc);
-    f.cmax = (const float *)(base + o_cm);
+    f.stats = (const float *)(base + o_st);
     f.n = n;
-    CU(cudaMemsetAsync(base + o_cm, 0, 4, ctx->stream));
-    launch_frame_pack(d_pts, d_cov, n, (float4 *)f.pa, (float4 *)f.pb, (float *)f.pc, (float *)f.cmax, ctx->stream);
+    // statistics start at: zero maxima of |c| and |p|, +inf minima, -inf maxima
+    static const uint32_t init[kStatCount] = {0, 0, 0, 0, kOrderedPosInf, kOrderedPosInf, kOrderedPosInf,
+                                              kOrderedNegInf, kOrderedNegInf, kOrderedNegInf};
+    CU(cudaMemcpyAsync(base + o_st, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+    launch_frame_pack(d_pts, d_cov, n, (float4 *)f.pa, (float4 *)f.pb, (float *)f.pc, (float *)f.stats, ctx->stream);
     ctx->launches += n > 0;
     CHECK_LAUNCH();
     TRY(put_frame_desc(ctx, idx));
@@ -259,10 +262,13 @@ bool is_pow2_res(double r)
     return std::frexp(r, &e) == 0.5;
 }
 
+size_t map_bytes(uint32_t cap);
+
 void fill_map_desc(MapDesc &m, char *base, uint32_t cap, double r)
 {
     m.keys = (uint64_t *)base;
     m.rec = (VoxelRec *)(base + align256((size_t)cap * 8));
+    m.kbox = (int32_t *)(base + map_bytes(cap) - 256 + 16);
     m.mask = cap - 1;
     uint32_t l = 0;
     while ((1u << l) < cap) ++l;
@@ -357,24 +363,6 @@ vgicp_status prepare_map(vgicp_ctx *ctx, uint32_t idx, int64_t n, double r, bool
 
 bool valid_res(double r) { return std::isfinite(r) && r > 0.0 && r < 1e30; }
 
-void split_host(const double *T, PoseParam &p)
-{
-    for (int i = 0; i < 12; ++i) p.T[i] = T[i];
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) {
-            const double v = T[4 * i + j];
-            const float h = (float)v;
-            p.Rh[3 * i + j] = h;
-            p.Rl[3 * i + j] = (float)(v - (double)h);
-        }
-        const double v = T[4 * i + 3];
-        const float h = (float)v;
-        p.th[i] = h;
-        p.tl[i] = (float)(v - (double)h);
-    }
-    p.pad0 = p.pad1 = 0;
-}
-
 bool finite_pose(const double *T)
 {
     for (int i = 0; i < 12; ++i)
@@ -453,6 +441,7 @@ vgicp_status vgicp_options_default(vgicp_options *opt)
     opt->block_threads = 256;
     opt->blocks_per_sm = 0;
     opt->hbm_budget_bytes = 0;
+    opt->overlap_cull = 1;
     return VGICP_OK;
 }
 
@@ -466,6 +455,8 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "block_threads must be 0, 128, 256 or 512");
     if (o->blocks_per_sm < 0 || o->hbm_budget_bytes < 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
+    if (o->overlap_cull != 0 && o->overlap_cull != 1)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_cull must be 0 or 1");
     return VGICP_OK;
 }
 
@@ -695,7 +686,8 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
     Plan &P = ctx->plan;
     TRY(ensure(ctx, ctx->ws_params, (size_t)n_f * sizeof(PoseParam)));
     PoseParam *d_params = (PoseParam *)ctx->ws_params.p;
-    launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)ctx->ws_poses.p, d_params, ctx->stream);
+    launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)ctx->ws_poses.p, ctx->d_maps,
+                           ctx->d_frames, d_params, ctx->stream);
     ctx->launches += 1;
     CHECK_LAUNCH();
     // outputs: caller's device buffers, or a device workspace copied back to the host
@@ -759,10 +751,6 @@ vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t tar
     if (!finite_pose(T)) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap: non-finite pose");
     const int64_t n = fo->n;
     if (n == 0) return fail(ctx, VGICP_ERR_EMPTY, "overlap of an empty source is undefined (Eq. 8)");
-    PoseParam p;
-    split_host(T, p);
-    p.map = (int32_t)mi;
-    p.frame = (int32_t)fi;
     std::vector<WorkItem> items;
     for (int64_t s = 0; s < n; s += 4096) {
         WorkItem w;
@@ -771,7 +759,11 @@ vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t tar
         w.count = (int32_t)std::min<int64_t>(4096, n - s);
         items.push_back(w);
     }
-    TRY(upload(ctx, ctx->ws_pairs, &p, 1));
+    TRY(upload(ctx, ctx->ws_poses, T, 12));
+    TRY(ensure(ctx, ctx->ws_pairs, sizeof(PoseParam)));
+    launch_prepare_given((const double *)ctx->ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames,
+                         ctx->opt.overlap_cull, (PoseParam *)ctx->ws_pairs.p, ctx->stream);
+    ctx->launches += 1;
     TRY(upload(ctx, ctx->ws_chunks, items.data(), items.size()));
     TRY(ensure(ctx, ctx->ws_counts, 8));
     CU(cudaMemsetAsync(ctx->ws_counts.p, 0, 8, ctx->stream));
@@ -822,7 +814,7 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
         if (!std::isfinite(poses_tgt[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
     // source chunks; the kernel enumerates (target tile, chunk, target) so the
     // CTAs in flight share a few target tables and a few source chunks
-    const int chunk = 4096, tile = 16;
+    const int chunk = overlap_matrix_chunk();
     std::vector<WorkItem> chunks;
     for (int64_t s = 0; s < n_src; ++s)
         for (int64_t o = 0; o < nsrc[s]; o += chunk) {
@@ -841,7 +833,8 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
     TRY(ensure(ctx, ctx->ws_pairs, (size_t)n_pairs * sizeof(PoseParam)));
     launch_prepare_pairs((const double *)ctx->ws_poses.p, (const double *)ctx->ws_stage.p,
                          (const int32_t *)ctx->ws_fidx.p, (const int32_t *)ctx->ws_midx.p, (int)n_src, (int)n_tgt,
-                         (PoseParam *)ctx->ws_pairs.p, ctx->stream);
+                         ctx->d_maps, ctx->d_frames, ctx->opt.overlap_cull, (PoseParam *)ctx->ws_pairs.p,
+                         ctx->stream);
     unsigned long long *dcounts = (unsigned long long *)counts;
     if (out_kind == VGICP_MEM_HOST) {
         TRY(ensure(ctx, ctx->ws_counts, (size_t)n_pairs * 8));
@@ -850,7 +843,7 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
     CU(cudaMemsetAsync(dcounts, 0, (size_t)n_pairs * 8, ctx->stream));
     const int grid = ctx->num_sms * 8;
     launch_overlap_matrix((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames,
-                          (const WorkItem *)ctx->ws_chunks.p, (int)chunks.size(), (int)n_tgt, tile, dcounts, grid,
+                          (const WorkItem *)ctx->ws_chunks.p, (int)chunks.size(), (int)n_tgt, dcounts, grid,
                           ctx->stream);
     ctx->launches += 2;
     CHECK_LAUNCH();
@@ -873,11 +866,11 @@ vgicp_status vgicp_debug_correspondences(vgicp_ctx *ctx, vgicp_frame_t source, v
         return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)target);
     const int64_t n = fo->n;
     if (n == 0) return VGICP_OK;
-    PoseParam p;
-    split_host(T, p);
-    p.map = (int32_t)mi;
-    p.frame = (int32_t)fi;
-    TRY(upload(ctx, ctx->ws_pairs, &p, 1));
+    TRY(upload(ctx, ctx->ws_poses, T, 12));
+    TRY(ensure(ctx, ctx->ws_pairs, sizeof(PoseParam)));
+    launch_prepare_given((const double *)ctx->ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames, 0,
+                         (PoseParam *)ctx->ws_pairs.p, ctx->stream);
+    ctx->launches += 1;
     TRY(ensure(ctx, ctx->ws_out, (size_t)n * (24 + 4)));
     int64_t *dk = (int64_t *)ctx->ws_out.p;
     int32_t *dh = (int32_t *)(dk + 3 * n);

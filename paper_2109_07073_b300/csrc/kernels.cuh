@@ -18,9 +18,9 @@ struct __align__(16) WorkItem {
 
 // ----------------------------------------------------------- frames ------
 // Re-lay n points (n x 3) and covariances (n x 6) into the three frame streams
-// and compute the frame's max |covariance entry| (cmax must be zeroed).
+// and gather the frame statistics (stats initialised as the kStat* layout says).
 void launch_frame_pack(const float *points, const float *covs, int64_t n, float4 *pa, float4 *pb, float *pc,
-                       float *cmax, cudaStream_t st);
+                       float *stats, cudaStream_t st);
 
 // Write n map descriptors into the device table: table[idx[i]] = src[i].
 void launch_scatter_map_descs(const uint32_t *idx, const MapDesc *src, int n, MapDesc *table, cudaStream_t st);
@@ -51,7 +51,12 @@ void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const B
 // ----------------------------------------------------------- linearise ---
 // Relative poses T_BA = T_B^-1 T_A for every factor, in the forms the kernels use.
 void launch_prepare_factors(const int32_t *factor_idx /* n_f x 4: map, frame, pose_t, pose_s */, int n_f,
-                            const double *poses, PoseParam *out, cudaStream_t st);
+                            const double *poses, const MapDesc *maps, const FrameDesc *frames, PoseParam *out,
+                            cudaStream_t st);
+
+// One pair with a given relative pose T (12 doubles, device).
+void launch_prepare_given(const double *T, int map, int frame, const MapDesc *maps, const FrameDesc *frames,
+                          int cull, PoseParam *out, cudaStream_t st);
 
 // Batched float32 path: one persistent launch over all work items; each item
 // writes 28 float64 partial sums and an inlier count.
@@ -78,15 +83,18 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
                     int n_items, unsigned long long *counts, int grid, cudaStream_t st);
 
 // Overlap matrix: counts[s * n_tgt + t] += hits of source s against target t.
-// chunks lists every source's point chunks (unit = source index); the items are
-// implied: target tiles outermost, then chunks, then the targets of the tile.
+// chunks lists every source's point chunks of overlap_matrix_chunk() points
+// (unit = source index); the kernel enumerates (target tile, chunk) items.
+int overlap_matrix_chunk();
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames,
-                           const WorkItem *chunks, int n_chunks, int n_tgt, int tile, unsigned long long *counts,
-                           int grid, cudaStream_t st);
+                           const WorkItem *chunks, int n_chunks, int n_tgt, unsigned long long *counts, int grid,
+                           cudaStream_t st);
 
-// Pair parameters of an overlap matrix: pair (s, t) -> T_t^-1 T_s.
+// Pair parameters of an overlap matrix: pair (s, t) -> T_t^-1 T_s; with cull set,
+// pairs whose source bounding box cannot meet the target's voxels are flagged.
 void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, const int32_t *frame_idx,
-                          const int32_t *map_idx, int n_src, int n_tgt, PoseParam *out, cudaStream_t st);
+                          const int32_t *map_idx, int n_src, int n_tgt, const MapDesc *maps,
+                          const FrameDesc *frames, int cull, PoseParam *out, cudaStream_t st);
 
 // Per-point association (debug / parity): keys n x 3 (INT64_MIN if invalid), hit n.
 void launch_correspondences(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,

@@ -66,7 +66,67 @@ __device__ __forceinline__ void split_pose(const double *T, PoseParam &p)
     }
 }
 
+// The per-pair bounds of the float32 floors and, when asked, the exact culling
+// test, from p.T, the target map and the source frame's statistics.
+__device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f, int cull)
+{
+    double pmax[3], mn[3], mx[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        pmax[j] = (double)f.stats[kStatPmax + j];
+        mn[j] = (double)from_ordered_bits(__float_as_uint(f.stats[kStatMin + j]));
+        mx[j] = (double)from_ordered_bits(__float_as_uint(f.stats[kStatMax + j]));
+    }
+    double tmax = 0.0, ext = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double t = p.T[4 * i + 3];
+        const double Xr = fabs(p.T[4 * i]) * pmax[0] + fabs(p.T[4 * i + 1]) * pmax[1] + fabs(p.T[4 * i + 2]) * pmax[2];
+        // split translation t = k0 r + tf (|tf| <= r / 2)
+        double k0 = rint(t * m.inv_r);
+        if (!(fabs(k0) < 4194304.0)) k0 = 0.0;   // |t| beyond 2^22 voxels: no split
+        const double tf = t - k0 * m.r;
+        p.k0[i] = (int32_t)k0;
+        p.tfh[i] = __double2float_rn(tf);
+        const double X = Xr + fabs(t), Xs = Xr + fabs(tf);
+        const double tol = 0x1p-21 * Xs + 0x1p-22 * m.r + 0x1p-47 * X + 0x1p-100;
+        p.tol[i] = __double2float_ru(tol);
+        p.rup[i] = __double2float_rd((double)m.r_h - tol);
+        const double fm = 0x1p-40 * X + 0x1p-100;
+        p.ffm[i] = __double2float_ru(fm);
+        p.ffup[i] = __double2float_rd((double)m.r_h - fm - 0x1p-22 * m.r);
+        tmax = fmax(tmax, fabs(t));
+        ext = fmax(ext, fmax(fabs(mn[i]), fabs(mx[i])));
+    }
+    p.cull = 0;
+    p.pad[0] = p.pad[1] = p.pad[2] = 0;
+    if (!cull) return;
+    // Every transformed point lies in the box of the transformed corners of the
+    // source's bounding box; if that box (grown by a margin far above the
+    // float64 rounding of any point) misses the target's voxel box on one axis,
+    // no point of the pair can find a voxel.
+    const int *kb = m.kbox;
+    if (!(mn[0] <= mx[0] && mn[1] <= mx[1] && mn[2] <= mx[2]) || kb[0] > kb[3]) {
+        p.cull = 1;
+        return;
+    }
+    const double mu = 1e-6 * (1.0 + tmax + 3.0 * ext);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        double lo = 0.0, hi = 0.0;
+        for (int c = 0; c < 8; ++c) {
+            const double x = p.T[4 * i] * ((c & 1) ? mx[0] : mn[0]) + p.T[4 * i + 1] * ((c & 2) ? mx[1] : mn[1]) +
+                             p.T[4 * i + 2] * ((c & 4) ? mx[2] : mn[2]) + p.T[4 * i + 3];
+            lo = (c == 0) ? x : fmin(lo, x);
+            hi = (c == 0) ? x : fmax(hi, x);
+        }
+        const double blo = (double)kb[i] * m.r, bhi = ((double)kb[3 + i] + 1.0) * m.r;
+        if (hi + mu < blo || lo - mu > bhi) p.cull = 1;
+    }
+}
+
 __global__ void k_prepare_factors(const int32_t *__restrict__ idx, int n_f, const double *__restrict__ poses,
+                                  const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
                                   PoseParam *__restrict__ out)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,13 +136,14 @@ __global__ void k_prepare_factors(const int32_t *__restrict__ idx, int n_f, cons
     split_pose(p.T, p);
     p.map = idx[4 * f + 0];
     p.frame = idx[4 * f + 1];
-    p.pad0 = p.pad1 = 0;
+    finish_param(p, maps[p.map], frames[p.frame], 0);
     out[f] = p;
 }
 
 __global__ void k_prepare_pairs(const double *__restrict__ ps, const double *__restrict__ pt,
                                 const int32_t *__restrict__ fidx, const int32_t *__restrict__ midx, int n_src,
-                                int n_tgt, PoseParam *__restrict__ out)
+                                int n_tgt, const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
+                                int cull, PoseParam *__restrict__ out)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= (int64_t)n_src * n_tgt) return;
@@ -92,8 +153,21 @@ __global__ void k_prepare_pairs(const double *__restrict__ ps, const double *__r
     split_pose(p.T, p);
     p.map = midx[t];
     p.frame = fidx[s];
-    p.pad0 = p.pad1 = 0;
+    finish_param(p, maps[p.map], frames[p.frame], cull);
     out[g] = p;
+}
+
+__global__ void k_prepare_given(const double *__restrict__ T, int map, int frame, const MapDesc *__restrict__ maps,
+                                const FrameDesc *__restrict__ frames, int cull, PoseParam *__restrict__ out)
+{
+    PoseParam p;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p.T[i] = T[i];
+    split_pose(p.T, p);
+    p.map = map;
+    p.frame = frame;
+    finish_param(p, maps[map], frames[frame], cull);
+    *out = p;
 }
 
 // Voxel coordinate and in-voxel offset of one point (batched path).
@@ -104,7 +178,7 @@ __device__ __forceinline__ bool point_key_ff(const PoseParam &P, const MapDesc &
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         decided &= axis_key_ff(P.Rh + 3 * a, P.Rl + 3 * a, P.th[a], P.tl[a], px, py, pz, m.r_h, m.r_l, m.inv_rf,
-                               k[a], d[a]);
+                               P.ffm[a], P.ffup[a], k[a], d[a]);
     if (decided) return k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN;
     double q[3];
     if (!key_f64(P.T, px, py, pz, m.inv_r, k, q)) return false;
@@ -182,7 +256,7 @@ __global__ void __launch_bounds__(BLOCK) k_linearize_f32(const PoseParam *__rest
             const float c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
             const float det = m00 * c00 + m01 * c01 + m02 * c02;
             if (!(det > 0.f)) continue;
-            const float id = 1.f / det;
+            const float id = __frcp_rn(det);
             const float o00 = c00 * id, o01 = c01 * id, o02 = c02 * id, o11 = c11 * id, o12 = c12 * id,
                         o22 = c22 * id;
             // w = Omega e, cost = e . w
@@ -486,19 +560,27 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
 
 }  // namespace
 
-void launch_prepare_factors(const int32_t *factor_idx, int n_f, const double *poses, PoseParam *out, cudaStream_t st)
+void launch_prepare_factors(const int32_t *factor_idx, int n_f, const double *poses, const MapDesc *maps,
+                            const FrameDesc *frames, PoseParam *out, cudaStream_t st)
 {
     if (n_f <= 0) return;
-    k_prepare_factors<<<(n_f + 127) / 128, 128, 0, st>>>(factor_idx, n_f, poses, out);
+    k_prepare_factors<<<(n_f + 127) / 128, 128, 0, st>>>(factor_idx, n_f, poses, maps, frames, out);
+}
+
+void launch_prepare_given(const double *T, int map, int frame, const MapDesc *maps, const FrameDesc *frames,
+                          int cull, PoseParam *out, cudaStream_t st)
+{
+    k_prepare_given<<<1, 1, 0, st>>>(T, map, frame, maps, frames, cull, out);
 }
 
 void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, const int32_t *frame_idx,
-                          const int32_t *map_idx, int n_src, int n_tgt, PoseParam *out, cudaStream_t st)
+                          const int32_t *map_idx, int n_src, int n_tgt, const MapDesc *maps,
+                          const FrameDesc *frames, int cull, PoseParam *out, cudaStream_t st)
 {
     const int64_t n = (int64_t)n_src * n_tgt;
     if (n <= 0) return;
     k_prepare_pairs<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(poses_src, poses_tgt, frame_idx, map_idx, n_src,
-                                                               n_tgt, out);
+                                                               n_tgt, maps, frames, cull, out);
 }
 
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,

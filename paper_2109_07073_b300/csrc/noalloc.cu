@@ -161,7 +161,7 @@ extern "C" vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_fact
     int threads = 32;
     while (threads < n_f) threads <<= 1;
     k_noalloc_plan<<<1, threads, 0, v.stream>>>(d_f, (int)n_f, v.d_frames, v.chunk, d_idx, d_begin, d_items);
-    launch_prepare_factors(d_idx, (int)n_f, d_poses, d_params, v.stream);
+    launch_prepare_factors(d_idx, (int)n_f, d_poses, v.d_maps, v.d_frames, d_params, v.stream);
     const int per_sm = v.blocks_per_sm > 0 ? v.blocks_per_sm : (2048 / v.block > 0 ? 2048 / v.block : 1);
     int grid = v.num_sms * per_sm;
     if (grid > n_items) grid = (int)n_items;

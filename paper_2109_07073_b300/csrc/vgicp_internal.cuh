@@ -37,6 +37,7 @@ struct __align__(16) VoxelRec {
 struct MapDesc {
     uint64_t *keys;
     VoxelRec *rec;
+    int32_t *kbox;       // device: min voxel coordinate (3), max voxel coordinate (3)
     uint32_t mask;       // cap - 1
     uint32_t log2cap;    // >= 4
     double r, inv_r;     // resolution and fl64(1 / r)
@@ -50,8 +51,30 @@ struct FrameDesc {
     const float4 *pb;
     const float *pc;
     int64_t n;
-    const float *cmax;   // device scalar: max |covariance entry| of the frame
+    const float *stats;  // device: kStat* entries below
 };
+
+// Frame statistics, over the points with finite coordinates.
+enum {
+    kStatCmax = 0,   // max |covariance entry|
+    kStatPmax = 1,   // max |x|, |y|, |z| (3)
+    kStatMin = 4,    // min x, y, z as order-preserving uint32 (3)
+    kStatMax = 7,    // max x, y, z as order-preserving uint32 (3)
+    kStatCount = 10
+};
+
+// float <-> uint32 mapping that preserves order (for atomicMin / atomicMax)
+constexpr uint32_t kOrderedPosInf = 0xFF800000u;   // ordered_bits(+inf)
+constexpr uint32_t kOrderedNegInf = 0x007FFFFFu;   // ordered_bits(-inf)
+__device__ __forceinline__ uint32_t ordered_bits(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered_bits(uint32_t o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
 
 // Per-factor (or per-pair) transform in the forms the kernels use.
 struct __align__(16) PoseParam {
@@ -59,7 +82,16 @@ struct __align__(16) PoseParam {
     float Rh[9], Rl[9];  // R = Rh + Rl (float32 pairs), row-major
     float th[3], tl[3];  // t = th + tl
     int32_t map, frame;  // descriptor-table indices
-    int32_t pad0, pad1;
+    // split translation t = k0 r + tf for the float32 voxel floor (overlap)
+    int32_t k0[3];
+    float tfh[3];        // fl32(tf)
+    float tol[3];        // float32 floor decided when tol <= x - k r <= rup
+    float rup[3];
+    // margins of the float32-pair floor (linearisation)
+    float ffm[3];        // decided when ffm <= x - k r <= ffup
+    float ffup[3];
+    int32_t cull;        // 1: the pair provably has no correspondence
+    int32_t pad[3];
 };
 
 // ---------------------------------------------------------------- keys ----
@@ -135,14 +167,16 @@ __device__ __forceinline__ float face_dist(float s, float lo, float k, float r_h
 // One axis of the voxel coordinate from a float32-pair transform.
 //
 // x = Rh.p + th + (Rl.p + tl) is formed as an unevaluated pair (s, lo) with
-// error-free products and sums, accurate to ~2^-45 of X = sum |Rh_j p_j| + |th|.
+// error-free products and sums, accurate to ~2^-44 of X = sum |R_j| pmax_j + |t|.
 // The float64 reference differs from the exact value by < 2^-50 X (three fmas,
-// one multiply by inv_r).  Returns false when x is within 2^-40 X of a voxel
-// face (or not finite); the caller then evaluates the float64 reference.
-// On success: k is the reference floor and d = x - k r in [0, r).
+// one multiply by inv_r).  The caller's margins: lo_m = 2^-40 X, and
+// up_m = r - lo_m - 2^-22 r (the face distance g0 carries ~2^-24 r of rounding).
+// Returns false when x - k r is outside [lo_m, up_m] (or not finite); the caller
+// then evaluates the float64 reference.  On success: k is the reference floor
+// and d = x - k r in [0, r).
 __device__ __forceinline__ bool axis_key_ff(const float *Rh, const float *Rl, float th, float tl, float px,
-                                            float py, float pz, float r_h, float r_l, float inv_rf, int &k,
-                                            float &d)
+                                            float py, float pz, float r_h, float r_l, float inv_rf, float lo_m,
+                                            float up_m, int &k, float &d)
 {
     const float h0 = __fmul_rn(Rh[0], px), l0 = __fmaf_rn(Rh[0], px, -h0);
     const float h1 = __fmul_rn(Rh[1], py), l1 = __fmaf_rn(Rh[1], py, -h1);
@@ -156,27 +190,35 @@ __device__ __forceinline__ bool axis_key_ff(const float *Rh, const float *Rl, fl
     lo = __fmaf_rn(Rl[0], px, lo);
     lo = __fmaf_rn(Rl[1], py, lo);
     lo = __fmaf_rn(Rl[2], pz, lo);
-    const float X = fabsf(h0) + fabsf(h1) + fabsf(h2) + fabsf(th);
-    const float m = fmaxf(X * 0x1p-40f, 0x1p-100f);
-    float kf = floorf(__fmul_rn(__fadd_rn(s, lo), inv_rf));
-    float g0 = face_dist(s, lo, kf, r_h, r_l);
-    float g1 = face_dist(s, lo, kf + 1.f, r_h, r_l);
-    if (g0 < 0.f) {
-        kf -= 1.f;
-        g1 = g0;
-        g0 = face_dist(s, lo, kf, r_h, r_l);
-    } else if (g1 >= 0.f) {
-        kf += 1.f;
-        g0 = g1;
-        g1 = face_dist(s, lo, kf + 1.f, r_h, r_l);
-    }
-    if (!(g0 >= m && g1 <= -m)) return false;   // also catches NaN / inf
+    // candidate floor (off by one only within ~2^-24 |x| of a face: then g0 < 0
+    // or g0 >= r and the point is left undecided)
+    const float kf = floorf(__fmul_rn(__fadd_rn(s, lo), inv_rf));
+    const float g0 = face_dist(s, lo, kf, r_h, r_l);
+    if (!(g0 >= lo_m && g0 <= up_m)) return false;   // also catches NaN / inf
     if (!(kf >= (float)kKeyMin && kf <= (float)kKeyMax)) {
-        k = INT32_MIN;                            // decided: out of range
+        k = INT32_MIN;                                // decided: out of range
         return true;
     }
     k = (int)kf;
     d = g0;
+    return true;
+}
+
+// One axis of the voxel floor from a plain float32 fma chain on the split
+// translation: x' = R p + tf with t = k0 r + tf, so floor(x / r) = floor(x' / r) + k0
+// and the float32 error bound depends on |R p| + |tf| only, not on |t|.  The
+// caller's tol covers the float32 error (2^-22 (sum |R_j| pmax_j + |tf|)), the
+// float64 reference's own rounding and the face-distance rounding.  Returns
+// false when undecided; k = INT32_MIN marks a decided out-of-range coordinate.
+__device__ __forceinline__ bool axis_key_split(const float *Rh, float tfh, float tol, float rup, int k0, float px,
+                                               float py, float pz, float r_h, float r_l, float inv_rf, int &k)
+{
+    const float x = __fmaf_rn(Rh[0], px, __fmaf_rn(Rh[1], py, __fmaf_rn(Rh[2], pz, tfh)));
+    const float kf = floorf(__fmul_rn(x, inv_rf));
+    const float d = __fmaf_rn(-kf, r_l, __fmaf_rn(-kf, r_h, x));
+    if (!(d >= tol && d <= rup)) return false;
+    const int kk = (int)kf + k0;
+    k = (kk >= -kKeyOffset && kk <= kKeyOffset - 1) ? kk : INT32_MIN;
     return true;
 }
 

@@ -19,11 +19,15 @@ namespace {
 
 constexpr int kAcc = 10;   // count, 3 mean sums, 6 covariance sums
 
+// Re-lay the points and covariances and gather the frame statistics (stats
+// must hold the initial values: zeros, then +inf minima and -inf maxima).
 __global__ void k_frame_pack(const float *__restrict__ pts, const float *__restrict__ cov, int64_t n,
                              float4 *__restrict__ pa, float4 *__restrict__ pb, float *__restrict__ pc,
-                             unsigned int *cmax_bits)
+                             unsigned int *stats)
 {
-    float m = 0.f;
+    float m = 0.f, am[3] = {0.f, 0.f, 0.f};
+    uint32_t mn[3] = {kOrderedPosInf, kOrderedPosInf, kOrderedPosInf};
+    uint32_t mx[3] = {kOrderedNegInf, kOrderedNegInf, kOrderedNegInf};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float *p = pts + 3 * i, *c = cov + 6 * i;
         pa[i] = make_float4(p[0], p[1], p[2], c[0]);
@@ -31,10 +35,34 @@ __global__ void k_frame_pack(const float *__restrict__ pts, const float *__restr
         pc[i] = c[5];
 #pragma unroll
         for (int j = 0; j < 6; ++j) m = fmaxf(m, fabsf(c[j]));
+        if (isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2])) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                am[j] = fmaxf(am[j], fabsf(p[j]));
+                mn[j] = min(mn[j], ordered_bits(p[j]));
+                mx[j] = max(mx[j], ordered_bits(p[j]));
+            }
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(cmax_bits, __float_as_uint(m));
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            am[j] = fmaxf(am[j], __shfl_xor_sync(0xffffffffu, am[j], o));
+            mn[j] = min(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
+            mx[j] = max(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (m > 0.f) atomicMax(stats + kStatCmax, __float_as_uint(m));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (am[j] > 0.f) atomicMax(stats + kStatPmax + j, __float_as_uint(am[j]));
+            atomicMin(stats + kStatMin + j, mn[j]);
+            atomicMax(stats + kStatMax + j, mx[j]);
+        }
+    }
 }
 
 __device__ __forceinline__ int find_unit(const int64_t *prefix, int n_units, int64_t g)
@@ -54,9 +82,14 @@ __global__ void k_build_clear(const MapDesc *__restrict__ maps, const BuildUnit 
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int u = find_unit(slot_prefix, n_units, g);
         const int64_t s = g - slot_prefix[u];
-        maps[units[u].map].keys[s] = kEmptyKey;
+        const MapDesc &m = maps[units[u].map];
+        m.keys[s] = kEmptyKey;
         vid_of_slot[g] = -1;
-        if (s == 0) *units[u].n_voxels = 0;
+        if (s == 0) {
+            *units[u].n_voxels = 0;
+            m.kbox[0] = m.kbox[1] = m.kbox[2] = INT32_MAX;
+            m.kbox[3] = m.kbox[4] = m.kbox[5] = INT32_MIN;
+        }
     }
 }
 
@@ -107,6 +140,11 @@ __global__ void k_build_insert(const MapDesc *__restrict__ maps, const FrameDesc
                         int64_t *acc = scr.acc + (u.point_base + vid) * kAcc;
 #pragma unroll
                         for (int j = 0; j < kAcc; ++j) acc[j] = 0;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            atomicMin(m.kbox + j, k[j]);
+                            atomicMax(m.kbox + 3 + j, k[j]);
+                        }
                         slot = (int32_t)s;
                         break;
                     }
@@ -119,9 +157,9 @@ __global__ void k_build_insert(const MapDesc *__restrict__ maps, const FrameDesc
     }
 }
 
-__device__ __forceinline__ float cov_scale(const float *cmax)
+__device__ __forceinline__ float cov_scale(const float *stats)
 {
-    const float c = *cmax;
+    const float c = stats[kStatCmax];
     if (!(c > 0.f)) return 1.f;
     int e;
     frexpf(c, &e);                 // c < 2^e
@@ -139,7 +177,7 @@ __global__ void k_build_accumulate(const MapDesc *__restrict__ maps, const Frame
         const BuildUnit u = units[w.unit];
         const MapDesc m = maps[u.map];
         const FrameDesc f = frames[u.frame];
-        const float sc = cov_scale(f.cmax), sm = mean_scale(m);
+        const float sc = cov_scale(f.stats), sm = mean_scale(m);
         for (int64_t i = w.start + threadIdx.x; i < w.start + w.count; i += blockDim.x) {
             const int32_t slot = scr.slot_of_point[u.point_base + i];
             if (slot < 0) continue;
@@ -177,7 +215,7 @@ __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDe
         const MapDesc m = maps[u.map];
         const FrameDesc f = frames[u.frame];
         const uint32_t nv = *u.n_voxels;
-        const float isc = 1.f / cov_scale(f.cmax), ism = 1.f / mean_scale(m);
+        const float isc = 1.f / cov_scale(f.stats), ism = 1.f / mean_scale(m);
         for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
             if (v >= (int64_t)nv) break;
             const int64_t *acc = scr.acc + (u.point_base + v) * kAcc;
@@ -217,13 +255,13 @@ __global__ void k_export(const MapDesc *__restrict__ mp, uint32_t cap, uint32_t 
 }  // namespace
 
 void launch_frame_pack(const float *points, const float *covs, int64_t n, float4 *pa, float4 *pb, float *pc,
-                       float *cmax, cudaStream_t st)
+                       float *stats, cudaStream_t st)
 {
     if (n <= 0) return;
     const int block = 256;
     int grid = (int)((n + block - 1) / block);
     if (grid > 148 * 16) grid = 148 * 16;
-    k_frame_pack<<<grid, block, 0, st>>>(points, covs, n, pa, pb, pc, (unsigned int *)cmax);
+    k_frame_pack<<<grid, block, 0, st>>>(points, covs, n, pa, pb, pc, (unsigned int *)stats);
 }
 
 void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const BuildUnit *units, int n_units,

@@ -102,6 +102,12 @@ def test_correspondences_bit_exact(ctx, single, r):
     T = dg.identity_pose()
     T[:, 3] = [r * 3, -r * 2, r]          # integer voxel shift: faces stay on faces
     poses.append(T)
+    T = dg.identity_pose()
+    T[:, 3] = [r * 1000, -r * 2000, r * 777]   # large shift: split translation, faces on faces
+    poses.append(T)
+    T = dg.random_pose(rng, 180, 1.0)
+    T[:, 3] += [512.0, -300.25, 40.5]           # large translation with rotation
+    poses.append(T)
     for pts in clouds:
         hf = ctx.add_frame(pts, np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (pts.shape[0], 1)))
         for P in poses:
@@ -129,20 +135,24 @@ def test_overlap_empty_source_is_an_error(ctx, single):
 
 @pytest.fixture(scope="module")
 def loop_frames():
-    """Eight consecutive frames of the urban loop (64 x 1024 LiDAR, 20,000 points each)."""
-    ids = list(range(10, 18))
+    """Eight frames of the urban loop (64 x 1024 LiDAR, 20,000 points each): five neighbours
+    and three far away, so some pairs overlap and some are provably disjoint."""
+    ids = [10, 11, 12, 13, 14, 200, 201, 330]
     g = dg.graph_workload(frame_ids=ids)
     pts = [g.points[i] for i in ids]
     covs = [oracle.covariances(p) for p in pts]
     return g, ids, pts, covs
 
 
-def test_overlap_matrix_bit_exact(ctx, loop_frames):
+@pytest.mark.parametrize("cull", [1, 0])
+def test_overlap_matrix_bit_exact(ctx, loop_frames, cull):
     g, ids, pts, covs = loop_frames
+    ctx.set_options(overlap_cull=cull)
     fr = [ctx.add_frame(p, c) for p, c in zip(pts, covs)]
     maps = ctx.build_voxelmaps(fr, g.resolution)
     P = g.poses[ids]
     counts = ctx.overlap_matrix(fr, maps, P, P)
+    ctx.set_options(overlap_cull=1)
     vms = [oracle.voxelmap(p, c, g.resolution) for p, c in zip(pts, covs)]
     for s in range(len(ids)):
         for t in range(len(ids)):
@@ -150,6 +160,7 @@ def test_overlap_matrix_bit_exact(ctx, loop_frames):
             assert counts[s, t] == oracle.overlap_count(vms[t], pts[s], T), (s, t)
     # T_i^-1 T_i is identity only up to rounding: nearly every point stays in its own voxel
     assert all(counts[i, i] >= 0.99 * pts[i].shape[0] for i in range(len(ids)))
+    assert counts[0, 7] == 0 and counts[7, 0] == 0      # far apart: no correspondence
     for h in list(maps) + fr:
         ctx.release(int(h))
 
