@@ -268,7 +268,9 @@ void fill_map_desc(MapDesc &m, char *base, uint32_t cap, double r)
 {
     m.keys = (uint64_t *)base;
     m.rec = (VoxelRec *)(base + align256((size_t)cap * 8));
+    m.ckeys = (uint32_t *)(base + align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)));
     m.kbox = (int32_t *)(base + map_bytes(cap) - 256 + 16);
+    m.cmeta = (int32_t *)(base + map_bytes(cap) - 256 + 48);
     m.mask = cap - 1;
     uint32_t l = 0;
     while ((1u << l) < cap) ++l;
@@ -281,7 +283,10 @@ void fill_map_desc(MapDesc &m, char *base, uint32_t cap, double r)
     m.pow2 = is_pow2_res(r) ? 1 : 0;
 }
 
-size_t map_bytes(uint32_t cap) { return align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)) + 256; }
+size_t map_bytes(uint32_t cap)
+{
+    return align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)) + align256((size_t)cap * 4) + 256;
+}
 
 uint32_t *map_nvox_ptr(const Obj &o) { return (uint32_t *)((char *)o.map_mem + o.map_bytes - 256); }
 
@@ -329,7 +334,7 @@ vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const 
     launch_voxelmap_build(ctx->d_maps, ctx->d_frames, (const BuildUnit *)ctx->ws_bunits.p, nu,
                           (const WorkItem *)ctx->ws_bitems.p, (int)items.size(), (const int64_t *)ctx->ws_bprefix.p,
                           scr, grid, ctx->stream);
-    ctx->launches += 1 + (items.empty() ? 0 : 3);
+    ctx->launches += 1 + (items.empty() ? 0 : 4);
     CHECK_LAUNCH();
     return VGICP_OK;
 }
@@ -812,24 +817,11 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
         if (!std::isfinite(poses_src[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
     for (int64_t i = 0; i < n_tgt * 12; ++i)
         if (!std::isfinite(poses_tgt[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
-    // source chunks; the kernel enumerates (target tile, chunk, target) so the
-    // CTAs in flight share a few target tables and a few source chunks
-    const int chunk = overlap_matrix_chunk();
-    std::vector<WorkItem> chunks;
-    for (int64_t s = 0; s < n_src; ++s)
-        for (int64_t o = 0; o < nsrc[s]; o += chunk) {
-            WorkItem w;
-            w.unit = (int32_t)s;
-            w.start = o;
-            w.count = (int32_t)std::min<int64_t>(chunk, nsrc[s] - o);
-            chunks.push_back(w);
-        }
     TRY(upload(ctx, ctx->ws_poses, poses_src, (size_t)n_src * 12));
     TRY(ensure(ctx, ctx->ws_stage, (size_t)n_tgt * 12 * 8));
     CU(cudaMemcpyAsync(ctx->ws_stage.p, poses_tgt, (size_t)n_tgt * 12 * 8, cudaMemcpyHostToDevice, ctx->stream));
     TRY(upload(ctx, ctx->ws_fidx, fidx.data(), fidx.size()));
     TRY(upload(ctx, ctx->ws_midx, midx.data(), midx.size()));
-    TRY(upload(ctx, ctx->ws_chunks, chunks.data(), chunks.size()));
     TRY(ensure(ctx, ctx->ws_pairs, (size_t)n_pairs * sizeof(PoseParam)));
     launch_prepare_pairs((const double *)ctx->ws_poses.p, (const double *)ctx->ws_stage.p,
                          (const int32_t *)ctx->ws_fidx.p, (const int32_t *)ctx->ws_midx.p, (int)n_src, (int)n_tgt,
@@ -841,10 +833,8 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
         dcounts = (unsigned long long *)ctx->ws_counts.p;
     }
     CU(cudaMemsetAsync(dcounts, 0, (size_t)n_pairs * 8, ctx->stream));
-    const int grid = ctx->num_sms * 8;
-    launch_overlap_matrix((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames,
-                          (const WorkItem *)ctx->ws_chunks.p, (int)chunks.size(), (int)n_tgt, dcounts, grid,
-                          ctx->stream);
+    launch_overlap_matrix((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames, (int)n_src, (int)n_tgt,
+                          dcounts, ctx->num_sms, ctx->stream);
     ctx->launches += 2;
     CHECK_LAUNCH();
     if (out_kind == VGICP_MEM_HOST) {

@@ -82,13 +82,10 @@ int linearize_f64_block();
 void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                     int n_items, unsigned long long *counts, int grid, cudaStream_t st);
 
-// Overlap matrix: counts[s * n_tgt + t] += hits of source s against target t.
-// chunks lists every source's point chunks of overlap_matrix_chunk() points
-// (unit = source index); the kernel enumerates (target tile, chunk) items.
-int overlap_matrix_chunk();
-void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames,
-                           const WorkItem *chunks, int n_chunks, int n_tgt, unsigned long long *counts, int grid,
-                           cudaStream_t st);
+// Overlap matrix: counts[s * n_tgt + t] += hits of source s against target t
+// (pairs[s * n_tgt + t] prepared by launch_prepare_pairs).  One CTA per SM.
+void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
+                           int n_tgt, unsigned long long *counts, int grid, cudaStream_t st);
 
 // Pair parameters of an overlap matrix: pair (s, t) -> T_t^-1 T_s; with cull set,
 // pairs whose source bounding box cannot meet the target's voxels are flagged.

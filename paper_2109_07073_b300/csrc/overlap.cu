@@ -85,102 +85,123 @@ __global__ void __launch_bounds__(256) k_overlap(const PoseParam *__restrict__ p
     }
 }
 
-// Overlap matrix.  A work item is (chunk of 1,024 points of one source, tile
-// of kTile targets): every thread keeps kPPT points in registers and, target by
-// target, computes their voxel keys and issues their kPPT first hash probes back
-// to back, so each thread has several independent loads in flight; collision
-// chains (rare at load <= 2/3) and undecided floors take a slower path.
-// Items are ordered target tile first, so the CTAs in flight share a few target
-// tables while the source chunks stream through.
-constexpr int kOvBlock = 256, kPPT = 4, kTile = 16, kOvChunk = kOvBlock * kPPT;
+// Overlap matrix.  A work item is (slice of kSlice sources, one target): the
+// CTA stages the target's compact presence table (32-bit keys relative to its
+// voxel box, capacity ~2x its voxel count) in shared memory once, then streams
+// the slice's live sources through it, kPPT points per thread per step.  Items
+// run slice-major, so the CTAs in flight share one slice of sources (a few MB,
+// L2-resident) while each holds a different target table.  Targets without a
+// compact table that fits (very large or very wide maps) probe the main table
+// in global memory instead; undecided floors take the slower exact path.
+constexpr int kOvBlock = 1024, kPPT = 4, kSlice = 32;
+constexpr int kSmemLog2 = 15;   // 32,768 compact keys = 128 KB of shared memory
 
-__global__ void __launch_bounds__(kOvBlock) k_overlap_matrix(const PoseParam *__restrict__ pairs,
-                                                             const MapDesc *__restrict__ maps,
-                                                             const FrameDesc *__restrict__ frames,
-                                                             const WorkItem *__restrict__ chunks, int n_chunks,
-                                                             int n_tgt, unsigned long long *__restrict__ counts)
+__device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, uint32_t lg, const int kb[6],
+                                            const int k[3])
 {
-    __shared__ PoseParam sP[kTile];
-    __shared__ MapDesc sM[kTile];
-    __shared__ unsigned int sHits[kTile];
+    const int dx = k[0] - kb[0], dy = k[1] - kb[1], dz = k[2] - kb[2];
+    if ((unsigned)dx > (unsigned)(kb[3] - kb[0]) || (unsigned)dy > (unsigned)(kb[4] - kb[1]) ||
+        (unsigned)dz > (unsigned)(kb[5] - kb[2]))
+        return false;                                   // outside the voxel box: no voxel
+    const uint32_t ck = pack_compact(dx, dy, dz), mask = (1u << lg) - 1u;
+    uint32_t s = hash_compact(ck, lg);
+    for (uint32_t i = 0; i <= mask; ++i) {
+        const uint32_t v = tab[s];
+        if (v == ck) return true;
+        if (v == kEmptyCompact) return false;
+        s = (s + 1) & mask;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam *__restrict__ pairs,
+                                                                const MapDesc *__restrict__ maps,
+                                                                const FrameDesc *__restrict__ frames, int n_src,
+                                                                int n_tgt, unsigned long long *__restrict__ counts)
+{
+    extern __shared__ uint4 s_tab4[];
+    const uint32_t *s_tab = (const uint32_t *)s_tab4;
+    __shared__ PoseParam sP;
+    __shared__ MapDesc sM;
+    __shared__ int s_kb[6], s_lg, s_smem, s_n;
+    __shared__ const float4 *s_pa;
+    __shared__ unsigned int s_hits;
     const int lane = threadIdx.x & 31;
-    const int n_tiles = (n_tgt + kTile - 1) / kTile;
-    const int64_t total = (int64_t)n_tiles * n_chunks;
+    const int n_slices = (n_src + kSlice - 1) / kSlice;
+    const int64_t total = (int64_t)n_slices * n_tgt;
     for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
-        const int tt = (int)(v / n_chunks), c = (int)(v - (int64_t)tt * n_chunks);
-        const WorkItem w = chunks[c];
-        const int t0 = tt * kTile, nt = min(kTile, n_tgt - t0);
-        __syncthreads();   // the previous item's readers of sP / sM / sHits are done
-        int live = 0;
-        if (threadIdx.x < nt) {
-            sP[threadIdx.x] = pairs[(int64_t)w.unit * n_tgt + t0 + threadIdx.x];
-            sM[threadIdx.x] = maps[sP[threadIdx.x].map];
-            sHits[threadIdx.x] = 0;
-            live = !sP[threadIdx.x].cull;
-        }
-        if (!__syncthreads_or(live)) continue;       // every pair of the tile culled: skip the points
-        const float4 *__restrict__ pa = frames[sP[0].frame].pa + w.start;
-        float px[kPPT], py[kPPT], pz[kPPT];
-        bool have[kPPT];
+        const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
+        const int s0 = sl * kSlice, s1 = min(n_src, s0 + kSlice);
+        __syncthreads();                                // previous item's readers are done
+        const int live = (threadIdx.x < s1 - s0) ? !pairs[(int64_t)(s0 + threadIdx.x) * n_tgt + t].cull : 0;
+        if (!__syncthreads_or(live)) continue;          // every pair of the item culled
+        if (threadIdx.x == 0) {
+            sM = maps[pairs[(int64_t)s0 * n_tgt + t].map];
+            s_lg = sM.cmeta[0];
+            s_smem = sM.cmeta[1] && s_lg <= kSmemLog2;
 #pragma unroll
-        for (int j = 0; j < kPPT; ++j) {
-            const int i = j * kOvBlock + threadIdx.x;
-            have[j] = i < w.count;
-            const float4 A = have[j] ? __ldg(pa + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            px[j] = A.x; py[j] = A.y; pz[j] = A.z;
-        }
-        for (int ti = 0; ti < nt; ++ti) {
-            const PoseParam &P = sP[ti];
-            if (P.cull) continue;                        // uniform across the block
-            const MapDesc &m = sM[ti];
-            const uint64_t *__restrict__ keys = m.keys;
-            const uint32_t mask = m.mask, lg = m.log2cap;
-            uint64_t key[kPPT];
-            uint32_t slot[kPPT];
-            int state[kPPT];                              // 0 miss, 1 hit, 2 probing, 3 undecided floor
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) {
-                int k[3];
-                bool dec = true;
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    dec &= axis_key_split(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.k0[a], px[j], py[j], pz[j],
-                                          m.r_h, m.r_l, m.inv_rf, k[a]);
-                const bool valid = k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN;
-                state[j] = !have[j] ? 0 : (!dec ? 3 : (valid ? 2 : 0));
-                key[j] = valid ? pack_key(k[0], k[1], k[2]) : 0ull;
-                slot[j] = hash_slot(key[j], lg);
-            }
-            uint64_t kv[kPPT];
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) kv[j] = (state[j] == 2) ? __ldg(keys + slot[j]) : kEmptyKey;
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) {
-                if (state[j] != 2) continue;
-                if (kv[j] == key[j]) state[j] = 1;
-                else if (kv[j] == kEmptyKey) state[j] = 0;
-                else {                                    // collision chain
-                    state[j] = probe(keys, mask, lg, key[j]) >= 0 ? 1 : 0;
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) {
-                if (state[j] == 3) {                      // face: float32-pair, then float64
-                    int k[3];
-                    state[j] = point_key_slow(P, m, px[j], py[j], pz[j], k) &&
-                                       probe(keys, mask, lg, pack_key(k[0], k[1], k[2])) >= 0
-                                   ? 1
-                                   : 0;
-                }
-            }
-            unsigned int h = 0;
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) h += __popc(__ballot_sync(0xffffffffu, state[j] == 1));
-            if (lane == 0 && h) atomicAdd(sHits + ti, h);
+            for (int j = 0; j < 6; ++j) s_kb[j] = sM.kbox[j];
         }
         __syncthreads();
-        if (threadIdx.x < nt && sHits[threadIdx.x])
-            atomicAdd(counts + (int64_t)w.unit * n_tgt + t0 + threadIdx.x, (unsigned long long)sHits[threadIdx.x]);
+        if (s_smem) {
+            const uint4 *src = (const uint4 *)sM.ckeys;
+            for (int i = threadIdx.x; i < (1 << s_lg) / 4; i += kOvBlock) s_tab4[i] = __ldg(src + i);
+        }
+        const MapDesc m = sM;
+        const bool smem = s_smem;
+        const uint32_t lg = (uint32_t)s_lg;
+        int kb[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) kb[j] = s_kb[j];
+        for (int s = s0; s < s1; ++s) {
+            __syncthreads();                            // table staged; previous source's count taken
+            if (threadIdx.x == 0) {
+                sP = pairs[(int64_t)s * n_tgt + t];
+                s_hits = 0;
+                s_pa = frames[sP.frame].pa;
+                s_n = (int)frames[sP.frame].n;
+            }
+            __syncthreads();
+            if (sP.cull) continue;                      // uniform across the block
+            const PoseParam &P = sP;
+            const float4 *__restrict__ pa = s_pa;
+            const int n = s_n;
+            unsigned int hits = 0;
+            for (int base = 0; base < n; base += kOvBlock * kPPT) {
+                float px[kPPT], py[kPPT], pz[kPPT];
+                bool have[kPPT];
+#pragma unroll
+                for (int j = 0; j < kPPT; ++j) {
+                    const int i = base + j * kOvBlock + threadIdx.x;
+                    have[j] = i < n;
+                    const float4 A = have[j] ? __ldg(pa + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    px[j] = A.x; py[j] = A.y; pz[j] = A.z;
+                }
+#pragma unroll
+                for (int j = 0; j < kPPT; ++j) {
+                    int k[3];
+                    bool dec = true;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        dec &= axis_key_split(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.k0[a], px[j], py[j],
+                                              pz[j], m.r_h, m.r_l, m.inv_rf, k[a]);
+                    bool hit = false;
+                    if (have[j]) {
+                        if (!dec) {                     // face: float32-pair, then float64
+                            hit = point_key_slow(P, m, px[j], py[j], pz[j], k) &&
+                                  probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
+                        } else if (k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN) {
+                            hit = smem ? compact_hit(s_tab, lg, kb, k)
+                                       : probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
+                        }
+                    }
+                    hits += __popc(__ballot_sync(0xffffffffu, hit));
+                }
+            }
+            if (lane == 0 && hits) atomicAdd(&s_hits, hits);
+            __syncthreads();
+            if (threadIdx.x == 0 && s_hits) atomicAdd(counts + (int64_t)s * n_tgt + t, (unsigned long long)s_hits);
+        }
     }
 }
 
@@ -225,14 +246,13 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
     k_overlap<<<grid, 256, 0, st>>>(params, maps, frames, items, n_items, counts);
 }
 
-int overlap_matrix_chunk() { return kOvChunk; }
-
-void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames,
-                           const WorkItem *chunks, int n_chunks, int n_tgt, unsigned long long *counts, int grid,
-                           cudaStream_t st)
+void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
+                           int n_tgt, unsigned long long *counts, int grid, cudaStream_t st)
 {
-    if (n_chunks <= 0 || n_tgt <= 0) return;
-    k_overlap_matrix<<<grid, kOvBlock, 0, st>>>(pairs, maps, frames, chunks, n_chunks, n_tgt, counts);
+    if (n_src <= 0 || n_tgt <= 0) return;
+    const int smem = (1 << kSmemLog2) * 4;
+    cudaFuncSetAttribute(k_overlap_matrix, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_overlap_matrix<<<grid, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt, counts);
 }
 
 void launch_correspondences(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,

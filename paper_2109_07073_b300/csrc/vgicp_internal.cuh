@@ -38,6 +38,8 @@ struct MapDesc {
     uint64_t *keys;
     VoxelRec *rec;
     int32_t *kbox;       // device: min voxel coordinate (3), max voxel coordinate (3)
+    uint32_t *ckeys;     // compact presence table (capacity cap; the first 2^cmeta[0] entries used)
+    int32_t *cmeta;      // device: log2 of the compact table's used capacity, 1 if the map has one
     uint32_t mask;       // cap - 1
     uint32_t log2cap;    // >= 4
     double r, inv_r;     // resolution and fl64(1 / r)
@@ -95,6 +97,22 @@ struct __align__(16) PoseParam {
 };
 
 // ---------------------------------------------------------------- keys ----
+
+// Compact 32-bit voxel key relative to the map's voxel bounding box: 11 bits
+// for x and y, 10 for z.  A map has a compact table when its box extent fits
+// (x, y <= 2046, z <= 1022), so the all-ones word never names a voxel.
+constexpr uint32_t kEmptyCompact = 0xFFFFFFFFu;
+constexpr int kCompactMaxX = 2046, kCompactMaxZ = 1022;
+
+__device__ __forceinline__ uint32_t pack_compact(int dx, int dy, int dz)
+{
+    return (uint32_t)dx | ((uint32_t)dy << 11) | ((uint32_t)dz << 22);
+}
+
+__device__ __forceinline__ uint32_t hash_compact(uint32_t ck, uint32_t log2cap)
+{
+    return (ck * 0x9E3779B1u) >> (32 - log2cap);
+}
 
 __device__ __forceinline__ uint64_t pack_key(int kx, int ky, int kz)
 {

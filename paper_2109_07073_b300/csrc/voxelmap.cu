@@ -2,7 +2,7 @@
 // distribution aggregates the distributions of the points that fall in it:
 // mean of the point means and mean of the point covariances).
 //
-// Build of all maps of a batch in four launches:
+// Build of all maps of a batch in five launches:
 //   clear      keys <- EMPTY, voxel counters <- 0
 //   insert     per point: voxel key, atomicCAS into the map's open-addressing
 //              table; the thread that claims a slot takes a dense voxel id and
@@ -11,6 +11,9 @@
 //              does not depend on the order the GPU runs the points in)
 //   finalize   per voxel: mean relative to the voxel's lower corner, mean
 //              covariance, count -> the slot's 48 B record
+//   compact    per voxel: its 32-bit key relative to the map's voxel box into a
+//              presence table sized by the voxel count (overlap queries stage
+//              it in shared memory)
 #include "kernels.cuh"
 
 namespace vg {
@@ -84,6 +87,7 @@ __global__ void k_build_clear(const MapDesc *__restrict__ maps, const BuildUnit 
         const int64_t s = g - slot_prefix[u];
         const MapDesc &m = maps[units[u].map];
         m.keys[s] = kEmptyKey;
+        m.ckeys[s] = kEmptyCompact;
         vid_of_slot[g] = -1;
         if (s == 0) {
             *units[u].n_voxels = 0;
@@ -232,6 +236,43 @@ __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDe
     }
 }
 
+// Compact presence table of each map: the compact key of every voxel, inserted
+// into the first 2^lg entries of ckeys (lg = log2 of the smallest power of two
+// >= 2 V, at most the main capacity), when the voxel box extent allows it.
+__global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units,
+                                const WorkItem *__restrict__ items, int n_items, BuildScratch scr)
+{
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const BuildUnit u = units[w.unit];
+        const MapDesc m = maps[u.map];
+        const uint32_t nv = *u.n_voxels;
+        const int *kb = m.kbox;
+        const bool ok = nv > 0 && kb[3] - kb[0] <= kCompactMaxX && kb[4] - kb[1] <= kCompactMaxX &&
+                        kb[5] - kb[2] <= kCompactMaxZ;
+        uint32_t lg = 4;
+        while (lg < m.log2cap && (1u << lg) < 2u * nv) ++lg;
+        if (w.start == 0 && threadIdx.x == 0) {
+            m.cmeta[0] = (int32_t)lg;
+            m.cmeta[1] = ok ? 1 : 0;
+        }
+        if (!ok) continue;
+        const uint32_t cmask = (1u << lg) - 1u;
+        for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
+            if (v >= (int64_t)nv) break;
+            int kx, ky, kz;
+            unpack_key(m.keys[scr.slot_of_vid[u.point_base + v]], kx, ky, kz);
+            const uint32_t ck = pack_compact(kx - kb[0], ky - kb[1], kz - kb[2]);
+            uint32_t s = hash_compact(ck, lg);
+            for (uint32_t t = 0; t <= cmask; ++t) {
+                const uint32_t old = atomicCAS(m.ckeys + s, kEmptyCompact, ck);
+                if (old == kEmptyCompact || old == ck) break;
+                s = (s + 1) & cmask;
+            }
+        }
+    }
+}
+
 __global__ void k_scatter_map_descs(const uint32_t *__restrict__ idx, const MapDesc *__restrict__ src, int n,
                                     MapDesc *__restrict__ table)
 {
@@ -274,6 +315,7 @@ void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const B
     k_build_insert<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
     k_build_accumulate<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
     k_build_finalize<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
+    k_build_compact<<<grid, 256, 0, st>>>(maps, units, items, n_items, scr);
 }
 
 void launch_scatter_map_descs(const uint32_t *idx, const MapDesc *src, int n, MapDesc *table, cudaStream_t st)
