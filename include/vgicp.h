@@ -91,9 +91,11 @@ typedef struct {
 
 typedef struct {
     int32_t precision;        /* VGICP_PREC_F32 (default) or VGICP_PREC_F64 */
-    int32_t chunk_points;     /* points per work item of the batched path (multiple of 32; 0 = default 2048) */
-    int32_t block_threads;    /* threads per block of the batched path (multiple of 32, <= 1024; 0 = default 256) */
-    int32_t blocks_per_sm;    /* persistent grid = SMs x this (0 = default from occupancy) */
+    int32_t chunk_points;     /* points per work item of the batched path (one warp per item; multiple of 32;
+                                 0 = default 2048) */
+    int32_t linearize_variant;/* batched kernel variant: 0 default, 1 or 2 (same results, different
+                                 latency hiding; chosen by measurement) */
+    int32_t blocks_per_sm;    /* persistent grid = SMs x this (0 = the variant's default) */
     int64_t hbm_budget_bytes; /* device bytes handles may hold in total (0 = unlimited) */
     /* 1 (default): overlap pairs whose source bounding box, moved by the pair's
      * pose and grown by a margin far above float64 rounding, misses the target's
@@ -160,6 +162,16 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
                              const double *poses, int64_t n_poses,
                              double *H, double *b, double *cost, int64_t *inliers, int out_kind);
 
+/* Autotuner for the batched float32 linearisation (Sec. III-D's "issue all
+ * factors, then synchronise" step): times every candidate (kernel variant x
+ * points per work item x persistent grid) on this factor set with CUDA events
+ * on the context stream, `reps` timed runs each after one warm-up, and keeps
+ * the fastest in the context options (precision is set to VGICP_PREC_F32).
+ * best (nullable) receives those options and best_ms (nullable) the time of one
+ * run.  Results differ between candidates only by float32 summation order. */
+vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
+                            int64_t n_poses, int32_t reps, vgicp_options *best, double *best_ms);
+
 /* Size limits of vgicp_linearize_noalloc() (its fixed scratch is sized for them). */
 #define VGICP_NOALLOC_MAX_FACTORS 1024
 #define VGICP_NOALLOC_MAX_POSES 2048
@@ -173,7 +185,7 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
  * context, frames and voxelmaps beforehand and pass their own outputs.
  *
  * Same results as vgicp_linearize() with VGICP_PREC_F32 and the context's
- * chunk_points / block_threads (the same kernels run over the same chunks).
+ * chunk_points / linearize_variant (the same kernels run over the same chunks).
  * factors and poses are host arrays copied on the context stream (a pinned
  * buffer must stay valid until the stream passes the copy); H (n_f x 144),
  * b (n_f x 12), cost (n_f) and inliers (n_f, nullable) are DEVICE memory,

@@ -32,7 +32,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_build_voxelmaps", "vgicp_voxelmap_size", "vgicp_linearize", "vgicp_overlap",
            "vgicp_overlap_matrix", "vgicp_debug_correspondences", "vgicp_export_voxelmap",
            "vgicp_estimate_covariances", "vgicp_release", "vgicp_memory_in_use", "vgicp_kernel_launches",
-           "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc"]
+           "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc", "vgicp_autotune"]
 
 
 class VgicpError(RuntimeError):
@@ -42,7 +42,7 @@ class VgicpError(RuntimeError):
 
 
 class Options(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("chunk_points", C.c_int32), ("block_threads", C.c_int32),
+    _fields_ = [("precision", C.c_int32), ("chunk_points", C.c_int32), ("linearize_variant", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("overlap_cull", C.c_int32),
                 ("reserved", C.c_int32)]
 
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_voxelmap_size": [vp, i64, C.POINTER(i64)],
         "vgicp_linearize": [vp, vp, i64, vp, i64, vp, vp, vp, vp, C.c_int],
         "vgicp_linearize_noalloc": [vp, vp, i64, vp, i64, vp, vp, vp, vp],
+        "vgicp_autotune": [vp, vp, i64, vp, i64, i32, C.POINTER(Options), C.POINTER(f64)],
         "vgicp_overlap": [vp, i64, i64, vp, C.POINTER(f64), C.POINTER(i64)],
         "vgicp_overlap_matrix": [vp, vp, i64, vp, i64, vp, vp, vp, C.c_int],
         "vgicp_debug_correspondences": [vp, i64, i64, vp, vp, vp],
@@ -260,6 +261,17 @@ def vgicp_linearize_noalloc(ctx, factors, poses, out):
     return H, b, cost, inl
 
 
+def vgicp_autotune(ctx, factors, poses, reps: int = 3):
+    """Time the batched linearisation's candidates on this factor set; keeps and returns
+    (best options, ms per run)."""
+    f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
+    P = _pose12(poses)
+    best, ms = Options(), C.c_double()
+    _check(ctx, load().vgicp_autotune(ctx, _ptr(f), f.shape[0], _ptr(P), P.shape[0], int(reps), C.byref(best),
+                                      C.byref(ms)))
+    return best, ms.value
+
+
 def vgicp_overlap(ctx, source: int, target: int, T_target_source):
     """Eq. 8: (fraction, count)."""
     T = _pose12(T_target_source)
@@ -371,6 +383,11 @@ class Context:
         for k, v in opts.items():
             setattr(self.options, k, v)
         vgicp_set_options(self.ctx, self.options)
+
+    def autotune(self, factors, poses, reps: int = 3):
+        best, ms = vgicp_autotune(self.ctx, factors, poses, reps)
+        self.options = best
+        return best, ms
 
     def __getattr__(self, name):
         fn = globals().get("vgicp_" + name)

@@ -68,7 +68,7 @@ struct vgicp_ctx {
     // workspaces
     Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
     Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
-    Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs;
+    Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs, ws_tune;
     Plan plan;
 };
 
@@ -385,7 +385,6 @@ vgicp_status read_nvox(vgicp_ctx *ctx, const Obj &o, int64_t *n)
 }
 
 int default_chunk(const vgicp_options &o) { return o.chunk_points > 0 ? o.chunk_points : 2048; }
-int default_block(const vgicp_options &o) { return o.block_threads > 0 ? o.block_threads : 256; }
 
 // Work list for a factor set (cached while the set and the chunk size stay the same).
 vgicp_status get_plan(vgicp_ctx *ctx, const vgicp_factor *f, int64_t n_f, const std::vector<int32_t> &idx)
@@ -427,11 +426,6 @@ vgicp_status get_plan(vgicp_ctx *ctx, const vgicp_factor *f, int64_t n_f, const 
     return VGICP_OK;
 }
 
-int occupancy_grid(vgicp_ctx *ctx, int block)
-{
-    int per_sm = ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : std::max(1, 2048 / block);
-    return ctx->num_sms * per_sm;
-}
 
 }  // namespace
 
@@ -443,7 +437,7 @@ vgicp_status vgicp_options_default(vgicp_options *opt)
     std::memset(opt, 0, sizeof(*opt));
     opt->precision = VGICP_PREC_F32;
     opt->chunk_points = 2048;
-    opt->block_threads = 256;
+    opt->linearize_variant = 0;
     opt->blocks_per_sm = 0;
     opt->hbm_budget_bytes = 0;
     opt->overlap_cull = 1;
@@ -456,8 +450,8 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "precision must be VGICP_PREC_F32 or VGICP_PREC_F64");
     if (o->chunk_points < 0 || (o->chunk_points % 32) != 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "chunk_points must be a non-negative multiple of 32");
-    if (o->block_threads != 0 && o->block_threads != 128 && o->block_threads != 256 && o->block_threads != 512)
-        return fail(ctx, VGICP_ERR_INVALID_ARG, "block_threads must be 0, 128, 256 or 512");
+    if (o->linearize_variant < 0 || o->linearize_variant > 2)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_variant must be 0, 1 or 2");
     if (o->blocks_per_sm < 0 || o->hbm_budget_bytes < 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
     if (o->overlap_cull != 0 && o->overlap_cull != 1)
@@ -507,7 +501,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
                    &ctx->ws_ticket, &ctx->ws_counts, &ctx->ws_stage, &ctx->ws_bunits, &ctx->ws_bitems,
                    &ctx->ws_bprefix, &ctx->ws_slot_of_point, &ctx->ws_acc, &ctx->ws_vid_of_slot,
                    &ctx->ws_slot_of_vid, &ctx->ws_pairs, &ctx->ws_fidx, &ctx->ws_midx, &ctx->ws_chunks,
-                   &ctx->ws_export_keys, &ctx->ws_export_rec, &ctx->ws_counter, &ctx->ws_descs, &ctx->plan.idx,
+                   &ctx->ws_export_keys, &ctx->ws_export_rec, &ctx->ws_counter, &ctx->ws_descs, &ctx->ws_tune, &ctx->plan.idx,
                    &ctx->plan.items, &ctx->plan.item_begin};
     for (Buf *b : bufs) free_buf(ctx, *b);
     if (ctx->d_maps) cudaFreeAsync(ctx->d_maps, ctx->stream);
@@ -722,12 +716,11 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         ctx->launches += n_f;
         CHECK_LAUNCH();
     } else {
-        const int block = default_block(ctx->opt);
         TRY(ensure(ctx, ctx->ws_partials, (size_t)std::max(1, P.n_items) * 28 * 8));
         TRY(ensure(ctx, ctx->ws_inl, (size_t)std::max(1, P.n_items) * 8));
-        const int grid = std::max(1, std::min(P.n_items, occupancy_grid(ctx, block)));
         launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
-                             (double *)ctx->ws_partials.p, (int64_t *)ctx->ws_inl.p, block, grid, ctx->stream);
+                             (double *)ctx->ws_partials.p, (int64_t *)ctx->ws_inl.p, ctx->opt.linearize_variant,
+                             ctx->opt.blocks_per_sm, ctx->num_sms, ctx->stream);
         launch_reduce_finalize(d_params, (const int32_t *)P.item_begin.p, (int)n_f, (const double *)ctx->ws_partials.p,
                                (const int64_t *)ctx->ws_inl.p, dH, db, dc, di, ctx->stream);
         ctx->launches += (P.n_items > 0) + 1;
@@ -740,6 +733,58 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         if (inliers) CU(cudaMemcpyAsync(inliers, di, (size_t)n_f * 8, cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
     }
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
+                            int64_t n_poses, int32_t reps, vgicp_options *best, double *best_ms)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n_f <= 0 || reps < 1 || !factors || !poses)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "autotune: needs factors, poses and reps >= 1");
+    const size_t out = (size_t)n_f * (144 + 12 + 1 + 1) * 8;
+    TRY(ensure(ctx, ctx->ws_tune, out));
+    double *H = (double *)ctx->ws_tune.p, *b = H + n_f * 144, *c = b + n_f * 12;
+    int64_t *inl = (int64_t *)(c + n_f);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    const vgicp_options keep = ctx->opt;
+    vgicp_options win = keep;
+    float win_ms = 1e30f;
+    static const int chunks[] = {1024, 2048, 4096, 8192};
+    vgicp_status st = VGICP_OK;
+    for (int variant = 0; variant <= 2 && st == VGICP_OK; ++variant)
+        for (int ci = 0; ci < 4 && st == VGICP_OK; ++ci) {
+            ctx->opt = keep;
+            ctx->opt.precision = VGICP_PREC_F32;
+            ctx->opt.linearize_variant = variant;
+            ctx->opt.chunk_points = chunks[ci];
+            ctx->opt.blocks_per_sm = 0;
+            st = vgicp_linearize(ctx, factors, n_f, poses, n_poses, H, b, c, inl, VGICP_MEM_DEVICE);
+            if (st != VGICP_OK) break;
+            cudaEventRecord(e0, ctx->stream);
+            for (int r = 0; r < reps && st == VGICP_OK; ++r)
+                st = vgicp_linearize(ctx, factors, n_f, poses, n_poses, H, b, c, inl, VGICP_MEM_DEVICE);
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(ctx, VGICP_ERR_CUDA, "autotune: event"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (ms < win_ms) {
+                win_ms = ms;
+                win = ctx->opt;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != VGICP_OK) {
+        ctx->opt = keep;
+        return st;
+    }
+    ctx->opt = win;
+    if (best) *best = win;
+    if (best_ms) *best_ms = win_ms;
     return VGICP_OK;
 }
 
@@ -1018,7 +1063,7 @@ bool ctx_view(vgicp_ctx *ctx, CtxView *v)
     v->device = ctx->device;
     v->num_sms = ctx->num_sms;
     v->chunk = default_chunk(ctx->opt);
-    v->block = default_block(ctx->opt);
+    v->variant = ctx->opt.linearize_variant;
     v->blocks_per_sm = ctx->opt.blocks_per_sm;
     v->d_maps = ctx->d_maps;
     v->d_frames = ctx->d_frames;

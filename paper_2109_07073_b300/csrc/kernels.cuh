@@ -58,11 +58,13 @@ void launch_prepare_factors(const int32_t *factor_idx /* n_f x 4: map, frame, po
 void launch_prepare_given(const double *T, int map, int frame, const MapDesc *maps, const FrameDesc *frames,
                           int cull, PoseParam *out, cudaStream_t st);
 
-// Batched float32 path: one persistent launch over all work items; each item
-// writes 28 float64 partial sums and an inlier count.
+// Batched float32 path: one persistent launch over all work items (one warp per
+// item at a time); each item writes 28 float64 partial sums and an inlier
+// count.  variant: 0 default, 1 and 2 alternatives (see linearize.cu);
+// grid_per_sm: blocks per SM of the persistent grid (0 = the variant's own).
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
-                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
-                          int block, int grid, cudaStream_t st);
+                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials, int variant,
+                          int grid_per_sm, int num_sms, cudaStream_t st);
 
 // Per-factor fixed-order float64 reduction of the item partials and expansion
 // to the 12x12 H, b, cost.  item_begin has n_f + 1 entries.
@@ -114,7 +116,7 @@ namespace vg {
 
 struct CtxView {
     cudaStream_t stream;
-    int device, num_sms, chunk, block, blocks_per_sm;
+    int device, num_sms, chunk, variant, blocks_per_sm;
     MapDesc *d_maps;
     FrameDesc *d_frames;
 };

@@ -170,15 +170,15 @@ __global__ void k_prepare_given(const double *__restrict__ T, int map, int frame
     *out = p;
 }
 
-// Voxel coordinate and in-voxel offset of one point (batched path).
+// Voxel coordinate, in-voxel offset and lever arm R p of one point (batched path).
 __device__ __forceinline__ bool point_key_ff(const PoseParam &P, const MapDesc &m, float px, float py, float pz,
-                                             int k[3], float d[3])
+                                             int k[3], float d[3], float rp[3])
 {
     bool decided = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         decided &= axis_key_ff(P.Rh + 3 * a, P.Rl + 3 * a, P.th[a], P.tl[a], px, py, pz, m.r_h, m.r_l, m.inv_rf,
-                               P.ffm[a], P.ffup[a], k[a], d[a]);
+                               P.ffm[a], P.ffup[a], k[a], d[a], rp[a]);
     if (decided) return k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN;
     double q[3];
     if (!key_f64(P.T, px, py, pz, m.inv_r, k, q)) return false;
@@ -187,136 +187,204 @@ __device__ __forceinline__ bool point_key_ff(const PoseParam &P, const MapDesc &
     return true;
 }
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_linearize_f32(const PoseParam *__restrict__ params,
-                                                         const MapDesc *__restrict__ maps,
-                                                         const FrameDesc *__restrict__ frames,
-                                                         const WorkItem *__restrict__ items, int n_items,
-                                                         double *__restrict__ partials,
-                                                         int64_t *__restrict__ inl_partials)
+// Slot of the voxel containing one source point, or -1; first probe issued by
+// the caller so two points' probes can be in flight together.
+struct PointSlot {
+    uint64_t key;
+    uint32_t h;
+    bool ok;
+};
+
+__device__ __forceinline__ PointSlot point_hash(const PoseParam &P, const MapDesc &m, float px, float py, float pz,
+                                                float d[3], float rp[3])
+{
+    int k[3];
+    PointSlot r;
+    r.ok = point_key_ff(P, m, px, py, pz, k, d, rp);
+    r.key = r.ok ? pack_key(k[0], k[1], k[2]) : 0ull;
+    r.h = hash_slot(r.key, m.log2cap);
+    return r;
+}
+
+__device__ __forceinline__ int resolve_slot(const MapDesc &m, const PointSlot &ps, uint64_t first)
+{
+    if (!ps.ok || first == kEmptyKey) return -1;
+    if (first == ps.key) return (int)ps.h;
+    return probe_from(m.keys, m.mask, ps.key, (ps.h + 1) & m.mask);
+}
+
+// One correspondence's contribution (Eq. 2, 5, 6 in the adjoint form) added to acc.
+__device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, const float4 &A, const float4 &B,
+                                                float C22, const VoxelRec &v, const float d[3], const float x[3])
+{
+    const float R0 = R[0], R1 = R[1], R2 = R[2], R3 = R[3], R4 = R[4], R5 = R[5], R6 = R[6], R7 = R[7], R8 = R[8];
+    // residual e = mu_B - q, both relative to the voxel's lower corner
+    const float e0 = v.a.x - d[0], e1 = v.a.y - d[1], e2 = v.a.z - d[2];
+    // R C_A (C_A symmetric: c00 c01 c02 / c11 c12 / c22)
+    const float a00 = A.w, a01 = B.x, a02 = B.y, a11 = B.z, a12 = B.w, a22 = C22;
+    const float T00 = R0 * a00 + R1 * a01 + R2 * a02, T01 = R0 * a01 + R1 * a11 + R2 * a12,
+                T02 = R0 * a02 + R1 * a12 + R2 * a22;
+    const float T10 = R3 * a00 + R4 * a01 + R5 * a02, T11 = R3 * a01 + R4 * a11 + R5 * a12,
+                T12 = R3 * a02 + R4 * a12 + R5 * a22;
+    const float T20 = R6 * a00 + R7 * a01 + R8 * a02, T21 = R6 * a01 + R7 * a11 + R8 * a12,
+                T22 = R6 * a02 + R7 * a12 + R8 * a22;
+    // M = C_B + (R C_A) R^T
+    const float m00 = v.a.w + T00 * R0 + T01 * R1 + T02 * R2;
+    const float m01 = v.b.x + T00 * R3 + T01 * R4 + T02 * R5;
+    const float m02 = v.b.y + T00 * R6 + T01 * R7 + T02 * R8;
+    const float m11 = v.b.z + T10 * R3 + T11 * R4 + T12 * R5;
+    const float m12 = v.b.w + T10 * R6 + T11 * R7 + T12 * R8;
+    const float m22 = v.c.x + T20 * R6 + T21 * R7 + T22 * R8;
+    // Omega = M^-1 by the adjugate
+    const float c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+    const float c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
+    const float det = m00 * c00 + m01 * c01 + m02 * c02;
+    if (!(det > 0.f)) return 0;
+    const float id = __frcp_rn(det);
+    const float o00 = c00 * id, o01 = c01 * id, o02 = c02 * id, o11 = c11 * id, o12 = c12 * id, o22 = c22 * id;
+    // w = Omega e, cost = e . w
+    const float w0 = o00 * e0 + o01 * e1 + o02 * e2;
+    const float w1 = o01 * e0 + o11 * e1 + o12 * e2;
+    const float w2 = o02 * e0 + o12 * e1 + o22 * e2;
+    const float x0 = x[0], x1 = x[1], x2 = x[2];   // lever arm a = R p
+    // P = [a]x Omega  (= H_wv contribution)
+    const float P00 = x1 * o02 - x2 * o01, P01 = x1 * o12 - x2 * o11, P02 = x1 * o22 - x2 * o12;
+    const float P10 = x2 * o00 - x0 * o02, P11 = x2 * o01 - x0 * o12, P12 = x2 * o02 - x0 * o22;
+    const float P20 = x0 * o01 - x1 * o00, P21 = x0 * o11 - x1 * o01, P22 = x0 * o12 - x1 * o02;
+    // H_ww = -[a]x Omega [a]x = -P [a]x (upper triangle)
+    acc[0] += P02 * x1 - P01 * x2;
+    acc[1] += P00 * x2 - P02 * x0;
+    acc[2] += P01 * x0 - P00 * x1;
+    acc[3] += P10 * x2 - P12 * x0;
+    acc[4] += P11 * x0 - P10 * x1;
+    acc[5] += P21 * x0 - P20 * x1;
+    acc[6] += P00; acc[7] += P01; acc[8] += P02;
+    acc[9] += P10; acc[10] += P11; acc[11] += P12;
+    acc[12] += P20; acc[13] += P21; acc[14] += P22;
+    acc[15] += o00; acc[16] += o01; acc[17] += o02; acc[18] += o11; acc[19] += o12; acc[20] += o22;
+    // b_w = a x w, b_v = w
+    acc[21] += x1 * w2 - x2 * w1;
+    acc[22] += x2 * w0 - x0 * w2;
+    acc[23] += x0 * w1 - x1 * w0;
+    acc[24] += w0; acc[25] += w1; acc[26] += w2;
+    acc[27] += e0 * w0 + e1 * w1 + e2 * w2;
+    return 1;
+}
+
+// Work items belong to single warps: a warp copies its factor's parameters to
+// its own shared-memory slot, runs over the item's points, reduces its 28 sums
+// by shuffles and writes them as float64 -- no block barriers anywhere.  Items
+// are taken in order by global warp index.
+//   PTS = 1: one point per lane per step, the next step's point loads issued
+//            before this step's key, probe and record chain;
+//   PTS = 2: two points per lane per step, both points' loads, keys and first
+//            probes issued before either record is needed.
+template <int PTS>
+__device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
+                                                    const WorkItem &w, int lane, float acc[kNT], int &inl)
+{
+    const float4 *__restrict__ pa = F.pa + w.start;
+    const float4 *__restrict__ pb = F.pb + w.start;
+    const float *__restrict__ pc = F.pc + w.start;
+    const int n = w.count;
+    if (PTS == 1) {
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
+        float C = 0.f;
+        if (lane < n) {
+            A = __ldg(pa + lane);
+            B = __ldg(pb + lane);
+            C = __ldg(pc + lane);
+        }
+        for (int i = lane; i < n; i += 32) {
+            const float4 A0 = A, B0 = B;
+            const float C0 = C;
+            if (i + 32 < n) {
+                A = __ldg(pa + i + 32);
+                B = __ldg(pb + i + 32);
+                C = __ldg(pc + i + 32);
+            }
+            float d0[3], x0[3];
+            const PointSlot s0 = point_hash(P, m, A0.x, A0.y, A0.z, d0, x0);
+            const uint64_t f0 = s0.ok ? __ldg(m.keys + s0.h) : kEmptyKey;
+            const int slot0 = resolve_slot(m, s0, f0);
+            if (slot0 < 0) continue;
+            const VoxelRec v0 = m.rec[slot0];
+            inl += accumulate_point(acc, P.Rh, A0, B0, C0, v0, d0, x0);
+        }
+    } else {
+        for (int i0 = lane; i0 < n; i0 += 64) {
+            const int i1 = i0 + 32;
+            const bool h1 = i1 < n;
+            const float4 A0 = __ldg(pa + i0), B0 = __ldg(pb + i0);
+            const float C0 = __ldg(pc + i0);
+            float4 A1 = make_float4(0.f, 0.f, 0.f, 0.f), B1 = A1;
+            float C1 = 0.f;
+            if (h1) {
+                A1 = __ldg(pa + i1);
+                B1 = __ldg(pb + i1);
+                C1 = __ldg(pc + i1);
+            }
+            float d0[3], x0[3], d1[3], x1[3];
+            PointSlot s0 = point_hash(P, m, A0.x, A0.y, A0.z, d0, x0);
+            PointSlot s1 = point_hash(P, m, A1.x, A1.y, A1.z, d1, x1);
+            s1.ok = s1.ok && h1;
+            const uint64_t f0 = s0.ok ? __ldg(m.keys + s0.h) : kEmptyKey;
+            const uint64_t f1 = s1.ok ? __ldg(m.keys + s1.h) : kEmptyKey;
+            const int slot0 = resolve_slot(m, s0, f0);
+            const int slot1 = resolve_slot(m, s1, f1);
+            VoxelRec v0, v1;
+            if (slot0 >= 0) v0 = m.rec[slot0];
+            if (slot1 >= 0) v1 = m.rec[slot1];
+            if (slot0 >= 0) inl += accumulate_point(acc, P.Rh, A0, B0, C0, v0, d0, x0);
+            if (slot1 >= 0) inl += accumulate_point(acc, P.Rh, A1, B1, C1, v1, d1, x1);
+        }
+    }
+}
+
+template <int BLOCK, int MINB, int PTS>
+__global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *__restrict__ params,
+                                                               const MapDesc *__restrict__ maps,
+                                                               const FrameDesc *__restrict__ frames,
+                                                               const WorkItem *__restrict__ items, int n_items,
+                                                               double *__restrict__ partials,
+                                                               int64_t *__restrict__ inl_partials)
 {
     constexpr int NW = BLOCK / 32;
-    __shared__ PoseParam sP;
-    __shared__ MapDesc sM;
-    __shared__ FrameDesc sF;
-    __shared__ float sRed[NW][kNT];
-    __shared__ int sInl[NW];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    constexpr int PW = (int)(sizeof(PoseParam) / 4);
+    __shared__ PoseParam sP[NW];
+    __shared__ MapDesc sM[NW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * NW + wib, nw = gridDim.x * NW;
+    for (int it = gw; it < n_items; it += nw) {
         const WorkItem w = items[it];
-        __syncthreads();   // previous item's readers of sP/sM/sF are done
-        if (threadIdx.x == 0) {
-            sP = params[w.unit];
-            sM = maps[sP.map];
-            sF = frames[sP.frame];
-        }
-        __syncthreads();
-        const PoseParam &P = sP;
-        const MapDesc m = sM;
-        const float R0 = P.Rh[0], R1 = P.Rh[1], R2 = P.Rh[2], R3 = P.Rh[3], R4 = P.Rh[4], R5 = P.Rh[5],
-                    R6 = P.Rh[6], R7 = P.Rh[7], R8 = P.Rh[8];
+        __syncwarp();                       // this warp's readers of its slots are done
+        const uint32_t *src = (const uint32_t *)(params + w.unit);
+        uint32_t *dst = (uint32_t *)(sP + wib);
+        for (int j = lane; j < PW; j += 32) dst[j] = __ldg(src + j);
+        __syncwarp();
+        if (lane == 0) sM[wib] = maps[sP[wib].map];
+        __syncwarp();
+        const PoseParam &P = sP[wib];
+        const MapDesc m = sM[wib];
+        const FrameDesc F = frames[P.frame];
         float acc[kNT];
 #pragma unroll
         for (int j = 0; j < kNT; ++j) acc[j] = 0.f;
         int inl = 0;
-        const float4 *__restrict__ pa = sF.pa;
-        const float4 *__restrict__ pb = sF.pb;
-        const float *__restrict__ pc = sF.pc;
-        const int64_t end = w.start + w.count;
-        for (int64_t i = w.start + threadIdx.x; i < end; i += BLOCK) {
-            const float4 A = __ldg(pa + i);
-            const float4 B = __ldg(pb + i);
-            const float C22 = __ldg(pc + i);
-            int k[3];
-            float d[3];
-            if (!point_key_ff(P, m, A.x, A.y, A.z, k, d)) continue;
-            const int slot = probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2]));
-            if (slot < 0) continue;
-            const VoxelRec v = m.rec[slot];
-            // residual e = mu_B - q, both relative to the voxel's lower corner
-            const float e0 = v.a.x - d[0], e1 = v.a.y - d[1], e2 = v.a.z - d[2];
-            // R C_A (C_A symmetric: c00 c01 c02 / c11 c12 / c22)
-            const float a00 = A.w, a01 = B.x, a02 = B.y, a11 = B.z, a12 = B.w, a22 = C22;
-            const float T00 = R0 * a00 + R1 * a01 + R2 * a02, T01 = R0 * a01 + R1 * a11 + R2 * a12,
-                        T02 = R0 * a02 + R1 * a12 + R2 * a22;
-            const float T10 = R3 * a00 + R4 * a01 + R5 * a02, T11 = R3 * a01 + R4 * a11 + R5 * a12,
-                        T12 = R3 * a02 + R4 * a12 + R5 * a22;
-            const float T20 = R6 * a00 + R7 * a01 + R8 * a02, T21 = R6 * a01 + R7 * a11 + R8 * a12,
-                        T22 = R6 * a02 + R7 * a12 + R8 * a22;
-            // M = C_B + (R C_A) R^T
-            const float m00 = v.a.w + T00 * R0 + T01 * R1 + T02 * R2;
-            const float m01 = v.b.x + T00 * R3 + T01 * R4 + T02 * R5;
-            const float m02 = v.b.y + T00 * R6 + T01 * R7 + T02 * R8;
-            const float m11 = v.b.z + T10 * R3 + T11 * R4 + T12 * R5;
-            const float m12 = v.b.w + T10 * R6 + T11 * R7 + T12 * R8;
-            const float m22 = v.c.x + T20 * R6 + T21 * R7 + T22 * R8;
-            // Omega = M^-1 by the adjugate
-            const float c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
-            const float c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
-            const float det = m00 * c00 + m01 * c01 + m02 * c02;
-            if (!(det > 0.f)) continue;
-            const float id = __frcp_rn(det);
-            const float o00 = c00 * id, o01 = c01 * id, o02 = c02 * id, o11 = c11 * id, o12 = c12 * id,
-                        o22 = c22 * id;
-            // w = Omega e, cost = e . w
-            const float w0 = o00 * e0 + o01 * e1 + o02 * e2;
-            const float w1 = o01 * e0 + o11 * e1 + o12 * e2;
-            const float w2 = o02 * e0 + o12 * e1 + o22 * e2;
-            // lever arm a = R p
-            const float x0 = R0 * A.x + R1 * A.y + R2 * A.z;
-            const float x1 = R3 * A.x + R4 * A.y + R5 * A.z;
-            const float x2 = R6 * A.x + R7 * A.y + R8 * A.z;
-            // P = [a]x Omega  (= H_wv contribution)
-            const float P00 = x1 * o02 - x2 * o01, P01 = x1 * o12 - x2 * o11, P02 = x1 * o22 - x2 * o12;
-            const float P10 = x2 * o00 - x0 * o02, P11 = x2 * o01 - x0 * o12, P12 = x2 * o02 - x0 * o22;
-            const float P20 = x0 * o01 - x1 * o00, P21 = x0 * o11 - x1 * o01, P22 = x0 * o12 - x1 * o02;
-            // H_ww = -[a]x Omega [a]x = -P [a]x (upper triangle)
-            acc[0] += P02 * x1 - P01 * x2;
-            acc[1] += P00 * x2 - P02 * x0;
-            acc[2] += P01 * x0 - P00 * x1;
-            acc[3] += P10 * x2 - P12 * x0;
-            acc[4] += P11 * x0 - P10 * x1;
-            acc[5] += P21 * x0 - P20 * x1;
-            acc[6] += P00; acc[7] += P01; acc[8] += P02;
-            acc[9] += P10; acc[10] += P11; acc[11] += P12;
-            acc[12] += P20; acc[13] += P21; acc[14] += P22;
-            acc[15] += o00; acc[16] += o01; acc[17] += o02; acc[18] += o11; acc[19] += o12; acc[20] += o22;
-            // b_w = a x w, b_v = w
-            acc[21] += x1 * w2 - x2 * w1;
-            acc[22] += x2 * w0 - x0 * w2;
-            acc[23] += x0 * w1 - x1 * w0;
-            acc[24] += w0; acc[25] += w1; acc[26] += w2;
-            acc[27] += e0 * w0 + e1 * w1 + e2 * w2;
-            ++inl;
-        }
-        // warp shuffle, then the block's warps in fixed order (float64)
+        linearize_warp_item<PTS>(P, m, F, w, lane, acc, inl);
+        // butterfly: every lane ends with the warp's sums; lane j writes sum j
+        double mine = 0.0;
 #pragma unroll
         for (int j = 0; j < kNT; ++j) {
             float x = acc[j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            acc[j] = x;
+            if (lane == j) mine = (double)x;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) inl += __shfl_xor_sync(0xffffffffu, inl, o);
-        if (lane == 0) {
-#pragma unroll
-            for (int j = 0; j < kNT; ++j) sRed[warp][j] = acc[j];
-            sInl[warp] = inl;
-        }
-        __syncthreads();
-        if (threadIdx.x < kNT) {
-            double s = 0.0;
-#pragma unroll
-            for (int q = 0; q < NW; ++q) s += (double)sRed[q][threadIdx.x];
-            partials[(int64_t)it * kNT + threadIdx.x] = s;
-        } else if (threadIdx.x == kNT) {
-            int64_t s = 0;
-#pragma unroll
-            for (int q = 0; q < NW; ++q) s += sInl[q];
-            inl_partials[it] = s;
-        }
+        if (lane < kNT) partials[(int64_t)it * kNT + lane] = mine;
+        if (lane == kNT) inl_partials[it] = inl;
     }
 }
 
@@ -583,15 +651,30 @@ void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, cons
                                                                n_tgt, maps, frames, cull, out);
 }
 
+// Variants of the batched kernel: (points per lane per step, blocks per SM the
+// register budget is set for).  Work items are per warp, so the block size only
+// sets the occupancy granularity.
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
-                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials, int block,
-                          int grid, cudaStream_t st)
+                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials, int variant,
+                          int grid_per_sm, int num_sms, cudaStream_t st)
 {
     if (n_items <= 0) return;
-    switch (block) {
-    case 128: k_linearize_f32<128><<<grid, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials); break;
-    case 512: k_linearize_f32<512><<<grid, 512, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials); break;
-    default: k_linearize_f32<256><<<grid, 256, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials); break;
+    switch (variant) {
+    case 1: {   // one point per step + prefetch, 128-thread blocks, 6 per SM
+        const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
+        k_linearize_f32<128, 6, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials);
+        break;
+    }
+    case 2: {   // two points per step, 128-thread blocks, 4 per SM
+        const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
+        k_linearize_f32<128, 4, 2><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials);
+        break;
+    }
+    default: {  // one point per step + prefetch, 128-thread blocks, 5 per SM
+        const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
+        k_linearize_f32<128, 5, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials);
+        break;
+    }
     }
 }
 

@@ -162,12 +162,8 @@ extern "C" vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_fact
     while (threads < n_f) threads <<= 1;
     k_noalloc_plan<<<1, threads, 0, v.stream>>>(d_f, (int)n_f, v.d_frames, v.chunk, d_idx, d_begin, d_items);
     launch_prepare_factors(d_idx, (int)n_f, d_poses, v.d_maps, v.d_frames, d_params, v.stream);
-    const int per_sm = v.blocks_per_sm > 0 ? v.blocks_per_sm : (2048 / v.block > 0 ? 2048 / v.block : 1);
-    int grid = v.num_sms * per_sm;
-    if (grid > n_items) grid = (int)n_items;
-    if (grid < 1) grid = 1;
-    launch_linearize_f32(d_params, v.d_maps, v.d_frames, d_items, (int)n_items, d_partials, d_inl, v.block, grid,
-                         v.stream);
+    launch_linearize_f32(d_params, v.d_maps, v.d_frames, d_items, (int)n_items, d_partials, d_inl, v.variant,
+                         v.blocks_per_sm, v.num_sms, v.stream);
     launch_reduce_finalize(d_params, d_begin, (int)n_f, d_partials, d_inl, H, b, cost, inliers, v.stream);
     ctx_count_launches(ctx, 3 + (n_items > 0));
     e = cudaGetLastError();

@@ -14,11 +14,11 @@ __device__ __noinline__ bool point_key_slow(const PoseParam &P, const MapDesc &m
                                            int k[3])
 {
     bool decided = true;
-    float d[3];
+    float d[3], rp[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         decided &= axis_key_ff(P.Rh + 3 * a, P.Rl + 3 * a, P.th[a], P.tl[a], px, py, pz, m.r_h, m.r_l, m.inv_rf,
-                               P.ffm[a], P.ffup[a], k[a], d[a]);
+                               P.ffm[a], P.ffup[a], k[a], d[a], rp[a]);
     if (decided) return k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN;
     double q[3];
     return key_f64(P.T, px, py, pz, m.inv_r, k, q);
@@ -121,20 +121,35 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
 {
     extern __shared__ uint4 s_tab4[];
     const uint32_t *s_tab = (const uint32_t *)s_tab4;
-    __shared__ PoseParam sP;
+    constexpr int PW = (int)(sizeof(PoseParam) / 4);
+    __shared__ PoseParam sP[kSlice];
     __shared__ MapDesc sM;
-    __shared__ int s_kb[6], s_lg, s_smem, s_n;
-    __shared__ const float4 *s_pa;
-    __shared__ unsigned int s_hits;
+    __shared__ int s_kb[6], s_lg, s_smem;
+    __shared__ const float4 *s_pa[kSlice];
+    __shared__ int s_n[kSlice];
     const int lane = threadIdx.x & 31;
     const int n_slices = (n_src + kSlice - 1) / kSlice;
     const int64_t total = (int64_t)n_slices * n_tgt;
     for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
         const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
-        const int s0 = sl * kSlice, s1 = min(n_src, s0 + kSlice);
+        const int s0 = sl * kSlice, ns = min(n_src, s0 + kSlice) - s0;
         __syncthreads();                                // previous item's readers are done
-        const int live = (threadIdx.x < s1 - s0) ? !pairs[(int64_t)(s0 + threadIdx.x) * n_tgt + t].cull : 0;
+        const int live = (threadIdx.x < ns) ? !pairs[(int64_t)(s0 + threadIdx.x) * n_tgt + t].cull : 0;
         if (!__syncthreads_or(live)) continue;          // every pair of the item culled
+        // the slice's pair parameters (one warp per source) and the target's table
+        {
+            const int wib = threadIdx.x >> 5;
+            if (wib < ns) {
+                const uint32_t *src = (const uint32_t *)(pairs + (int64_t)(s0 + wib) * n_tgt + t);
+                uint32_t *dst = (uint32_t *)(sP + wib);
+                for (int j = lane; j < PW; j += 32) dst[j] = __ldg(src + j);
+                if (lane == 0) {
+                    const FrameDesc &F = frames[__ldg((const int *)&pairs[(int64_t)(s0 + wib) * n_tgt + t].frame)];
+                    s_pa[wib] = F.pa;
+                    s_n[wib] = (int)F.n;
+                }
+            }
+        }
         if (threadIdx.x == 0) {
             sM = maps[pairs[(int64_t)s0 * n_tgt + t].map];
             s_lg = sM.cmeta[0];
@@ -147,25 +162,18 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
             const uint4 *src = (const uint4 *)sM.ckeys;
             for (int i = threadIdx.x; i < (1 << s_lg) / 4; i += kOvBlock) s_tab4[i] = __ldg(src + i);
         }
+        __syncthreads();
         const MapDesc m = sM;
         const bool smem = s_smem;
         const uint32_t lg = (uint32_t)s_lg;
         int kb[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) kb[j] = s_kb[j];
-        for (int s = s0; s < s1; ++s) {
-            __syncthreads();                            // table staged; previous source's count taken
-            if (threadIdx.x == 0) {
-                sP = pairs[(int64_t)s * n_tgt + t];
-                s_hits = 0;
-                s_pa = frames[sP.frame].pa;
-                s_n = (int)frames[sP.frame].n;
-            }
-            __syncthreads();
-            if (sP.cull) continue;                      // uniform across the block
-            const PoseParam &P = sP;
-            const float4 *__restrict__ pa = s_pa;
-            const int n = s_n;
+        for (int si = 0; si < ns; ++si) {
+            const PoseParam &P = sP[si];
+            if (P.cull) continue;                       // uniform across the block
+            const float4 *__restrict__ pa = s_pa[si];
+            const int n = s_n[si];
             unsigned int hits = 0;
             for (int base = 0; base < n; base += kOvBlock * kPPT) {
                 float px[kPPT], py[kPPT], pz[kPPT];
@@ -198,9 +206,8 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
                     hits += __popc(__ballot_sync(0xffffffffu, hit));
                 }
             }
-            if (lane == 0 && hits) atomicAdd(&s_hits, hits);
-            __syncthreads();
-            if (threadIdx.x == 0 && s_hits) atomicAdd(counts + (int64_t)s * n_tgt + t, (unsigned long long)s_hits);
+            if (lane == 0 && hits)
+                atomicAdd(counts + (int64_t)(s0 + si) * n_tgt + t, (unsigned long long)hits);
         }
     }
 }
@@ -216,12 +223,12 @@ __global__ void k_correspondences(const PoseParam *__restrict__ prm, const MapDe
         const float4 A = F.pa[i];
         // the batched linearisation's association: float32-pair transform, float64 at faces
         int k[3];
-        float d[3];
+        float d[3], rp[3];
         bool decided = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             decided &= axis_key_ff(P.Rh + 3 * a, P.Rl + 3 * a, P.th[a], P.tl[a], A.x, A.y, A.z, m.r_h, m.r_l,
-                                   m.inv_rf, P.ffm[a], P.ffup[a], k[a], d[a]);
+                                   m.inv_rf, P.ffm[a], P.ffup[a], k[a], d[a], rp[a]);
         bool ok;
         if (decided) {
             ok = k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN;

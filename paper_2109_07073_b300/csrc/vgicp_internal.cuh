@@ -133,6 +133,18 @@ __device__ __forceinline__ uint32_t hash_slot(uint64_t key, uint32_t log2cap)
     return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - log2cap));
 }
 
+// Continue a probe for key from slot s (the caller has checked the slots before).
+__device__ __forceinline__ int probe_from(const uint64_t *__restrict__ keys, uint32_t mask, uint64_t key, uint32_t s)
+{
+    for (uint32_t i = 0; i < mask; ++i) {
+        const uint64_t k = __ldg(keys + s);
+        if (k == key) return (int)s;
+        if (k == kEmptyKey) return -1;
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
 // Slot of key in the map, or -1.  Linear probing; the table always holds an
 // empty slot (load <= 2/3), so the loop ends at the first empty slot.
 __device__ __forceinline__ int probe(const uint64_t *__restrict__ keys, uint32_t mask, uint32_t log2cap,
@@ -194,7 +206,7 @@ __device__ __forceinline__ float face_dist(float s, float lo, float k, float r_h
 // and d = x - k r in [0, r).
 __device__ __forceinline__ bool axis_key_ff(const float *Rh, const float *Rl, float th, float tl, float px,
                                             float py, float pz, float r_h, float r_l, float inv_rf, float lo_m,
-                                            float up_m, int &k, float &d)
+                                            float up_m, int &k, float &d, float &rp)
 {
     const float h0 = __fmul_rn(Rh[0], px), l0 = __fmaf_rn(Rh[0], px, -h0);
     const float h1 = __fmul_rn(Rh[1], py), l1 = __fmaf_rn(Rh[1], py, -h1);
@@ -202,6 +214,7 @@ __device__ __forceinline__ bool axis_key_ff(const float *Rh, const float *Rl, fl
     float s, e1, e2, e3;
     two_sum(h0, h1, s, e1);
     two_sum(s, h2, s, e2);
+    rp = s;                                         // fl32(Rh . p): the lever arm
     two_sum(s, th, s, e3);
     float lo = __fadd_rn(__fadd_rn(l0, l1), __fadd_rn(l2, e1));
     lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(e2, e3), tl));

@@ -48,7 +48,7 @@ def test_binding_covers_every_export(lib):
 def test_host_only_calls_without_a_gpu(lib):
     vg.load()
     o = vg.vgicp_options_default()
-    assert o.precision == vg.VGICP_PREC_F32 and o.chunk_points == 2048 and o.block_threads == 256
+    assert o.precision == vg.VGICP_PREC_F32 and o.chunk_points == 2048 and o.linearize_variant == 0 and o.overlap_cull == 1
     assert vg.load().vgicp_status_string(4) == b"VGICP_ERR_EMPTY"
     assert vg.load().vgicp_last_error(None) == b"null context"
     # null context is rejected before any CUDA call

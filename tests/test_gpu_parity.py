@@ -296,6 +296,43 @@ def test_knn_covariances_match_oracle(ctx, single):
     assert np.array_equal(ctx.estimate_covariances(tiny, 10, 1e-3), oracle.covariances(tiny))
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_linearize_variants_agree(ctx, variant):
+    tg, tcov, src, scov, poses, factors = _ragged_case(seed=45)
+    hm = [ctx.build_voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
+    hf = [ctx.add_frame(p, c) for p, c in zip(src, scov)]
+    f = vg.make_factors([hm[t] for t, _, _, _ in factors], [hf[s] for _, s, _, _ in factors],
+                        [a for _, _, a, _ in factors], [b for _, _, _, b in factors])
+    ctx.set_options(linearize_variant=0)
+    H0, b0, c0, i0 = ctx.linearize(f, poses)
+    ctx.set_options(linearize_variant=variant)
+    H1, b1, c1, i1 = ctx.linearize(f, poses)
+    ctx.set_options(linearize_variant=0)
+    # same chunks, same per-lane order: the variants differ only in scheduling
+    assert np.array_equal(i0, i1)
+    assert np.allclose(H0, H1, rtol=1e-5, atol=1e-9 * np.abs(H0).max())
+    assert np.allclose(b0, b1, rtol=1e-5, atol=1e-9 * np.abs(b0).max())
+    for h in hm + hf:
+        ctx.release(h)
+
+
+def test_autotune_keeps_results(ctx, single):
+    w, cb, ca = single
+    hm = ctx.build_voxelmap(w.points_target, cb, w.resolution)
+    hf = ctx.add_frame(w.points_source, ca)
+    poses = np.stack([w.T_target, w.T_source])
+    f = vg.make_factors([hm, hm], [hf, hf], [0, 1], [1, 0])
+    best, ms = ctx.autotune(f, poses, reps=1)
+    assert ms > 0 and best.linearize_variant in (0, 1, 2) and best.chunk_points in (1024, 2048, 4096, 8192)
+    H, b, cost, inl = ctx.linearize(f, poses)
+    vm = oracle.voxelmap(w.points_target, cb, w.resolution)
+    L = _oracle_factor(vm, w.points_source, ca, w.T_target, w.T_source)
+    assert inl[0] == L.inliers and err_metric(H[0], L.H, L.SH) <= TOL[vg.VGICP_PREC_F32]
+    ctx.set_options(linearize_variant=0, chunk_points=2048)
+    ctx.release(hm)
+    ctx.release(hf)
+
+
 def test_kernel_launch_counter_moves(ctx, single):
     w, cb, _ = single
     before = ctx.kernel_launches()
