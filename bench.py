@@ -135,32 +135,6 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-def dist_setup(n_gpus):
-    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
-    if world > 1:
-        import torch
-        import torch.distributed as tdist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        tdist.init_process_group("nccl")
-    return rank, world
-
-
-def barrier(world):
-    if world > 1:
-        import torch.distributed as tdist
-        tdist.barrier()
-
-
-def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as tdist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    return float(t.item())
-
-
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -169,7 +143,8 @@ def run_ours(a):
     import torch
 
     import paper_2109_07073_b300 as vg
-    rank, world = dist_setup(a.gpus)
+    from paper_2109_07073_b300.dist import barrier, init, max_over_ranks, weak_scaling_value
+    rank, world = init("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     seed = dg.config_seed(2) + 1000 * rank          # weak scaling: an independent batch per rank
     pts, poses, _ = load_frames(a.frames, a.points, seed)
@@ -241,7 +216,7 @@ def run_ours(a):
         torch.cuda.synchronize()
         barrier(world)
     launches = ctx.kernel_launches() - launches0
-    ms_total = max_over_ranks(t0.elapsed_time(t1), world)
+    ms_total = max_over_ranks(t0.elapsed_time(t1), world, dev)
     ms_step = ms_total / a.steps
     per_step = [e[0].elapsed_time(e[3]) for e in phase_ev]
     ph = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in phase_ev])
@@ -306,31 +281,47 @@ def run_ours(a):
         for _ in range(n_e2e):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_ms = max_over_ranks((time.perf_counter() - w0) * 1e3 / n_e2e, world)
+        e2e_ms = max_over_ranks((time.perf_counter() - w0) * 1e3 / n_e2e, world, dev)
         h2d = sum(p.nbytes for p in np_pts) + sum(c.nbytes for c in np_cov) + poses.nbytes * 3
         d2h = sum(x.nbytes for x in h_out) + h_counts.nbytes
-        e2e = {"value": corr_units * world / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+        e2e = {"value": weak_scaling_value(corr_units, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     peaks, peak_kind = measured_peaks()
-    # dominant phase and its roofline
-    names = ["voxelmap_build", "overlap_matrix", "linearize_f32"]
-    dom = int(np.argmax(ph_mean))
-    n_pairs = n_frames * n_frames
-    alg_bytes = [
-        # build: read 36 B/pt, write 56 B per slot of the tables (keys + records)
-        36 * int(n_src.sum()) + 56 * sum(int(1 << max(4, math.ceil(math.log2(n + n // 2 + 1)))) for n in n_src),
-        # overlap matrix: 12 B of xyz per (point, target) lookup + 8 B count per pair
-        12 * int(n_src.sum()) * n_frames + 8 * n_pairs,
-        # linearise: 36 B per source point + 1,256 B of outputs per factor
-        36 * corr_units + (144 + 12 + 1 + 1) * 8 * n_f,
-    ]
-    achieved = alg_bytes[dom] / (ph_mean[dom] / 1e3) / 1e9
+    lookups_live = ctx.overlap_matrix_work()[1]
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s, FMA = 2 flops
     hbm = float(peaks.get("hbm_gbs", 6400.0))
+    names = ["voxelmap_build", "overlap_matrix", "linearize_f32"]
+    n_pairs = n_frames * n_frames
+    dom = int(np.argmax(ph_mean))
+    lin_bytes = 36 * corr_units + (144 + 12 + 1 + 1) * 8 * n_f        # 36 B per point + outputs
+    lin_gbs = lin_bytes / (ph_mean[2] / 1e3) / 1e9
+    roof_lin = {"bound": "hbm", "kernel": "linearize_f32", "achieved": lin_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": lin_gbs / hbm, "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": int(lin_bytes)}
+    if dom == 1:
+        # the floor of Eq. 8's lookup, x = R p + t and x / r per axis: 21 flops per performed lookup
+        flops = 21.0 * lookups_live
+        ach = flops / (ph_mean[1] / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "overlap_matrix", "achieved": ach, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                    "peak_source": "FP32 lanes x 2 x max SM clock (SMs x 128 x 2 x %.0f MHz)" % sm_max,
+                    "algorithmic_flops_per_launch": flops, "lookups_per_launch": int(lookups_live)}
+    elif dom == 2:
+        roofline = dict(roof_lin)
+    else:
+        b_bytes = 36 * int(n_src.sum()) + 60 * sum(int(1 << max(4, math.ceil(math.log2(n + n // 2 + 1))))
+                                                   for n in n_src)
+        ach = b_bytes / (ph_mean[0] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "voxelmap_build", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None, "peak_source": peak_kind,
+                    "algorithmic_bytes_per_launch": int(b_bytes)}
     clocks = clk.summary()
     res = {
         "metric": METRIC,
-        "value": corr_units * world / (ms_step / 1e3),
+        "value": weak_scaling_value(corr_units, world, ms_step),
         "unit": UNIT,
         "n_gpus": world,
         "steps": a.steps,
@@ -359,14 +350,14 @@ def run_ours(a):
                                "note": "overlap matrix with pair culling off (every point of every pair looked up)"},
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": peak_kind,
-                     "algorithmic_bytes_per_launch": int(alg_bytes[dom])},
+        "roofline": roofline,
+        "roofline_linearize": roof_lin,
+        "overlap_work": {"live_pairs": ctx.overlap_matrix_work()[0], "lookups": int(lookups_live)},
         "clocks": clocks,
         "inliers_total": int(inl.sum()),
     }
     if rank == 0 and not a.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(pts, poses, tgt, src, budget_s=15.0)
+        res["cpu_baseline"] = cpu_baseline(pts, poses, tgt, src)
     if rank == 0:
         print(json.dumps(res), flush=True)
     ctx.close()
@@ -377,15 +368,18 @@ def run_ours(a):
 # ---------------------------------------------------------------------------
 
 def _oracle_sample(pts, poses, tgt, src, n_factors, seed=7):
+    """n_factors factors of the workload, with the oracle's own covariances and voxelmaps."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
     rng = dg.Stream(seed)
     pick = rng.choose(len(tgt), min(n_factors, len(tgt)))
     frames = sorted(set(int(tgt[i]) for i in pick) | set(int(src[i]) for i in pick))
-    covs = {f: oracle.covariances(pts[f]) for f in frames}
-    vms = {f: oracle.voxelmap(pts[f], covs[f], 1.0) for f in set(int(tgt[i]) for i in pick)}
-    jobs = [(vms[int(tgt[i])], pts[int(src[i])], covs[int(src[i])],
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        covs = dict(zip(frames, ex.map(lambda f: oracle.covariances(pts[f]), frames)))
+        tset = sorted(set(int(tgt[i]) for i in pick))
+        vms = dict(zip(tset, ex.map(lambda f: oracle.voxelmap(pts[f], covs[f], 1.0), tset)))
+    return [(vms[int(tgt[i])], pts[int(src[i])], covs[int(src[i])],
              oracle.relative_pose(poses[int(tgt[i])], poses[int(src[i])])) for i in pick]
-    return jobs
 
 
 def _time_oracle(jobs, cores):
@@ -398,16 +392,19 @@ def _time_oracle(jobs, cores):
     return sum(j[1].shape[0] for j in jobs) / dt, dt
 
 
-def cpu_baseline(pts, poses, tgt, src, budget_s=15.0):
+def cpu_baseline(pts, poses, tgt, src, cpu_seconds=20.0):
+    """The FP64 oracle (single-threaded per factor, factors spread over all host cores)
+    on a sample of about cpu_seconds of CPU work."""
     cores = os.cpu_count() or 1
-    jobs = _oracle_sample(pts, poses, tgt, src, 64)
-    v1, dt1 = _time_oracle(jobs[:4], 1)
-    n = max(cores, min(len(jobs), int(budget_s * v1 * cores / max(1, np.mean([j[1].shape[0] for j in jobs])))))
-    jobs = jobs[:n]
+    probe = _oracle_sample(pts, poses, tgt, src, 8, seed=11)
+    v1, _ = _time_oracle(probe, 1)
+    mean_n = float(np.mean([j[1].shape[0] for j in probe]))
+    n = int(max(cores, min(len(tgt), cpu_seconds * v1 / mean_n)))
+    jobs = _oracle_sample(pts, poses, tgt, src, n)
     v, dt = _time_oracle(jobs, cores)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(jobs)} factors of the same workload (FP64 oracle linearisation, "
-                      f"one factor per thread, {dt:.1f} s); 1-core rate {v1:.3g}",
+            "sample": f"{len(jobs)} of the workload's factors (~{cpu_seconds:.0f} s of CPU work; FP64 oracle "
+                      f"linearisation, one factor per thread, {dt:.1f} s wall)",
             "one_core_value": v1}
 
 

@@ -217,6 +217,11 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
                                   const double *poses_src, const double *poses_tgt,
                                   int64_t *counts, int out_kind);
 
+/* Work of the last vgicp_overlap_matrix() call on this context: the number of
+ * pairs not culled and the number of point lookups those pairs performed (the
+ * sum of their source sizes).  Synchronises the context stream. */
+vgicp_status vgicp_overlap_matrix_work(vgicp_ctx *ctx, int64_t *live_pairs, int64_t *lookups);
+
 /* Per-point voxel association of a source against a target (debug / parity):
  * keys (n x 3 int64, host) receives each point's voxel coordinate under
  * T_target_source (INT64_MIN on every axis when invalid), hit (n int32, host)

@@ -32,7 +32,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_build_voxelmaps", "vgicp_voxelmap_size", "vgicp_linearize", "vgicp_overlap",
            "vgicp_overlap_matrix", "vgicp_debug_correspondences", "vgicp_export_voxelmap",
            "vgicp_estimate_covariances", "vgicp_release", "vgicp_memory_in_use", "vgicp_kernel_launches",
-           "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc", "vgicp_autotune"]
+           "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc", "vgicp_autotune", "vgicp_overlap_matrix_work"]
 
 
 class VgicpError(RuntimeError):
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_linearize": [vp, vp, i64, vp, i64, vp, vp, vp, vp, C.c_int],
         "vgicp_linearize_noalloc": [vp, vp, i64, vp, i64, vp, vp, vp, vp],
         "vgicp_autotune": [vp, vp, i64, vp, i64, i32, C.POINTER(Options), C.POINTER(f64)],
+        "vgicp_overlap_matrix_work": [vp, C.POINTER(i64), C.POINTER(i64)],
         "vgicp_overlap": [vp, i64, i64, vp, C.POINTER(f64), C.POINTER(i64)],
         "vgicp_overlap_matrix": [vp, vp, i64, vp, i64, vp, vp, vp, C.c_int],
         "vgicp_debug_correspondences": [vp, i64, i64, vp, vp, vp],
@@ -291,6 +292,13 @@ def vgicp_overlap_matrix(ctx, sources, targets, poses_src, poses_tgt, out=None) 
     _check(ctx, load().vgicp_overlap_matrix(ctx, _ptr(s), s.shape[0], _ptr(t), t.shape[0], _ptr(ps), _ptr(pt),
                                             _ptr(out), kind))
     return out
+
+
+def vgicp_overlap_matrix_work(ctx):
+    """(live pairs, point lookups) of the last overlap matrix on this context."""
+    lp, lk = C.c_int64(), C.c_int64()
+    _check(ctx, load().vgicp_overlap_matrix_work(ctx, C.byref(lp), C.byref(lk)))
+    return lp.value, lk.value
 
 
 def vgicp_debug_correspondences(ctx, source: int, target: int, T_target_source):

@@ -59,6 +59,7 @@ struct vgicp_ctx {
     std::vector<uint32_t> free_idx;
     int64_t bytes_in_use = 0;
     int64_t launches = 0;
+    int64_t last_matrix_pairs = 0;   // pairs of the last overlap matrix (params kept in ws_pairs)
     // descriptor tables (device) and host mirrors
     MapDesc *d_maps = nullptr;
     FrameDesc *d_frames = nullptr;
@@ -811,6 +812,7 @@ vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t tar
     }
     TRY(upload(ctx, ctx->ws_poses, T, 12));
     TRY(ensure(ctx, ctx->ws_pairs, sizeof(PoseParam)));
+    ctx->last_matrix_pairs = 0;
     launch_prepare_given((const double *)ctx->ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames,
                          ctx->opt.overlap_cull, (PoseParam *)ctx->ws_pairs.p, ctx->stream);
     ctx->launches += 1;
@@ -872,6 +874,7 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
                          (const int32_t *)ctx->ws_fidx.p, (const int32_t *)ctx->ws_midx.p, (int)n_src, (int)n_tgt,
                          ctx->d_maps, ctx->d_frames, ctx->opt.overlap_cull, (PoseParam *)ctx->ws_pairs.p,
                          ctx->stream);
+    ctx->last_matrix_pairs = n_pairs;
     unsigned long long *dcounts = (unsigned long long *)counts;
     if (out_kind == VGICP_MEM_HOST) {
         TRY(ensure(ctx, ctx->ws_counts, (size_t)n_pairs * 8));
@@ -889,6 +892,26 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
     return VGICP_OK;
 }
 
+vgicp_status vgicp_overlap_matrix_work(vgicp_ctx *ctx, int64_t *live_pairs, int64_t *lookups)
+{
+    if (!ctx || !live_pairs || !lookups) return VGICP_ERR_INVALID_ARG;
+    *live_pairs = 0;
+    *lookups = 0;
+    if (ctx->last_matrix_pairs <= 0) return VGICP_OK;
+    TRY(ensure(ctx, ctx->ws_counter, 16));
+    CU(cudaMemsetAsync(ctx->ws_counter.p, 0, 16, ctx->stream));
+    launch_count_live((const PoseParam *)ctx->ws_pairs.p, ctx->last_matrix_pairs, ctx->d_frames,
+                      (unsigned long long *)ctx->ws_counter.p, ctx->stream);
+    ctx->launches += 1;
+    CHECK_LAUNCH();
+    unsigned long long h[2];
+    CU(cudaMemcpyAsync(h, ctx->ws_counter.p, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *live_pairs = (int64_t)h[0];
+    *lookups = (int64_t)h[1];
+    return VGICP_OK;
+}
+
 vgicp_status vgicp_debug_correspondences(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t target, const double *T,
                                          int64_t *keys, int32_t *hit)
 {
@@ -903,6 +926,7 @@ vgicp_status vgicp_debug_correspondences(vgicp_ctx *ctx, vgicp_frame_t source, v
     if (n == 0) return VGICP_OK;
     TRY(upload(ctx, ctx->ws_poses, T, 12));
     TRY(ensure(ctx, ctx->ws_pairs, sizeof(PoseParam)));
+    ctx->last_matrix_pairs = 0;
     launch_prepare_given((const double *)ctx->ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames, 0,
                          (PoseParam *)ctx->ws_pairs.p, ctx->stream);
     ctx->launches += 1;

@@ -89,6 +89,10 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
                            int n_tgt, unsigned long long *counts, int grid, cudaStream_t st);
 
+// out[0] += pairs not culled, out[1] += their source sizes (out zeroed).
+void launch_count_live(const PoseParam *pairs, int64_t n_pairs, const FrameDesc *frames, unsigned long long *out,
+                       cudaStream_t st);
+
 // Pair parameters of an overlap matrix: pair (s, t) -> T_t^-1 T_s; with cull set,
 // pairs whose source bounding box cannot meet the target's voxels are flagged.
 void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, const int32_t *frame_idx,

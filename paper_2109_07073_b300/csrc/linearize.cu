@@ -99,7 +99,11 @@ __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f,
         ext = fmax(ext, fmax(fabs(mn[i]), fabs(mx[i])));
     }
     p.cull = 0;
-    p.pad[0] = p.pad[1] = p.pad[2] = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const long long off = (long long)m.kbox[i] - (long long)p.k0[i];
+        p.koff[i] = (off > INT32_MAX / 2 || off < INT32_MIN / 2) ? INT32_MAX / 2 : (int32_t)off;
+    }
     if (!cull) return;
     // Every transformed point lies in the box of the transformed corners of the
     // source's bounding box; if that box (grown by a margin far above the

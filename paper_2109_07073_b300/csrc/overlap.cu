@@ -96,13 +96,12 @@ __global__ void __launch_bounds__(256) k_overlap(const PoseParam *__restrict__ p
 constexpr int kOvBlock = 1024, kPPT = 4, kSlice = 32;
 constexpr int kSmemLog2 = 15;   // 32,768 compact keys = 128 KB of shared memory
 
-__device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, uint32_t lg, const int kb[6],
-                                            const int k[3])
+// Presence of the voxel at box-relative coordinate (dx, dy, dz) in a compact
+// table (ext = box extents); anything outside the box is absent.
+__device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, uint32_t lg, int ex, int ey, int ez,
+                                            int dx, int dy, int dz)
 {
-    const int dx = k[0] - kb[0], dy = k[1] - kb[1], dz = k[2] - kb[2];
-    if ((unsigned)dx > (unsigned)(kb[3] - kb[0]) || (unsigned)dy > (unsigned)(kb[4] - kb[1]) ||
-        (unsigned)dz > (unsigned)(kb[5] - kb[2]))
-        return false;                                   // outside the voxel box: no voxel
+    if ((unsigned)dx > (unsigned)ex || (unsigned)dy > (unsigned)ey || (unsigned)dz > (unsigned)ez) return false;
     const uint32_t ck = pack_compact(dx, dy, dz), mask = (1u << lg) - 1u;
     uint32_t s = hash_compact(ck, lg);
     for (uint32_t i = 0; i <= mask; ++i) {
@@ -124,7 +123,7 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
     constexpr int PW = (int)(sizeof(PoseParam) / 4);
     __shared__ PoseParam sP[kSlice];
     __shared__ MapDesc sM;
-    __shared__ int s_kb[6], s_lg, s_smem;
+    __shared__ int s_kb[6], s_lg, s_smem;   // voxel box, compact table size, staged?
     __shared__ const float4 *s_pa[kSlice];
     __shared__ int s_n[kSlice];
     const int lane = threadIdx.x & 31;
@@ -166,9 +165,7 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
         const MapDesc m = sM;
         const bool smem = s_smem;
         const uint32_t lg = (uint32_t)s_lg;
-        int kb[6];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) kb[j] = s_kb[j];
+        const int ex = s_kb[3] - s_kb[0], ey = s_kb[4] - s_kb[1], ez = s_kb[5] - s_kb[2];
         for (int si = 0; si < ns; ++si) {
             const PoseParam &P = sP[si];
             if (P.cull) continue;                       // uniform across the block
@@ -188,21 +185,24 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
 #pragma unroll
                 for (int j = 0; j < kPPT; ++j) {
                     int k[3];
-                    bool dec = true;
+                    bool dec = true, hit = false;
+                    if (smem) {
 #pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        dec &= axis_key_split(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.k0[a], px[j], py[j],
-                                              pz[j], m.r_h, m.r_l, m.inv_rf, k[a]);
-                    bool hit = false;
-                    if (have[j]) {
-                        if (!dec) {                     // face: float32-pair, then float64
-                            hit = point_key_slow(P, m, px[j], py[j], pz[j], k) &&
-                                  probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
-                        } else if (k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN) {
-                            hit = smem ? compact_hit(s_tab, lg, kb, k)
-                                       : probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
-                        }
+                        for (int a = 0; a < 3; ++a)
+                            dec &= axis_box(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.koff[a], px[j], py[j],
+                                            pz[j], m.r_h, m.r_l, m.inv_rf, k[a]);
+                        if (have[j] && dec) hit = compact_hit(s_tab, lg, ex, ey, ez, k[0], k[1], k[2]);
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            dec &= axis_key_split(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.k0[a], px[j],
+                                                  py[j], pz[j], m.r_h, m.r_l, m.inv_rf, k[a]);
+                        if (have[j] && dec && k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN)
+                            hit = probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
                     }
+                    if (have[j] && !dec)                // face: float32-pair, then float64
+                        hit = point_key_slow(P, m, px[j], py[j], pz[j], k) &&
+                              probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
                     hits += __popc(__ballot_sync(0xffffffffu, hit));
                 }
             }
@@ -244,7 +244,34 @@ __global__ void k_correspondences(const PoseParam *__restrict__ prm, const MapDe
     }
 }
 
+__global__ void k_count_live(const PoseParam *__restrict__ pairs, int64_t n_pairs,
+                             const FrameDesc *__restrict__ frames, unsigned long long *out)
+{
+    unsigned long long live = 0, pts = 0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_pairs; g += (int64_t)gridDim.x * blockDim.x)
+        if (!pairs[g].cull) {
+            ++live;
+            pts += (unsigned long long)frames[pairs[g].frame].n;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        live += __shfl_xor_sync(0xffffffffu, live, o);
+        pts += __shfl_xor_sync(0xffffffffu, pts, o);
+    }
+    if ((threadIdx.x & 31) == 0 && live) {
+        atomicAdd(out, live);
+        atomicAdd(out + 1, pts);
+    }
+}
+
 }  // namespace
+
+void launch_count_live(const PoseParam *pairs, int64_t n_pairs, const FrameDesc *frames, unsigned long long *out,
+                       cudaStream_t st)
+{
+    if (n_pairs <= 0) return;
+    k_count_live<<<148 * 4, 256, 0, st>>>(pairs, n_pairs, frames, out);
+}
 
 void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                     int n_items, unsigned long long *counts, int grid, cudaStream_t st)

@@ -93,7 +93,7 @@ struct __align__(16) PoseParam {
     float ffm[3];        // decided when ffm <= x - k r <= ffup
     float ffup[3];
     int32_t cull;        // 1: the pair provably has no correspondence
-    int32_t pad[3];
+    int32_t koff[3];     // target voxel-box minimum minus k0: compact coordinate = floor(x'/r) - koff
 };
 
 // ---------------------------------------------------------------- keys ----
@@ -251,6 +251,20 @@ __device__ __forceinline__ bool axis_key_split(const float *Rh, float tfh, float
     const int kk = (int)kf + k0;
     k = (kk >= -kKeyOffset && kk <= kKeyOffset - 1) ? kk : INT32_MIN;
     return true;
+}
+
+// One axis of the floor on the split translation, returned relative to the
+// target's voxel box (dx = floor(x / r) - box minimum) for the compact tables:
+// coordinates outside the box fail the caller's unsigned range test, so no
+// separate validity check is needed.  Returns false when undecided.
+__device__ __forceinline__ bool axis_box(const float *Rh, float tfh, float tol, float rup, int koff, float px,
+                                         float py, float pz, float r_h, float r_l, float inv_rf, int &dx)
+{
+    const float x = __fmaf_rn(Rh[0], px, __fmaf_rn(Rh[1], py, __fmaf_rn(Rh[2], pz, tfh)));
+    const float kf = floorf(__fmul_rn(x, inv_rf));
+    const float d = __fmaf_rn(-kf, r_l, __fmaf_rn(-kf, r_h, x));
+    dx = (int)kf - koff;
+    return d >= tol && d <= rup;
 }
 
 // One axis from a plain float32 fma chain with the error bound

@@ -238,7 +238,8 @@ __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDe
 
 // Compact presence table of each map: the compact key of every voxel, inserted
 // into the first 2^lg entries of ckeys (lg = log2 of the smallest power of two
-// >= 2 V, at most the main capacity), when the voxel box extent allows it.
+// >= 4 V, at most the main capacity: load <= 1/4, short probe chains), when the
+// voxel box extent allows it.
 __global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units,
                                 const WorkItem *__restrict__ items, int n_items, BuildScratch scr)
 {
@@ -251,7 +252,7 @@ __global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUni
         const bool ok = nv > 0 && kb[3] - kb[0] <= kCompactMaxX && kb[4] - kb[1] <= kCompactMaxX &&
                         kb[5] - kb[2] <= kCompactMaxZ;
         uint32_t lg = 4;
-        while (lg < m.log2cap && (1u << lg) < 2u * nv) ++lg;
+        while (lg < m.log2cap && (1u << lg) < 4u * nv) ++lg;
         if (w.start == 0 && threadIdx.x == 0) {
             m.cmeta[0] = (int32_t)lg;
             m.cmeta[1] = ok ? 1 : 0;
