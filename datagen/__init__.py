@@ -268,7 +268,8 @@ class Lidar:
 
 
 def raycast(boxes: Boxes, pose: np.ndarray, lidar: Lidar, rng: Stream) -> np.ndarray:
-    """Sensor-frame hit points (float64) of one spin from world pose `pose` (sensor origin)."""
+    """Sensor-frame hit points (float64) of one spin from world pose `pose` (sensor origin),
+    in firing order (column by column, the rings of a column together)."""
     d_s = lidar.directions()
     R, o = pose[:, :3], pose[:, 3]
     d_w = d_s @ R.T
@@ -306,6 +307,9 @@ def raycast(boxes: Boxes, pose: np.ndarray, lidar: Lidar, rng: Stream) -> np.nda
             tmax = np.nanmin(np.maximum(t1, t2), axis=1)
         hit = (tmax >= tmin) & (tmin > 0.0)
         np.minimum.at(t_best, ray_ids[hit], tmin[hit])
+    # firing order of a spinning LiDAR: column by column, all rings of a column together
+    cm = (np.arange(lidar.rings)[None, :] * lidar.cols + np.arange(lidar.cols)[:, None]).ravel()
+    t_best, d_s = t_best[cm], d_s[cm]
     ok = t_best <= lidar.max_range
     t = t_best[ok] + rng.normal(int(ok.sum()), lidar.noise)
     return d_s[ok] * t[:, None]
@@ -363,3 +367,72 @@ def log_uniform_sizes(rng: Stream, n: int, lo: int = 2000, hi: int = 60000) -> n
 
 def subsample(rng: Stream, points: np.ndarray, n: int) -> np.ndarray:
     return points[rng.choose(points.shape[0], n)]
+
+
+@dataclass
+class UnevenWorkload:
+    """Batched factors of uneven size over a pool of target frames.
+
+    frames[i]: full raycast of frame i (sensor frame, firing order); poses[i] its
+    perturbed world pose.  Target t is frame target_frame[t], downsampled to
+    target_idx[t] (indices into frames[...]), with resolution target_res[t].
+    Factor f pairs target factor_target[f] with source frame factor_frame[f],
+    subsampled to factor_idx[f] (indices into that frame's points).
+    """
+    frames: list
+    poses: np.ndarray
+    target_frame: np.ndarray
+    target_idx: list
+    target_res: np.ndarray
+    factor_target: np.ndarray
+    factor_frame: np.ndarray
+    factor_idx: list
+
+
+def _raycast_job(args):
+    boxes, pose, lidar, seed = args
+    return raycast(boxes, pose, lidar, Stream(seed)).astype(np.float32)
+
+
+def raycast_many(boxes: Boxes, poses, lidar: Lidar, seeds, workers: int = 0) -> list:
+    """Raycasts of many poses; workers > 1 uses a spawn process pool (safe next to CUDA)."""
+    jobs = [(boxes, p, lidar, int(s)) for p, s in zip(poses, seeds)]
+    if workers and workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            return pool.map(_raycast_job, jobs, chunksize=max(1, len(jobs) // (4 * workers)))
+    return [_raycast_job(j) for j in jobs]
+
+
+def uneven_workload(seed: int = None, n_frames: int = 1000, spacing: float = 2.0, n_factors: int = 10000,
+                    target_points: int = 20000, lo: int = 2000, hi: int = 60000, max_offset: float = 10.0,
+                    resolutions=(0.5, 1.0, 2.0), n_boxes: int = 400, lidar: Lidar = None,
+                    rot_sigma_deg: float = 1.0, trans_sigma: float = 0.1, workers: int = 0) -> UnevenWorkload:
+    """Factors with source sizes floor(exp(U[ln lo, ln hi])), targets from a pool of
+    n_frames frames (one per frame) at resolutions drawn from `resolutions`, each source a
+    frame within max_offset metres (along the loop) of its target's frame, subsampled."""
+    lidar = lidar or Lidar()
+    rng = Stream(config_seed(3) if seed is None else seed)
+    road = Road()
+    boxes = urban_scene(rng, road, n_boxes)
+    poses = np.zeros((n_frames, 3, 4))
+    gt = np.zeros((n_frames, 3, 4))
+    for i in range(n_frames):
+        x, y, hd = road.at(i * spacing)
+        T = np.zeros((3, 4))
+        T[:, :3] = so3_exp([0.0, 0.0, hd])
+        T[:, 3] = [x, y, lidar.height]
+        gt[i] = T
+        xi = np.concatenate([rng.normal(3, math.radians(rot_sigma_deg)), rng.normal(3, trans_sigma)])
+        poses[i] = compose(T, se3_exp(xi))
+    seeds = [int(rng.seed) ^ (0x5851F42D4C957F2D * (i + 1) & 0xFFFFFFFFFFFFFFFF) for i in range(n_frames)]
+    frames = raycast_many(boxes, gt, lidar, seeds, workers)
+    target_idx = [rng.choose(f.shape[0], target_points) for f in frames]
+    target_res = np.array(resolutions)[np.floor(rng.uniform(n_frames, 0, len(resolutions))).astype(int)]
+    k = int(max_offset // spacing)
+    tgt = np.floor(rng.uniform(n_factors, 0, n_frames)).astype(np.int64)
+    off = np.floor(rng.uniform(n_factors, 1, k + 1)).astype(np.int64) * np.where(rng.uniform(n_factors) < 0.5, -1, 1)
+    src = (tgt + off) % n_frames
+    sizes = log_uniform_sizes(rng, n_factors, lo, hi)
+    idx = [rng.choose(frames[s].shape[0], int(n)) for s, n in zip(src, sizes)]
+    return UnevenWorkload(frames, poses, np.arange(n_frames), target_idx, target_res, tgt, src, idx)

@@ -100,9 +100,13 @@ typedef struct {
     /* 1 (default): overlap pairs whose source bounding box, moved by the pair's
      * pose and grown by a margin far above float64 rounding, misses the target's
      * voxel bounding box are answered 0 without visiting their points (exact:
-     * such a pair has no correspondence).  0: every point is looked up. */
+     * such a pair has no correspondence), and chunks of consecutive points whose
+     * box misses it are skipped.  0: every point is looked up. */
     int32_t overlap_cull;
-    int32_t reserved;
+    /* 1 (default): the same exact test per chunk of consecutive source points
+     * (chunk boxes kept per frame) lets the linearisation skip work items whose
+     * chunks all miss the target's voxels; results are unchanged. */
+    int32_t linearize_cull;
 } vgicp_options;
 
 /* Fill *opt with the defaults above. */
@@ -122,7 +126,15 @@ vgicp_status vgicp_set_options(vgicp_ctx *ctx, const vgicp_options *opt);
 /* Order subsequent work on another stream (NULL = the context's own stream). */
 vgicp_status vgicp_set_stream(vgicp_ctx *ctx, void *cuda_stream);
 
-/* Block until all work enqueued by the context has finished. */
+/* Select the lane later calls use (0 <= lane < 4).  Each lane has its own CUDA
+ * stream (cuda_stream, or NULL for one the context creates on first use) and
+ * its own scratch buffers, so calls on different lanes may be in flight at
+ * the same time; handles and their device data are shared by all lanes.  The
+ * caller must not release or rebuild a handle that another lane's enqueued
+ * work still reads.  Lane 0 is the context's initial stream. */
+vgicp_status vgicp_set_lane(vgicp_ctx *ctx, int32_t lane, void *cuda_stream);
+
+/* Block until all work enqueued on the context's current lane has finished. */
 vgicp_status vgicp_synchronize(vgicp_ctx *ctx);
 
 /* Register a point cloud with per-point covariances as a source frame (its
@@ -172,6 +184,41 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
 vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
                             int64_t n_poses, int32_t reps, vgicp_options *best, double *best_ms);
 
+/* Gauss-Newton iteration plan.  The global optimisation of Sec. III-D
+ * re-linearises the same factor set at new poses every iteration; a plan
+ * fixes that set once and runs each iteration as one CUDA graph (pose upload,
+ * per-factor pose preparation, the persistent batched float32 linearisation,
+ * the fixed-order per-factor reduction), so an iteration costs one graph
+ * launch instead of per-call validation, work-list and launch overhead.
+ * Results are bit-identical to vgicp_linearize() with the same options.
+ *
+ * The plan keeps the factor handles and reads their device data at run time,
+ * so voxelmaps rebuilt in place between iterations are used as they are then.
+ * A plan run after a handle was released returns VGICP_ERR_NOT_FOUND; one run
+ * after the options (chunk_points, variant, blocks_per_sm, linearize_cull) or
+ * the context's descriptor tables changed captures its graph again first.
+ * Plans are destroyed before their context; a plan is used by one host thread
+ * at a time and runs on the context's current lane. */
+typedef struct vgicp_plan vgicp_plan;
+
+/* Fix n_f factors whose pose indices are < n_poses, capture the graph. */
+vgicp_status vgicp_plan_create(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, int64_t n_poses,
+                               vgicp_plan **plan);
+
+/* One iteration: poses n_poses x 12 doubles (host, copied into the plan's
+ * pinned staging buffer before the call returns; a run first waits until the
+ * previous run of this plan has read it).  H, b, cost, inliers (nullable) as
+ * for vgicp_linearize(), in out_kind memory; HOST outputs return synchronised,
+ * DEVICE outputs are written in stream order.  Needs VGICP_PREC_F32. */
+vgicp_status vgicp_plan_linearize(vgicp_ctx *ctx, vgicp_plan *plan, const double *poses, double *H, double *b,
+                                  double *cost, int64_t *inliers, int out_kind);
+
+/* Number of runs and of graph captures so far (either may be NULL). */
+vgicp_status vgicp_plan_info(vgicp_ctx *ctx, const vgicp_plan *plan, int64_t *runs, int64_t *captures);
+
+/* Wait for the plan's last run and free it. */
+vgicp_status vgicp_plan_destroy(vgicp_ctx *ctx, vgicp_plan *plan);
+
 /* Size limits of vgicp_linearize_noalloc() (its fixed scratch is sized for them). */
 #define VGICP_NOALLOC_MAX_FACTORS 1024
 #define VGICP_NOALLOC_MAX_POSES 2048
@@ -208,6 +255,13 @@ vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_factor *factors
 vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t target,
                            const double *T_target_source, double *fraction, int64_t *count);
 
+/* Overlap counts of n listed pairs (Eq. 7-8 numerators): counts[i] = #{k :
+ * voxel(T_i p_k) in targets[i]} for the points p_k of sources[i], T n x 12
+ * doubles (host, target-from-source).  counts int64 in out_kind memory.
+ * Sources with N = 0 give count 0 (the caller decides what Eq. 8 means then). */
+vgicp_status vgicp_overlap_pairs(vgicp_ctx *ctx, const vgicp_frame_t *sources, const vgicp_map_t *targets,
+                                 int64_t n, const double *T, int64_t *counts, int out_kind);
+
 /* Overlap counts of every (source, target) pair (Eq. 7-8 numerators):
  * counts[s * n_tgt + t] = #{k : voxel(T_t^-1 T_s p_k) in map t}, poses_src
  * n_src x 12 and poses_tgt n_tgt x 12 (world-from-frame, host).  counts is
@@ -218,8 +272,8 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
                                   int64_t *counts, int out_kind);
 
 /* Work of the last vgicp_overlap_matrix() call on this context: the number of
- * pairs not culled and the number of point lookups those pairs performed (the
- * sum of their source sizes).  Synchronises the context stream. */
+ * pairs not culled and the number of point lookups performed (the points of
+ * their live chunks).  Synchronises the context stream. */
 vgicp_status vgicp_overlap_matrix_work(vgicp_ctx *ctx, int64_t *live_pairs, int64_t *lookups);
 
 /* Per-point voxel association of a source against a target (debug / parity):
@@ -259,6 +313,97 @@ const char *vgicp_last_error(const vgicp_ctx *ctx);
 
 /* Human-readable name of a status code. */
 const char *vgicp_status_string(vgicp_status s);
+
+/* ------------------------------------------------------------------------
+ * Serving loop.  An online mapper (Sec. IV's online mapping and loop closing)
+ * keeps adding frames and asks, at uneven rates and sizes, for overlaps
+ * (Eq. 8) to pick factor candidates and for linearisations (Eq. 3-6) of the
+ * factors it keeps.  A server owns one context and one scheduler thread that
+ * runs the requests submitted by any number of client threads in continuous
+ * batches: whenever one of its lanes is free it launches every pending
+ * request that fits (one batched linearisation plus one batched overlap
+ * list), so batches overlap on the device.  Target clouds and source frames
+ * are registered once under caller keys; the server keeps host copies and
+ * makes them resident on demand (targets as voxelmaps), releasing the least
+ * recently used idle ones when the device-memory budget would be exceeded.
+ * A request's result is bit-identical to the same request run alone: the
+ * batched float32 linearisation sums fixed chunks in a fixed order and
+ * overlap counts are exact.
+ * ---------------------------------------------------------------------- */
+typedef struct vgicp_server vgicp_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;    /* device bytes resident maps and frames may hold (0 = unlimited) */
+    int32_t max_batch_requests;  /* requests per batch (0 = 4096) */
+    int32_t lanes;               /* concurrent batches, 1..4 (0 = 2) */
+    int64_t max_batch_points;    /* source points per batch (0 = 2^27); a larger single request still runs */
+} vgicp_server_options;
+
+enum { VGICP_REQ_LINEARIZE = 0, VGICP_REQ_OVERLAP = 1 };
+
+typedef struct {
+    int32_t kind;                /* VGICP_REQ_LINEARIZE or VGICP_REQ_OVERLAP */
+    int32_t reserved;            /* 0 */
+    int64_t target;              /* key given to vgicp_server_put_map() */
+    int64_t source;              /* key given to vgicp_server_put_frame() */
+    double T_target_source[12];  /* relative pose T_BA, row-major 3x4, finite */
+} vgicp_request;
+
+typedef struct {
+    vgicp_status status;         /* VGICP_OK, or why the request failed (VGICP_ERR_BUDGET: the pair
+                                    cannot fit the budget even with everything else released) */
+    int32_t kind;
+    double H[144];               /* LINEARIZE: as vgicp_linearize() with T_target = I, T_source = T_BA */
+    double b[12];
+    double cost;
+    int64_t count;               /* LINEARIZE: inliers; OVERLAP: points with a target voxel */
+    double fraction;             /* OVERLAP: count / N (status VGICP_ERR_EMPTY when N = 0) */
+    double latency_ms;           /* submit to completion, host clock */
+} vgicp_result;
+
+typedef struct {
+    int64_t submitted, completed, batches, admissions, evictions;
+    int64_t resident_bytes;      /* device bytes held by resident maps and frames */
+    double mean_batch_requests;
+    double p50_ms, p99_ms, max_ms; /* latency quantiles of completed requests */
+} vgicp_server_counters;
+
+/* Create a server on the current CUDA device.  opt and kernel_opt (kernel
+ * variant, chunk size, culling; precision is forced to VGICP_PREC_F32) may be
+ * NULL for defaults. */
+vgicp_status vgicp_server_create(vgicp_server **server, const vgicp_server_options *opt,
+                                 const vgicp_options *kernel_opt);
+
+/* Finish every batch in flight, stop the scheduler and free everything.
+ * Requests still pending are dropped. */
+vgicp_status vgicp_server_destroy(vgicp_server *server);
+
+/* Register a target cloud (n x 3 points, n x 6 covariances, host float32) to be
+ * voxelised at resolution r.  The data are copied.  Keys are 0 <= key < 2^62;
+ * a key already registered returns VGICP_ERR_INVALID_ARG. */
+vgicp_status vgicp_server_put_map(vgicp_server *server, int64_t key, const float *points, const float *covs,
+                                  int64_t n, double resolution);
+
+/* Register a source frame (host float32, copied).  Same key rules; maps and
+ * frames have separate key spaces. */
+vgicp_status vgicp_server_put_frame(vgicp_server *server, int64_t key, const float *points, const float *covs,
+                                    int64_t n);
+
+/* Queue a request; *ticket identifies it to vgicp_server_wait().  Unknown keys
+ * return VGICP_ERR_NOT_FOUND and queue nothing.  Thread-safe. */
+vgicp_status vgicp_server_submit(vgicp_server *server, const vgicp_request *req, int64_t *ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; on VGICP_OK *out
+ * holds its result (whose own status may be an error) and the ticket is
+ * retired.  VGICP_ERR_TIMEOUT leaves the ticket valid.  Thread-safe. */
+vgicp_status vgicp_server_wait(vgicp_server *server, int64_t ticket, double timeout_s, vgicp_result *out);
+
+/* Counters and latency quantiles since creation or the last reset. */
+vgicp_status vgicp_server_stats(vgicp_server *server, vgicp_server_counters *out);
+vgicp_status vgicp_server_reset_stats(vgicp_server *server);
+
+/* Text of the server's last error ("" if none). */
+const char *vgicp_server_last_error(const vgicp_server *server);
 
 #ifdef __cplusplus
 }

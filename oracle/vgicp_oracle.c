@@ -471,8 +471,9 @@ static int64_t cell_first(const cell_t *cs, int64_t m, const int64_t *c)
 
 /* The same k nearest neighbours with a uniform grid of cell size h: cubes of
  * cells around the query grow shell by shell until every point not yet seen is
- * provably farther than the current k-th neighbour.  Points with non-finite
- * coordinates get no neighbours (-1). */
+ * provably farther than the current k-th neighbour (after 16 shells the query
+ * scans every point instead).  Points with non-finite coordinates get no
+ * neighbours (-1). */
 void oracle_knn_grid(const float *pts, int64_t n, int k, double h, int64_t *nbr)
 {
     cell_t *cs = (cell_t *)malloc(sizeof(cell_t) * (size_t)(n > 0 ? n : 1));
@@ -501,17 +502,26 @@ void oracle_knn_grid(const float *pts, int64_t n, int k, double h, int64_t *nbr)
             int64_t c0[3];
             for (int d = 0; d < 3; ++d) c0[d] = (int64_t)floor((double)pts[3 * i + d] / h);
             for (int64_t s = 0;; ++s) {
-                /* visit the cells at Chebyshev distance exactly s from c0 */
+                if (s > 16) {
+                    /* sparse neighbourhood: scan every point instead */
+                    cnt = 0;
+                    for (int64_t j = 0; j < n; ++j) {
+                        int fin = 1;
+                        for (int d = 0; d < 3; ++d) fin &= isfinite(pts[3 * j + d]);
+                        if (fin) nb_insert(bd, out, &cnt, k, dist2(pts + 3 * i, pts + 3 * j), j);
+                    }
+                    break;
+                }
+                /* visit the cells at Chebyshev distance exactly s from c0 (the shell's surface) */
                 for (int64_t dx = -s; dx <= s; ++dx)
-                    for (int64_t dy = -s; dy <= s; ++dy)
-                        for (int64_t dz = -s; dz <= s; ++dz) {
-                            int64_t a = llabs(dx) > llabs(dy) ? llabs(dx) : llabs(dy);
-                            if (llabs(dz) > a) a = llabs(dz);
-                            if (a != s) continue;
+                    for (int64_t dy = -s; dy <= s; ++dy) {
+                        const int edge = (llabs(dx) == s || llabs(dy) == s);
+                        for (int64_t dz = -s; dz <= s; dz += (edge || s == 0) ? 1 : 2 * s) {
                             int64_t c[3] = {c0[0] + dx, c0[1] + dy, c0[2] + dz};
                             for (int64_t t = cell_first(cs, m, c); t < m && key_cmp(cs[t].c, c) == 0; ++t)
                                 nb_insert(bd, out, &cnt, k, dist2(pts + 3 * i, pts + 3 * cs[t].idx), cs[t].idx);
                         }
+                    }
                 /* everything unseen is at distance >= s*h from the query */
                 const double reach = (double)s * h;
                 if (cnt == k && bd[k - 1] < reach * reach * (1.0 - 1e-9)) break;

@@ -32,7 +32,12 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_build_voxelmaps", "vgicp_voxelmap_size", "vgicp_linearize", "vgicp_overlap",
            "vgicp_overlap_matrix", "vgicp_debug_correspondences", "vgicp_export_voxelmap",
            "vgicp_estimate_covariances", "vgicp_release", "vgicp_memory_in_use", "vgicp_kernel_launches",
-           "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc", "vgicp_autotune", "vgicp_overlap_matrix_work"]
+           "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc", "vgicp_autotune", "vgicp_overlap_matrix_work", "vgicp_set_lane",
+           "vgicp_overlap_pairs", "vgicp_server_create", "vgicp_server_destroy", "vgicp_server_put_map",
+           "vgicp_server_put_frame", "vgicp_server_submit", "vgicp_server_wait", "vgicp_server_stats",
+           "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_plan_create", "vgicp_plan_linearize",
+           "vgicp_plan_info", "vgicp_plan_destroy"]
+VGICP_REQ_LINEARIZE, VGICP_REQ_OVERLAP = 0, 1
 
 
 class VgicpError(RuntimeError):
@@ -44,12 +49,34 @@ class VgicpError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("chunk_points", C.c_int32), ("linearize_variant", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("overlap_cull", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("linearize_cull", C.c_int32)]
 
 
 class Factor(C.Structure):
     _fields_ = [("target", C.c_int64), ("source", C.c_int64), ("target_pose", C.c_int32),
                 ("source_pose", C.c_int32)]
+
+
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch_requests", C.c_int32), ("lanes", C.c_int32),
+                ("max_batch_points", C.c_int64)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("target", C.c_int64), ("source", C.c_int64),
+                ("T_target_source", C.c_double * 12)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("kind", C.c_int32), ("H", C.c_double * 144), ("b", C.c_double * 12),
+                ("cost", C.c_double), ("count", C.c_int64), ("fraction", C.c_double), ("latency_ms", C.c_double)]
+
+
+class ServerCounters(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("batches", C.c_int64),
+                ("admissions", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_int64),
+                ("mean_batch_requests", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("max_ms", C.c_double)]
 
 
 FACTOR_DTYPE = np.dtype([("target", np.int64), ("source", np.int64), ("target_pose", np.int32),
@@ -73,6 +100,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_destroy": [vp],
         "vgicp_set_options": [vp, C.POINTER(Options)],
         "vgicp_set_stream": [vp, vp],
+        "vgicp_set_lane": [vp, i32, vp],
+        "vgicp_overlap_pairs": [vp, vp, vp, i64, vp, vp, C.c_int],
         "vgicp_synchronize": [vp],
         "vgicp_add_frame": [vp, vp, vp, i64, C.c_int, C.POINTER(i64)],
         "vgicp_frame_size": [vp, i64, C.POINTER(i64)],
@@ -91,6 +120,18 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_release": [vp, i64],
         "vgicp_memory_in_use": [vp, C.POINTER(i64)],
         "vgicp_kernel_launches": [vp, C.POINTER(i64)],
+        "vgicp_plan_create": [vp, vp, i64, i64, C.POINTER(vp)],
+        "vgicp_plan_linearize": [vp, vp, vp, vp, vp, vp, vp, C.c_int],
+        "vgicp_plan_info": [vp, vp, C.POINTER(i64), C.POINTER(i64)],
+        "vgicp_plan_destroy": [vp, vp],
+        "vgicp_server_create": [C.POINTER(vp), C.POINTER(ServerOptions), C.POINTER(Options)],
+        "vgicp_server_destroy": [vp],
+        "vgicp_server_put_map": [vp, i64, vp, vp, i64, f64],
+        "vgicp_server_put_frame": [vp, i64, vp, vp, i64],
+        "vgicp_server_submit": [vp, C.POINTER(Request), C.POINTER(i64)],
+        "vgicp_server_wait": [vp, i64, f64, C.POINTER(Result)],
+        "vgicp_server_stats": [vp, C.POINTER(ServerCounters)],
+        "vgicp_server_reset_stats": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -98,6 +139,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         fn.restype = C.c_int
     lib.vgicp_last_error.argtypes = [vp]
     lib.vgicp_last_error.restype = C.c_char_p
+    lib.vgicp_server_last_error.argtypes = [vp]
+    lib.vgicp_server_last_error.restype = C.c_char_p
     lib.vgicp_status_string.argtypes = [C.c_int]
     lib.vgicp_status_string.restype = C.c_char_p
     _lib = lib
@@ -187,6 +230,11 @@ def vgicp_set_stream(ctx, stream=None):
     _check(ctx, load().vgicp_set_stream(ctx, _stream_arg(stream)))
 
 
+def vgicp_set_lane(ctx, lane: int, stream=None):
+    """Select the lane (own stream and scratch; shared handles) of later calls."""
+    _check(ctx, load().vgicp_set_lane(ctx, int(lane), _stream_arg(stream)))
+
+
 def vgicp_synchronize(ctx):
     _check(ctx, load().vgicp_synchronize(ctx))
 
@@ -248,6 +296,38 @@ def vgicp_linearize(ctx, factors, poses, out=None):
     return H, b, cost, inl
 
 
+def vgicp_plan_create(ctx, factors, n_poses: int):
+    """A Gauss-Newton iteration plan: the factor set fixed, each run one CUDA graph launch."""
+    f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
+    plan = C.c_void_p()
+    _check(ctx, load().vgicp_plan_create(ctx, _ptr(f), f.shape[0], int(n_poses), C.byref(plan)))
+    plan.n_f = f.shape[0]
+    return plan
+
+
+def vgicp_plan_linearize(ctx, plan, poses, out=None):
+    """One iteration of a plan at `poses`; same outputs as vgicp_linearize."""
+    P = _pose12(poses)
+    nf = plan.n_f
+    if out is None:
+        out = (np.zeros((nf, 12, 12)), np.zeros((nf, 12)), np.zeros(nf), np.zeros(nf, np.int64))
+    H, b, cost, inl = out
+    kind = VGICP_MEM_DEVICE if _is_torch_cuda(H) else VGICP_MEM_HOST
+    _check(ctx, load().vgicp_plan_linearize(ctx, plan, _ptr(P), _ptr(H), _ptr(b), _ptr(cost), _ptr(inl), kind))
+    return H, b, cost, inl
+
+
+def vgicp_plan_info(ctx, plan):
+    """(runs, graph captures) of a plan."""
+    r, c = C.c_int64(), C.c_int64()
+    _check(ctx, load().vgicp_plan_info(ctx, plan, C.byref(r), C.byref(c)))
+    return r.value, c.value
+
+
+def vgicp_plan_destroy(ctx, plan):
+    _check(ctx, load().vgicp_plan_destroy(ctx, plan))
+
+
 def vgicp_linearize_noalloc(ctx, factors, poses, out):
     """vgicp_linearize without allocating: out = (H, b, cost, inliers) torch CUDA tensors
     (n,12,12) float64, (n,12) float64, (n,) float64, (n,) int64, written asynchronously on the
@@ -279,6 +359,17 @@ def vgicp_overlap(ctx, source: int, target: int, T_target_source):
     fr, cnt = C.c_double(), C.c_int64()
     _check(ctx, load().vgicp_overlap(ctx, source, target, _ptr(T), C.byref(fr), C.byref(cnt)))
     return fr.value, cnt.value
+
+
+def vgicp_overlap_pairs(ctx, sources, targets, T, out=None) -> np.ndarray:
+    """counts (n,) int64: hits of sources[i] in targets[i] under T[i] (target-from-source)."""
+    s, t = _host(sources, np.int64), _host(targets, np.int64)
+    P = _pose12(T)
+    if out is None:
+        out = np.zeros(s.shape[0], np.int64)
+    kind = VGICP_MEM_DEVICE if _is_torch_cuda(out) else VGICP_MEM_HOST
+    _check(ctx, load().vgicp_overlap_pairs(ctx, _ptr(s), _ptr(t), s.shape[0], _ptr(P), _ptr(out), kind))
+    return out
 
 
 def vgicp_overlap_matrix(ctx, sources, targets, poses_src, poses_tgt, out=None) -> np.ndarray:
@@ -402,3 +493,94 @@ class Context:
         if fn is None or name.startswith("_"):
             raise AttributeError(name)
         return lambda *a, **k: fn(self.ctx, *a, **k)
+
+
+def _scheck(server, status: int):
+    if status != VGICP_OK:
+        msg = load().vgicp_server_last_error(server).decode() if server else ""
+        raise VgicpError(status, msg)
+
+
+def vgicp_server_create(options: ServerOptions = None, kernel_options: Options = None):
+    s = C.c_void_p()
+    _scheck(None, load().vgicp_server_create(C.byref(s), C.byref(options) if options is not None else None,
+                                             C.byref(kernel_options) if kernel_options is not None else None))
+    return s
+
+
+def vgicp_server_destroy(server):
+    _scheck(None, load().vgicp_server_destroy(server))
+
+
+def vgicp_server_put_map(server, key: int, points, covs, resolution: float):
+    p, c = _host(points, np.float32, 3), _host(covs, np.float32, 6)
+    _scheck(server, load().vgicp_server_put_map(server, key, _ptr(p), _ptr(c), p.shape[0], resolution))
+
+
+def vgicp_server_put_frame(server, key: int, points, covs):
+    p, c = _host(points, np.float32, 3), _host(covs, np.float32, 6)
+    _scheck(server, load().vgicp_server_put_frame(server, key, _ptr(p), _ptr(c), p.shape[0]))
+
+
+def vgicp_server_submit(server, kind: int, target: int, source: int, T_target_source) -> int:
+    r = Request(kind=kind, target=target, source=source)
+    T = _pose12(T_target_source)
+    if T.shape != (1, 12):
+        raise ValueError("T_target_source must hold 12 values (row-major 3x4)")
+    r.T_target_source[:] = [float(x) for x in T[0]]
+    t = C.c_int64()
+    _scheck(server, load().vgicp_server_submit(server, C.byref(r), C.byref(t)))
+    return t.value
+
+
+def vgicp_server_wait(server, ticket: int, timeout_s: float = -1.0) -> Result:
+    """Result of a request (raises VgicpError(VGICP_ERR_TIMEOUT) when the wait runs out)."""
+    r = Result()
+    _scheck(server, load().vgicp_server_wait(server, ticket, timeout_s, C.byref(r)))
+    return r
+
+
+def vgicp_server_stats(server) -> ServerCounters:
+    c = ServerCounters()
+    _scheck(server, load().vgicp_server_stats(server, C.byref(c)))
+    return c
+
+
+def vgicp_server_reset_stats(server):
+    _scheck(server, load().vgicp_server_reset_stats(server))
+
+
+def vgicp_server_last_error(server) -> str:
+    return load().vgicp_server_last_error(server).decode()
+
+
+class Server:
+    """A vgicp_server with the calls bound as methods (names without the vgicp_server_ prefix)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, lanes: int = 2, max_batch_requests: int = 0,
+                 max_batch_points: int = 0, kernel_options: Options = None):
+        self.server = vgicp_server_create(ServerOptions(hbm_budget_bytes, max_batch_requests, lanes,
+                                                        max_batch_points), kernel_options)
+
+    def close(self):
+        if self.server:
+            vgicp_server_destroy(self.server)
+            self.server = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __getattr__(self, name):
+        fn = globals().get("vgicp_server_" + name)
+        if fn is None or name.startswith("_"):
+            raise AttributeError(name)
+        return lambda *a, **k: fn(self.server, *a, **k)

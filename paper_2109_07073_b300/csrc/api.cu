@@ -46,11 +46,24 @@ struct Plan {
     Buf idx, items, item_begin;
 };
 
+constexpr int kMaxLanes = 4;
+
+// Everything one stream of work needs on its own: the stream, the work lists
+// and the scratch buffers.  Handles, descriptor tables and options are shared
+// by all lanes of a context.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
+    Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
+    Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs, ws_tune, ws_knn;
+    Plan plan;
+    int64_t last_matrix_pairs = 0;   // pairs of the last overlap matrix (params kept in ws_pairs)
+};
+
 }  // namespace
 
 struct vgicp_ctx {
-    cudaStream_t stream = nullptr;
-    cudaStream_t own_stream = nullptr;
     int device = 0;
     int num_sms = 148;
     vgicp_options opt{};
@@ -59,19 +72,18 @@ struct vgicp_ctx {
     std::vector<uint32_t> free_idx;
     int64_t bytes_in_use = 0;
     int64_t launches = 0;
-    int64_t last_matrix_pairs = 0;   // pairs of the last overlap matrix (params kept in ws_pairs)
     // descriptor tables (device) and host mirrors
     MapDesc *d_maps = nullptr;
     FrameDesc *d_frames = nullptr;
     std::vector<MapDesc> h_maps;
     std::vector<FrameDesc> h_frames;
     size_t tab_cap = 0;
-    // workspaces
-    Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
-    Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
-    Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs, ws_tune;
-    Plan plan;
+    Lane lanes[kMaxLanes];
+    int lane = 0;
 };
+
+// the current lane's stream and buffers
+#define LN (ctx->lanes[ctx->lane])
 
 namespace {
 
@@ -113,18 +125,18 @@ vgicp_status ensure(vgicp_ctx *ctx, Buf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return VGICP_OK;
-    if (b.p) CU(cudaFreeAsync(b.p, ctx->stream));
+    if (b.p) CU(cudaFreeAsync(b.p, LN.stream));
     b.p = nullptr;
     b.bytes = 0;
     size_t nb = std::max(bytes, b.bytes * 3 / 2);
-    CU(cudaMallocAsync(&b.p, nb, ctx->stream));
+    CU(cudaMallocAsync(&b.p, nb, LN.stream));
     b.bytes = nb;
     return VGICP_OK;
 }
 
 void free_buf(vgicp_ctx *ctx, Buf &b)
 {
-    if (b.p) cudaFreeAsync(b.p, ctx->stream);
+    if (b.p) cudaFreeAsync(b.p, LN.stream);
     b.p = nullptr;
     b.bytes = 0;
 }
@@ -133,7 +145,7 @@ template <class T>
 vgicp_status upload(vgicp_ctx *ctx, Buf &b, const T *src, size_t count)
 {
     TRY(ensure(ctx, b, count * sizeof(T)));
-    if (count) CU(cudaMemcpyAsync(b.p, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    if (count) CU(cudaMemcpyAsync(b.p, src, count * sizeof(T), cudaMemcpyHostToDevice, LN.stream));
     return VGICP_OK;
 }
 
@@ -153,20 +165,23 @@ Obj *lookup(vgicp_ctx *ctx, int64_t h, Obj::Kind kind, uint32_t *idx_out = nullp
 vgicp_status grow_tables(vgicp_ctx *ctx, size_t need)
 {
     if (need <= ctx->tab_cap) return VGICP_OK;
+    // other lanes may be reading or writing the current tables
+    for (int l = 0; l < kMaxLanes; ++l)
+        if (l != ctx->lane && ctx->lanes[l].stream) CU(cudaStreamSynchronize(ctx->lanes[l].stream));
     size_t cap = std::max<size_t>(64, ctx->tab_cap);
     while (cap < need) cap *= 2;
     MapDesc *nm = nullptr;
     FrameDesc *nf = nullptr;
-    CU(cudaMallocAsync((void **)&nm, cap * sizeof(MapDesc), ctx->stream));
-    CU(cudaMallocAsync((void **)&nf, cap * sizeof(FrameDesc), ctx->stream));
-    CU(cudaMemsetAsync(nm, 0, cap * sizeof(MapDesc), ctx->stream));
-    CU(cudaMemsetAsync(nf, 0, cap * sizeof(FrameDesc), ctx->stream));
+    CU(cudaMallocAsync((void **)&nm, cap * sizeof(MapDesc), LN.stream));
+    CU(cudaMallocAsync((void **)&nf, cap * sizeof(FrameDesc), LN.stream));
+    CU(cudaMemsetAsync(nm, 0, cap * sizeof(MapDesc), LN.stream));
+    CU(cudaMemsetAsync(nf, 0, cap * sizeof(FrameDesc), LN.stream));
     if (ctx->tab_cap) {
-        CU(cudaMemcpyAsync(nm, ctx->d_maps, ctx->tab_cap * sizeof(MapDesc), cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(nm, ctx->d_maps, ctx->tab_cap * sizeof(MapDesc), cudaMemcpyDeviceToDevice, LN.stream));
         CU(cudaMemcpyAsync(nf, ctx->d_frames, ctx->tab_cap * sizeof(FrameDesc), cudaMemcpyDeviceToDevice,
-                           ctx->stream));
-        CU(cudaFreeAsync(ctx->d_maps, ctx->stream));
-        CU(cudaFreeAsync(ctx->d_frames, ctx->stream));
+                           LN.stream));
+        CU(cudaFreeAsync(ctx->d_maps, LN.stream));
+        CU(cudaFreeAsync(ctx->d_frames, LN.stream));
     }
     ctx->d_maps = nm;
     ctx->d_frames = nf;
@@ -205,7 +220,7 @@ vgicp_status budget_check(vgicp_ctx *ctx, int64_t extra)
 vgicp_status put_frame_desc(vgicp_ctx *ctx, uint32_t idx)
 {
     CU(cudaMemcpyAsync(ctx->d_frames + idx, &ctx->h_frames[idx], sizeof(FrameDesc), cudaMemcpyHostToDevice,
-                       ctx->stream));
+                       LN.stream));
     return VGICP_OK;
 }
 
@@ -215,13 +230,13 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, int64_t n, uint32_t *out_idx)
 {
     const size_t o_pb = align256((size_t)n * 16), o_pc = o_pb + align256((size_t)n * 16);
-    const size_t o_st = o_pc + align256((size_t)n * 4), bytes = o_st + 256;
+    const size_t o_st = o_pc + align256((size_t)n * 4), o_cb = o_st + 256, bytes = o_cb + 1024;
     TRY(budget_check(ctx, (int64_t)bytes));
     uint32_t idx;
     TRY(new_obj(ctx, Obj::FRAME, &idx));
     Obj &o = ctx->objs[idx];
     char *base = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&base, bytes, ctx->stream);
+    cudaError_t e = cudaMallocAsync((void **)&base, bytes, LN.stream);
     if (e != cudaSuccess) {
         o.kind = Obj::FREE;
         ctx->free_idx.push_back(idx);
@@ -236,13 +251,18 @@ vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, 
     f.pb = (const float4 *)(base + o_pb);
     f.pc = (const float *)(base + o_pc);
     f.stats = (const float *)(base + o_st);
+    f.cbox = (const float *)(base + o_cb);
     f.n = n;
+    f.cshift = 10;
+    while (((int64_t)kMaxCullChunks << f.cshift) < n) ++f.cshift;
+    f.nchunks = (int32_t)((n + ((int64_t)1 << f.cshift) - 1) >> f.cshift);
     // statistics start at: zero maxima of |c| and |p|, +inf minima, -inf maxima
     static const uint32_t init[kStatCount] = {0, 0, 0, 0, kOrderedPosInf, kOrderedPosInf, kOrderedPosInf,
                                               kOrderedNegInf, kOrderedNegInf, kOrderedNegInf};
-    CU(cudaMemcpyAsync(base + o_st, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
-    launch_frame_pack(d_pts, d_cov, n, (float4 *)f.pa, (float4 *)f.pb, (float *)f.pc, (float *)f.stats, ctx->stream);
-    ctx->launches += n > 0;
+    CU(cudaMemcpyAsync(base + o_st, init, sizeof(init), cudaMemcpyHostToDevice, LN.stream));
+    launch_frame_pack(d_pts, d_cov, n, (float4 *)f.pa, (float4 *)f.pb, (float *)f.pc, (float *)f.stats, LN.stream);
+    launch_chunk_boxes(f.pa, n, f.cshift, f.nchunks, (float *)f.cbox, LN.stream);
+    ctx->launches += n > 0 ? 2 : 0;
     CHECK_LAUNCH();
     TRY(put_frame_desc(ctx, idx));
     *out_idx = idx;
@@ -319,22 +339,22 @@ vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const 
         }
         pts += fo.n;
     }
-    TRY(upload(ctx, ctx->ws_bunits, units.data(), units.size()));
-    TRY(upload(ctx, ctx->ws_bprefix, prefix.data(), prefix.size()));
-    TRY(upload(ctx, ctx->ws_bitems, items.data(), items.size()));
-    TRY(ensure(ctx, ctx->ws_slot_of_point, (size_t)pts * 4));
-    TRY(ensure(ctx, ctx->ws_acc, (size_t)pts * 80));
-    TRY(ensure(ctx, ctx->ws_vid_of_slot, (size_t)prefix[nu] * 4));
-    TRY(ensure(ctx, ctx->ws_slot_of_vid, (size_t)pts * 4));
+    TRY(upload(ctx, LN.ws_bunits, units.data(), units.size()));
+    TRY(upload(ctx, LN.ws_bprefix, prefix.data(), prefix.size()));
+    TRY(upload(ctx, LN.ws_bitems, items.data(), items.size()));
+    TRY(ensure(ctx, LN.ws_slot_of_point, (size_t)pts * 4));
+    TRY(ensure(ctx, LN.ws_acc, (size_t)pts * 80));
+    TRY(ensure(ctx, LN.ws_vid_of_slot, (size_t)prefix[nu] * 4));
+    TRY(ensure(ctx, LN.ws_slot_of_vid, (size_t)pts * 4));
     BuildScratch scr;
-    scr.slot_of_point = (int32_t *)ctx->ws_slot_of_point.p;
-    scr.acc = (int64_t *)ctx->ws_acc.p;
-    scr.vid_of_slot = (int32_t *)ctx->ws_vid_of_slot.p;
-    scr.slot_of_vid = (int32_t *)ctx->ws_slot_of_vid.p;
+    scr.slot_of_point = (int32_t *)LN.ws_slot_of_point.p;
+    scr.acc = (int64_t *)LN.ws_acc.p;
+    scr.vid_of_slot = (int32_t *)LN.ws_vid_of_slot.p;
+    scr.slot_of_vid = (int32_t *)LN.ws_slot_of_vid.p;
     const int grid = std::max(1, std::min<int>((int)items.size(), ctx->num_sms * 8));
-    launch_voxelmap_build(ctx->d_maps, ctx->d_frames, (const BuildUnit *)ctx->ws_bunits.p, nu,
-                          (const WorkItem *)ctx->ws_bitems.p, (int)items.size(), (const int64_t *)ctx->ws_bprefix.p,
-                          scr, grid, ctx->stream);
+    launch_voxelmap_build(ctx->d_maps, ctx->d_frames, (const BuildUnit *)LN.ws_bunits.p, nu,
+                          (const WorkItem *)LN.ws_bitems.p, (int)items.size(), (const int64_t *)LN.ws_bprefix.p,
+                          scr, grid, LN.stream);
     ctx->launches += 1 + (items.empty() ? 0 : 4);
     CHECK_LAUNCH();
     return VGICP_OK;
@@ -350,11 +370,11 @@ vgicp_status prepare_map(vgicp_ctx *ctx, uint32_t idx, int64_t n, double r, bool
         const size_t bytes = map_bytes(cap);
         TRY(budget_check(ctx, (int64_t)bytes - (int64_t)o.map_bytes));
         if (o.map_mem) {
-            CU(cudaFreeAsync(o.map_mem, ctx->stream));
+            CU(cudaFreeAsync(o.map_mem, LN.stream));
             ctx->bytes_in_use -= (int64_t)o.map_bytes;
             o.map_mem = nullptr;
         }
-        CU(cudaMallocAsync(&o.map_mem, bytes, ctx->stream));
+        CU(cudaMallocAsync(&o.map_mem, bytes, LN.stream));
         o.map_bytes = bytes;
         o.cap = cap;
         ctx->bytes_in_use += (int64_t)bytes;
@@ -379,8 +399,8 @@ bool finite_pose(const double *T)
 vgicp_status read_nvox(vgicp_ctx *ctx, const Obj &o, int64_t *n)
 {
     uint32_t v = 0;
-    CU(cudaMemcpyAsync(&v, map_nvox_ptr(o), 4, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(&v, map_nvox_ptr(o), 4, cudaMemcpyDeviceToHost, LN.stream));
+    CU(cudaStreamSynchronize(LN.stream));
     *n = v;
     return VGICP_OK;
 }
@@ -390,7 +410,7 @@ int default_chunk(const vgicp_options &o) { return o.chunk_points > 0 ? o.chunk_
 // Work list for a factor set (cached while the set and the chunk size stay the same).
 vgicp_status get_plan(vgicp_ctx *ctx, const vgicp_factor *f, int64_t n_f, const std::vector<int32_t> &idx)
 {
-    Plan &P = ctx->plan;
+    Plan &P = LN.plan;
     const int chunk = default_chunk(ctx->opt);
     bool same = P.chunk == chunk && (int64_t)P.key.size() == n_f &&
                 std::memcmp(P.key.data(), f, sizeof(vgicp_factor) * (size_t)n_f) == 0;
@@ -442,6 +462,7 @@ vgicp_status vgicp_options_default(vgicp_options *opt)
     opt->blocks_per_sm = 0;
     opt->hbm_budget_bytes = 0;
     opt->overlap_cull = 1;
+    opt->linearize_cull = 1;
     return VGICP_OK;
 }
 
@@ -457,6 +478,8 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
     if (o->overlap_cull != 0 && o->overlap_cull != 1)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_cull must be 0 or 1");
+    if (o->linearize_cull != 0 && o->linearize_cull != 1)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_cull must be 0 or 1");
     return VGICP_OK;
 }
 
@@ -473,7 +496,7 @@ vgicp_status vgicp_create(vgicp_ctx **out, const vgicp_options *opt, void *cuda_
     }
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    if (e == cudaSuccess && !cuda_stream) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !cuda_stream) e = cudaStreamCreateWithFlags(&LN.own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         cudaMemPool_t pool;
         e = cudaDeviceGetDefaultMemPool(&pool, ctx->device);
@@ -486,7 +509,7 @@ vgicp_status vgicp_create(vgicp_ctx **out, const vgicp_options *opt, void *cuda_
         delete ctx;
         return VGICP_ERR_CUDA;
     }
-    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+    LN.stream = cuda_stream ? (cudaStream_t)cuda_stream : LN.own_stream;
     *out = ctx;
     return VGICP_OK;
 }
@@ -494,23 +517,46 @@ vgicp_status vgicp_create(vgicp_ctx **out, const vgicp_options *opt, void *cuda_
 vgicp_status vgicp_destroy(vgicp_ctx *ctx)
 {
     if (!ctx) return VGICP_ERR_INVALID_ARG;
+    ctx->lane = 0;
     for (Obj &o : ctx->objs) {
-        if (o.frame_mem) cudaFreeAsync(o.frame_mem, ctx->stream);
-        if (o.map_mem) cudaFreeAsync(o.map_mem, ctx->stream);
+        if (o.frame_mem) cudaFreeAsync(o.frame_mem, LN.stream);
+        if (o.map_mem) cudaFreeAsync(o.map_mem, LN.stream);
     }
-    Buf *bufs[] = {&ctx->ws_poses, &ctx->ws_params, &ctx->ws_partials, &ctx->ws_inl, &ctx->ws_out, &ctx->ws_f64,
-                   &ctx->ws_ticket, &ctx->ws_counts, &ctx->ws_stage, &ctx->ws_bunits, &ctx->ws_bitems,
-                   &ctx->ws_bprefix, &ctx->ws_slot_of_point, &ctx->ws_acc, &ctx->ws_vid_of_slot,
-                   &ctx->ws_slot_of_vid, &ctx->ws_pairs, &ctx->ws_fidx, &ctx->ws_midx, &ctx->ws_chunks,
-                   &ctx->ws_export_keys, &ctx->ws_export_rec, &ctx->ws_counter, &ctx->ws_descs, &ctx->ws_tune, &ctx->plan.idx,
-                   &ctx->plan.items, &ctx->plan.item_begin};
-    for (Buf *b : bufs) free_buf(ctx, *b);
-    if (ctx->d_maps) cudaFreeAsync(ctx->d_maps, ctx->stream);
-    if (ctx->d_frames) cudaFreeAsync(ctx->d_frames, ctx->stream);
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->d_maps) cudaFreeAsync(ctx->d_maps, LN.stream);
+    if (ctx->d_frames) cudaFreeAsync(ctx->d_frames, LN.stream);
+    cudaError_t e = cudaSuccess;
+    for (int l = kMaxLanes - 1; l >= 0; --l) {
+        ctx->lane = l;
+        if (!LN.stream) continue;
+        Buf *bufs[] = {&LN.ws_poses, &LN.ws_params, &LN.ws_partials, &LN.ws_inl, &LN.ws_out, &LN.ws_f64,
+                       &LN.ws_ticket, &LN.ws_counts, &LN.ws_stage, &LN.ws_bunits, &LN.ws_bitems,
+                       &LN.ws_bprefix, &LN.ws_slot_of_point, &LN.ws_acc, &LN.ws_vid_of_slot,
+                       &LN.ws_slot_of_vid, &LN.ws_pairs, &LN.ws_fidx, &LN.ws_midx, &LN.ws_chunks,
+                       &LN.ws_export_keys, &LN.ws_export_rec, &LN.ws_counter, &LN.ws_descs, &LN.ws_tune,
+                       &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_begin};
+        for (Buf *b : bufs) free_buf(ctx, *b);
+        const cudaError_t e2 = cudaStreamSynchronize(LN.stream);
+        if (e == cudaSuccess) e = e2;
+        if (LN.own_stream) cudaStreamDestroy(LN.own_stream);
+    }
     delete ctx;
     return e == cudaSuccess ? VGICP_OK : VGICP_ERR_CUDA;
+}
+
+vgicp_status vgicp_set_lane(vgicp_ctx *ctx, int32_t lane, void *cuda_stream)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (lane < 0 || lane >= kMaxLanes) return fail(ctx, VGICP_ERR_INVALID_ARG, "lane must be in [0, %d)", kMaxLanes);
+    // work already enqueued on other lanes must be done with the shared tables
+    // before this lane can grow them; tables are grown only on lane switches
+    ctx->lane = lane;
+    if (cuda_stream) {
+        LN.stream = (cudaStream_t)cuda_stream;
+    } else if (!LN.stream) {
+        CU(cudaStreamCreateWithFlags(&LN.own_stream, cudaStreamNonBlocking));
+        LN.stream = LN.own_stream;
+    }
+    return VGICP_OK;
 }
 
 vgicp_status vgicp_set_options(vgicp_ctx *ctx, const vgicp_options *opt)
@@ -524,10 +570,10 @@ vgicp_status vgicp_set_options(vgicp_ctx *ctx, const vgicp_options *opt)
 vgicp_status vgicp_set_stream(vgicp_ctx *ctx, void *cuda_stream)
 {
     if (!ctx) return VGICP_ERR_INVALID_ARG;
-    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
-    if (!ctx->stream) {
-        CU(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
-        ctx->stream = ctx->own_stream;
+    LN.stream = cuda_stream ? (cudaStream_t)cuda_stream : LN.own_stream;
+    if (!LN.stream) {
+        CU(cudaStreamCreateWithFlags(&LN.own_stream, cudaStreamNonBlocking));
+        LN.stream = LN.own_stream;
     }
     return VGICP_OK;
 }
@@ -535,7 +581,7 @@ vgicp_status vgicp_set_stream(vgicp_ctx *ctx, void *cuda_stream)
 vgicp_status vgicp_synchronize(vgicp_ctx *ctx)
 {
     if (!ctx) return VGICP_ERR_INVALID_ARG;
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaStreamSynchronize(LN.stream));
     return VGICP_OK;
 }
 
@@ -549,10 +595,10 @@ static vgicp_status stage_inputs(vgicp_ctx *ctx, const float *points, const floa
         return VGICP_OK;
     }
     const size_t pb = align256((size_t)n * 12), cb = covs ? (size_t)n * 24 : 0;
-    TRY(ensure(ctx, ctx->ws_stage, pb + cb));
-    char *base = (char *)ctx->ws_stage.p;
-    if (n) CU(cudaMemcpyAsync(base, points, (size_t)n * 12, cudaMemcpyHostToDevice, ctx->stream));
-    if (covs && n) CU(cudaMemcpyAsync(base + pb, covs, (size_t)n * 24, cudaMemcpyHostToDevice, ctx->stream));
+    TRY(ensure(ctx, LN.ws_stage, pb + cb));
+    char *base = (char *)LN.ws_stage.p;
+    if (n) CU(cudaMemcpyAsync(base, points, (size_t)n * 12, cudaMemcpyHostToDevice, LN.stream));
+    if (covs && n) CU(cudaMemcpyAsync(base + pb, covs, (size_t)n * 24, cudaMemcpyHostToDevice, LN.stream));
     *d_pts = (const float *)base;
     if (d_cov) *d_cov = covs ? (const float *)(base + pb) : nullptr;
     return VGICP_OK;
@@ -618,9 +664,9 @@ vgicp_status vgicp_build_voxelmaps(vgicp_ctx *ctx, const vgicp_frame_t *frames, 
         std::vector<char> host(o_d + upd.size() * sizeof(MapDesc));
         std::memcpy(host.data(), upd_idx.data(), upd_idx.size() * 4);
         std::memcpy(host.data() + o_d, upd.data(), upd.size() * sizeof(MapDesc));
-        TRY(upload(ctx, ctx->ws_descs, host.data(), host.size()));
-        launch_scatter_map_descs((const uint32_t *)ctx->ws_descs.p, (const MapDesc *)((char *)ctx->ws_descs.p + o_d),
-                                 (int)upd.size(), ctx->d_maps, ctx->stream);
+        TRY(upload(ctx, LN.ws_descs, host.data(), host.size()));
+        launch_scatter_map_descs((const uint32_t *)LN.ws_descs.p, (const MapDesc *)((char *)LN.ws_descs.p + o_d),
+                                 (int)upd.size(), ctx->d_maps, LN.stream);
         ctx->launches += 1;
         CHECK_LAUNCH();
     }
@@ -681,13 +727,13 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
     }
     for (int64_t i = 0; i < n_poses * 12; ++i)
         if (!std::isfinite(poses[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: non-finite pose entry");
-    TRY(upload(ctx, ctx->ws_poses, poses, (size_t)n_poses * 12));
+    TRY(upload(ctx, LN.ws_poses, poses, (size_t)n_poses * 12));
     TRY(get_plan(ctx, factors, n_f, idx));
-    Plan &P = ctx->plan;
-    TRY(ensure(ctx, ctx->ws_params, (size_t)n_f * sizeof(PoseParam)));
-    PoseParam *d_params = (PoseParam *)ctx->ws_params.p;
-    launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)ctx->ws_poses.p, ctx->d_maps,
-                           ctx->d_frames, d_params, ctx->stream);
+    Plan &P = LN.plan;
+    TRY(ensure(ctx, LN.ws_params, (size_t)n_f * sizeof(PoseParam)));
+    PoseParam *d_params = (PoseParam *)LN.ws_params.p;
+    launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)LN.ws_poses.p, ctx->d_maps,
+                           ctx->d_frames, ctx->opt.linearize_cull, d_params, LN.stream);
     ctx->launches += 1;
     CHECK_LAUNCH();
     // outputs: caller's device buffers, or a device workspace copied back to the host
@@ -695,8 +741,8 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
     int64_t *di = inliers;
     const size_t out_bytes = (size_t)n_f * (144 + 12 + 1) * 8 + (size_t)n_f * 8;
     if (out_kind == VGICP_MEM_HOST) {
-        TRY(ensure(ctx, ctx->ws_out, out_bytes));
-        dH = (double *)ctx->ws_out.p;
+        TRY(ensure(ctx, LN.ws_out, out_bytes));
+        dH = (double *)LN.ws_out.p;
         db = dH + n_f * 144;
         dc = db + n_f * 12;
         di = (int64_t *)(dc + n_f);
@@ -704,38 +750,271 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
     if (ctx->opt.precision == VGICP_PREC_F64) {
         const int blk = linearize_f64_block();
         int max_grid = ctx->num_sms * 16;
-        TRY(ensure(ctx, ctx->ws_f64, (size_t)max_grid * 92 * 8));
-        TRY(ensure(ctx, ctx->ws_ticket, 4));
-        CU(cudaMemsetAsync(ctx->ws_ticket.p, 0, 4, ctx->stream));
+        TRY(ensure(ctx, LN.ws_f64, (size_t)max_grid * 92 * 8));
+        TRY(ensure(ctx, LN.ws_ticket, 4));
+        CU(cudaMemsetAsync(LN.ws_ticket.p, 0, 4, LN.stream));
         for (int64_t i = 0; i < n_f; ++i) {
             const int64_t n = ctx->objs[idx[4 * i + 1]].n;
             int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, (n + blk - 1) / blk));
-            launch_linearize_f64(d_params + i, ctx->d_maps, ctx->d_frames, n, (double *)ctx->ws_f64.p,
-                                 (unsigned int *)ctx->ws_ticket.p, dH + 144 * i, db + 12 * i, dc + i,
-                                 di ? di + i : nullptr, grid, ctx->stream);
+            launch_linearize_f64(d_params + i, ctx->d_maps, ctx->d_frames, n, (double *)LN.ws_f64.p,
+                                 (unsigned int *)LN.ws_ticket.p, dH + 144 * i, db + 12 * i, dc + i,
+                                 di ? di + i : nullptr, grid, LN.stream);
         }
         ctx->launches += n_f;
         CHECK_LAUNCH();
     } else {
-        TRY(ensure(ctx, ctx->ws_partials, (size_t)std::max(1, P.n_items) * 28 * 8));
-        TRY(ensure(ctx, ctx->ws_inl, (size_t)std::max(1, P.n_items) * 8));
+        TRY(ensure(ctx, LN.ws_partials, (size_t)std::max(1, P.n_items) * 28 * 8));
+        TRY(ensure(ctx, LN.ws_inl, (size_t)std::max(1, P.n_items) * 8));
         launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
-                             (double *)ctx->ws_partials.p, (int64_t *)ctx->ws_inl.p, ctx->opt.linearize_variant,
-                             ctx->opt.blocks_per_sm, ctx->num_sms, ctx->stream);
-        launch_reduce_finalize(d_params, (const int32_t *)P.item_begin.p, (int)n_f, (const double *)ctx->ws_partials.p,
-                               (const int64_t *)ctx->ws_inl.p, dH, db, dc, di, ctx->stream);
+                             (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, ctx->opt.linearize_variant,
+                             ctx->opt.blocks_per_sm, ctx->num_sms, LN.stream);
+        launch_reduce_finalize(d_params, (const int32_t *)P.item_begin.p, (int)n_f, (const double *)LN.ws_partials.p,
+                               (const int64_t *)LN.ws_inl.p, dH, db, dc, di, LN.stream);
         ctx->launches += (P.n_items > 0) + 1;
         CHECK_LAUNCH();
     }
     if (out_kind == VGICP_MEM_HOST) {
-        CU(cudaMemcpyAsync(H, dH, (size_t)n_f * 144 * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaMemcpyAsync(b, db, (size_t)n_f * 12 * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaMemcpyAsync(cost, dc, (size_t)n_f * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        if (inliers) CU(cudaMemcpyAsync(inliers, di, (size_t)n_f * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaMemcpyAsync(H, dH, (size_t)n_f * 144 * 8, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaMemcpyAsync(b, db, (size_t)n_f * 12 * 8, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaMemcpyAsync(cost, dc, (size_t)n_f * 8, cudaMemcpyDeviceToHost, LN.stream));
+        if (inliers) CU(cudaMemcpyAsync(inliers, di, (size_t)n_f * 8, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaStreamSynchronize(LN.stream));
     }
     return VGICP_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- plans --
+//
+// One Gauss-Newton iteration of a fixed factor set as a CUDA graph: the pose
+// upload, the per-factor pose preparation, the persistent linearisation launch
+// and the fixed-order per-factor reduction, instantiated once and relaunched
+// with new poses every iteration.  The graph holds plan-owned buffers only and
+// reads descriptor tables at run time, so voxelmaps rebuilt in place between
+// iterations are seen; a change of the tables' addresses, of a factor's
+// handles or of the kernel options makes the next run capture it again.
+
+struct vgicp_plan {
+    std::vector<vgicp_factor> factors;
+    std::vector<int32_t> idx;
+    std::vector<int64_t> frame_n;
+    int64_t n_f = 0, n_poses = 0;
+    int n_items = 0;
+    Buf d_idx, d_items, d_begin, d_poses, d_params, d_partials, d_inl, d_out;
+    double *h_poses = nullptr;           // pinned staging read by the graph's upload node
+    cudaStream_t cap = nullptr;          // capture stream (nothing runs on it)
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool in_flight = false;
+    // what the graph was captured with
+    MapDesc *maps = nullptr;
+    FrameDesc *frames = nullptr;
+    int chunk = 0, variant = -1, bps = -1, cull = -1;
+    int64_t runs = 0, captures = 0;
+};
+
+namespace {
+
+// Resolve the plan's handles; rebuild its work list and graph when anything
+// they depend on has changed since the last capture.
+vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
+{
+    const int64_t n_f = P->n_f;
+    std::vector<int32_t> idx((size_t)n_f * 4);
+    std::vector<int64_t> fn((size_t)n_f);
+    for (int64_t i = 0; i < n_f; ++i) {
+        uint32_t mi, fi;
+        if (!lookup(ctx, P->factors[i].target, Obj::MAP, &mi))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "plan factor %lld: map handle %lld not found", (long long)i,
+                        (long long)P->factors[i].target);
+        if (!lookup(ctx, P->factors[i].source, Obj::FRAME, &fi))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "plan factor %lld: frame handle %lld not found", (long long)i,
+                        (long long)P->factors[i].source);
+        idx[4 * i + 0] = (int32_t)mi;
+        idx[4 * i + 1] = (int32_t)fi;
+        idx[4 * i + 2] = P->factors[i].target_pose;
+        idx[4 * i + 3] = P->factors[i].source_pose;
+        fn[i] = ctx->objs[fi].n;
+    }
+    const int chunk = default_chunk(ctx->opt);
+    const bool same_work = chunk == P->chunk && idx == P->idx && fn == P->frame_n;
+    if (same_work && P->exec && P->maps == ctx->d_maps && P->frames == ctx->d_frames &&
+        P->variant == ctx->opt.linearize_variant && P->bps == ctx->opt.blocks_per_sm &&
+        P->cull == ctx->opt.linearize_cull)
+        return VGICP_OK;
+    if (P->in_flight) {
+        CU(cudaEventSynchronize(P->done));
+        P->in_flight = false;
+    }
+    if (!same_work) {
+        std::vector<WorkItem> items;
+        std::vector<int32_t> begin((size_t)n_f + 1, 0);
+        for (int64_t i = 0; i < n_f; ++i) {
+            begin[i] = (int32_t)items.size();
+            for (int64_t s = 0; s < fn[i]; s += chunk) {
+                WorkItem w;
+                w.unit = (int32_t)i;
+                w.start = s;
+                w.count = (int32_t)std::min<int64_t>(chunk, fn[i] - s);
+                items.push_back(w);
+            }
+        }
+        begin[n_f] = (int32_t)items.size();
+        TRY(upload(ctx, P->d_idx, idx.data(), idx.size()));
+        TRY(upload(ctx, P->d_items, items.data(), std::max<size_t>(1, items.size())));
+        TRY(upload(ctx, P->d_begin, begin.data(), begin.size()));
+        TRY(ensure(ctx, P->d_partials, std::max<size_t>(1, items.size()) * 28 * 8));
+        TRY(ensure(ctx, P->d_inl, std::max<size_t>(1, items.size()) * 8));
+        CU(cudaStreamSynchronize(LN.stream));   // buffers ready before the graph can run on any stream
+        P->idx = idx;
+        P->frame_n = fn;
+        P->chunk = chunk;
+        P->n_items = (int)items.size();
+    }
+    if (P->exec) {
+        cudaGraphExecDestroy(P->exec);
+        P->exec = nullptr;
+    }
+    PoseParam *params = (PoseParam *)P->d_params.p;
+    double *H = (double *)P->d_out.p, *b = H + n_f * 144, *c = b + n_f * 12;
+    int64_t *inl = (int64_t *)(c + n_f);
+    CU(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(P->d_poses.p, P->h_poses, (size_t)P->n_poses * 12 * 8, cudaMemcpyHostToDevice, P->cap);
+    launch_prepare_factors((const int32_t *)P->d_idx.p, (int)n_f, (const double *)P->d_poses.p, ctx->d_maps,
+                           ctx->d_frames, ctx->opt.linearize_cull, params, P->cap);
+    launch_linearize_f32(params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P->d_items.p, P->n_items,
+                         (double *)P->d_partials.p, (int64_t *)P->d_inl.p, ctx->opt.linearize_variant,
+                         ctx->opt.blocks_per_sm, ctx->num_sms, P->cap);
+    launch_reduce_finalize(params, (const int32_t *)P->d_begin.p, (int)n_f, (const double *)P->d_partials.p,
+                           (const int64_t *)P->d_inl.p, H, b, c, inl, P->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e1 = cudaStreamEndCapture(P->cap, &g);
+    const cudaError_t e0 = cudaGetLastError();
+    if (e1 != cudaSuccess || e0 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, VGICP_ERR_CUDA, "plan capture: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e0));
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&P->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        P->exec = nullptr;
+        return fail(ctx, VGICP_ERR_CUDA, "plan instantiate: %s", cudaGetErrorString(e2));
+    }
+    P->maps = ctx->d_maps;
+    P->frames = ctx->d_frames;
+    P->variant = ctx->opt.linearize_variant;
+    P->bps = ctx->opt.blocks_per_sm;
+    P->cull = ctx->opt.linearize_cull;
+    P->captures += 1;
+    return VGICP_OK;
+}
+
+void plan_free(vgicp_ctx *ctx, vgicp_plan *P)
+{
+    if (P->in_flight) cudaEventSynchronize(P->done);
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    Buf *bufs[] = {&P->d_idx, &P->d_items, &P->d_begin, &P->d_poses, &P->d_params, &P->d_partials, &P->d_inl,
+                   &P->d_out};
+    for (Buf *b : bufs) free_buf(ctx, *b);
+    if (P->h_poses) cudaFreeHost(P->h_poses);
+    if (P->done) cudaEventDestroy(P->done);
+    if (P->cap) cudaStreamDestroy(P->cap);
+    delete P;
+}
+
+}  // namespace
+
+extern "C" {
+
+vgicp_status vgicp_plan_create(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, int64_t n_poses,
+                               vgicp_plan **plan)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (!plan || n_f < 0 || n_poses < 0 || (n_f > 0 && !factors) || n_f > (1 << 30))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "plan_create: null pointer or bad size");
+    *plan = nullptr;
+    for (int64_t i = 0; i < n_f; ++i)
+        if (factors[i].target_pose < 0 || factors[i].target_pose >= n_poses || factors[i].source_pose < 0 ||
+            factors[i].source_pose >= n_poses)
+            return fail(ctx, VGICP_ERR_INVALID_ARG, "plan factor %lld: pose index out of range", (long long)i);
+    vgicp_plan *P = new vgicp_plan();
+    P->factors.assign(factors, factors + n_f);
+    P->n_f = n_f;
+    P->n_poses = n_poses;
+    vgicp_status st = VGICP_OK;
+    auto cu = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && st == VGICP_OK)
+            st = fail(ctx, e == cudaErrorMemoryAllocation ? VGICP_ERR_OOM : VGICP_ERR_CUDA, "plan_create: %s: %s",
+                      what, cudaGetErrorString(e));
+    };
+    cu(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking), "stream");
+    cu(cudaEventCreateWithFlags(&P->done, cudaEventDisableTiming), "event");
+    cu(cudaMallocHost(&P->h_poses, (size_t)std::max<int64_t>(1, n_poses) * 12 * 8), "pinned poses");
+    if (st == VGICP_OK) st = ensure(ctx, P->d_poses, (size_t)std::max<int64_t>(1, n_poses) * 12 * 8);
+    if (st == VGICP_OK) st = ensure(ctx, P->d_params, (size_t)std::max<int64_t>(1, n_f) * sizeof(PoseParam));
+    if (st == VGICP_OK) st = ensure(ctx, P->d_out, (size_t)std::max<int64_t>(1, n_f) * (144 + 12 + 1 + 1) * 8);
+    if (st == VGICP_OK && n_f > 0) st = plan_refresh(ctx, P);
+    if (st != VGICP_OK) {
+        plan_free(ctx, P);
+        return st;
+    }
+    *plan = P;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_plan_linearize(vgicp_ctx *ctx, vgicp_plan *P, const double *poses, double *H, double *b,
+                                  double *cost, int64_t *inliers, int out_kind)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (!P || (P->n_poses > 0 && !poses) || (P->n_f > 0 && (!H || !b || !cost)))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "plan_linearize: null pointer");
+    if (out_kind != VGICP_MEM_HOST && out_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "plan_linearize: bad out_kind %d", out_kind);
+    if (P->n_f == 0) return VGICP_OK;
+    for (int64_t i = 0; i < P->n_poses * 12; ++i)
+        if (!std::isfinite(poses[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "plan_linearize: non-finite pose");
+    if (ctx->opt.precision != VGICP_PREC_F32)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "plan_linearize: plans run the batched float32 path");
+    TRY(plan_refresh(ctx, P));
+    if (P->in_flight) CU(cudaEventSynchronize(P->done));   // the previous run has read the staging buffer
+    std::memcpy(P->h_poses, poses, (size_t)P->n_poses * 12 * 8);
+    CU(cudaGraphLaunch(P->exec, LN.stream));
+    CU(cudaEventRecord(P->done, LN.stream));
+    P->in_flight = true;
+    P->runs += 1;
+    ctx->launches += 2 + (P->n_items > 0);
+    const int64_t n_f = P->n_f;
+    const double *dH = (const double *)P->d_out.p, *db = dH + n_f * 144, *dc = db + n_f * 12;
+    const int64_t *di = (const int64_t *)(dc + n_f);
+    const cudaMemcpyKind k = out_kind == VGICP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CU(cudaMemcpyAsync(H, dH, (size_t)n_f * 144 * 8, k, LN.stream));
+    CU(cudaMemcpyAsync(b, db, (size_t)n_f * 12 * 8, k, LN.stream));
+    CU(cudaMemcpyAsync(cost, dc, (size_t)n_f * 8, k, LN.stream));
+    if (inliers) CU(cudaMemcpyAsync(inliers, di, (size_t)n_f * 8, k, LN.stream));
+    if (out_kind == VGICP_MEM_HOST) CU(cudaStreamSynchronize(LN.stream));
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_plan_info(vgicp_ctx *ctx, const vgicp_plan *P, int64_t *runs, int64_t *captures)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (!P) return fail(ctx, VGICP_ERR_INVALID_ARG, "plan_info: null plan");
+    if (runs) *runs = P->runs;
+    if (captures) *captures = P->captures;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_plan_destroy(vgicp_ctx *ctx, vgicp_plan *P)
+{
+    if (!ctx || !P) return VGICP_ERR_INVALID_ARG;
+    plan_free(ctx, P);
+    return VGICP_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
                             int64_t n_poses, int32_t reps, vgicp_options *best, double *best_ms)
@@ -744,8 +1023,8 @@ vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     if (n_f <= 0 || reps < 1 || !factors || !poses)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "autotune: needs factors, poses and reps >= 1");
     const size_t out = (size_t)n_f * (144 + 12 + 1 + 1) * 8;
-    TRY(ensure(ctx, ctx->ws_tune, out));
-    double *H = (double *)ctx->ws_tune.p, *b = H + n_f * 144, *c = b + n_f * 12;
+    TRY(ensure(ctx, LN.ws_tune, out));
+    double *H = (double *)LN.ws_tune.p, *b = H + n_f * 144, *c = b + n_f * 12;
     int64_t *inl = (int64_t *)(c + n_f);
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
@@ -764,10 +1043,10 @@ vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
             ctx->opt.blocks_per_sm = 0;
             st = vgicp_linearize(ctx, factors, n_f, poses, n_poses, H, b, c, inl, VGICP_MEM_DEVICE);
             if (st != VGICP_OK) break;
-            cudaEventRecord(e0, ctx->stream);
+            cudaEventRecord(e0, LN.stream);
             for (int r = 0; r < reps && st == VGICP_OK; ++r)
                 st = vgicp_linearize(ctx, factors, n_f, poses, n_poses, H, b, c, inl, VGICP_MEM_DEVICE);
-            cudaEventRecord(e1, ctx->stream);
+            cudaEventRecord(e1, LN.stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(ctx, VGICP_ERR_CUDA, "autotune: event"); break; }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
@@ -810,25 +1089,80 @@ vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t tar
         w.count = (int32_t)std::min<int64_t>(4096, n - s);
         items.push_back(w);
     }
-    TRY(upload(ctx, ctx->ws_poses, T, 12));
-    TRY(ensure(ctx, ctx->ws_pairs, sizeof(PoseParam)));
-    ctx->last_matrix_pairs = 0;
-    launch_prepare_given((const double *)ctx->ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames,
-                         ctx->opt.overlap_cull, (PoseParam *)ctx->ws_pairs.p, ctx->stream);
+    TRY(upload(ctx, LN.ws_poses, T, 12));
+    TRY(ensure(ctx, LN.ws_pairs, sizeof(PoseParam)));
+    LN.last_matrix_pairs = 0;
+    launch_prepare_given((const double *)LN.ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames,
+                         ctx->opt.overlap_cull, (PoseParam *)LN.ws_pairs.p, LN.stream);
     ctx->launches += 1;
-    TRY(upload(ctx, ctx->ws_chunks, items.data(), items.size()));
-    TRY(ensure(ctx, ctx->ws_counts, 8));
-    CU(cudaMemsetAsync(ctx->ws_counts.p, 0, 8, ctx->stream));
+    TRY(upload(ctx, LN.ws_chunks, items.data(), items.size()));
+    TRY(ensure(ctx, LN.ws_counts, 8));
+    CU(cudaMemsetAsync(LN.ws_counts.p, 0, 8, LN.stream));
     const int grid = std::max(1, std::min((int)items.size(), ctx->num_sms * 8));
-    launch_overlap((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames, (const WorkItem *)ctx->ws_chunks.p,
-                   (int)items.size(), (unsigned long long *)ctx->ws_counts.p, grid, ctx->stream);
+    launch_overlap((const PoseParam *)LN.ws_pairs.p, ctx->d_maps, ctx->d_frames, (const WorkItem *)LN.ws_chunks.p,
+                   (int)items.size(), (unsigned long long *)LN.ws_counts.p, grid, LN.stream);
     ctx->launches += 1;
     CHECK_LAUNCH();
     unsigned long long c = 0;
-    CU(cudaMemcpyAsync(&c, ctx->ws_counts.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(&c, LN.ws_counts.p, 8, cudaMemcpyDeviceToHost, LN.stream));
+    CU(cudaStreamSynchronize(LN.stream));
     if (count) *count = (int64_t)c;
     *fraction = (double)c / (double)n;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_overlap_pairs(vgicp_ctx *ctx, const vgicp_frame_t *sources, const vgicp_map_t *targets,
+                                 int64_t n, const double *T, int64_t *counts, int out_kind)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!sources || !targets || !T || !counts)))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_pairs: null pointer or negative size");
+    if (out_kind != VGICP_MEM_HOST && out_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_pairs: bad out_kind %d", out_kind);
+    if (n == 0) return VGICP_OK;
+    if (n > (1 << 30)) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_pairs: too many pairs");
+    std::vector<int32_t> idx((size_t)n * 2);
+    std::vector<WorkItem> items;
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t fi, mi;
+        Obj *fo = lookup(ctx, sources[i], Obj::FRAME, &fi);
+        if (!fo) return fail(ctx, VGICP_ERR_NOT_FOUND, "pair %lld: frame handle not found", (long long)i);
+        if (!lookup(ctx, targets[i], Obj::MAP, &mi))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "pair %lld: map handle not found", (long long)i);
+        if (!finite_pose(T + 12 * i)) return fail(ctx, VGICP_ERR_INVALID_ARG, "pair %lld: non-finite pose", (long long)i);
+        idx[i] = (int32_t)mi;
+        idx[n + i] = (int32_t)fi;
+        for (int64_t s = 0; s < fo->n; s += 4096) {
+            WorkItem w;
+            w.unit = (int32_t)i;
+            w.start = s;
+            w.count = (int32_t)std::min<int64_t>(4096, fo->n - s);
+            items.push_back(w);
+        }
+    }
+    TRY(upload(ctx, LN.ws_poses, T, (size_t)n * 12));
+    TRY(upload(ctx, LN.ws_fidx, idx.data(), idx.size()));
+    TRY(upload(ctx, LN.ws_chunks, items.data(), items.size()));
+    TRY(ensure(ctx, LN.ws_pairs, (size_t)n * sizeof(PoseParam)));
+    LN.last_matrix_pairs = 0;
+    const int32_t *d_idx = (const int32_t *)LN.ws_fidx.p;
+    launch_prepare_list((const double *)LN.ws_poses.p, d_idx, d_idx + n, (int)n, ctx->d_maps, ctx->d_frames,
+                        ctx->opt.overlap_cull, (PoseParam *)LN.ws_pairs.p, LN.stream);
+    unsigned long long *dc = (unsigned long long *)counts;
+    if (out_kind == VGICP_MEM_HOST) {
+        TRY(ensure(ctx, LN.ws_counts, (size_t)n * 8));
+        dc = (unsigned long long *)LN.ws_counts.p;
+    }
+    CU(cudaMemsetAsync(dc, 0, (size_t)n * 8, LN.stream));
+    const int grid = std::max(1, std::min((int)items.size(), ctx->num_sms * 8));
+    launch_overlap((const PoseParam *)LN.ws_pairs.p, ctx->d_maps, ctx->d_frames, (const WorkItem *)LN.ws_chunks.p,
+                   (int)items.size(), dc, grid, LN.stream);
+    ctx->launches += 1 + !items.empty();
+    CHECK_LAUNCH();
+    if (out_kind == VGICP_MEM_HOST) {
+        CU(cudaMemcpyAsync(counts, dc, (size_t)n * 8, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaStreamSynchronize(LN.stream));
+    }
     return VGICP_OK;
 }
 
@@ -864,30 +1198,30 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
         if (!std::isfinite(poses_src[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
     for (int64_t i = 0; i < n_tgt * 12; ++i)
         if (!std::isfinite(poses_tgt[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
-    TRY(upload(ctx, ctx->ws_poses, poses_src, (size_t)n_src * 12));
-    TRY(ensure(ctx, ctx->ws_stage, (size_t)n_tgt * 12 * 8));
-    CU(cudaMemcpyAsync(ctx->ws_stage.p, poses_tgt, (size_t)n_tgt * 12 * 8, cudaMemcpyHostToDevice, ctx->stream));
-    TRY(upload(ctx, ctx->ws_fidx, fidx.data(), fidx.size()));
-    TRY(upload(ctx, ctx->ws_midx, midx.data(), midx.size()));
-    TRY(ensure(ctx, ctx->ws_pairs, (size_t)n_pairs * sizeof(PoseParam)));
-    launch_prepare_pairs((const double *)ctx->ws_poses.p, (const double *)ctx->ws_stage.p,
-                         (const int32_t *)ctx->ws_fidx.p, (const int32_t *)ctx->ws_midx.p, (int)n_src, (int)n_tgt,
-                         ctx->d_maps, ctx->d_frames, ctx->opt.overlap_cull, (PoseParam *)ctx->ws_pairs.p,
-                         ctx->stream);
-    ctx->last_matrix_pairs = n_pairs;
+    TRY(upload(ctx, LN.ws_poses, poses_src, (size_t)n_src * 12));
+    TRY(ensure(ctx, LN.ws_stage, (size_t)n_tgt * 12 * 8));
+    CU(cudaMemcpyAsync(LN.ws_stage.p, poses_tgt, (size_t)n_tgt * 12 * 8, cudaMemcpyHostToDevice, LN.stream));
+    TRY(upload(ctx, LN.ws_fidx, fidx.data(), fidx.size()));
+    TRY(upload(ctx, LN.ws_midx, midx.data(), midx.size()));
+    TRY(ensure(ctx, LN.ws_pairs, (size_t)n_pairs * sizeof(PoseParam)));
+    launch_prepare_pairs((const double *)LN.ws_poses.p, (const double *)LN.ws_stage.p,
+                         (const int32_t *)LN.ws_fidx.p, (const int32_t *)LN.ws_midx.p, (int)n_src, (int)n_tgt,
+                         ctx->d_maps, ctx->d_frames, ctx->opt.overlap_cull, (PoseParam *)LN.ws_pairs.p,
+                         LN.stream);
+    LN.last_matrix_pairs = n_pairs;
     unsigned long long *dcounts = (unsigned long long *)counts;
     if (out_kind == VGICP_MEM_HOST) {
-        TRY(ensure(ctx, ctx->ws_counts, (size_t)n_pairs * 8));
-        dcounts = (unsigned long long *)ctx->ws_counts.p;
+        TRY(ensure(ctx, LN.ws_counts, (size_t)n_pairs * 8));
+        dcounts = (unsigned long long *)LN.ws_counts.p;
     }
-    CU(cudaMemsetAsync(dcounts, 0, (size_t)n_pairs * 8, ctx->stream));
-    launch_overlap_matrix((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames, (int)n_src, (int)n_tgt,
-                          dcounts, ctx->num_sms, ctx->stream);
+    CU(cudaMemsetAsync(dcounts, 0, (size_t)n_pairs * 8, LN.stream));
+    launch_overlap_matrix((const PoseParam *)LN.ws_pairs.p, ctx->d_maps, ctx->d_frames, (int)n_src, (int)n_tgt,
+                          dcounts, ctx->num_sms, LN.stream);
     ctx->launches += 2;
     CHECK_LAUNCH();
     if (out_kind == VGICP_MEM_HOST) {
-        CU(cudaMemcpyAsync(counts, dcounts, (size_t)n_pairs * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaMemcpyAsync(counts, dcounts, (size_t)n_pairs * 8, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaStreamSynchronize(LN.stream));
     }
     return VGICP_OK;
 }
@@ -897,16 +1231,16 @@ vgicp_status vgicp_overlap_matrix_work(vgicp_ctx *ctx, int64_t *live_pairs, int6
     if (!ctx || !live_pairs || !lookups) return VGICP_ERR_INVALID_ARG;
     *live_pairs = 0;
     *lookups = 0;
-    if (ctx->last_matrix_pairs <= 0) return VGICP_OK;
-    TRY(ensure(ctx, ctx->ws_counter, 16));
-    CU(cudaMemsetAsync(ctx->ws_counter.p, 0, 16, ctx->stream));
-    launch_count_live((const PoseParam *)ctx->ws_pairs.p, ctx->last_matrix_pairs, ctx->d_frames,
-                      (unsigned long long *)ctx->ws_counter.p, ctx->stream);
+    if (LN.last_matrix_pairs <= 0) return VGICP_OK;
+    TRY(ensure(ctx, LN.ws_counter, 16));
+    CU(cudaMemsetAsync(LN.ws_counter.p, 0, 16, LN.stream));
+    launch_count_live((const PoseParam *)LN.ws_pairs.p, LN.last_matrix_pairs, ctx->d_frames,
+                      (unsigned long long *)LN.ws_counter.p, LN.stream);
     ctx->launches += 1;
     CHECK_LAUNCH();
     unsigned long long h[2];
-    CU(cudaMemcpyAsync(h, ctx->ws_counter.p, 16, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(h, LN.ws_counter.p, 16, cudaMemcpyDeviceToHost, LN.stream));
+    CU(cudaStreamSynchronize(LN.stream));
     *live_pairs = (int64_t)h[0];
     *lookups = (int64_t)h[1];
     return VGICP_OK;
@@ -924,21 +1258,21 @@ vgicp_status vgicp_debug_correspondences(vgicp_ctx *ctx, vgicp_frame_t source, v
         return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)target);
     const int64_t n = fo->n;
     if (n == 0) return VGICP_OK;
-    TRY(upload(ctx, ctx->ws_poses, T, 12));
-    TRY(ensure(ctx, ctx->ws_pairs, sizeof(PoseParam)));
-    ctx->last_matrix_pairs = 0;
-    launch_prepare_given((const double *)ctx->ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames, 0,
-                         (PoseParam *)ctx->ws_pairs.p, ctx->stream);
+    TRY(upload(ctx, LN.ws_poses, T, 12));
+    TRY(ensure(ctx, LN.ws_pairs, sizeof(PoseParam)));
+    LN.last_matrix_pairs = 0;
+    launch_prepare_given((const double *)LN.ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames, 0,
+                         (PoseParam *)LN.ws_pairs.p, LN.stream);
     ctx->launches += 1;
-    TRY(ensure(ctx, ctx->ws_out, (size_t)n * (24 + 4)));
-    int64_t *dk = (int64_t *)ctx->ws_out.p;
+    TRY(ensure(ctx, LN.ws_out, (size_t)n * (24 + 4)));
+    int64_t *dk = (int64_t *)LN.ws_out.p;
     int32_t *dh = (int32_t *)(dk + 3 * n);
-    launch_correspondences((const PoseParam *)ctx->ws_pairs.p, ctx->d_maps, ctx->d_frames, n, dk, dh, ctx->stream);
+    launch_correspondences((const PoseParam *)LN.ws_pairs.p, ctx->d_maps, ctx->d_frames, n, dk, dh, LN.stream);
     ctx->launches += 1;
     CHECK_LAUNCH();
-    if (keys) CU(cudaMemcpyAsync(keys, dk, (size_t)n * 24, cudaMemcpyDeviceToHost, ctx->stream));
-    if (hit) CU(cudaMemcpyAsync(hit, dh, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    if (keys) CU(cudaMemcpyAsync(keys, dk, (size_t)n * 24, cudaMemcpyDeviceToHost, LN.stream));
+    if (hit) CU(cudaMemcpyAsync(hit, dh, (size_t)n * 4, cudaMemcpyDeviceToHost, LN.stream));
+    CU(cudaStreamSynchronize(LN.stream));
     return VGICP_OK;
 }
 
@@ -956,22 +1290,22 @@ vgicp_status vgicp_export_voxelmap(vgicp_ctx *ctx, vgicp_map_t map, int64_t *key
     if (!keys && !counts && !mu && !cov) return VGICP_OK;
     if (capacity < nv) return fail(ctx, VGICP_ERR_INVALID_ARG, "export: capacity %lld < %lld voxels",
                                    (long long)capacity, (long long)nv);
-    TRY(ensure(ctx, ctx->ws_export_keys, (size_t)std::max<int64_t>(nv, 1) * 8));
-    TRY(ensure(ctx, ctx->ws_export_rec, (size_t)std::max<int64_t>(nv, 1) * sizeof(VoxelRec)));
-    TRY(ensure(ctx, ctx->ws_counter, 4));
-    CU(cudaMemsetAsync(ctx->ws_counter.p, 0, 4, ctx->stream));
-    launch_export_voxels(ctx->d_maps + mi, o->cap, (uint32_t *)ctx->ws_counter.p, (uint64_t *)ctx->ws_export_keys.p,
-                         (VoxelRec *)ctx->ws_export_rec.p, ctx->stream);
+    TRY(ensure(ctx, LN.ws_export_keys, (size_t)std::max<int64_t>(nv, 1) * 8));
+    TRY(ensure(ctx, LN.ws_export_rec, (size_t)std::max<int64_t>(nv, 1) * sizeof(VoxelRec)));
+    TRY(ensure(ctx, LN.ws_counter, 4));
+    CU(cudaMemsetAsync(LN.ws_counter.p, 0, 4, LN.stream));
+    launch_export_voxels(ctx->d_maps + mi, o->cap, (uint32_t *)LN.ws_counter.p, (uint64_t *)LN.ws_export_keys.p,
+                         (VoxelRec *)LN.ws_export_rec.p, LN.stream);
     ctx->launches += 1;
     CHECK_LAUNCH();
     std::vector<uint64_t> hk(nv);
     std::vector<VoxelRec> hr(nv);
     if (nv) {
-        CU(cudaMemcpyAsync(hk.data(), ctx->ws_export_keys.p, (size_t)nv * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaMemcpyAsync(hr.data(), ctx->ws_export_rec.p, (size_t)nv * sizeof(VoxelRec), cudaMemcpyDeviceToHost,
-                           ctx->stream));
+        CU(cudaMemcpyAsync(hk.data(), LN.ws_export_keys.p, (size_t)nv * 8, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaMemcpyAsync(hr.data(), LN.ws_export_rec.p, (size_t)nv * sizeof(VoxelRec), cudaMemcpyDeviceToHost,
+                           LN.stream));
     }
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaStreamSynchronize(LN.stream));
     std::vector<int64_t> order(nv);
     for (int64_t i = 0; i < nv; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return hk[a] < hk[b]; });
@@ -1011,15 +1345,16 @@ vgicp_status vgicp_estimate_covariances(vgicp_ctx *ctx, const float *points, int
     TRY(stage_inputs(ctx, points, nullptr, n, mem_kind, &dp, nullptr));
     float *dc = covs_out;
     if (mem_kind == VGICP_MEM_HOST) {
-        TRY(ensure(ctx, ctx->ws_out, (size_t)n * 24));
-        dc = (float *)ctx->ws_out.p;
+        TRY(ensure(ctx, LN.ws_out, (size_t)n * 24));
+        dc = (float *)LN.ws_out.p;
     }
-    launch_knn_covariances(dp, n, k, eps, dc, ctx->stream);
-    ctx->launches += 1;
+    TRY(ensure(ctx, LN.ws_knn, knn_scratch_bytes(n)));
+    launch_knn_covariances(dp, n, k, eps, 1.0, LN.ws_knn.p, dc, LN.stream);
+    ctx->launches += 5;
     CHECK_LAUNCH();
     if (mem_kind == VGICP_MEM_HOST) {
-        CU(cudaMemcpyAsync(covs_out, dc, (size_t)n * 24, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaMemcpyAsync(covs_out, dc, (size_t)n * 24, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaStreamSynchronize(LN.stream));
     }
     return VGICP_OK;
 }
@@ -1031,14 +1366,14 @@ vgicp_status vgicp_release(vgicp_ctx *ctx, int64_t handle)
     Obj *o = lookup(ctx, handle, Obj::FRAME, &idx);
     if (!o) o = lookup(ctx, handle, Obj::MAP, &idx);
     if (!o) return fail(ctx, VGICP_ERR_NOT_FOUND, "handle %lld not found", (long long)handle);
-    if (o->frame_mem) CU(cudaFreeAsync(o->frame_mem, ctx->stream));
-    if (o->map_mem) CU(cudaFreeAsync(o->map_mem, ctx->stream));
+    if (o->frame_mem) CU(cudaFreeAsync(o->frame_mem, LN.stream));
+    if (o->map_mem) CU(cudaFreeAsync(o->map_mem, LN.stream));
     ctx->bytes_in_use -= (int64_t)(o->frame_bytes + o->map_bytes);
     const uint32_t gen = o->gen;
     *o = Obj();
     o->gen = gen;
     ctx->free_idx.push_back(idx);
-    ctx->plan.key.clear();   // a cached work list may name this handle
+    LN.plan.key.clear();   // a cached work list may name this handle
     return VGICP_OK;
 }
 
@@ -1083,11 +1418,12 @@ namespace vg {
 bool ctx_view(vgicp_ctx *ctx, CtxView *v)
 {
     if (!ctx || !v) return false;
-    v->stream = ctx->stream;
+    v->stream = LN.stream;
     v->device = ctx->device;
     v->num_sms = ctx->num_sms;
     v->chunk = default_chunk(ctx->opt);
     v->variant = ctx->opt.linearize_variant;
+    v->linearize_cull = ctx->opt.linearize_cull;
     v->blocks_per_sm = ctx->opt.blocks_per_sm;
     v->d_maps = ctx->d_maps;
     v->d_frames = ctx->d_frames;

@@ -22,6 +22,9 @@ struct __align__(16) WorkItem {
 void launch_frame_pack(const float *points, const float *covs, int64_t n, float4 *pa, float4 *pb, float *pc,
                        float *stats, cudaStream_t st);
 
+// Bounding boxes of a frame's cull chunks (2^shift points each).
+void launch_chunk_boxes(const float4 *pa, int64_t n, int shift, int nchunks, float *cbox, cudaStream_t st);
+
 // Write n map descriptors into the device table: table[idx[i]] = src[i].
 void launch_scatter_map_descs(const uint32_t *idx, const MapDesc *src, int n, MapDesc *table, cudaStream_t st);
 
@@ -51,8 +54,12 @@ void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const B
 // ----------------------------------------------------------- linearise ---
 // Relative poses T_BA = T_B^-1 T_A for every factor, in the forms the kernels use.
 void launch_prepare_factors(const int32_t *factor_idx /* n_f x 4: map, frame, pose_t, pose_s */, int n_f,
-                            const double *poses, const MapDesc *maps, const FrameDesc *frames, PoseParam *out,
-                            cudaStream_t st);
+                            const double *poses, const MapDesc *maps, const FrameDesc *frames, int cull,
+                            PoseParam *out, cudaStream_t st);
+
+// n pairs with given relative poses T (n x 12 doubles, device).
+void launch_prepare_list(const double *T, const int32_t *map_idx, const int32_t *frame_idx, int n,
+                         const MapDesc *maps, const FrameDesc *frames, int cull, PoseParam *out, cudaStream_t st);
 
 // One pair with a given relative pose T (12 doubles, device).
 void launch_prepare_given(const double *T, int map, int frame, const MapDesc *maps, const FrameDesc *frames,
@@ -108,7 +115,10 @@ void launch_export_voxels(const MapDesc *map_dev, uint32_t cap, uint32_t *counte
                           VoxelRec *rec_out, cudaStream_t st);
 
 // ----------------------------------------------------------- covariances --
-void launch_knn_covariances(const float *points, int64_t n, int k, double eps, float *covs, cudaStream_t st);
+// kNN covariances on a uniform grid of cell size h (any h gives the same result).
+size_t knn_scratch_bytes(int64_t n);
+void launch_knn_covariances(const float *points, int64_t n, int k, double eps, double h, void *scratch, float *covs,
+                            cudaStream_t st);
 
 }  // namespace vg
 
@@ -120,7 +130,7 @@ namespace vg {
 
 struct CtxView {
     cudaStream_t stream;
-    int device, num_sms, chunk, variant, blocks_per_sm;
+    int device, num_sms, chunk, variant, blocks_per_sm, linearize_cull;
     MapDesc *d_maps;
     FrameDesc *d_frames;
 };

@@ -66,8 +66,44 @@ __device__ __forceinline__ void split_pose(const double *T, PoseParam &p)
     }
 }
 
+// Live cull chunks of the source for this pair: chunk c's box (min/max of its
+// points), moved by the pose, is tested against the target's voxel box.  The
+// moved box is c' +- |R| h (centre, half extent) in float32, grown by 2^-18 of
+// the magnitudes involved -- 16 times the float32 error of that evaluation --
+// so a dead chunk provably holds no point that can find a voxel.
+__device__ uint32_t chunk_mask(const PoseParam &p, const MapDesc &m, const FrameDesc &f)
+{
+    const int *kb = m.kbox;
+    if (kb[0] > kb[3]) return 0u;
+    const float blo[3] = {(float)((double)kb[0] * m.r), (float)((double)kb[1] * m.r), (float)((double)kb[2] * m.r)};
+    const float bhi[3] = {(float)(((double)kb[3] + 1.0) * m.r), (float)(((double)kb[4] + 1.0) * m.r),
+                          (float)(((double)kb[5] + 1.0) * m.r)};
+    uint32_t mask = 0u;
+    for (int c = 0; c < f.nchunks; ++c) {
+        const float *b = f.cbox + 6 * c;
+        if (!(b[0] <= b[3] && b[1] <= b[4] && b[2] <= b[5])) continue;    // no finite point
+        const float cc[3] = {0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5])};
+        const float hh[3] = {0.5f * (b[3] - b[0]), 0.5f * (b[4] - b[1]), 0.5f * (b[5] - b[2])};
+        bool live = true;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float ci = p.th[i], hi = 0.f, mag = fabsf(p.th[i]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                ci = fmaf(p.Rh[3 * i + j], cc[j], ci);
+                hi = fmaf(fabsf(p.Rh[3 * i + j]), hh[j], hi);
+                mag = fmaf(fabsf(p.Rh[3 * i + j]), fabsf(cc[j]) + hh[j], mag);
+            }
+            const float mu = mag * 0x1p-18f + 1e-6f * (float)m.r + 1e-30f;
+            live = live && (ci + hi + mu >= blo[i]) && (ci - hi - mu <= bhi[i]);
+        }
+        if (live) mask |= 1u << c;
+    }
+    return mask;
+}
+
 // The per-pair bounds of the float32 floors and, when asked, the exact culling
-// test, from p.T, the target map and the source frame's statistics.
+// tests, from p.T, the target map and the source frame's statistics.
 __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f, int cull)
 {
     double pmax[3], mn[3], mx[3];
@@ -99,6 +135,8 @@ __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f,
         ext = fmax(ext, fmax(fabs(mn[i]), fabs(mx[i])));
     }
     p.cull = 0;
+    p.cmask = f.nchunks >= 32 ? 0xffffffffu : ((1u << f.nchunks) - 1u);
+    p.pad2[0] = p.pad2[1] = p.pad2[2] = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const long long off = (long long)m.kbox[i] - (long long)p.k0[i];
@@ -127,10 +165,16 @@ __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f,
         const double blo = (double)kb[i] * m.r, bhi = ((double)kb[3 + i] + 1.0) * m.r;
         if (hi + mu < blo || lo - mu > bhi) p.cull = 1;
     }
+    if (!p.cull) {
+        p.cmask = chunk_mask(p, m, f);
+        if (p.cmask == 0u) p.cull = 1;
+    } else {
+        p.cmask = 0u;
+    }
 }
 
 __global__ void k_prepare_factors(const int32_t *__restrict__ idx, int n_f, const double *__restrict__ poses,
-                                  const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
+                                  const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames, int cull,
                                   PoseParam *__restrict__ out)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -140,7 +184,7 @@ __global__ void k_prepare_factors(const int32_t *__restrict__ idx, int n_f, cons
     split_pose(p.T, p);
     p.map = idx[4 * f + 0];
     p.frame = idx[4 * f + 1];
-    finish_param(p, maps[p.map], frames[p.frame], 0);
+    finish_param(p, maps[p.map], frames[p.frame], cull);
     out[f] = p;
 }
 
@@ -157,6 +201,22 @@ __global__ void k_prepare_pairs(const double *__restrict__ ps, const double *__r
     split_pose(p.T, p);
     p.map = midx[t];
     p.frame = fidx[s];
+    finish_param(p, maps[p.map], frames[p.frame], cull);
+    out[g] = p;
+}
+
+__global__ void k_prepare_list(const double *__restrict__ T, const int32_t *__restrict__ midx,
+                               const int32_t *__restrict__ fidx, int n, const MapDesc *__restrict__ maps,
+                               const FrameDesc *__restrict__ frames, int cull, PoseParam *__restrict__ out)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    PoseParam p;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p.T[i] = T[12 * (int64_t)g + i];
+    split_pose(p.T, p);
+    p.map = midx[g];
+    p.frame = fidx[g];
     finish_param(p, maps[p.map], frames[p.frame], cull);
     out[g] = p;
 }
@@ -283,9 +343,14 @@ __device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, 
 //            before this step's key, probe and record chain;
 //   PTS = 2: two points per lane per step, both points' loads, keys and first
 //            probes issued before either record is needed.
+// Points of one work item, 32 per warp step.
+//   PTS = 1: one point per lane per step, the next step's point loads issued
+//            before this step's key, probe and record chain;
+//   PTS = 2: two points per lane per step, both points' loads, keys and first
+//            probes issued before either record is needed.
 template <int PTS>
-__device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
-                                                    const WorkItem &w, int lane, float acc[kNT], int &inl)
+__device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
+                                                 const WorkItem &w, int lane, float acc[kNT], int &inl)
 {
     const float4 *__restrict__ pa = F.pa + w.start;
     const float4 *__restrict__ pb = F.pb + w.start;
@@ -343,6 +408,19 @@ __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const Ma
             if (slot1 >= 0) inl += accumulate_point(acc, P.Rh, A1, B1, C1, v1, d1, x1);
         }
     }
+}
+
+// One work item: skipped when every cull chunk it spans is dead (no point of it
+// can find a voxel), otherwise all of its points.
+template <int PTS>
+__device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
+                                                    const WorkItem &w, int lane, float acc[kNT], int &inl)
+{
+    if (w.count <= 0) return;
+    const int c0 = (int)(w.start >> F.cshift), c1 = (int)((w.start + w.count - 1) >> F.cshift);
+    const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
+    if ((P.cmask & span) == 0u) return;
+    linearize_points<PTS>(P, m, F, w, lane, acc, inl);
 }
 
 template <int BLOCK, int MINB, int PTS>
@@ -633,10 +711,17 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
 }  // namespace
 
 void launch_prepare_factors(const int32_t *factor_idx, int n_f, const double *poses, const MapDesc *maps,
-                            const FrameDesc *frames, PoseParam *out, cudaStream_t st)
+                            const FrameDesc *frames, int cull, PoseParam *out, cudaStream_t st)
 {
     if (n_f <= 0) return;
-    k_prepare_factors<<<(n_f + 127) / 128, 128, 0, st>>>(factor_idx, n_f, poses, maps, frames, out);
+    k_prepare_factors<<<(n_f + 127) / 128, 128, 0, st>>>(factor_idx, n_f, poses, maps, frames, cull, out);
+}
+
+void launch_prepare_list(const double *T, const int32_t *map_idx, const int32_t *frame_idx, int n,
+                         const MapDesc *maps, const FrameDesc *frames, int cull, PoseParam *out, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_prepare_list<<<(n + 127) / 128, 128, 0, st>>>(T, map_idx, frame_idx, n, maps, frames, cull, out);
 }
 
 void launch_prepare_given(const double *T, int map, int frame, const MapDesc *maps, const FrameDesc *frames,

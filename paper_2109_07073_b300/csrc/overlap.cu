@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
     __shared__ MapDesc sM;
     __shared__ int s_kb[6], s_lg, s_smem;   // voxel box, compact table size, staged?
     __shared__ const float4 *s_pa[kSlice];
-    __shared__ int s_n[kSlice];
+    __shared__ int s_n[kSlice], s_csh[kSlice], s_nlive[kSlice];
+    __shared__ unsigned char s_live[kSlice][kMaxCullChunks];   // live cull chunks of each source, in order
     const int lane = threadIdx.x & 31;
     const int n_slices = (n_src + kSlice - 1) / kSlice;
     const int64_t total = (int64_t)n_slices * n_tgt;
@@ -142,10 +143,15 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
                 const uint32_t *src = (const uint32_t *)(pairs + (int64_t)(s0 + wib) * n_tgt + t);
                 uint32_t *dst = (uint32_t *)(sP + wib);
                 for (int j = lane; j < PW; j += 32) dst[j] = __ldg(src + j);
+                const PoseParam &Pg = pairs[(int64_t)(s0 + wib) * n_tgt + t];
+                const FrameDesc &F = frames[__ldg((const int *)&Pg.frame)];
+                const uint32_t cm = __ldg((const unsigned int *)&Pg.cmask);
+                if ((cm >> lane) & 1u) s_live[wib][__popc(cm & ((1u << lane) - 1u))] = (unsigned char)lane;
                 if (lane == 0) {
-                    const FrameDesc &F = frames[__ldg((const int *)&pairs[(int64_t)(s0 + wib) * n_tgt + t].frame)];
                     s_pa[wib] = F.pa;
                     s_n[wib] = (int)F.n;
+                    s_csh[wib] = F.cshift;
+                    s_nlive[wib] = __popc(cm);
                 }
             }
         }
@@ -170,42 +176,87 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
             const PoseParam &P = sP[si];
             if (P.cull) continue;                       // uniform across the block
             const float4 *__restrict__ pa = s_pa[si];
-            const int n = s_n[si];
+            const int n = s_n[si], csh = s_csh[si];
+            const int nv = s_nlive[si] << csh;          // points of the live chunks, end to end
+            const unsigned char *live = s_live[si];
             unsigned int hits = 0;
-            for (int base = 0; base < n; base += kOvBlock * kPPT) {
+            for (int base = 0; base < nv; base += kOvBlock * kPPT) {
                 float px[kPPT], py[kPPT], pz[kPPT];
                 bool have[kPPT];
 #pragma unroll
                 for (int j = 0; j < kPPT; ++j) {
-                    const int i = base + j * kOvBlock + threadIdx.x;
+                    const int vi = base + j * kOvBlock + threadIdx.x;
+                    const int i = vi < nv ? ((int)live[vi >> csh] << csh) + (vi & ((1 << csh) - 1)) : n;
                     have[j] = i < n;
                     const float4 A = have[j] ? __ldg(pa + i) : make_float4(0.f, 0.f, 0.f, 0.f);
                     px[j] = A.x; py[j] = A.y; pz[j] = A.z;
                 }
+                if (smem) {
+                    // keys of all points first, then all first probes, then the rare chains
+                    uint32_t ck[kPPT], slot[kPPT];
+                    int state[kPPT];                    // 0 no, 1 yes, 2 probing, 3 undecided floor
 #pragma unroll
-                for (int j = 0; j < kPPT; ++j) {
-                    int k[3];
-                    bool dec = true, hit = false;
-                    if (smem) {
+                    for (int j = 0; j < kPPT; ++j) {
+                        int d[3];
+                        bool dec = true;
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
                             dec &= axis_box(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.koff[a], px[j], py[j],
-                                            pz[j], m.r_h, m.r_l, m.inv_rf, k[a]);
-                        if (have[j] && dec) hit = compact_hit(s_tab, lg, ex, ey, ez, k[0], k[1], k[2]);
-                    } else {
+                                            pz[j], m.r_h, m.r_l, m.inv_rf, d[a]);
+                        const bool in = (unsigned)d[0] <= (unsigned)ex && (unsigned)d[1] <= (unsigned)ey &&
+                                        (unsigned)d[2] <= (unsigned)ez;
+                        state[j] = !have[j] ? 0 : (!dec ? 3 : (in ? 2 : 0));
+                        ck[j] = pack_compact(d[0], d[1], d[2]);
+                        slot[j] = hash_compact(ck[j], lg);
+                    }
+                    uint32_t first[kPPT];
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) first[j] = (state[j] == 2) ? s_tab[slot[j]] : kEmptyCompact;
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        if (state[j] == 2) {
+                            if (first[j] == ck[j]) state[j] = 1;
+                            else if (first[j] == kEmptyCompact) state[j] = 0;
+                            else {
+                                const uint32_t mask = (1u << lg) - 1u;
+                                uint32_t s = (slot[j] + 1) & mask;
+                                state[j] = 0;
+                                for (uint32_t q = 0; q < mask; ++q) {
+                                    const uint32_t v = s_tab[s];
+                                    if (v == ck[j]) { state[j] = 1; break; }
+                                    if (v == kEmptyCompact) break;
+                                    s = (s + 1) & mask;
+                                }
+                            }
+                        } else if (state[j] == 3) {     // face: float32-pair, then float64
+                            int k[3];
+                            state[j] = point_key_slow(P, m, px[j], py[j], pz[j], k) &&
+                                               probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0
+                                           ? 1
+                                           : 0;
+                        }
+                        hits += (state[j] == 1);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        int k[3];
+                        bool dec = true, hit = false;
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
                             dec &= axis_key_split(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.k0[a], px[j],
                                                   py[j], pz[j], m.r_h, m.r_l, m.inv_rf, k[a]);
                         if (have[j] && dec && k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN)
                             hit = probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
+                        if (have[j] && !dec)
+                            hit = point_key_slow(P, m, px[j], py[j], pz[j], k) &&
+                                  probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
+                        hits += hit;
                     }
-                    if (have[j] && !dec)                // face: float32-pair, then float64
-                        hit = point_key_slow(P, m, px[j], py[j], pz[j], k) &&
-                              probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
-                    hits += __popc(__ballot_sync(0xffffffffu, hit));
                 }
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
             if (lane == 0 && hits)
                 atomicAdd(counts + (int64_t)(s0 + si) * n_tgt + t, (unsigned long long)hits);
         }
@@ -251,7 +302,13 @@ __global__ void k_count_live(const PoseParam *__restrict__ pairs, int64_t n_pair
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_pairs; g += (int64_t)gridDim.x * blockDim.x)
         if (!pairs[g].cull) {
             ++live;
-            pts += (unsigned long long)frames[pairs[g].frame].n;
+            const FrameDesc &F = frames[pairs[g].frame];
+            const uint32_t cm = pairs[g].cmask;
+            for (int c = 0; c < F.nchunks; ++c)
+                if ((cm >> c) & 1u) {
+                    const int64_t b = (int64_t)c << F.cshift, e = min(F.n, b + ((int64_t)1 << F.cshift));
+                    pts += (unsigned long long)(e - b);
+                }
         }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

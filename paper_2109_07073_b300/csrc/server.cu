@@ -1,0 +1,541 @@
+// Serving loop: an online mapper submits linearisation (Eq. 3-6) and overlap
+// (Eq. 8) requests of uneven size; they run in continuous batches.
+//
+//   * Clients register target clouds (built into voxelmaps on the device when
+//     needed) and source frames under their own keys; the server keeps host
+//     copies and makes objects resident on demand, evicting the least recently
+//     used idle objects when the device-memory budget would be exceeded.
+//   * One scheduler thread owns the context.  Whenever a lane (a CUDA stream
+//     with its own scratch) is free and requests are pending, it admits as many
+//     pending requests as the batch limits and the budget allow and launches
+//     them as one batched linearisation plus one batched overlap list; requests
+//     that arrive meanwhile form the next batch on another lane, so their work
+//     overlaps on the device with the batch in flight.  Requests that do not
+//     fit the budget wait until objects of finished batches become evictable.
+//   * A host callback on the lane's stream marks the batch done; the scheduler
+//     copies each request's result out and wakes its waiter.
+// A request's result does not depend on the batch it ran in: a factor's sums
+// use fixed chunks and a fixed reduction order, and overlap counts are exact.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "vgicp.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Resident {
+    bool is_map = false;
+    std::vector<float> pts, covs;   // host copies (immutable once registered)
+    int64_t n = 0;
+    double r = 0.0;
+    int64_t handle = -1;            // device handle while resident
+    uint64_t last_use = 0;
+    int pins = 0;                   // batches in flight that use it
+};
+
+struct Pending {
+    vgicp_request req;
+    Clock::time_point t0;
+    vgicp_result res;
+    bool done = false;
+};
+
+struct LaneState {
+    cudaStream_t stream = nullptr;
+    bool busy = false;
+    std::atomic<bool> finished{false};
+    std::pair<vgicp_server *, int> cb;      // host-callback argument
+    std::vector<int64_t> lin, ovl;          // tickets of the batch
+    std::vector<int64_t> pinned;            // tagged keys pinned by the batch
+    double *dH = nullptr, *db = nullptr, *dc = nullptr;
+    int64_t *di = nullptr, *dcount = nullptr;
+    double *hH = nullptr, *hb = nullptr, *hc = nullptr;
+    int64_t *hi = nullptr, *hcount = nullptr;
+    int64_t cap = 0;
+    vgicp_status status = VGICP_OK;
+};
+
+}  // namespace
+
+struct vgicp_server {
+    vgicp_ctx *ctx = nullptr;
+    vgicp_server_options opt{};
+    std::thread thr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::unordered_map<int64_t, Resident> objs;   // tagged key -> object (references stay valid)
+    std::deque<int64_t> pending;
+    std::unordered_map<int64_t, Pending> reqs;
+    int64_t next_ticket = 1;
+    uint64_t clock = 0;
+    int nl = 2;
+    LaneState lanes[4];
+    std::vector<double> lat_ms;
+    int64_t resident_bytes = 0;
+    int64_t submitted = 0, completed = 0, batches = 0, admissions = 0, evictions = 0, batch_requests = 0;
+    std::string err;
+};
+
+namespace {
+
+inline int64_t tag(int64_t key, bool is_map) { return (int64_t)(((uint64_t)key << 1) | (is_map ? 1u : 0u)); }
+
+void CUDART_CB lane_done(void *p)
+{
+    auto *a = static_cast<std::pair<vgicp_server *, int> *>(p);
+    vgicp_server *s = a->first;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->lanes[a->second].finished.store(true);
+    }
+    s->cv_work.notify_all();
+}
+
+// Release the least recently used idle resident object (scheduler thread).
+bool evict_one(vgicp_server *s)
+{
+    Resident *best = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto &kv : s->objs) {
+            Resident &o = kv.second;
+            if (o.handle >= 0 && o.pins == 0 && (!best || o.last_use < best->last_use)) best = &o;
+        }
+        if (!best) return false;
+        ++s->evictions;
+    }
+    vgicp_release(s->ctx, best->handle);
+    best->handle = -1;
+    return true;
+}
+
+// Make an object resident (scheduler thread).  VGICP_ERR_BUDGET when it cannot
+// fit even with every idle object released.
+vgicp_status admit(vgicp_server *s, Resident &o)
+{
+    if (o.handle >= 0) return VGICP_OK;
+    for (;;) {
+        vgicp_status st;
+        int64_t h = -1;
+        if (o.is_map) {
+            vgicp_frame_t fr;
+            st = vgicp_add_frame(s->ctx, o.pts.data(), o.covs.data(), o.n, VGICP_MEM_HOST, &fr);
+            if (st == VGICP_OK) {
+                st = vgicp_build_voxelmaps(s->ctx, &fr, 1, o.r, &h);
+                vgicp_release(s->ctx, fr);
+            }
+        } else {
+            st = vgicp_add_frame(s->ctx, o.pts.data(), o.covs.data(), o.n, VGICP_MEM_HOST, &h);
+        }
+        if (st == VGICP_OK) {
+            o.handle = h;
+            std::lock_guard<std::mutex> lk(s->mu);
+            ++s->admissions;
+            return VGICP_OK;
+        }
+        if (st != VGICP_ERR_BUDGET) return st;
+        if (!evict_one(s)) return VGICP_ERR_BUDGET;
+    }
+}
+
+vgicp_status ensure_lane_buffers(LaneState &L, int64_t n)
+{
+    if (n <= L.cap) return VGICP_OK;
+    const int64_t cap = std::max<int64_t>(n, L.cap * 2);
+    cudaFree(L.dH); cudaFree(L.db); cudaFree(L.dc); cudaFree(L.di); cudaFree(L.dcount);
+    cudaFreeHost(L.hH); cudaFreeHost(L.hb); cudaFreeHost(L.hc); cudaFreeHost(L.hi); cudaFreeHost(L.hcount);
+    L.dH = L.db = L.dc = L.hH = L.hb = L.hc = nullptr;
+    L.di = L.dcount = L.hi = L.hcount = nullptr;
+    L.cap = 0;
+    if (cudaMalloc(&L.dH, cap * 144 * 8) || cudaMalloc(&L.db, cap * 12 * 8) || cudaMalloc(&L.dc, cap * 8) ||
+        cudaMalloc(&L.di, cap * 8) || cudaMalloc(&L.dcount, cap * 8) || cudaMallocHost(&L.hH, cap * 144 * 8) ||
+        cudaMallocHost(&L.hb, cap * 12 * 8) || cudaMallocHost(&L.hc, cap * 8) || cudaMallocHost(&L.hi, cap * 8) ||
+        cudaMallocHost(&L.hcount, cap * 8))
+        return VGICP_ERR_OOM;
+    L.cap = cap;
+    return VGICP_OK;
+}
+
+void complete(vgicp_server *s, int64_t t, vgicp_status st)   // mutex held
+{
+    Pending &p = s->reqs[t];
+    p.res.status = st;
+    p.res.kind = p.req.kind;
+    p.res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - p.t0).count();
+    p.done = true;
+}
+
+// Admit and launch one batch on lane li (scheduler thread, mutex not held).
+// Returns the tickets deferred for lack of memory.
+std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int64_t> &tickets)
+{
+    LaneState &L = s->lanes[li];
+    L.lin.clear();
+    L.ovl.clear();
+    L.pinned.clear();
+    std::vector<int64_t> deferred;
+    std::vector<vgicp_factor> fac;
+    std::vector<double> poses(12, 0.0);
+    poses[0] = poses[5] = poses[10] = 1.0;               // pose 0: identity, so T_BA = T exactly
+    std::vector<vgicp_frame_t> osrc;
+    std::vector<vgicp_map_t> otgt;
+    std::vector<double> oT;
+    vgicp_set_lane(s->ctx, li, L.stream);
+    for (int64_t t : tickets) {
+        vgicp_request r;
+        Resident *m, *f;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            r = s->reqs[t].req;
+            m = &s->objs[tag(r.target, true)];
+            f = &s->objs[tag(r.source, false)];
+        }
+        vgicp_status st = admit(s, *m);
+        if (st == VGICP_OK) {
+            { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
+            st = admit(s, *f);
+            std::lock_guard<std::mutex> lk(s->mu);
+            m->pins--;
+        }
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (st == VGICP_ERR_BUDGET) {
+            deferred.push_back(t);
+            continue;
+        }
+        if (st != VGICP_OK) {
+            complete(s, t, st);
+            continue;
+        }
+        m->pins++;
+        f->pins++;
+        m->last_use = f->last_use = ++s->clock;
+        L.pinned.push_back(tag(r.target, true));
+        L.pinned.push_back(tag(r.source, false));
+        if (r.kind == VGICP_REQ_LINEARIZE) {
+            vgicp_factor x;
+            x.target = m->handle;
+            x.source = f->handle;
+            x.target_pose = 0;
+            x.source_pose = (int32_t)(poses.size() / 12);
+            poses.insert(poses.end(), r.T_target_source, r.T_target_source + 12);
+            fac.push_back(x);
+            L.lin.push_back(t);
+        } else {
+            osrc.push_back(f->handle);
+            otgt.push_back(m->handle);
+            oT.insert(oT.end(), r.T_target_source, r.T_target_source + 12);
+            L.ovl.push_back(t);
+        }
+    }
+    const size_t nf = fac.size(), no = osrc.size();
+    vgicp_status st = ensure_lane_buffers(L, (int64_t)std::max<size_t>(std::max(nf, no), 1));
+    if (st == VGICP_OK && nf)
+        st = vgicp_linearize(s->ctx, fac.data(), (int64_t)nf, poses.data(), (int64_t)(poses.size() / 12), L.dH, L.db,
+                             L.dc, L.di, VGICP_MEM_DEVICE);
+    if (st == VGICP_OK && no)
+        st = vgicp_overlap_pairs(s->ctx, osrc.data(), otgt.data(), (int64_t)no, oT.data(), L.dcount,
+                                 VGICP_MEM_DEVICE);
+    if (st == VGICP_OK && nf) {
+        cudaMemcpyAsync(L.hH, L.dH, nf * 144 * 8, cudaMemcpyDeviceToHost, L.stream);
+        cudaMemcpyAsync(L.hb, L.db, nf * 12 * 8, cudaMemcpyDeviceToHost, L.stream);
+        cudaMemcpyAsync(L.hc, L.dc, nf * 8, cudaMemcpyDeviceToHost, L.stream);
+        cudaMemcpyAsync(L.hi, L.di, nf * 8, cudaMemcpyDeviceToHost, L.stream);
+    }
+    if (st == VGICP_OK && no) cudaMemcpyAsync(L.hcount, L.dcount, no * 8, cudaMemcpyDeviceToHost, L.stream);
+    L.status = st;
+    L.finished.store(false);
+    if (nf + no && cudaLaunchHostFunc(L.stream, lane_done, &L.cb) != cudaSuccess) {
+        cudaStreamSynchronize(L.stream);
+        L.finished.store(true);
+    }
+    int64_t bytes = 0;
+    vgicp_memory_in_use(s->ctx, &bytes);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->resident_bytes = bytes;
+    return deferred;
+}
+
+void finish_batch(vgicp_server *s, int li)   // mutex held
+{
+    LaneState &L = s->lanes[li];
+    const auto now = Clock::now();
+    for (size_t i = 0; i < L.lin.size(); ++i) {
+        Pending &p = s->reqs[L.lin[i]];
+        p.res.status = L.status;
+        p.res.kind = VGICP_REQ_LINEARIZE;
+        if (L.status == VGICP_OK) {
+            std::memcpy(p.res.H, L.hH + 144 * i, 144 * 8);
+            std::memcpy(p.res.b, L.hb + 12 * i, 12 * 8);
+            p.res.cost = L.hc[i];
+            p.res.count = L.hi[i];
+        }
+        p.res.latency_ms = std::chrono::duration<double, std::milli>(now - p.t0).count();
+        p.done = true;
+        s->lat_ms.push_back(p.res.latency_ms);
+    }
+    for (size_t i = 0; i < L.ovl.size(); ++i) {
+        Pending &p = s->reqs[L.ovl[i]];
+        p.res.kind = VGICP_REQ_OVERLAP;
+        p.res.status = L.status;
+        if (L.status == VGICP_OK) {
+            const int64_t n = s->objs[tag(p.req.source, false)].n;
+            p.res.count = L.hcount[i];
+            if (n == 0) p.res.status = VGICP_ERR_EMPTY;
+            else p.res.fraction = (double)L.hcount[i] / (double)n;
+        }
+        p.res.latency_ms = std::chrono::duration<double, std::milli>(now - p.t0).count();
+        p.done = true;
+        s->lat_ms.push_back(p.res.latency_ms);
+    }
+    for (int64_t k : L.pinned) s->objs[k].pins--;
+    s->completed += (int64_t)(L.lin.size() + L.ovl.size());
+    ++s->batches;
+    s->batch_requests += (int64_t)(L.lin.size() + L.ovl.size());
+    L.busy = false;
+}
+
+void scheduler(vgicp_server *s)
+{
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        bool harvested = false;
+        for (int li = 0; li < s->nl; ++li)
+            if (s->lanes[li].busy && s->lanes[li].finished.load()) {
+                finish_batch(s, li);
+                harvested = true;
+            }
+        if (harvested) s->cv_done.notify_all();
+        bool any_busy = false;
+        int free_lane = -1;
+        for (int li = 0; li < s->nl; ++li) {
+            any_busy = any_busy || s->lanes[li].busy;
+            if (!s->lanes[li].busy && free_lane < 0) free_lane = li;
+        }
+        if (s->stop && !any_busy) return;
+        if (!s->stop && free_lane >= 0 && !s->pending.empty()) {
+            std::vector<int64_t> take;
+            int64_t pts = 0;
+            while (!s->pending.empty() && (int)take.size() < s->opt.max_batch_requests) {
+                const int64_t t = s->pending.front();
+                const int64_t n = s->objs[tag(s->reqs[t].req.source, false)].n;
+                if (!take.empty() && pts + n > s->opt.max_batch_points) break;
+                pts += n;
+                take.push_back(t);
+                s->pending.pop_front();
+            }
+            LaneState &L = s->lanes[free_lane];
+            L.busy = true;
+            lk.unlock();
+            std::vector<int64_t> deferred = launch_batch(s, free_lane, take);
+            lk.lock();
+            for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) s->pending.push_front(*it);
+            if (L.lin.empty() && L.ovl.empty()) {
+                L.busy = false;
+                bool other = false;
+                for (int li = 0; li < s->nl; ++li) other = other || s->lanes[li].busy;
+                if (!other && !deferred.empty()) {
+                    // nothing in flight and still no room: the head request can never fit
+                    const int64_t t = s->pending.front();
+                    s->pending.pop_front();
+                    complete(s, t, VGICP_ERR_BUDGET);
+                    s->cv_done.notify_all();
+                }
+                if (other) s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            }
+            s->cv_done.notify_all();
+            continue;
+        }
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+    }
+}
+
+vgicp_status put(vgicp_server *s, int64_t key, bool is_map, const float *pts, const float *covs, int64_t n, double r)
+{
+    if (!s) return VGICP_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!pts || !covs)) || key < 0 || key >= ((int64_t)1 << 62)) return VGICP_ERR_INVALID_ARG;
+    if (is_map && !(r > 0.0 && r < 1e30)) return VGICP_ERR_INVALID_ARG;
+    Resident o;
+    o.is_map = is_map;
+    o.pts.assign(pts, pts + 3 * n);
+    o.covs.assign(covs, covs + 6 * n);
+    o.n = n;
+    o.r = r;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int64_t t = tag(key, is_map);
+    if (s->objs.count(t)) {
+        s->err = "key already registered";
+        return VGICP_ERR_INVALID_ARG;
+    }
+    s->objs.emplace(t, std::move(o));
+    return VGICP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vgicp_status vgicp_server_create(vgicp_server **out, const vgicp_server_options *opt, const vgicp_options *kopt)
+{
+    if (!out) return VGICP_ERR_INVALID_ARG;
+    *out = nullptr;
+    vgicp_server *s = new vgicp_server();
+    if (opt) s->opt = *opt;
+    if (s->opt.max_batch_requests <= 0) s->opt.max_batch_requests = 4096;
+    if (s->opt.max_batch_points <= 0) s->opt.max_batch_points = (int64_t)1 << 27;
+    if (s->opt.lanes <= 0) s->opt.lanes = 2;
+    if (s->opt.lanes > 4 || s->opt.hbm_budget_bytes < 0) {
+        delete s;
+        return VGICP_ERR_INVALID_ARG;
+    }
+    s->nl = s->opt.lanes;
+    vgicp_options ko;
+    vgicp_options_default(&ko);
+    if (kopt) ko = *kopt;
+    ko.precision = VGICP_PREC_F32;
+    ko.hbm_budget_bytes = s->opt.hbm_budget_bytes;
+    vgicp_status st = vgicp_create(&s->ctx, &ko, nullptr);
+    if (st != VGICP_OK) {
+        delete s;
+        return st;
+    }
+    for (int li = 0; li < s->nl; ++li) {
+        s->lanes[li].cb = {s, li};
+        if (cudaStreamCreateWithFlags(&s->lanes[li].stream, cudaStreamNonBlocking) != cudaSuccess) {
+            vgicp_destroy(s->ctx);
+            delete s;
+            return VGICP_ERR_CUDA;
+        }
+    }
+    s->thr = std::thread(scheduler, s);
+    *out = s;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_server_destroy(vgicp_server *s)
+{
+    if (!s) return VGICP_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    s->thr.join();
+    for (int li = 0; li < s->nl; ++li) cudaStreamSynchronize(s->lanes[li].stream);
+    vgicp_set_lane(s->ctx, 0, nullptr);
+    vgicp_destroy(s->ctx);
+    for (int li = 0; li < s->nl; ++li) {
+        LaneState &L = s->lanes[li];
+        cudaFree(L.dH); cudaFree(L.db); cudaFree(L.dc); cudaFree(L.di); cudaFree(L.dcount);
+        cudaFreeHost(L.hH); cudaFreeHost(L.hb); cudaFreeHost(L.hc); cudaFreeHost(L.hi); cudaFreeHost(L.hcount);
+        cudaStreamDestroy(L.stream);
+    }
+    delete s;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_server_put_map(vgicp_server *s, int64_t key, const float *points, const float *covs, int64_t n,
+                                  double resolution)
+{
+    return put(s, key, true, points, covs, n, resolution);
+}
+
+vgicp_status vgicp_server_put_frame(vgicp_server *s, int64_t key, const float *points, const float *covs, int64_t n)
+{
+    return put(s, key, false, points, covs, n, 0.0);
+}
+
+vgicp_status vgicp_server_submit(vgicp_server *s, const vgicp_request *req, int64_t *ticket)
+{
+    if (!s || !req || !ticket) return VGICP_ERR_INVALID_ARG;
+    if (req->kind != VGICP_REQ_LINEARIZE && req->kind != VGICP_REQ_OVERLAP) return VGICP_ERR_INVALID_ARG;
+    for (int i = 0; i < 12; ++i)
+        if (!(req->T_target_source[i] - req->T_target_source[i] == 0.0)) return VGICP_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->objs.count(tag(req->target, true)) || !s->objs.count(tag(req->source, false))) {
+            s->err = "request names an unregistered key";
+            return VGICP_ERR_NOT_FOUND;
+        }
+        const int64_t t = s->next_ticket++;
+        Pending &p = s->reqs[t];
+        p.req = *req;
+        p.t0 = Clock::now();
+        std::memset(&p.res, 0, sizeof(p.res));
+        s->pending.push_back(t);
+        ++s->submitted;
+        *ticket = t;
+    }
+    s->cv_work.notify_all();
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_server_wait(vgicp_server *s, int64_t ticket, double timeout_s, vgicp_result *out)
+{
+    if (!s || !out) return VGICP_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return VGICP_ERR_NOT_FOUND;
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(timeout_s < 0 ? 1e9 : timeout_s));
+    while (!it->second.done) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !it->second.done)
+            return VGICP_ERR_TIMEOUT;
+        it = s->reqs.find(ticket);
+    }
+    *out = it->second.res;
+    s->reqs.erase(it);
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_server_stats(vgicp_server *s, vgicp_server_counters *out)
+{
+    if (!s || !out) return VGICP_ERR_INVALID_ARG;
+    std::vector<double> lat;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        std::memset(out, 0, sizeof(*out));
+        out->submitted = s->submitted;
+        out->completed = s->completed;
+        out->batches = s->batches;
+        out->admissions = s->admissions;
+        out->evictions = s->evictions;
+        out->mean_batch_requests = s->batches ? (double)s->batch_requests / (double)s->batches : 0.0;
+        out->resident_bytes = s->resident_bytes;
+        lat = s->lat_ms;
+    }
+    if (!lat.empty()) {
+        std::sort(lat.begin(), lat.end());
+        auto q = [&](double f) { return lat[std::min(lat.size() - 1, (size_t)(f * (double)(lat.size() - 1) + 0.5))]; };
+        out->p50_ms = q(0.50);
+        out->p99_ms = q(0.99);
+        out->max_ms = lat.back();
+    }
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_server_reset_stats(vgicp_server *s)
+{
+    if (!s) return VGICP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->lat_ms.clear();
+    s->submitted = s->completed = s->batches = s->admissions = s->evictions = s->batch_requests = 0;
+    return VGICP_OK;
+}
+
+const char *vgicp_server_last_error(const vgicp_server *s) { return s ? s->err.c_str() : "null server"; }
+
+}  // extern "C"

@@ -54,7 +54,12 @@ struct FrameDesc {
     const float *pc;
     int64_t n;
     const float *stats;  // device: kStat* entries below
+    const float *cbox;   // device: per cull chunk min xyz, max xyz (6 floats; at most kMaxCullChunks)
+    int32_t cshift;      // cull chunk = 2^cshift consecutive points (>= 10, so <= 32 chunks)
+    int32_t nchunks;
 };
+
+constexpr int kMaxCullChunks = 32;
 
 // Frame statistics, over the points with finite coordinates.
 enum {
@@ -94,6 +99,8 @@ struct __align__(16) PoseParam {
     float ffup[3];
     int32_t cull;        // 1: the pair provably has no correspondence
     int32_t koff[3];     // target voxel-box minimum minus k0: compact coordinate = floor(x'/r) - koff
+    uint32_t cmask;      // bit c: cull chunk c of the source may have correspondences
+    int32_t pad2[3];
 };
 
 // ---------------------------------------------------------------- keys ----

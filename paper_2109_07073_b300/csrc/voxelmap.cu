@@ -68,6 +68,42 @@ __global__ void k_frame_pack(const float *__restrict__ pts, const float *__restr
     }
 }
 
+// Bounding box of each cull chunk of a frame (finite points only; an empty
+// chunk gets min > max).  One block per chunk.
+__global__ void k_chunk_boxes(const float4 *__restrict__ pa, int64_t n, int shift, float *__restrict__ cbox)
+{
+    const int c = blockIdx.x;
+    const int64_t b = (int64_t)c << shift, e = min(n, b + ((int64_t)1 << shift));
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const float4 p = pa[i];
+        if (isfinite(p.x) && isfinite(p.y) && isfinite(p.z)) {
+            mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+            mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+        }
+    }
+    __shared__ float s[6][8];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[j] = fminf(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
+            mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
+        }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { s[j][w] = mn[j]; s[3 + j][w] = mx[j]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float v = s[threadIdx.x][0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+            v = threadIdx.x < 3 ? fminf(v, s[threadIdx.x][q]) : fmaxf(v, s[threadIdx.x][q]);
+        cbox[6 * c + threadIdx.x] = v;
+    }
+}
+
 __device__ __forceinline__ int find_unit(const int64_t *prefix, int n_units, int64_t g)
 {
     int lo = 0, hi = n_units - 1;
@@ -304,6 +340,12 @@ void launch_frame_pack(const float *points, const float *covs, int64_t n, float4
     int grid = (int)((n + block - 1) / block);
     if (grid > 148 * 16) grid = 148 * 16;
     k_frame_pack<<<grid, block, 0, st>>>(points, covs, n, pa, pb, pc, (unsigned int *)stats);
+}
+
+void launch_chunk_boxes(const float4 *pa, int64_t n, int shift, int nchunks, float *cbox, cudaStream_t st)
+{
+    if (nchunks <= 0) return;
+    k_chunk_boxes<<<nchunks, 256, 0, st>>>(pa, n, shift, cbox);
 }
 
 void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const BuildUnit *units, int n_units,

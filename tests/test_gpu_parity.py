@@ -316,6 +316,32 @@ def test_linearize_variants_agree(ctx, variant):
         ctx.release(h)
 
 
+def test_linearize_chunk_culling_is_exact(ctx, loop_frames):
+    """Skipping source chunks whose moved box misses the target's voxels changes no sum."""
+    g, ids, pts, covs = loop_frames
+    fr = [ctx.add_frame(p, c) for p, c in zip(pts, covs)]
+    maps = ctx.build_voxelmaps(fr, g.resolution)
+    P = g.poses[ids]
+    tg = [0, 0, 1, 2, 3, 4, 5, 6, 0]
+    sc = [1, 4, 4, 3, 0, 2, 6, 5, 7]
+    f = vg.make_factors(maps[tg], np.array(fr)[sc], tg, sc)
+    out = {}
+    for cull in (0, 1):
+        ctx.set_options(linearize_cull=cull)
+        out[cull] = ctx.linearize(f, P)
+    ctx.set_options(linearize_cull=1)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    vms = {t: oracle.voxelmap(pts[t], covs[t], g.resolution) for t in set(tg)}
+    for k, (t, s) in enumerate(zip(tg, sc)):
+        L = oracle.linearize(vms[t], pts[s], covs[s], oracle.relative_pose(P[t], P[s]))
+        assert out[1][3][k] == L.inliers
+        if L.inliers:
+            assert err_metric(out[1][0][k], L.H, L.SH) <= TOL[vg.VGICP_PREC_F32]
+    for h in list(maps) + fr:
+        ctx.release(int(h))
+
+
 def test_autotune_keeps_results(ctx, single):
     w, cb, ca = single
     hm = ctx.build_voxelmap(w.points_target, cb, w.resolution)
@@ -331,6 +357,15 @@ def test_autotune_keeps_results(ctx, single):
     ctx.set_options(linearize_variant=0, chunk_points=2048)
     ctx.release(hm)
     ctx.release(hf)
+
+
+def test_knn_covariances_full_frame(ctx, loop_frames):
+    """Grid kNN on a 20,000-point LiDAR frame: the same covariances as the oracle."""
+    g, ids, pts, covs = loop_frames
+    for p, c in zip(pts[:2], covs[:2]):
+        assert np.max(np.abs(ctx.estimate_covariances(p, 10, 1e-3) - c)) <= 2e-6
+    far = np.concatenate([pts[0][:3000], np.array([[900.0, 900.0, 900.0]], np.float32)])   # an isolated point
+    assert np.max(np.abs(ctx.estimate_covariances(far, 10, 1e-3) - oracle.covariances(far))) <= 2e-6
 
 
 def test_kernel_launch_counter_moves(ctx, single):

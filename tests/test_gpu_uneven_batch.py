@@ -1,0 +1,114 @@
+"""Batched linearisation of 10,000 factors of uneven size at full scale.
+
+Source sizes are log-uniform in 2,000..60,000 points; targets come from a pool
+of 1,000 voxelmaps at resolutions {0.5, 1, 2} m; every factor runs in one
+persistent launch (autotuned).  Sampled factors are recomputed one by one by
+the FP64 oracle (their frames' covariances computed by the oracle too), for
+the batched float32 path and the plain float64 path.  Throughput and the
+per-path error statistics (max / p99 / median of err(H), err(b), err(cost))
+go to gpurun_out/uneven_batch_report.json when that folder exists.
+"""
+import json
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import datagen as dg
+import oracle
+import paper_2109_07073_b300 as vg
+from util import err_metric
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_uneven_batch_sampled_parity():
+    import torch
+    cores = os.cpu_count() or 1
+    w = dg.uneven_workload(workers=min(16, cores))
+    n_f = len(w.factor_idx)
+    rng = dg.Stream(3030)
+    pick = rng.choose(n_f, 24)
+    need = sorted(set(int(x) for x in w.factor_frame[pick]) | set(int(x) for x in w.factor_target[pick]))
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        ocov = dict(zip(need, ex.map(lambda i: oracle.covariances(w.frames[i]), need)))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    with vg.Context(stream=stream) as ctx:
+        dev_pts, dev_cov = [], []
+        for i, f in enumerate(w.frames):
+            p = torch.from_numpy(f).cuda()
+            dev_pts.append(p)
+            dev_cov.append(torch.from_numpy(ocov[i]).cuda() if i in ocov else ctx.estimate_covariances(p, 10, 1e-3))
+        maps = np.full(len(w.frames), -1, np.int64)
+        for r in sorted(set(w.target_res.tolist())):
+            ts = np.nonzero(w.target_res == r)[0]
+            fr = [ctx.add_frame(dev_pts[t][torch.from_numpy(w.target_idx[t]).cuda()],
+                                dev_cov[t][torch.from_numpy(w.target_idx[t]).cuda()]) for t in ts]
+            maps[ts] = ctx.build_voxelmaps(fr, float(r))
+            for h in fr:
+                ctx.release(h)
+        srcs = []
+        for f in range(n_f):
+            j = int(w.factor_frame[f])
+            ix = torch.from_numpy(w.factor_idx[f]).cuda()
+            srcs.append(ctx.add_frame(dev_pts[j][ix], dev_cov[j][ix]))
+        factors = vg.make_factors(maps[w.factor_target], srcs, w.factor_target, w.factor_frame)
+        n_points = int(sum(len(i) for i in w.factor_idx))
+        best, tuned_ms = ctx.autotune(factors, w.poses, reps=2)
+        out = (torch.zeros((n_f, 12, 12), dtype=torch.float64, device="cuda"),
+               torch.zeros((n_f, 12), dtype=torch.float64, device="cuda"),
+               torch.zeros(n_f, dtype=torch.float64, device="cuda"), torch.zeros(n_f, dtype=torch.int64, device="cuda"))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.linearize(factors, w.poses, out=out)
+        e0.record(stream)
+        for _ in range(3):
+            ctx.linearize(factors, w.poses, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        H, b, cost, inl = (x.cpu().numpy() for x in out)
+        ctx.set_options(precision=vg.VGICP_PREC_F64)
+        H64, b64, c64, i64 = ctx.linearize(factors[pick], w.poses)
+        ctx.set_options(precision=vg.VGICP_PREC_F32)
+
+        def ref(k):
+            f = pick[k]
+            t, j = int(w.factor_target[f]), int(w.factor_frame[f])
+            ti = w.target_idx[t]
+            vm = oracle.voxelmap(w.frames[t][ti], ocov[t][ti], float(w.target_res[t]))
+            ix = w.factor_idx[f]
+            return oracle.linearize(vm, w.frames[j][ix], ocov[j][ix], oracle.relative_pose(w.poses[t], w.poses[j]))
+        with ThreadPoolExecutor(max_workers=cores) as ex:
+            refs = list(ex.map(ref, range(len(pick))))
+        report = {"factors": n_f, "points": n_points, "batched_f32_ms": ms,
+                  "point_correspondences_per_s": n_points / (ms / 1e3), "factors_per_s": n_f / (ms / 1e3),
+                  "autotuned": {"variant": int(best.linearize_variant), "chunk_points": int(best.chunk_points)},
+                  "f32": {"H": [], "b": [], "cost": []}, "f64": {"H": [], "b": [], "cost": []}}
+        for k, L in enumerate(refs):
+            f = pick[k]
+            assert inl[f] == L.inliers and i64[k] == L.inliers, k
+            if L.inliers == 0:
+                continue
+            e32 = (err_metric(H[f], L.H, L.SH), err_metric(b[f], L.b, L.Sb), abs(cost[f] - L.cost) / L.Scost)
+            e64 = (err_metric(H64[k], L.H, L.SH), err_metric(b64[k], L.b, L.Sb), abs(c64[k] - L.cost) / L.Scost)
+            for nm, v in zip(("H", "b", "cost"), e32):
+                report["f32"][nm].append(v)
+            for nm, v in zip(("H", "b", "cost"), e64):
+                report["f64"][nm].append(v)
+            assert max(e32) <= 1e-4, (k, e32)
+            assert max(e64) <= 1e-5, (k, e64)
+        for path in ("f32", "f64"):
+            for nm in ("H", "b", "cost"):
+                v = np.array(report[path][nm])
+                report[path][nm] = {"max": float(v.max()), "p99": float(np.percentile(v, 99)),
+                                    "median": float(np.median(v))}
+        d = os.path.join(ROOT, "gpurun_out")
+        if os.path.isdir(d):
+            with open(os.path.join(d, "uneven_batch_report.json"), "w") as fh:
+                json.dump(report, fh, indent=1)
+        for h in list(srcs) + [int(m) for m in maps if m >= 0]:
+            ctx.release(int(h))

@@ -336,6 +336,9 @@ def test_knn_grid_matches_bruteforce(cell):
     rng = dg.Stream(4)
     lat = np.floor(rng.uniform(900, 0, 6)).reshape(-1, 3).astype(np.float32)
     assert np.array_equal(oracle.knn(lat, 10, cell=cell), oracle.knn(lat, 10, brute_force=True))
+    # an isolated point far from the rest: the shell search gives up and scans
+    far = np.concatenate([w.points_target[:500], np.array([[900.0, 900.0, 900.0]], np.float32)])
+    assert np.array_equal(oracle.knn(far, 10, cell=cell), oracle.knn(far, 10, brute_force=True))
 
 
 def test_jacobi_diagonal_and_random_spectra():
