@@ -43,7 +43,7 @@ struct Plan {
     std::vector<int64_t> frame_n;
     int chunk = 0;
     int n_items = 0;
-    Buf idx, items, item_begin;
+    Buf idx, items, item_range;
 };
 
 constexpr int kMaxLanes = 4;
@@ -57,6 +57,7 @@ struct Lane {
     Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
     Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
     Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs, ws_tune, ws_knn;
+    Buf ws_fetch, ws_items;
     Plan plan;
     int64_t last_matrix_pairs = 0;   // pairs of the last overlap matrix (params kept in ws_pairs)
 };
@@ -407,6 +408,38 @@ vgicp_status read_nvox(vgicp_ctx *ctx, const Obj &o, int64_t *n)
 
 int default_chunk(const vgicp_options &o) { return o.chunk_points > 0 ? o.chunk_points : 2048; }
 
+// Work items of a factor set: each factor's points in chunks of `chunk`, the
+// chunks of one factor contiguous, and factors grouped by target voxelmap (then
+// by source frame) so that the warps running at any moment share few maps and
+// their voxel records stay in L2.  range[2 f], range[2 f + 1] delimit factor f's
+// items.  The order changes no sum: each factor's chunks are reduced in chunk
+// order whatever their position in the list.
+void build_items(const std::vector<int32_t> &idx, const std::vector<int64_t> &frame_n, int chunk,
+                 std::vector<WorkItem> &items, std::vector<int32_t> &range)
+{
+    const int64_t n_f = (int64_t)frame_n.size();
+    std::vector<int32_t> order((size_t)n_f);
+    for (int64_t i = 0; i < n_f; ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (idx[4 * a] != idx[4 * b]) return idx[4 * a] < idx[4 * b];
+        return idx[4 * a + 1] < idx[4 * b + 1];
+    });
+    items.clear();
+    range.assign((size_t)n_f * 2, 0);
+    for (int32_t i : order) {
+        const int64_t n = frame_n[i];
+        range[2 * i] = (int32_t)items.size();
+        for (int64_t s = 0; s < n; s += chunk) {
+            WorkItem w;
+            w.unit = i;
+            w.start = s;
+            w.count = (int32_t)std::min<int64_t>(chunk, n - s);
+            items.push_back(w);
+        }
+        range[2 * i + 1] = (int32_t)items.size();
+    }
+}
+
 // Work list for a factor set (cached while the set and the chunk size stay the same).
 vgicp_status get_plan(vgicp_ctx *ctx, const vgicp_factor *f, int64_t n_f, const std::vector<int32_t> &idx)
 {
@@ -422,25 +455,14 @@ vgicp_status get_plan(vgicp_ctx *ctx, const vgicp_factor *f, int64_t n_f, const 
         // validated by the caller, so the cached copy is still exact
         return VGICP_OK;
     }
-    std::vector<WorkItem> items;
-    std::vector<int32_t> begin(n_f + 1, 0);
     P.frame_n.resize(n_f);
-    for (int64_t i = 0; i < n_f; ++i) {
-        const int64_t n = ctx->objs[idx[4 * i + 1]].n;
-        P.frame_n[i] = n;
-        begin[i] = (int32_t)items.size();
-        for (int64_t s = 0; s < n; s += chunk) {
-            WorkItem w;
-            w.unit = (int32_t)i;
-            w.start = s;
-            w.count = (int32_t)std::min<int64_t>(chunk, n - s);
-            items.push_back(w);
-        }
-    }
-    begin[n_f] = (int32_t)items.size();
+    for (int64_t i = 0; i < n_f; ++i) P.frame_n[i] = ctx->objs[idx[4 * i + 1]].n;
+    std::vector<WorkItem> items;
+    std::vector<int32_t> range;
+    build_items(idx, P.frame_n, chunk, items, range);
     TRY(upload(ctx, P.idx, idx.data(), idx.size()));
     TRY(upload(ctx, P.items, items.data(), items.size()));
-    TRY(upload(ctx, P.item_begin, begin.data(), begin.size()));
+    TRY(upload(ctx, P.item_range, range.data(), range.size()));
     P.key.assign(f, f + n_f);
     P.chunk = chunk;
     P.n_items = (int)items.size();
@@ -472,8 +494,8 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "precision must be VGICP_PREC_F32 or VGICP_PREC_F64");
     if (o->chunk_points < 0 || (o->chunk_points % 32) != 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "chunk_points must be a non-negative multiple of 32");
-    if (o->linearize_variant < 0 || o->linearize_variant > 2)
-        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_variant must be 0, 1 or 2");
+    if (o->linearize_variant < 0 || o->linearize_variant > 3)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_variant must be 0, 1, 2 or 3");
     if (o->blocks_per_sm < 0 || o->hbm_budget_bytes < 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
     if (o->overlap_cull != 0 && o->overlap_cull != 1)
@@ -533,7 +555,8 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
                        &LN.ws_bprefix, &LN.ws_slot_of_point, &LN.ws_acc, &LN.ws_vid_of_slot,
                        &LN.ws_slot_of_vid, &LN.ws_pairs, &LN.ws_fidx, &LN.ws_midx, &LN.ws_chunks,
                        &LN.ws_export_keys, &LN.ws_export_rec, &LN.ws_counter, &LN.ws_descs, &LN.ws_tune,
-                       &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_begin};
+                       &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_range, &LN.ws_fetch,
+                       &LN.ws_items};
         for (Buf *b : bufs) free_buf(ctx, *b);
         const cudaError_t e2 = cudaStreamSynchronize(LN.stream);
         if (e == cudaSuccess) e = e2;
@@ -765,10 +788,12 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
     } else {
         TRY(ensure(ctx, LN.ws_partials, (size_t)std::max(1, P.n_items) * 28 * 8));
         TRY(ensure(ctx, LN.ws_inl, (size_t)std::max(1, P.n_items) * 8));
+        TRY(ensure(ctx, LN.ws_fetch, 16));
         launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
-                             (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, ctx->opt.linearize_variant,
+                             (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p,
+                             ctx->opt.linearize_variant,
                              ctx->opt.blocks_per_sm, ctx->num_sms, LN.stream);
-        launch_reduce_finalize(d_params, (const int32_t *)P.item_begin.p, (int)n_f, (const double *)LN.ws_partials.p,
+        launch_reduce_finalize(d_params, (const int32_t *)P.item_range.p, (int)n_f, (const double *)LN.ws_partials.p,
                                (const int64_t *)LN.ws_inl.p, dH, db, dc, di, LN.stream);
         ctx->launches += (P.n_items > 0) + 1;
         CHECK_LAUNCH();
@@ -801,7 +826,7 @@ struct vgicp_plan {
     std::vector<int64_t> frame_n;
     int64_t n_f = 0, n_poses = 0;
     int n_items = 0;
-    Buf d_idx, d_items, d_begin, d_poses, d_params, d_partials, d_inl, d_out;
+    Buf d_idx, d_items, d_range, d_poses, d_params, d_partials, d_inl, d_out, d_fetch;
     double *h_poses = nullptr;           // pinned staging read by the graph's upload node
     cudaStream_t cap = nullptr;          // capture stream (nothing runs on it)
     cudaGraphExec_t exec = nullptr;
@@ -849,21 +874,11 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
     }
     if (!same_work) {
         std::vector<WorkItem> items;
-        std::vector<int32_t> begin((size_t)n_f + 1, 0);
-        for (int64_t i = 0; i < n_f; ++i) {
-            begin[i] = (int32_t)items.size();
-            for (int64_t s = 0; s < fn[i]; s += chunk) {
-                WorkItem w;
-                w.unit = (int32_t)i;
-                w.start = s;
-                w.count = (int32_t)std::min<int64_t>(chunk, fn[i] - s);
-                items.push_back(w);
-            }
-        }
-        begin[n_f] = (int32_t)items.size();
+        std::vector<int32_t> range;
+        build_items(idx, fn, chunk, items, range);
         TRY(upload(ctx, P->d_idx, idx.data(), idx.size()));
-        TRY(upload(ctx, P->d_items, items.data(), std::max<size_t>(1, items.size())));
-        TRY(upload(ctx, P->d_begin, begin.data(), begin.size()));
+        TRY(upload(ctx, P->d_items, items.data(), items.size()));
+        TRY(upload(ctx, P->d_range, range.data(), range.size()));
         TRY(ensure(ctx, P->d_partials, std::max<size_t>(1, items.size()) * 28 * 8));
         TRY(ensure(ctx, P->d_inl, std::max<size_t>(1, items.size()) * 8));
         CU(cudaStreamSynchronize(LN.stream));   // buffers ready before the graph can run on any stream
@@ -884,9 +899,10 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
     launch_prepare_factors((const int32_t *)P->d_idx.p, (int)n_f, (const double *)P->d_poses.p, ctx->d_maps,
                            ctx->d_frames, ctx->opt.linearize_cull, params, P->cap);
     launch_linearize_f32(params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P->d_items.p, P->n_items,
-                         (double *)P->d_partials.p, (int64_t *)P->d_inl.p, ctx->opt.linearize_variant,
+                         (double *)P->d_partials.p, (int64_t *)P->d_inl.p, (int *)P->d_fetch.p,
+                         ctx->opt.linearize_variant,
                          ctx->opt.blocks_per_sm, ctx->num_sms, P->cap);
-    launch_reduce_finalize(params, (const int32_t *)P->d_begin.p, (int)n_f, (const double *)P->d_partials.p,
+    launch_reduce_finalize(params, (const int32_t *)P->d_range.p, (int)n_f, (const double *)P->d_partials.p,
                            (const int64_t *)P->d_inl.p, H, b, c, inl, P->cap);
     cudaGraph_t g = nullptr;
     const cudaError_t e1 = cudaStreamEndCapture(P->cap, &g);
@@ -914,8 +930,8 @@ void plan_free(vgicp_ctx *ctx, vgicp_plan *P)
 {
     if (P->in_flight) cudaEventSynchronize(P->done);
     if (P->exec) cudaGraphExecDestroy(P->exec);
-    Buf *bufs[] = {&P->d_idx, &P->d_items, &P->d_begin, &P->d_poses, &P->d_params, &P->d_partials, &P->d_inl,
-                   &P->d_out};
+    Buf *bufs[] = {&P->d_idx, &P->d_items, &P->d_range, &P->d_poses, &P->d_params, &P->d_partials, &P->d_inl,
+                   &P->d_out, &P->d_fetch};
     for (Buf *b : bufs) free_buf(ctx, *b);
     if (P->h_poses) cudaFreeHost(P->h_poses);
     if (P->done) cudaEventDestroy(P->done);
@@ -954,6 +970,7 @@ vgicp_status vgicp_plan_create(vgicp_ctx *ctx, const vgicp_factor *factors, int6
     if (st == VGICP_OK) st = ensure(ctx, P->d_poses, (size_t)std::max<int64_t>(1, n_poses) * 12 * 8);
     if (st == VGICP_OK) st = ensure(ctx, P->d_params, (size_t)std::max<int64_t>(1, n_f) * sizeof(PoseParam));
     if (st == VGICP_OK) st = ensure(ctx, P->d_out, (size_t)std::max<int64_t>(1, n_f) * (144 + 12 + 1 + 1) * 8);
+    if (st == VGICP_OK) st = ensure(ctx, P->d_fetch, 16);
     if (st == VGICP_OK && n_f > 0) st = plan_refresh(ctx, P);
     if (st != VGICP_OK) {
         plan_free(ctx, P);
@@ -1034,7 +1051,7 @@ vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     float win_ms = 1e30f;
     static const int chunks[] = {1024, 2048, 4096, 8192};
     vgicp_status st = VGICP_OK;
-    for (int variant = 0; variant <= 2 && st == VGICP_OK; ++variant)
+    for (int variant = 0; variant <= 3 && st == VGICP_OK; ++variant)
         for (int ci = 0; ci < 4 && st == VGICP_OK; ++ci) {
             ctx->opt = keep;
             ctx->opt.precision = VGICP_PREC_F32;
@@ -1215,9 +1232,10 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
         dcounts = (unsigned long long *)LN.ws_counts.p;
     }
     CU(cudaMemsetAsync(dcounts, 0, (size_t)n_pairs * 8, LN.stream));
+    TRY(ensure(ctx, LN.ws_items, overlap_matrix_scratch_bytes((int)n_src, (int)n_tgt)));
     launch_overlap_matrix((const PoseParam *)LN.ws_pairs.p, ctx->d_maps, ctx->d_frames, (int)n_src, (int)n_tgt,
-                          dcounts, ctx->num_sms, LN.stream);
-    ctx->launches += 2;
+                          dcounts, LN.ws_items.p, ctx->num_sms, LN.stream);
+    ctx->launches += 3;
     CHECK_LAUNCH();
     if (out_kind == VGICP_MEM_HOST) {
         CU(cudaMemcpyAsync(counts, dcounts, (size_t)n_pairs * 8, cudaMemcpyDeviceToHost, LN.stream));

@@ -70,12 +70,12 @@ void launch_prepare_given(const double *T, int map, int frame, const MapDesc *ma
 // count.  variant: 0 default, 1 and 2 alternatives (see linearize.cu);
 // grid_per_sm: blocks per SM of the persistent grid (0 = the variant's own).
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
-                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials, int variant,
-                          int grid_per_sm, int num_sms, cudaStream_t st);
+                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
+                          int *next_item, int variant, int grid_per_sm, int num_sms, cudaStream_t st);
 
 // Per-factor fixed-order float64 reduction of the item partials and expansion
 // to the 12x12 H, b, cost.  item_begin has n_f + 1 entries.
-void launch_reduce_finalize(const PoseParam *params, const int32_t *item_begin, int n_f, const double *partials,
+void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, int n_f, const double *partials,
                             const int64_t *inl_partials, double *H, double *b, double *cost, int64_t *inliers,
                             cudaStream_t st);
 
@@ -93,8 +93,9 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
 
 // Overlap matrix: counts[s * n_tgt + t] += hits of source s against target t
 // (pairs[s * n_tgt + t] prepared by launch_prepare_pairs).  One CTA per SM.
+size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt);
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
-                           int n_tgt, unsigned long long *counts, int grid, cudaStream_t st);
+                           int n_tgt, unsigned long long *counts, void *scratch, int grid, cudaStream_t st);
 
 // out[0] += pairs not culled, out[1] += their source sizes (out zeroed).
 void launch_count_live(const PoseParam *pairs, int64_t n_pairs, const FrameDesc *frames, unsigned long long *out,

@@ -337,8 +337,8 @@ __device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, 
 
 // Work items belong to single warps: a warp copies its factor's parameters to
 // its own shared-memory slot, runs over the item's points, reduces its 28 sums
-// by shuffles and writes them as float64 -- no block barriers anywhere.  Items
-// are taken in order by global warp index.
+// by shuffles and writes them as float64 -- no block barriers anywhere.  Warps
+// take items in list order from a global counter.
 //   PTS = 1: one point per lane per step, the next step's point loads issued
 //            before this step's key, probe and record chain;
 //   PTS = 2: two points per lane per step, both points' loads, keys and first
@@ -429,15 +429,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
                                                                const FrameDesc *__restrict__ frames,
                                                                const WorkItem *__restrict__ items, int n_items,
                                                                double *__restrict__ partials,
-                                                               int64_t *__restrict__ inl_partials)
+                                                               int64_t *__restrict__ inl_partials,
+                                                               int *__restrict__ next_item)
 {
     constexpr int NW = BLOCK / 32;
     constexpr int PW = (int)(sizeof(PoseParam) / 4);
     __shared__ PoseParam sP[NW];
     __shared__ MapDesc sM[NW];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * NW + wib, nw = gridDim.x * NW;
-    for (int it = gw; it < n_items; it += nw) {
+    for (;;) {
+        // items in list order, each to the next free warp (uneven items cannot
+        // leave SMs idle while one warp finishes a long static share)
+        int it = 0;
+        if (lane == 0) it = atomicAdd(next_item, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
         const WorkItem w = items[it];
         __syncwarp();                       // this warp's readers of its slots are done
         const uint32_t *src = (const uint32_t *)(params + w.unit);
@@ -472,7 +478,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
 
 // One warp per factor: fixed-order float64 sum of the factor's item partials,
 // then H = L H^t L', b = L b^t with L = [S' ; -D'] (12 x 6).
-__global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const int32_t *__restrict__ item_begin,
+__global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const int32_t *__restrict__ item_range,
                                   int n_f, const double *__restrict__ partials, const int64_t *__restrict__ inl_p,
                                   double *__restrict__ H, double *__restrict__ b, double *__restrict__ cost,
                                   int64_t *__restrict__ inliers)
@@ -482,7 +488,7 @@ __global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const in
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int f = blockIdx.x * WPB + warp;
     if (f >= n_f) return;
-    const int i0 = item_begin[f], i1 = item_begin[f + 1];
+    const int i0 = item_range[2 * f], i1 = item_range[2 * f + 1];
     double s = 0.0;
     if (lane < kNT)
         for (int i = i0; i < i1; ++i) s += partials[(int64_t)i * kNT + lane];
@@ -744,35 +750,45 @@ void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, cons
 // register budget is set for).  Work items are per warp, so the block size only
 // sets the occupancy granularity.
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
-                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials, int variant,
-                          int grid_per_sm, int num_sms, cudaStream_t st)
+                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
+                          int *next_item, int variant, int grid_per_sm, int num_sms, cudaStream_t st)
 {
     if (n_items <= 0) return;
+    cudaMemsetAsync(next_item, 0, sizeof(int), st);
     switch (variant) {
     case 1: {   // one point per step + prefetch, 128-thread blocks, 6 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
-        k_linearize_f32<128, 6, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials);
+        k_linearize_f32<128, 6, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials,
+                                                       next_item);
         break;
     }
     case 2: {   // two points per step, 128-thread blocks, 4 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
-        k_linearize_f32<128, 4, 2><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials);
+        k_linearize_f32<128, 4, 2><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials,
+                                                       next_item);
+        break;
+    }
+    case 3: {   // one point per step + prefetch, 128-thread blocks, 4 per SM (no register cap below 128)
+        const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
+        k_linearize_f32<128, 4, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials,
+                                                       next_item);
         break;
     }
     default: {  // one point per step + prefetch, 128-thread blocks, 5 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
-        k_linearize_f32<128, 5, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials);
+        k_linearize_f32<128, 5, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials,
+                                                       next_item);
         break;
     }
     }
 }
 
-void launch_reduce_finalize(const PoseParam *params, const int32_t *item_begin, int n_f, const double *partials,
+void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, int n_f, const double *partials,
                             const int64_t *inl_partials, double *H, double *b, double *cost, int64_t *inliers,
                             cudaStream_t st)
 {
     if (n_f <= 0) return;
-    k_reduce_finalize<<<(n_f + 3) / 4, 128, 0, st>>>(params, item_begin, n_f, partials, inl_partials, H, b, cost,
+    k_reduce_finalize<<<(n_f + 3) / 4, 128, 0, st>>>(params, item_range, n_f, partials, inl_partials, H, b, cost,
                                                     inliers);
 }
 

@@ -42,10 +42,11 @@ constexpr size_t kOffPoses = kOffFactors + al(sizeof(vgicp_factor) * kMaxFactors
 constexpr size_t kOffIdx = kOffPoses + al(sizeof(double) * 12 * kMaxPoses);
 constexpr size_t kOffParams = kOffIdx + al(sizeof(int32_t) * 4 * kMaxFactors);
 constexpr size_t kOffBegin = kOffParams + al(sizeof(PoseParam) * kMaxFactors);
-constexpr size_t kOffItems = kOffBegin + al(sizeof(int32_t) * (kMaxFactors + 1));
+constexpr size_t kOffItems = kOffBegin + al(sizeof(int32_t) * 2 * kMaxFactors);
 constexpr size_t kOffPartials = kOffItems + al(sizeof(WorkItem) * kMaxItems);
 constexpr size_t kOffInl = kOffPartials + al(sizeof(double) * 28 * kMaxItems);
-constexpr size_t kScratchBytes = kOffInl + al(sizeof(int64_t) * kMaxItems);
+constexpr size_t kOffFetch = kOffInl + al(sizeof(int64_t) * kMaxItems);
+constexpr size_t kScratchBytes = kOffFetch + al(sizeof(int));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -67,9 +68,10 @@ cudaError_t scratch_address(int device, void **out)
 }
 
 // One block: factor handles -> descriptor-table indices, then each factor's
-// chunk count, an exclusive scan, and the chunk work items.
+// chunk count, an exclusive scan, the chunk work items and each factor's item
+// range.
 __global__ void k_noalloc_plan(const vgicp_factor *__restrict__ f, int n_f, const FrameDesc *__restrict__ frames,
-                               int chunk, int32_t *__restrict__ idx, int32_t *__restrict__ item_begin,
+                               int chunk, int32_t *__restrict__ idx, int32_t *__restrict__ item_range,
                                WorkItem *__restrict__ items)
 {
     __shared__ int32_t s_scan[kMaxFactors];
@@ -95,7 +97,8 @@ __global__ void k_noalloc_plan(const vgicp_factor *__restrict__ f, int n_f, cons
     }
     if (i < n_f) {
         const int32_t begin = s_scan[i] - nchunks;
-        item_begin[i] = begin;
+        item_range[2 * i] = begin;
+        item_range[2 * i + 1] = begin + nchunks;
         for (int32_t c = 0; c < nchunks; ++c) {
             WorkItem w;
             w.unit = i;
@@ -103,7 +106,6 @@ __global__ void k_noalloc_plan(const vgicp_factor *__restrict__ f, int n_f, cons
             w.count = (int32_t)((n - w.start < chunk) ? (n - w.start) : chunk);
             items[begin + c] = w;
         }
-        if (i == n_f - 1) item_begin[n_f] = s_scan[i];
     }
 }
 
@@ -154,6 +156,7 @@ extern "C" vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_fact
     WorkItem *d_items = (WorkItem *)(s + kOffItems);
     double *d_partials = (double *)(s + kOffPartials);
     int64_t *d_inl = (int64_t *)(s + kOffInl);
+    int *d_fetch = (int *)(s + kOffFetch);
     e = cudaMemcpyAsync(d_f, factors, sizeof(vgicp_factor) * (size_t)n_f, cudaMemcpyHostToDevice, v.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_poses, poses, sizeof(double) * 12 * (size_t)n_poses, cudaMemcpyHostToDevice, v.stream);
@@ -162,7 +165,7 @@ extern "C" vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_fact
     while (threads < n_f) threads <<= 1;
     k_noalloc_plan<<<1, threads, 0, v.stream>>>(d_f, (int)n_f, v.d_frames, v.chunk, d_idx, d_begin, d_items);
     launch_prepare_factors(d_idx, (int)n_f, d_poses, v.d_maps, v.d_frames, v.linearize_cull, d_params, v.stream);
-    launch_linearize_f32(d_params, v.d_maps, v.d_frames, d_items, (int)n_items, d_partials, d_inl, v.variant,
+    launch_linearize_f32(d_params, v.d_maps, v.d_frames, d_items, (int)n_items, d_partials, d_inl, d_fetch, v.variant,
                          v.blocks_per_sm, v.num_sms, v.stream);
     launch_reduce_finalize(d_params, d_begin, (int)n_f, d_partials, d_inl, H, b, cost, inliers, v.stream);
     ctx_count_launches(ctx, 3 + (n_items > 0));

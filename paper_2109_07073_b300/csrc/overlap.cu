@@ -88,12 +88,15 @@ __global__ void __launch_bounds__(256) k_overlap(const PoseParam *__restrict__ p
 // Overlap matrix.  A work item is (slice of kSlice sources, one target): the
 // CTA stages the target's compact presence table (32-bit keys relative to its
 // voxel box, capacity ~2x its voxel count) in shared memory once, then streams
-// the slice's live sources through it, kPPT points per thread per step.  Items
-// run slice-major, so the CTAs in flight share one slice of sources (a few MB,
-// L2-resident) while each holds a different target table.  Targets without a
+// the slice's live sources through it, kPPT points per thread per step.  Only
+// items with a pair that survives culling are listed (k_overlap_items), in
+// slice-major order up to warp interleaving, and CTAs take them from that list
+// through a global counter, so the CTAs in flight share one slice of sources (a
+// few MB, L2-resident) while each holds a different target table, and no SM
+// sits idle while another works through a long static share.  Targets without a
 // compact table that fits (very large or very wide maps) probe the main table
 // in global memory instead; undecided floors take the slower exact path.
-constexpr int kOvBlock = 1024, kPPT = 4, kSlice = 32;
+constexpr int kOvBlock = 1024, kPPT = 4, kSlice = 16;
 constexpr int kSmemLog2 = 15;   // 32,768 compact keys = 128 KB of shared memory
 
 // Presence of the voxel at box-relative coordinate (dx, dy, dz) in a compact
@@ -113,10 +116,33 @@ __device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, ui
     return false;
 }
 
+// List the (slice, target) items with at least one pair not culled: hdr[0]
+// counts them (hdr[1] is the matrix kernel's fetch counter, both zeroed first).
+__global__ void k_overlap_items(const PoseParam *__restrict__ pairs, int n_src, int n_tgt,
+                                int32_t *__restrict__ list, int *__restrict__ hdr)
+{
+    const int n_slices = (n_src + kSlice - 1) / kSlice;
+    const int64_t total = (int64_t)n_slices * n_tgt;
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool live = false;
+    if (v < total) {
+        const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
+        const int s0 = sl * kSlice, s1 = min(n_src, s0 + kSlice);
+        for (int s = s0; s < s1 && !live; ++s) live = !__ldg(&pairs[(int64_t)s * n_tgt + t].cull);
+    }
+    const unsigned lane = threadIdx.x & 31, b = __ballot_sync(0xffffffffu, live);
+    int base = 0;
+    if (lane == 0 && b) base = atomicAdd(hdr, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (live) list[base + __popc(b & ((1u << lane) - 1u))] = (int32_t)v;
+}
+
 __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam *__restrict__ pairs,
                                                                 const MapDesc *__restrict__ maps,
                                                                 const FrameDesc *__restrict__ frames, int n_src,
-                                                                int n_tgt, unsigned long long *__restrict__ counts)
+                                                                int n_tgt, const int32_t *__restrict__ list,
+                                                                int *__restrict__ hdr,
+                                                                unsigned long long *__restrict__ counts)
 {
     extern __shared__ uint4 s_tab4[];
     const uint32_t *s_tab = (const uint32_t *)s_tab4;
@@ -127,15 +153,18 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
     __shared__ const float4 *s_pa[kSlice];
     __shared__ int s_n[kSlice], s_csh[kSlice], s_nlive[kSlice];
     __shared__ unsigned char s_live[kSlice][kMaxCullChunks];   // live cull chunks of each source, in order
+    __shared__ int s_q;
     const int lane = threadIdx.x & 31;
-    const int n_slices = (n_src + kSlice - 1) / kSlice;
-    const int64_t total = (int64_t)n_slices * n_tgt;
-    for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
+    const int n_live = hdr[0];
+    for (;;) {
+        __syncthreads();                                // previous item's readers are done
+        if (threadIdx.x == 0) s_q = atomicAdd(hdr + 1, 1);
+        __syncthreads();
+        const int q = s_q;
+        if (q >= n_live) break;
+        const int64_t v = list[q];
         const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
         const int s0 = sl * kSlice, ns = min(n_src, s0 + kSlice) - s0;
-        __syncthreads();                                // previous item's readers are done
-        const int live = (threadIdx.x < ns) ? !pairs[(int64_t)(s0 + threadIdx.x) * n_tgt + t].cull : 0;
-        if (!__syncthreads_or(live)) continue;          // every pair of the item culled
         // the slice's pair parameters (one warp per source) and the target's table
         {
             const int wib = threadIdx.x >> 5;
@@ -337,13 +366,24 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
     k_overlap<<<grid, 256, 0, st>>>(params, maps, frames, items, n_items, counts);
 }
 
+size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt)
+{
+    const int64_t n_slices = (n_src + kSlice - 1) / kSlice;
+    return (size_t)(n_slices * n_tgt + 4) * sizeof(int32_t);
+}
+
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
-                           int n_tgt, unsigned long long *counts, int grid, cudaStream_t st)
+                           int n_tgt, unsigned long long *counts, void *scratch, int grid, cudaStream_t st)
 {
     if (n_src <= 0 || n_tgt <= 0) return;
+    int *hdr = (int *)scratch;
+    int32_t *list = (int32_t *)scratch + 4;
+    const int64_t total = (int64_t)((n_src + kSlice - 1) / kSlice) * n_tgt;
+    cudaMemsetAsync(hdr, 0, 4 * sizeof(int), st);
+    k_overlap_items<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pairs, n_src, n_tgt, list, hdr);
     const int smem = (1 << kSmemLog2) * 4;
     cudaFuncSetAttribute(k_overlap_matrix, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_overlap_matrix<<<grid, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt, counts);
+    k_overlap_matrix<<<grid, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt, list, hdr, counts);
 }
 
 void launch_correspondences(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,

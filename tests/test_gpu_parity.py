@@ -296,7 +296,7 @@ def test_knn_covariances_match_oracle(ctx, single):
     assert np.array_equal(ctx.estimate_covariances(tiny, 10, 1e-3), oracle.covariances(tiny))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_linearize_variants_agree(ctx, variant):
     tg, tcov, src, scov, poses, factors = _ragged_case(seed=45)
     hm = [ctx.build_voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
