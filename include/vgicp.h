@@ -67,13 +67,20 @@ enum { VGICP_MEM_HOST = 0, VGICP_MEM_DEVICE = 1 };
 /* Linearisation precision (vgicp_options.precision). */
 enum {
     /* Batched path: one persistent launch over all factors; per-point transform,
-     * inverse and Jacobian products in float32 (voxel index and residual taken
-     * from an error-free float32-pair transform, with a float64 fallback at voxel
-     * faces); per-chunk sums in float64; 12x12 expansion in float64. */
+     * inverse and Jacobian products in float32.  The voxel index is exact (the
+     * float32 floor on a split translation is accepted only farther than its
+     * proven error bound from a voxel face, else the float64 floor is taken);
+     * per-chunk sums across a warp in float32, sums of chunks in float64; 12x12
+     * expansion in float64. */
     VGICP_PREC_F32 = 0,
     /* Plain path: one launch per factor; everything in float64 with the literal
      * 3x12 Jacobian and all 78 unique entries of J^T Omega J per point. */
-    VGICP_PREC_F64 = 1
+    VGICP_PREC_F64 = 1,
+    /* Batched path with a compensated transform: the point's position relative
+     * to its voxel (the residual) and the lever arm come from an error-free
+     * float32-pair transform instead of plain float32; the rest as
+     * VGICP_PREC_F32.  Slower, about ten times more accurate residuals. */
+    VGICP_PREC_F32_COMP = 2
 };
 
 typedef struct vgicp_ctx vgicp_ctx;
@@ -90,7 +97,7 @@ typedef struct {
 } vgicp_factor;
 
 typedef struct {
-    int32_t precision;        /* VGICP_PREC_F32 (default) or VGICP_PREC_F64 */
+    int32_t precision;        /* VGICP_PREC_F32 (default), VGICP_PREC_F64 or VGICP_PREC_F32_COMP */
     int32_t chunk_points;     /* points per work item of the batched path (one warp per item; multiple of 32;
                                  0 = default 2048) */
     int32_t linearize_variant;/* batched kernel variant: 0 default, 1, 2 or 3 (same results, different
@@ -178,7 +185,8 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
  * factors, then synchronise" step): times every candidate (kernel variant x
  * points per work item x persistent grid) on this factor set with CUDA events
  * on the context stream, `reps` timed runs each after one warm-up, and keeps
- * the fastest in the context options (precision is set to VGICP_PREC_F32).
+ * the fastest in the context options (VGICP_PREC_F64 becomes VGICP_PREC_F32;
+ * VGICP_PREC_F32_COMP is kept).
  * best (nullable) receives those options and best_ms (nullable) the time of one
  * run.  Results differ between candidates only by float32 summation order. */
 vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
@@ -209,7 +217,8 @@ vgicp_status vgicp_plan_create(vgicp_ctx *ctx, const vgicp_factor *factors, int6
  * pinned staging buffer before the call returns; a run first waits until the
  * previous run of this plan has read it).  H, b, cost, inliers (nullable) as
  * for vgicp_linearize(), in out_kind memory; HOST outputs return synchronised,
- * DEVICE outputs are written in stream order.  Needs VGICP_PREC_F32. */
+ * DEVICE outputs are written in stream order.  Needs VGICP_PREC_F32 or
+ * VGICP_PREC_F32_COMP. */
 vgicp_status vgicp_plan_linearize(vgicp_ctx *ctx, vgicp_plan *plan, const double *poses, double *H, double *b,
                                   double *cost, int64_t *inliers, int out_kind);
 
@@ -231,7 +240,9 @@ vgicp_status vgicp_plan_destroy(vgicp_ctx *ctx, vgicp_plan *plan);
  * application whose own allocator owns all device memory.  They create the
  * context, frames and voxelmaps beforehand and pass their own outputs.
  *
- * Same results as vgicp_linearize() with VGICP_PREC_F32 and the context's
+ * Same results as vgicp_linearize() with the context's batched precision
+ * (VGICP_PREC_F32, or VGICP_PREC_F32_COMP when set; VGICP_PREC_F64 runs as
+ * VGICP_PREC_F32) and its
  * chunk_points / linearize_variant (the same kernels run over the same chunks).
  * factors and poses are host arrays copied on the context stream (a pinned
  * buffer must stay valid until the stream passes the copy); H (n_f x 144),

@@ -25,7 +25,7 @@ VGICP_OK = 0
 STATUS = {0: "VGICP_OK", 1: "VGICP_ERR_INVALID_ARG", 2: "VGICP_ERR_OOM", 3: "VGICP_ERR_NOT_FOUND",
           4: "VGICP_ERR_EMPTY", 5: "VGICP_ERR_CUDA", 6: "VGICP_ERR_TIMEOUT", 7: "VGICP_ERR_BUDGET"}
 VGICP_MEM_HOST, VGICP_MEM_DEVICE = 0, 1
-VGICP_PREC_F32, VGICP_PREC_F64 = 0, 1
+VGICP_PREC_F32, VGICP_PREC_F64, VGICP_PREC_F32_COMP = 0, 1, 2
 
 EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_options", "vgicp_set_stream",
            "vgicp_synchronize", "vgicp_add_frame", "vgicp_frame_size", "vgicp_build_voxelmap",

@@ -490,8 +490,8 @@ vgicp_status vgicp_options_default(vgicp_options *opt)
 
 static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
 {
-    if (o->precision != VGICP_PREC_F32 && o->precision != VGICP_PREC_F64)
-        return fail(ctx, VGICP_ERR_INVALID_ARG, "precision must be VGICP_PREC_F32 or VGICP_PREC_F64");
+    if (o->precision != VGICP_PREC_F32 && o->precision != VGICP_PREC_F64 && o->precision != VGICP_PREC_F32_COMP)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "precision must be VGICP_PREC_F32, VGICP_PREC_F64 or VGICP_PREC_F32_COMP");
     if (o->chunk_points < 0 || (o->chunk_points % 32) != 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "chunk_points must be a non-negative multiple of 32");
     if (o->linearize_variant < 0 || o->linearize_variant > 3)
@@ -791,8 +791,8 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         TRY(ensure(ctx, LN.ws_fetch, 16));
         launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
                              (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p,
-                             ctx->opt.linearize_variant,
-                             ctx->opt.blocks_per_sm, ctx->num_sms, LN.stream);
+                             ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
+                             ctx->opt.precision == VGICP_PREC_F32_COMP, LN.stream);
         launch_reduce_finalize(d_params, (const int32_t *)P.item_range.p, (int)n_f, (const double *)LN.ws_partials.p,
                                (const int64_t *)LN.ws_inl.p, dH, db, dc, di, LN.stream);
         ctx->launches += (P.n_items > 0) + 1;
@@ -835,7 +835,7 @@ struct vgicp_plan {
     // what the graph was captured with
     MapDesc *maps = nullptr;
     FrameDesc *frames = nullptr;
-    int chunk = 0, variant = -1, bps = -1, cull = -1;
+    int chunk = 0, variant = -1, bps = -1, cull = -1, prec = -1;
     int64_t runs = 0, captures = 0;
 };
 
@@ -866,7 +866,7 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
     const bool same_work = chunk == P->chunk && idx == P->idx && fn == P->frame_n;
     if (same_work && P->exec && P->maps == ctx->d_maps && P->frames == ctx->d_frames &&
         P->variant == ctx->opt.linearize_variant && P->bps == ctx->opt.blocks_per_sm &&
-        P->cull == ctx->opt.linearize_cull)
+        P->cull == ctx->opt.linearize_cull && P->prec == ctx->opt.precision)
         return VGICP_OK;
     if (P->in_flight) {
         CU(cudaEventSynchronize(P->done));
@@ -900,8 +900,8 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
                            ctx->d_frames, ctx->opt.linearize_cull, params, P->cap);
     launch_linearize_f32(params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P->d_items.p, P->n_items,
                          (double *)P->d_partials.p, (int64_t *)P->d_inl.p, (int *)P->d_fetch.p,
-                         ctx->opt.linearize_variant,
-                         ctx->opt.blocks_per_sm, ctx->num_sms, P->cap);
+                         ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
+                         ctx->opt.precision == VGICP_PREC_F32_COMP, P->cap);
     launch_reduce_finalize(params, (const int32_t *)P->d_range.p, (int)n_f, (const double *)P->d_partials.p,
                            (const int64_t *)P->d_inl.p, H, b, c, inl, P->cap);
     cudaGraph_t g = nullptr;
@@ -922,6 +922,7 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
     P->variant = ctx->opt.linearize_variant;
     P->bps = ctx->opt.blocks_per_sm;
     P->cull = ctx->opt.linearize_cull;
+    P->prec = ctx->opt.precision;
     P->captures += 1;
     return VGICP_OK;
 }
@@ -991,7 +992,7 @@ vgicp_status vgicp_plan_linearize(vgicp_ctx *ctx, vgicp_plan *P, const double *p
     if (P->n_f == 0) return VGICP_OK;
     for (int64_t i = 0; i < P->n_poses * 12; ++i)
         if (!std::isfinite(poses[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "plan_linearize: non-finite pose");
-    if (ctx->opt.precision != VGICP_PREC_F32)
+    if (ctx->opt.precision == VGICP_PREC_F64)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "plan_linearize: plans run the batched float32 path");
     TRY(plan_refresh(ctx, P));
     if (P->in_flight) CU(cudaEventSynchronize(P->done));   // the previous run has read the staging buffer
@@ -1054,7 +1055,7 @@ vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     for (int variant = 0; variant <= 3 && st == VGICP_OK; ++variant)
         for (int ci = 0; ci < 4 && st == VGICP_OK; ++ci) {
             ctx->opt = keep;
-            ctx->opt.precision = VGICP_PREC_F32;
+            if (keep.precision == VGICP_PREC_F64) ctx->opt.precision = VGICP_PREC_F32;
             ctx->opt.linearize_variant = variant;
             ctx->opt.chunk_points = chunks[ci];
             ctx->opt.blocks_per_sm = 0;
@@ -1442,6 +1443,7 @@ bool ctx_view(vgicp_ctx *ctx, CtxView *v)
     v->chunk = default_chunk(ctx->opt);
     v->variant = ctx->opt.linearize_variant;
     v->linearize_cull = ctx->opt.linearize_cull;
+    v->compensated = ctx->opt.precision == VGICP_PREC_F32_COMP;
     v->blocks_per_sm = ctx->opt.blocks_per_sm;
     v->d_maps = ctx->d_maps;
     v->d_frames = ctx->d_frames;

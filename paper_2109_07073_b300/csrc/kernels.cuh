@@ -71,7 +71,8 @@ void launch_prepare_given(const double *T, int map, int frame, const MapDesc *ma
 // grid_per_sm: blocks per SM of the persistent grid (0 = the variant's own).
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
                           const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
-                          int *next_item, int variant, int grid_per_sm, int num_sms, cudaStream_t st);
+                          int *next_item, int variant, int grid_per_sm, int num_sms, bool compensated,
+                          cudaStream_t st);
 
 // Per-factor fixed-order float64 reduction of the item partials and expansion
 // to the 12x12 H, b, cost.  item_begin has n_f + 1 entries.
@@ -132,6 +133,7 @@ namespace vg {
 struct CtxView {
     cudaStream_t stream;
     int device, num_sms, chunk, variant, blocks_per_sm, linearize_cull;
+    bool compensated;
     MapDesc *d_maps;
     FrameDesc *d_frames;
 };

@@ -251,6 +251,37 @@ __device__ __forceinline__ bool point_key_ff(const PoseParam &P, const MapDesc &
     return true;
 }
 
+// Voxel coordinate, in-voxel offset and lever arm R p of one point from the
+// plain float32 transform on the split translation t = k0 r + tf (the float32
+// path's per-point transform).  The floor is exact: a point whose float32
+// distance to a voxel face is within the proven error bound tol of the float64
+// reference is left undecided and takes the float64 reference.  The offset and
+// the lever arm carry float32 rounding (about 2^-22 of |R p| + |tf|).
+__device__ __forceinline__ bool point_key_split(const PoseParam &P, const MapDesc &m, float px, float py, float pz,
+                                                int k[3], float d[3], float rp[3])
+{
+    bool decided = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float *R = P.Rh + 3 * a;
+        const float tf = P.tfh[a];
+        const float x = __fmaf_rn(R[0], px, __fmaf_rn(R[1], py, __fmaf_rn(R[2], pz, tf)));
+        const float kf = floorf(__fmul_rn(x, m.inv_rf));
+        const float dd = __fmaf_rn(-kf, m.r_l, __fmaf_rn(-kf, m.r_h, x));
+        decided &= (dd >= P.tol[a]) & (dd <= P.rup[a]);
+        const int kk = (int)kf + P.k0[a];
+        k[a] = (kk >= -kKeyOffset && kk <= kKeyOffset - 1) ? kk : INT32_MIN;
+        d[a] = dd;
+        rp[a] = __fsub_rn(x, tf);
+    }
+    if (decided) return k[0] != INT32_MIN && k[1] != INT32_MIN && k[2] != INT32_MIN;
+    double q[3];
+    if (!key_f64(P.T, px, py, pz, m.inv_r, k, q)) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = __double2float_rn(q[a] - (double)k[a] * m.r);
+    return true;
+}
+
 // Slot of the voxel containing one source point, or -1; first probe issued by
 // the caller so two points' probes can be in flight together.
 struct PointSlot {
@@ -259,12 +290,13 @@ struct PointSlot {
     bool ok;
 };
 
+template <bool FF>
 __device__ __forceinline__ PointSlot point_hash(const PoseParam &P, const MapDesc &m, float px, float py, float pz,
                                                 float d[3], float rp[3])
 {
     int k[3];
     PointSlot r;
-    r.ok = point_key_ff(P, m, px, py, pz, k, d, rp);
+    r.ok = FF ? point_key_ff(P, m, px, py, pz, k, d, rp) : point_key_split(P, m, px, py, pz, k, d, rp);
     r.key = r.ok ? pack_key(k[0], k[1], k[2]) : 0ull;
     r.h = hash_slot(r.key, m.log2cap);
     return r;
@@ -275,6 +307,16 @@ __device__ __forceinline__ int resolve_slot(const MapDesc &m, const PointSlot &p
     if (!ps.ok || first == kEmptyKey) return -1;
     if (first == ps.key) return (int)ps.h;
     return probe_from(m.keys, m.mask, ps.key, (ps.h + 1) & m.mask);
+}
+
+// The parts of a voxel record the linearisation reads (mean, covariance).
+__device__ __forceinline__ VoxelRec load_rec(const VoxelRec *r)
+{
+    VoxelRec v;
+    v.a = __ldg(&r->a);
+    v.b = __ldg(&r->b);
+    v.c = make_float4(__ldg(&r->c.x), 0.f, 0.f, 0.f);
+    return v;
 }
 
 // One correspondence's contribution (Eq. 2, 5, 6 in the adjoint form) added to acc.
@@ -348,7 +390,7 @@ __device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, 
 //            before this step's key, probe and record chain;
 //   PTS = 2: two points per lane per step, both points' loads, keys and first
 //            probes issued before either record is needed.
-template <int PTS>
+template <int PTS, bool FF>
 __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
                                                  const WorkItem &w, int lane, float acc[kNT], int &inl)
 {
@@ -373,11 +415,16 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
                 C = __ldg(pc + i + 32);
             }
             float d0[3], x0[3];
-            const PointSlot s0 = point_hash(P, m, A0.x, A0.y, A0.z, d0, x0);
-            const uint64_t f0 = s0.ok ? __ldg(m.keys + s0.h) : kEmptyKey;
+            const PointSlot s0 = point_hash<FF>(P, m, A0.x, A0.y, A0.z, d0, x0);
+            uint64_t f0 = kEmptyKey;
+            VoxelRec v0;
+            if (s0.ok) {   // the record of the first slot probed travels with its key
+                f0 = __ldg(m.keys + s0.h);
+                v0 = load_rec(m.rec + s0.h);
+            }
             const int slot0 = resolve_slot(m, s0, f0);
             if (slot0 < 0) continue;
-            const VoxelRec v0 = m.rec[slot0];
+            if (slot0 != (int)s0.h) v0 = load_rec(m.rec + slot0);
             inl += accumulate_point(acc, P.Rh, A0, B0, C0, v0, d0, x0);
         }
     } else {
@@ -394,16 +441,23 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
                 C1 = __ldg(pc + i1);
             }
             float d0[3], x0[3], d1[3], x1[3];
-            PointSlot s0 = point_hash(P, m, A0.x, A0.y, A0.z, d0, x0);
-            PointSlot s1 = point_hash(P, m, A1.x, A1.y, A1.z, d1, x1);
+            PointSlot s0 = point_hash<FF>(P, m, A0.x, A0.y, A0.z, d0, x0);
+            PointSlot s1 = point_hash<FF>(P, m, A1.x, A1.y, A1.z, d1, x1);
             s1.ok = s1.ok && h1;
-            const uint64_t f0 = s0.ok ? __ldg(m.keys + s0.h) : kEmptyKey;
-            const uint64_t f1 = s1.ok ? __ldg(m.keys + s1.h) : kEmptyKey;
+            uint64_t f0 = kEmptyKey, f1 = kEmptyKey;
+            VoxelRec v0, v1;
+            if (s0.ok) {
+                f0 = __ldg(m.keys + s0.h);
+                v0 = load_rec(m.rec + s0.h);
+            }
+            if (s1.ok) {
+                f1 = __ldg(m.keys + s1.h);
+                v1 = load_rec(m.rec + s1.h);
+            }
             const int slot0 = resolve_slot(m, s0, f0);
             const int slot1 = resolve_slot(m, s1, f1);
-            VoxelRec v0, v1;
-            if (slot0 >= 0) v0 = m.rec[slot0];
-            if (slot1 >= 0) v1 = m.rec[slot1];
+            if (slot0 >= 0 && slot0 != (int)s0.h) v0 = load_rec(m.rec + slot0);
+            if (slot1 >= 0 && slot1 != (int)s1.h) v1 = load_rec(m.rec + slot1);
             if (slot0 >= 0) inl += accumulate_point(acc, P.Rh, A0, B0, C0, v0, d0, x0);
             if (slot1 >= 0) inl += accumulate_point(acc, P.Rh, A1, B1, C1, v1, d1, x1);
         }
@@ -412,7 +466,7 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
 
 // One work item: skipped when every cull chunk it spans is dead (no point of it
 // can find a voxel), otherwise all of its points.
-template <int PTS>
+template <int PTS, bool FF>
 __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
                                                     const WorkItem &w, int lane, float acc[kNT], int &inl)
 {
@@ -420,10 +474,10 @@ __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const Ma
     const int c0 = (int)(w.start >> F.cshift), c1 = (int)((w.start + w.count - 1) >> F.cshift);
     const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
     if ((P.cmask & span) == 0u) return;
-    linearize_points<PTS>(P, m, F, w, lane, acc, inl);
+    linearize_points<PTS, FF>(P, m, F, w, lane, acc, inl);
 }
 
-template <int BLOCK, int MINB, int PTS>
+template <int BLOCK, int MINB, int PTS, bool FF>
 __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *__restrict__ params,
                                                                const MapDesc *__restrict__ maps,
                                                                const FrameDesc *__restrict__ frames,
@@ -459,7 +513,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
 #pragma unroll
         for (int j = 0; j < kNT; ++j) acc[j] = 0.f;
         int inl = 0;
-        linearize_warp_item<PTS>(P, m, F, w, lane, acc, inl);
+        linearize_warp_item<PTS, FF>(P, m, F, w, lane, acc, inl);
         // butterfly: every lane ends with the warp's sums; lane j writes sum j
         double mine = 0.0;
 #pragma unroll
@@ -749,38 +803,52 @@ void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, cons
 // Variants of the batched kernel: (points per lane per step, blocks per SM the
 // register budget is set for).  Work items are per warp, so the block size only
 // sets the occupancy granularity.
-void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
-                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
-                          int *next_item, int variant, int grid_per_sm, int num_sms, cudaStream_t st)
+template <bool FF>
+void launch_variant(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
+                    int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
+                    int grid_per_sm, int num_sms, cudaStream_t st)
 {
-    if (n_items <= 0) return;
-    cudaMemsetAsync(next_item, 0, sizeof(int), st);
     switch (variant) {
     case 1: {   // one point per step + prefetch, 128-thread blocks, 6 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
-        k_linearize_f32<128, 6, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials,
-                                                       next_item);
+        k_linearize_f32<128, 6, 1, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+                                                           inl_partials, next_item);
         break;
     }
     case 2: {   // two points per step, 128-thread blocks, 4 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
-        k_linearize_f32<128, 4, 2><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials,
-                                                       next_item);
+        k_linearize_f32<128, 4, 2, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+                                                           inl_partials, next_item);
         break;
     }
     case 3: {   // one point per step + prefetch, 128-thread blocks, 4 per SM (no register cap below 128)
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
-        k_linearize_f32<128, 4, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials,
-                                                       next_item);
+        k_linearize_f32<128, 4, 1, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+                                                           inl_partials, next_item);
         break;
     }
     default: {  // one point per step + prefetch, 128-thread blocks, 5 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
-        k_linearize_f32<128, 5, 1><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials, inl_partials,
-                                                       next_item);
+        k_linearize_f32<128, 5, 1, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+                                                           inl_partials, next_item);
         break;
     }
     }
+}
+
+void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
+                          const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
+                          int *next_item, int variant, int grid_per_sm, int num_sms, bool compensated,
+                          cudaStream_t st)
+{
+    if (n_items <= 0) return;
+    cudaMemsetAsync(next_item, 0, sizeof(int), st);
+    if (compensated)
+        launch_variant<true>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
+                             grid_per_sm, num_sms, st);
+    else
+        launch_variant<false>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
+                              grid_per_sm, num_sms, st);
 }
 
 void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, int n_f, const double *partials,

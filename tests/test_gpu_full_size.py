@@ -69,10 +69,13 @@ def test_paper_scale_graph_sampled_parity(graph):
         pick = rng.choose(len(tgt), 24)
         sub = factors[pick]
         H64, b64, c64, i64 = ctx.linearize(sub, g.poses)
+        ctx.set_options(precision=vg.VGICP_PREC_F32_COMP)
+        Hc, bc, cc, ic = ctx.linearize(sub, g.poses)
         ctx.set_options(precision=vg.VGICP_PREC_F32)
         report = {"factors": int(len(tgt)), "autotuned": {"variant": int(best.linearize_variant),
                                                          "chunk_points": int(best.chunk_points)},
-                  "f32": {"H": [], "b": [], "cost": []}, "f64": {"H": [], "b": [], "cost": []}}
+                  "f32": {"H": [], "b": [], "cost": []}, "f64": {"H": [], "b": [], "cost": []},
+                  "f32_comp": {"H": [], "b": [], "cost": []}}
 
         def ref(k):
             f = pick[k]
@@ -82,16 +85,20 @@ def test_paper_scale_graph_sampled_parity(graph):
             refs = list(ex.map(ref, range(len(pick))))
         for k, L in enumerate(refs):
             f = pick[k]
-            assert inl[f] == L.inliers and i64[k] == L.inliers
+            assert inl[f] == L.inliers and i64[k] == L.inliers and ic[k] == L.inliers
             e32 = (err_metric(H[f], L.H, L.SH), err_metric(b[f], L.b, L.Sb), abs(cost[f] - L.cost) / L.Scost)
             e64 = (err_metric(H64[k], L.H, L.SH), err_metric(b64[k], L.b, L.Sb), abs(c64[k] - L.cost) / L.Scost)
             for name, v in zip(("H", "b", "cost"), e32):
                 report["f32"][name].append(v)
+            ec = (err_metric(Hc[k], L.H, L.SH), err_metric(bc[k], L.b, L.Sb), abs(cc[k] - L.cost) / L.Scost)
             for name, v in zip(("H", "b", "cost"), e64):
                 report["f64"][name].append(v)
+            for name, v in zip(("H", "b", "cost"), ec):
+                report["f32_comp"][name].append(v)
             assert max(e32) <= 1e-4, (k, e32)
             assert max(e64) <= 1e-5, (k, e64)
-        for path in ("f32", "f64"):
+            assert max(ec) <= 1e-4, (k, ec)
+        for path in ("f32", "f64", "f32_comp"):
             for name in ("H", "b", "cost"):
                 v = np.array(report[path][name])
                 report[path][name] = {"max": float(v.max()), "p99": float(np.percentile(v, 99)),

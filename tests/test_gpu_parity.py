@@ -16,7 +16,7 @@ from util import err_metric
 
 pytestmark = pytest.mark.gpu
 
-TOL = {vg.VGICP_PREC_F32: 1e-4, vg.VGICP_PREC_F64: 1e-5}
+TOL = {vg.VGICP_PREC_F32: 1e-4, vg.VGICP_PREC_F64: 1e-5, vg.VGICP_PREC_F32_COMP: 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -184,7 +184,7 @@ def _oracle_factor(vm, pts, covs, TB, TA):
     return oracle.linearize(vm, pts, covs, oracle.relative_pose(TB, TA))
 
 
-@pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64])
+@pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64, vg.VGICP_PREC_F32_COMP])
 def test_linearize_single_factor(ctx, single, prec):
     w, cb, ca = single
     ctx.set_options(precision=prec)
@@ -205,7 +205,7 @@ def test_linearize_single_factor(ctx, single, prec):
     ctx.release(hf)
 
 
-@pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64])
+@pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64, vg.VGICP_PREC_F32_COMP])
 @pytest.mark.parametrize("chunk", [64, 2048])
 def test_linearize_ragged_batch(ctx, prec, chunk):
     tg, tcov, src, scov, poses, factors = _ragged_case()
@@ -349,7 +349,7 @@ def test_autotune_keeps_results(ctx, single):
     poses = np.stack([w.T_target, w.T_source])
     f = vg.make_factors([hm, hm], [hf, hf], [0, 1], [1, 0])
     best, ms = ctx.autotune(f, poses, reps=1)
-    assert ms > 0 and best.linearize_variant in (0, 1, 2) and best.chunk_points in (1024, 2048, 4096, 8192)
+    assert ms > 0 and best.linearize_variant in range(4) and best.chunk_points in (1024, 2048, 4096, 8192)
     H, b, cost, inl = ctx.linearize(f, poses)
     vm = oracle.voxelmap(w.points_target, cb, w.resolution)
     L = _oracle_factor(vm, w.points_source, ca, w.T_target, w.T_source)

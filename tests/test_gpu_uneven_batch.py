@@ -71,8 +71,22 @@ def test_uneven_batch_sampled_parity():
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 3
         H, b, cost, inl = (x.cpu().numpy() for x in out)
+        # the same iteration as one CUDA graph: bit-identical, timed the same way
+        plan = ctx.plan_create(factors, len(w.poses))
+        ctx.plan_linearize(plan, w.poses, out=out)
+        e0.record(stream)
+        for _ in range(3):
+            ctx.plan_linearize(plan, w.poses, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1) / 3
+        for x, y in zip((H, b, cost, inl), out):
+            assert np.array_equal(x, y.cpu().numpy())
+        ctx.plan_destroy(plan)
         ctx.set_options(precision=vg.VGICP_PREC_F64)
         H64, b64, c64, i64 = ctx.linearize(factors[pick], w.poses)
+        ctx.set_options(precision=vg.VGICP_PREC_F32_COMP)
+        Hc, bc, cc, ic = ctx.linearize(factors[pick], w.poses)
         ctx.set_options(precision=vg.VGICP_PREC_F32)
 
         def ref(k):
@@ -84,24 +98,29 @@ def test_uneven_batch_sampled_parity():
             return oracle.linearize(vm, w.frames[j][ix], ocov[j][ix], oracle.relative_pose(w.poses[t], w.poses[j]))
         with ThreadPoolExecutor(max_workers=cores) as ex:
             refs = list(ex.map(ref, range(len(pick))))
-        report = {"factors": n_f, "points": n_points, "batched_f32_ms": ms,
+        report = {"factors": n_f, "points": n_points, "batched_f32_ms": ms, "graph_iteration_ms": graph_ms,
                   "point_correspondences_per_s": n_points / (ms / 1e3), "factors_per_s": n_f / (ms / 1e3),
                   "autotuned": {"variant": int(best.linearize_variant), "chunk_points": int(best.chunk_points)},
-                  "f32": {"H": [], "b": [], "cost": []}, "f64": {"H": [], "b": [], "cost": []}}
+                  "f32": {"H": [], "b": [], "cost": []}, "f64": {"H": [], "b": [], "cost": []},
+                  "f32_comp": {"H": [], "b": [], "cost": []}}
         for k, L in enumerate(refs):
             f = pick[k]
-            assert inl[f] == L.inliers and i64[k] == L.inliers, k
+            assert inl[f] == L.inliers and i64[k] == L.inliers and ic[k] == L.inliers, k
             if L.inliers == 0:
                 continue
             e32 = (err_metric(H[f], L.H, L.SH), err_metric(b[f], L.b, L.Sb), abs(cost[f] - L.cost) / L.Scost)
             e64 = (err_metric(H64[k], L.H, L.SH), err_metric(b64[k], L.b, L.Sb), abs(c64[k] - L.cost) / L.Scost)
             for nm, v in zip(("H", "b", "cost"), e32):
                 report["f32"][nm].append(v)
+            ec = (err_metric(Hc[k], L.H, L.SH), err_metric(bc[k], L.b, L.Sb), abs(cc[k] - L.cost) / L.Scost)
             for nm, v in zip(("H", "b", "cost"), e64):
                 report["f64"][nm].append(v)
+            for nm, v in zip(("H", "b", "cost"), ec):
+                report["f32_comp"][nm].append(v)
             assert max(e32) <= 1e-4, (k, e32)
             assert max(e64) <= 1e-5, (k, e64)
-        for path in ("f32", "f64"):
+            assert max(ec) <= 1e-4, (k, ec)
+        for path in ("f32", "f64", "f32_comp"):
             for nm in ("H", "b", "cost"):
                 v = np.array(report[path][nm])
                 report[path][nm] = {"max": float(v.max()), "p99": float(np.percentile(v, 99)),
