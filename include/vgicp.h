@@ -100,7 +100,7 @@ typedef struct {
     int32_t precision;        /* VGICP_PREC_F32 (default), VGICP_PREC_F64 or VGICP_PREC_F32_COMP */
     int32_t chunk_points;     /* points per work item of the batched path (one warp per item; multiple of 32;
                                  0 = default 2048) */
-    int32_t linearize_variant;/* batched kernel variant: 0 default, 1, 2 or 3 (same results, different
+    int32_t linearize_variant;/* batched kernel variant: 0 default, 1 to 5 (same results, different
                                  latency hiding; chosen by measurement) */
     int32_t blocks_per_sm;    /* persistent grid = SMs x this (0 = the variant's default) */
     int64_t hbm_budget_bytes; /* device bytes handles may hold in total (0 = unlimited) */

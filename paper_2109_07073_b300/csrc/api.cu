@@ -494,8 +494,8 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "precision must be VGICP_PREC_F32, VGICP_PREC_F64 or VGICP_PREC_F32_COMP");
     if (o->chunk_points < 0 || (o->chunk_points % 32) != 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "chunk_points must be a non-negative multiple of 32");
-    if (o->linearize_variant < 0 || o->linearize_variant > 3)
-        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_variant must be 0, 1, 2 or 3");
+    if (o->linearize_variant < 0 || o->linearize_variant > 5)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_variant must be in 0..5");
     if (o->blocks_per_sm < 0 || o->hbm_budget_bytes < 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
     if (o->overlap_cull != 0 && o->overlap_cull != 1)
@@ -1052,7 +1052,7 @@ vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     float win_ms = 1e30f;
     static const int chunks[] = {1024, 2048, 4096, 8192};
     vgicp_status st = VGICP_OK;
-    for (int variant = 0; variant <= 3 && st == VGICP_OK; ++variant)
+    for (int variant = 0; variant <= 5 && st == VGICP_OK; ++variant)
         for (int ci = 0; ci < 4 && st == VGICP_OK; ++ci) {
             ctx->opt = keep;
             if (keep.precision == VGICP_PREC_F64) ctx->opt.precision = VGICP_PREC_F32;

@@ -464,17 +464,141 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
     }
 }
 
+// Asynchronous global -> shared copies (cp.async): data in flight occupy
+// shared memory, not registers.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// One warp's staging area: a ring of three 32-point steps of source data and a
+// double buffer of the first probed slot's key and record, one entry per lane.
+struct WarpStage {
+    float4 pa[3][32];
+    float4 pb[3][32];
+    float pc[3][32];
+    float4 ra[2][32];
+    float4 rb[2][32];
+    float rc[2][32];
+    unsigned long long key[2][32];
+};
+
+// Points of one work item as a software pipeline per lane: step st + 2's point
+// data are copied in while step st + 1's voxel key is computed and its first
+// probe (key and record together) is copied in, while step st's correspondence
+// is resolved and accumulated.  Each lane reads back only the slots it filled,
+// and refills a slot only after it consumed the slot's values.
+template <bool FF>
+__device__ __forceinline__ void linearize_points_staged(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
+                                                        const WorkItem &w, int lane, float acc[kNT], int &inl,
+                                                        WarpStage &S)
+{
+    const float4 *__restrict__ pa = F.pa + w.start;
+    const float4 *__restrict__ pb = F.pb + w.start;
+    const float *__restrict__ pc = F.pc + w.start;
+    const int n = w.count, steps = (n + 31) >> 5;
+    auto issue_points = [&](int st) {
+        const int i = (st << 5) + lane;
+        if (st < steps && i < n) {
+            const int b = st % 3;
+            cp_async16(&S.pa[b][lane], pa + i);
+            cp_async16(&S.pb[b][lane], pb + i);
+            cp_async4(&S.pc[b][lane], pc + i);
+        }
+    };
+    auto issue_probe = [&](const PointSlot &ps, int b) {
+        if (ps.ok) {
+            cp_async8(&S.key[b][lane], m.keys + ps.h);
+            cp_async16(&S.ra[b][lane], &m.rec[ps.h].a);
+            cp_async16(&S.rb[b][lane], &m.rec[ps.h].b);
+            cp_async4(&S.rc[b][lane], &m.rec[ps.h].c.x);
+        }
+    };
+    issue_points(0);
+    cp_async_commit();
+    issue_points(1);
+    cp_async_commit();
+    cp_async_wait<1>();                               // step 0's points
+    PointSlot s;
+    float d[3], x[3];
+    {
+        const float4 A = S.pa[0][lane];
+        s = point_hash<FF>(P, m, A.x, A.y, A.z, d, x);
+        s.ok = s.ok && lane < n;
+        issue_probe(s, 0);
+        cp_async_commit();
+    }
+    for (int st = 0; st < steps; ++st) {
+        // in flight: the points of st + 1, then the probe of st
+        issue_points(st + 2);
+        cp_async_commit();
+        cp_async_wait<1>();                           // all but step st + 2's points
+        PointSlot s1;
+        float d1[3], x1[3];
+        s1.ok = false;
+        if (st + 1 < steps) {
+            const float4 A = S.pa[(st + 1) % 3][lane];
+            s1 = point_hash<FF>(P, m, A.x, A.y, A.z, d1, x1);
+            s1.ok = s1.ok && ((st + 1) << 5) + lane < n;
+            issue_probe(s1, (st + 1) & 1);
+        }
+        cp_async_commit();
+        if (s.ok) {
+            const int b = st & 1;
+            const int slot = resolve_slot(m, s, S.key[b][lane]);
+            if (slot >= 0) {
+                VoxelRec v;
+                if (slot == (int)s.h) {
+                    v.a = S.ra[b][lane];
+                    v.b = S.rb[b][lane];
+                    v.c = make_float4(S.rc[b][lane], 0.f, 0.f, 0.f);
+                } else {
+                    v = load_rec(m.rec + slot);
+                }
+                const int q = st % 3;
+                inl += accumulate_point(acc, P.Rh, S.pa[q][lane], S.pb[q][lane], S.pc[q][lane], v, d, x);
+            }
+        }
+        s = s1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            d[a] = d1[a];
+            x[a] = x1[a];
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // One work item: skipped when every cull chunk it spans is dead (no point of it
 // can find a voxel), otherwise all of its points.
 template <int PTS, bool FF>
 __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
-                                                    const WorkItem &w, int lane, float acc[kNT], int &inl)
+                                                    const WorkItem &w, int lane, float acc[kNT], int &inl,
+                                                    WarpStage *S)
 {
     if (w.count <= 0) return;
     const int c0 = (int)(w.start >> F.cshift), c1 = (int)((w.start + w.count - 1) >> F.cshift);
     const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
     if ((P.cmask & span) == 0u) return;
-    linearize_points<PTS, FF>(P, m, F, w, lane, acc, inl);
+    if constexpr (PTS == 0)
+        linearize_points_staged<FF>(P, m, F, w, lane, acc, inl, *S);
+    else
+        linearize_points<PTS, FF>(P, m, F, w, lane, acc, inl);
 }
 
 template <int BLOCK, int MINB, int PTS, bool FF>
@@ -490,6 +614,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
     constexpr int PW = (int)(sizeof(PoseParam) / 4);
     __shared__ PoseParam sP[NW];
     __shared__ MapDesc sM[NW];
+    __shared__ WarpStage sS[PTS == 0 ? NW : 1];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (;;) {
         // items in list order, each to the next free warp (uneven items cannot
@@ -513,7 +638,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
 #pragma unroll
         for (int j = 0; j < kNT; ++j) acc[j] = 0.f;
         int inl = 0;
-        linearize_warp_item<PTS, FF>(P, m, F, w, lane, acc, inl);
+        linearize_warp_item<PTS, FF>(P, m, F, w, lane, acc, inl, sS + (PTS == 0 ? wib : 0));
         // butterfly: every lane ends with the warp's sums; lane j writes sum j
         double mine = 0.0;
 #pragma unroll
@@ -824,6 +949,18 @@ void launch_variant(const PoseParam *params, const MapDesc *maps, const FrameDes
     case 3: {   // one point per step + prefetch, 128-thread blocks, 4 per SM (no register cap below 128)
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
         k_linearize_f32<128, 4, 1, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+                                                           inl_partials, next_item);
+        break;
+    }
+    case 4: {   // cp.async pipeline (points two steps, probes one step ahead), 128-thread blocks, 5 per SM
+        const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
+        k_linearize_f32<128, 5, 0, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+                                                           inl_partials, next_item);
+        break;
+    }
+    case 5: {   // cp.async pipeline, 128-thread blocks, 6 per SM
+        const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
+        k_linearize_f32<128, 6, 0, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
                                                            inl_partials, next_item);
         break;
     }

@@ -296,7 +296,7 @@ def test_knn_covariances_match_oracle(ctx, single):
     assert np.array_equal(ctx.estimate_covariances(tiny, 10, 1e-3), oracle.covariances(tiny))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_linearize_variants_agree(ctx, variant):
     tg, tcov, src, scov, poses, factors = _ragged_case(seed=45)
     hm = [ctx.build_voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
@@ -349,7 +349,7 @@ def test_autotune_keeps_results(ctx, single):
     poses = np.stack([w.T_target, w.T_source])
     f = vg.make_factors([hm, hm], [hf, hf], [0, 1], [1, 0])
     best, ms = ctx.autotune(f, poses, reps=1)
-    assert ms > 0 and best.linearize_variant in range(4) and best.chunk_points in (1024, 2048, 4096, 8192)
+    assert ms > 0 and best.linearize_variant in range(6) and best.chunk_points in (1024, 2048, 4096, 8192)
     H, b, cost, inl = ctx.linearize(f, poses)
     vm = oracle.voxelmap(w.points_target, cb, w.resolution)
     L = _oracle_factor(vm, w.points_source, ca, w.T_target, w.T_source)
