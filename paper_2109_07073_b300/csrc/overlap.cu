@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
     constexpr int PW = (int)(sizeof(PoseParam) / 4);
     __shared__ PoseParam sP[kSlice];
     __shared__ MapDesc sM;
-    __shared__ int s_kb[6], s_lg, s_smem;   // voxel box, compact table size, staged?
+    __shared__ int s_kb[6], s_lg, s_smem, s_words;   // voxel box, compact table size, staged: 1 table, 2 bitmap
     __shared__ const float4 *s_pa[kSlice];
     __shared__ int s_n[kSlice], s_csh[kSlice], s_nlive[kSlice];
     __shared__ unsigned char s_live[kSlice][kMaxCullChunks];   // live cull chunks of each source, in order
@@ -187,18 +187,20 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
         if (threadIdx.x == 0) {
             sM = maps[pairs[(int64_t)s0 * n_tgt + t].map];
             s_lg = sM.cmeta[0];
-            s_smem = sM.cmeta[1] && s_lg <= kSmemLog2;
+            s_words = sM.cmeta[3];
+            s_smem = sM.cmeta[2] ? 2 : ((sM.cmeta[1] && s_lg <= kSmemLog2) ? 1 : 0);
 #pragma unroll
             for (int j = 0; j < 6; ++j) s_kb[j] = sM.kbox[j];
         }
         __syncthreads();
         if (s_smem) {
             const uint4 *src = (const uint4 *)sM.ckeys;
-            for (int i = threadIdx.x; i < (1 << s_lg) / 4; i += kOvBlock) s_tab4[i] = __ldg(src + i);
+            const int n4 = s_smem == 2 ? (s_words + 3) / 4 : (1 << s_lg) / 4;
+            for (int i = threadIdx.x; i < n4; i += kOvBlock) s_tab4[i] = __ldg(src + i);
         }
         __syncthreads();
         const MapDesc m = sM;
-        const bool smem = s_smem;
+        const int smem = s_smem;
         const uint32_t lg = (uint32_t)s_lg;
         const int ex = s_kb[3] - s_kb[0], ey = s_kb[4] - s_kb[1], ez = s_kb[5] - s_kb[2];
         for (int si = 0; si < ns; ++si) {
@@ -220,7 +222,29 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
                     const float4 A = have[j] ? __ldg(pa + i) : make_float4(0.f, 0.f, 0.f, 0.f);
                     px[j] = A.x; py[j] = A.y; pz[j] = A.z;
                 }
-                if (smem) {
+                if (smem == 2) {
+                    // presence bitmap: box test, then one bit; floors undecided at a face take the exact path
+                    const uint32_t X = (uint32_t)ex + 1u, XY = X * ((uint32_t)ey + 1u);
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        int d[3];
+                        bool dec = true;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            dec &= axis_box(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.koff[a], px[j], py[j],
+                                            pz[j], m.r_h, m.r_l, m.inv_rf, d[a]);
+                        const bool in = (unsigned)d[0] <= (unsigned)ex && (unsigned)d[1] <= (unsigned)ey &&
+                                        (unsigned)d[2] <= (unsigned)ez;
+                        const uint32_t bit = (uint32_t)d[0] + X * (uint32_t)d[1] + XY * (uint32_t)d[2];
+                        const uint32_t word = (have[j] && dec && in) ? s_tab[bit >> 5] : 0xFFFFFFFFu;
+                        hits += ((word >> (bit & 31)) & 1u) ^ 1u;
+                        if (have[j] && !dec) {
+                            int k[3];
+                            hits += point_key_slow(P, m, px[j], py[j], pz[j], k) &&
+                                    probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0;
+                        }
+                    }
+                } else if (smem) {
                     // keys of all points first, then all first probes, then the rare chains
                     uint32_t ck[kPPT], slot[kPPT];
                     int state[kPPT];                    // 0 no, 1 yes, 2 probing, 3 undecided floor

@@ -110,6 +110,11 @@ struct __align__(16) PoseParam {
 // (x, y <= 2046, z <= 1022), so the all-ones word never names a voxel.
 constexpr uint32_t kEmptyCompact = 0xFFFFFFFFu;
 constexpr int kCompactMaxX = 2046, kCompactMaxZ = 1022;
+// Presence bitmap over a map's voxel box (in place of the compact table when
+// it is this small): voxel (dx, dy, dz) relative to the box minimum is bit
+// dx + X (dy + Y dz) of the ckeys words, CLEARED when the voxel exists (the
+// words start as all ones, like an empty compact table).
+constexpr uint32_t kBitmapMaxWords = 32768;
 
 __device__ __forceinline__ uint32_t pack_compact(int dx, int dy, int dz)
 {

@@ -272,10 +272,12 @@ __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDe
     }
 }
 
-// Compact presence table of each map: the compact key of every voxel, inserted
-// into the first 2^lg entries of ckeys (lg = log2 of the smallest power of two
-// >= 4 V, at most the main capacity: load <= 1/4, short probe chains), when the
-// voxel box extent allows it.
+// Presence structure of each map in its ckeys words: a bitmap over the voxel
+// box when the box needs at most min(capacity, kBitmapMaxWords) words
+// (cmeta[2] = 1, cmeta[3] = words); otherwise the compact presence table, the
+// compact key of every voxel inserted into the first 2^lg entries (lg = log2 of
+// the smallest power of two >= 4 V, at most the main capacity: load <= 1/4,
+// short probe chains), when the voxel box extent allows it (cmeta[1] = 1).
 __global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units,
                                 const WorkItem *__restrict__ items, int n_items, BuildScratch scr)
 {
@@ -289,11 +291,27 @@ __global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUni
                         kb[5] - kb[2] <= kCompactMaxZ;
         uint32_t lg = 4;
         while (lg < m.log2cap && (1u << lg) < 4u * nv) ++lg;
+        const uint64_t X = nv > 0 ? (uint64_t)(kb[3] - kb[0] + 1) : 0, Y = nv > 0 ? (uint64_t)(kb[4] - kb[1] + 1) : 0,
+                       Z = nv > 0 ? (uint64_t)(kb[5] - kb[2] + 1) : 0;
+        const uint64_t words = (X * Y * Z + 31) / 32;
+        const bool bitmap = ok && words <= (uint64_t)(m.mask + 1) && words <= kBitmapMaxWords;
         if (w.start == 0 && threadIdx.x == 0) {
             m.cmeta[0] = (int32_t)lg;
-            m.cmeta[1] = ok ? 1 : 0;
+            m.cmeta[1] = (ok && !bitmap) ? 1 : 0;
+            m.cmeta[2] = bitmap ? 1 : 0;
+            m.cmeta[3] = bitmap ? (int32_t)words : 0;
         }
         if (!ok) continue;
+        if (bitmap) {
+            for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
+                if (v >= (int64_t)nv) break;
+                int kx, ky, kz;
+                unpack_key(m.keys[scr.slot_of_vid[u.point_base + v]], kx, ky, kz);
+                const uint64_t bit = (uint64_t)(kx - kb[0]) + X * ((uint64_t)(ky - kb[1]) + Y * (uint64_t)(kz - kb[2]));
+                atomicAnd(m.ckeys + (bit >> 5), ~(1u << (bit & 31)));
+            }
+            continue;
+        }
         const uint32_t cmask = (1u << lg) - 1u;
         for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
             if (v >= (int64_t)nv) break;

@@ -165,6 +165,32 @@ def test_overlap_matrix_bit_exact(ctx, loop_frames, cull):
         ctx.release(int(h))
 
 
+def test_overlap_matrix_presence_structures(ctx):
+    """Targets whose voxel boxes select each presence structure of the overlap
+    matrix: a bitmap over a small box, the compact hash table for a sparse wide
+    box, and the main table for a box too wide for either."""
+    rng = dg.Stream(77)
+    dense = dg.sample_small_scene(rng, 4000)                        # ~20 m box: bitmap
+    wide = np.concatenate([dg.sample_small_scene(rng, 600) + np.float32([dx, dy, 0])
+                           for dx, dy in ((0, 0), (900, 0), (0, 900), (900, 900))]).astype(np.float32)   # compact
+    huge = np.concatenate([dg.sample_small_scene(rng, 600) + np.float32([dx, 0, 0])
+                           for dx in (0, 3000)]).astype(np.float32)                                   # main table
+    clouds = [dense, wide, huge]
+    covs = [oracle.covariances(c) for c in clouds]
+    fr = [ctx.add_frame(c, v) for c, v in zip(clouds, covs)]
+    maps = ctx.build_voxelmaps(fr, 1.0)
+    P = np.stack([dg.identity_pose()] + [dg.random_pose(rng, 3, 0.4) for _ in range(2)])
+    counts = ctx.overlap_matrix(fr, maps, P, P)
+    vms = [oracle.voxelmap(c, v, 1.0) for c, v in zip(clouds, covs)]
+    for si in range(3):
+        for ti in range(3):
+            T = oracle.relative_pose(P[ti], P[si])
+            assert counts[si, ti] == oracle.overlap_count(vms[ti], clouds[si], T), (si, ti)
+    assert counts[0, 1] > 0 and counts[0, 2] > 0
+    for h in list(maps) + fr:
+        ctx.release(int(h))
+
+
 def _ragged_case(seed=41):
     """Several targets, sources of 0, 1, 31, 2047, 2048, 2049, 5000 and 12345 points."""
     rng = dg.Stream(seed)
