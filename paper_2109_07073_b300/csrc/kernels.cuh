@@ -96,7 +96,8 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
 // (pairs[s * n_tgt + t] prepared by launch_prepare_pairs).  One CTA per SM.
 size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt);
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
-                           int n_tgt, unsigned long long *counts, void *scratch, int grid, cudaStream_t st);
+                           int n_tgt, unsigned long long *counts, void *scratch, uint32_t max_cap, int num_sms,
+                           cudaStream_t st);
 
 // out[0] += pairs not culled, out[1] += their source sizes (out zeroed).
 void launch_count_live(const PoseParam *pairs, int64_t n_pairs, const FrameDesc *frames, unsigned long long *out,

@@ -4,6 +4,8 @@
 // proven per-pair error bound; the points that bound cannot decide take the
 // float32-pair transform, and the float64 reference only if that too is
 // undecided (points on voxel faces).
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace vg {
@@ -137,11 +139,12 @@ __global__ void k_overlap_items(const PoseParam *__restrict__ pairs, int n_src, 
     if (live) list[base + __popc(b & ((1u << lane) - 1u))] = (int32_t)v;
 }
 
-__global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam *__restrict__ pairs,
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam *__restrict__ pairs,
                                                                 const MapDesc *__restrict__ maps,
                                                                 const FrameDesc *__restrict__ frames, int n_src,
                                                                 int n_tgt, const int32_t *__restrict__ list,
-                                                                int *__restrict__ hdr,
+                                                                int *__restrict__ hdr, int smem_words,
                                                                 unsigned long long *__restrict__ counts)
 {
     extern __shared__ uint4 s_tab4[];
@@ -166,9 +169,8 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
         const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
         const int s0 = sl * kSlice, ns = min(n_src, s0 + kSlice) - s0;
         // the slice's pair parameters (one warp per source) and the target's table
-        {
-            const int wib = threadIdx.x >> 5;
-            if (wib < ns) {
+        for (int wib = threadIdx.x >> 5; wib < ns; wib += BLOCK / 32) {
+            {
                 const uint32_t *src = (const uint32_t *)(pairs + (int64_t)(s0 + wib) * n_tgt + t);
                 uint32_t *dst = (uint32_t *)(sP + wib);
                 for (int j = lane; j < PW; j += 32) dst[j] = __ldg(src + j);
@@ -188,7 +190,8 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
             sM = maps[pairs[(int64_t)s0 * n_tgt + t].map];
             s_lg = sM.cmeta[0];
             s_words = sM.cmeta[3];
-            s_smem = sM.cmeta[2] ? 2 : ((sM.cmeta[1] && s_lg <= kSmemLog2) ? 1 : 0);
+            s_smem = (sM.cmeta[2] && s_words <= smem_words) ? 2
+                                                              : ((sM.cmeta[1] && (1 << s_lg) <= smem_words) ? 1 : 0);
 #pragma unroll
             for (int j = 0; j < 6; ++j) s_kb[j] = sM.kbox[j];
         }
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
         if (s_smem) {
             const uint4 *src = (const uint4 *)sM.ckeys;
             const int n4 = s_smem == 2 ? (s_words + 3) / 4 : (1 << s_lg) / 4;
-            for (int i = threadIdx.x; i < n4; i += kOvBlock) s_tab4[i] = __ldg(src + i);
+            for (int i = threadIdx.x; i < n4; i += BLOCK) s_tab4[i] = __ldg(src + i);
         }
         __syncthreads();
         const MapDesc m = sM;
@@ -211,12 +214,12 @@ __global__ void __launch_bounds__(kOvBlock, 1) k_overlap_matrix(const PoseParam 
             const int nv = s_nlive[si] << csh;          // points of the live chunks, end to end
             const unsigned char *live = s_live[si];
             unsigned int hits = 0;
-            for (int base = 0; base < nv; base += kOvBlock * kPPT) {
+            for (int base = 0; base < nv; base += BLOCK * kPPT) {
                 float px[kPPT], py[kPPT], pz[kPPT];
                 bool have[kPPT];
 #pragma unroll
                 for (int j = 0; j < kPPT; ++j) {
-                    const int vi = base + j * kOvBlock + threadIdx.x;
+                    const int vi = base + j * BLOCK + threadIdx.x;
                     const int i = vi < nv ? ((int)live[vi >> csh] << csh) + (vi & ((1 << csh) - 1)) : n;
                     have[j] = i < n;
                     const float4 A = have[j] ? __ldg(pa + i) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -397,7 +400,8 @@ size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt)
 }
 
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
-                           int n_tgt, unsigned long long *counts, void *scratch, int grid, cudaStream_t st)
+                           int n_tgt, unsigned long long *counts, void *scratch, uint32_t max_cap, int num_sms,
+                           cudaStream_t st)
 {
     if (n_src <= 0 || n_tgt <= 0) return;
     int *hdr = (int *)scratch;
@@ -405,9 +409,20 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
     const int64_t total = (int64_t)((n_src + kSlice - 1) / kSlice) * n_tgt;
     cudaMemsetAsync(hdr, 0, 4 * sizeof(int), st);
     k_overlap_items<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pairs, n_src, n_tgt, list, hdr);
-    const int smem = (1 << kSmemLog2) * 4;
-    cudaFuncSetAttribute(k_overlap_matrix, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_overlap_matrix<<<grid, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt, list, hdr, counts);
+    // every target's presence structure fits in max_cap words: small tables run
+    // four 256-thread CTAs per SM, each with its own item and staged table
+    if (max_cap <= 12288) {
+        const int words = (int)std::max<uint32_t>(max_cap, 4);
+        const int smem = words * 4;
+        cudaFuncSetAttribute(k_overlap_matrix<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_overlap_matrix<256, 4><<<num_sms * 4, 256, smem, st>>>(pairs, maps, frames, n_src, n_tgt, list, hdr,
+                                                                  words, counts);
+    } else {
+        const int words = 1 << kSmemLog2, smem = words * 4;
+        cudaFuncSetAttribute(k_overlap_matrix<kOvBlock, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_overlap_matrix<kOvBlock, 1><<<num_sms, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt, list, hdr,
+                                                                     words, counts);
+    }
 }
 
 void launch_correspondences(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,
