@@ -404,10 +404,20 @@ vgicp_status vgicp_server_put_frame(vgicp_server *server, int64_t key, const flo
  * return VGICP_ERR_NOT_FOUND and queue nothing.  Thread-safe. */
 vgicp_status vgicp_server_submit(vgicp_server *server, const vgicp_request *req, int64_t *ticket);
 
+/* Queue n requests at once (all or none: any invalid request or unknown key
+ * fails the call before anything is queued); tickets[k] for reqs[k]. */
+vgicp_status vgicp_server_submit_batch(vgicp_server *server, const vgicp_request *reqs, int64_t n, int64_t *tickets);
+
 /* Wait up to timeout_s seconds (< 0: no limit) for a request; on VGICP_OK *out
  * holds its result (whose own status may be an error) and the ticket is
  * retired.  VGICP_ERR_TIMEOUT leaves the ticket valid.  Thread-safe. */
 vgicp_status vgicp_server_wait(vgicp_server *server, int64_t ticket, double timeout_s, vgicp_result *out);
+
+/* vgicp_server_wait() for n tickets in order, results to out[0..n).  On
+ * VGICP_ERR_TIMEOUT the tickets already returned are retired, the rest stay
+ * valid; an unknown ticket fails the call before anything is retired. */
+vgicp_status vgicp_server_wait_batch(vgicp_server *server, const int64_t *tickets, int64_t n, double timeout_s,
+                                     vgicp_result *out);
 
 /* Counters and latency quantiles since creation or the last reset. */
 vgicp_status vgicp_server_stats(vgicp_server *server, vgicp_server_counters *out);

@@ -35,7 +35,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc", "vgicp_autotune", "vgicp_overlap_matrix_work", "vgicp_set_lane",
            "vgicp_overlap_pairs", "vgicp_server_create", "vgicp_server_destroy", "vgicp_server_put_map",
            "vgicp_server_put_frame", "vgicp_server_submit", "vgicp_server_wait", "vgicp_server_stats",
-           "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_plan_create", "vgicp_plan_linearize",
+           "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_server_submit_batch", "vgicp_server_wait_batch", "vgicp_plan_create", "vgicp_plan_linearize",
            "vgicp_plan_info", "vgicp_plan_destroy"]
 VGICP_REQ_LINEARIZE, VGICP_REQ_OVERLAP = 0, 1
 
@@ -129,6 +129,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_server_put_map": [vp, i64, vp, vp, i64, f64],
         "vgicp_server_put_frame": [vp, i64, vp, vp, i64],
         "vgicp_server_submit": [vp, C.POINTER(Request), C.POINTER(i64)],
+        "vgicp_server_submit_batch": [vp, vp, i64, vp],
+        "vgicp_server_wait_batch": [vp, vp, i64, f64, vp],
         "vgicp_server_wait": [vp, i64, f64, C.POINTER(Result)],
         "vgicp_server_stats": [vp, C.POINTER(ServerCounters)],
         "vgicp_server_reset_stats": [vp],
@@ -531,6 +533,32 @@ def vgicp_server_submit(server, kind: int, target: int, source: int, T_target_so
     t = C.c_int64()
     _scheck(server, load().vgicp_server_submit(server, C.byref(r), C.byref(t)))
     return t.value
+
+
+def vgicp_server_submit_batch(server, kinds, targets, sources, T) -> np.ndarray:
+    """Queue len(kinds) requests at once; T (n, 3, 4) or (n, 12).  Returns the tickets."""
+    k = np.ascontiguousarray(kinds, np.int32)
+    n = k.shape[0]
+    P = _pose12(T)
+    if P.shape != (n, 12):
+        raise ValueError("T must hold 12 values per request")
+    reqs = (Request * n)()
+    arr = np.frombuffer(reqs, dtype=np.dtype([("kind", np.int32), ("reserved", np.int32), ("target", np.int64),
+                                              ("source", np.int64), ("T", np.float64, 12)]), count=n)
+    arr["kind"], arr["reserved"] = k, 0
+    arr["target"], arr["source"] = np.asarray(targets, np.int64), np.asarray(sources, np.int64)
+    arr["T"] = P
+    tickets = np.zeros(n, np.int64)
+    _scheck(server, load().vgicp_server_submit_batch(server, C.cast(reqs, C.c_void_p), n, _ptr(tickets)))
+    return tickets
+
+
+def vgicp_server_wait_batch(server, tickets, timeout_s: float = -1.0):
+    """Results of many tickets at once (a ctypes array of Result, in ticket order)."""
+    t = np.ascontiguousarray(tickets, np.int64)
+    out = (Result * t.shape[0])()
+    _scheck(server, load().vgicp_server_wait_batch(server, _ptr(t), t.shape[0], timeout_s, C.cast(out, C.c_void_p)))
+    return out
 
 
 def vgicp_server_wait(server, ticket: int, timeout_s: float = -1.0) -> Result:

@@ -195,21 +195,31 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
     std::vector<vgicp_map_t> otgt;
     std::vector<double> oT;
     vgicp_set_lane(s->ctx, li, L.stream);
-    for (int64_t t : tickets) {
-        vgicp_request r;
-        Resident *m, *f;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            r = s->reqs[t].req;
-            m = &s->objs[tag(r.target, true)];
-            f = &s->objs[tag(r.source, false)];
+    std::vector<vgicp_request> rq(tickets.size());
+    std::vector<Resident *> om(tickets.size()), of(tickets.size());
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t k = 0; k < tickets.size(); ++k) {
+            rq[k] = s->reqs[tickets[k]].req;
+            om[k] = &s->objs[tag(rq[k].target, true)];
+            of[k] = &s->objs[tag(rq[k].source, false)];
         }
-        vgicp_status st = admit(s, *m);
-        if (st == VGICP_OK) {
-            { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
-            st = admit(s, *f);
-            std::lock_guard<std::mutex> lk(s->mu);
-            m->pins--;
+    }
+    fac.reserve(tickets.size());
+    poses.reserve(12 * (tickets.size() + 1));
+    for (size_t k = 0; k < tickets.size(); ++k) {
+        const int64_t t = tickets[k];
+        const vgicp_request &r = rq[k];
+        Resident *m = om[k], *f = of[k];
+        vgicp_status st = VGICP_OK;
+        if (m->handle < 0 || f->handle < 0) {      // admission (scheduler thread owns the handles)
+            st = admit(s, *m);
+            if (st == VGICP_OK) {
+                { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
+                st = admit(s, *f);
+                std::lock_guard<std::mutex> lk(s->mu);
+                m->pins--;
+            }
         }
         std::lock_guard<std::mutex> lk(s->mu);
         if (st == VGICP_ERR_BUDGET) {
@@ -483,6 +493,38 @@ vgicp_status vgicp_server_submit(vgicp_server *s, const vgicp_request *req, int6
     return VGICP_OK;
 }
 
+vgicp_status vgicp_server_submit_batch(vgicp_server *s, const vgicp_request *reqs, int64_t n, int64_t *tickets)
+{
+    if (!s || n < 0 || (n > 0 && (!reqs || !tickets))) return VGICP_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < n; ++k) {
+        const vgicp_request *req = reqs + k;
+        if (req->kind != VGICP_REQ_LINEARIZE && req->kind != VGICP_REQ_OVERLAP) return VGICP_ERR_INVALID_ARG;
+        for (int i = 0; i < 12; ++i)
+            if (!(req->T_target_source[i] - req->T_target_source[i] == 0.0)) return VGICP_ERR_INVALID_ARG;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (int64_t k = 0; k < n; ++k)
+            if (!s->objs.count(tag(reqs[k].target, true)) || !s->objs.count(tag(reqs[k].source, false))) {
+                s->err = "request names an unregistered key";
+                return VGICP_ERR_NOT_FOUND;
+            }
+        const auto now = Clock::now();
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t t = s->next_ticket++;
+            Pending &p = s->reqs[t];
+            p.req = reqs[k];
+            p.t0 = now;
+            std::memset(&p.res, 0, sizeof(p.res));
+            s->pending.push_back(t);
+            tickets[k] = t;
+        }
+        s->submitted += n;
+    }
+    s->cv_work.notify_all();
+    return VGICP_OK;
+}
+
 vgicp_status vgicp_server_wait(vgicp_server *s, int64_t ticket, double timeout_s, vgicp_result *out)
 {
     if (!s || !out) return VGICP_ERR_INVALID_ARG;
@@ -498,6 +540,28 @@ vgicp_status vgicp_server_wait(vgicp_server *s, int64_t ticket, double timeout_s
     }
     *out = it->second.res;
     s->reqs.erase(it);
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_server_wait_batch(vgicp_server *s, const int64_t *tickets, int64_t n, double timeout_s,
+                                     vgicp_result *out)
+{
+    if (!s || n < 0 || (n > 0 && (!tickets || !out))) return VGICP_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (int64_t k = 0; k < n; ++k)
+        if (!s->reqs.count(tickets[k])) return VGICP_ERR_NOT_FOUND;
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(timeout_s < 0 ? 1e9 : timeout_s));
+    for (int64_t k = 0; k < n; ++k) {
+        auto it = s->reqs.find(tickets[k]);
+        while (!it->second.done) {
+            if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !it->second.done)
+                return VGICP_ERR_TIMEOUT;    // tickets before k are retired, k and later stay valid
+            it = s->reqs.find(tickets[k]);
+        }
+        out[k] = it->second.res;
+        s->reqs.erase(it);
+    }
     return VGICP_OK;
 }
 

@@ -71,7 +71,12 @@ def serve(maps, frames, reqs, clients=4, **opts):
 
         def client(j):
             mine = list(range(j, len(reqs), clients))
-            tickets = [srv.submit(reqs[i][0], reqs[i][1], reqs[i][2], reqs[i][3]) for i in mine]
+            if j % 2:      # odd clients queue all their requests in one call
+                tickets = srv.submit_batch([reqs[i][0] for i in mine], [reqs[i][1] for i in mine],
+                                           [reqs[i][2] for i in mine], np.stack([reqs[i][3] for i in mine]))
+                tickets = [int(t) for t in tickets]
+            else:
+                tickets = [srv.submit(reqs[i][0], reqs[i][1], reqs[i][2], reqs[i][3]) for i in mine]
             for i, tk in zip(mine, tickets):
                 res[i] = srv.wait(tk, 120.0)
         th = [threading.Thread(target=client, args=(j,)) for j in range(clients)]
