@@ -521,7 +521,9 @@ def run_serving(a):
                          "point_correspondences_per_s": pts / wall, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
                          "max_ms": st.max_ms, "mean_batch_requests": st.mean_batch_requests,
                          "evictions": st.evictions, "admissions": st.admissions,
-                         "resident_gb": st.resident_bytes / 2**30})
+                         "resident_gb": st.resident_bytes / 2**30, "host_launch_ms": st.host_launch_ms,
+                         "host_finish_ms": st.host_finish_ms, "device_ms": st.device_ms, "wall_ms": wall * 1e3,
+                         "host_admit_ms": st.host_admit_ms, "host_enqueue_ms": st.host_enqueue_ms})
             for rate in [float(x) for x in a.serving_rates.split(",")]:
                 gaps = -np.log(1.0 - rng.uniform(n_req)) / rate      # exponential inter-arrival times
                 arrive = np.cumsum(gaps)

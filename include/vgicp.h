@@ -313,6 +313,11 @@ vgicp_status vgicp_estimate_covariances(vgicp_ctx *ctx, const float *points, int
 /* Release a map or frame handle and its device memory. */
 vgicp_status vgicp_release(vgicp_ctx *ctx, int64_t handle);
 
+/* Device bytes a handle holds: a frame of n points (is_map = 0) or a voxelmap
+ * built from n points (is_map = 1; building it also needs the n-point frame
+ * it is built from).  For admission control under hbm_budget_bytes. */
+vgicp_status vgicp_memory_estimate(vgicp_ctx *ctx, int64_t n, int32_t is_map, int64_t *bytes);
+
 /* Device bytes currently held by handles of this context. */
 vgicp_status vgicp_memory_in_use(vgicp_ctx *ctx, int64_t *bytes);
 
@@ -377,6 +382,11 @@ typedef struct {
     int64_t resident_bytes;      /* device bytes held by resident maps and frames */
     double mean_batch_requests;
     double p50_ms, p99_ms, max_ms; /* latency quantiles of completed requests */
+    double host_launch_ms;       /* scheduler time spent admitting and launching batches */
+    double host_finish_ms;       /* scheduler time spent handing results out */
+    double device_ms;            /* device time of the batches (event-timed on each lane's stream) */
+    double host_admit_ms;        /* part of host_launch_ms spent making objects resident */
+    double host_enqueue_ms;      /* part of host_launch_ms spent in the batched library calls */
 } vgicp_server_counters;
 
 /* Create a server on the current CUDA device.  opt and kernel_opt (kernel

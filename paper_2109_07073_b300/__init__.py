@@ -36,7 +36,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_overlap_pairs", "vgicp_server_create", "vgicp_server_destroy", "vgicp_server_put_map",
            "vgicp_server_put_frame", "vgicp_server_submit", "vgicp_server_wait", "vgicp_server_stats",
            "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_server_submit_batch", "vgicp_server_wait_batch", "vgicp_plan_create", "vgicp_plan_linearize",
-           "vgicp_plan_info", "vgicp_plan_destroy"]
+           "vgicp_plan_info", "vgicp_plan_destroy", "vgicp_memory_estimate"]
 VGICP_REQ_LINEARIZE, VGICP_REQ_OVERLAP = 0, 1
 
 
@@ -76,7 +76,8 @@ class ServerCounters(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("batches", C.c_int64),
                 ("admissions", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_int64),
                 ("mean_batch_requests", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
-                ("max_ms", C.c_double)]
+                ("max_ms", C.c_double), ("host_launch_ms", C.c_double), ("host_finish_ms", C.c_double),
+                ("device_ms", C.c_double), ("host_admit_ms", C.c_double), ("host_enqueue_ms", C.c_double)]
 
 
 FACTOR_DTYPE = np.dtype([("target", np.int64), ("source", np.int64), ("target_pose", np.int32),
@@ -119,6 +120,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_estimate_covariances": [vp, vp, i64, i32, f64, vp, C.c_int],
         "vgicp_release": [vp, i64],
         "vgicp_memory_in_use": [vp, C.POINTER(i64)],
+        "vgicp_memory_estimate": [vp, i64, i32, C.POINTER(i64)],
         "vgicp_kernel_launches": [vp, C.POINTER(i64)],
         "vgicp_plan_create": [vp, vp, i64, i64, C.POINTER(vp)],
         "vgicp_plan_linearize": [vp, vp, vp, vp, vp, vp, vp, C.c_int],
@@ -439,6 +441,12 @@ def vgicp_release(ctx, handle: int):
 def vgicp_memory_in_use(ctx) -> int:
     v = C.c_int64()
     _check(ctx, load().vgicp_memory_in_use(ctx, C.byref(v)))
+    return v.value
+
+
+def vgicp_memory_estimate(ctx, n: int, is_map: bool) -> int:
+    v = C.c_int64()
+    _check(ctx, load().vgicp_memory_estimate(ctx, int(n), int(bool(is_map)), C.byref(v)))
     return v.value
 
 

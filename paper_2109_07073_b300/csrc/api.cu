@@ -60,6 +60,15 @@ struct Lane {
     Buf ws_fetch, ws_items;
     Plan plan;
     int64_t last_matrix_pairs = 0;   // pairs of the last overlap matrix (params kept in ws_pairs)
+    // pinned staging for host -> device copies: two arenas used in turn, each
+    // with an event after its latest copy, so copies never wait for the stream
+    struct Arena {
+        char *p = nullptr;
+        size_t cap = 0, off = 0;
+        cudaEvent_t ev = nullptr;
+        bool pending = false;
+    } arena[2];
+    int arena_cur = 0;
 };
 
 }  // namespace
@@ -142,12 +151,50 @@ void free_buf(vgicp_ctx *ctx, Buf &b)
     b.bytes = 0;
 }
 
+// Host -> device copy in stream order that returns without waiting for the
+// stream: the bytes go through a pinned staging arena of the lane (a copy from
+// pageable memory may first wait for the work queued before it).  An arena is
+// reused only after every copy from it has run; very large copies go direct.
+constexpr size_t kArenaMaxCopy = (size_t)64 << 20;
+
+vgicp_status h2d(vgicp_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    if (bytes == 0) return VGICP_OK;
+    if (bytes > kArenaMaxCopy) {
+        CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, LN.stream));
+        return VGICP_OK;
+    }
+    Lane::Arena *A = &LN.arena[LN.arena_cur];
+    if (A->off + bytes > A->cap) {
+        LN.arena_cur ^= 1;
+        A = &LN.arena[LN.arena_cur];
+        if (A->pending) CU(cudaEventSynchronize(A->ev));
+        A->pending = false;
+        A->off = 0;
+        if (A->cap < bytes) {
+            if (A->p) CU(cudaFreeHost(A->p));
+            A->p = nullptr;
+            A->cap = 0;
+            const size_t cap = std::max<size_t>(std::max<size_t>(bytes * 2, (size_t)4 << 20), A->cap * 2);
+            CU(cudaMallocHost((void **)&A->p, cap));
+            A->cap = cap;
+        }
+        if (!A->ev) CU(cudaEventCreateWithFlags(&A->ev, cudaEventDisableTiming));
+    }
+    char *stage = A->p + A->off;
+    A->off = (A->off + bytes + 255) & ~(size_t)255;
+    std::memcpy(stage, src, bytes);
+    CU(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, LN.stream));
+    CU(cudaEventRecord(A->ev, LN.stream));
+    A->pending = true;
+    return VGICP_OK;
+}
+
 template <class T>
 vgicp_status upload(vgicp_ctx *ctx, Buf &b, const T *src, size_t count)
 {
     TRY(ensure(ctx, b, count * sizeof(T)));
-    if (count) CU(cudaMemcpyAsync(b.p, src, count * sizeof(T), cudaMemcpyHostToDevice, LN.stream));
-    return VGICP_OK;
+    return h2d(ctx, b.p, src, count * sizeof(T));
 }
 
 inline int64_t make_handle(uint32_t idx, uint32_t gen) { return ((int64_t)gen << 32) | (int64_t)idx; }
@@ -220,12 +267,16 @@ vgicp_status budget_check(vgicp_ctx *ctx, int64_t extra)
 
 vgicp_status put_frame_desc(vgicp_ctx *ctx, uint32_t idx)
 {
-    CU(cudaMemcpyAsync(ctx->d_frames + idx, &ctx->h_frames[idx], sizeof(FrameDesc), cudaMemcpyHostToDevice,
-                       LN.stream));
-    return VGICP_OK;
+    return h2d(ctx, ctx->d_frames + idx, &ctx->h_frames[idx], sizeof(FrameDesc));
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device bytes of a frame of n points: pa, pb, pc, statistics, chunk boxes.
+size_t frame_bytes(int64_t n)
+{
+    return align256((size_t)n * 16) * 2 + align256((size_t)n * 4) + 256 + 1024;
+}
 
 // Allocate and fill a frame from device-resident points / covariances.
 vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, int64_t n, uint32_t *out_idx)
@@ -260,7 +311,7 @@ vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, 
     // statistics start at: zero maxima of |c| and |p|, +inf minima, -inf maxima
     static const uint32_t init[kStatCount] = {0, 0, 0, 0, kOrderedPosInf, kOrderedPosInf, kOrderedPosInf,
                                               kOrderedNegInf, kOrderedNegInf, kOrderedNegInf};
-    CU(cudaMemcpyAsync(base + o_st, init, sizeof(init), cudaMemcpyHostToDevice, LN.stream));
+    TRY(h2d(ctx, base + o_st, init, sizeof(init)));
     launch_frame_pack(d_pts, d_cov, n, (float4 *)f.pa, (float4 *)f.pb, (float *)f.pc, (float *)f.stats, LN.stream);
     launch_chunk_boxes(f.pa, n, f.cshift, f.nchunks, (float *)f.cbox, LN.stream);
     ctx->launches += n > 0 ? 2 : 0;
@@ -560,6 +611,10 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
         for (Buf *b : bufs) free_buf(ctx, *b);
         const cudaError_t e2 = cudaStreamSynchronize(LN.stream);
         if (e == cudaSuccess) e = e2;
+        for (Lane::Arena &A : LN.arena) {
+            if (A.p) cudaFreeHost(A.p);
+            if (A.ev) cudaEventDestroy(A.ev);
+        }
         if (LN.own_stream) cudaStreamDestroy(LN.own_stream);
     }
     delete ctx;
@@ -620,8 +675,8 @@ static vgicp_status stage_inputs(vgicp_ctx *ctx, const float *points, const floa
     const size_t pb = align256((size_t)n * 12), cb = covs ? (size_t)n * 24 : 0;
     TRY(ensure(ctx, LN.ws_stage, pb + cb));
     char *base = (char *)LN.ws_stage.p;
-    if (n) CU(cudaMemcpyAsync(base, points, (size_t)n * 12, cudaMemcpyHostToDevice, LN.stream));
-    if (covs && n) CU(cudaMemcpyAsync(base + pb, covs, (size_t)n * 24, cudaMemcpyHostToDevice, LN.stream));
+    TRY(h2d(ctx, base, points, (size_t)n * 12));
+    if (covs) TRY(h2d(ctx, base + pb, covs, (size_t)n * 24));
     *d_pts = (const float *)base;
     if (d_cov) *d_cov = covs ? (const float *)(base + pb) : nullptr;
     return VGICP_OK;
@@ -1220,7 +1275,7 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
         if (!std::isfinite(poses_tgt[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
     TRY(upload(ctx, LN.ws_poses, poses_src, (size_t)n_src * 12));
     TRY(ensure(ctx, LN.ws_stage, (size_t)n_tgt * 12 * 8));
-    CU(cudaMemcpyAsync(LN.ws_stage.p, poses_tgt, (size_t)n_tgt * 12 * 8, cudaMemcpyHostToDevice, LN.stream));
+    TRY(h2d(ctx, LN.ws_stage.p, poses_tgt, (size_t)n_tgt * 12 * 8));
     TRY(upload(ctx, LN.ws_fidx, fidx.data(), fidx.size()));
     TRY(upload(ctx, LN.ws_midx, midx.data(), midx.size()));
     TRY(ensure(ctx, LN.ws_pairs, (size_t)n_pairs * sizeof(PoseParam)));
@@ -1395,6 +1450,14 @@ vgicp_status vgicp_release(vgicp_ctx *ctx, int64_t handle)
     o->gen = gen;
     ctx->free_idx.push_back(idx);
     LN.plan.key.clear();   // a cached work list may name this handle
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_memory_estimate(vgicp_ctx *ctx, int64_t n, int32_t is_map, int64_t *bytes)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (!bytes || n < 0) return fail(ctx, VGICP_ERR_INVALID_ARG, "memory_estimate: bad arguments");
+    *bytes = is_map ? (int64_t)map_bytes(map_capacity(n)) : (int64_t)frame_bytes(n);
     return VGICP_OK;
 }
 

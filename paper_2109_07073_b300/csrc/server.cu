@@ -23,6 +23,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -43,6 +44,7 @@ struct Resident {
     double r = 0.0;
     int64_t handle = -1;            // device handle while resident
     uint64_t last_use = 0;
+    int64_t key = 0;                // tagged key (position in the LRU order: (last_use, key))
     int pins = 0;                   // batches in flight that use it
 };
 
@@ -66,6 +68,7 @@ struct LaneState {
     int64_t *hi = nullptr, *hcount = nullptr;
     int64_t cap = 0;
     vgicp_status status = VGICP_OK;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // device time of the batch
 };
 
 }  // namespace
@@ -78,6 +81,7 @@ struct vgicp_server {
     std::condition_variable cv_work, cv_done;
     bool stop = false;
     std::unordered_map<int64_t, Resident> objs;   // tagged key -> object (references stay valid)
+    std::set<std::pair<uint64_t, int64_t>> lru;   // resident objects by (last use, tagged key)
     std::deque<int64_t> pending;
     std::unordered_map<int64_t, Pending> reqs;
     int64_t next_ticket = 1;
@@ -86,6 +90,7 @@ struct vgicp_server {
     LaneState lanes[4];
     std::vector<double> lat_ms;
     int64_t resident_bytes = 0;
+    double host_launch_ms = 0.0, host_finish_ms = 0.0, device_ms = 0.0, host_admit_ms = 0.0, host_enqueue_ms = 0.0;
     int64_t submitted = 0, completed = 0, batches = 0, admissions = 0, evictions = 0, batch_requests = 0;
     std::string err;
 };
@@ -111,9 +116,13 @@ bool evict_one(vgicp_server *s)
     Resident *best = nullptr;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        for (auto &kv : s->objs) {
-            Resident &o = kv.second;
-            if (o.handle >= 0 && o.pins == 0 && (!best || o.last_use < best->last_use)) best = &o;
+        for (auto it = s->lru.begin(); it != s->lru.end(); ++it) {   // pinned objects are few: skip them
+            Resident &o = s->objs[it->second];
+            if (o.pins == 0) {
+                best = &o;
+                s->lru.erase(it);
+                break;
+            }
         }
         if (!best) return false;
         ++s->evictions;
@@ -128,6 +137,14 @@ bool evict_one(vgicp_server *s)
 vgicp_status admit(vgicp_server *s, Resident &o)
 {
     if (o.handle >= 0) return VGICP_OK;
+    if (s->opt.hbm_budget_bytes > 0) {
+        // make room for the estimate first, so a failed attempt (and its copy) is rare
+        int64_t need = 0, used = 0, fb = 0;
+        vgicp_memory_estimate(s->ctx, o.n, o.is_map ? 1 : 0, &need);
+        if (o.is_map) vgicp_memory_estimate(s->ctx, o.n, 0, &fb);
+        vgicp_memory_in_use(s->ctx, &used);
+        while (used + need + fb > s->opt.hbm_budget_bytes && evict_one(s)) vgicp_memory_in_use(s->ctx, &used);
+    }
     for (;;) {
         vgicp_status st;
         int64_t h = -1;
@@ -144,6 +161,8 @@ vgicp_status admit(vgicp_server *s, Resident &o)
         if (st == VGICP_OK) {
             o.handle = h;
             std::lock_guard<std::mutex> lk(s->mu);
+            o.last_use = ++s->clock;
+            s->lru.insert({o.last_use, o.key});
             ++s->admissions;
             return VGICP_OK;
         }
@@ -207,12 +226,14 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
     }
     fac.reserve(tickets.size());
     poses.reserve(12 * (tickets.size() + 1));
+    double admit_ms = 0.0;
     for (size_t k = 0; k < tickets.size(); ++k) {
         const int64_t t = tickets[k];
         const vgicp_request &r = rq[k];
         Resident *m = om[k], *f = of[k];
         vgicp_status st = VGICP_OK;
         if (m->handle < 0 || f->handle < 0) {      // admission (scheduler thread owns the handles)
+            const auto ta = Clock::now();
             st = admit(s, *m);
             if (st == VGICP_OK) {
                 { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
@@ -220,6 +241,7 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
                 std::lock_guard<std::mutex> lk(s->mu);
                 m->pins--;
             }
+            admit_ms += std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
         }
         std::lock_guard<std::mutex> lk(s->mu);
         if (st == VGICP_ERR_BUDGET) {
@@ -232,7 +254,11 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
         }
         m->pins++;
         f->pins++;
-        m->last_use = f->last_use = ++s->clock;
+        for (Resident *o : {m, f}) {
+            s->lru.erase({o->last_use, o->key});
+            o->last_use = ++s->clock;
+            s->lru.insert({o->last_use, o->key});
+        }
         L.pinned.push_back(tag(r.target, true));
         L.pinned.push_back(tag(r.source, false));
         if (r.kind == VGICP_REQ_LINEARIZE) {
@@ -252,6 +278,8 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
         }
     }
     const size_t nf = fac.size(), no = osrc.size();
+    const auto te = Clock::now();
+    if (nf + no) cudaEventRecord(L.ev0, L.stream);
     vgicp_status st = ensure_lane_buffers(L, (int64_t)std::max<size_t>(std::max(nf, no), 1));
     if (st == VGICP_OK && nf)
         st = vgicp_linearize(s->ctx, fac.data(), (int64_t)nf, poses.data(), (int64_t)(poses.size() / 12), L.dH, L.db,
@@ -267,15 +295,19 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
     }
     if (st == VGICP_OK && no) cudaMemcpyAsync(L.hcount, L.dcount, no * 8, cudaMemcpyDeviceToHost, L.stream);
     L.status = st;
+    if (nf + no) cudaEventRecord(L.ev1, L.stream);
     L.finished.store(false);
     if (nf + no && cudaLaunchHostFunc(L.stream, lane_done, &L.cb) != cudaSuccess) {
         cudaStreamSynchronize(L.stream);
         L.finished.store(true);
     }
+    const double enq_ms = std::chrono::duration<double, std::milli>(Clock::now() - te).count();
     int64_t bytes = 0;
     vgicp_memory_in_use(s->ctx, &bytes);
     std::lock_guard<std::mutex> lk(s->mu);
     s->resident_bytes = bytes;
+    s->host_admit_ms += admit_ms;
+    s->host_enqueue_ms += enq_ms;
     return deferred;
 }
 
@@ -312,6 +344,8 @@ void finish_batch(vgicp_server *s, int li)   // mutex held
         s->lat_ms.push_back(p.res.latency_ms);
     }
     for (int64_t k : L.pinned) s->objs[k].pins--;
+    float gms = 0.f;
+    if (cudaEventElapsedTime(&gms, L.ev0, L.ev1) == cudaSuccess) s->device_ms += gms;
     s->completed += (int64_t)(L.lin.size() + L.ovl.size());
     ++s->batches;
     s->batch_requests += (int64_t)(L.lin.size() + L.ovl.size());
@@ -325,7 +359,9 @@ void scheduler(vgicp_server *s)
         bool harvested = false;
         for (int li = 0; li < s->nl; ++li)
             if (s->lanes[li].busy && s->lanes[li].finished.load()) {
+                const auto tf = Clock::now();
                 finish_batch(s, li);
+                s->host_finish_ms += std::chrono::duration<double, std::milli>(Clock::now() - tf).count();
                 harvested = true;
             }
         if (harvested) s->cv_done.notify_all();
@@ -350,8 +386,11 @@ void scheduler(vgicp_server *s)
             LaneState &L = s->lanes[free_lane];
             L.busy = true;
             lk.unlock();
+            const auto tl = Clock::now();
             std::vector<int64_t> deferred = launch_batch(s, free_lane, take);
+            const double dl = std::chrono::duration<double, std::milli>(Clock::now() - tl).count();
             lk.lock();
+            s->host_launch_ms += dl;
             for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) s->pending.push_front(*it);
             if (L.lin.empty() && L.ovl.empty()) {
                 L.busy = false;
@@ -380,6 +419,7 @@ vgicp_status put(vgicp_server *s, int64_t key, bool is_map, const float *pts, co
     if (is_map && !(r > 0.0 && r < 1e30)) return VGICP_ERR_INVALID_ARG;
     Resident o;
     o.is_map = is_map;
+    o.key = tag(key, is_map);
     o.pts.assign(pts, pts + 3 * n);
     o.covs.assign(covs, covs + 6 * n);
     o.n = n;
@@ -424,6 +464,8 @@ vgicp_status vgicp_server_create(vgicp_server **out, const vgicp_server_options 
     }
     for (int li = 0; li < s->nl; ++li) {
         s->lanes[li].cb = {s, li};
+        cudaEventCreate(&s->lanes[li].ev0);
+        cudaEventCreate(&s->lanes[li].ev1);
         if (cudaStreamCreateWithFlags(&s->lanes[li].stream, cudaStreamNonBlocking) != cudaSuccess) {
             vgicp_destroy(s->ctx);
             delete s;
@@ -452,6 +494,8 @@ vgicp_status vgicp_server_destroy(vgicp_server *s)
         cudaFree(L.dH); cudaFree(L.db); cudaFree(L.dc); cudaFree(L.di); cudaFree(L.dcount);
         cudaFreeHost(L.hH); cudaFreeHost(L.hb); cudaFreeHost(L.hc); cudaFreeHost(L.hi); cudaFreeHost(L.hcount);
         cudaStreamDestroy(L.stream);
+        cudaEventDestroy(L.ev0);
+        cudaEventDestroy(L.ev1);
     }
     delete s;
     return VGICP_OK;
@@ -579,6 +623,11 @@ vgicp_status vgicp_server_stats(vgicp_server *s, vgicp_server_counters *out)
         out->evictions = s->evictions;
         out->mean_batch_requests = s->batches ? (double)s->batch_requests / (double)s->batches : 0.0;
         out->resident_bytes = s->resident_bytes;
+        out->host_launch_ms = s->host_launch_ms;
+        out->host_finish_ms = s->host_finish_ms;
+        out->device_ms = s->device_ms;
+        out->host_admit_ms = s->host_admit_ms;
+        out->host_enqueue_ms = s->host_enqueue_ms;
         lat = s->lat_ms;
     }
     if (!lat.empty()) {
@@ -597,6 +646,7 @@ vgicp_status vgicp_server_reset_stats(vgicp_server *s)
     std::lock_guard<std::mutex> lk(s->mu);
     s->lat_ms.clear();
     s->submitted = s->completed = s->batches = s->admissions = s->evictions = s->batch_requests = 0;
+    s->host_launch_ms = s->host_finish_ms = s->device_ms = s->host_admit_ms = s->host_enqueue_ms = 0.0;
     return VGICP_OK;
 }
 
