@@ -55,6 +55,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-only", action="store_true", help="run warm-up and timed steps only (for ncu)")
+    p.add_argument("--uneven", action="store_true",
+                   help="the batched uneven-factor workload: one linearisation of 10,000 factors of 2,000-60,000 "
+                        "points over 1,000 voxelmaps at 0.5 / 1 / 2 m, direct and as a CUDA-graph iteration")
+    p.add_argument("--uneven-frames", type=int, default=1000)
+    p.add_argument("--uneven-factors", type=int, default=10000)
     p.add_argument("--serving", action="store_true",
                    help="the serving-loop workload: Poisson request streams through vgicp_server")
     p.add_argument("--serving-maps", type=int, default=2000)
@@ -132,6 +137,23 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def dram_traffic(kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu capture of this
+    workload, or None when the kernel's source has changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic_paper_scale_graph.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 4 and parts[0] == kernel:
+                    with open(os.path.join(ROOT, parts[2]), "rb") as src:
+                        if hashlib.sha256(src.read()).hexdigest() == parts[3]:
+                            return int(parts[1])
+    except OSError:
+        pass
+    return None
 
 
 def measured_peaks():
@@ -306,14 +328,14 @@ def run_ours(a):
     lin_bytes = 36 * corr_units + (144 + 12 + 1 + 1) * 8 * n_f        # 36 B per point + outputs
     lin_gbs = lin_bytes / (ph_mean[2] / 1e3) / 1e9
     roof_lin = {"bound": "hbm", "kernel": "linearize_f32", "achieved": lin_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": lin_gbs / hbm, "traffic": None, "peak_source": peak_kind,
+                "frac": lin_gbs / hbm, "traffic": dram_traffic("linearize_f32"), "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(lin_bytes)}
     if dom == 1:
         # the floor of Eq. 8's lookup, x = R p + t and x / r per axis: 21 flops per performed lookup
         flops = 21.0 * lookups_live
         ach = flops / (ph_mean[1] / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": "overlap_matrix", "achieved": ach, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": dram_traffic("overlap_matrix"),
                     "peak_source": "FP32 lanes x 2 x max SM clock (SMs x 128 x 2 x %.0f MHz)" % sm_max,
                     "algorithmic_flops_per_launch": flops, "lookups_per_launch": int(lookups_live)}
     elif dom == 2:
@@ -459,6 +481,114 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------------------
+# batched uneven factors
+# ---------------------------------------------------------------------------
+
+def run_uneven(a):
+    """One Gauss-Newton iteration's linearisation of a batch of uneven factors:
+    source sizes log-uniform in 2,000-60,000 points, targets from a pool of
+    voxelmaps (20,000 points each) at 0.5, 1 or 2 m, each source a subsample of
+    a frame within 10 m of its target's.  Timed as direct vgicp_linearize calls
+    and as runs of a plan (one CUDA graph per iteration); inputs exceed L2."""
+    import torch
+
+    import paper_2109_07073_b300 as vg
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    w = dg.uneven_workload(n_frames=a.uneven_frames, n_factors=a.uneven_factors,
+                           workers=min(16, os.cpu_count() or 1))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = vg.Context(stream=stream)
+    dp = [torch.from_numpy(f).cuda() for f in w.frames]
+    dc = [ctx.estimate_covariances(p, 10, 1e-3) for p in dp]
+    maps = np.full(len(w.frames), -1, np.int64)
+    for r in sorted(set(w.target_res.tolist())):
+        ts = np.nonzero(w.target_res == r)[0]
+        fr = []
+        for t in ts:
+            ix = torch.from_numpy(w.target_idx[t]).cuda()
+            fr.append(ctx.add_frame(dp[t][ix], dc[t][ix]))
+        maps[ts] = ctx.build_voxelmaps(fr, float(r))
+        for h in fr:
+            ctx.release(h)
+    srcs = []
+    for f in range(len(w.factor_idx)):
+        j = int(w.factor_frame[f])
+        ix = torch.from_numpy(w.factor_idx[f]).cuda()
+        srcs.append(ctx.add_frame(dp[j][ix], dc[j][ix]))
+    del dp, dc
+    factors = vg.make_factors(maps[w.factor_target], srcs, w.factor_target, w.factor_frame)
+    n_f = len(factors)
+    pts = int(sum(len(i) for i in w.factor_idx))
+    out = (torch.zeros((n_f, 12, 12), dtype=torch.float64, device="cuda"),
+           torch.zeros((n_f, 12), dtype=torch.float64, device="cuda"),
+           torch.zeros(n_f, dtype=torch.float64, device="cuda"), torch.zeros(n_f, dtype=torch.int64, device="cuda"))
+    best, tuned_ms = ctx.autotune(factors, w.poses, reps=2)
+    plan = ctx.plan_create(factors, len(w.poses))
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(a.warmup):
+        ctx.linearize(factors, w.poses, out=out)
+        ctx.plan_linearize(plan, w.poses, out=out)
+    torch.cuda.synchronize()
+    if a.profile_only:
+        torch.cuda.profiler.start()
+        for _ in range(a.steps):
+            ctx.plan_linearize(plan, w.poses, out=out)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
+    res_t = {}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for name, fn in (("direct", lambda: ctx.linearize(factors, w.poses, out=out)),
+                         ("graph", lambda: ctx.plan_linearize(plan, w.poses, out=out))):
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(a.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res_t[name] = e0.elapsed_time(e1) / a.steps
+    ctx.set_options(precision=vg.VGICP_PREC_F64)
+    sub = factors[: max(1, n_f // 20)]
+    sub_pts = int(sum(len(w.factor_idx[i]) for i in range(len(sub))))
+    ctx.linearize(sub, w.poses)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    ctx.linearize(sub, w.poses)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f64_ms = e0.elapsed_time(e1)
+    ctx.set_options(precision=vg.VGICP_PREC_F32)
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    ms = min(res_t.values())
+    lin_bytes = 36 * pts + (144 + 12 + 1 + 1) * 8 * n_f
+    ach = lin_bytes / (ms / 1e3) / 1e9
+    res = {"metric": "point-correspondences/s (batched uneven factors)", "value": pts / (ms / 1e3),
+           "unit": "point-correspondences/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded urban-loop LiDAR raycasts)",
+           "config": {"workload": f"batched uneven factors: {n_f} factors, sources of 2,000-60,000 points, "
+                                  f"{len(w.frames)} voxelmaps at 0.5/1/2 m", "factors": n_f, "points": pts,
+                      "l2": "inputs larger than L2 (sources %.1f GB)" % (36 * pts / 1e9)},
+           "factors_per_s": n_f / (ms / 1e3), "direct_ms": res_t["direct"], "graph_iteration_ms": res_t["graph"],
+           "autotuned": {"linearize_variant": int(best.linearize_variant), "chunk_points": int(best.chunk_points),
+                         "ms": tuned_ms},
+           "plain_f64": {"factors": len(sub), "ms": f64_ms, "point_correspondences_per_s": sub_pts / (f64_ms / 1e3),
+                         "factors_per_s": len(sub) / (f64_ms / 1e3)},
+           "roofline": {"bound": "hbm", "kernel": "linearize_f32", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "traffic": None, "peak_source": peak_kind,
+                        "algorithmic_bytes_per_launch": int(lin_bytes)},
+           "clocks": clk.summary()}
+    print(json.dumps(res), flush=True)
+    ctx.plan_destroy(plan)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
 # serving loop
 # ---------------------------------------------------------------------------
 
@@ -567,6 +697,8 @@ def main():
         run_reference(a)
     elif a.serving:
         run_serving(a)
+    elif a.uneven:
+        run_uneven(a)
     else:
         run_ours(a)
 

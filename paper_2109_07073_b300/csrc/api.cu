@@ -155,12 +155,23 @@ void free_buf(vgicp_ctx *ctx, Buf &b)
 // stream: the bytes go through a pinned staging arena of the lane (a copy from
 // pageable memory may first wait for the work queued before it).  An arena is
 // reused only after every copy from it has run; very large copies go direct.
-constexpr size_t kArenaMaxCopy = (size_t)64 << 20;
+constexpr size_t kArenaMaxCopy = (size_t)4 << 20;
+
+bool page_locked(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
 
 vgicp_status h2d(vgicp_ctx *ctx, void *dst, const void *src, size_t bytes)
 {
     if (bytes == 0) return VGICP_OK;
-    if (bytes > kArenaMaxCopy) {
+    if (bytes > kArenaMaxCopy || (bytes >= 65536 && page_locked(src))) {
+        // large copies: the driver stages pageable memory itself; page-locked memory is copied directly
         CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, LN.stream));
         return VGICP_OK;
     }
