@@ -59,7 +59,8 @@ typedef enum {
     VGICP_ERR_EMPTY = 4,        /* overlap of a source with zero points (Eq. 8 undefined) */
     VGICP_ERR_CUDA = 5,         /* a CUDA runtime call failed; see vgicp_last_error() */
     VGICP_ERR_TIMEOUT = 6,      /* a bounded device wait ran out */
-    VGICP_ERR_BUDGET = 7        /* admission would exceed the context's device-memory budget */
+    VGICP_ERR_BUDGET = 7,       /* admission would exceed the context's device-memory budget */
+    VGICP_ERR_NUMERIC = 8       /* a linear system is not positive definite */
 } vgicp_status;
 
 enum { VGICP_MEM_HOST = 0, VGICP_MEM_DEVICE = 1 };
@@ -180,6 +181,16 @@ vgicp_status vgicp_voxelmap_size(vgicp_ctx *ctx, vgicp_map_t map, int64_t *n_vox
 vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f,
                              const double *poses, int64_t n_poses,
                              double *H, double *b, double *cost, int64_t *inliers, int out_kind);
+
+/* Error evaluation (Sec. III-D: the optimiser evaluates the summed matching
+ * cost of Eq. 1 to accept or reject a step): each factor's cost
+ * sum e' Omega e and inlier count at the given poses, by the batched path with
+ * only the cost accumulated -- the same chunks, order and kernel variant as
+ * vgicp_linearize(), so the costs agree with its cost output bit for bit.
+ * Runs VGICP_PREC_F32 (or VGICP_PREC_F32_COMP when set; VGICP_PREC_F64 runs as
+ * VGICP_PREC_F32).  cost and inliers (nullable): n_f entries in out_kind memory. */
+vgicp_status vgicp_evaluate(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
+                            int64_t n_poses, double *cost, int64_t *inliers, int out_kind);
 
 /* Autotuner for the batched float32 linearisation (Sec. III-D's "issue all
  * factors, then synchronise" step): times every candidate (kernel variant x
@@ -326,6 +337,53 @@ vgicp_status vgicp_kernel_launches(vgicp_ctx *ctx, int64_t *count);
 
 /* Text of the last error of this context ("" if none).  Valid until the next call. */
 const char *vgicp_last_error(const vgicp_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Gauss-Newton / Levenberg-Marquardt (Sec. III-D: every factor is linearised
+ * on the GPU, the linear system is collected and solved on the host).  The
+ * factor blocks H_f, b_f of vgicp_linearize() define the Gauss-Newton model of
+ * the summed cost F = sum cost_f around the current poses,
+ *     F(d) = F + 2 b' d + d' H d,   d = (omega, v) per pose, T <- T Exp(d),
+ * with H and b assembled from the factors' [xi_B ; xi_A] blocks.
+ * ---------------------------------------------------------------------- */
+
+/* Host only (no device work): the damped step (H + lambda D) d = -b with the
+ * anchor pose held fixed (d = 0 there), D = diag(H) floored at 1e-12 of its
+ * mean (plus that floor), solved by a sparse Cholesky factorisation (reverse
+ * Cuthill-McKee pose order, envelope storage).  pairs: n_f x 2 int32
+ * (target_pose, source_pose); H n_f x 144, b n_f x 12 as vgicp_linearize()
+ * writes them; delta: n_poses x 6 out.  model_decrease (nullable) receives
+ * F(0) - F(d) of the undamped model.  VGICP_ERR_NUMERIC if the damped system
+ * is not positive definite. */
+vgicp_status vgicp_solve_step(const int32_t *pairs, const double *H, const double *b, int64_t n_f, int64_t n_poses,
+                              int32_t anchor, double lambda, double *delta, double *model_decrease);
+
+/* Host only: T_p <- T_p Exp(delta_p) for every pose (12 doubles each, in place),
+ * Exp the SE(3) exponential of (omega, v). */
+vgicp_status vgicp_se3_retract(double *poses, const double *delta, int64_t n_poses);
+
+typedef struct {
+    int32_t max_iterations;     /* 0 = 20 */
+    int32_t anchor;             /* pose held fixed (the gauge) */
+    double lambda_init;         /* initial damping, 0 = 1e-4 */
+    double relative_tolerance;  /* stop once an accepted step lowers F by less than this fraction (0 = 1e-6) */
+} vgicp_lm_options;
+
+typedef struct {
+    int32_t iterations, accepted, n_history;
+    int32_t reserved;
+    double initial_cost, final_cost, lambda;
+    double linearize_ms, evaluate_ms, solve_ms;   /* host wall time per phase */
+    double history[64];                           /* F at the start and after each accepted step */
+} vgicp_lm_report;
+
+/* Levenberg-Marquardt over the factors: poses (n_poses x 12, host) are updated
+ * in place.  Each iteration linearises through a plan (one CUDA graph), solves
+ * vgicp_solve_step on the host, evaluates the trial poses with
+ * vgicp_evaluate(), and accepts (damping / 10) or rejects (damping x 10) the
+ * step.  Correspondences are re-associated at every linearisation. */
+vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, double *poses,
+                            int64_t n_poses, const vgicp_lm_options *opt, vgicp_lm_report *report);
 
 /* Human-readable name of a status code. */
 const char *vgicp_status_string(vgicp_status s);

@@ -248,3 +248,62 @@ def covariances(points, k: int = 10, eps: float = 1e-3, nbr=None) -> np.ndarray:
     _load().oracle_covariances_from_neighbors(p, n, k, np.ascontiguousarray(nbr, dtype=np.int64),
                                               float(eps), out)
     return out[:n]
+
+
+# --------------------------------------------------------------------------
+# Gauss-Newton step of the global optimisation (Sec. III-D): the factors'
+# blocks assembled into one dense system and solved plainly.
+# --------------------------------------------------------------------------
+
+def se3_exp(xi) -> np.ndarray:
+    """Exp of a twist xi = (omega, v) as a 3x4 [R | t]: Rodrigues' formula for R and
+    t = V v, V = I + (1 - cos th) / th^2 [w]x + (th - sin th) / th^3 [w]x^2."""
+    xi = np.asarray(xi, dtype=np.float64)
+    w, v = xi[:3], xi[3:]
+    th = float(np.sqrt(w @ w))
+    K = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    if th < 1e-8:
+        A, B, Cc = 1.0, 0.5, 1.0 / 6.0
+    else:
+        A, B, Cc = np.sin(th) / th, (1.0 - np.cos(th)) / th**2, (th - np.sin(th)) / th**3
+    R = np.eye(3) + A * K + B * (K @ K)
+    V = np.eye(3) + B * K + Cc * (K @ K)
+    return np.hstack([R, (V @ v)[:, None]])
+
+
+def retract(poses, delta) -> np.ndarray:
+    """T_p Exp(delta_p) for every pose (right perturbation)."""
+    out = []
+    for T, d in zip(np.asarray(poses, dtype=np.float64).reshape(-1, 3, 4), np.asarray(delta).reshape(-1, 6)):
+        E = se3_exp(d)
+        out.append(np.hstack([T[:, :3] @ E[:, :3], (T[:, :3] @ E[:, 3] + T[:, 3])[:, None]]))
+    return np.stack(out)
+
+
+def assemble(pairs, H, b, n_poses):
+    """Dense global H (6n x 6n) and b (6n) from factor blocks in [xi_target ; xi_source] order."""
+    n = int(n_poses)
+    Hg, bg = np.zeros((6 * n, 6 * n)), np.zeros(6 * n)
+    for (t, s), Hf, bf in zip(np.asarray(pairs).reshape(-1, 2), np.asarray(H).reshape(-1, 12, 12),
+                              np.asarray(b).reshape(-1, 12)):
+        idx = np.r_[6 * t:6 * t + 6, 6 * s:6 * s + 6]
+        for i in range(12):
+            bg[idx[i]] += bf[i]
+            for j in range(12):
+                Hg[idx[i], idx[j]] += Hf[i, j]
+    return Hg, bg
+
+
+def gn_step(pairs, H, b, n_poses, anchor=0, lam=0.0):
+    """Damped step (H + lam D) d = -b over every pose but the anchor (d = 0 there),
+    D = diag(H) floored at 1e-12 of its mean over the free variables, plus that floor;
+    returns d (n, 6) and the undamped model decrease -(2 b'd + d'H d)."""
+    Hg, bg = assemble(pairs, H, b, n_poses)
+    free = np.array([i for i in range(6 * int(n_poses)) if i // 6 != anchor])
+    A = Hg[np.ix_(free, free)].copy()
+    fl = 1e-12 * max(float(np.mean(np.diag(A))), 1e-300)
+    dg = np.diag(A).copy()
+    A[np.diag_indices_from(A)] = dg + lam * np.maximum(dg, fl) + fl
+    d = np.zeros(6 * int(n_poses))
+    d[free] = np.linalg.solve(A, -bg[free])
+    return d.reshape(-1, 6), float(-(2.0 * bg @ d + d @ Hg @ d))

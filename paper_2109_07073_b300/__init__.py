@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(_PKG, "libvgicp.so")
 
 VGICP_OK = 0
 STATUS = {0: "VGICP_OK", 1: "VGICP_ERR_INVALID_ARG", 2: "VGICP_ERR_OOM", 3: "VGICP_ERR_NOT_FOUND",
-          4: "VGICP_ERR_EMPTY", 5: "VGICP_ERR_CUDA", 6: "VGICP_ERR_TIMEOUT", 7: "VGICP_ERR_BUDGET"}
+          4: "VGICP_ERR_EMPTY", 5: "VGICP_ERR_CUDA", 6: "VGICP_ERR_TIMEOUT", 7: "VGICP_ERR_BUDGET",
+          8: "VGICP_ERR_NUMERIC"}
 VGICP_MEM_HOST, VGICP_MEM_DEVICE = 0, 1
 VGICP_PREC_F32, VGICP_PREC_F64, VGICP_PREC_F32_COMP = 0, 1, 2
 
@@ -36,7 +37,8 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_overlap_pairs", "vgicp_server_create", "vgicp_server_destroy", "vgicp_server_put_map",
            "vgicp_server_put_frame", "vgicp_server_submit", "vgicp_server_wait", "vgicp_server_stats",
            "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_server_submit_batch", "vgicp_server_wait_batch", "vgicp_plan_create", "vgicp_plan_linearize",
-           "vgicp_plan_info", "vgicp_plan_destroy", "vgicp_memory_estimate"]
+           "vgicp_plan_info", "vgicp_plan_destroy", "vgicp_memory_estimate", "vgicp_evaluate", "vgicp_solve_step",
+           "vgicp_se3_retract", "vgicp_optimize"]
 VGICP_REQ_LINEARIZE, VGICP_REQ_OVERLAP = 0, 1
 
 
@@ -55,6 +57,18 @@ class Options(C.Structure):
 class Factor(C.Structure):
     _fields_ = [("target", C.c_int64), ("source", C.c_int64), ("target_pose", C.c_int32),
                 ("source_pose", C.c_int32)]
+
+
+class LMOptions(C.Structure):
+    _fields_ = [("max_iterations", C.c_int32), ("anchor", C.c_int32), ("lambda_init", C.c_double),
+                ("relative_tolerance", C.c_double)]
+
+
+class LMReport(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("accepted", C.c_int32), ("n_history", C.c_int32),
+                ("reserved", C.c_int32), ("initial_cost", C.c_double), ("final_cost", C.c_double),
+                ("lambda_", C.c_double), ("linearize_ms", C.c_double), ("evaluate_ms", C.c_double),
+                ("solve_ms", C.c_double), ("history", C.c_double * 64)]
 
 
 class ServerOptions(C.Structure):
@@ -123,6 +137,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_memory_estimate": [vp, i64, i32, C.POINTER(i64)],
         "vgicp_kernel_launches": [vp, C.POINTER(i64)],
         "vgicp_plan_create": [vp, vp, i64, i64, C.POINTER(vp)],
+        "vgicp_evaluate": [vp, vp, i64, vp, i64, vp, vp, C.c_int],
+        "vgicp_solve_step": [vp, vp, vp, i64, i64, i32, f64, vp, C.POINTER(f64)],
+        "vgicp_se3_retract": [vp, vp, i64],
+        "vgicp_optimize": [vp, vp, i64, vp, i64, C.POINTER(LMOptions), C.POINTER(LMReport)],
         "vgicp_plan_linearize": [vp, vp, vp, vp, vp, vp, vp, C.c_int],
         "vgicp_plan_info": [vp, vp, C.POINTER(i64), C.POINTER(i64)],
         "vgicp_plan_destroy": [vp, vp],
@@ -298,6 +316,52 @@ def vgicp_linearize(ctx, factors, poses, out=None):
     _check(ctx, load().vgicp_linearize(ctx, _ptr(f), nf, _ptr(P), P.shape[0], _ptr(H), _ptr(b), _ptr(cost),
                                        _ptr(inl), kind))
     return H, b, cost, inl
+
+
+def vgicp_evaluate(ctx, factors, poses, out=None):
+    """Each factor's cost (and inliers) at the poses, by the cost-only batched pass."""
+    f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
+    P = _pose12(poses)
+    nf = f.shape[0]
+    if out is None:
+        out = (np.zeros(nf), np.zeros(nf, np.int64))
+    cost, inl = out
+    kind = VGICP_MEM_DEVICE if _is_torch_cuda(cost) else VGICP_MEM_HOST
+    _check(ctx, load().vgicp_evaluate(ctx, _ptr(f), nf, _ptr(P), P.shape[0], _ptr(cost), _ptr(inl), kind))
+    return cost, inl
+
+
+def vgicp_solve_step(pairs, H, b, n_poses: int, anchor: int = 0, lam: float = 0.0):
+    """Host-only damped Gauss-Newton step: returns (delta (n_poses, 6), model decrease)."""
+    pr = np.ascontiguousarray(pairs, np.int32).reshape(-1, 2)
+    Hh = np.ascontiguousarray(H, np.float64).reshape(-1, 144)
+    bh = np.ascontiguousarray(b, np.float64).reshape(-1, 12)
+    delta = np.zeros((int(n_poses), 6))
+    dec = C.c_double()
+    _check(None, load().vgicp_solve_step(_ptr(pr), _ptr(Hh), _ptr(bh), pr.shape[0], int(n_poses), int(anchor),
+                                         float(lam), _ptr(delta), C.byref(dec)))
+    return delta, dec.value
+
+
+def vgicp_se3_retract(poses, delta) -> np.ndarray:
+    """Host-only: T <- T Exp(delta) per pose; returns new poses (n, 3, 4)."""
+    P = np.array(_pose12(poses), dtype=np.float64)
+    d = np.ascontiguousarray(delta, np.float64).reshape(-1, 6)
+    if d.shape[0] != P.shape[0]:
+        raise ValueError("one delta per pose")
+    _check(None, load().vgicp_se3_retract(_ptr(P), _ptr(d), P.shape[0]))
+    return P.reshape(-1, 3, 4)
+
+
+def vgicp_optimize(ctx, factors, poses, max_iterations: int = 20, anchor: int = 0, lambda_init: float = 0.0,
+                   relative_tolerance: float = 0.0):
+    """Levenberg-Marquardt over the factors; returns (optimised poses (n, 3, 4), LMReport)."""
+    f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
+    P = np.array(_pose12(poses), dtype=np.float64)
+    opt = LMOptions(max_iterations, anchor, lambda_init, relative_tolerance)
+    rep = LMReport()
+    _check(ctx, load().vgicp_optimize(ctx, _ptr(f), f.shape[0], _ptr(P), P.shape[0], C.byref(opt), C.byref(rep)))
+    return P.reshape(-1, 3, 4), rep
 
 
 def vgicp_plan_create(ctx, factors, n_poses: int):

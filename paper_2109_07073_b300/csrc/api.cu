@@ -470,6 +470,34 @@ vgicp_status read_nvox(vgicp_ctx *ctx, const Obj &o, int64_t *n)
 
 int default_chunk(const vgicp_options &o) { return o.chunk_points > 0 ? o.chunk_points : 2048; }
 
+// Descriptor-table indices of a factor set (map, frame, target pose, source
+// pose per factor), after checking handles, pose indices and pose entries.
+vgicp_status factor_indices(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
+                            int64_t n_poses, std::vector<int32_t> &idx)
+{
+    if (n_f > (1 << 30)) return fail(ctx, VGICP_ERR_INVALID_ARG, "too many factors");
+    idx.resize((size_t)n_f * 4);
+    for (int64_t i = 0; i < n_f; ++i) {
+        uint32_t mi, fi;
+        if (!lookup(ctx, factors[i].target, Obj::MAP, &mi))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "factor %lld: map handle %lld not found", (long long)i,
+                        (long long)factors[i].target);
+        if (!lookup(ctx, factors[i].source, Obj::FRAME, &fi))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "factor %lld: frame handle %lld not found", (long long)i,
+                        (long long)factors[i].source);
+        if (factors[i].target_pose < 0 || factors[i].target_pose >= n_poses || factors[i].source_pose < 0 ||
+            factors[i].source_pose >= n_poses)
+            return fail(ctx, VGICP_ERR_INVALID_ARG, "factor %lld: pose index out of range", (long long)i);
+        idx[4 * i + 0] = (int32_t)mi;
+        idx[4 * i + 1] = (int32_t)fi;
+        idx[4 * i + 2] = factors[i].target_pose;
+        idx[4 * i + 3] = factors[i].source_pose;
+    }
+    for (int64_t i = 0; i < n_poses * 12; ++i)
+        if (!std::isfinite(poses[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "non-finite pose entry");
+    return VGICP_OK;
+}
+
 // Work items of a factor set: each factor's points in chunks of `chunk`, the
 // chunks of one factor contiguous, and factors grouped by target voxelmap (then
 // by source frame) so that the warps running at any moment share few maps and
@@ -796,26 +824,8 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
     if (out_kind != VGICP_MEM_HOST && out_kind != VGICP_MEM_DEVICE)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: bad out_kind %d", out_kind);
     if (n_f == 0) return VGICP_OK;
-    if (n_f > (1 << 30)) return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: too many factors");
-    std::vector<int32_t> idx((size_t)n_f * 4);
-    for (int64_t i = 0; i < n_f; ++i) {
-        uint32_t mi, fi;
-        if (!lookup(ctx, factors[i].target, Obj::MAP, &mi))
-            return fail(ctx, VGICP_ERR_NOT_FOUND, "factor %lld: map handle %lld not found", (long long)i,
-                        (long long)factors[i].target);
-        if (!lookup(ctx, factors[i].source, Obj::FRAME, &fi))
-            return fail(ctx, VGICP_ERR_NOT_FOUND, "factor %lld: frame handle %lld not found", (long long)i,
-                        (long long)factors[i].source);
-        if (factors[i].target_pose < 0 || factors[i].target_pose >= n_poses || factors[i].source_pose < 0 ||
-            factors[i].source_pose >= n_poses)
-            return fail(ctx, VGICP_ERR_INVALID_ARG, "factor %lld: pose index out of range", (long long)i);
-        idx[4 * i + 0] = (int32_t)mi;
-        idx[4 * i + 1] = (int32_t)fi;
-        idx[4 * i + 2] = factors[i].target_pose;
-        idx[4 * i + 3] = factors[i].source_pose;
-    }
-    for (int64_t i = 0; i < n_poses * 12; ++i)
-        if (!std::isfinite(poses[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: non-finite pose entry");
+    std::vector<int32_t> idx;
+    TRY(factor_indices(ctx, factors, n_f, poses, n_poses, idx));
     TRY(upload(ctx, LN.ws_poses, poses, (size_t)n_poses * 12));
     TRY(get_plan(ctx, factors, n_f, idx));
     Plan &P = LN.plan;
@@ -1099,6 +1109,50 @@ vgicp_status vgicp_plan_destroy(vgicp_ctx *ctx, vgicp_plan *P)
 }  // extern "C"
 
 extern "C" {
+
+vgicp_status vgicp_evaluate(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
+                            int64_t n_poses, double *cost, int64_t *inliers, int out_kind)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n_f < 0 || n_poses < 0 || (n_f > 0 && (!factors || !cost)) || (n_poses > 0 && !poses))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "evaluate: null pointer or negative size");
+    if (out_kind != VGICP_MEM_HOST && out_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "evaluate: bad out_kind %d", out_kind);
+    if (n_f == 0) return VGICP_OK;
+    std::vector<int32_t> idx;
+    TRY(factor_indices(ctx, factors, n_f, poses, n_poses, idx));
+    TRY(upload(ctx, LN.ws_poses, poses, (size_t)n_poses * 12));
+    TRY(get_plan(ctx, factors, n_f, idx));
+    Plan &P = LN.plan;
+    TRY(ensure(ctx, LN.ws_params, (size_t)n_f * sizeof(PoseParam)));
+    PoseParam *d_params = (PoseParam *)LN.ws_params.p;
+    launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)LN.ws_poses.p, ctx->d_maps,
+                           ctx->d_frames, ctx->opt.linearize_cull, d_params, LN.stream);
+    double *dc = cost;
+    int64_t *di = inliers;
+    if (out_kind == VGICP_MEM_HOST) {
+        TRY(ensure(ctx, LN.ws_out, (size_t)n_f * 16));
+        dc = (double *)LN.ws_out.p;
+        di = (int64_t *)(dc + n_f);
+    }
+    TRY(ensure(ctx, LN.ws_partials, (size_t)std::max(1, P.n_items) * 8));
+    TRY(ensure(ctx, LN.ws_inl, (size_t)std::max(1, P.n_items) * 8));
+    TRY(ensure(ctx, LN.ws_fetch, 16));
+    launch_cost_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
+                    (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p,
+                    ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
+                    ctx->opt.precision == VGICP_PREC_F32_COMP, LN.stream);
+    launch_reduce_cost((const int32_t *)P.item_range.p, (int)n_f, (const double *)LN.ws_partials.p,
+                       (const int64_t *)LN.ws_inl.p, dc, di, LN.stream);
+    ctx->launches += 2 + (P.n_items > 0);
+    CHECK_LAUNCH();
+    if (out_kind == VGICP_MEM_HOST) {
+        CU(cudaMemcpyAsync(cost, dc, (size_t)n_f * 8, cudaMemcpyDeviceToHost, LN.stream));
+        if (inliers) CU(cudaMemcpyAsync(inliers, di, (size_t)n_f * 8, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaStreamSynchronize(LN.stream));
+    }
+    return VGICP_OK;
+}
 
 vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
                             int64_t n_poses, int32_t reps, vgicp_options *best, double *best_ms)
@@ -1499,6 +1553,7 @@ const char *vgicp_status_string(vgicp_status s)
     case VGICP_ERR_CUDA: return "VGICP_ERR_CUDA";
     case VGICP_ERR_TIMEOUT: return "VGICP_ERR_TIMEOUT";
     case VGICP_ERR_BUDGET: return "VGICP_ERR_BUDGET";
+    case VGICP_ERR_NUMERIC: return "VGICP_ERR_NUMERIC";
     }
     return "unknown";
 }

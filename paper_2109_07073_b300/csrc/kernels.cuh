@@ -76,6 +76,11 @@ void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const Fr
 
 // Per-factor fixed-order float64 reduction of the item partials and expansion
 // to the 12x12 H, b, cost.  item_begin has n_f + 1 entries.
+void launch_cost_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
+                     int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
+                     int grid_per_sm, int num_sms, bool compensated, cudaStream_t st);
+void launch_reduce_cost(const int32_t *item_range, int n_f, const double *partials, const int64_t *inl_partials,
+                        double *cost, int64_t *inliers, cudaStream_t st);
 void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, int n_f, const double *partials,
                             const int64_t *inl_partials, double *H, double *b, double *cost, int64_t *inliers,
                             cudaStream_t st);

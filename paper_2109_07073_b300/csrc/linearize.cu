@@ -319,13 +319,17 @@ __device__ __forceinline__ VoxelRec load_rec(const VoxelRec *r)
     return v;
 }
 
-// One correspondence's contribution (Eq. 2, 5, 6 in the adjoint form) added to acc.
-__device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, const float4 &A, const float4 &B,
-                                                float C22, const VoxelRec &v, const float d[3], const float x[3])
+// Residual e = mu_B - q (both relative to the voxel's lower corner), the
+// information matrix Omega = (C_B + R C_A R^T)^-1 (Eq. 2, by the adjugate) and
+// w = Omega e of one correspondence.  False when the combined covariance is not
+// positive definite (the point then contributes nothing).
+__device__ __forceinline__ bool point_omega(const float *R, const float4 &A, const float4 &B, float C22,
+                                            const VoxelRec &v, const float d[3], float e[3], float o[6], float w[3])
 {
     const float R0 = R[0], R1 = R[1], R2 = R[2], R3 = R[3], R4 = R[4], R5 = R[5], R6 = R[6], R7 = R[7], R8 = R[8];
-    // residual e = mu_B - q, both relative to the voxel's lower corner
-    const float e0 = v.a.x - d[0], e1 = v.a.y - d[1], e2 = v.a.z - d[2];
+    e[0] = v.a.x - d[0];
+    e[1] = v.a.y - d[1];
+    e[2] = v.a.z - d[2];
     // R C_A (C_A symmetric: c00 c01 c02 / c11 c12 / c22)
     const float a00 = A.w, a01 = B.x, a02 = B.y, a11 = B.z, a12 = B.w, a22 = C22;
     const float T00 = R0 * a00 + R1 * a01 + R2 * a02, T01 = R0 * a01 + R1 * a11 + R2 * a12,
@@ -345,13 +349,39 @@ __device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, 
     const float c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
     const float c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
     const float det = m00 * c00 + m01 * c01 + m02 * c02;
-    if (!(det > 0.f)) return 0;
+    if (!(det > 0.f)) return false;
     const float id = __frcp_rn(det);
-    const float o00 = c00 * id, o01 = c01 * id, o02 = c02 * id, o11 = c11 * id, o12 = c12 * id, o22 = c22 * id;
-    // w = Omega e, cost = e . w
-    const float w0 = o00 * e0 + o01 * e1 + o02 * e2;
-    const float w1 = o01 * e0 + o11 * e1 + o12 * e2;
-    const float w2 = o02 * e0 + o12 * e1 + o22 * e2;
+    o[0] = c00 * id;
+    o[1] = c01 * id;
+    o[2] = c02 * id;
+    o[3] = c11 * id;
+    o[4] = c12 * id;
+    o[5] = c22 * id;
+    w[0] = o[0] * e[0] + o[1] * e[1] + o[2] * e[2];
+    w[1] = o[1] * e[0] + o[3] * e[1] + o[4] * e[2];
+    w[2] = o[2] * e[0] + o[4] * e[1] + o[5] * e[2];
+    return true;
+}
+
+// One correspondence's cost e' Omega e (Eq. 2) added to acc[0] (error evaluation).
+__device__ __forceinline__ int accumulate_cost(float acc[1], const float *R, const float4 &A, const float4 &B,
+                                               float C22, const VoxelRec &v, const float d[3])
+{
+    float e[3], o[6], w[3];
+    if (!point_omega(R, A, B, C22, v, d, e, o, w)) return 0;
+    acc[0] += e[0] * w[0] + e[1] * w[1] + e[2] * w[2];
+    return 1;
+}
+
+// One correspondence's contribution (Eq. 2, 5, 6 in the adjoint form) added to acc.
+__device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, const float4 &A, const float4 &B,
+                                                float C22, const VoxelRec &v, const float d[3], const float x[3])
+{
+    float e[3], o[6], w[3];
+    if (!point_omega(R, A, B, C22, v, d, e, o, w)) return 0;
+    const float e0 = e[0], e1 = e[1], e2 = e[2];
+    const float o00 = o[0], o01 = o[1], o02 = o[2], o11 = o[3], o12 = o[4], o22 = o[5];
+    const float w0 = w[0], w1 = w[1], w2 = w[2];
     const float x0 = x[0], x1 = x[1], x2 = x[2];   // lever arm a = R p
     // P = [a]x Omega  (= H_wv contribution)
     const float P00 = x1 * o02 - x2 * o01, P01 = x1 * o12 - x2 * o11, P02 = x1 * o22 - x2 * o12;
@@ -377,6 +407,16 @@ __device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, 
     return 1;
 }
 
+template <int NT>
+__device__ __forceinline__ int accumulate(float acc[NT], const float *R, const float4 &A, const float4 &B, float C22,
+                                          const VoxelRec &v, const float d[3], const float x[3])
+{
+    if constexpr (NT == 1)
+        return accumulate_cost(acc, R, A, B, C22, v, d);
+    else
+        return accumulate_point(acc, R, A, B, C22, v, d, x);
+}
+
 // Work items belong to single warps: a warp copies its factor's parameters to
 // its own shared-memory slot, runs over the item's points, reduces its 28 sums
 // by shuffles and writes them as float64 -- no block barriers anywhere.  Warps
@@ -390,9 +430,9 @@ __device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, 
 //            before this step's key, probe and record chain;
 //   PTS = 2: two points per lane per step, both points' loads, keys and first
 //            probes issued before either record is needed.
-template <int PTS, bool FF>
+template <int PTS, bool FF, int NT>
 __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
-                                                 const WorkItem &w, int lane, float acc[kNT], int &inl)
+                                                 const WorkItem &w, int lane, float acc[NT], int &inl)
 {
     const float4 *__restrict__ pa = F.pa + w.start;
     const float4 *__restrict__ pb = F.pb + w.start;
@@ -425,7 +465,7 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
             const int slot0 = resolve_slot(m, s0, f0);
             if (slot0 < 0) continue;
             if (slot0 != (int)s0.h) v0 = load_rec(m.rec + slot0);
-            inl += accumulate_point(acc, P.Rh, A0, B0, C0, v0, d0, x0);
+            inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
         }
     } else {
         for (int i0 = lane; i0 < n; i0 += 64) {
@@ -458,8 +498,8 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
             const int slot1 = resolve_slot(m, s1, f1);
             if (slot0 >= 0 && slot0 != (int)s0.h) v0 = load_rec(m.rec + slot0);
             if (slot1 >= 0 && slot1 != (int)s1.h) v1 = load_rec(m.rec + slot1);
-            if (slot0 >= 0) inl += accumulate_point(acc, P.Rh, A0, B0, C0, v0, d0, x0);
-            if (slot1 >= 0) inl += accumulate_point(acc, P.Rh, A1, B1, C1, v1, d1, x1);
+            if (slot0 >= 0) inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
+            if (slot1 >= 0) inl += accumulate<NT>(acc, P.Rh, A1, B1, C1, v1, d1, x1);
         }
     }
 }
@@ -503,9 +543,9 @@ struct WarpStage {
 // probe (key and record together) is copied in, while step st's correspondence
 // is resolved and accumulated.  Each lane reads back only the slots it filled,
 // and refills a slot only after it consumed the slot's values.
-template <bool FF>
+template <bool FF, int NT>
 __device__ __forceinline__ void linearize_points_staged(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
-                                                        const WorkItem &w, int lane, float acc[kNT], int &inl,
+                                                        const WorkItem &w, int lane, float acc[NT], int &inl,
                                                         WarpStage &S)
 {
     const float4 *__restrict__ pa = F.pa + w.start;
@@ -571,7 +611,7 @@ __device__ __forceinline__ void linearize_points_staged(const PoseParam &P, cons
                     v = load_rec(m.rec + slot);
                 }
                 const int q = st % 3;
-                inl += accumulate_point(acc, P.Rh, S.pa[q][lane], S.pb[q][lane], S.pc[q][lane], v, d, x);
+                inl += accumulate<NT>(acc, P.Rh, S.pa[q][lane], S.pb[q][lane], S.pc[q][lane], v, d, x);
             }
         }
         s = s1;
@@ -586,9 +626,9 @@ __device__ __forceinline__ void linearize_points_staged(const PoseParam &P, cons
 
 // One work item: skipped when every cull chunk it spans is dead (no point of it
 // can find a voxel), otherwise all of its points.
-template <int PTS, bool FF>
+template <int PTS, bool FF, int NT>
 __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
-                                                    const WorkItem &w, int lane, float acc[kNT], int &inl,
+                                                    const WorkItem &w, int lane, float acc[NT], int &inl,
                                                     WarpStage *S)
 {
     if (w.count <= 0) return;
@@ -596,12 +636,12 @@ __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const Ma
     const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
     if ((P.cmask & span) == 0u) return;
     if constexpr (PTS == 0)
-        linearize_points_staged<FF>(P, m, F, w, lane, acc, inl, *S);
+        linearize_points_staged<FF, NT>(P, m, F, w, lane, acc, inl, *S);
     else
-        linearize_points<PTS, FF>(P, m, F, w, lane, acc, inl);
+        linearize_points<PTS, FF, NT>(P, m, F, w, lane, acc, inl);
 }
 
-template <int BLOCK, int MINB, int PTS, bool FF>
+template <int BLOCK, int MINB, int PTS, bool FF, int NT = kNT>
 __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *__restrict__ params,
                                                                const MapDesc *__restrict__ maps,
                                                                const FrameDesc *__restrict__ frames,
@@ -634,25 +674,47 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
         const PoseParam &P = sP[wib];
         const MapDesc m = sM[wib];
         const FrameDesc F = frames[P.frame];
-        float acc[kNT];
+        float acc[NT];
 #pragma unroll
-        for (int j = 0; j < kNT; ++j) acc[j] = 0.f;
+        for (int j = 0; j < NT; ++j) acc[j] = 0.f;
         int inl = 0;
-        linearize_warp_item<PTS, FF>(P, m, F, w, lane, acc, inl, sS + (PTS == 0 ? wib : 0));
+        linearize_warp_item<PTS, FF, NT>(P, m, F, w, lane, acc, inl, sS + (PTS == 0 ? wib : 0));
         // butterfly: every lane ends with the warp's sums; lane j writes sum j
+        // (a cost-only pass takes its sum from the lane that holds the cost in the
+        // full pass, so both passes' costs agree bit for bit)
         double mine = 0.0;
 #pragma unroll
-        for (int j = 0; j < kNT; ++j) {
+        for (int j = 0; j < NT; ++j) {
             float x = acc[j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == j) mine = (double)x;
+            if (lane == (NT == 1 ? kNT - 1 : j)) mine = (double)x;
         }
+        if (NT == 1) mine = __shfl_sync(0xffffffffu, mine, kNT - 1);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) inl += __shfl_xor_sync(0xffffffffu, inl, o);
-        if (lane < kNT) partials[(int64_t)it * kNT + lane] = mine;
-        if (lane == kNT) inl_partials[it] = inl;
+        if (lane < NT) partials[(int64_t)it * NT + lane] = mine;
+        if (lane == NT) inl_partials[it] = inl;
     }
+}
+
+// Cost-only reduction: each factor's item costs summed in item order (the order
+// of the full reduction, so the costs agree bit for bit), and its inliers.
+__global__ void k_reduce_cost(const int32_t *__restrict__ item_range, int n_f, const double *__restrict__ partials,
+                              const int64_t *__restrict__ inl_p, double *__restrict__ cost,
+                              int64_t *__restrict__ inliers)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n_f) return;
+    const int i0 = item_range[2 * f], i1 = item_range[2 * f + 1];
+    double s = 0.0;
+    int64_t ni = 0;
+    for (int i = i0; i < i1; ++i) {
+        s += partials[i];
+        ni += inl_p[i];
+    }
+    cost[f] = s;
+    if (inliers) inliers[f] = ni;
 }
 
 // One warp per factor: fixed-order float64 sum of the factor's item partials,
@@ -928,7 +990,7 @@ void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, cons
 // Variants of the batched kernel: (points per lane per step, blocks per SM the
 // register budget is set for).  Work items are per warp, so the block size only
 // sets the occupancy granularity.
-template <bool FF>
+template <bool FF, int NT>
 void launch_variant(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                     int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
                     int grid_per_sm, int num_sms, cudaStream_t st)
@@ -936,37 +998,37 @@ void launch_variant(const PoseParam *params, const MapDesc *maps, const FrameDes
     switch (variant) {
     case 1: {   // one point per step + prefetch, 128-thread blocks, 6 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
-        k_linearize_f32<128, 6, 1, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+        k_linearize_f32<128, 6, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
                                                            inl_partials, next_item);
         break;
     }
     case 2: {   // two points per step, 128-thread blocks, 4 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
-        k_linearize_f32<128, 4, 2, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+        k_linearize_f32<128, 4, 2, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
                                                            inl_partials, next_item);
         break;
     }
     case 3: {   // one point per step + prefetch, 128-thread blocks, 4 per SM (no register cap below 128)
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
-        k_linearize_f32<128, 4, 1, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+        k_linearize_f32<128, 4, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
                                                            inl_partials, next_item);
         break;
     }
     case 4: {   // cp.async pipeline (points two steps, probes one step ahead), 128-thread blocks, 5 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
-        k_linearize_f32<128, 5, 0, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+        k_linearize_f32<128, 5, 0, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
                                                            inl_partials, next_item);
         break;
     }
     case 5: {   // cp.async pipeline, 128-thread blocks, 6 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
-        k_linearize_f32<128, 6, 0, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+        k_linearize_f32<128, 6, 0, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
                                                            inl_partials, next_item);
         break;
     }
     default: {  // one point per step + prefetch, 128-thread blocks, 5 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
-        k_linearize_f32<128, 5, 1, FF><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
+        k_linearize_f32<128, 5, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
                                                            inl_partials, next_item);
         break;
     }
@@ -981,11 +1043,25 @@ void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const Fr
     if (n_items <= 0) return;
     cudaMemsetAsync(next_item, 0, sizeof(int), st);
     if (compensated)
-        launch_variant<true>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
-                             grid_per_sm, num_sms, st);
+        launch_variant<true, kNT>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
+                                  grid_per_sm, num_sms, st);
     else
-        launch_variant<false>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
-                              grid_per_sm, num_sms, st);
+        launch_variant<false, kNT>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
+                                   grid_per_sm, num_sms, st);
+}
+
+void launch_cost_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
+                     int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
+                     int grid_per_sm, int num_sms, bool compensated, cudaStream_t st)
+{
+    if (n_items <= 0) return;
+    cudaMemsetAsync(next_item, 0, sizeof(int), st);
+    if (compensated)
+        launch_variant<true, 1>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
+                                grid_per_sm, num_sms, st);
+    else
+        launch_variant<false, 1>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
+                                 grid_per_sm, num_sms, st);
 }
 
 void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, int n_f, const double *partials,
@@ -995,6 +1071,13 @@ void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, 
     if (n_f <= 0) return;
     k_reduce_finalize<<<(n_f + 3) / 4, 128, 0, st>>>(params, item_range, n_f, partials, inl_partials, H, b, cost,
                                                     inliers);
+}
+
+void launch_reduce_cost(const int32_t *item_range, int n_f, const double *partials, const int64_t *inl_partials,
+                        double *cost, int64_t *inliers, cudaStream_t st)
+{
+    if (n_f <= 0) return;
+    k_reduce_cost<<<(n_f + 127) / 128, 128, 0, st>>>(item_range, n_f, partials, inl_partials, cost, inliers);
 }
 
 int linearize_f64_block() { return kF64Block; }
