@@ -381,7 +381,9 @@ typedef struct {
  * in place.  Each iteration linearises through a plan (one CUDA graph), solves
  * vgicp_solve_step on the host, evaluates the trial poses with
  * vgicp_evaluate(), and accepts (damping / 10) or rejects (damping x 10) the
- * step.  Correspondences are re-associated at every linearisation. */
+ * step.  It stops after max_iterations, when an accepted step lowers F by less
+ * than relative_tolerance F, or when the Gauss-Newton model predicts less than
+ * that.  Correspondences are re-associated at every linearisation. */
 vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, double *poses,
                             int64_t n_poses, const vgicp_lm_options *opt, vgicp_lm_report *report);
 

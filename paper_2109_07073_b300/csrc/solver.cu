@@ -92,10 +92,19 @@ bool cholesky(Skyline &S, int64_t n)
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t j = S.first[i]; j <= i; ++j) {
             const int64_t k0 = std::max(S.first[i], S.first[j]);
-            double s = S.at(i, j);
             const double *li = &S.a[S.off[i] + (k0 - S.first[i])];
             const double *lj = &S.a[S.off[j] + (k0 - S.first[j])];
-            for (int64_t k = 0; k < j - k0; ++k) s -= li[k] * lj[k];
+            const int64_t len = j - k0;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four partial sums: independent FMA chains
+            int64_t k = 0;
+            for (; k + 4 <= len; k += 4) {
+                s0 += li[k] * lj[k];
+                s1 += li[k + 1] * lj[k + 1];
+                s2 += li[k + 2] * lj[k + 2];
+                s3 += li[k + 3] * lj[k + 3];
+            }
+            for (; k < len; ++k) s0 += li[k] * lj[k];
+            const double s = S.at(i, j) - ((s0 + s1) + (s2 + s3));
             if (j < i) {
                 S.at(i, j) = s / S.at(j, j);
             } else {
@@ -347,6 +356,7 @@ vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
             continue;
         }
         if (st != VGICP_OK) break;
+        if (pred <= opt.relative_tolerance * F) break;   // the model promises no further progress
         std::memcpy(trial.data(), poses, trial.size() * sizeof(double));
         vgicp_se3_retract(trial.data(), delta.data(), n_poses);
         t0 = Clock::now();
@@ -370,7 +380,6 @@ vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
             lambda *= 10.0;
             if (++rejects > 10) break;
         }
-        (void)pred;
     }
     rep.final_cost = F;
     rep.lambda = lambda;
