@@ -60,6 +60,8 @@ def _load():
     P("oracle_overlap_count", [_i64p, _i64, _f64, _f32p, _i64, _f64p], _i64)
     P("oracle_linearize", [_i64p, _f64p, _f64p, _i64, _f64, _f32p, _f32p, _i64, _f64p,
                            _f64p, _f64p, _f64p, _i64p, vp, vp, vp, vp])
+    P("oracle_linearize_ex", [_i64p, _f64p, _f64p, vp, _i64, _f64, C.c_int, _f32p, _f32p, _i64, _f64p,
+                              _f64p, _f64p, _f64p, _i64p, vp, vp, vp, vp])
     P("oracle_residuals", [_f64p, _f64p, _f32p, _f32p, _i64, _f64p, _i64p, _f64p, vp, vp])
     P("oracle_knn_bruteforce", [_f32p, _i64, C.c_int, _i64p])
     P("oracle_knn_grid", [_f32p, _i64, C.c_int, _f64, _i64p])
@@ -185,8 +187,14 @@ class Linearization:
     corr: np.ndarray     # (n,) voxel index per source point or -1
 
 
-def linearize(vm: Voxelmap, source_points, source_covs, T_target_source) -> Linearization:
-    """Eq. 3-6 for one factor, FP64, literal 3x12 Jacobians, naive sums in point order."""
+def linearize(vm: Voxelmap, source_points, source_covs, T_target_source, neighbors: int = 1,
+              count_weighted: bool = False) -> Linearization:
+    """Eq. 3-6 for one factor, FP64, literal 3x12 Jacobians, naive sums in point order.
+    neighbors 7 / 27: every face neighbour / every voxel of the 3x3x3 block around the
+    containing voxel is a correspondence too; count_weighted: each correspondence
+    weighted by its voxel's point count.  inliers counts correspondences."""
+    if neighbors not in (1, 7, 27):
+        raise ValueError("neighbors must be 1, 7 or 27")
     p, c = _pts(source_points), _covs(source_covs)
     n = p.shape[0]
     H, b, cost = np.zeros(144), np.zeros(12), np.zeros(1)
@@ -195,9 +203,10 @@ def linearize(vm: Voxelmap, source_points, source_covs, T_target_source) -> Line
     corr = np.zeros(max(n, 1), np.int64)
     mu = vm.mu if vm.n_voxels else np.zeros((1, 3))
     cov = vm.cov if vm.n_voxels else np.zeros((1, 6))
-    _load().oracle_linearize(_keys_arg(vm), np.ascontiguousarray(mu), np.ascontiguousarray(cov),
-                             vm.n_voxels, vm.resolution, p, c, n, _pose(T_target_source),
-                             H, b, cost, inl, _ptr(SH), _ptr(Sb), _ptr(Sc), _ptr(corr))
+    counts = np.ascontiguousarray(vm.counts, dtype=np.int64) if (count_weighted and vm.n_voxels) else None
+    _load().oracle_linearize_ex(_keys_arg(vm), np.ascontiguousarray(mu), np.ascontiguousarray(cov), _ptr(counts),
+                                vm.n_voxels, vm.resolution, int(neighbors), p, c, n, _pose(T_target_source),
+                                H, b, cost, inl, _ptr(SH), _ptr(Sb), _ptr(Sc), _ptr(corr))
     return Linearization(H.reshape(12, 12), b, float(cost[0]), int(inl[0]), SH.reshape(12, 12), Sb,
                          float(Sc[0]), corr[:n])
 

@@ -317,17 +317,47 @@ static int point_term(const double *T, const float *p, const float *ca,
     return 1;
 }
 
+/* Voxel offsets searched around a point's own voxel k: DIRECT1 = {0};
+ * DIRECT7 = k and its six face neighbours; DIRECT27 = the 3x3x3 block.  Listed
+ * as: (0,0,0), then -x, +x, -y, +y, -z, +z, then the remaining twenty with
+ * x outermost, each coordinate running -1, 0, 1. */
+static int neighbour_offsets(int nb, int off[27][3])
+{
+    static const int face[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    int m = 0;
+    for (int i = 0; i < 7 && i < nb; ++i, ++m)
+        for (int a = 0; a < 3; ++a) off[m][a] = face[i][a];
+    if (nb == 27)
+        for (int x = -1; x <= 1; ++x)
+            for (int y = -1; y <= 1; ++y)
+                for (int z = -1; z <= 1; ++z) {
+                    if (abs(x) + abs(y) + abs(z) <= 1) continue;
+                    off[m][0] = x;
+                    off[m][1] = y;
+                    off[m][2] = z;
+                    ++m;
+                }
+    return m;
+}
+
 /* Linearisation of one factor (Eq. 3-6): cost = sum e^T Omega e,
- * H = sum J^T Omega J (12x12, full), b = sum J^T Omega e, over every source point
- * whose transformed point falls in a target voxel.  S* receive the sums of the
- * absolute per-point contributions (the scale used by the error metric).
- * corr (n, nullable) receives each point's voxel index or -1. */
-void oracle_linearize(const int64_t *keys, const double *mu, const double *cov, int64_t nv, double r,
-                      const float *src, const float *src_cov, int64_t n, const double *TBA,
-                      double *H, double *b, double *cost, int64_t *inliers,
-                      double *SH, double *Sb, double *Scost, int64_t *corr)
+ * H = sum J^T Omega J (12x12, full), b = sum J^T Omega e, over every
+ * correspondence (source point, target voxel).  nb = 1: the voxel containing
+ * the transformed point (Sec. III-A); nb = 7 or 27: also its face neighbours
+ * or its whole 3x3x3 block (the DIRECT7 / DIRECT27 association of the earlier
+ * VGICP paper), each neighbour a correspondence of its own with e = mu_v - q.
+ * counts != NULL weights each correspondence by its voxel's point count.
+ * S* receive the sums of the absolute per-correspondence contributions (the
+ * scale used by the error metric); inliers counts correspondences.  corr (n,
+ * nullable) receives each point's containing-voxel index or -1. */
+void oracle_linearize_ex(const int64_t *keys, const double *mu, const double *cov, const int64_t *counts,
+                         int64_t nv, double r, int nb, const float *src, const float *src_cov, int64_t n,
+                         const double *TBA, double *H, double *b, double *cost, int64_t *inliers, double *SH,
+                         double *Sb, double *Scost, int64_t *corr)
 {
     const double inv_r = 1.0 / r;
+    int off[27][3];
+    const int no = neighbour_offsets(nb, off);
     memset(H, 0, sizeof(double) * 144);
     memset(b, 0, sizeof(double) * 12);
     if (SH) memset(SH, 0, sizeof(double) * 144);
@@ -336,39 +366,54 @@ void oracle_linearize(const int64_t *keys, const double *mu, const double *cov, 
     int64_t in = 0;
     for (int64_t i = 0; i < n; ++i) {
         double q[3], e[3], Om[3][3], J[3][12];
-        int64_t k[3], v = -1;
-        if (voxel_coord(TBA, src + 3 * i, inv_r, q, k)) v = oracle_lookup(keys, nv, k);
-        if (corr) corr[i] = v;
-        if (v < 0) continue;
-        if (!point_term(TBA, src + 3 * i, src_cov + 6 * i, mu + 3 * v, cov + 6 * v, q, e, Om, J)) continue;
-        double OJ[3][12], Oe[3];
-        for (int a = 0; a < 3; ++a) {
-            for (int j = 0; j < 12; ++j) {
-                double s = 0.0;
-                for (int m = 0; m < 3; ++m) s = s + Om[a][m] * J[m][j];
-                OJ[a][j] = s;
+        int64_t k[3];
+        const int valid = voxel_coord(TBA, src + 3 * i, inv_r, q, k);
+        if (corr) corr[i] = valid ? oracle_lookup(keys, nv, k) : -1;
+        if (!valid) continue;
+        for (int o = 0; o < no; ++o) {
+            int64_t kk[3];
+            int inside = 1;
+            for (int a = 0; a < 3; ++a) {
+                kk[a] = k[a] + off[o][a];
+                inside = inside && kk[a] >= -1048576 && kk[a] <= 1048575;
             }
-            double s = 0.0;
-            for (int m = 0; m < 3; ++m) s = s + Om[a][m] * e[m];
-            Oe[a] = s;
-        }
-        double ck = 0.0;
-        for (int a = 0; a < 3; ++a) ck = ck + e[a] * Oe[a];
-        c = c + ck;
-        sc = sc + fabs(ck);
-        for (int a = 0; a < 12; ++a) {
-            for (int j = a; j < 12; ++j) {   /* upper triangle; H is symmetric by definition */
-                double s = 0.0;
-                for (int m = 0; m < 3; ++m) s = s + J[m][a] * OJ[m][j];
-                H[12 * a + j] = H[12 * a + j] + s;
-                if (SH) SH[12 * a + j] = SH[12 * a + j] + fabs(s);
+            const int64_t v = inside ? oracle_lookup(keys, nv, kk) : -1;
+            if (v < 0) continue;
+            if (!point_term(TBA, src + 3 * i, src_cov + 6 * i, mu + 3 * v, cov + 6 * v, q, e, Om, J)) continue;
+            if (counts) {
+                const double w = (double)counts[v];
+                for (int a = 0; a < 3; ++a)
+                    for (int m = 0; m < 3; ++m) Om[a][m] = Om[a][m] * w;
             }
-            double s = 0.0;
-            for (int m = 0; m < 3; ++m) s = s + J[m][a] * Oe[m];
-            b[a] = b[a] + s;
-            if (Sb) Sb[a] = Sb[a] + fabs(s);
+            double OJ[3][12], Oe[3];
+            for (int a = 0; a < 3; ++a) {
+                for (int j = 0; j < 12; ++j) {
+                    double s = 0.0;
+                    for (int m = 0; m < 3; ++m) s = s + Om[a][m] * J[m][j];
+                    OJ[a][j] = s;
+                }
+                double s = 0.0;
+                for (int m = 0; m < 3; ++m) s = s + Om[a][m] * e[m];
+                Oe[a] = s;
+            }
+            double ck = 0.0;
+            for (int a = 0; a < 3; ++a) ck = ck + e[a] * Oe[a];
+            c = c + ck;
+            sc = sc + fabs(ck);
+            for (int a = 0; a < 12; ++a) {
+                for (int j = a; j < 12; ++j) {   /* upper triangle; H is symmetric by definition */
+                    double s = 0.0;
+                    for (int m = 0; m < 3; ++m) s = s + J[m][a] * OJ[m][j];
+                    H[12 * a + j] = H[12 * a + j] + s;
+                    if (SH) SH[12 * a + j] = SH[12 * a + j] + fabs(s);
+                }
+                double s = 0.0;
+                for (int m = 0; m < 3; ++m) s = s + J[m][a] * Oe[m];
+                b[a] = b[a] + s;
+                if (Sb) Sb[a] = Sb[a] + fabs(s);
+            }
+            ++in;
         }
-        ++in;
     }
     for (int a = 0; a < 12; ++a)
         for (int j = 0; j < a; ++j) {
@@ -378,6 +423,16 @@ void oracle_linearize(const int64_t *keys, const double *mu, const double *cov, 
     *cost = c;
     if (Scost) *Scost = sc;
     if (inliers) *inliers = in;
+}
+
+/* The single-voxel, unweighted linearisation (Sec. III-A association). */
+void oracle_linearize(const int64_t *keys, const double *mu, const double *cov, int64_t nv, double r,
+                      const float *src, const float *src_cov, int64_t n, const double *TBA,
+                      double *H, double *b, double *cost, int64_t *inliers,
+                      double *SH, double *Sb, double *Scost, int64_t *corr)
+{
+    oracle_linearize_ex(keys, mu, cov, NULL, nv, r, 1, src, src_cov, n, TBA, H, b, cost, inliers, SH, Sb, Scost,
+                        corr);
 }
 
 /* Per-point residuals and Jacobians under a frozen correspondence list corr
