@@ -115,6 +115,17 @@ typedef struct {
      * (chunk boxes kept per frame) lets the linearisation skip work items whose
      * chunks all miss the target's voxels; results are unchanged. */
     int32_t linearize_cull;
+    /* Correspondences of a source point (linearisation and evaluation; the
+     * overlap of Eq. 8 always uses the containing voxel): 1 (default) the voxel
+     * containing the transformed point (Sec. III-A); 7 also its six face
+     * neighbours; 27 every voxel of its 3x3x3 block (the DIRECT7 / DIRECT27
+     * association of the earlier VGICP formulation).  Each found voxel v is a
+     * correspondence of its own with e = mu_v - T_BA p; inliers count them.
+     * Chunk culling is off for 7 and 27. */
+    int32_t neighbors;
+    /* 1: each correspondence weighted by its voxel's point count (Omega scaled
+     * by it); 0 (default): unweighted, as Eq. 2, 5, 6. */
+    int32_t count_weighted;
 } vgicp_options;
 
 /* Fill *opt with the defaults above. */

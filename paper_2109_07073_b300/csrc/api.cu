@@ -469,6 +469,9 @@ vgicp_status read_nvox(vgicp_ctx *ctx, const Obj &o, int64_t *n)
 }
 
 int default_chunk(const vgicp_options &o) { return o.chunk_points > 0 ? o.chunk_points : 2048; }
+int neighbor_count(const vgicp_options &o) { return o.neighbors > 1 ? o.neighbors : 1; }
+// chunk culling tests the target's voxel box, so it holds for the containing voxel only
+int lin_cull(const vgicp_options &o) { return neighbor_count(o) == 1 ? o.linearize_cull : 0; }
 
 // Descriptor-table indices of a factor set (map, frame, target pose, source
 // pose per factor), after checking handles, pose indices and pose entries.
@@ -570,6 +573,7 @@ vgicp_status vgicp_options_default(vgicp_options *opt)
     std::memset(opt, 0, sizeof(*opt));
     opt->precision = VGICP_PREC_F32;
     opt->chunk_points = 2048;
+    opt->neighbors = 1;
     opt->linearize_variant = 0;
     opt->blocks_per_sm = 0;
     opt->hbm_budget_bytes = 0;
@@ -584,6 +588,10 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "precision must be VGICP_PREC_F32, VGICP_PREC_F64 or VGICP_PREC_F32_COMP");
     if (o->chunk_points < 0 || (o->chunk_points % 32) != 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "chunk_points must be a non-negative multiple of 32");
+    if (o->neighbors != 0 && o->neighbors != 1 && o->neighbors != 7 && o->neighbors != 27)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "neighbors must be 1, 7 or 27");
+    if (o->count_weighted != 0 && o->count_weighted != 1)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "count_weighted must be 0 or 1");
     if (o->linearize_variant < 0 || o->linearize_variant > 5)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_variant must be in 0..5");
     if (o->blocks_per_sm < 0 || o->hbm_budget_bytes < 0)
@@ -832,7 +840,7 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
     TRY(ensure(ctx, LN.ws_params, (size_t)n_f * sizeof(PoseParam)));
     PoseParam *d_params = (PoseParam *)LN.ws_params.p;
     launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)LN.ws_poses.p, ctx->d_maps,
-                           ctx->d_frames, ctx->opt.linearize_cull, d_params, LN.stream);
+                           ctx->d_frames, lin_cull(ctx->opt), d_params, LN.stream);
     ctx->launches += 1;
     CHECK_LAUNCH();
     // outputs: caller's device buffers, or a device workspace copied back to the host
@@ -857,7 +865,8 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
             int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, (n + blk - 1) / blk));
             launch_linearize_f64(d_params + i, ctx->d_maps, ctx->d_frames, n, (double *)LN.ws_f64.p,
                                  (unsigned int *)LN.ws_ticket.p, dH + 144 * i, db + 12 * i, dc + i,
-                                 di ? di + i : nullptr, grid, LN.stream);
+                                 di ? di + i : nullptr, grid, neighbor_count(ctx->opt), ctx->opt.count_weighted,
+                                 LN.stream);
         }
         ctx->launches += n_f;
         CHECK_LAUNCH();
@@ -868,7 +877,8 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
                              (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p,
                              ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
-                             ctx->opt.precision == VGICP_PREC_F32_COMP, LN.stream);
+                             ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt),
+                             ctx->opt.count_weighted, LN.stream);
         launch_reduce_finalize(d_params, (const int32_t *)P.item_range.p, (int)n_f, (const double *)LN.ws_partials.p,
                                (const int64_t *)LN.ws_inl.p, dH, db, dc, di, LN.stream);
         ctx->launches += (P.n_items > 0) + 1;
@@ -911,7 +921,7 @@ struct vgicp_plan {
     // what the graph was captured with
     MapDesc *maps = nullptr;
     FrameDesc *frames = nullptr;
-    int chunk = 0, variant = -1, bps = -1, cull = -1, prec = -1;
+    int chunk = 0, variant = -1, bps = -1, cull = -1, prec = -1, nb = -1, weighted = -1;
     int64_t runs = 0, captures = 0;
 };
 
@@ -942,7 +952,8 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
     const bool same_work = chunk == P->chunk && idx == P->idx && fn == P->frame_n;
     if (same_work && P->exec && P->maps == ctx->d_maps && P->frames == ctx->d_frames &&
         P->variant == ctx->opt.linearize_variant && P->bps == ctx->opt.blocks_per_sm &&
-        P->cull == ctx->opt.linearize_cull && P->prec == ctx->opt.precision)
+        P->cull == ctx->opt.linearize_cull && P->prec == ctx->opt.precision && P->nb == neighbor_count(ctx->opt) &&
+        P->weighted == ctx->opt.count_weighted)
         return VGICP_OK;
     if (P->in_flight) {
         CU(cudaEventSynchronize(P->done));
@@ -973,11 +984,12 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
     CU(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(P->d_poses.p, P->h_poses, (size_t)P->n_poses * 12 * 8, cudaMemcpyHostToDevice, P->cap);
     launch_prepare_factors((const int32_t *)P->d_idx.p, (int)n_f, (const double *)P->d_poses.p, ctx->d_maps,
-                           ctx->d_frames, ctx->opt.linearize_cull, params, P->cap);
+                           ctx->d_frames, lin_cull(ctx->opt), params, P->cap);
     launch_linearize_f32(params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P->d_items.p, P->n_items,
                          (double *)P->d_partials.p, (int64_t *)P->d_inl.p, (int *)P->d_fetch.p,
                          ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
-                         ctx->opt.precision == VGICP_PREC_F32_COMP, P->cap);
+                         ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt),
+                         ctx->opt.count_weighted, P->cap);
     launch_reduce_finalize(params, (const int32_t *)P->d_range.p, (int)n_f, (const double *)P->d_partials.p,
                            (const int64_t *)P->d_inl.p, H, b, c, inl, P->cap);
     cudaGraph_t g = nullptr;
@@ -999,6 +1011,8 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
     P->bps = ctx->opt.blocks_per_sm;
     P->cull = ctx->opt.linearize_cull;
     P->prec = ctx->opt.precision;
+    P->nb = neighbor_count(ctx->opt);
+    P->weighted = ctx->opt.count_weighted;
     P->captures += 1;
     return VGICP_OK;
 }
@@ -1127,7 +1141,7 @@ vgicp_status vgicp_evaluate(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     TRY(ensure(ctx, LN.ws_params, (size_t)n_f * sizeof(PoseParam)));
     PoseParam *d_params = (PoseParam *)LN.ws_params.p;
     launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)LN.ws_poses.p, ctx->d_maps,
-                           ctx->d_frames, ctx->opt.linearize_cull, d_params, LN.stream);
+                           ctx->d_frames, lin_cull(ctx->opt), d_params, LN.stream);
     double *dc = cost;
     int64_t *di = inliers;
     if (out_kind == VGICP_MEM_HOST) {
@@ -1141,7 +1155,8 @@ vgicp_status vgicp_evaluate(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     launch_cost_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
                     (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p,
                     ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
-                    ctx->opt.precision == VGICP_PREC_F32_COMP, LN.stream);
+                    ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt), ctx->opt.count_weighted,
+                    LN.stream);
     launch_reduce_cost((const int32_t *)P.item_range.p, (int)n_f, (const double *)LN.ws_partials.p,
                        (const int64_t *)LN.ws_inl.p, dc, di, LN.stream);
     ctx->launches += 2 + (P.n_items > 0);
@@ -1575,6 +1590,9 @@ bool ctx_view(vgicp_ctx *ctx, CtxView *v)
     v->variant = ctx->opt.linearize_variant;
     v->linearize_cull = ctx->opt.linearize_cull;
     v->compensated = ctx->opt.precision == VGICP_PREC_F32_COMP;
+    v->neighbors = neighbor_count(ctx->opt);
+    v->count_weighted = ctx->opt.count_weighted;
+    v->linearize_cull = lin_cull(ctx->opt);
     v->blocks_per_sm = ctx->opt.blocks_per_sm;
     v->d_maps = ctx->d_maps;
     v->d_frames = ctx->d_frames;

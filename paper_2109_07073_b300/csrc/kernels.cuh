@@ -71,14 +71,14 @@ void launch_prepare_given(const double *T, int map, int frame, const MapDesc *ma
 // grid_per_sm: blocks per SM of the persistent grid (0 = the variant's own).
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
                           const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
-                          int *next_item, int variant, int grid_per_sm, int num_sms, bool compensated,
-                          cudaStream_t st);
+                          int *next_item, int variant, int grid_per_sm, int num_sms, bool compensated, int nb,
+                          int weighted, cudaStream_t st);
 
 // Per-factor fixed-order float64 reduction of the item partials and expansion
 // to the 12x12 H, b, cost.  item_begin has n_f + 1 entries.
 void launch_cost_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                      int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
-                     int grid_per_sm, int num_sms, bool compensated, cudaStream_t st);
+                     int grid_per_sm, int num_sms, bool compensated, int nb, int weighted, cudaStream_t st);
 void launch_reduce_cost(const int32_t *item_range, int n_f, const double *partials, const int64_t *inl_partials,
                         double *cost, int64_t *inliers, cudaStream_t st);
 void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, int n_f, const double *partials,
@@ -89,7 +89,7 @@ void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, 
 // scratch holds grid x 92 doubles; ticket is one zeroed int (reset by the kernel).
 void launch_linearize_f64(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,
                           double *scratch, unsigned int *ticket, double *H, double *b, double *cost,
-                          int64_t *inliers, int grid, cudaStream_t st);
+                          int64_t *inliers, int grid, int nb, int weighted, cudaStream_t st);
 int linearize_f64_block();
 
 // ----------------------------------------------------------- overlap -----
@@ -140,6 +140,7 @@ struct CtxView {
     cudaStream_t stream;
     int device, num_sms, chunk, variant, blocks_per_sm, linearize_cull;
     bool compensated;
+    int neighbors, count_weighted;
     MapDesc *d_maps;
     FrameDesc *d_frames;
 };

@@ -374,11 +374,9 @@ __device__ __forceinline__ int accumulate_cost(float acc[1], const float *R, con
 }
 
 // One correspondence's contribution (Eq. 2, 5, 6 in the adjoint form) added to acc.
-__device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, const float4 &A, const float4 &B,
-                                                float C22, const VoxelRec &v, const float d[3], const float x[3])
+__device__ __forceinline__ void accumulate_terms(float acc[kNT], const float e[3], const float o[6], const float w[3],
+                                                 const float x[3])
 {
-    float e[3], o[6], w[3];
-    if (!point_omega(R, A, B, C22, v, d, e, o, w)) return 0;
     const float e0 = e[0], e1 = e[1], e2 = e[2];
     const float o00 = o[0], o01 = o[1], o02 = o[2], o11 = o[3], o12 = o[4], o22 = o[5];
     const float w0 = w[0], w1 = w[1], w2 = w[2];
@@ -404,6 +402,14 @@ __device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, 
     acc[23] += x0 * w1 - x1 * w0;
     acc[24] += w0; acc[25] += w1; acc[26] += w2;
     acc[27] += e0 * w0 + e1 * w1 + e2 * w2;
+}
+
+__device__ __forceinline__ int accumulate_point(float acc[kNT], const float *R, const float4 &A, const float4 &B,
+                                                float C22, const VoxelRec &v, const float d[3], const float x[3])
+{
+    float e[3], o[6], w[3];
+    if (!point_omega(R, A, B, C22, v, d, e, o, w)) return 0;
+    accumulate_terms(acc, e, o, w, x);
     return 1;
 }
 
@@ -415,6 +421,75 @@ __device__ __forceinline__ int accumulate(float acc[NT], const float *R, const f
         return accumulate_cost(acc, R, A, B, C22, v, d);
     else
         return accumulate_point(acc, R, A, B, C22, v, d, x);
+}
+
+// A correspondence weighted by wgt (the voxel's point count): Omega scaled.
+template <int NT>
+__device__ __forceinline__ int accumulate_weighted(float acc[NT], const float *R, const float4 &A, const float4 &B,
+                                                   float C22, const VoxelRec &v, const float d[3], const float x[3],
+                                                   float wgt)
+{
+    float e[3], o[6], w[3];
+    if (!point_omega(R, A, B, C22, v, d, e, o, w)) return 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) o[j] *= wgt;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) w[j] *= wgt;
+    if constexpr (NT == 1)
+        acc[0] += e[0] * w[0] + e[1] * w[1] + e[2] * w[2];
+    else
+        accumulate_terms(acc, e, o, w, x);
+    return 1;
+}
+
+// Voxel offsets searched around a point's own voxel for the neighbour
+// association: the own voxel, the six face neighbours (-x, +x, -y, +y, -z, +z),
+// then the twenty other voxels of the 3x3x3 block, x outermost, each coordinate
+// running -1, 0, 1.  The first 1, 7 or 27 entries are used.
+__constant__ int8_t c_nb_off[27][3] = {
+    {0, 0, 0},   {-1, 0, 0},  {1, 0, 0},   {0, -1, 0},  {0, 1, 0},   {0, 0, -1},  {0, 0, 1},
+    {-1, -1, -1}, {-1, -1, 0}, {-1, -1, 1}, {-1, 0, -1}, {-1, 0, 1},  {-1, 1, -1}, {-1, 1, 0},
+    {-1, 1, 1},  {0, -1, -1}, {0, -1, 1},  {0, 1, -1},  {0, 1, 1},   {1, -1, -1}, {1, -1, 0},
+    {1, -1, 1},  {1, 0, -1},  {1, 0, 1},   {1, 1, -1},  {1, 1, 0},   {1, 1, 1}};
+
+// Points of one work item for the variants: every voxel of the neighbour set
+// around the point's own voxel is a correspondence (e = mu_v - q, the point's
+// offset taken relative to that voxel's corner), optionally weighted by the
+// voxel's point count.  One point per lane per step, plain loads.
+template <int NT, bool FF>
+__device__ __forceinline__ void linearize_points_general(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
+                                                         const WorkItem &w, int lane, float acc[NT], int &inl,
+                                                         int nb, int weighted)
+{
+    const float4 *__restrict__ pa = F.pa + w.start;
+    const float4 *__restrict__ pb = F.pb + w.start;
+    const float *__restrict__ pc = F.pc + w.start;
+    for (int i = lane; i < w.count; i += 32) {
+        const float4 A = __ldg(pa + i), B = __ldg(pb + i);
+        const float C = __ldg(pc + i);
+        int k[3];
+        float d[3], x[3];
+        const bool ok = FF ? point_key_ff(P, m, A.x, A.y, A.z, k, d, x) : point_key_split(P, m, A.x, A.y, A.z, k, d, x);
+        if (!ok) continue;
+        for (int j = 0; j < nb; ++j) {
+            int kk[3];
+            bool in = true;
+            float dj[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int o = c_nb_off[j][a];
+                kk[a] = k[a] + o;
+                in = in && kk[a] >= -kKeyOffset && kk[a] <= kKeyOffset - 1;
+                dj[a] = __fmaf_rn(-(float)o, m.r_l, __fmaf_rn(-(float)o, m.r_h, d[a]));
+            }
+            if (!in) continue;
+            const int slot = probe(m.keys, m.mask, m.log2cap, pack_key(kk[0], kk[1], kk[2]));
+            if (slot < 0) continue;
+            const VoxelRec v = m.rec[slot];
+            const float wgt = weighted ? (float)__float_as_uint(v.c.y) : 1.f;
+            inl += accumulate_weighted<NT>(acc, P.Rh, A, B, C, v, dj, x, wgt);
+        }
+    }
 }
 
 // Work items belong to single warps: a warp copies its factor's parameters to
@@ -629,13 +704,15 @@ __device__ __forceinline__ void linearize_points_staged(const PoseParam &P, cons
 template <int PTS, bool FF, int NT>
 __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
                                                     const WorkItem &w, int lane, float acc[NT], int &inl,
-                                                    WarpStage *S)
+                                                    WarpStage *S, int nb, int weighted)
 {
     if (w.count <= 0) return;
     const int c0 = (int)(w.start >> F.cshift), c1 = (int)((w.start + w.count - 1) >> F.cshift);
     const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
     if ((P.cmask & span) == 0u) return;
-    if constexpr (PTS == 0)
+    if (nb > 1 || weighted)
+        linearize_points_general<NT, FF>(P, m, F, w, lane, acc, inl, nb, weighted);
+    else if constexpr (PTS == 0)
         linearize_points_staged<FF, NT>(P, m, F, w, lane, acc, inl, *S);
     else
         linearize_points<PTS, FF, NT>(P, m, F, w, lane, acc, inl);
@@ -648,7 +725,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
                                                                const WorkItem *__restrict__ items, int n_items,
                                                                double *__restrict__ partials,
                                                                int64_t *__restrict__ inl_partials,
-                                                               int *__restrict__ next_item)
+                                                               int *__restrict__ next_item, int nb, int weighted)
 {
     constexpr int NW = BLOCK / 32;
     constexpr int PW = (int)(sizeof(PoseParam) / 4);
@@ -678,7 +755,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
 #pragma unroll
         for (int j = 0; j < NT; ++j) acc[j] = 0.f;
         int inl = 0;
-        linearize_warp_item<PTS, FF, NT>(P, m, F, w, lane, acc, inl, sS + (PTS == 0 ? wib : 0));
+        linearize_warp_item<PTS, FF, NT>(P, m, F, w, lane, acc, inl, sS + (PTS == 0 ? wib : 0), nb, weighted);
         // butterfly: every lane ends with the warp's sums; lane j writes sum j
         // (a cost-only pass takes its sum from the lane that holds the cost in the
         // full pass, so both passes' costs agree bit for bit)
@@ -812,7 +889,8 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
                                                              const FrameDesc *__restrict__ frames, int64_t n,
                                                              double *__restrict__ scratch, unsigned int *ticket,
                                                              double *__restrict__ H, double *__restrict__ b,
-                                                             double *__restrict__ cost, int64_t *__restrict__ inliers)
+                                                             double *__restrict__ cost, int64_t *__restrict__ inliers,
+                                                             int nb, int weighted)
 {
     __shared__ double sT[kF64Terms][kF64Block];
     __shared__ int sInl[kF64Block];
@@ -825,89 +903,91 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
     int inl = 0;
     for (int64_t base = (int64_t)blockIdx.x * kF64Block; base < n; base += (int64_t)gridDim.x * kF64Block) {
         const int64_t i = base + tid;
-        bool have = false;
-        double J[3][12], e[3], Om[3][3];
+#pragma unroll
+        for (int t = 0; t < kF64Terms; ++t) sT[t][tid] = 0.0;
         if (i < n) {
             const float4 A = F.pa[i], B = F.pb[i];
             const float C22 = F.pc[i];
             int k[3];
             double q[3];
-            if (key_f64(P.T, A.x, A.y, A.z, m.inv_r, k, q)) {
-                const int slot = probe(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2]));
-                if (slot >= 0) {
-                    const VoxelRec v = m.rec[slot];
-                    double R[3][3];
+            const bool valid = key_f64(P.T, A.x, A.y, A.z, m.inv_r, k, q);
+            // correspondences: the containing voxel, or every voxel of the neighbour set
+            for (int j = 0; valid && j < nb; ++j) {
+                int kk[3];
+                bool in = true;
 #pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) R[r][c] = P.T[4 * r + c];
-                    const double CA[3][3] = {{A.w, B.x, B.y}, {B.x, B.z, B.w}, {B.y, B.w, C22}};
-                    const double CB[3][3] = {{v.a.w, v.b.x, v.b.y}, {v.b.x, v.b.z, v.b.w}, {v.b.y, v.b.w, v.c.x}};
-                    double RC[3][3], M[3][3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) RC[r][c] = R[r][0] * CA[0][c] + R[r][1] * CA[1][c] + R[r][2] * CA[2][c];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            M[r][c] = CB[r][c] + RC[r][0] * R[c][0] + RC[r][1] * R[c][1] + RC[r][2] * R[c][2];
-                    // symmetric inverse by the adjugate (M is symmetric positive definite)
-                    const double c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
-                    const double c01 = M[0][2] * M[2][1] - M[0][1] * M[2][2];
-                    const double c02 = M[0][1] * M[1][2] - M[0][2] * M[1][1];
-                    const double c11 = M[0][0] * M[2][2] - M[0][2] * M[2][0];
-                    const double c12 = M[0][2] * M[1][0] - M[0][0] * M[1][2];
-                    const double c22 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
-                    const double det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
-                    if (det > 0.0) {
-                        const double id = 1.0 / det;
-                        Om[0][0] = c00 * id; Om[0][1] = c01 * id; Om[0][2] = c02 * id;
-                        Om[1][0] = c01 * id; Om[1][1] = c11 * id; Om[1][2] = c12 * id;
-                        Om[2][0] = c02 * id; Om[2][1] = c12 * id; Om[2][2] = c22 * id;
-                        // mean relative to the voxel corner back to absolute target coordinates
-                        const double mu[3] = {(double)k[0] * m.r + (double)v.a.x, (double)k[1] * m.r + (double)v.a.y,
-                                              (double)k[2] * m.r + (double)v.a.z};
-#pragma unroll
-                        for (int r = 0; r < 3; ++r) e[r] = mu[r] - q[r];
-                        const double px = A.x, py = A.y, pz = A.z;
-                        const double Pm[3][3] = {{0, -pz, py}, {pz, 0, -px}, {-py, px, 0}};
-                        const double Qm[3][3] = {{0, -q[2], q[1]}, {q[2], 0, -q[0]}, {-q[1], q[0], 0}};
-#pragma unroll
-                        for (int r = 0; r < 3; ++r)
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                J[r][c] = -Qm[r][c];
-                                J[r][3 + c] = (r == c) ? 1.0 : 0.0;
-                                J[r][6 + c] = R[r][0] * Pm[0][c] + R[r][1] * Pm[1][c] + R[r][2] * Pm[2][c];
-                                J[r][9 + c] = -R[r][c];
-                            }
-                        have = true;
-                    }
+                for (int a = 0; a < 3; ++a) {
+                    kk[a] = k[a] + c_nb_off[j][a];
+                    in = in && kk[a] >= -kKeyOffset && kk[a] <= kKeyOffset - 1;
                 }
+                if (!in) continue;
+                const int slot = probe(m.keys, m.mask, m.log2cap, pack_key(kk[0], kk[1], kk[2]));
+                if (slot < 0) continue;
+                const VoxelRec v = m.rec[slot];
+                double R[3][3], J[3][12], e[3], Om[3][3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) R[r][c] = P.T[4 * r + c];
+                const double CA[3][3] = {{A.w, B.x, B.y}, {B.x, B.z, B.w}, {B.y, B.w, C22}};
+                const double CB[3][3] = {{v.a.w, v.b.x, v.b.y}, {v.b.x, v.b.z, v.b.w}, {v.b.y, v.b.w, v.c.x}};
+                double RC[3][3], M[3][3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) RC[r][c] = R[r][0] * CA[0][c] + R[r][1] * CA[1][c] + R[r][2] * CA[2][c];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        M[r][c] = CB[r][c] + RC[r][0] * R[c][0] + RC[r][1] * R[c][1] + RC[r][2] * R[c][2];
+                // symmetric inverse by the adjugate (M is symmetric positive definite)
+                const double c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+                const double c01 = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+                const double c02 = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+                const double c11 = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+                const double c12 = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+                const double c22 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+                const double det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
+                if (!(det > 0.0)) continue;
+                const double id = (weighted ? (double)__float_as_uint(v.c.y) : 1.0) / det;
+                Om[0][0] = c00 * id; Om[0][1] = c01 * id; Om[0][2] = c02 * id;
+                Om[1][0] = c01 * id; Om[1][1] = c11 * id; Om[1][2] = c12 * id;
+                Om[2][0] = c02 * id; Om[2][1] = c12 * id; Om[2][2] = c22 * id;
+                // mean relative to the voxel corner back to absolute target coordinates
+                const double mu[3] = {(double)kk[0] * m.r + (double)v.a.x, (double)kk[1] * m.r + (double)v.a.y,
+                                      (double)kk[2] * m.r + (double)v.a.z};
+#pragma unroll
+                for (int r = 0; r < 3; ++r) e[r] = mu[r] - q[r];
+                const double px = A.x, py = A.y, pz = A.z;
+                const double Pm[3][3] = {{0, -pz, py}, {pz, 0, -px}, {-py, px, 0}};
+                const double Qm[3][3] = {{0, -q[2], q[1]}, {q[2], 0, -q[0]}, {-q[1], q[0], 0}};
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        J[r][c] = -Qm[r][c];
+                        J[r][3 + c] = (r == c) ? 1.0 : 0.0;
+                        J[r][6 + c] = R[r][0] * Pm[0][c] + R[r][1] * Pm[1][c] + R[r][2] * Pm[2][c];
+                        J[r][9 + c] = -R[r][c];
+                    }
+                ++inl;
+                double W[3][12], Oe[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) W[r][c] = Om[r][0] * J[0][c] + Om[r][1] * J[1][c] + Om[r][2] * J[2][c];
+                    Oe[r] = Om[r][0] * e[0] + Om[r][1] * e[1] + Om[r][2] * e[2];
+                }
+                int t = 0;
+#pragma unroll
+                for (int a = 0; a < 12; ++a)
+#pragma unroll
+                    for (int c = a; c < 12; ++c) sT[t++][tid] += J[0][a] * W[0][c] + J[1][a] * W[1][c] + J[2][a] * W[2][c];
+#pragma unroll
+                for (int a = 0; a < 12; ++a) sT[78 + a][tid] += J[0][a] * Oe[0] + J[1][a] * Oe[1] + J[2][a] * Oe[2];
+                sT[90][tid] += e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];
             }
-        }
-        if (have) {
-            ++inl;
-            double W[3][12], Oe[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-#pragma unroll
-                for (int c = 0; c < 12; ++c) W[r][c] = Om[r][0] * J[0][c] + Om[r][1] * J[1][c] + Om[r][2] * J[2][c];
-                Oe[r] = Om[r][0] * e[0] + Om[r][1] * e[1] + Om[r][2] * e[2];
-            }
-            int t = 0;
-#pragma unroll
-            for (int a = 0; a < 12; ++a)
-#pragma unroll
-                for (int c = a; c < 12; ++c) sT[t++][tid] = J[0][a] * W[0][c] + J[1][a] * W[1][c] + J[2][a] * W[2][c];
-#pragma unroll
-            for (int a = 0; a < 12; ++a) sT[78 + a][tid] = J[0][a] * Oe[0] + J[1][a] * Oe[1] + J[2][a] * Oe[2];
-            sT[90][tid] = e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];
-        } else {
-#pragma unroll
-            for (int t = 0; t < kF64Terms; ++t) sT[t][tid] = 0.0;
         }
         __syncthreads();
         for (int c = 0; c < kF64Block; ++c) {
@@ -993,43 +1073,43 @@ void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, cons
 template <bool FF, int NT>
 void launch_variant(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                     int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
-                    int grid_per_sm, int num_sms, cudaStream_t st)
+                    int grid_per_sm, int num_sms, int nb, int weighted, cudaStream_t st)
 {
     switch (variant) {
     case 1: {   // one point per step + prefetch, 128-thread blocks, 6 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
         k_linearize_f32<128, 6, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item);
+                                                           inl_partials, next_item, nb, weighted);
         break;
     }
     case 2: {   // two points per step, 128-thread blocks, 4 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
         k_linearize_f32<128, 4, 2, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item);
+                                                           inl_partials, next_item, nb, weighted);
         break;
     }
     case 3: {   // one point per step + prefetch, 128-thread blocks, 4 per SM (no register cap below 128)
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
         k_linearize_f32<128, 4, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item);
+                                                           inl_partials, next_item, nb, weighted);
         break;
     }
     case 4: {   // cp.async pipeline (points two steps, probes one step ahead), 128-thread blocks, 5 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
         k_linearize_f32<128, 5, 0, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item);
+                                                           inl_partials, next_item, nb, weighted);
         break;
     }
     case 5: {   // cp.async pipeline, 128-thread blocks, 6 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
         k_linearize_f32<128, 6, 0, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item);
+                                                           inl_partials, next_item, nb, weighted);
         break;
     }
     default: {  // one point per step + prefetch, 128-thread blocks, 5 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
         k_linearize_f32<128, 5, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item);
+                                                           inl_partials, next_item, nb, weighted);
         break;
     }
     }
@@ -1037,31 +1117,31 @@ void launch_variant(const PoseParam *params, const MapDesc *maps, const FrameDes
 
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
                           const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
-                          int *next_item, int variant, int grid_per_sm, int num_sms, bool compensated,
-                          cudaStream_t st)
+                          int *next_item, int variant, int grid_per_sm, int num_sms, bool compensated, int nb,
+                          int weighted, cudaStream_t st)
 {
     if (n_items <= 0) return;
     cudaMemsetAsync(next_item, 0, sizeof(int), st);
     if (compensated)
         launch_variant<true, kNT>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
-                                  grid_per_sm, num_sms, st);
+                                  grid_per_sm, num_sms, nb, weighted, st);
     else
         launch_variant<false, kNT>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
-                                   grid_per_sm, num_sms, st);
+                                   grid_per_sm, num_sms, nb, weighted, st);
 }
 
 void launch_cost_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                      int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
-                     int grid_per_sm, int num_sms, bool compensated, cudaStream_t st)
+                     int grid_per_sm, int num_sms, bool compensated, int nb, int weighted, cudaStream_t st)
 {
     if (n_items <= 0) return;
     cudaMemsetAsync(next_item, 0, sizeof(int), st);
     if (compensated)
         launch_variant<true, 1>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
-                                grid_per_sm, num_sms, st);
+                                grid_per_sm, num_sms, nb, weighted, st);
     else
         launch_variant<false, 1>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
-                                 grid_per_sm, num_sms, st);
+                                 grid_per_sm, num_sms, nb, weighted, st);
 }
 
 void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, int n_f, const double *partials,
@@ -1084,9 +1164,10 @@ int linearize_f64_block() { return kF64Block; }
 
 void launch_linearize_f64(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,
                           double *scratch, unsigned int *ticket, double *H, double *b, double *cost,
-                          int64_t *inliers, int grid, cudaStream_t st)
+                          int64_t *inliers, int grid, int nb, int weighted, cudaStream_t st)
 {
-    k_linearize_f64<<<grid, kF64Block, 0, st>>>(param, maps, frames, n, scratch, ticket, H, b, cost, inliers);
+    k_linearize_f64<<<grid, kF64Block, 0, st>>>(param, maps, frames, n, scratch, ticket, H, b, cost, inliers, nb,
+                                                weighted);
 }
 
 }  // namespace vg

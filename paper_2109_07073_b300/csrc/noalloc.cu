@@ -166,7 +166,7 @@ extern "C" vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_fact
     k_noalloc_plan<<<1, threads, 0, v.stream>>>(d_f, (int)n_f, v.d_frames, v.chunk, d_idx, d_begin, d_items);
     launch_prepare_factors(d_idx, (int)n_f, d_poses, v.d_maps, v.d_frames, v.linearize_cull, d_params, v.stream);
     launch_linearize_f32(d_params, v.d_maps, v.d_frames, d_items, (int)n_items, d_partials, d_inl, d_fetch, v.variant,
-                         v.blocks_per_sm, v.num_sms, v.compensated, v.stream);
+                         v.blocks_per_sm, v.num_sms, v.compensated, v.neighbors, v.count_weighted, v.stream);
     launch_reduce_finalize(d_params, d_begin, (int)n_f, d_partials, d_inl, H, b, cost, inliers, v.stream);
     ctx_count_launches(ctx, 3 + (n_items > 0));
     e = cudaGetLastError();

@@ -256,6 +256,37 @@ def test_linearize_ragged_batch(ctx, prec, chunk):
         ctx.release(h)
 
 
+@pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64, vg.VGICP_PREC_F32_COMP])
+@pytest.mark.parametrize("nb,weighted", [(7, 0), (27, 0), (1, 1), (27, 1)])
+def test_linearize_neighbour_and_weighted_variants(ctx, prec, nb, weighted):
+    """DIRECT7 / DIRECT27 association and count weights against the oracle's variants;
+    the cost-only evaluation agrees with the linearisation's cost bit for bit."""
+    tg, tcov, src, scov, poses, factors = _ragged_case(seed=49)
+    ctx.set_options(precision=prec, neighbors=nb, count_weighted=weighted)
+    hm = [ctx.build_voxelmap(p, c, 0.5) for p, c in zip(tg, tcov)]
+    hf = [ctx.add_frame(p, c) for p, c in zip(src, scov)]
+    f = vg.make_factors([hm[t] for t, _, _, _ in factors], [hf[s] for _, s, _, _ in factors],
+                        [a for _, _, a, _ in factors], [b for _, _, _, b in factors])
+    H, b, cost, inl = ctx.linearize(f, poses)
+    c2, i2 = ctx.evaluate(f, poses)
+    if prec != vg.VGICP_PREC_F64:
+        assert np.array_equal(c2, cost) and np.array_equal(i2, inl)
+    vms = [oracle.voxelmap(p, c, 0.5) for p, c in zip(tg, tcov)]
+    for i, (t, s_, pt, ps) in enumerate(factors):
+        L = oracle.linearize(vms[t], src[s_], scov[s_], oracle.relative_pose(poses[pt], poses[ps]),
+                             neighbors=nb, count_weighted=bool(weighted))
+        assert inl[i] == L.inliers, i
+        if L.inliers == 0:
+            assert not H[i].any() and cost[i] == 0.0
+            continue
+        assert err_metric(H[i], L.H, L.SH) <= TOL[prec], i
+        assert err_metric(b[i], L.b, L.Sb) <= TOL[prec], i
+        assert abs(cost[i] - L.cost) <= TOL[prec] * L.Scost, i
+    ctx.set_options(precision=vg.VGICP_PREC_F32, neighbors=1, count_weighted=0)
+    for h in hm + hf:
+        ctx.release(h)
+
+
 def test_factor_alone_equals_factor_in_batch(ctx):
     tg, tcov, src, scov, poses, factors = _ragged_case(seed=43)
     hm = [ctx.build_voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
