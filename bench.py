@@ -289,21 +289,21 @@ def run_ours(a):
     # the overlap matrix and linearises with host outputs
     e2e = None
     if not a.no_e2e:
-        h_pts = [torch.from_numpy(p).pin_memory() for p in pts]
-        h_cov = [c.cpu().pin_memory() for c in d_cov]
+        # the frames one after another in pinned host memory, registered by one call
+        h_pts = torch.cat([torch.from_numpy(p) for p in pts]).pin_memory()
+        h_cov = torch.cat([c.cpu() for c in d_cov]).pin_memory()
+        sizes = np.array([p.shape[0] for p in pts], np.int64)
         h_out = (np.zeros((n_f, 12, 12)), np.zeros((n_f, 12)), np.zeros(n_f), np.zeros(n_f, np.int64))
         h_counts = np.zeros((n_frames, n_frames), np.int64)
-        np_pts = [p.numpy() for p in h_pts]
-        np_cov = [c.numpy() for c in h_cov]
+        np_pts, np_cov = [h_pts.numpy()], [h_cov.numpy()]
 
         def e2e_step():
-            fr = np.array([ctx.add_frame(p, c) for p, c in zip(np_pts, np_cov)], np.int64)
+            fr = ctx.add_frames(np_pts[0], np_cov[0], sizes)
             mp = ctx.build_voxelmaps(fr, 1.0)
             ctx.overlap_matrix(fr, mp, poses, poses, out=h_counts)
             fac = vg.make_factors(mp[tgt], fr[src], tgt, src)
             ctx.linearize(fac, poses, out=h_out)
-            for h in list(fr) + list(mp):
-                ctx.release(int(h))
+            ctx.release_many(np.concatenate([fr, mp]))
 
         for _ in range(2):
             e2e_step()

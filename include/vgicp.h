@@ -162,6 +162,14 @@ vgicp_status vgicp_synchronize(vgicp_ctx *ctx);
 vgicp_status vgicp_add_frame(vgicp_ctx *ctx, const float *points, const float *covs, int64_t n,
                              int mem_kind, vgicp_frame_t *out);
 
+/* Register m frames in one call: frame u has n[u] points, stored one frame
+ * after another in points (total x 3) and covs (total x 6), total = sum n[u],
+ * both in mem_kind memory; out[u] receives its handle.  The same frames as m
+ * vgicp_add_frame() calls, with one copy of each array and one batched pass
+ * for all of them.  All or nothing: on an error no handle is created. */
+vgicp_status vgicp_add_frames(vgicp_ctx *ctx, const float *points, const float *covs, const int64_t *n, int64_t m,
+                              int mem_kind, vgicp_frame_t *out);
+
 /* Number of points of a frame. */
 vgicp_status vgicp_frame_size(vgicp_ctx *ctx, vgicp_frame_t frame, int64_t *n);
 
@@ -334,6 +342,10 @@ vgicp_status vgicp_estimate_covariances(vgicp_ctx *ctx, const float *points, int
 
 /* Release a map or frame handle and its device memory. */
 vgicp_status vgicp_release(vgicp_ctx *ctx, int64_t handle);
+
+/* Release n handles (all are checked first: an unknown handle releases none;
+ * a handle listed twice fails when it is reached the second time). */
+vgicp_status vgicp_release_many(vgicp_ctx *ctx, const int64_t *handles, int64_t n);
 
 /* Device bytes a handle holds: a frame of n points (is_map = 0) or a voxelmap
  * built from n points (is_map = 1; building it also needs the n-point frame

@@ -38,7 +38,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_server_put_frame", "vgicp_server_submit", "vgicp_server_wait", "vgicp_server_stats",
            "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_server_submit_batch", "vgicp_server_wait_batch", "vgicp_plan_create", "vgicp_plan_linearize",
            "vgicp_plan_info", "vgicp_plan_destroy", "vgicp_memory_estimate", "vgicp_evaluate", "vgicp_solve_step",
-           "vgicp_se3_retract", "vgicp_optimize"]
+           "vgicp_se3_retract", "vgicp_optimize", "vgicp_add_frames", "vgicp_release_many"]
 VGICP_REQ_LINEARIZE, VGICP_REQ_OVERLAP = 0, 1
 
 
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_overlap_pairs": [vp, vp, vp, i64, vp, vp, C.c_int],
         "vgicp_synchronize": [vp],
         "vgicp_add_frame": [vp, vp, vp, i64, C.c_int, C.POINTER(i64)],
+        "vgicp_add_frames": [vp, vp, vp, vp, i64, C.c_int, vp],
         "vgicp_frame_size": [vp, i64, C.POINTER(i64)],
         "vgicp_build_voxelmap": [vp, vp, vp, i64, f64, C.c_int, C.POINTER(i64)],
         "vgicp_build_voxelmaps": [vp, vp, i64, f64, vp],
@@ -133,6 +134,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_export_voxelmap": [vp, i64, vp, vp, vp, vp, C.POINTER(i64)],
         "vgicp_estimate_covariances": [vp, vp, i64, i32, f64, vp, C.c_int],
         "vgicp_release": [vp, i64],
+        "vgicp_release_many": [vp, vp, i64],
         "vgicp_memory_in_use": [vp, C.POINTER(i64)],
         "vgicp_memory_estimate": [vp, i64, i32, C.POINTER(i64)],
         "vgicp_kernel_launches": [vp, C.POINTER(i64)],
@@ -266,6 +268,19 @@ def vgicp_add_frame(ctx, points, covs) -> int:
     h = C.c_int64()
     _check(ctx, load().vgicp_add_frame(ctx, _ptr(p), _ptr(c), n, kind, C.byref(h)))
     return h.value
+
+
+def vgicp_add_frames(ctx, points, covs, sizes) -> np.ndarray:
+    """Register len(sizes) frames stored one after another in points (total, 3) and covs
+    (total, 6): numpy arrays (host) or torch CUDA tensors (device).  Returns the handles."""
+    n = np.ascontiguousarray(sizes, np.int64)
+    out = np.zeros(n.shape[0], np.int64)
+    if _is_torch_cuda(points):
+        p, c, kind = points, covs, VGICP_MEM_DEVICE
+    else:
+        p, c, kind = _host(points, np.float32, 3), _host(covs, np.float32, 6), VGICP_MEM_HOST
+    _check(ctx, load().vgicp_add_frames(ctx, _ptr(p), _ptr(c), _ptr(n), n.shape[0], kind, _ptr(out)))
+    return out
 
 
 def vgicp_frame_size(ctx, frame: int) -> int:
@@ -500,6 +515,11 @@ def vgicp_estimate_covariances(ctx, points, k: int = 10, eps: float = 1e-3, out=
 
 def vgicp_release(ctx, handle: int):
     _check(ctx, load().vgicp_release(ctx, handle))
+
+
+def vgicp_release_many(ctx, handles):
+    h = np.ascontiguousarray(handles, np.int64)
+    _check(ctx, load().vgicp_release_many(ctx, _ptr(h), h.shape[0]))
 
 
 def vgicp_memory_in_use(ctx) -> int:

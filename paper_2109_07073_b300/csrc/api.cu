@@ -289,8 +289,9 @@ size_t frame_bytes(int64_t n)
     return align256((size_t)n * 16) * 2 + align256((size_t)n * 4) + 256 + 1024;
 }
 
-// Allocate and fill a frame from device-resident points / covariances.
-vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, int64_t n, uint32_t *out_idx)
+// Allocate a frame handle of n points and fill its host descriptor (the
+// device copy of the descriptor and the data are the caller's business).
+vgicp_status alloc_frame(vgicp_ctx *ctx, int64_t n, uint32_t *out_idx)
 {
     const size_t o_pb = align256((size_t)n * 16), o_pc = o_pb + align256((size_t)n * 16);
     const size_t o_st = o_pc + align256((size_t)n * 4), o_cb = o_st + 256, bytes = o_cb + 1024;
@@ -319,6 +320,18 @@ vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, 
     f.cshift = 10;
     while (((int64_t)kMaxCullChunks << f.cshift) < n) ++f.cshift;
     f.nchunks = (int32_t)((n + ((int64_t)1 << f.cshift) - 1) >> f.cshift);
+    *out_idx = idx;
+    return VGICP_OK;
+}
+
+// Allocate and fill a frame from device-resident points / covariances.
+vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, int64_t n, uint32_t *out_idx)
+{
+    uint32_t idx;
+    TRY(alloc_frame(ctx, n, &idx));
+    char *base = (char *)ctx->objs[idx].frame_mem;
+    FrameDesc &f = ctx->h_frames[idx];
+    const size_t o_st = (size_t)((const char *)f.stats - base);
     // statistics start at: zero maxima of |c| and |p|, +inf minima, -inf maxima
     static const uint32_t init[kStatCount] = {0, 0, 0, 0, kOrderedPosInf, kOrderedPosInf, kOrderedPosInf,
                                               kOrderedNegInf, kOrderedNegInf, kOrderedNegInf};
@@ -743,6 +756,82 @@ vgicp_status vgicp_add_frame(vgicp_ctx *ctx, const float *points, const float *c
     uint32_t idx;
     TRY(make_frame(ctx, dp, dc, n, &idx));
     *out = make_handle(idx, ctx->objs[idx].gen);
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_add_frames(vgicp_ctx *ctx, const float *points, const float *covs, const int64_t *n, int64_t m,
+                              int mem_kind, vgicp_frame_t *out)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (m < 0 || (m > 0 && (!n || !out)) || m > (1 << 24))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frames: null pointer or bad count");
+    if (mem_kind != VGICP_MEM_HOST && mem_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frames: bad mem_kind %d", mem_kind);
+    int64_t total = 0;
+    for (int64_t u = 0; u < m; ++u) {
+        if (n[u] < 0 || n[u] > ((int64_t)1 << 31) - 1)
+            return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frames: frame %lld: bad size", (long long)u);
+        total += n[u];
+    }
+    if (total > 0 && (!points || !covs)) return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frames: null pointer");
+    if (m == 0) return VGICP_OK;
+    const float *dp = nullptr, *dc = nullptr;
+    TRY(stage_inputs(ctx, points, covs, total, mem_kind, &dp, &dc));
+    // handles first (all or none), then one descriptor scatter and the batched kernels
+    std::vector<uint32_t> idx((size_t)m);
+    for (int64_t u = 0; u < m; ++u) {
+        const vgicp_status st = alloc_frame(ctx, n[u], &idx[u]);
+        if (st != VGICP_OK) {
+            for (int64_t v = 0; v < u; ++v) vgicp_release(ctx, make_handle(idx[v], ctx->objs[idx[v]].gen));
+            return st;
+        }
+    }
+    std::vector<int64_t> off((size_t)m);
+    std::vector<int32_t> fidx((size_t)m);
+    std::vector<FrameDesc> descs((size_t)m);
+    std::vector<WorkItem> items, chunks;
+    int64_t o = 0;
+    for (int64_t u = 0; u < m; ++u) {
+        off[u] = o;
+        o += n[u];
+        fidx[u] = (int32_t)idx[u];
+        descs[u] = ctx->h_frames[idx[u]];
+        for (int64_t s0 = 0; s0 < n[u]; s0 += 4096) {
+            WorkItem w;
+            w.unit = (int32_t)u;
+            w.start = s0;
+            w.count = (int32_t)std::min<int64_t>(4096, n[u] - s0);
+            items.push_back(w);
+        }
+        for (int c = 0; c < descs[u].nchunks; ++c) {
+            WorkItem w;
+            w.unit = (int32_t)u;
+            w.start = c;
+            w.count = 0;
+            chunks.push_back(w);
+        }
+    }
+    // one upload: offsets, table indices (twice: as int32 for the kernels and
+    // uint32 for the scatter), descriptors, point items, chunk items
+    const size_t o_f = align256((size_t)m * 8), o_d = o_f + align256((size_t)m * 4);
+    const size_t o_i = o_d + align256((size_t)m * sizeof(FrameDesc));
+    const size_t o_c = o_i + align256(items.size() * sizeof(WorkItem));
+    const size_t bytes = o_c + chunks.size() * sizeof(WorkItem);
+    std::vector<char> host(bytes);
+    std::memcpy(host.data(), off.data(), (size_t)m * 8);
+    std::memcpy(host.data() + o_f, fidx.data(), (size_t)m * 4);
+    std::memcpy(host.data() + o_d, descs.data(), (size_t)m * sizeof(FrameDesc));
+    if (!items.empty()) std::memcpy(host.data() + o_i, items.data(), items.size() * sizeof(WorkItem));
+    if (!chunks.empty()) std::memcpy(host.data() + o_c, chunks.data(), chunks.size() * sizeof(WorkItem));
+    TRY(upload(ctx, LN.ws_descs, host.data(), host.size()));
+    char *d = (char *)LN.ws_descs.p;
+    launch_frames_register(dp, dc, (const int64_t *)d, (const int32_t *)(d + o_f), (int)m,
+                           (const WorkItem *)(d + o_i), (int)items.size(), (const WorkItem *)(d + o_c),
+                           (int)chunks.size(), (const uint32_t *)(d + o_f), (const FrameDesc *)(d + o_d),
+                           ctx->d_frames, LN.stream);
+    ctx->launches += 2 + !items.empty() + !chunks.empty();
+    CHECK_LAUNCH();
+    for (int64_t u = 0; u < m; ++u) out[u] = make_handle(idx[u], ctx->objs[idx[u]].gen);
     return VGICP_OK;
 }
 
@@ -1530,6 +1619,20 @@ vgicp_status vgicp_release(vgicp_ctx *ctx, int64_t handle)
     o->gen = gen;
     ctx->free_idx.push_back(idx);
     LN.plan.key.clear();   // a cached work list may name this handle
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_release_many(vgicp_ctx *ctx, const int64_t *handles, int64_t n)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && !handles)) return fail(ctx, VGICP_ERR_INVALID_ARG, "release_many: bad arguments");
+    for (int64_t i = 0; i < n; ++i)
+        if (!lookup(ctx, handles[i], Obj::FRAME) && !lookup(ctx, handles[i], Obj::MAP))
+            return fail(ctx, VGICP_ERR_NOT_FOUND, "release_many: handle %lld not found", (long long)handles[i]);
+    for (int64_t i = 0; i < n; ++i) {
+        const vgicp_status st = vgicp_release(ctx, handles[i]);
+        if (st != VGICP_OK) return st;    // a handle listed twice
+    }
     return VGICP_OK;
 }
 

@@ -23,6 +23,9 @@ void launch_frame_pack(const float *points, const float *covs, int64_t n, float4
                        float *stats, cudaStream_t st);
 
 // Bounding boxes of a frame's cull chunks (2^shift points each).
+void launch_frames_register(const float *pts, const float *cov, const int64_t *src_off, const int32_t *fidx, int m,
+                            const WorkItem *items, int n_items, const WorkItem *chunks, int n_chunks,
+                            const uint32_t *desc_idx, const FrameDesc *descs, FrameDesc *table, cudaStream_t st);
 void launch_chunk_boxes(const float4 *pa, int64_t n, int shift, int nchunks, float *cbox, cudaStream_t st);
 
 // Write n map descriptors into the device table: table[idx[i]] = src[i].

@@ -14,6 +14,7 @@
 //   compact    per voxel: its 32-bit key relative to the map's voxel box into a
 //              presence table sized by the voxel count (overlap queries stage
 //              it in shared memory)
+#include <algorithm>
 #include "kernels.cuh"
 
 namespace vg {
@@ -66,6 +67,122 @@ __global__ void k_frame_pack(const float *__restrict__ pts, const float *__restr
             atomicMax(stats + kStatMax + j, mx[j]);
         }
     }
+}
+
+// Batched frame registration: frame u's n points start at src_off[u] of the
+// staged point / covariance arrays; its descriptor is in the table at index
+// fidx[u].  Items are (frame, start, count) chunks of points.
+__global__ void k_frames_init(const int32_t *__restrict__ fidx, int m, const FrameDesc *__restrict__ frames)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= m) return;
+    unsigned int *st = (unsigned int *)frames[fidx[u]].stats;
+    st[kStatCmax] = 0u;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        st[kStatPmax + j] = 0u;
+        st[kStatMin + j] = kOrderedPosInf;
+        st[kStatMax + j] = kOrderedNegInf;
+    }
+}
+
+__global__ void k_frames_pack(const float *__restrict__ pts, const float *__restrict__ cov,
+                              const int64_t *__restrict__ src_off, const int32_t *__restrict__ fidx,
+                              const WorkItem *__restrict__ items, int n_items, const FrameDesc *__restrict__ frames)
+{
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const FrameDesc F = frames[fidx[w.unit]];
+        const float *p0 = pts + 3 * src_off[w.unit], *c0 = cov + 6 * src_off[w.unit];
+        float m = 0.f, am[3] = {0.f, 0.f, 0.f};
+        uint32_t mn[3] = {kOrderedPosInf, kOrderedPosInf, kOrderedPosInf};
+        uint32_t mx[3] = {kOrderedNegInf, kOrderedNegInf, kOrderedNegInf};
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const int64_t i = w.start + k;
+            const float *p = p0 + 3 * i, *c = c0 + 6 * i;
+            ((float4 *)F.pa)[i] = make_float4(p[0], p[1], p[2], c[0]);
+            ((float4 *)F.pb)[i] = make_float4(c[1], c[2], c[3], c[4]);
+            ((float *)F.pc)[i] = c[5];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) m = fmaxf(m, fabsf(c[j]));
+            if (isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2])) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    am[j] = fmaxf(am[j], fabsf(p[j]));
+                    mn[j] = min(mn[j], ordered_bits(p[j]));
+                    mx[j] = max(mx[j], ordered_bits(p[j]));
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                am[j] = fmaxf(am[j], __shfl_xor_sync(0xffffffffu, am[j], o));
+                mn[j] = min(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
+                mx[j] = max(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            unsigned int *st = (unsigned int *)F.stats;
+            if (m > 0.f) atomicMax(st + kStatCmax, __float_as_uint(m));
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (am[j] > 0.f) atomicMax(st + kStatPmax + j, __float_as_uint(am[j]));
+                atomicMin(st + kStatMin + j, mn[j]);
+                atomicMax(st + kStatMax + j, mx[j]);
+            }
+        }
+    }
+}
+
+// Chunk boxes of many frames: item (frame, chunk) per block, as k_chunk_boxes.
+__global__ void k_frames_chunk_boxes(const int32_t *__restrict__ fidx, const WorkItem *__restrict__ chunks,
+                                     int n_chunks, const FrameDesc *__restrict__ frames)
+{
+    __shared__ float s[6][8];
+    for (int it = blockIdx.x; it < n_chunks; it += gridDim.x) {
+        const WorkItem w = chunks[it];      // start = chunk index
+        const FrameDesc F = frames[fidx[w.unit]];
+        const int c = (int)w.start;
+        const int64_t b = (int64_t)c << F.cshift, e = min(F.n, b + ((int64_t)1 << F.cshift));
+        float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+            const float4 p = F.pa[i];
+            if (isfinite(p.x) && isfinite(p.y) && isfinite(p.z)) {
+                mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+                mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn[j] = fminf(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
+                mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
+            }
+        const int wq = threadIdx.x >> 5;
+        __syncthreads();                                // previous item's readers are done
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) { s[j][wq] = mn[j]; s[3 + j][wq] = mx[j]; }
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            float v = s[threadIdx.x][0];
+            for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+                v = threadIdx.x < 3 ? fminf(v, s[threadIdx.x][q]) : fmaxf(v, s[threadIdx.x][q]);
+            ((float *)F.cbox)[6 * c + threadIdx.x] = v;
+        }
+    }
+}
+
+__global__ void k_scatter_frame_descs(const uint32_t *__restrict__ idx, const FrameDesc *__restrict__ src, int n,
+                                      FrameDesc *__restrict__ table)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) table[idx[i]] = src[i];
 }
 
 // Bounding box of each cull chunk of a frame (finite points only; an empty
@@ -358,6 +475,19 @@ void launch_frame_pack(const float *points, const float *covs, int64_t n, float4
     int grid = (int)((n + block - 1) / block);
     if (grid > 148 * 16) grid = 148 * 16;
     k_frame_pack<<<grid, block, 0, st>>>(points, covs, n, pa, pb, pc, (unsigned int *)stats);
+}
+
+void launch_frames_register(const float *pts, const float *cov, const int64_t *src_off, const int32_t *fidx, int m,
+                            const WorkItem *items, int n_items, const WorkItem *chunks, int n_chunks,
+                            const uint32_t *desc_idx, const FrameDesc *descs, FrameDesc *table, cudaStream_t st)
+{
+    if (m <= 0) return;
+    k_scatter_frame_descs<<<(m + 127) / 128, 128, 0, st>>>(desc_idx, descs, m, table);
+    k_frames_init<<<(m + 127) / 128, 128, 0, st>>>(fidx, m, table);
+    if (n_items > 0)
+        k_frames_pack<<<std::min(n_items, 148 * 16), 256, 0, st>>>(pts, cov, src_off, fidx, items, n_items, table);
+    if (n_chunks > 0)
+        k_frames_chunk_boxes<<<std::min(n_chunks, 148 * 16), 256, 0, st>>>(fidx, chunks, n_chunks, table);
 }
 
 void launch_chunk_boxes(const float4 *pa, int64_t n, int shift, int nchunks, float *cbox, cudaStream_t st)

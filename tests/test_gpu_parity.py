@@ -191,6 +191,40 @@ def test_overlap_matrix_presence_structures(ctx):
         ctx.release(int(h))
 
 
+def test_add_frames_equals_single_registrations(ctx, loop_frames):
+    """Frames registered in one batched call (host and device inputs, an empty frame
+    among them) give the same voxelmaps, overlaps and linearisations bit for bit."""
+    import torch
+    g, ids, pts, covs = loop_frames
+    sizes = [p.shape[0] for p in pts[:4]] + [0] + [p.shape[0] for p in pts[4:]]
+    cat_p = np.concatenate(pts[:4] + [np.zeros((0, 3), np.float32)] + pts[4:])
+    cat_c = np.concatenate(covs[:4] + [np.zeros((0, 6), np.float32)] + covs[4:])
+    single = [ctx.add_frame(p, c) for p, c in zip(pts, covs)]
+    host = list(ctx.add_frames(cat_p, cat_c, sizes))
+    dev = list(ctx.add_frames(torch.from_numpy(cat_p).cuda(), torch.from_numpy(cat_c).cuda(), sizes))
+    assert ctx.frame_size(host[4]) == 0 and ctx.frame_size(dev[2]) == pts[2].shape[0]
+    P = g.poses[ids]
+    tg, sc = [0, 1, 2, 3, 5, 6], [1, 0, 3, 2, 6, 7]
+    ref = None
+    for fr in (single, host[:4] + host[5:], dev[:4] + dev[5:]):
+        maps = ctx.build_voxelmaps(fr, g.resolution)
+        exp = [ctx.export_voxelmap(int(h)) for h in maps]
+        cnt = ctx.overlap_matrix(fr, maps, P, P)
+        lin = ctx.linearize(vg.make_factors(maps[tg], np.array(fr)[sc], tg, sc), P)
+        if ref is None:
+            ref = (exp, cnt, lin)
+        else:
+            for a, b in zip(exp, ref[0]):
+                assert all(np.array_equal(x, y) for x, y in zip(a, b))
+            assert np.array_equal(cnt, ref[1])
+            assert all(np.array_equal(x, y) for x, y in zip(lin, ref[2]))
+        for h in maps:
+            ctx.release(int(h))
+    with pytest.raises(vg.VgicpError):
+        ctx.release_many([single[0], 12345678901])         # unknown handle: nothing released
+    ctx.release_many(single + host + dev)
+
+
 def _ragged_case(seed=41):
     """Several targets, sources of 0, 1, 31, 2047, 2048, 2049, 5000 and 12345 points."""
     rng = dg.Stream(seed)
