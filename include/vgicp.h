@@ -410,6 +410,33 @@ typedef struct {
 vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, double *poses,
                             int64_t n_poses, const vgicp_lm_options *opt, vgicp_lm_report *report);
 
+/* SE(3) loop constraint (Sec. III-D, Eq. 10-11): an explicit relative pose
+ * measurement T_ij ~ T_i^-1 T_j with residual r = Log(T_ij^-1 T_i^-1 T_j)
+ * (twist (omega, v)), constant information Omega (6x6, row-major), and the
+ * shifted Tukey kernel on the whitened error norm x = sqrt(r' Omega r): weight
+ * psi(x) = (max(0, 1 - (x - offset)^2 / width))^2.  The factor's cost is the loss
+ * rho(x^2) = int_0^x psi(u) 2u du (so d rho / d(x^2) = psi), and its Gauss-Newton
+ * blocks are psi(x) J' Omega J and psi(x) J' Omega r with psi frozen at the
+ * linearisation point. */
+typedef struct {
+    int32_t pose_i, pose_j;
+    double T_ij[12];
+    double information[36];
+    double width;
+    double offset;
+} vgicp_loop_factor;
+
+/* Host only: cost (n_loops), and when non-NULL the blocks H (n_loops x 144, order
+ * [xi_i ; xi_j]) and b (n_loops x 12) of the loop factors at the poses. */
+vgicp_status vgicp_loop_linearize(const vgicp_loop_factor *loops, int64_t n_loops, const double *poses,
+                                  int64_t n_poses, double *H, double *b, double *cost);
+
+/* vgicp_optimize() with SE(3) loop factors added to the matching cost factors:
+ * F = sum of the factors' costs + sum of the loop factors' losses. */
+vgicp_status vgicp_optimize_with_loops(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f,
+                                       const vgicp_loop_factor *loops, int64_t n_loops, double *poses,
+                                       int64_t n_poses, const vgicp_lm_options *opt, vgicp_lm_report *report);
+
 /* Human-readable name of a status code. */
 const char *vgicp_status_string(vgicp_status s);
 

@@ -316,3 +316,57 @@ def gn_step(pairs, H, b, n_poses, anchor=0, lam=0.0):
     d = np.zeros(6 * int(n_poses))
     d[free] = np.linalg.solve(A, -bg[free])
     return d.reshape(-1, 6), float(-(2.0 * bg @ d + d @ Hg @ d))
+
+
+# --------------------------------------------------------------------------
+# SE(3) loop constraint with the shifted Tukey kernel (Sec. III-D, Eq. 10-11)
+# --------------------------------------------------------------------------
+
+def se3_log(T) -> np.ndarray:
+    """Twist (omega, v) of a rigid transform: the principal matrix logarithm of its 4x4 form."""
+    import scipy.linalg
+    M = np.vstack([np.asarray(T, dtype=np.float64).reshape(3, 4), [0.0, 0.0, 0.0, 1.0]])
+    Lg = np.real(scipy.linalg.logm(M))
+    return np.array([Lg[2, 1], Lg[0, 2], Lg[1, 0], Lg[0, 3], Lg[1, 3], Lg[2, 3]])
+
+
+def tukey_weight(x, width, offset) -> float:
+    """Shifted Tukey weight of a whitened error norm: (max(0, 1 - (x - offset)^2 / width))^2."""
+    u = 1.0 - (x - offset) ** 2 / width
+    return u * u if u > 0.0 else 0.0
+
+
+def tukey_loss(x, width, offset) -> float:
+    """rho(x^2) = int_0^x weight(u) 2u du (adaptive quadrature)."""
+    import scipy.integrate
+    if x <= 0.0:
+        return 0.0
+    return scipy.integrate.quad(lambda u: tukey_weight(u, width, offset) * 2.0 * u, 0.0, x,
+                                points=[max(0.0, offset - np.sqrt(width)), offset, offset + np.sqrt(width)],
+                                epsabs=0.0, epsrel=1e-13, limit=200)[0]
+
+
+def _h(T):
+    return np.vstack([np.asarray(T, dtype=np.float64).reshape(3, 4), [0.0, 0.0, 0.0, 1.0]])
+
+
+def loop_residual(Ti, Tj, T_ij) -> np.ndarray:
+    """r = Log(T_ij^-1 T_i^-1 T_j)."""
+    return se3_log((np.linalg.inv(_h(T_ij)) @ np.linalg.inv(_h(Ti)) @ _h(Tj))[:3])
+
+
+def loop_factor(Ti, Tj, T_ij, information, width, offset, h=1e-6):
+    """Cost, H (12x12, [xi_i ; xi_j]) and b of one loop factor: Jacobian of r by central
+    differences over right perturbations, weight frozen at the given poses."""
+    Om = np.asarray(information, dtype=np.float64).reshape(6, 6)
+    r = loop_residual(Ti, Tj, T_ij)
+    x = float(np.sqrt(max(r @ Om @ r, 0.0)))
+    J = np.zeros((6, 12))
+    for k in range(12):
+        d = np.zeros(12)
+        d[k] = h
+        rp = loop_residual(retract(Ti, d[:6])[0], retract(Tj, d[6:])[0], T_ij)
+        rm = loop_residual(retract(Ti, -d[:6])[0], retract(Tj, -d[6:])[0], T_ij)
+        J[:, k] = (rp - rm) / (2 * h)
+    w = tukey_weight(x, width, offset)
+    return tukey_loss(x, width, offset), w * J.T @ Om @ J, w * J.T @ Om @ r

@@ -38,7 +38,8 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_server_put_frame", "vgicp_server_submit", "vgicp_server_wait", "vgicp_server_stats",
            "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_server_submit_batch", "vgicp_server_wait_batch", "vgicp_plan_create", "vgicp_plan_linearize",
            "vgicp_plan_info", "vgicp_plan_destroy", "vgicp_memory_estimate", "vgicp_evaluate", "vgicp_solve_step",
-           "vgicp_se3_retract", "vgicp_optimize", "vgicp_add_frames", "vgicp_release_many"]
+           "vgicp_se3_retract", "vgicp_optimize", "vgicp_add_frames", "vgicp_release_many", "vgicp_loop_linearize",
+           "vgicp_optimize_with_loops"]
 VGICP_REQ_LINEARIZE, VGICP_REQ_OVERLAP = 0, 1
 
 
@@ -69,6 +70,27 @@ class LMReport(C.Structure):
                 ("reserved", C.c_int32), ("initial_cost", C.c_double), ("final_cost", C.c_double),
                 ("lambda_", C.c_double), ("linearize_ms", C.c_double), ("evaluate_ms", C.c_double),
                 ("solve_ms", C.c_double), ("history", C.c_double * 64)]
+
+
+class LoopFactor(C.Structure):
+    _fields_ = [("pose_i", C.c_int32), ("pose_j", C.c_int32), ("T_ij", C.c_double * 12),
+                ("information", C.c_double * 36), ("width", C.c_double), ("offset", C.c_double)]
+
+
+def make_loop_factors(pose_i, pose_j, T_ij, information, width, offset):
+    """A ctypes array of SE(3) loop factors (one per entry of the inputs)."""
+    n = len(pose_i)
+    arr = (LoopFactor * n)()
+    T = np.asarray(T_ij, np.float64).reshape(n, 12)
+    I6 = np.broadcast_to(np.asarray(information, np.float64).reshape(-1, 36), (n, 36))
+    w = np.broadcast_to(np.asarray(width, np.float64), (n,))
+    o = np.broadcast_to(np.asarray(offset, np.float64), (n,))
+    for k in range(n):
+        arr[k].pose_i, arr[k].pose_j = int(pose_i[k]), int(pose_j[k])
+        arr[k].T_ij[:] = [float(x) for x in T[k]]
+        arr[k].information[:] = [float(x) for x in I6[k]]
+        arr[k].width, arr[k].offset = float(w[k]), float(o[k])
+    return arr
 
 
 class ServerOptions(C.Structure):
@@ -143,6 +165,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_solve_step": [vp, vp, vp, i64, i64, i32, f64, vp, C.POINTER(f64)],
         "vgicp_se3_retract": [vp, vp, i64],
         "vgicp_optimize": [vp, vp, i64, vp, i64, C.POINTER(LMOptions), C.POINTER(LMReport)],
+        "vgicp_optimize_with_loops": [vp, vp, i64, vp, i64, vp, i64, C.POINTER(LMOptions), C.POINTER(LMReport)],
+        "vgicp_loop_linearize": [vp, i64, vp, i64, vp, vp, vp],
         "vgicp_plan_linearize": [vp, vp, vp, vp, vp, vp, vp, C.c_int],
         "vgicp_plan_info": [vp, vp, C.POINTER(i64), C.POINTER(i64)],
         "vgicp_plan_destroy": [vp, vp],
@@ -376,6 +400,28 @@ def vgicp_optimize(ctx, factors, poses, max_iterations: int = 20, anchor: int = 
     opt = LMOptions(max_iterations, anchor, lambda_init, relative_tolerance)
     rep = LMReport()
     _check(ctx, load().vgicp_optimize(ctx, _ptr(f), f.shape[0], _ptr(P), P.shape[0], C.byref(opt), C.byref(rep)))
+    return P.reshape(-1, 3, 4), rep
+
+
+def vgicp_loop_linearize(loops, poses, blocks: bool = True):
+    """Host-only: (H (n,12,12), b (n,12), cost (n,)) of SE(3) loop factors at the poses."""
+    P = np.array(_pose12(poses), dtype=np.float64)
+    n = len(loops)
+    H, b, cost = np.zeros((n, 12, 12)), np.zeros((n, 12)), np.zeros(n)
+    _check(None, load().vgicp_loop_linearize(C.cast(loops, C.c_void_p), n, _ptr(P), P.shape[0],
+                                             _ptr(H) if blocks else None, _ptr(b) if blocks else None, _ptr(cost)))
+    return H, b, cost
+
+
+def vgicp_optimize_with_loops(ctx, factors, loops, poses, max_iterations: int = 20, anchor: int = 0,
+                              lambda_init: float = 0.0, relative_tolerance: float = 0.0):
+    """vgicp_optimize with SE(3) loop factors (make_loop_factors) added."""
+    f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
+    P = np.array(_pose12(poses), dtype=np.float64)
+    opt = LMOptions(max_iterations, anchor, lambda_init, relative_tolerance)
+    rep = LMReport()
+    _check(ctx, load().vgicp_optimize_with_loops(ctx, _ptr(f), f.shape[0], C.cast(loops, C.c_void_p), len(loops),
+                                                 _ptr(P), P.shape[0], C.byref(opt), C.byref(rep)))
     return P.reshape(-1, 3, 4), rep
 
 

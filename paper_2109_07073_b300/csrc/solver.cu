@@ -182,6 +182,140 @@ void se3_exp(const double xi[6], double T[12])
     }
 }
 
+// ---------------------------------------------------------- SE(3) helpers --
+
+void compose34(const double A[12], const double B[12], double C[12])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 4; ++j) {
+            double s = j == 3 ? A[4 * i + 3] : 0.0;
+            for (int k = 0; k < 3; ++k) s += A[4 * i + k] * B[4 * k + j];
+            C[4 * i + j] = s;
+        }
+}
+
+void invert34(const double T[12], double Ti[12])
+{
+    for (int i = 0; i < 3; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            Ti[4 * i + k] = T[4 * k + i];
+            s -= T[4 * k + i] * T[4 * k + 3];
+        }
+        Ti[4 * i + 3] = s;
+    }
+}
+
+void skew(const double a[3], double K[9])
+{
+    K[0] = 0.0;   K[1] = -a[2]; K[2] = a[1];
+    K[3] = a[2];  K[4] = 0.0;   K[5] = -a[0];
+    K[6] = -a[1]; K[7] = a[0];  K[8] = 0.0;
+}
+
+// Log of a rotation (axis-angle), robust at 0 and at pi.
+void so3_log(const double R[9], double w[3])
+{
+    const double c = std::max(-1.0, std::min(1.0, 0.5 * (R[0] + R[4] + R[8] - 1.0)));
+    const double th = std::acos(c);
+    const double v[3] = {R[7] - R[5], R[2] - R[6], R[3] - R[1]};
+    if (th < 1e-5) {
+        for (int a = 0; a < 3; ++a) w[a] = 0.5 * (1.0 + th * th / 6.0) * v[a];
+    } else if (M_PI - th < 1e-5) {
+        int k = 0;
+        for (int a = 1; a < 3; ++a)
+            if (R[4 * a] > R[4 * k]) k = a;
+        const double d = std::sqrt(2.0 * (1.0 + R[4 * k]));
+        for (int a = 0; a < 3; ++a) w[a] = th * (R[3 * a + k] + (a == k ? 1.0 : 0.0)) / d;
+    } else {
+        const double f = th / (2.0 * std::sin(th));
+        for (int a = 0; a < 3; ++a) w[a] = f * v[a];
+    }
+}
+
+// Log of a rigid transform as a twist (omega, v): v = V(omega)^-1 t.
+void se3_log(const double T[12], double xi[6])
+{
+    const double R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+    so3_log(R, xi);
+    const double th2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2], th = std::sqrt(th2);
+    double c;   // coefficient of [w]x^2 in V^-1
+    if (th < 1e-4) c = 1.0 / 12.0 + th2 / 720.0;
+    else c = (1.0 - th * std::sin(th) / (2.0 * (1.0 - std::cos(th)))) / th2;
+    double K[9];
+    skew(xi, K);
+    const double t[3] = {T[3], T[7], T[11]};
+    for (int i = 0; i < 3; ++i) {
+        double s = t[i];
+        for (int j = 0; j < 3; ++j) {
+            double KK = 0.0;
+            for (int k = 0; k < 3; ++k) KK += K[3 * i + k] * K[3 * k + j];
+            s += (-0.5 * K[3 * i + j] + c * KK) * t[j];
+        }
+        xi[3 + i] = s;
+    }
+}
+
+// Adjoint of T on twists (omega, v): [[R, 0], [[t]x R, R]] (6x6 row-major).
+void adjoint(const double T[12], double Ad[36])
+{
+    double tx[9];
+    const double t[3] = {T[3], T[7], T[11]};
+    skew(t, tx);
+    std::fill(Ad, Ad + 36, 0.0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const double r = T[4 * i + j];
+            Ad[6 * i + j] = r;
+            Ad[6 * (3 + i) + 3 + j] = r;
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += tx[3 * i + k] * T[4 * k + j];
+            Ad[6 * (3 + i) + j] = s;
+        }
+}
+
+// Inverse right Jacobian of SE(3) to second order: I + ad/2 + ad^2/12 with
+// ad(omega, v) = [[ [w]x, 0 ], [ [v]x, [w]x ]].
+void jr_inverse(const double xi[6], double J[36])
+{
+    double a[36] = {0}, W[9], V[9];
+    skew(xi, W);
+    skew(xi + 3, V);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            a[6 * i + j] = W[3 * i + j];
+            a[6 * (3 + i) + 3 + j] = W[3 * i + j];
+            a[6 * (3 + i) + j] = V[3 * i + j];
+        }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double aa = 0.0;
+            for (int k = 0; k < 6; ++k) aa += a[6 * i + k] * a[6 * k + j];
+            J[6 * i + j] = (i == j ? 1.0 : 0.0) + 0.5 * a[6 * i + j] + aa / 12.0;
+        }
+}
+
+// Shifted Tukey weight of the whitened error norm x: tukey(|x - offset|, w)
+// with tukey(y, w) = (max(0, 1 - y^2 / w))^2.
+double tukey_weight(double x, double w, double offset)
+{
+    const double y = x - offset, u = 1.0 - y * y / w;
+    return u > 0.0 ? u * u : 0.0;
+}
+
+// Robust loss whose derivative in s = x^2 is that weight: rho = int_0^x weight(u) 2u du,
+// by three-point Gauss-Legendre on the weight's support (exact: a degree-5 polynomial).
+double tukey_loss(double x, double w, double offset)
+{
+    const double h = std::sqrt(w), lo = std::max(0.0, offset - h), hi = std::min(x, offset + h);
+    if (!(hi > lo)) return 0.0;
+    const double c = 0.5 * (lo + hi), r = 0.5 * (hi - lo), g = std::sqrt(0.6);
+    const double nodes[3] = {c - r * g, c, c + r * g}, wts[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) s += wts[k] * tukey_weight(nodes[k], w, offset) * 2.0 * nodes[k];
+    return r * s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -309,11 +443,75 @@ vgicp_status vgicp_solve_step(const int32_t *pairs, const double *H, const doubl
     return VGICP_OK;
 }
 
+vgicp_status vgicp_loop_linearize(const vgicp_loop_factor *loops, int64_t n_loops, const double *poses,
+                                  int64_t n_poses, double *H, double *b, double *cost)
+{
+    if (n_loops < 0 || (n_loops > 0 && (!loops || !poses || !cost)) || n_poses < 0) return VGICP_ERR_INVALID_ARG;
+    for (int64_t l = 0; l < n_loops; ++l) {
+        const vgicp_loop_factor &L = loops[l];
+        if (L.pose_i < 0 || L.pose_i >= n_poses || L.pose_j < 0 || L.pose_j >= n_poses || !(L.width > 0.0))
+            return VGICP_ERR_INVALID_ARG;
+        // r = Log(That^-1 T_i^-1 T_j), x = sqrt(r' Omega r)
+        double Ti_inv[12], D[12], Mi[12], E[12], r[6];
+        invert34(poses + 12 * L.pose_i, Ti_inv);
+        compose34(Ti_inv, poses + 12 * L.pose_j, D);
+        invert34(L.T_ij, Mi);
+        compose34(Mi, D, E);
+        se3_log(E, r);
+        double Or[6];
+        for (int i = 0; i < 6; ++i) {
+            Or[i] = 0.0;
+            for (int j = 0; j < 6; ++j) Or[i] += L.information[6 * i + j] * r[j];
+        }
+        double s2 = 0.0;
+        for (int i = 0; i < 6; ++i) s2 += r[i] * Or[i];
+        const double x = std::sqrt(std::max(s2, 0.0));
+        cost[l] = tukey_loss(x, L.width, L.offset);
+        if (!H && !b) continue;
+        const double wgt = tukey_weight(x, L.width, L.offset);
+        // J_j = Jr^-1(r), J_i = -Jr^-1(r) Ad(D^-1)  (right perturbations of T_i and T_j)
+        double Jinv[36], Dinv[12], Ad[36], J[6][12];
+        jr_inverse(r, Jinv);
+        invert34(D, Dinv);
+        adjoint(Dinv, Ad);
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += Jinv[6 * i + k] * Ad[6 * k + j];
+                J[i][j] = -s;
+                J[i][6 + j] = Jinv[6 * i + j];
+            }
+        if (H)
+            for (int a = 0; a < 12; ++a)
+                for (int c = 0; c < 12; ++c) {
+                    double s = 0.0;
+                    for (int i = 0; i < 6; ++i)
+                        for (int j = 0; j < 6; ++j) s += J[i][a] * L.information[6 * i + j] * J[j][c];
+                    H[144 * l + 12 * a + c] = wgt * s;
+                }
+        if (b)
+            for (int a = 0; a < 12; ++a) {
+                double s = 0.0;
+                for (int i = 0; i < 6; ++i) s += J[i][a] * Or[i];
+                b[12 * l + a] = wgt * s;
+            }
+    }
+    return VGICP_OK;
+}
+
 vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, double *poses,
                             int64_t n_poses, const vgicp_lm_options *opt_in, vgicp_lm_report *report)
 {
+    return vgicp_optimize_with_loops(ctx, factors, n_f, nullptr, 0, poses, n_poses, opt_in, report);
+}
+
+vgicp_status vgicp_optimize_with_loops(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f,
+                                       const vgicp_loop_factor *loops, int64_t n_loops, double *poses,
+                                       int64_t n_poses, const vgicp_lm_options *opt_in, vgicp_lm_report *report)
+{
     if (!ctx) return VGICP_ERR_INVALID_ARG;
-    if (n_f <= 0 || n_poses <= 0 || !factors || !poses) return VGICP_ERR_INVALID_ARG;
+    if (n_f <= 0 || n_poses <= 0 || !factors || !poses || n_loops < 0 || (n_loops > 0 && !loops))
+        return VGICP_ERR_INVALID_ARG;
     vgicp_lm_options opt{};
     if (opt_in) opt = *opt_in;
     if (opt.max_iterations <= 0) opt.max_iterations = 20;
@@ -321,23 +519,47 @@ vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     if (opt.relative_tolerance <= 0.0) opt.relative_tolerance = 1e-6;
     if (opt.anchor < 0 || opt.anchor >= n_poses) return VGICP_ERR_INVALID_ARG;
     vgicp_lm_report rep{};
-    std::vector<int32_t> pairs((size_t)n_f * 2);
+    // system rows: the matching cost factors, then the loop factors
+    const int64_t n_all = n_f + n_loops;
+    std::vector<int32_t> pairs((size_t)n_all * 2);
     for (int64_t f = 0; f < n_f; ++f) {
         pairs[2 * f] = factors[f].target_pose;
         pairs[2 * f + 1] = factors[f].source_pose;
     }
+    for (int64_t l = 0; l < n_loops; ++l) {
+        if (loops[l].pose_i < 0 || loops[l].pose_i >= n_poses || loops[l].pose_j < 0 || loops[l].pose_j >= n_poses)
+            return VGICP_ERR_INVALID_ARG;
+        pairs[2 * (n_f + l)] = loops[l].pose_i;
+        pairs[2 * (n_f + l) + 1] = loops[l].pose_j;
+    }
     vgicp_plan *plan = nullptr;
     vgicp_status st = vgicp_plan_create(ctx, factors, n_f, n_poses, &plan);
     if (st != VGICP_OK) return st;
-    std::vector<double> H((size_t)n_f * 144), b((size_t)n_f * 12), cost((size_t)n_f), delta((size_t)n_poses * 6);
+    std::vector<double> H((size_t)n_all * 144), b((size_t)n_all * 12), cost((size_t)n_all),
+        delta((size_t)n_poses * 6);
     std::vector<double> trial((size_t)n_poses * 12);
     auto sum = [](const std::vector<double> &v) {
         double s = 0.0;
         for (double x : v) s += x;
         return s;
     };
+    // F and the system at `at`: matching cost factors on the GPU, loop factors on the host
+    auto linearize_all = [&](const double *at) {
+        vgicp_status e = vgicp_plan_linearize(ctx, plan, at, H.data(), b.data(), cost.data(), nullptr,
+                                              VGICP_MEM_HOST);
+        if (e == VGICP_OK && n_loops)
+            e = vgicp_loop_linearize(loops, n_loops, at, n_poses, H.data() + 144 * n_f, b.data() + 12 * n_f,
+                                     cost.data() + n_f);
+        return e;
+    };
+    auto evaluate_all = [&](const double *at) {
+        vgicp_status e = vgicp_evaluate(ctx, factors, n_f, at, n_poses, cost.data(), nullptr, VGICP_MEM_HOST);
+        if (e == VGICP_OK && n_loops)
+            e = vgicp_loop_linearize(loops, n_loops, at, n_poses, nullptr, nullptr, cost.data() + n_f);
+        return e;
+    };
     auto t0 = Clock::now();
-    st = vgicp_plan_linearize(ctx, plan, poses, H.data(), b.data(), cost.data(), nullptr, VGICP_MEM_HOST);
+    st = linearize_all(poses);
     rep.linearize_ms += ms_since(t0);
     double F = sum(cost), lambda = opt.lambda_init;
     rep.initial_cost = F;
@@ -347,7 +569,8 @@ vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
         ++rep.iterations;
         double pred = 0.0;
         t0 = Clock::now();
-        st = vgicp_solve_step(pairs.data(), H.data(), b.data(), n_f, n_poses, opt.anchor, lambda, delta.data(), &pred);
+        st = vgicp_solve_step(pairs.data(), H.data(), b.data(), n_all, n_poses, opt.anchor, lambda, delta.data(),
+                              &pred);
         rep.solve_ms += ms_since(t0);
         if (st == VGICP_ERR_NUMERIC) {   // not positive definite at this damping: damp more
             st = VGICP_OK;
@@ -360,7 +583,7 @@ vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
         std::memcpy(trial.data(), poses, trial.size() * sizeof(double));
         vgicp_se3_retract(trial.data(), delta.data(), n_poses);
         t0 = Clock::now();
-        st = vgicp_evaluate(ctx, factors, n_f, trial.data(), n_poses, cost.data(), nullptr, VGICP_MEM_HOST);
+        st = evaluate_all(trial.data());
         rep.evaluate_ms += ms_since(t0);
         if (st != VGICP_OK) break;
         const double Fn = sum(cost);
@@ -374,7 +597,7 @@ vgicp_status vgicp_optimize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
             lambda = std::max(lambda / 10.0, 1e-12);
             if (rel < opt.relative_tolerance) break;
             t0 = Clock::now();
-            st = vgicp_plan_linearize(ctx, plan, poses, H.data(), b.data(), cost.data(), nullptr, VGICP_MEM_HOST);
+            st = linearize_all(poses);
             rep.linearize_ms += ms_since(t0);
         } else {
             lambda *= 10.0;

@@ -107,3 +107,25 @@ def test_optimize_reduces_cost_and_pose_error(stretch):
         r0, t0 = _rel_errors(poses, gt)
         r1, t1 = _rel_errors(out, gt)
         assert r1 < 0.5 * r0 and t1 < 0.5 * t0, (r0, t0, r1, t1)
+
+
+def test_optimize_with_loop_factor(stretch):
+    """A ground-truth loop measurement between the stretch's ends, under the shifted
+    Tukey kernel, is honoured by the optimiser together with the matching cost factors."""
+    pts, covs, poses, gt = stretch
+    h = lambda T: np.vstack([T, [0, 0, 0, 1]])
+    rel_gt = (np.linalg.inv(h(gt[0])) @ h(gt[N_FRAMES - 1]))[:3]
+    loops = vg.make_loop_factors([0], [N_FRAMES - 1], rel_gt[None], 100.0 * np.eye(6), 25.0, 0.0)
+    with vg.Context() as ctx:
+        fr, maps, f, tgt, src = _setup(ctx, pts, covs, poses)
+        out, rep = ctx.optimize_with_loops(f, loops, poses, max_iterations=15, anchor=0)
+        hist = np.array(rep.history[:rep.n_history])
+        assert rep.accepted >= 2 and np.all(np.diff(hist) < 0)
+        _, _, lc0 = vg.vgicp_loop_linearize(loops, poses)
+        _, _, lc1 = vg.vgicp_loop_linearize(loops, out)
+        assert lc1[0] < lc0[0]
+        c1, _ = ctx.evaluate(f, out)
+        assert float(np.sum(c1)) + lc1[0] == pytest.approx(rep.final_cost, rel=1e-12)
+        err0 = np.linalg.norm(oracle.loop_residual(poses[0], poses[N_FRAMES - 1], rel_gt))
+        err1 = np.linalg.norm(oracle.loop_residual(out[0], out[N_FRAMES - 1], rel_gt))
+        assert err1 < err0

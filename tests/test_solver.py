@@ -113,3 +113,48 @@ def test_solve_step_errors():
         vg.vgicp_solve_step(np.array([[0, 5]]), np.eye(12)[None], b, 2, 0, 0.0)   # pose index out of range
     with pytest.raises(vg.VgicpError):
         vg.vgicp_solve_step(np.array([[0, 1]]), np.eye(12)[None], b, 2, 3, 0.0)   # anchor out of range
+
+
+# ----------------------------------------------------- SE(3) loop factors --
+
+def test_oracle_se3_log_inverts_exp():
+    rng = dg.Stream(21)
+    for scale in (1e-6, 0.1, 1.0, 2.5):
+        xi = rng.normal(6) * scale
+        if np.linalg.norm(xi[:3]) >= np.pi:
+            continue
+        assert np.allclose(oracle.se3_log(oracle.se3_exp(xi)), xi, rtol=0, atol=1e-10 * max(1.0, scale))
+
+
+def test_oracle_tukey_loss_derivative_is_the_weight():
+    # d rho / d(x^2) = weight(x); the weight peaks at the offset and vanishes outside the support
+    for w, o in ((1.0, 0.0), (4.0, 1.5), (0.25, 3.0)):
+        assert oracle.tukey_weight(o, w, o) == 1.0
+        assert oracle.tukey_weight(o + np.sqrt(w) * 1.0001, w, o) == 0.0
+        for x in (0.3, 1.0, 2.2, 3.4):
+            h = 1e-5
+            d = (oracle.tukey_loss(x + h, w, o) - oracle.tukey_loss(x - h, w, o)) / ((x + h) ** 2 - (x - h) ** 2)
+            assert d == pytest.approx(oracle.tukey_weight(x, w, o), abs=1e-7)
+        far = o + np.sqrt(w) + 1.0
+        assert oracle.tukey_loss(far, w, o) == pytest.approx(oracle.tukey_loss(far + 5.0, w, o), rel=1e-12)
+
+
+@pytest.mark.parametrize("offset,width", [(0.0, 4.0), (0.5, 2.0), (2.0, 9.0)])
+def test_loop_factor_matches_oracle(offset, width):
+    rng = dg.Stream(int(40 + 10 * offset))
+    poses = np.stack([dg.random_pose(rng, 40, 20.0) for _ in range(4)])
+    # measurements near the current relative poses: residuals of a few degrees / decimetres
+    Tij = []
+    pi, pj = [0, 1, 3], [2, 3, 0]
+    for i, j in zip(pi, pj):
+        rel = np.linalg.inv(oracle._h(poses[i])) @ oracle._h(poses[j])
+        Tij.append(dg.compose(rel[:3], dg.random_pose(rng, 4, 0.2)))
+    A = rng.normal(36).reshape(6, 6)
+    info = A @ A.T + 6 * np.eye(6)
+    loops = vg.make_loop_factors(pi, pj, np.stack(Tij), info, width, offset)
+    H, b, cost = vg.vgicp_loop_linearize(loops, poses)
+    for k, (i, j) in enumerate(zip(pi, pj)):
+        c_ref, H_ref, b_ref = oracle.loop_factor(poses[i], poses[j], Tij[k], info, width, offset)
+        assert cost[k] == pytest.approx(c_ref, rel=1e-9, abs=1e-12)
+        assert np.allclose(H[k], H_ref, rtol=1e-4, atol=1e-6 * max(1.0, np.abs(H_ref).max()))
+        assert np.allclose(b[k], b_ref, rtol=1e-4, atol=1e-6 * max(1.0, np.abs(b_ref).max()))
