@@ -335,29 +335,60 @@ __global__ void k_build_accumulate(const MapDesc *__restrict__ maps, const Frame
         const MapDesc m = maps[u.map];
         const FrameDesc f = frames[u.frame];
         const float sc = cov_scale(f.stats), sm = mean_scale(m);
-        for (int64_t i = w.start + threadIdx.x; i < w.start + w.count; i += blockDim.x) {
-            const int32_t slot = scr.slot_of_point[u.point_base + i];
-            if (slot < 0) continue;
-            const int32_t vid = scr.vid_of_slot[u.slot_base + slot];
-            const float4 a = __ldg(f.pa + i), b = __ldg(f.pb + i);
-            const float c22 = __ldg(f.pc + i);
-            int kx, ky, kz;
-            unpack_key(m.keys[slot], kx, ky, kz);
-            // offset from the voxel's lower corner k r, r = r_h + r_l
-            const float dx = __fmaf_rn(-(float)kx, m.r_l, __fmaf_rn(-(float)kx, m.r_h, a.x));
-            const float dy = __fmaf_rn(-(float)ky, m.r_l, __fmaf_rn(-(float)ky, m.r_h, a.y));
-            const float dz = __fmaf_rn(-(float)kz, m.r_l, __fmaf_rn(-(float)kz, m.r_h, a.z));
-            unsigned long long *acc = (unsigned long long *)(scr.acc + (u.point_base + vid) * kAcc);
-            atomicAdd(acc + 0, 1ull);
-            atomicAdd(acc + 1, (unsigned long long)__float2ll_rn(dx * sm));
-            atomicAdd(acc + 2, (unsigned long long)__float2ll_rn(dy * sm));
-            atomicAdd(acc + 3, (unsigned long long)__float2ll_rn(dz * sm));
-            atomicAdd(acc + 4, (unsigned long long)__float2ll_rn(a.w * sc));
-            atomicAdd(acc + 5, (unsigned long long)__float2ll_rn(b.x * sc));
-            atomicAdd(acc + 6, (unsigned long long)__float2ll_rn(b.y * sc));
-            atomicAdd(acc + 7, (unsigned long long)__float2ll_rn(b.z * sc));
-            atomicAdd(acc + 8, (unsigned long long)__float2ll_rn(b.w * sc));
-            atomicAdd(acc + 9, (unsigned long long)__float2ll_rn(c22 * sc));
+        const unsigned lane = threadIdx.x & 31;
+        // whole warps step together (the run reduction below shuffles across lanes)
+        for (int64_t i0 = w.start + (threadIdx.x & ~31u); i0 < w.start + w.count; i0 += blockDim.x) {
+            const int64_t i = i0 + lane;
+            int32_t vid = -1;
+            long long v[kAcc];
+#pragma unroll
+            for (int j = 0; j < kAcc; ++j) v[j] = 0;
+            if (i < w.start + w.count) {
+                const int32_t slot = scr.slot_of_point[u.point_base + i];
+                if (slot >= 0) {
+                    vid = scr.vid_of_slot[u.slot_base + slot];
+                    const float4 a = __ldg(f.pa + i), b = __ldg(f.pb + i);
+                    const float c22 = __ldg(f.pc + i);
+                    int kx, ky, kz;
+                    unpack_key(m.keys[slot], kx, ky, kz);
+                    // offset from the voxel's lower corner k r, r = r_h + r_l
+                    const float dx = __fmaf_rn(-(float)kx, m.r_l, __fmaf_rn(-(float)kx, m.r_h, a.x));
+                    const float dy = __fmaf_rn(-(float)ky, m.r_l, __fmaf_rn(-(float)ky, m.r_h, a.y));
+                    const float dz = __fmaf_rn(-(float)kz, m.r_l, __fmaf_rn(-(float)kz, m.r_h, a.z));
+                    v[0] = 1;
+                    v[1] = __float2ll_rn(dx * sm);
+                    v[2] = __float2ll_rn(dy * sm);
+                    v[3] = __float2ll_rn(dz * sm);
+                    v[4] = __float2ll_rn(a.w * sc);
+                    v[5] = __float2ll_rn(b.x * sc);
+                    v[6] = __float2ll_rn(b.y * sc);
+                    v[7] = __float2ll_rn(b.z * sc);
+                    v[8] = __float2ll_rn(b.w * sc);
+                    v[9] = __float2ll_rn(c22 * sc);
+                }
+            }
+            // consecutive points (firing order) often share a voxel: a segmented
+            // inclusive scan over runs of equal voxel ids, then one atomic per run
+            // and sum from the run's last lane.  Integer sums: the result does not
+            // depend on the grouping.
+            const int32_t prev = __shfl_up_sync(0xffffffffu, vid, 1);
+            bool seg = lane == 0 || prev != vid;       // a run starts here
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const bool up_seg = __shfl_up_sync(0xffffffffu, seg, d);
+#pragma unroll
+                for (int j = 0; j < kAcc; ++j) {
+                    const long long x = __shfl_up_sync(0xffffffffu, v[j], d);
+                    if (lane >= (unsigned)d && !seg) v[j] += x;
+                }
+                if (lane >= (unsigned)d) seg = seg || up_seg;
+            }
+            const int32_t next = __shfl_down_sync(0xffffffffu, vid, 1);
+            if (vid >= 0 && (lane == 31 || next != vid)) {
+                unsigned long long *acc = (unsigned long long *)(scr.acc + (u.point_base + vid) * kAcc);
+#pragma unroll
+                for (int j = 0; j < kAcc; ++j) atomicAdd(acc + j, (unsigned long long)v[j]);
+            }
         }
     }
 }
