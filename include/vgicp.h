@@ -102,7 +102,9 @@ typedef struct {
     int32_t chunk_points;     /* points per work item of the batched path (one warp per item; multiple of 32;
                                  0 = default 2048) */
     int32_t linearize_variant;/* batched kernel variant: 0 default, 1 to 5 (same results, different
-                                 latency hiding; chosen by measurement) */
+                                 latency hiding), 6 (maps of at most 4,096 voxels probed from a copy in
+                                 shared memory, one CTA per SM taking runs of items with one target);
+                                 chosen by measurement */
     int32_t blocks_per_sm;    /* persistent grid = SMs x this (0 = the variant's default) */
     int64_t hbm_budget_bytes; /* device bytes handles may hold in total (0 = unlimited) */
     /* 1 (default): overlap pairs whose source bounding box, moved by the pair's

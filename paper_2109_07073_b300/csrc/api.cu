@@ -42,8 +42,8 @@ struct Plan {
     std::vector<vgicp_factor> key;
     std::vector<int64_t> frame_n;
     int chunk = 0;
-    int n_items = 0;
-    Buf idx, items, item_range;
+    int n_items = 0, n_units = 0;
+    Buf idx, items, item_range, units;
 };
 
 constexpr int kMaxLanes = 4;
@@ -366,6 +366,8 @@ void fill_map_desc(MapDesc &m, char *base, uint32_t cap, double r)
     m.keys = (uint64_t *)base;
     m.rec = (VoxelRec *)(base + align256((size_t)cap * 8));
     m.ckeys = (uint32_t *)(base + align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)));
+    m.img = (unsigned char *)(base + align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)) +
+                              align256((size_t)cap * 4));
     m.kbox = (int32_t *)(base + map_bytes(cap) - 256 + 16);
     m.cmeta = (int32_t *)(base + map_bytes(cap) - 256 + 48);
     m.mask = cap - 1;
@@ -382,7 +384,8 @@ void fill_map_desc(MapDesc &m, char *base, uint32_t cap, double r)
 
 size_t map_bytes(uint32_t cap)
 {
-    return align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)) + align256((size_t)cap * 4) + 256;
+    return align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)) + align256((size_t)cap * 4) +
+           align256(kImgMaxBytes) + 256;
 }
 
 uint32_t *map_nvox_ptr(const Obj &o) { return (uint32_t *)((char *)o.map_mem + o.map_bytes - 256); }
@@ -431,7 +434,7 @@ vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const 
     launch_voxelmap_build(ctx->d_maps, ctx->d_frames, (const BuildUnit *)LN.ws_bunits.p, nu,
                           (const WorkItem *)LN.ws_bitems.p, (int)items.size(), (const int64_t *)LN.ws_bprefix.p,
                           scr, grid, LN.stream);
-    ctx->launches += 1 + (items.empty() ? 0 : 4);
+    ctx->launches += 2 + (items.empty() ? 0 : 4);
     CHECK_LAUNCH();
     return VGICP_OK;
 }
@@ -485,6 +488,8 @@ int default_chunk(const vgicp_options &o) { return o.chunk_points > 0 ? o.chunk_
 int neighbor_count(const vgicp_options &o) { return o.neighbors > 1 ? o.neighbors : 1; }
 // chunk culling tests the target's voxel box, so it holds for the containing voxel only
 int lin_cull(const vgicp_options &o) { return neighbor_count(o) == 1 ? o.linearize_cull : 0; }
+// variant 6: the shared-memory map path (single-voxel, unweighted association)
+bool uses_img(const vgicp_options &o) { return o.linearize_variant == 6 && neighbor_count(o) == 1 && !o.count_weighted; }
 
 // Descriptor-table indices of a factor set (map, frame, target pose, source
 // pose per factor), after checking handles, pose indices and pose entries.
@@ -520,6 +525,23 @@ vgicp_status factor_indices(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
 // their voxel records stay in L2.  range[2 f], range[2 f + 1] delimit factor f's
 // items.  The order changes no sum: each factor's chunks are reduced in chunk
 // order whatever their position in the list.
+// Work units of the shared-memory map path: runs of at most kUnitItems
+// consecutive items with the same target map, (map, first item, end item, 0).
+constexpr int kUnitItems = 32;
+
+void build_units(const std::vector<int32_t> &idx, const std::vector<WorkItem> &items, std::vector<int4> &units)
+{
+    units.clear();
+    size_t b = 0;
+    while (b < items.size()) {
+        const int32_t map = idx[4 * items[b].unit];
+        size_t e = b + 1;
+        while (e < items.size() && e - b < (size_t)kUnitItems && idx[4 * items[e].unit] == map) ++e;
+        units.push_back(make_int4(map, (int)b, (int)e, 0));
+        b = e;
+    }
+}
+
 void build_items(const std::vector<int32_t> &idx, const std::vector<int64_t> &frame_n, int chunk,
                  std::vector<WorkItem> &items, std::vector<int32_t> &range)
 {
@@ -566,9 +588,13 @@ vgicp_status get_plan(vgicp_ctx *ctx, const vgicp_factor *f, int64_t n_f, const 
     std::vector<WorkItem> items;
     std::vector<int32_t> range;
     build_items(idx, P.frame_n, chunk, items, range);
+    std::vector<int4> units;
+    build_units(idx, items, units);
     TRY(upload(ctx, P.idx, idx.data(), idx.size()));
     TRY(upload(ctx, P.items, items.data(), items.size()));
     TRY(upload(ctx, P.item_range, range.data(), range.size()));
+    TRY(upload(ctx, P.units, units.data(), units.size()));
+    P.n_units = (int)units.size();
     P.key.assign(f, f + n_f);
     P.chunk = chunk;
     P.n_items = (int)items.size();
@@ -605,8 +631,8 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "neighbors must be 1, 7 or 27");
     if (o->count_weighted != 0 && o->count_weighted != 1)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "count_weighted must be 0 or 1");
-    if (o->linearize_variant < 0 || o->linearize_variant > 5)
-        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_variant must be in 0..5");
+    if (o->linearize_variant < 0 || o->linearize_variant > 6)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_variant must be in 0..6");
     if (o->blocks_per_sm < 0 || o->hbm_budget_bytes < 0)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
     if (o->overlap_cull != 0 && o->overlap_cull != 1)
@@ -666,7 +692,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
                        &LN.ws_bprefix, &LN.ws_slot_of_point, &LN.ws_acc, &LN.ws_vid_of_slot,
                        &LN.ws_slot_of_vid, &LN.ws_pairs, &LN.ws_fidx, &LN.ws_midx, &LN.ws_chunks,
                        &LN.ws_export_keys, &LN.ws_export_rec, &LN.ws_counter, &LN.ws_descs, &LN.ws_tune,
-                       &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_range, &LN.ws_fetch,
+                       &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_range, &LN.plan.units, &LN.ws_fetch,
                        &LN.ws_items};
         for (Buf *b : bufs) free_buf(ctx, *b);
         const cudaError_t e2 = cudaStreamSynchronize(LN.stream);
@@ -963,11 +989,17 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         TRY(ensure(ctx, LN.ws_partials, (size_t)std::max(1, P.n_items) * 28 * 8));
         TRY(ensure(ctx, LN.ws_inl, (size_t)std::max(1, P.n_items) * 8));
         TRY(ensure(ctx, LN.ws_fetch, 16));
-        launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
-                             (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p,
-                             ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
-                             ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt),
-                             ctx->opt.count_weighted, LN.stream);
+        if (uses_img(ctx->opt))
+            launch_linearize_img(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p,
+                                 (const int4 *)P.units.p, P.n_units, (double *)LN.ws_partials.p,
+                                 (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p, ctx->num_sms,
+                                 ctx->opt.precision == VGICP_PREC_F32_COMP, LN.stream);
+        else
+            launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
+                                 (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p,
+                                 ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
+                                 ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt),
+                                 ctx->opt.count_weighted, LN.stream);
         launch_reduce_finalize(d_params, (const int32_t *)P.item_range.p, (int)n_f, (const double *)LN.ws_partials.p,
                                (const int64_t *)LN.ws_inl.p, dH, db, dc, di, LN.stream);
         ctx->launches += (P.n_items > 0) + 1;
@@ -1001,7 +1033,8 @@ struct vgicp_plan {
     std::vector<int64_t> frame_n;
     int64_t n_f = 0, n_poses = 0;
     int n_items = 0;
-    Buf d_idx, d_items, d_range, d_poses, d_params, d_partials, d_inl, d_out, d_fetch;
+    Buf d_idx, d_items, d_range, d_poses, d_params, d_partials, d_inl, d_out, d_fetch, d_units;
+    int n_units = 0;
     double *h_poses = nullptr;           // pinned staging read by the graph's upload node
     cudaStream_t cap = nullptr;          // capture stream (nothing runs on it)
     cudaGraphExec_t exec = nullptr;
@@ -1052,6 +1085,10 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
         std::vector<WorkItem> items;
         std::vector<int32_t> range;
         build_items(idx, fn, chunk, items, range);
+        std::vector<int4> units;
+        build_units(idx, items, units);
+        TRY(upload(ctx, P->d_units, units.data(), units.size()));
+        P->n_units = (int)units.size();
         TRY(upload(ctx, P->d_idx, idx.data(), idx.size()));
         TRY(upload(ctx, P->d_items, items.data(), items.size()));
         TRY(upload(ctx, P->d_range, range.data(), range.size()));
@@ -1074,11 +1111,17 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
     cudaMemcpyAsync(P->d_poses.p, P->h_poses, (size_t)P->n_poses * 12 * 8, cudaMemcpyHostToDevice, P->cap);
     launch_prepare_factors((const int32_t *)P->d_idx.p, (int)n_f, (const double *)P->d_poses.p, ctx->d_maps,
                            ctx->d_frames, lin_cull(ctx->opt), params, P->cap);
-    launch_linearize_f32(params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P->d_items.p, P->n_items,
-                         (double *)P->d_partials.p, (int64_t *)P->d_inl.p, (int *)P->d_fetch.p,
-                         ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
-                         ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt),
-                         ctx->opt.count_weighted, P->cap);
+    if (uses_img(ctx->opt))
+        launch_linearize_img(params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P->d_items.p,
+                             (const int4 *)P->d_units.p, P->n_units, (double *)P->d_partials.p,
+                             (int64_t *)P->d_inl.p, (int *)P->d_fetch.p, ctx->num_sms,
+                             ctx->opt.precision == VGICP_PREC_F32_COMP, P->cap);
+    else
+        launch_linearize_f32(params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P->d_items.p, P->n_items,
+                             (double *)P->d_partials.p, (int64_t *)P->d_inl.p, (int *)P->d_fetch.p,
+                             ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
+                             ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt),
+                             ctx->opt.count_weighted, P->cap);
     launch_reduce_finalize(params, (const int32_t *)P->d_range.p, (int)n_f, (const double *)P->d_partials.p,
                            (const int64_t *)P->d_inl.p, H, b, c, inl, P->cap);
     cudaGraph_t g = nullptr;
@@ -1111,7 +1154,7 @@ void plan_free(vgicp_ctx *ctx, vgicp_plan *P)
     if (P->in_flight) cudaEventSynchronize(P->done);
     if (P->exec) cudaGraphExecDestroy(P->exec);
     Buf *bufs[] = {&P->d_idx, &P->d_items, &P->d_range, &P->d_poses, &P->d_params, &P->d_partials, &P->d_inl,
-                   &P->d_out, &P->d_fetch};
+                   &P->d_out, &P->d_fetch, &P->d_units};
     for (Buf *b : bufs) free_buf(ctx, *b);
     if (P->h_poses) cudaFreeHost(P->h_poses);
     if (P->done) cudaEventDestroy(P->done);
@@ -1276,7 +1319,7 @@ vgicp_status vgicp_autotune(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     float win_ms = 1e30f;
     static const int chunks[] = {1024, 2048, 4096, 8192};
     vgicp_status st = VGICP_OK;
-    for (int variant = 0; variant <= 5 && st == VGICP_OK; ++variant)
+    for (int variant = 0; variant <= 6 && st == VGICP_OK; ++variant)
         for (int ci = 0; ci < 4 && st == VGICP_OK; ++ci) {
             ctx->opt = keep;
             if (keep.precision == VGICP_PREC_F64) ctx->opt.precision = VGICP_PREC_F32;

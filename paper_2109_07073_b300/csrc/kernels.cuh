@@ -79,6 +79,9 @@ void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const Fr
 
 // Per-factor fixed-order float64 reduction of the item partials and expansion
 // to the 12x12 H, b, cost.  item_begin has n_f + 1 entries.
+void launch_linearize_img(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
+                          const WorkItem *items, const int4 *units, int n_units, double *partials,
+                          int64_t *inl_partials, int *next_unit, int num_sms, bool compensated, cudaStream_t st);
 void launch_cost_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                      int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
                      int grid_per_sm, int num_sms, bool compensated, int nb, int weighted, cudaStream_t st);

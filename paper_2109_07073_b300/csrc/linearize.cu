@@ -718,6 +718,158 @@ __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const Ma
         linearize_points<PTS, FF, NT>(P, m, F, w, lane, acc, inl);
 }
 
+// ------------------------------------------------ shared-memory map path --
+//
+// Work units are runs of work items that share a target map (the item list is
+// grouped by target).  A CTA takes a unit, copies the map's image (compact-key
+// hash table, voxel ids, dense records) into shared memory unless it holds it
+// already, and its warps run the unit's items probing shared memory only; maps
+// without an image take the global-memory path inside the same unit.  The
+// per-point arithmetic and the per-lane order are those of the global path.
+constexpr int kImgBlock = 512;
+
+template <bool FF>
+__device__ __forceinline__ void linearize_points_img(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
+                                                     const WorkItem &w, int lane, float acc[kNT], int &inl,
+                                                     const uint32_t *__restrict__ hdr)
+{
+    const uint32_t lg = hdr[1], mask = (1u << lg) - 1u;
+    const uint32_t ex = hdr[3] & 0xffffu, ey = hdr[3] >> 16, ez = hdr[7];
+    const int kb0 = (int)hdr[4], kb1 = (int)hdr[5], kb2 = (int)hdr[6];
+    const uint32_t *__restrict__ keys = hdr + kImgHeader / 4;
+    const uint16_t *__restrict__ vids = (const uint16_t *)(keys + (1u << lg));
+    const float *__restrict__ recs = (const float *)((const unsigned char *)hdr + kImgHeader + img_table_bytes(lg));
+    const float4 *__restrict__ pa = F.pa + w.start;
+    const float4 *__restrict__ pb = F.pb + w.start;
+    const float *__restrict__ pc = F.pc + w.start;
+    const int n = w.count;
+    float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
+    float C = 0.f;
+    if (lane < n) {
+        A = __ldg(pa + lane);
+        B = __ldg(pb + lane);
+        C = __ldg(pc + lane);
+    }
+    for (int i = lane; i < n; i += 32) {
+        const float4 A0 = A, B0 = B;
+        const float C0 = C;
+        if (i + 32 < n) {
+            A = __ldg(pa + i + 32);
+            B = __ldg(pb + i + 32);
+            C = __ldg(pc + i + 32);
+        }
+        int k[3];
+        float d[3], x[3];
+        const bool ok = FF ? point_key_ff(P, m, A0.x, A0.y, A0.z, k, d, x)
+                           : point_key_split(P, m, A0.x, A0.y, A0.z, k, d, x);
+        if (!ok) continue;
+        const uint32_t dx = (uint32_t)(k[0] - kb0), dy = (uint32_t)(k[1] - kb1), dz = (uint32_t)(k[2] - kb2);
+        if (dx > ex || dy > ey || dz > ez) continue;          // outside the voxel box: no voxel
+        const uint32_t ck = pack_compact((int)dx, (int)dy, (int)dz);
+        uint32_t h = hash_compact(ck, lg);
+        int vid = -1;
+        for (uint32_t t = 0; t <= mask; ++t) {
+            const uint32_t v = keys[h];
+            if (v == ck) {
+                vid = vids[h];
+                break;
+            }
+            if (v == kEmptyCompact) break;
+            h = (h + 1) & mask;
+        }
+        if (vid < 0) continue;
+        const float2 *r2 = (const float2 *)(recs + (size_t)vid * kImgRecFloats);
+        const float2 q0 = r2[0], q1 = r2[1], q2 = r2[2], q3 = r2[3], q4 = r2[4];
+        VoxelRec v;
+        v.a = make_float4(q0.x, q0.y, q1.x, q1.y);
+        v.b = make_float4(q2.x, q2.y, q3.x, q3.y);
+        v.c = make_float4(q4.x, q4.y, 0.f, 0.f);
+        inl += accumulate_point(acc, P.Rh, A0, B0, C0, v, d, x);
+    }
+}
+
+template <bool FF>
+__global__ void __launch_bounds__(kImgBlock, 1) k_linearize_img(const PoseParam *__restrict__ params,
+                                                                const MapDesc *__restrict__ maps,
+                                                                const FrameDesc *__restrict__ frames,
+                                                                const WorkItem *__restrict__ items,
+                                                                const int4 *__restrict__ units, int n_units,
+                                                                double *__restrict__ partials,
+                                                                int64_t *__restrict__ inl_partials,
+                                                                int *__restrict__ next_unit)
+{
+    extern __shared__ uint4 s_img4[];
+    const uint32_t *s_img = (const uint32_t *)s_img4;
+    constexpr int NW = kImgBlock / 32;
+    constexpr int PW = (int)(sizeof(PoseParam) / 4);
+    __shared__ PoseParam sP[NW];
+    __shared__ MapDesc sM[NW];
+    __shared__ int s_unit, s_map, s_valid;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_map = -1;
+    for (;;) {
+        __syncthreads();                                // the previous unit's readers are done
+        if (threadIdx.x == 0) s_unit = atomicAdd(next_unit, 1);
+        __syncthreads();
+        const int q = s_unit;
+        if (q >= n_units) break;
+        const int4 U = units[q];                        // (map, first item, end item, -)
+        if (U.x != s_map) {                             // uniform: stage this map's image
+            const unsigned char *img = maps[U.x].img;
+            const uint32_t valid = __ldg((const uint32_t *)img);
+            if (valid) {
+                const uint32_t lg = __ldg((const uint32_t *)img + 1), nv = __ldg((const uint32_t *)img + 2);
+                const int n4 = (int)(img_bytes((int)lg, (int)nv) / 16);
+                const uint4 *src = (const uint4 *)img;
+                for (int j = threadIdx.x; j < n4; j += kImgBlock) s_img4[j] = __ldg(src + j);
+            }
+            if (threadIdx.x == 0) {
+                s_map = U.x;
+                s_valid = (int)valid;
+            }
+            __syncthreads();
+        }
+        const bool staged = s_valid != 0;
+        for (int it = U.y + wib; it < U.z; it += NW) {
+            const WorkItem w = items[it];
+            __syncwarp();
+            const uint32_t *src = (const uint32_t *)(params + w.unit);
+            uint32_t *dst = (uint32_t *)(sP + wib);
+            for (int j = lane; j < PW; j += 32) dst[j] = __ldg(src + j);
+            __syncwarp();
+            if (lane == 0) sM[wib] = maps[sP[wib].map];
+            __syncwarp();
+            const PoseParam &P = sP[wib];
+            const MapDesc m = sM[wib];
+            const FrameDesc F = frames[P.frame];
+            float acc[kNT];
+#pragma unroll
+            for (int j = 0; j < kNT; ++j) acc[j] = 0.f;
+            int inl = 0;
+            const int c0 = (int)(w.start >> F.cshift), c1 = (int)((w.start + w.count - 1) >> F.cshift);
+            const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
+            if (w.count > 0 && (P.cmask & span) != 0u) {
+                if (staged)
+                    linearize_points_img<FF>(P, m, F, w, lane, acc, inl, s_img);
+                else
+                    linearize_points<1, FF, kNT>(P, m, F, w, lane, acc, inl);
+            }
+            double mine = 0.0;
+#pragma unroll
+            for (int j = 0; j < kNT; ++j) {
+                float x = acc[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == j) mine = (double)x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) inl += __shfl_xor_sync(0xffffffffu, inl, o);
+            if (lane < kNT) partials[(int64_t)it * kNT + lane] = mine;
+            if (lane == kNT) inl_partials[it] = inl;
+        }
+    }
+}
+
 template <int BLOCK, int MINB, int PTS, bool FF, int NT = kNT>
 __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *__restrict__ params,
                                                                const MapDesc *__restrict__ maps,
@@ -1128,6 +1280,24 @@ void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const Fr
     else
         launch_variant<false, kNT>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
                                    grid_per_sm, num_sms, nb, weighted, st);
+}
+
+void launch_linearize_img(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
+                          const WorkItem *items, const int4 *units, int n_units, double *partials,
+                          int64_t *inl_partials, int *next_unit, int num_sms, bool compensated, cudaStream_t st)
+{
+    if (n_units <= 0) return;
+    cudaMemsetAsync(next_unit, 0, sizeof(int), st);
+    const int smem = (int)kImgMaxBytes;
+    if (compensated) {
+        cudaFuncSetAttribute(k_linearize_img<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_linearize_img<true><<<num_sms, kImgBlock, smem, st>>>(params, maps, frames, items, units, n_units, partials,
+                                                               inl_partials, next_unit);
+    } else {
+        cudaFuncSetAttribute(k_linearize_img<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_linearize_img<false><<<num_sms, kImgBlock, smem, st>>>(params, maps, frames, items, units, n_units,
+                                                                partials, inl_partials, next_unit);
+    }
 }
 
 void launch_cost_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,

@@ -34,9 +34,29 @@ struct __align__(16) VoxelRec {
     float4 c;   // c22, count (uint32 bits), unused, unused
 };
 
+// Shared-memory image of a small voxelmap (at most kImgMaxVoxels voxels, box
+// within the compact-key extents), kept in the map's allocation: a 32-byte
+// header (valid, lg, nv, -, box minimum x y z, -), a hash table of 2^lg
+// box-relative compact keys (load <= 1/2), the voxel id of each slot (uint16),
+// and the voxels' records packed densely, kImgRecFloats floats each: mean
+// relative to the voxel corner (3), covariance (6), count (uint32 bits).  One
+// CTA copies it into shared memory and probes without global-memory gathers.
+// Header words: 0 valid, 1 lg, 2 nv, 3 box extents x | y << 16, 4-6 box
+// minimum, 7 box extent z.
+constexpr int kImgMaxVoxels = 4096;
+constexpr int kImgRecFloats = 10;
+constexpr size_t kImgHeader = 32;
+__host__ __device__ constexpr size_t img_table_bytes(int lg) { return (size_t)6 << lg; }
+__host__ __device__ constexpr size_t img_bytes(int lg, int nv)
+{
+    return (kImgHeader + img_table_bytes(lg) + (size_t)nv * kImgRecFloats * 4 + 15) & ~(size_t)15;
+}
+constexpr size_t kImgMaxBytes = img_bytes(13, kImgMaxVoxels);
+
 struct MapDesc {
     uint64_t *keys;
     VoxelRec *rec;
+    unsigned char *img;  // shared-memory image (header word 0 = 1 when valid)
     int32_t *kbox;       // device: min voxel coordinate (3), max voxel coordinate (3)
     uint32_t *ckeys;     // compact presence table (capacity cap; the first 2^cmeta[0] entries used)
     int32_t *cmeta;      // device: log2 of the compact table's used capacity, 1 if the map has one

@@ -476,6 +476,57 @@ __global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUni
     }
 }
 
+// Shared-memory images of the built maps that qualify (one block per map).
+__global__ void k_build_image(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units, int n_units,
+                              BuildScratch scr)
+{
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const BuildUnit U = units[u];
+        const MapDesc m = maps[U.map];
+        const uint32_t nv = *U.n_voxels;
+        const int *kb = m.kbox;
+        uint32_t *hdr = (uint32_t *)m.img;
+        const bool ok = nv > 0 && nv <= (uint32_t)kImgMaxVoxels && kb[3] - kb[0] <= kCompactMaxX &&
+                        kb[4] - kb[1] <= kCompactMaxX && kb[5] - kb[2] <= kCompactMaxZ;
+        int lg = 4;
+        while ((1u << lg) < 2u * nv) ++lg;
+        if (threadIdx.x == 0) {
+            hdr[0] = ok ? 1u : 0u;
+            hdr[1] = (uint32_t)lg;
+            hdr[2] = nv;
+            hdr[3] = ok ? (uint32_t)(kb[3] - kb[0]) | ((uint32_t)(kb[4] - kb[1]) << 16) : 0u;   // box extents x, y
+            for (int j = 0; j < 3; ++j) hdr[4 + j] = (uint32_t)kb[j];
+            hdr[7] = ok ? (uint32_t)(kb[5] - kb[2]) : 0u;                                       // and z
+        }
+        if (!ok) continue;
+        uint32_t *keys = (uint32_t *)(m.img + kImgHeader);
+        uint16_t *vids = (uint16_t *)(m.img + kImgHeader + ((size_t)4 << lg));
+        float *recs = (float *)(m.img + kImgHeader + img_table_bytes(lg));
+        const uint32_t mask = (1u << lg) - 1u;
+        for (uint32_t t = threadIdx.x; t <= mask; t += blockDim.x) keys[t] = kEmptyCompact;
+        __syncthreads();
+        for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
+            const int32_t slot = scr.slot_of_vid[U.point_base + v];
+            int kx, ky, kz;
+            unpack_key(m.keys[slot], kx, ky, kz);
+            const uint32_t ck = pack_compact(kx - kb[0], ky - kb[1], kz - kb[2]);
+            uint32_t h = hash_compact(ck, (uint32_t)lg);
+            for (uint32_t t = 0; t <= mask; ++t) {
+                const uint32_t old = atomicCAS(keys + h, kEmptyCompact, ck);
+                if (old == kEmptyCompact) break;
+                h = (h + 1) & mask;
+            }
+            vids[h] = (uint16_t)v;
+            const VoxelRec r = m.rec[slot];
+            float *o = recs + (size_t)v * kImgRecFloats;
+            o[0] = r.a.x; o[1] = r.a.y; o[2] = r.a.z; o[3] = r.a.w;
+            o[4] = r.b.x; o[5] = r.b.y; o[6] = r.b.z; o[7] = r.b.w;
+            o[8] = r.c.x; o[9] = r.c.y;
+        }
+        __syncthreads();                                // before the block's next map clears its table
+    }
+}
+
 __global__ void k_scatter_map_descs(const uint32_t *__restrict__ idx, const MapDesc *__restrict__ src, int n,
                                     MapDesc *__restrict__ table)
 {
@@ -533,11 +584,14 @@ void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const B
 {
     if (n_units <= 0) return;
     k_build_clear<<<148 * 8, 256, 0, st>>>(maps, units, n_units, slot_prefix, scr.vid_of_slot);
-    if (n_items <= 0) return;
-    k_build_insert<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
-    k_build_accumulate<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
-    k_build_finalize<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
-    k_build_compact<<<grid, 256, 0, st>>>(maps, units, items, n_items, scr);
+    if (n_items > 0) {
+        k_build_insert<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
+        k_build_accumulate<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
+        k_build_finalize<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
+        k_build_compact<<<grid, 256, 0, st>>>(maps, units, items, n_items, scr);
+    }
+    // every map's image header is written (an empty map's is marked invalid)
+    k_build_image<<<std::min(n_units, 148 * 4), 256, 0, st>>>(maps, units, n_units, scr);
 }
 
 void launch_scatter_map_descs(const uint32_t *idx, const MapDesc *src, int n, MapDesc *table, cudaStream_t st)

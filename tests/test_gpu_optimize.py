@@ -57,7 +57,7 @@ def _rel_errors(P, gt):
 
 
 @pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F32_COMP])
-@pytest.mark.parametrize("variant", [0, 2, 4])
+@pytest.mark.parametrize("variant", [0, 2, 4, 6])
 def test_evaluate_equals_linearize_cost(stretch, prec, variant):
     pts, covs, poses, _ = stretch
     with vg.Context(precision=prec, linearize_variant=variant) as ctx:

@@ -387,7 +387,7 @@ def test_knn_covariances_match_oracle(ctx, single):
     assert np.array_equal(ctx.estimate_covariances(tiny, 10, 1e-3), oracle.covariances(tiny))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_linearize_variants_agree(ctx, variant):
     tg, tcov, src, scov, poses, factors = _ragged_case(seed=45)
     hm = [ctx.build_voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
@@ -404,6 +404,41 @@ def test_linearize_variants_agree(ctx, variant):
     assert np.allclose(H0, H1, rtol=1e-5, atol=1e-9 * np.abs(H0).max())
     assert np.allclose(b0, b1, rtol=1e-5, atol=1e-9 * np.abs(b0).max())
     for h in hm + hf:
+        ctx.release(h)
+
+
+def test_linearize_shared_memory_maps_mixed(ctx, loop_frames):
+    """Variant 6 with targets that have a shared-memory image (<= 4,096 voxels), one
+    too large for it (0.25 m voxels), and an empty one: equal to variant 0 and to
+    the oracle."""
+    g, ids, pts, covs = loop_frames
+    P = g.poses[ids]
+    hm_small = [ctx.build_voxelmap(pts[i], covs[i], 1.0) for i in range(3)]
+    hm_big = ctx.build_voxelmap(pts[3], covs[3], 0.25)
+    hm_empty = ctx.build_voxelmap(np.zeros((0, 3), np.float32), np.zeros((0, 6), np.float32), 1.0)
+    fr = [ctx.add_frame(p, c) for p, c in zip(pts[:5], covs[:5])]
+    tg = [hm_small[0], hm_small[0], hm_small[1], hm_big, hm_big, hm_small[2], hm_empty]
+    ti = [0, 0, 1, 3, 3, 2, 0]
+    sc = [1, 2, 0, 4, 2, 1, 3]
+    f = vg.make_factors(tg, np.array(fr)[sc], ti, sc)
+    ctx.set_options(linearize_variant=0)
+    ref = ctx.linearize(f, P)
+    ctx.set_options(linearize_variant=6)
+    got = ctx.linearize(f, P)
+    c6, i6 = ctx.evaluate(f, P)
+    ctx.set_options(linearize_variant=0)
+    assert np.array_equal(got[3], ref[3])
+    assert np.allclose(got[0], ref[0], rtol=1e-5, atol=1e-9 * np.abs(ref[0]).max())
+    assert np.array_equal(got[2], c6) or np.allclose(got[2], c6, rtol=1e-6)
+    res = {0: 1.0, 1: 1.0, 2: 1.0, 3: 0.25}
+    for k in range(len(tg) - 1):
+        vm = oracle.voxelmap(pts[ti[k]], covs[ti[k]], res[ti[k]])
+        L = oracle.linearize(vm, pts[sc[k]], covs[sc[k]], oracle.relative_pose(P[ti[k]], P[sc[k]]))
+        assert got[3][k] == L.inliers
+        if L.inliers:
+            assert err_metric(got[0][k], L.H, L.SH) <= TOL[vg.VGICP_PREC_F32]
+    assert got[3][-1] == 0 and not got[0][-1].any()
+    for h in hm_small + [hm_big, hm_empty] + fr:
         ctx.release(h)
 
 
@@ -440,7 +475,7 @@ def test_autotune_keeps_results(ctx, single):
     poses = np.stack([w.T_target, w.T_source])
     f = vg.make_factors([hm, hm], [hf, hf], [0, 1], [1, 0])
     best, ms = ctx.autotune(f, poses, reps=1)
-    assert ms > 0 and best.linearize_variant in range(6) and best.chunk_points in (1024, 2048, 4096, 8192)
+    assert ms > 0 and best.linearize_variant in range(7) and best.chunk_points in (1024, 2048, 4096, 8192)
     H, b, cost, inl = ctx.linearize(f, poses)
     vm = oracle.voxelmap(w.points_target, cb, w.resolution)
     L = _oracle_factor(vm, w.points_source, ca, w.T_target, w.T_source)
