@@ -80,7 +80,9 @@ def load_frames(n_frames, n_points, seed):
         z = np.load(path)
         pts = [z[f"p{i}"] for i in range(n_frames)]
         return pts, z["poses"], z["poses_gt"]
-    g = dg.graph_workload(seed=seed, n_frames=n_frames, n_points=n_points)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    g = dg.graph_workload(seed=seed, n_frames=n_frames, n_points=n_points,
+                          workers=max(1, (os.cpu_count() or 1) // max(1, world)))
     os.makedirs(os.path.dirname(path), exist_ok=True)
     np.savez(path, poses=g.poses, poses_gt=g.poses_gt, **{f"p{i}": p for i, p in enumerate(g.points)})
     return g.points, g.poses, g.poses_gt

@@ -325,14 +325,23 @@ class GraphWorkload:
     boxes: Boxes = None
 
 
+def _graph_frame_job(args):
+    boxes, pose, lidar, seed, n_points = args
+    frng = Stream(seed)
+    p = raycast(boxes, pose, lidar, frng)
+    sel = frng.choose(p.shape[0], n_points)
+    return p[sel].astype(np.float32)
+
+
 def graph_workload(seed: int = None, n_frames: int = 500, spacing: float = 4.0,
                    n_points: int = 20000, n_boxes: int = 400, lidar: Lidar = None,
                    resolution: float = 1.0, rot_sigma_deg: float = 1.0,
-                   trans_sigma: float = 0.1, frame_ids=None) -> GraphWorkload:
+                   trans_sigma: float = 0.1, frame_ids=None, workers: int = 0) -> GraphWorkload:
     """Frames of a 2 km closed loop through the urban scene.
 
     frame_ids: optional subset of frame indices to raycast (the others are left
-    as None); poses are always produced for every frame.
+    as None); poses are always produced for every frame.  workers > 1 raycasts in a
+    spawn process pool (same frames).
     """
     lidar = lidar or Lidar()
     rng = Stream(config_seed(2) if seed is None else seed)
@@ -349,15 +358,17 @@ def graph_workload(seed: int = None, n_frames: int = 500, spacing: float = 4.0,
         xi = np.concatenate([rng.normal(3, math.radians(rot_sigma_deg)), rng.normal(3, trans_sigma)])
         poses[i] = compose(T, se3_exp(xi))
     wanted = set(range(n_frames)) if frame_ids is None else set(int(f) for f in frame_ids)
-    points = []
-    for i in range(n_frames):
-        frng = Stream(int(rng.seed) ^ (0x5851F42D4C957F2D * (i + 1) & 0xFFFFFFFFFFFFFFFF))
-        if i not in wanted:
-            points.append(None)
-            continue
-        p = raycast(boxes, poses_gt[i], lidar, frng)
-        sel = frng.choose(p.shape[0], n_points)
-        points.append(p[sel].astype(np.float32))
+    jobs = {i: (boxes, poses_gt[i], lidar, int(rng.seed) ^ (0x5851F42D4C957F2D * (i + 1) & 0xFFFFFFFFFFFFFFFF),
+                n_points) for i in range(n_frames) if i in wanted}
+    keys = sorted(jobs)
+    if workers and workers > 1 and len(keys) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            done = dict(zip(keys, pool.map(_graph_frame_job, [jobs[k] for k in keys],
+                                           chunksize=max(1, len(keys) // (4 * workers)))))
+    else:
+        done = {k: _graph_frame_job(jobs[k]) for k in keys}
+    points = [done.get(i) for i in range(n_frames)]
     return GraphWorkload(points, poses, poses_gt, resolution, boxes)
 
 
