@@ -29,6 +29,7 @@ struct Obj {
     size_t map_bytes = 0;
     uint32_t cap = 0;
     double r = 0.0;
+    bool img = false;   // shared-memory image made since the last build
 };
 
 struct Buf {
@@ -57,7 +58,7 @@ struct Lane {
     Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
     Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
     Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs, ws_tune, ws_knn;
-    Buf ws_fetch, ws_items;
+    Buf ws_fetch, ws_items, ws_img;
     Plan plan;
     int64_t last_matrix_pairs = 0;   // pairs of the last overlap matrix (params kept in ws_pairs)
     // pinned staging for host -> device copies: two arenas used in turn, each
@@ -434,7 +435,7 @@ vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const 
     launch_voxelmap_build(ctx->d_maps, ctx->d_frames, (const BuildUnit *)LN.ws_bunits.p, nu,
                           (const WorkItem *)LN.ws_bitems.p, (int)items.size(), (const int64_t *)LN.ws_bprefix.p,
                           scr, grid, LN.stream);
-    ctx->launches += 2 + (items.empty() ? 0 : 4);
+    ctx->launches += 1 + (items.empty() ? 0 : 4);
     CHECK_LAUNCH();
     return VGICP_OK;
 }
@@ -459,6 +460,7 @@ vgicp_status prepare_map(vgicp_ctx *ctx, uint32_t idx, int64_t n, double r, bool
         ctx->bytes_in_use += (int64_t)bytes;
     }
     o.r = r;
+    o.img = false;
     MapDesc d{};
     fill_map_desc(d, (char *)o.map_mem, o.cap, r);
     *changed = std::memcmp(&d, &ctx->h_maps[idx], sizeof(MapDesc)) != 0;
@@ -490,6 +492,26 @@ int neighbor_count(const vgicp_options &o) { return o.neighbors > 1 ? o.neighbor
 int lin_cull(const vgicp_options &o) { return neighbor_count(o) == 1 ? o.linearize_cull : 0; }
 // variant 6: the shared-memory map path (single-voxel, unweighted association)
 bool uses_img(const vgicp_options &o) { return o.linearize_variant == 6 && neighbor_count(o) == 1 && !o.count_weighted; }
+
+// Shared-memory images of a factor set's maps that have none since their last
+// build, made on the lane's stream ahead of the linearisation that reads them.
+vgicp_status ensure_images(vgicp_ctx *ctx, const std::vector<int32_t> &idx, int64_t n_f)
+{
+    std::vector<int32_t> todo;
+    for (int64_t i = 0; i < n_f; ++i) {
+        Obj &o = ctx->objs[idx[4 * i]];
+        if (!o.img) {
+            o.img = true;
+            todo.push_back(idx[4 * i]);
+        }
+    }
+    if (todo.empty()) return VGICP_OK;
+    TRY(upload(ctx, LN.ws_img, todo.data(), todo.size()));
+    launch_map_images(ctx->d_maps, (const int32_t *)LN.ws_img.p, (int)todo.size(), ctx->num_sms, LN.stream);
+    ctx->launches += 1;
+    CHECK_LAUNCH();
+    return VGICP_OK;
+}
 
 // Descriptor-table indices of a factor set (map, frame, target pose, source
 // pose per factor), after checking handles, pose indices and pose entries.
@@ -690,7 +712,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
         Buf *bufs[] = {&LN.ws_poses, &LN.ws_params, &LN.ws_partials, &LN.ws_inl, &LN.ws_out, &LN.ws_f64,
                        &LN.ws_ticket, &LN.ws_counts, &LN.ws_stage, &LN.ws_bunits, &LN.ws_bitems,
                        &LN.ws_bprefix, &LN.ws_slot_of_point, &LN.ws_acc, &LN.ws_vid_of_slot,
-                       &LN.ws_slot_of_vid, &LN.ws_pairs, &LN.ws_fidx, &LN.ws_midx, &LN.ws_chunks,
+                       &LN.ws_slot_of_vid, &LN.ws_img, &LN.ws_pairs, &LN.ws_fidx, &LN.ws_midx, &LN.ws_chunks,
                        &LN.ws_export_keys, &LN.ws_export_rec, &LN.ws_counter, &LN.ws_descs, &LN.ws_tune,
                        &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_range, &LN.plan.units, &LN.ws_fetch,
                        &LN.ws_items};
@@ -989,6 +1011,7 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         TRY(ensure(ctx, LN.ws_partials, (size_t)std::max(1, P.n_items) * 28 * 8));
         TRY(ensure(ctx, LN.ws_inl, (size_t)std::max(1, P.n_items) * 8));
         TRY(ensure(ctx, LN.ws_fetch, 16));
+        if (uses_img(ctx->opt)) TRY(ensure_images(ctx, idx, n_f));
         if (uses_img(ctx->opt))
             launch_linearize_img(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p,
                                  (const int4 *)P.units.p, P.n_units, (double *)LN.ws_partials.p,
@@ -1070,6 +1093,7 @@ vgicp_status plan_refresh(vgicp_ctx *ctx, vgicp_plan *P)
         idx[4 * i + 3] = P->factors[i].source_pose;
         fn[i] = ctx->objs[fi].n;
     }
+    if (uses_img(ctx->opt)) TRY(ensure_images(ctx, idx, n_f));
     const int chunk = default_chunk(ctx->opt);
     const bool same_work = chunk == P->chunk && idx == P->idx && fn == P->frame_n;
     if (same_work && P->exec && P->maps == ctx->d_maps && P->frames == ctx->d_frames &&

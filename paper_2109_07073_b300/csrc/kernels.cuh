@@ -53,6 +53,8 @@ struct BuildUnit {
 void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const BuildUnit *units, int n_units,
                            const WorkItem *items, int n_items, const int64_t *slot_items /* n_units+1 prefix */,
                            BuildScratch scr, int grid, cudaStream_t st);
+// Shared-memory images of the maps idx[0..n) (table indices), made on demand.
+void launch_map_images(const MapDesc *maps, const int32_t *idx, int n, int num_sms, cudaStream_t st);
 
 // ----------------------------------------------------------- linearise ---
 // Relative poses T_BA = T_B^-1 T_A for every factor, in the forms the kernels use.

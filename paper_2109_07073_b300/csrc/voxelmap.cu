@@ -476,15 +476,35 @@ __global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUni
     }
 }
 
-// Shared-memory images of the built maps that qualify (one block per map).
-__global__ void k_build_image(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units, int n_units,
-                              BuildScratch scr)
+// Shared-memory images of the listed maps (one block per map), made on first
+// use by the shared-memory linearisation: the occupied slots are counted, and a
+// map that qualifies gets its compact key table, voxel ids and dense records;
+// every listed map's header is written (one that does not qualify is marked
+// invalid).  Voxel ids follow the order the slots are claimed in; lookups see
+// the same records whatever that order.
+constexpr int kImgBuildBlock = 512;
+
+__global__ void __launch_bounds__(kImgBuildBlock) k_map_image(const MapDesc *__restrict__ maps,
+                                                              const int32_t *__restrict__ idx, int n)
 {
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const BuildUnit U = units[u];
-        const MapDesc m = maps[U.map];
-        const uint32_t nv = *U.n_voxels;
-        const int *kb = m.kbox;
+    __shared__ uint32_t s_cnt, s_next;
+    for (int u = blockIdx.x; u < n; u += gridDim.x) {
+        const MapDesc m = maps[idx[u]];
+        const uint32_t cap = m.mask + 1u;
+        if (threadIdx.x == 0) {
+            s_cnt = 0u;
+            s_next = 0u;
+        }
+        __syncthreads();
+        uint32_t c = 0;
+        for (uint32_t s = threadIdx.x; s < cap; s += blockDim.x) c += __ldg(m.keys + s) != kEmptyKey;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt, c);
+        __syncthreads();
+        const uint32_t nv = s_cnt;
+        int kb[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) kb[j] = m.kbox[j];
         uint32_t *hdr = (uint32_t *)m.img;
         const bool ok = nv > 0 && nv <= (uint32_t)kImgMaxVoxels && kb[3] - kb[0] <= kCompactMaxX &&
                         kb[4] - kb[1] <= kCompactMaxX && kb[5] - kb[2] <= kCompactMaxZ;
@@ -498,32 +518,35 @@ __global__ void k_build_image(const MapDesc *__restrict__ maps, const BuildUnit 
             for (int j = 0; j < 3; ++j) hdr[4 + j] = (uint32_t)kb[j];
             hdr[7] = ok ? (uint32_t)(kb[5] - kb[2]) : 0u;                                       // and z
         }
-        if (!ok) continue;
-        uint32_t *keys = (uint32_t *)(m.img + kImgHeader);
-        uint16_t *vids = (uint16_t *)(m.img + kImgHeader + ((size_t)4 << lg));
-        float *recs = (float *)(m.img + kImgHeader + img_table_bytes(lg));
-        const uint32_t mask = (1u << lg) - 1u;
-        for (uint32_t t = threadIdx.x; t <= mask; t += blockDim.x) keys[t] = kEmptyCompact;
-        __syncthreads();
-        for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
-            const int32_t slot = scr.slot_of_vid[U.point_base + v];
-            int kx, ky, kz;
-            unpack_key(m.keys[slot], kx, ky, kz);
-            const uint32_t ck = pack_compact(kx - kb[0], ky - kb[1], kz - kb[2]);
-            uint32_t h = hash_compact(ck, (uint32_t)lg);
-            for (uint32_t t = 0; t <= mask; ++t) {
-                const uint32_t old = atomicCAS(keys + h, kEmptyCompact, ck);
-                if (old == kEmptyCompact) break;
-                h = (h + 1) & mask;
+        if (ok) {
+            uint32_t *keys = (uint32_t *)(m.img + kImgHeader);
+            uint16_t *vids = (uint16_t *)(m.img + kImgHeader + ((size_t)4 << lg));
+            float *recs = (float *)(m.img + kImgHeader + img_table_bytes(lg));
+            const uint32_t mask = (1u << lg) - 1u;
+            for (uint32_t t = threadIdx.x; t <= mask; t += blockDim.x) keys[t] = kEmptyCompact;
+            __syncthreads();
+            for (uint32_t s = threadIdx.x; s < cap; s += blockDim.x) {
+                const uint64_t key = __ldg(m.keys + s);
+                if (key == kEmptyKey) continue;
+                const uint32_t v = atomicAdd(&s_next, 1u);
+                int kx, ky, kz;
+                unpack_key(key, kx, ky, kz);
+                const uint32_t ck = pack_compact(kx - kb[0], ky - kb[1], kz - kb[2]);
+                uint32_t h = hash_compact(ck, (uint32_t)lg);
+                for (uint32_t t = 0; t <= mask; ++t) {
+                    const uint32_t old = atomicCAS(keys + h, kEmptyCompact, ck);
+                    if (old == kEmptyCompact) break;
+                    h = (h + 1) & mask;
+                }
+                vids[h] = (uint16_t)v;
+                const VoxelRec r = m.rec[s];
+                float *o = recs + (size_t)v * kImgRecFloats;
+                o[0] = r.a.x; o[1] = r.a.y; o[2] = r.a.z; o[3] = r.a.w;
+                o[4] = r.b.x; o[5] = r.b.y; o[6] = r.b.z; o[7] = r.b.w;
+                o[8] = r.c.x; o[9] = r.c.y;
             }
-            vids[h] = (uint16_t)v;
-            const VoxelRec r = m.rec[slot];
-            float *o = recs + (size_t)v * kImgRecFloats;
-            o[0] = r.a.x; o[1] = r.a.y; o[2] = r.a.z; o[3] = r.a.w;
-            o[4] = r.b.x; o[5] = r.b.y; o[6] = r.b.z; o[7] = r.b.w;
-            o[8] = r.c.x; o[9] = r.c.y;
         }
-        __syncthreads();                                // before the block's next map clears its table
+        __syncthreads();                                // before the block's next map resets the counters
     }
 }
 
@@ -590,8 +613,12 @@ void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const B
         k_build_finalize<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
         k_build_compact<<<grid, 256, 0, st>>>(maps, units, items, n_items, scr);
     }
-    // every map's image header is written (an empty map's is marked invalid)
-    k_build_image<<<std::min(n_units, 148 * 4), 256, 0, st>>>(maps, units, n_units, scr);
+}
+
+void launch_map_images(const MapDesc *maps, const int32_t *idx, int n, int num_sms, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_map_image<<<std::min(n, num_sms * 4), kImgBuildBlock, 0, st>>>(maps, idx, n);
 }
 
 void launch_scatter_map_descs(const uint32_t *idx, const MapDesc *src, int n, MapDesc *table, cudaStream_t st)

@@ -442,6 +442,35 @@ def test_linearize_shared_memory_maps_mixed(ctx, loop_frames):
         ctx.release(h)
 
 
+def test_shared_memory_images_follow_rebuilds(ctx, loop_frames):
+    """Images are made on first use by variant 6 and made again after a map is rebuilt
+    in place (same handle): direct calls and a captured plan both see the new voxels."""
+    g, ids, pts, covs = loop_frames
+    P = g.poses[ids]
+    fr = [ctx.add_frame(p, c) for p, c in zip(pts[:4], covs[:4])]
+    maps = ctx.build_voxelmaps(fr[:2], 1.0)
+    f = vg.make_factors([maps[0], maps[1], maps[0]], [fr[2], fr[3], fr[1]], [0, 1, 0], [2, 3, 1])
+    ctx.set_options(linearize_variant=6)
+    plan = ctx.plan_create(f, len(P))
+    first = ctx.linearize(f, P)
+    first_plan = ctx.plan_linearize(plan, P)
+    ctx.build_voxelmaps([fr[1], fr[0]], 1.0, maps=maps)     # contents swapped, handles kept
+    again = ctx.linearize(f, P)
+    again_plan = ctx.plan_linearize(plan, P)
+    ctx.set_options(linearize_variant=0)
+    ref = ctx.linearize(f, P)
+    ctx.build_voxelmaps([fr[0], fr[1]], 1.0, maps=maps)
+    ref_first = ctx.linearize(f, P)
+    ctx.plan_destroy(plan)
+    assert not np.array_equal(ref[3], ref_first[3])
+    for got, want in ((first, ref_first), (first_plan, ref_first), (again, ref), (again_plan, ref)):
+        assert np.array_equal(got[3], want[3])
+        assert np.allclose(got[0], want[0], rtol=1e-5, atol=1e-9 * np.abs(want[0]).max())
+        assert np.allclose(got[1], want[1], rtol=1e-5, atol=1e-9 * np.abs(want[1]).max())
+    for h in list(maps) + fr:
+        ctx.release(h)
+
+
 def test_linearize_chunk_culling_is_exact(ctx, loop_frames):
     """Skipping source chunks whose moved box misses the target's voxels changes no sum."""
     g, ids, pts, covs = loop_frames
