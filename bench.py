@@ -308,15 +308,15 @@ def run_ours(a):
         h_counts = pinned((n_frames, n_frames), torch.int64)
         np_pts, np_cov = h_pts.numpy(), h_cov.numpy()
 
-        def compute(fr):
-            mp = ctx.build_voxelmaps(fr, 1.0)
+        def finish(fr, mp):
             ctx.overlap_matrix(fr, mp, poses, poses, out=h_counts)
             fac = vg.make_factors(mp[tgt], fr[src], tgt, src)
             ctx.linearize(fac, poses, out=h_out)
             ctx.release_many(np.concatenate([fr, mp]))
 
         def sequential_step():
-            compute(ctx.add_frames(np_pts, np_cov, sizes))
+            fr = ctx.add_frames(np_pts, np_cov, sizes)
+            finish(fr, ctx.build_voxelmaps(fr, 1.0))
 
         def timed(fn, n):
             torch.cuda.synchronize()
@@ -344,8 +344,9 @@ def run_ours(a):
             ctx.set_lane(1)
             ctx.synchronize()                    # this step's frames are in
             ctx.set_lane(0)
+            mp = ctx.build_voxelmaps(fr, 1.0)
             prefetch()                           # the next step's copy overlaps this step's compute
-            compute(fr)
+            finish(fr, mp)
 
         prefetch()
         for _ in range(2):

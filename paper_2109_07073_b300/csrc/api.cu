@@ -65,6 +65,7 @@ struct Lane {
     // with an event after its latest copy, so copies never wait for the stream
     struct Arena {
         char *p = nullptr;
+        char *dp = nullptr;   // the same memory as the device addresses it
         size_t cap = 0, off = 0;
         cudaEvent_t ev = nullptr;
         bool pending = false;
@@ -156,7 +157,7 @@ void free_buf(vgicp_ctx *ctx, Buf &b)
 // stream: the bytes go through a pinned staging arena of the lane (a copy from
 // pageable memory may first wait for the work queued before it).  An arena is
 // reused only after every copy from it has run; very large copies go direct.
-constexpr size_t kArenaMaxCopy = (size_t)4 << 20;
+constexpr size_t kArenaMaxCopy = (size_t)4 << 20, kCopyPiece = (size_t)8 << 20;
 
 bool page_locked(const void *p)
 {
@@ -168,11 +169,34 @@ bool page_locked(const void *p)
     return a.type == cudaMemoryTypeHost;
 }
 
+// Small uploads are a kernel that reads the lane's page-locked arena over the
+// bus: copy-engine work from several streams is served in submission order, so
+// a cudaMemcpyAsync here could wait behind another lane's large frame copy.
+__global__ void k_upload(unsigned char *__restrict__ dst, const unsigned char *__restrict__ src, size_t bytes)
+{
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+        const size_t n16 = bytes >> 4;
+        for (size_t i = tid; i < n16; i += stride) ((uint4 *)dst)[i] = ((const uint4 *)src)[i];
+        for (size_t i = (n16 << 4) + tid; i < bytes; i += stride) dst[i] = src[i];
+    } else {
+        for (size_t i = tid; i < bytes; i += stride) dst[i] = src[i];
+    }
+}
+
 vgicp_status h2d(vgicp_ctx *ctx, void *dst, const void *src, size_t bytes)
 {
     if (bytes == 0) return VGICP_OK;
-    if (bytes > kArenaMaxCopy || (bytes >= 65536 && page_locked(src))) {
-        // large copies: the driver stages pageable memory itself; page-locked memory is copied directly
+    if (bytes >= 65536 && page_locked(src)) {
+        // page-locked memory is copied directly, in pieces: another lane's small
+        // copies share the copy engine and then wait for one piece, not the whole
+        for (size_t o = 0; o < bytes; o += kCopyPiece)
+            CU(cudaMemcpyAsync((char *)dst + o, (const char *)src + o, std::min(kCopyPiece, bytes - o),
+                               cudaMemcpyHostToDevice, LN.stream));
+        return VGICP_OK;
+    }
+    if (bytes > kArenaMaxCopy) {
+        // large pageable copies: the driver stages them itself
         CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, LN.stream));
         return VGICP_OK;
     }
@@ -189,14 +213,18 @@ vgicp_status h2d(vgicp_ctx *ctx, void *dst, const void *src, size_t bytes)
             A->cap = 0;
             const size_t cap = std::max<size_t>(std::max<size_t>(bytes * 2, (size_t)4 << 20), A->cap * 2);
             CU(cudaMallocHost((void **)&A->p, cap));
+            CU(cudaHostGetDevicePointer((void **)&A->dp, A->p, 0));
             A->cap = cap;
         }
         if (!A->ev) CU(cudaEventCreateWithFlags(&A->ev, cudaEventDisableTiming));
     }
-    char *stage = A->p + A->off;
+    const size_t at = A->off;
     A->off = (A->off + bytes + 255) & ~(size_t)255;
-    std::memcpy(stage, src, bytes);
-    CU(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, LN.stream));
+    std::memcpy(A->p + at, src, bytes);
+    const int grid = (int)std::min<size_t>((bytes + 4095) / 4096, (size_t)ctx->num_sms * 2);
+    k_upload<<<grid, 256, 0, LN.stream>>>((unsigned char *)dst, (const unsigned char *)(A->dp + at), bytes);
+    ctx->launches += 1;
+    CHECK_LAUNCH();
     CU(cudaEventRecord(A->ev, LN.stream));
     A->pending = true;
     return VGICP_OK;
@@ -243,6 +271,8 @@ vgicp_status grow_tables(vgicp_ctx *ctx, size_t need)
         CU(cudaFreeAsync(ctx->d_maps, LN.stream));
         CU(cudaFreeAsync(ctx->d_frames, LN.stream));
     }
+    // the new tables are complete before any lane's later work can read them
+    CU(cudaStreamSynchronize(LN.stream));
     ctx->d_maps = nm;
     ctx->d_frames = nf;
     ctx->tab_cap = cap;
@@ -733,8 +763,6 @@ vgicp_status vgicp_set_lane(vgicp_ctx *ctx, int32_t lane, void *cuda_stream)
 {
     if (!ctx) return VGICP_ERR_INVALID_ARG;
     if (lane < 0 || lane >= kMaxLanes) return fail(ctx, VGICP_ERR_INVALID_ARG, "lane must be in [0, %d)", kMaxLanes);
-    // work already enqueued on other lanes must be done with the shared tables
-    // before this lane can grow them; tables are grown only on lane switches
     ctx->lane = lane;
     if (cuda_stream) {
         LN.stream = (cudaStream_t)cuda_stream;
