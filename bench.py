@@ -481,8 +481,9 @@ def cpu_baseline(pts, poses, tgt, src, cpu_seconds=20.0):
     jobs = _oracle_sample(pts, poses, tgt, src, n)
     v, dt = _time_oracle(jobs, cores)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(jobs)} of the workload's factors (about {cpu_seconds:.0f} s of one-core work; FP64 "
-                      f"oracle linearisation, one factor per thread on {cores} threads, {dt:.2f} s wall)",
+            "sample": f"{len(jobs)} of the workload's factors (sized by a one-core probe of 8 factors to about "
+                      f"{cpu_seconds:.0f} s of one-core work; FP64 oracle linearisation, one factor per thread on "
+                      f"{cores} threads, {dt:.2f} s wall)",
             "one_core_value": v1}
 
 

@@ -155,3 +155,36 @@ def test_server_errors(data):
         assert r1.status == 4 and r1.count == 0                  # VGICP_ERR_EMPTY (Eq. 8 undefined)
         assert r2.status == vg.VGICP_OK and r2.count == 0 and r2.cost == 0.0
         assert not np.any(np.array(r2.H))
+
+
+def test_server_wait_timeout_keeps_the_ticket(data):
+    """A wait that runs out returns VGICP_ERR_TIMEOUT and leaves the ticket valid: a
+    later wait gets the same result as a request that was never timed out."""
+    maps, frames, _ = data
+    p, c, r = maps[0]
+    with vg.Server() as srv:
+        srv.put_map(0, p, c, r)
+        srv.put_frame(0, *frames[0])
+        first = srv.wait(srv.submit(vg.VGICP_REQ_LINEARIZE, 0, 0, IDENT), 60.0)
+        timed_out = 0
+        for _ in range(8):
+            tk = srv.submit(vg.VGICP_REQ_LINEARIZE, 0, 0, IDENT)
+            try:
+                srv.wait(tk, 0.0)                                 # no time to run: runs out
+            except vg.VgicpError as e:
+                assert e.status == 6                              # VGICP_ERR_TIMEOUT
+                timed_out += 1
+                res = srv.wait(tk, 60.0)
+                assert res.status == vg.VGICP_OK and res.cost == first.cost
+                assert np.array_equal(np.array(res.H), np.array(first.H))
+        assert timed_out > 0
+        tks = [srv.submit(vg.VGICP_REQ_LINEARIZE, 0, 0, IDENT) for _ in range(4)]
+        try:
+            srv.wait_batch(tks, 0.0)
+        except vg.VgicpError as e:
+            assert e.status == 6
+        for tk in tks:                                            # retired or still valid
+            try:
+                assert srv.wait(tk, 60.0).cost == first.cost
+            except vg.VgicpError as e:
+                assert e.status == 3                              # VGICP_ERR_NOT_FOUND: retired by the batch
