@@ -64,6 +64,9 @@ def parse():
                    help="Levenberg-Marquardt over the paper-scale graph (500 frames): iterations, cost and pose "
                         "errors against the ground truth")
     p.add_argument("--lm-iterations", type=int, default=10)
+    p.add_argument("--single", action="store_true",
+                   help="the single-factor workload: one 2,000-point factor, latency per call (us/factor) for the "
+                        "plain float64 and batched float32 paths, overlap, and the oracle on one core")
     p.add_argument("--serving", action="store_true",
                    help="the serving-loop workload: Poisson request streams through vgicp_server")
     p.add_argument("--serving-maps", type=int, default=2000)
@@ -800,10 +803,74 @@ def run_serving(a):
     print(json.dumps(res), flush=True)
 
 
+def run_single(a):
+    """One factor of two 2,000-point clouds (ground plus three walls), 1 m voxels:
+    launch-latency bound, so reported as microseconds per call from host inputs
+    already registered on the device (handles), host outputs, synchronised."""
+    import torch
+
+    import oracle
+    import paper_2109_07073_b300 as vg
+    oracle.build()
+    w = dg.single_factor_workload()
+    cb, ca = oracle.covariances(w.points_target), oracle.covariances(w.points_source)
+    T = oracle.relative_pose(w.T_target, w.T_source)
+    poses = np.stack([w.T_target, w.T_source])
+    n_src = w.points_source.shape[0]
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    res = {}
+    with vg.Context() as ctx:
+        hm = ctx.build_voxelmap(w.points_target, cb, w.resolution)
+        hf = ctx.add_frame(w.points_source, ca)
+        f = vg.make_factors([hm], [hf], [0], [1])
+        out = (np.zeros((1, 12, 12)), np.zeros((1, 12)), np.zeros(1), np.zeros(1, np.int64))
+
+        def per_call_us(fn, reps):
+            for _ in range(max(3, a.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) * 1e6 / reps
+
+        reps = max(200, 50 * a.steps)
+        for name, prec in (("plain_f64", vg.VGICP_PREC_F64), ("batched_f32", vg.VGICP_PREC_F32)):
+            ctx.set_options(precision=prec)
+            us = per_call_us(lambda: ctx.linearize(f, poses, out=out), reps)
+            res[name] = {"us_per_factor": us, "factors_per_s": 1e6 / us,
+                         "point_correspondences_per_s": n_src * 1e6 / us}
+        ctx.set_options(precision=vg.VGICP_PREC_F32)
+        res["overlap_us"] = per_call_us(lambda: ctx.overlap(hf, hm, T), reps)
+        launches = ctx.kernel_launches()
+    vm = oracle.voxelmap(w.points_target, cb, w.resolution)
+    oracle.linearize(vm, w.points_source, ca, T)
+    t0 = time.perf_counter()
+    n_or = 20
+    for _ in range(n_or):
+        oracle.linearize(vm, w.points_source, ca, T)
+    us_or = (time.perf_counter() - t0) * 1e6 / n_or
+    main_v = res["batched_f32"]
+    line = {"metric": METRIC + " (single factor)", "value": main_v["point_correspondences_per_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": reps, "warmup": max(3, a.warmup), "ms_per_step": main_v["us_per_factor"] / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ground plane and walls, 2,000 points per cloud)",
+            "config": {"workload": "single factor: 2,000 + 2,000 points, 1.0 m voxels, host outputs per call"},
+            "plain_f64": res["plain_f64"], "batched_f32": res["batched_f32"], "overlap_us": res["overlap_us"],
+            "gpu_launches": launches,
+            "cpu_baseline": {"value": n_src * 1e6 / us_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the same factor, {n_or} calls on one core ({us_or:.0f} us each)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.single:
+        run_single(a)
     elif a.serving:
         run_serving(a)
     elif a.uneven:

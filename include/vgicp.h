@@ -100,7 +100,10 @@ typedef struct {
 typedef struct {
     int32_t precision;        /* VGICP_PREC_F32 (default), VGICP_PREC_F64 or VGICP_PREC_F32_COMP */
     int32_t chunk_points;     /* points per work item of the batched path (one warp per item; multiple of 32;
-                                 0 = default 2048) */
+                                 0 = default 2048); a factor of n points is cut into items of
+                                 min(chunk_points, max(64, ceil(n / 8) rounded up to 32)) points, so that a
+                                 small factor spreads over several warps (a function of n only: a factor's
+                                 result is the same alone and in any batch) */
     int32_t linearize_variant;/* batched kernel variant: 0 default, 1 to 5 (same results, different
                                  latency hiding), 6 (maps of at most 4,096 voxels probed from a copy in
                                  shared memory, one CTA per SM taking runs of items with one target);
@@ -263,7 +266,7 @@ vgicp_status vgicp_plan_destroy(vgicp_ctx *ctx, vgicp_plan *plan);
 /* Size limits of vgicp_linearize_noalloc() (its fixed scratch is sized for them). */
 #define VGICP_NOALLOC_MAX_FACTORS 1024
 #define VGICP_NOALLOC_MAX_POSES 2048
-#define VGICP_NOALLOC_MAX_ITEMS 16384   /* sum over factors of ceil(source points / chunk_points) */
+#define VGICP_NOALLOC_MAX_ITEMS 16384   /* sum over factors of their work items (see chunk_points) */
 
 /* vgicp_linearize() without any allocation.  The paper has no counterpart:
  * this serves callers that must not allocate device memory when they

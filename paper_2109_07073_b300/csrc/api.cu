@@ -71,6 +71,8 @@ struct Lane {
         bool pending = false;
     } arena[2];
     int arena_cur = 0;
+    char *d2h_stage = nullptr;   // page-locked landing buffer for small results
+    size_t d2h_cap = 0;
 };
 
 }  // namespace
@@ -227,6 +229,45 @@ vgicp_status h2d(vgicp_ctx *ctx, void *dst, const void *src, size_t bytes)
     CHECK_LAUNCH();
     CU(cudaEventRecord(A->ev, LN.stream));
     A->pending = true;
+    return VGICP_OK;
+}
+
+// A contiguous device block [src, src + sum of bytes) read back into k host
+// destinations in order (a null destination skips its piece), then the lane is
+// synchronised.  Small results land in a page-locked buffer of the lane with
+// one copy and are spread by the host: a copy into pageable memory costs a
+// driver round trip each.
+constexpr size_t kD2HStageMax = (size_t)256 << 10;
+
+vgicp_status d2h_pieces(vgicp_ctx *ctx, const void *src, void *const *dst, const size_t *bytes, int k)
+{
+    size_t total = 0;
+    for (int i = 0; i < k; ++i) total += bytes[i];
+    if (total == 0) return VGICP_OK;
+    if (total <= kD2HStageMax) {
+        if (LN.d2h_cap < total) {
+            if (LN.d2h_stage) CU(cudaFreeHost(LN.d2h_stage));
+            LN.d2h_stage = nullptr;
+            LN.d2h_cap = 0;
+            CU(cudaMallocHost((void **)&LN.d2h_stage, kD2HStageMax));
+            LN.d2h_cap = kD2HStageMax;
+        }
+        CU(cudaMemcpyAsync(LN.d2h_stage, src, total, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaStreamSynchronize(LN.stream));
+        size_t o = 0;
+        for (int i = 0; i < k; ++i) {
+            if (dst[i] && bytes[i]) std::memcpy(dst[i], LN.d2h_stage + o, bytes[i]);
+            o += bytes[i];
+        }
+        return VGICP_OK;
+    }
+    size_t o = 0;
+    for (int i = 0; i < k; ++i) {
+        if (dst[i] && bytes[i])
+            CU(cudaMemcpyAsync(dst[i], (const char *)src + o, bytes[i], cudaMemcpyDeviceToHost, LN.stream));
+        o += bytes[i];
+    }
+    CU(cudaStreamSynchronize(LN.stream));
     return VGICP_OK;
 }
 
@@ -608,12 +649,13 @@ void build_items(const std::vector<int32_t> &idx, const std::vector<int64_t> &fr
     range.assign((size_t)n_f * 2, 0);
     for (int32_t i : order) {
         const int64_t n = frame_n[i];
+        const int c = item_chunk(n, chunk);
         range[2 * i] = (int32_t)items.size();
-        for (int64_t s = 0; s < n; s += chunk) {
+        for (int64_t s = 0; s < n; s += c) {
             WorkItem w;
             w.unit = i;
             w.start = s;
-            w.count = (int32_t)std::min<int64_t>(chunk, n - s);
+            w.count = (int32_t)std::min<int64_t>(c, n - s);
             items.push_back(w);
         }
         range[2 * i + 1] = (int32_t)items.size();
@@ -753,6 +795,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
             if (A.p) cudaFreeHost(A.p);
             if (A.ev) cudaEventDestroy(A.ev);
         }
+        if (LN.d2h_stage) cudaFreeHost(LN.d2h_stage);
         if (LN.own_stream) cudaStreamDestroy(LN.own_stream);
     }
     delete ctx;
@@ -1057,11 +1100,9 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         CHECK_LAUNCH();
     }
     if (out_kind == VGICP_MEM_HOST) {
-        CU(cudaMemcpyAsync(H, dH, (size_t)n_f * 144 * 8, cudaMemcpyDeviceToHost, LN.stream));
-        CU(cudaMemcpyAsync(b, db, (size_t)n_f * 12 * 8, cudaMemcpyDeviceToHost, LN.stream));
-        CU(cudaMemcpyAsync(cost, dc, (size_t)n_f * 8, cudaMemcpyDeviceToHost, LN.stream));
-        if (inliers) CU(cudaMemcpyAsync(inliers, di, (size_t)n_f * 8, cudaMemcpyDeviceToHost, LN.stream));
-        CU(cudaStreamSynchronize(LN.stream));
+        void *const dst[4] = {H, b, cost, inliers};
+        const size_t nb[4] = {(size_t)n_f * 144 * 8, (size_t)n_f * 12 * 8, (size_t)n_f * 8, (size_t)n_f * 8};
+        TRY(d2h_pieces(ctx, dH, dst, nb, 4));
     }
     return VGICP_OK;
 }
@@ -1346,9 +1387,9 @@ vgicp_status vgicp_evaluate(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t
     ctx->launches += 2 + (P.n_items > 0);
     CHECK_LAUNCH();
     if (out_kind == VGICP_MEM_HOST) {
-        CU(cudaMemcpyAsync(cost, dc, (size_t)n_f * 8, cudaMemcpyDeviceToHost, LN.stream));
-        if (inliers) CU(cudaMemcpyAsync(inliers, di, (size_t)n_f * 8, cudaMemcpyDeviceToHost, LN.stream));
-        CU(cudaStreamSynchronize(LN.stream));
+        void *const dst[2] = {cost, inliers};
+        const size_t nb[2] = {(size_t)n_f * 8, (size_t)n_f * 8};
+        TRY(d2h_pieces(ctx, dc, dst, nb, 2));
     }
     return VGICP_OK;
 }
@@ -1441,8 +1482,11 @@ vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t tar
     ctx->launches += 1;
     CHECK_LAUNCH();
     unsigned long long c = 0;
-    CU(cudaMemcpyAsync(&c, LN.ws_counts.p, 8, cudaMemcpyDeviceToHost, LN.stream));
-    CU(cudaStreamSynchronize(LN.stream));
+    {
+        void *const dst[1] = {&c};
+        const size_t nb[1] = {8};
+        TRY(d2h_pieces(ctx, LN.ws_counts.p, dst, nb, 1));
+    }
     if (count) *count = (int64_t)c;
     *fraction = (double)c / (double)n;
     return VGICP_OK;
@@ -1497,8 +1541,9 @@ vgicp_status vgicp_overlap_pairs(vgicp_ctx *ctx, const vgicp_frame_t *sources, c
     ctx->launches += 1 + !items.empty();
     CHECK_LAUNCH();
     if (out_kind == VGICP_MEM_HOST) {
-        CU(cudaMemcpyAsync(counts, dc, (size_t)n * 8, cudaMemcpyDeviceToHost, LN.stream));
-        CU(cudaStreamSynchronize(LN.stream));
+        void *const dst[1] = {counts};
+        const size_t nb[1] = {(size_t)n * 8};
+        TRY(d2h_pieces(ctx, dc, dst, nb, 1));
     }
     return VGICP_OK;
 }
@@ -1560,8 +1605,9 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
     ctx->launches += 3;
     CHECK_LAUNCH();
     if (out_kind == VGICP_MEM_HOST) {
-        CU(cudaMemcpyAsync(counts, dcounts, (size_t)n_pairs * 8, cudaMemcpyDeviceToHost, LN.stream));
-        CU(cudaStreamSynchronize(LN.stream));
+        void *const dst[1] = {counts};
+        const size_t nb[1] = {(size_t)n_pairs * 8};
+        TRY(d2h_pieces(ctx, dcounts, dst, nb, 1));
     }
     return VGICP_OK;
 }

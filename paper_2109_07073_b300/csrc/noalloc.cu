@@ -78,6 +78,7 @@ __global__ void k_noalloc_plan(const vgicp_factor *__restrict__ f, int n_f, cons
     const int i = threadIdx.x;
     int32_t nchunks = 0;
     int64_t n = 0;
+    int c = chunk;
     if (i < n_f) {
         const int32_t mi = (int32_t)(f[i].target & 0xffffffff), fi = (int32_t)(f[i].source & 0xffffffff);
         idx[4 * i + 0] = mi;
@@ -85,7 +86,8 @@ __global__ void k_noalloc_plan(const vgicp_factor *__restrict__ f, int n_f, cons
         idx[4 * i + 2] = f[i].target_pose;
         idx[4 * i + 3] = f[i].source_pose;
         n = frames[fi].n;
-        nchunks = (int32_t)((n + chunk - 1) / chunk);
+        c = item_chunk(n, chunk);
+        nchunks = (int32_t)((n + c - 1) / c);
     }
     s_scan[i] = nchunks;
     __syncthreads();
@@ -99,12 +101,12 @@ __global__ void k_noalloc_plan(const vgicp_factor *__restrict__ f, int n_f, cons
         const int32_t begin = s_scan[i] - nchunks;
         item_range[2 * i] = begin;
         item_range[2 * i + 1] = begin + nchunks;
-        for (int32_t c = 0; c < nchunks; ++c) {
+        for (int32_t k = 0; k < nchunks; ++k) {
             WorkItem w;
             w.unit = i;
-            w.start = (int64_t)c * chunk;
-            w.count = (int32_t)((n - w.start < chunk) ? (n - w.start) : chunk);
-            items[begin + c] = w;
+            w.start = (int64_t)k * c;
+            w.count = (int32_t)((n - w.start < c) ? (n - w.start) : c);
+            items[begin + k] = w;
         }
     }
 }
@@ -133,7 +135,8 @@ extern "C" vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_fact
         if (factors[i].target_pose < 0 || factors[i].target_pose >= n_poses || factors[i].source_pose < 0 ||
             factors[i].source_pose >= n_poses)
             return ctx_fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_noalloc: pose index out of range");
-        n_items += (n + v.chunk - 1) / v.chunk;
+        const int c = item_chunk(n, v.chunk);
+        n_items += (n + c - 1) / c;
     }
     if (n_items > kMaxItems)
         return ctx_fail(ctx, VGICP_ERR_INVALID_ARG,

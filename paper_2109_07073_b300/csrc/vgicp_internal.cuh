@@ -81,6 +81,20 @@ struct FrameDesc {
 
 constexpr int kMaxCullChunks = 32;
 
+// Points per work item of a factor of n source points: the configured chunk,
+// except that a small factor is cut into at least kMinFactorItems items (a
+// multiple of 32 points each, at least 64) so that it alone still keeps several
+// warps busy.  It depends on the factor's own size only, so a factor's items,
+// and its sums, are the same alone and in any batch.
+constexpr int kMinFactorItems = 8;
+__host__ __device__ inline int item_chunk(int64_t n, int chunk)
+{
+    int64_t c = (n + kMinFactorItems - 1) / kMinFactorItems;
+    c = (c + 31) & ~(int64_t)31;
+    if (c < 64) c = 64;
+    return (int)(c < chunk ? c : chunk);
+}
+
 // Frame statistics, over the points with finite coordinates.
 enum {
     kStatCmax = 0,   // max |covariance entry|
