@@ -39,7 +39,8 @@ using Clock = std::chrono::steady_clock;
 
 struct Resident {
     bool is_map = false;
-    std::vector<float> pts, covs;   // host copies (immutable once registered)
+    const float *pts = nullptr, *covs = nullptr;   // host copies (immutable once registered)
+    std::vector<float> own;         // their storage when no page-locked slab could be had
     int64_t n = 0;
     double r = 0.0;
     int64_t handle = -1;            // device handle while resident
@@ -93,6 +94,10 @@ struct vgicp_server {
     double host_launch_ms = 0.0, host_finish_ms = 0.0, device_ms = 0.0, host_admit_ms = 0.0, host_enqueue_ms = 0.0;
     int64_t submitted = 0, completed = 0, batches = 0, admissions = 0, evictions = 0, batch_requests = 0;
     std::string err;
+    // page-locked host copies of the registered objects, bump-allocated in slabs
+    // that live as long as the server (re-admission copies them directly)
+    std::vector<char *> slabs;
+    size_t slab_cap = 0, slab_off = 0;
 };
 
 namespace {
@@ -144,19 +149,22 @@ vgicp_status admit(vgicp_server *s, Resident &o)
         if (o.is_map) vgicp_memory_estimate(s->ctx, o.n, 0, &fb);
         vgicp_memory_in_use(s->ctx, &used);
         while (used + need + fb > s->opt.hbm_budget_bytes && evict_one(s)) vgicp_memory_in_use(s->ctx, &used);
+        // nothing left to evict (the rest is pinned by batches in flight): defer
+        // without staging the object's data for an allocation that would fail
+        if (used + need + fb > s->opt.hbm_budget_bytes) return VGICP_ERR_BUDGET;
     }
     for (;;) {
         vgicp_status st;
         int64_t h = -1;
         if (o.is_map) {
             vgicp_frame_t fr;
-            st = vgicp_add_frame(s->ctx, o.pts.data(), o.covs.data(), o.n, VGICP_MEM_HOST, &fr);
+            st = vgicp_add_frame(s->ctx, o.pts, o.covs, o.n, VGICP_MEM_HOST, &fr);
             if (st == VGICP_OK) {
                 st = vgicp_build_voxelmaps(s->ctx, &fr, 1, o.r, &h);
                 vgicp_release(s->ctx, fr);
             }
         } else {
-            st = vgicp_add_frame(s->ctx, o.pts.data(), o.covs.data(), o.n, VGICP_MEM_HOST, &h);
+            st = vgicp_add_frame(s->ctx, o.pts, o.covs, o.n, VGICP_MEM_HOST, &h);
         }
         if (st == VGICP_OK) {
             o.handle = h;
@@ -412,20 +420,58 @@ void scheduler(vgicp_server *s)
     }
 }
 
+// Room for `bytes` in the page-locked slabs (mutex held), or null when no
+// page-locked memory can be had.
+char *slab_alloc(vgicp_server *s, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (s->slabs.empty() || s->slab_off + bytes > s->slab_cap) {
+        const size_t cap = std::max(bytes, (size_t)256 << 20);
+        char *p = nullptr;
+        if (cudaMallocHost((void **)&p, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        s->slabs.push_back(p);
+        s->slab_cap = cap;
+        s->slab_off = 0;
+    }
+    char *r = s->slabs.back() + s->slab_off;
+    s->slab_off += bytes;
+    return r;
+}
+
 vgicp_status put(vgicp_server *s, int64_t key, bool is_map, const float *pts, const float *covs, int64_t n, double r)
 {
     if (!s) return VGICP_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && (!pts || !covs)) || key < 0 || key >= ((int64_t)1 << 62)) return VGICP_ERR_INVALID_ARG;
     if (is_map && !(r > 0.0 && r < 1e30)) return VGICP_ERR_INVALID_ARG;
+    const int64_t t = tag(key, is_map);
     Resident o;
     o.is_map = is_map;
-    o.key = tag(key, is_map);
-    o.pts.assign(pts, pts + 3 * n);
-    o.covs.assign(covs, covs + 6 * n);
+    o.key = t;
     o.n = n;
     o.r = r;
+    float *h = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->objs.count(t)) {
+            s->err = "key already registered";
+            return VGICP_ERR_INVALID_ARG;
+        }
+        if (n > 0) h = (float *)slab_alloc(s, (size_t)n * 36);
+    }
+    if (n > 0) {                                        // the copy runs without the lock
+        if (!h) {
+            o.own.resize((size_t)n * 9);
+            h = o.own.data();
+        }
+        std::memcpy(h, pts, (size_t)n * 12);
+        std::memcpy(h + 3 * n, covs, (size_t)n * 24);
+        o.pts = h;
+        o.covs = h + 3 * n;
+    }
     std::lock_guard<std::mutex> lk(s->mu);
-    const int64_t t = tag(key, is_map);
     if (s->objs.count(t)) {
         s->err = "key already registered";
         return VGICP_ERR_INVALID_ARG;
@@ -497,6 +543,7 @@ vgicp_status vgicp_server_destroy(vgicp_server *s)
         cudaEventDestroy(L.ev0);
         cudaEventDestroy(L.ev1);
     }
+    for (char *p : s->slabs) cudaFreeHost(p);
     delete s;
     return VGICP_OK;
 }
