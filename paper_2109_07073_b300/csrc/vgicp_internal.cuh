@@ -41,6 +41,8 @@ struct __align__(16) VoxelRec {
 // and the voxels' records packed densely, kImgRecFloats floats each: mean
 // relative to the voxel corner (3), covariance (6), count (uint32 bits).  One
 // CTA copies it into shared memory and probes without global-memory gathers.
+// It is made on demand: when a linearisation that reads it first runs, and
+// again after the map is rebuilt.
 // Header words: 0 valid, 1 lg, 2 nv, 3 box extents x | y << 16, 4-6 box
 // minimum, 7 box extent z.
 constexpr int kImgMaxVoxels = 4096;
