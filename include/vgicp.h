@@ -31,7 +31,12 @@
  * Memory: mem_kind / out_kind say where a caller pointer lives.  HOST
  * pointers may be pageable; DEVICE pointers are read on the context stream and
  * copied into library-owned device memory before the call returns control of
- * the stream.  Handles own their device memory until vgicp_release() or
+ * the stream.  HOST inputs in pageable memory (and any below 64 KB) are staged
+ * before the call returns, so the caller may reuse them at once; HOST inputs in
+ * page-locked memory of 64 KB or more are copied by the device in stream order,
+ * like cudaMemcpyAsync: leave them unchanged until the lane has been
+ * synchronised (vgicp_synchronize, or any later call with HOST outputs on the
+ * same lane).  Handles own their device memory until vgicp_release() or
  * vgicp_destroy().  Output buffers are always caller-owned.
  *
  * Synchronisation: every call is ordered on the context's CUDA stream.  Calls
