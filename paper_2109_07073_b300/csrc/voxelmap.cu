@@ -221,29 +221,25 @@ __global__ void k_chunk_boxes(const float4 *__restrict__ pa, int64_t n, int shif
     }
 }
 
-__device__ __forceinline__ int find_unit(const int64_t *prefix, int n_units, int64_t g)
-{
-    int lo = 0, hi = n_units - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
+// Empty tables, one block per map: keys, compact presence entries and slot ->
+// voxel ids in 16-byte stores (capacities are powers of two >= 16, so every
+// array holds a whole number of vectors), the voxel count and the box.
 __global__ void k_build_clear(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units, int n_units,
                               const int64_t *__restrict__ slot_prefix, int32_t *__restrict__ vid_of_slot)
 {
-    const int64_t total = slot_prefix[n_units];
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
-        const int u = find_unit(slot_prefix, n_units, g);
-        const int64_t s = g - slot_prefix[u];
-        const MapDesc &m = maps[units[u].map];
-        m.keys[s] = kEmptyKey;
-        m.ckeys[s] = kEmptyCompact;
-        vid_of_slot[g] = -1;
-        if (s == 0) {
-            *units[u].n_voxels = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const BuildUnit U = units[u];
+        const MapDesc &m = maps[U.map];
+        const int64_t base = slot_prefix[u], cap = slot_prefix[u + 1] - base;
+        uint4 *keys = (uint4 *)m.keys, *ck = (uint4 *)m.ckeys, *vos = (uint4 *)(vid_of_slot + base);
+        const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+        for (int64_t v = threadIdx.x; v < cap / 2; v += blockDim.x) keys[v] = ones;   // kEmptyKey = all ones
+        for (int64_t v = threadIdx.x; v < cap / 4; v += blockDim.x) {
+            ck[v] = ones;                                                       // kEmptyCompact = all ones
+            vos[v] = ones;                                                      // -1
+        }
+        if (threadIdx.x == 0) {
+            *U.n_voxels = 0;
             m.kbox[0] = m.kbox[1] = m.kbox[2] = INT32_MAX;
             m.kbox[3] = m.kbox[4] = m.kbox[5] = INT32_MIN;
         }
@@ -606,7 +602,7 @@ void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const B
                            int grid, cudaStream_t st)
 {
     if (n_units <= 0) return;
-    k_build_clear<<<148 * 8, 256, 0, st>>>(maps, units, n_units, slot_prefix, scr.vid_of_slot);
+    k_build_clear<<<std::min(n_units, 148 * 8), 512, 0, st>>>(maps, units, n_units, slot_prefix, scr.vid_of_slot);
     if (n_items > 0) {
         k_build_insert<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
         k_build_accumulate<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
