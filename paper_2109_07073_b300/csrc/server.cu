@@ -420,25 +420,31 @@ void scheduler(vgicp_server *s)
     }
 }
 
-// Room for `bytes` in the page-locked slabs (mutex held), or null when no
-// page-locked memory can be had.
+// Room for `bytes` in the page-locked slabs, or null when no page-locked memory
+// can be had.  A new slab is pinned without the lock held (pinning 256 MB takes
+// tens of milliseconds, which the scheduler thread must not wait for).
 char *slab_alloc(vgicp_server *s, size_t bytes)
 {
     bytes = (bytes + 255) & ~(size_t)255;
-    if (s->slabs.empty() || s->slab_off + bytes > s->slab_cap) {
-        const size_t cap = std::max(bytes, (size_t)256 << 20);
-        char *p = nullptr;
-        if (cudaMallocHost((void **)&p, cap) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->slabs.empty() && s->slab_off + bytes <= s->slab_cap) {
+            char *r = s->slabs.back() + s->slab_off;
+            s->slab_off += bytes;
+            return r;
         }
-        s->slabs.push_back(p);
-        s->slab_cap = cap;
-        s->slab_off = 0;
     }
-    char *r = s->slabs.back() + s->slab_off;
-    s->slab_off += bytes;
-    return r;
+    const size_t cap = std::max(bytes, (size_t)256 << 20);
+    char *p = nullptr;
+    if (cudaMallocHost((void **)&p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->slabs.push_back(p);
+    s->slab_cap = cap;
+    s->slab_off = bytes;
+    return p;
 }
 
 vgicp_status put(vgicp_server *s, int64_t key, bool is_map, const float *pts, const float *covs, int64_t n, double r)
@@ -452,15 +458,14 @@ vgicp_status put(vgicp_server *s, int64_t key, bool is_map, const float *pts, co
     o.key = t;
     o.n = n;
     o.r = r;
-    float *h = nullptr;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->objs.count(t)) {
             s->err = "key already registered";
             return VGICP_ERR_INVALID_ARG;
         }
-        if (n > 0) h = (float *)slab_alloc(s, (size_t)n * 36);
     }
+    float *h = n > 0 ? (float *)slab_alloc(s, (size_t)n * 36) : nullptr;
     if (n > 0) {                                        // the copy runs without the lock
         if (!h) {
             o.own.resize((size_t)n * 9);
