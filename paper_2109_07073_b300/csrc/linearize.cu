@@ -106,14 +106,9 @@ __device__ uint32_t chunk_mask(const PoseParam &p, const MapDesc &m, const Frame
 // tests, from p.T, the target map and the source frame's statistics.
 __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f, int cull)
 {
-    double pmax[3], mn[3], mx[3];
+    double pmax[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        pmax[j] = (double)f.stats[kStatPmax + j];
-        mn[j] = (double)from_ordered_bits(__float_as_uint(f.stats[kStatMin + j]));
-        mx[j] = (double)from_ordered_bits(__float_as_uint(f.stats[kStatMax + j]));
-    }
-    double tmax = 0.0, ext = 0.0;
+    for (int j = 0; j < 3; ++j) pmax[j] = (double)f.stats[kStatPmax + j];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const double t = p.T[4 * i + 3];
@@ -131,8 +126,6 @@ __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f,
         const double fm = 0x1p-40 * X + 0x1p-100;
         p.ffm[i] = __double2float_ru(fm);
         p.ffup[i] = __double2float_rd((double)m.r_h - fm - 0x1p-22 * m.r);
-        tmax = fmax(tmax, fabs(t));
-        ext = fmax(ext, fmax(fabs(mn[i]), fabs(mx[i])));
     }
     p.cull = 0;
     p.cmask = f.nchunks >= 32 ? 0xffffffffu : ((1u << f.nchunks) - 1u);
@@ -143,34 +136,23 @@ __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f,
         p.koff[i] = (off > INT32_MAX / 2 || off < INT32_MIN / 2) ? INT32_MAX / 2 : (int32_t)off;
     }
     if (!cull) return;
-    // Every transformed point lies in the box of the transformed corners of the
-    // source's bounding box; if that box (grown by a margin far above the
-    // float64 rounding of any point) misses the target's voxel box on one axis,
-    // no point of the pair can find a voxel.
+    // A source without a finite point or a map without a voxel: nothing can hit.
+    // Otherwise the float32 chunk boxes decide (every chunk dead: the pair is
+    // culled); their bound is proven like the floors', and the pose test needs
+    // no float64 (B300's float64 rate is a small fraction of float32's).
     const int *kb = m.kbox;
-    if (!(mn[0] <= mx[0] && mn[1] <= mx[1] && mn[2] <= mx[2]) || kb[0] > kb[3]) {
+    bool finite = true;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        finite = finite && from_ordered_bits(__float_as_uint(f.stats[kStatMin + j])) <=
+                               from_ordered_bits(__float_as_uint(f.stats[kStatMax + j]));
+    if (!finite || kb[0] > kb[3]) {
         p.cull = 1;
+        p.cmask = 0u;
         return;
     }
-    const double mu = 1e-6 * (1.0 + tmax + 3.0 * ext);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        double lo = 0.0, hi = 0.0;
-        for (int c = 0; c < 8; ++c) {
-            const double x = p.T[4 * i] * ((c & 1) ? mx[0] : mn[0]) + p.T[4 * i + 1] * ((c & 2) ? mx[1] : mn[1]) +
-                             p.T[4 * i + 2] * ((c & 4) ? mx[2] : mn[2]) + p.T[4 * i + 3];
-            lo = (c == 0) ? x : fmin(lo, x);
-            hi = (c == 0) ? x : fmax(hi, x);
-        }
-        const double blo = (double)kb[i] * m.r, bhi = ((double)kb[3 + i] + 1.0) * m.r;
-        if (hi + mu < blo || lo - mu > bhi) p.cull = 1;
-    }
-    if (!p.cull) {
-        p.cmask = chunk_mask(p, m, f);
-        if (p.cmask == 0u) p.cull = 1;
-    } else {
-        p.cmask = 0u;
-    }
+    p.cmask = chunk_mask(p, m, f);
+    if (p.cmask == 0u) p.cull = 1;
 }
 
 __global__ void k_prepare_factors(const int32_t *__restrict__ idx, int n_f, const double *__restrict__ poses,
