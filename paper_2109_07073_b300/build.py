@@ -33,7 +33,8 @@ def nvcc() -> str:
 
 
 def _headers_mtime() -> float:
-    hs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    hs = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+          glob.glob(os.path.join(INCLUDE, "*.h")))
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
@@ -51,6 +52,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)
+    # host-only C++ (no device code): the system compiler, same language level
+    for s in sorted(glob.glob(os.path.join(CSRC, "*.cpp"))):
+        o = os.path.join(BUILD, os.path.basename(s)[:-4] + ".cpp.o")
+        objs.append(o)
+        if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
+            jobs.append([os.environ.get("CXX", "g++"), "-O3", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
+                         "-I", CSRC, "-c", s, "-o", o])
 
     def run(cmd):
         p = subprocess.run(cmd, capture_output=True, text=True)
@@ -64,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if p.returncode:
                 failed.append(cmd[-3])
     if failed:
-        raise RuntimeError(f"nvcc failed for {failed}")
+        raise RuntimeError(f"compiler failed for {failed}")
     if force or jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]

@@ -18,6 +18,7 @@
 #include <deque>
 #include <vector>
 
+#include "envelope_cholesky.h"
 #include "vgicp.h"
 
 namespace {
@@ -85,36 +86,6 @@ struct Skyline {
     double &at(int64_t r, int64_t c) { return a[off[r] + (c - first[r])]; }
     bool inside(int64_t r, int64_t c) const { return c >= first[r] && c <= r; }
 };
-
-// In-place L L^T factorisation of the envelope; false if not positive definite.
-bool cholesky(Skyline &S, int64_t n)
-{
-    for (int64_t i = 0; i < n; ++i) {
-        for (int64_t j = S.first[i]; j <= i; ++j) {
-            const int64_t k0 = std::max(S.first[i], S.first[j]);
-            const double *li = &S.a[S.off[i] + (k0 - S.first[i])];
-            const double *lj = &S.a[S.off[j] + (k0 - S.first[j])];
-            const int64_t len = j - k0;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four partial sums: independent FMA chains
-            int64_t k = 0;
-            for (; k + 4 <= len; k += 4) {
-                s0 += li[k] * lj[k];
-                s1 += li[k + 1] * lj[k + 1];
-                s2 += li[k + 2] * lj[k + 2];
-                s3 += li[k + 3] * lj[k + 3];
-            }
-            for (; k < len; ++k) s0 += li[k] * lj[k];
-            const double s = S.at(i, j) - ((s0 + s1) + (s2 + s3));
-            if (j < i) {
-                S.at(i, j) = s / S.at(j, j);
-            } else {
-                if (!(s > 0.0)) return false;
-                S.at(i, i) = std::sqrt(s);
-            }
-        }
-    }
-    return true;
-}
 
 // The global system's product H x from the factor blocks (x, y: 6 per pose).
 void global_matvec(const int32_t *pairs, const double *H, int64_t n_f, const double *x, double *y, int64_t n_poses)
@@ -392,12 +363,14 @@ vgicp_status vgicp_solve_step(const int32_t *pairs, const double *H, const doubl
             for (int r = 0; r < 6; ++r) rhs[6 * pi + r] -= bf[6 * bi + r];
             for (int bj = 0; bj < 2; ++bj) {
                 const int64_t pj = pose[bj] == anchor ? -1 : pos[pose[bj]];
-                if (pj < 0) continue;
-                for (int r = 0; r < 6; ++r)
-                    for (int c = 0; c < 6; ++c) {
-                        const int64_t R = 6 * pi + r, Cc = 6 * pj + c;
-                        if (Cc <= R) S.at(R, Cc) += Hf[12 * (6 * bi + r) + 6 * bj + c];
-                    }
+                if (pj < 0 || pj > pi) continue;   // lower blocks only (the other is its transpose)
+                for (int r = 0; r < 6; ++r) {
+                    const int64_t R = 6 * pi + r;
+                    double *row = S.a.data() + S.off[R] + (6 * pj - S.first[R]);
+                    const double *h = Hf + 12 * (6 * bi + r) + 6 * bj;
+                    const int cmax = pj == pi ? r + 1 : 6;
+                    for (int c = 0; c < cmax; ++c) row[c] += h[c];
+                }
             }
         }
     }
@@ -410,7 +383,7 @@ vgicp_status vgicp_solve_step(const int32_t *pairs, const double *H, const doubl
         double &d = S.at(r, r);
         d += lambda * std::max(d, floor_d) + floor_d;
     }
-    if (!cholesky(S, nv)) return VGICP_ERR_NUMERIC;
+    if (!vg::envelope_cholesky6(S.a.data(), S.first.data(), S.off.data(), nv)) return VGICP_ERR_NUMERIC;
     // L y = rhs, L' x = y
     std::vector<double> x(rhs);
     for (int64_t i = 0; i < nv; ++i) {
