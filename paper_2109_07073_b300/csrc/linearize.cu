@@ -170,6 +170,60 @@ __global__ void k_prepare_factors(const int32_t *__restrict__ idx, int n_f, cons
     out[f] = p;
 }
 
+// A float32 look at a pair before its float64 parameters: the relative pose in
+// float32 (the translation difference taken in float64 first), the source's
+// bounding box moved by it and grown by 2^-16 of the magnitudes involved (the
+// float32 errors of the pose and of the moved box stay below 2^-20 of them),
+// against the target's voxel box.  True when the grown box misses it on an
+// axis, so no point of the pair can find a voxel; most pairs of an overlap
+// matrix are such far pairs, and they skip the float64 work.
+__device__ bool quick_cull(const double *__restrict__ TB, const double *__restrict__ TA, const MapDesc &m,
+                           const FrameDesc &f)
+{
+    const int *kb = m.kbox;
+    if (kb[0] > kb[3]) return true;                     // a map without voxels
+    float mn[3], mx[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        mn[j] = from_ordered_bits(__float_as_uint(f.stats[kStatMin + j]));
+        mx[j] = from_ordered_bits(__float_as_uint(f.stats[kStatMax + j]));
+    }
+    if (!(mn[0] <= mx[0] && mn[1] <= mx[1] && mn[2] <= mx[2])) return true;   // no finite point
+    float d[3], dmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d[k] = (float)(TA[4 * k + 3] - TB[4 * k + 3]);
+        dmax = fmaxf(dmax, fabsf(d[k]));
+    }
+    const float rf = (float)m.r;
+    bool miss = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float R[3], t = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v = fmaf((float)TB[4 * k + i], (float)TA[4 * k + j], v);
+            R[j] = v;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) t = fmaf((float)TB[4 * k + i], d[k], t);
+        float c = t, h = 0.f, mag = fabsf(t);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float cc = 0.5f * (mn[j] + mx[j]), hh = 0.5f * (mx[j] - mn[j]);
+            c = fmaf(R[j], cc, c);
+            h = fmaf(fabsf(R[j]), hh, h);
+            mag = fmaf(fabsf(R[j]), fabsf(cc) + hh, mag);
+        }
+        const float mu = (mag + dmax + 1.f) * 0x1p-16f + 1e-6f * rf + 1e-30f;
+        const float blo = (float)((double)kb[i] * m.r), bhi = (float)(((double)kb[3 + i] + 1.0) * m.r);
+        miss = miss || (c + h + mu < blo) || (c - h - mu > bhi);
+    }
+    return miss;
+}
+
 __global__ void k_prepare_pairs(const double *__restrict__ ps, const double *__restrict__ pt,
                                 const int32_t *__restrict__ fidx, const int32_t *__restrict__ midx, int n_src,
                                 int n_tgt, const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
@@ -178,6 +232,14 @@ __global__ void k_prepare_pairs(const double *__restrict__ ps, const double *__r
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= (int64_t)n_src * n_tgt) return;
     const int s = (int)(g / n_tgt), t = (int)(g % n_tgt);
+    if (cull && quick_cull(pt + 12 * (int64_t)t, ps + 12 * (int64_t)s, maps[midx[t]], frames[fidx[s]])) {
+        PoseParam q = {};
+        q.map = midx[t];
+        q.frame = fidx[s];
+        q.cull = 1;
+        out[g] = q;
+        return;
+    }
     PoseParam p;
     rel_pose(pt + 12 * (int64_t)t, ps + 12 * (int64_t)s, p.T);
     split_pose(p.T, p);
