@@ -283,6 +283,18 @@ __global__ void k_build_insert(const MapDesc *__restrict__ maps, const FrameDesc
                 const uint64_t key = pack_key(k[0], k[1], k[2]);
                 uint32_t s = hash_slot(key, m.log2cap);
                 for (uint32_t t = 0; t <= m.mask; ++t) {
+                    // a plain read first: a slot's key never changes once set, so a
+                    // key read here is final and only an empty slot needs the CAS
+                    // (points of one voxel mostly find their key already there)
+                    const uint64_t seen = __ldcg(m.keys + s);
+                    if (seen == key) {
+                        slot = (int32_t)s;
+                        break;
+                    }
+                    if (seen != kEmptyKey) {
+                        s = (s + 1) & m.mask;
+                        continue;
+                    }
                     const unsigned long long old =
                         atomicCAS((unsigned long long *)(m.keys + s), (unsigned long long)kEmptyKey,
                                   (unsigned long long)key);
