@@ -357,8 +357,19 @@ __global__ void k_build_accumulate(const MapDesc *__restrict__ maps, const Frame
                     vid = scr.vid_of_slot[u.slot_base + slot];
                     const float4 a = __ldg(f.pa + i), b = __ldg(f.pb + i);
                     const float c22 = __ldg(f.pc + i);
+                    // the point's own voxel coordinate (the key it was inserted under):
+                    // recomputed where that is three float32 floors (power-of-two r),
+                    // else read from the slot
                     int kx, ky, kz;
-                    unpack_key(m.keys[slot], kx, ky, kz);
+                    if (m.pow2) {
+                        int k[3];
+                        own_key(m, a.x, a.y, a.z, k);
+                        kx = k[0];
+                        ky = k[1];
+                        kz = k[2];
+                    } else {
+                        unpack_key(m.keys[slot], kx, ky, kz);
+                    }
                     // offset from the voxel's lower corner k r, r = r_h + r_l
                     const float dx = __fmaf_rn(-(float)kx, m.r_l, __fmaf_rn(-(float)kx, m.r_h, a.x));
                     const float dy = __fmaf_rn(-(float)ky, m.r_l, __fmaf_rn(-(float)ky, m.r_h, a.y));
