@@ -516,7 +516,7 @@ def run_reference(a):
                 tgt.append(i)
                 src.append(j)
     cores = os.cpu_count() or 1
-    jobs = _oracle_sample(pts, poses, tgt, src, max(cores, 2 * cores))
+    jobs = _oracle_sample(pts, poses, tgt, src, 8 * cores)
     for _ in range(a.warmup):
         _time_oracle(jobs[:cores], cores)
     vals = [_time_oracle(jobs, cores) for _ in range(a.steps)]
