@@ -165,6 +165,29 @@ def test_overlap_matrix_bit_exact(ctx, loop_frames, cull):
         ctx.release(int(h))
 
 
+@pytest.mark.parametrize("far", [1.0e4, 2.5e5])
+def test_overlap_matrix_far_from_origin(ctx, loop_frames, far):
+    """The same frames with every pose moved far from the origin (a common rigid
+    shift of 10 km or 250 km plus a rotation): the float32 pair and chunk culling keep
+    their margins when the absolute translations dwarf the relative ones, and the
+    counts equal the oracle's at those poses, pair by pair."""
+    g, ids, pts, covs = loop_frames
+    fr = [ctx.add_frame(p, c) for p, c in zip(pts, covs)]
+    maps = ctx.build_voxelmaps(fr, g.resolution)
+    a = 0.7
+    G = np.array([[np.cos(a), -np.sin(a), 0.0, far], [np.sin(a), np.cos(a), 0.0, -0.5 * far], [0.0, 0.0, 1.0, 37.0]])
+    P = np.stack([dg.compose(G, T) for T in g.poses[ids]])
+    counts = ctx.overlap_matrix(fr, maps, P, P)
+    vms = [oracle.voxelmap(p, c, g.resolution) for p, c in zip(pts, covs)]
+    for s in range(len(ids)):
+        for t in range(len(ids)):
+            T = oracle.relative_pose(P[t], P[s])
+            assert counts[s, t] == oracle.overlap_count(vms[t], pts[s], T), (s, t)
+    assert counts[0, 1] > 0 and counts[0, 7] == 0
+    for h in list(maps) + fr:
+        ctx.release(int(h))
+
+
 def test_overlap_matrix_presence_structures(ctx):
     """Targets whose voxel boxes select each presence structure of the overlap
     matrix: a bitmap over a small box, the compact hash table for a sparse wide
