@@ -368,6 +368,18 @@ vgicp_status vgicp_memory_in_use(vgicp_ctx *ctx, int64_t *bytes);
 /* Number of kernels this context has launched since creation. */
 vgicp_status vgicp_kernel_launches(vgicp_ctx *ctx, int64_t *count);
 
+/* Device time of the hot kernels, from CUDA events recorded on the launching
+ * lane's stream around each launch: vgicp_linearize's batched kernel (with the
+ * reset of its work counter), vgicp_overlap_matrix's matrix kernel, and
+ * vgicp_build_voxelmap(s)'s build kernels as one span.  Launches inside a
+ * plan's CUDA graph are not timed.  vgicp_kernel_timing waits for the recorded
+ * launches of `kernel` on the current lane since the last reset (at most 1,024)
+ * and returns their summed milliseconds and their number;
+ * vgicp_kernel_timing_reset forgets the current lane's records. */
+enum { VGICP_KERNEL_LINEARIZE = 0, VGICP_KERNEL_OVERLAP_MATRIX = 1, VGICP_KERNEL_VOXELMAP_BUILD = 2 };
+vgicp_status vgicp_kernel_timing(vgicp_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches);
+vgicp_status vgicp_kernel_timing_reset(vgicp_ctx *ctx);
+
 /* Text of the last error of this context ("" if none).  Valid until the next call. */
 const char *vgicp_last_error(const vgicp_ctx *ctx);
 

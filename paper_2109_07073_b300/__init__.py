@@ -32,7 +32,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_synchronize", "vgicp_add_frame", "vgicp_frame_size", "vgicp_build_voxelmap",
            "vgicp_build_voxelmaps", "vgicp_voxelmap_size", "vgicp_linearize", "vgicp_overlap",
            "vgicp_overlap_matrix", "vgicp_debug_correspondences", "vgicp_export_voxelmap",
-           "vgicp_estimate_covariances", "vgicp_release", "vgicp_memory_in_use", "vgicp_kernel_launches",
+           "vgicp_estimate_covariances", "vgicp_release", "vgicp_memory_in_use", "vgicp_kernel_launches", "vgicp_kernel_timing", "vgicp_kernel_timing_reset",
            "vgicp_last_error", "vgicp_status_string", "vgicp_linearize_noalloc", "vgicp_autotune", "vgicp_overlap_matrix_work", "vgicp_set_lane",
            "vgicp_overlap_pairs", "vgicp_server_create", "vgicp_server_destroy", "vgicp_server_put_map",
            "vgicp_server_put_frame", "vgicp_server_submit", "vgicp_server_wait", "vgicp_server_stats",
@@ -160,6 +160,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_memory_in_use": [vp, C.POINTER(i64)],
         "vgicp_memory_estimate": [vp, i64, i32, C.POINTER(i64)],
         "vgicp_kernel_launches": [vp, C.POINTER(i64)],
+        "vgicp_kernel_timing": [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)],
+        "vgicp_kernel_timing_reset": [vp],
         "vgicp_plan_create": [vp, vp, i64, i64, C.POINTER(vp)],
         "vgicp_evaluate": [vp, vp, i64, vp, i64, vp, vp, C.c_int],
         "vgicp_solve_step": [vp, vp, vp, i64, i64, i32, f64, vp, C.POINTER(f64)],
@@ -584,6 +586,21 @@ def vgicp_kernel_launches(ctx) -> int:
     v = C.c_int64()
     _check(ctx, load().vgicp_kernel_launches(ctx, C.byref(v)))
     return v.value
+
+
+VGICP_KERNEL_LINEARIZE, VGICP_KERNEL_OVERLAP_MATRIX, VGICP_KERNEL_VOXELMAP_BUILD = 0, 1, 2
+
+
+def vgicp_kernel_timing(ctx, kernel: int):
+    """(summed device milliseconds, launches) of a hot kernel's timed launches on the
+    current lane since the last reset."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(ctx, load().vgicp_kernel_timing(ctx, int(kernel), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def vgicp_kernel_timing_reset(ctx):
+    _check(ctx, load().vgicp_kernel_timing_reset(ctx))
 
 
 def vgicp_last_error(ctx) -> str:

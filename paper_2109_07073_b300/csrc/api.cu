@@ -73,6 +73,11 @@ struct Lane {
     int arena_cur = 0;
     char *d2h_stage = nullptr;   // page-locked landing buffer for small results
     size_t d2h_cap = 0;
+    // event pairs around the hot kernels' launches (vgicp_kernel_timing)
+    struct KTimer {
+        std::vector<cudaEvent_t> begin, end;
+        int used = 0;
+    } ktimer[3];
 };
 
 }  // namespace
@@ -269,6 +274,37 @@ vgicp_status d2h_pieces(vgicp_ctx *ctx, const void *src, void *const *dst, const
     }
     CU(cudaStreamSynchronize(LN.stream));
     return VGICP_OK;
+}
+
+// Event pair around one launch of hot kernel `id` on the current lane; -1 when
+// the lane's record is full (1,024 launches since the last reset).
+constexpr int kMaxTimed = 1024;
+
+int ktimer_begin(vgicp_ctx *ctx, int id)
+{
+    Lane::KTimer &K = LN.ktimer[id];
+    if (K.used >= kMaxTimed) return -1;
+    if (K.used == (int)K.begin.size()) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+            if (a) cudaEventDestroy(a);
+            cudaGetLastError();
+            return -1;
+        }
+        K.begin.push_back(a);
+        K.end.push_back(b);
+    }
+    if (cudaEventRecord(K.begin[K.used], LN.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return K.used++;
+}
+
+void ktimer_end(vgicp_ctx *ctx, int id, int slot)
+{
+    if (slot < 0) return;
+    if (cudaEventRecord(LN.ktimer[id].end[slot], LN.stream) != cudaSuccess) cudaGetLastError();
 }
 
 template <class T>
@@ -503,9 +539,11 @@ vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const 
     scr.vid_of_slot = (int32_t *)LN.ws_vid_of_slot.p;
     scr.slot_of_vid = (int32_t *)LN.ws_slot_of_vid.p;
     const int grid = std::max(1, std::min<int>((int)items.size(), ctx->num_sms * 8));
+    const int kt = ktimer_begin(ctx, VGICP_KERNEL_VOXELMAP_BUILD);
     launch_voxelmap_build(ctx->d_maps, ctx->d_frames, (const BuildUnit *)LN.ws_bunits.p, nu,
                           (const WorkItem *)LN.ws_bitems.p, (int)items.size(), (const int64_t *)LN.ws_bprefix.p,
                           scr, grid, LN.stream);
+    ktimer_end(ctx, VGICP_KERNEL_VOXELMAP_BUILD, kt);
     ctx->launches += 1 + (items.empty() ? 0 : 4);
     CHECK_LAUNCH();
     return VGICP_OK;
@@ -796,6 +834,10 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
             if (A.ev) cudaEventDestroy(A.ev);
         }
         if (LN.d2h_stage) cudaFreeHost(LN.d2h_stage);
+        for (Lane::KTimer &K : LN.ktimer) {
+            for (cudaEvent_t e : K.begin) cudaEventDestroy(e);
+            for (cudaEvent_t e : K.end) cudaEventDestroy(e);
+        }
         if (LN.own_stream) cudaStreamDestroy(LN.own_stream);
     }
     delete ctx;
@@ -1083,6 +1125,7 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         TRY(ensure(ctx, LN.ws_inl, (size_t)std::max(1, P.n_items) * 8));
         TRY(ensure(ctx, LN.ws_fetch, 16));
         if (uses_img(ctx->opt)) TRY(ensure_images(ctx, idx, n_f));
+        const int kt = ktimer_begin(ctx, VGICP_KERNEL_LINEARIZE);
         if (uses_img(ctx->opt))
             launch_linearize_img(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p,
                                  (const int4 *)P.units.p, P.n_units, (double *)LN.ws_partials.p,
@@ -1094,6 +1137,7 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
                                  ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
                                  ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt),
                                  ctx->opt.count_weighted, LN.stream);
+        ktimer_end(ctx, VGICP_KERNEL_LINEARIZE, kt);
         launch_reduce_finalize(d_params, (const int32_t *)P.item_range.p, (int)n_f, (const double *)LN.ws_partials.p,
                                (const int64_t *)LN.ws_inl.p, dH, db, dc, di, LN.stream);
         ctx->launches += (P.n_items > 0) + 1;
@@ -1600,8 +1644,10 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
     }
     CU(cudaMemsetAsync(dcounts, 0, (size_t)n_pairs * 8, LN.stream));
     TRY(ensure(ctx, LN.ws_items, overlap_matrix_scratch_bytes((int)n_src, (int)n_tgt)));
+    const int kt = ktimer_begin(ctx, VGICP_KERNEL_OVERLAP_MATRIX);
     launch_overlap_matrix((const PoseParam *)LN.ws_pairs.p, ctx->d_maps, ctx->d_frames, (int)n_src, (int)n_tgt,
                           dcounts, LN.ws_items.p, max_cap, ctx->num_sms, LN.stream);
+    ktimer_end(ctx, VGICP_KERNEL_OVERLAP_MATRIX, kt);
     ctx->launches += 3;
     CHECK_LAUNCH();
     if (out_kind == VGICP_MEM_HOST) {
@@ -1796,6 +1842,31 @@ vgicp_status vgicp_kernel_launches(vgicp_ctx *ctx, int64_t *count)
 {
     if (!ctx || !count) return VGICP_ERR_INVALID_ARG;
     *count = ctx->launches;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_kernel_timing(vgicp_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (kernel < 0 || kernel > 2 || !total_ms) return fail(ctx, VGICP_ERR_INVALID_ARG, "kernel_timing: bad arguments");
+    const Lane::KTimer &K = LN.ktimer[kernel];
+    double sum = 0.0;
+    for (int i = 0; i < K.used; ++i) {
+        CU(cudaEventSynchronize(K.end[i]));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, K.begin[i], K.end[i]));
+        sum += ms;
+    }
+    *total_ms = sum;
+    if (launches) *launches = K.used;
+    return VGICP_OK;
+}
+
+vgicp_status vgicp_kernel_timing_reset(vgicp_ctx *ctx)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    CU(cudaStreamSynchronize(LN.stream));   // no recorded event is still pending when its slot is reused
+    for (Lane::KTimer &K : LN.ktimer) K.used = 0;
     return VGICP_OK;
 }
 

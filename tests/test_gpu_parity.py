@@ -552,3 +552,36 @@ def test_kernel_launch_counter_moves(ctx, single):
     h = ctx.build_voxelmap(w.points_target, cb, 1.0)
     assert ctx.kernel_launches() > before
     ctx.release(h)
+
+
+def test_kernel_timing_records_the_hot_launches(ctx, single):
+    """Each build, overlap-matrix and linearisation call adds one timed launch of
+    its kernel (device milliseconds from events around the launch); a reset forgets
+    them; plan runs (CUDA graphs) are not timed."""
+    w, cb, ca = single
+    ctx.kernel_timing_reset()
+    for k in (vg.VGICP_KERNEL_LINEARIZE, vg.VGICP_KERNEL_OVERLAP_MATRIX, vg.VGICP_KERNEL_VOXELMAP_BUILD):
+        assert ctx.kernel_timing(k) == (0.0, 0)
+    fr = [ctx.add_frame(w.points_target, cb), ctx.add_frame(w.points_source, ca)]
+    maps = ctx.build_voxelmaps(fr, 1.0)
+    P = np.stack([w.T_target, w.T_source])
+    for _ in range(3):
+        ctx.overlap_matrix(fr, maps, P, P)
+    f = vg.make_factors([maps[0]], [fr[1]], [0], [1])
+    ctx.linearize(f, P)
+    ctx.linearize(f, P)
+    plan = ctx.plan_create(f, 2)
+    ctx.plan_linearize(plan, P)
+    ctx.plan_destroy(plan)
+    got = {k: ctx.kernel_timing(k) for k in (vg.VGICP_KERNEL_VOXELMAP_BUILD, vg.VGICP_KERNEL_OVERLAP_MATRIX,
+                                              vg.VGICP_KERNEL_LINEARIZE)}
+    assert got[vg.VGICP_KERNEL_VOXELMAP_BUILD][1] == 1
+    assert got[vg.VGICP_KERNEL_OVERLAP_MATRIX][1] == 3
+    assert got[vg.VGICP_KERNEL_LINEARIZE][1] == 2
+    assert all(ms > 0.0 for ms, _ in got.values())
+    with pytest.raises(vg.VgicpError):
+        ctx.kernel_timing(7)
+    ctx.kernel_timing_reset()
+    assert ctx.kernel_timing(vg.VGICP_KERNEL_LINEARIZE) == (0.0, 0)
+    for h in list(maps) + fr:
+        ctx.release(int(h))
