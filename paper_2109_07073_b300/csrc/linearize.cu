@@ -123,13 +123,16 @@ __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f,
         const double tol = 0x1p-21 * Xs + 0x1p-22 * m.r + 0x1p-47 * X + 0x1p-100;
         p.tol[i] = __double2float_ru(tol);
         p.rup[i] = __double2float_rd((double)m.r_h - tol);
+        // the same decision on y = x / r (overlap): tol in voxel units plus the
+        // float32 rounding of y, of fl32(1/r) and of its fraction, with margin
+        const double ty = tol * m.inv_r + 0x1p-21 * (Xs * m.inv_r + 1.0);
+        p.hm[i] = ty < 0.5 ? __double2float_rd(0.5 - ty) : -1.f;
         const double fm = 0x1p-40 * X + 0x1p-100;
         p.ffm[i] = __double2float_ru(fm);
         p.ffup[i] = __double2float_rd((double)m.r_h - fm - 0x1p-22 * m.r);
     }
     p.cull = 0;
     p.cmask = f.nchunks >= 32 ? 0xffffffffu : ((1u << f.nchunks) - 1u);
-    p.pad2[0] = p.pad2[1] = p.pad2[2] = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const long long off = (long long)m.kbox[i] - (long long)p.k0[i];

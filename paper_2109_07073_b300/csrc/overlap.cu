@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
                         bool dec = true;
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
-                            dec &= axis_box(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.koff[a], px[j], py[j],
-                                            pz[j], m.r_h, m.r_l, m.inv_rf, d[a]);
+                            dec &= axis_box(P.Rh + 3 * a, P.tfh[a], P.hm[a], P.koff[a], px[j], py[j], pz[j],
+                                            m.inv_rf, d[a]);
                         const bool in = (unsigned)d[0] <= (unsigned)ex && (unsigned)d[1] <= (unsigned)ey &&
                                         (unsigned)d[2] <= (unsigned)ez;
                         const uint32_t bit = (uint32_t)d[0] + X * (uint32_t)d[1] + XY * (uint32_t)d[2];
@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
                         bool dec = true;
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
-                            dec &= axis_box(P.Rh + 3 * a, P.tfh[a], P.tol[a], P.rup[a], P.koff[a], px[j], py[j],
-                                            pz[j], m.r_h, m.r_l, m.inv_rf, d[a]);
+                            dec &= axis_box(P.Rh + 3 * a, P.tfh[a], P.hm[a], P.koff[a], px[j], py[j], pz[j],
+                                            m.inv_rf, d[a]);
                         const bool in = (unsigned)d[0] <= (unsigned)ex && (unsigned)d[1] <= (unsigned)ey &&
                                         (unsigned)d[2] <= (unsigned)ez;
                         state[j] = !have[j] ? 0 : (!dec ? 3 : (in ? 2 : 0));

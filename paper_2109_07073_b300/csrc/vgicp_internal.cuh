@@ -136,7 +136,7 @@ struct __align__(16) PoseParam {
     int32_t cull;        // 1: the pair provably has no correspondence
     int32_t koff[3];     // target voxel-box minimum minus k0: compact coordinate = floor(x'/r) - koff
     uint32_t cmask;      // bit c: cull chunk c of the source may have correspondences
-    int32_t pad2[3];
+    float hm[3];         // overlap floor decided when |frac(x / r) - 1/2| <= hm (see axis_box)
 };
 
 // ---------------------------------------------------------------- keys ----
@@ -305,14 +305,18 @@ __device__ __forceinline__ bool axis_key_split(const float *Rh, float tfh, float
 // target's voxel box (dx = floor(x / r) - box minimum) for the compact tables:
 // coordinates outside the box fail the caller's unsigned range test, so no
 // separate validity check is needed.  Returns false when undecided.
-__device__ __forceinline__ bool axis_box(const float *Rh, float tfh, float tol, float rup, int koff, float px,
-                                         float py, float pz, float r_h, float r_l, float inv_rf, int &dx)
+__device__ __forceinline__ bool axis_box(const float *Rh, float tfh, float hm, int koff, float px, float py,
+                                         float pz, float inv_rf, int &dx)
 {
+    // y = x / r in float32; its distance to the reference y* = fl64(x64 * fl64(1/r))
+    // is below 1/2 - hm (per-pair bound), so floor(y) = floor(y*) when the
+    // fraction of y keeps that distance from both faces.  y - floor(y) is exact
+    // or rounds towards a face, and so does the 1/2 taken off it.
     const float x = __fmaf_rn(Rh[0], px, __fmaf_rn(Rh[1], py, __fmaf_rn(Rh[2], pz, tfh)));
-    const float kf = floorf(__fmul_rn(x, inv_rf));
-    const float d = __fmaf_rn(-kf, r_l, __fmaf_rn(-kf, r_h, x));
+    const float y = __fmul_rn(x, inv_rf);
+    const float kf = floorf(y);
     dx = (int)kf - koff;
-    return d >= tol && d <= rup;
+    return fabsf(__fsub_rn(__fsub_rn(y, kf), 0.5f)) <= hm;
 }
 
 // One axis from a plain float32 fma chain with the error bound
