@@ -71,6 +71,8 @@ struct Lane {
         bool pending = false;
     } arena[2];
     int arena_cur = 0;
+    cudaEvent_t big_copy = nullptr;   // after this lane's last large host -> device copy
+    bool big_copy_pending = false;
     char *d2h_stage = nullptr;   // page-locked landing buffer for small results
     size_t d2h_cap = 0;
     // event pairs around the hot kernels' launches (vgicp_kernel_timing)
@@ -176,9 +178,12 @@ bool page_locked(const void *p)
     return a.type == cudaMemoryTypeHost;
 }
 
-// Small uploads are a kernel that reads the lane's page-locked arena over the
-// bus: copy-engine work from several streams is served in submission order, so
-// a cudaMemcpyAsync here could wait behind another lane's large frame copy.
+// Small uploads go through the lane's page-locked arena.  The copy engine
+// serves the work of several streams in submission order, so while another
+// lane's large copy is in flight a cudaMemcpyAsync here would wait for all of
+// it; then the upload is a kernel that reads the arena over the bus instead.
+// Otherwise the copy engine takes it (a kernel could in turn wait for SMs that
+// another lane's persistent kernel holds).
 __global__ void k_upload(unsigned char *__restrict__ dst, const unsigned char *__restrict__ src, size_t bytes)
 {
     const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
@@ -191,15 +196,35 @@ __global__ void k_upload(unsigned char *__restrict__ dst, const unsigned char *_
     }
 }
 
+// Whether a large host -> device copy issued on another lane may still be running.
+bool other_lane_copying(vgicp_ctx *ctx)
+{
+    bool busy = false;
+    for (int l = 0; l < kMaxLanes; ++l) {
+        Lane &L = ctx->lanes[l];
+        if (l == ctx->lane || !L.big_copy_pending) continue;
+        const cudaError_t q = cudaEventQuery(L.big_copy);
+        if (q == cudaSuccess) {
+            L.big_copy_pending = false;
+        } else {
+            if (cudaPeekAtLastError() == q) cudaGetLastError();   // "not ready" is a state, not a failure
+            busy = true;
+        }
+    }
+    return busy;
+}
+
 vgicp_status h2d(vgicp_ctx *ctx, void *dst, const void *src, size_t bytes)
 {
     if (bytes == 0) return VGICP_OK;
     if (bytes >= 65536 && page_locked(src)) {
-        // page-locked memory is copied directly, in pieces: another lane's small
-        // copies share the copy engine and then wait for one piece, not the whole
+        // page-locked memory is copied directly, in pieces
         for (size_t o = 0; o < bytes; o += kCopyPiece)
             CU(cudaMemcpyAsync((char *)dst + o, (const char *)src + o, std::min(kCopyPiece, bytes - o),
                                cudaMemcpyHostToDevice, LN.stream));
+        if (!LN.big_copy) CU(cudaEventCreateWithFlags(&LN.big_copy, cudaEventDisableTiming));
+        CU(cudaEventRecord(LN.big_copy, LN.stream));
+        LN.big_copy_pending = true;
         return VGICP_OK;
     }
     if (bytes > kArenaMaxCopy) {
@@ -228,10 +253,14 @@ vgicp_status h2d(vgicp_ctx *ctx, void *dst, const void *src, size_t bytes)
     const size_t at = A->off;
     A->off = (A->off + bytes + 255) & ~(size_t)255;
     std::memcpy(A->p + at, src, bytes);
-    const int grid = (int)std::min<size_t>((bytes + 4095) / 4096, (size_t)ctx->num_sms * 2);
-    k_upload<<<grid, 256, 0, LN.stream>>>((unsigned char *)dst, (const unsigned char *)(A->dp + at), bytes);
-    ctx->launches += 1;
-    CHECK_LAUNCH();
+    if (other_lane_copying(ctx)) {
+        const int grid = (int)std::min<size_t>((bytes + 4095) / 4096, (size_t)ctx->num_sms * 2);
+        k_upload<<<grid, 256, 0, LN.stream>>>((unsigned char *)dst, (const unsigned char *)(A->dp + at), bytes);
+        ctx->launches += 1;
+        CHECK_LAUNCH();
+    } else {
+        CU(cudaMemcpyAsync(dst, A->p + at, bytes, cudaMemcpyHostToDevice, LN.stream));
+    }
     CU(cudaEventRecord(A->ev, LN.stream));
     A->pending = true;
     return VGICP_OK;
@@ -834,6 +863,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
             if (A.ev) cudaEventDestroy(A.ev);
         }
         if (LN.d2h_stage) cudaFreeHost(LN.d2h_stage);
+        if (LN.big_copy) cudaEventDestroy(LN.big_copy);
         for (Lane::KTimer &K : LN.ktimer) {
             for (cudaEvent_t e : K.begin) cudaEventDestroy(e);
             for (cudaEvent_t e : K.end) cudaEventDestroy(e);
