@@ -1678,7 +1678,7 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
     launch_overlap_matrix((const PoseParam *)LN.ws_pairs.p, ctx->d_maps, ctx->d_frames, (int)n_src, (int)n_tgt,
                           dcounts, LN.ws_items.p, max_cap, ctx->num_sms, LN.stream);
     ktimer_end(ctx, VGICP_KERNEL_OVERLAP_MATRIX, kt);
-    ctx->launches += 3;
+    ctx->launches += 4;   // pair preparation, item lists, the two matrix kernels
     CHECK_LAUNCH();
     if (out_kind == VGICP_MEM_HOST) {
         void *const dst[1] = {counts};

@@ -118,25 +118,40 @@ __device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, ui
     return false;
 }
 
-// List the (slice, target) items with at least one pair not culled: hdr[0]
-// counts them (hdr[1] is the matrix kernel's fetch counter, both zeroed first).
-__global__ void k_overlap_items(const PoseParam *__restrict__ pairs, int n_src, int n_tgt,
-                                int32_t *__restrict__ list, int *__restrict__ hdr)
+// Shared-memory words of the small CTAs (four 256-thread CTAs per SM, 48 KB
+// each) and of the large ones (one 1024-thread CTA per SM, 128 KB).
+constexpr int kSmallWords = 12288;
+
+// List the (slice, target) items with at least one pair not culled, in two
+// lists by the target's presence structure: one that fits kSmallWords words
+// (list A: hdr[0] items, fetched through hdr[1]) or not (list B, from
+// list + total: hdr[2] items, fetched through hdr[3]); hdr zeroed first.
+__global__ void k_overlap_items(const PoseParam *__restrict__ pairs, const MapDesc *__restrict__ maps, int n_src,
+                                int n_tgt, int32_t *__restrict__ list, int *__restrict__ hdr)
 {
     const int n_slices = (n_src + kSlice - 1) / kSlice;
     const int64_t total = (int64_t)n_slices * n_tgt;
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool live = false;
+    bool live = false, small = false;
     if (v < total) {
         const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
         const int s0 = sl * kSlice, s1 = min(n_src, s0 + kSlice);
         for (int s = s0; s < s1 && !live; ++s) live = !__ldg(&pairs[(int64_t)s * n_tgt + t].cull);
+        if (live) {
+            const int32_t *cm = maps[__ldg(&pairs[(int64_t)s0 * n_tgt + t].map)].cmeta;
+            small = (cm[2] && cm[3] <= kSmallWords) || (cm[1] && (1 << cm[0]) <= kSmallWords);
+        }
     }
-    const unsigned lane = threadIdx.x & 31, b = __ballot_sync(0xffffffffu, live);
-    int base = 0;
-    if (lane == 0 && b) base = atomicAdd(hdr, __popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (live) list[base + __popc(b & ((1u << lane) - 1u))] = (int32_t)v;
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool mine = live && (small == (k == 0));
+        const unsigned b = __ballot_sync(0xffffffffu, mine);
+        int base = 0;
+        if (lane == 0 && b) base = atomicAdd(hdr + 2 * k, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (mine) list[k * total + base + __popc(b & ((1u << lane) - 1u))] = (int32_t)v;
+    }
 }
 
 template <int BLOCK, int MINB>
@@ -396,7 +411,7 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
 size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt)
 {
     const int64_t n_slices = (n_src + kSlice - 1) / kSlice;
-    return (size_t)(n_slices * n_tgt + 4) * sizeof(int32_t);
+    return (size_t)(2 * n_slices * n_tgt + 4) * sizeof(int32_t);
 }
 
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
@@ -408,20 +423,22 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
     int32_t *list = (int32_t *)scratch + 4;
     const int64_t total = (int64_t)((n_src + kSlice - 1) / kSlice) * n_tgt;
     cudaMemsetAsync(hdr, 0, 4 * sizeof(int), st);
-    k_overlap_items<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pairs, n_src, n_tgt, list, hdr);
-    // every target's presence structure fits in max_cap words: small tables run
-    // four 256-thread CTAs per SM, each with its own item and staged table
-    if (max_cap <= 12288) {
-        const int words = (int)std::max<uint32_t>(max_cap, 4);
-        const int smem = words * 4;
+    k_overlap_items<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pairs, maps, n_src, n_tgt, list, hdr);
+    // items whose target's table fits 48 KB: four 256-thread CTAs per SM, each
+    // with its own item and staged table; the others one 1024-thread CTA per SM
+    // with up to 128 KB (an empty list's kernel exits at once; max_cap, the
+    // largest target capacity, is not needed to choose)
+    {
+        const int smem = kSmallWords * 4;
         cudaFuncSetAttribute(k_overlap_matrix<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_overlap_matrix<256, 4><<<num_sms * 4, 256, smem, st>>>(pairs, maps, frames, n_src, n_tgt, list, hdr,
-                                                                  words, counts);
-    } else {
+                                                                  kSmallWords, counts);
+    }
+    {
         const int words = 1 << kSmemLog2, smem = words * 4;
         cudaFuncSetAttribute(k_overlap_matrix<kOvBlock, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_overlap_matrix<kOvBlock, 1><<<num_sms, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt, list, hdr,
-                                                                     words, counts);
+        k_overlap_matrix<kOvBlock, 1><<<num_sms, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt,
+                                                                     list + total, hdr + 2, words, counts);
     }
 }
 
