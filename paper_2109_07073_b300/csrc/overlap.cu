@@ -118,9 +118,9 @@ __device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, ui
     return false;
 }
 
-// Shared-memory words of the small CTAs (four 256-thread CTAs per SM, 48 KB
+// Shared-memory words of the small CTAs (two 512-thread CTAs per SM, 64 KB
 // each) and of the large ones (one 1024-thread CTA per SM, 128 KB).
-constexpr int kSmallWords = 12288;
+constexpr int kSmallWords = 16384;
 
 // List the (slice, target) items with at least one pair not culled, in two
 // lists by the target's presence structure: one that fits kSmallWords words
@@ -424,14 +424,14 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
     const int64_t total = (int64_t)((n_src + kSlice - 1) / kSlice) * n_tgt;
     cudaMemsetAsync(hdr, 0, 4 * sizeof(int), st);
     k_overlap_items<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pairs, maps, n_src, n_tgt, list, hdr);
-    // items whose target's table fits 48 KB: four 256-thread CTAs per SM, each
+    // items whose target's table fits 64 KB: two 512-thread CTAs per SM, each
     // with its own item and staged table; the others one 1024-thread CTA per SM
     // with up to 128 KB (an empty list's kernel exits at once; max_cap, the
     // largest target capacity, is not needed to choose)
     {
         const int smem = kSmallWords * 4;
-        cudaFuncSetAttribute(k_overlap_matrix<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_overlap_matrix<256, 4><<<num_sms * 4, 256, smem, st>>>(pairs, maps, frames, n_src, n_tgt, list, hdr,
+        cudaFuncSetAttribute(k_overlap_matrix<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_overlap_matrix<512, 2><<<num_sms * 2, 512, smem, st>>>(pairs, maps, frames, n_src, n_tgt, list, hdr,
                                                                   kSmallWords, counts);
     }
     {
