@@ -122,6 +122,38 @@ def test_correspondences_bit_exact(ctx, single, r):
     ctx.release(hm)
 
 
+@pytest.mark.parametrize("r", [1.0, 0.5, 0.3])
+def test_overlap_matrix_faces_bit_exact(ctx, single, r):
+    """The overlap matrix's float32 floor (decided on the fraction of x / r) on points
+    exactly on voxel faces and corners, under poses that keep them there (identity,
+    whole-voxel shifts, a 1,000-voxel shift) and under rotations: every undecided
+    point takes the exact path, so the counts equal the oracle's."""
+    w, cb, _ = single
+    vm = oracle.voxelmap(w.points_target, cb, r)
+    rng = dg.Stream(33)
+    srcs = [w.points_source, _face_cloud(6, 3000, r), _face_cloud(7, 2000, r)]
+    poses = [dg.identity_pose()]
+    T = dg.identity_pose()
+    T[:, 3] = [r * 3, -r * 2, r]
+    poses.append(T)
+    T = dg.identity_pose()
+    T[:, 3] = [r * 1000, -r * 2000, r * 777]
+    poses.append(T)
+    poses.append(dg.random_pose(rng, 60, 3.0))
+    cov1 = lambda n: np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (n, 1))
+    fr = [ctx.add_frame(p, cov1(p.shape[0])) for p in srcs]
+    hm = ctx.build_voxelmap(w.points_target, cb, r)
+    # every (source, pose) combination as one row of the matrix; the target at identity
+    rows = [(k, T) for k in range(len(srcs)) for T in poses]
+    frs = np.array([fr[k] for k, _ in rows], np.int64)
+    Ps = np.stack([T for _, T in rows])
+    counts = ctx.overlap_matrix(frs, np.array([hm], np.int64), Ps, dg.identity_pose()[None])
+    for q, (k, T) in enumerate(rows):
+        assert counts[q, 0] == oracle.overlap_count(vm, srcs[k], T), (k, q)
+    for h in fr + [hm]:
+        ctx.release(int(h))
+
+
 def test_overlap_empty_source_is_an_error(ctx, single):
     w, cb, _ = single
     hm = ctx.build_voxelmap(w.points_target, cb, 1.0)
