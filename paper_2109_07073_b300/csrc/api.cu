@@ -1644,13 +1644,11 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
         fidx[i] = (int32_t)k;
         nsrc[i] = o->n;
     }
-    uint32_t max_cap = 0;
     for (int64_t i = 0; i < n_tgt; ++i) {
         uint32_t k;
         Obj *o = lookup(ctx, targets[i], Obj::MAP, &k);
         if (!o) return fail(ctx, VGICP_ERR_NOT_FOUND, "map handle %lld not found", (long long)targets[i]);
         midx[i] = (int32_t)k;
-        max_cap = std::max(max_cap, o->cap);
     }
     for (int64_t i = 0; i < n_src * 12; ++i)
         if (!std::isfinite(poses_src[i])) return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_matrix: non-finite pose");
@@ -1676,7 +1674,7 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
     TRY(ensure(ctx, LN.ws_items, overlap_matrix_scratch_bytes((int)n_src, (int)n_tgt)));
     const int kt = ktimer_begin(ctx, VGICP_KERNEL_OVERLAP_MATRIX);
     launch_overlap_matrix((const PoseParam *)LN.ws_pairs.p, ctx->d_maps, ctx->d_frames, (int)n_src, (int)n_tgt,
-                          dcounts, LN.ws_items.p, max_cap, ctx->num_sms, LN.stream);
+                          dcounts, LN.ws_items.p, ctx->num_sms, LN.stream);
     ktimer_end(ctx, VGICP_KERNEL_OVERLAP_MATRIX, kt);
     ctx->launches += 4;   // pair preparation, item lists, the two matrix kernels
     CHECK_LAUNCH();

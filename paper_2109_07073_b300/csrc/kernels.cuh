@@ -106,10 +106,12 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
                     int n_items, unsigned long long *counts, int grid, cudaStream_t st);
 
 // Overlap matrix: counts[s * n_tgt + t] += hits of source s against target t
-// (pairs[s * n_tgt + t] prepared by launch_prepare_pairs).  One CTA per SM.
+// (pairs[s * n_tgt + t] prepared by launch_prepare_pairs).  Items whose target
+// table fits 64 KB run on two 512-thread CTAs per SM, the others on one
+// 1024-thread CTA per SM.
 size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt);
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
-                           int n_tgt, unsigned long long *counts, void *scratch, uint32_t max_cap, int num_sms,
+                           int n_tgt, unsigned long long *counts, void *scratch, int num_sms,
                            cudaStream_t st);
 
 // out[0] += pairs not culled, out[1] += their source sizes (out zeroed).

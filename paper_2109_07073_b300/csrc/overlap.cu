@@ -415,7 +415,7 @@ size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt)
 }
 
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
-                           int n_tgt, unsigned long long *counts, void *scratch, uint32_t max_cap, int num_sms,
+                           int n_tgt, unsigned long long *counts, void *scratch, int num_sms,
                            cudaStream_t st)
 {
     if (n_src <= 0 || n_tgt <= 0) return;
@@ -426,8 +426,7 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
     k_overlap_items<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pairs, maps, n_src, n_tgt, list, hdr);
     // items whose target's table fits 64 KB: two 512-thread CTAs per SM, each
     // with its own item and staged table; the others one 1024-thread CTA per SM
-    // with up to 128 KB (an empty list's kernel exits at once; max_cap, the
-    // largest target capacity, is not needed to choose)
+    // with up to 128 KB (an empty list's kernel exits at once)
     {
         const int smem = kSmallWords * 4;
         cudaFuncSetAttribute(k_overlap_matrix<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
