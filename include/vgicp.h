@@ -399,7 +399,9 @@ const char *vgicp_last_error(const vgicp_ctx *ctx);
  * (target_pose, source_pose); H n_f x 144, b n_f x 12 as vgicp_linearize()
  * writes them; delta: n_poses x 6 out.  model_decrease (nullable) receives
  * F(0) - F(d) of the undamped model.  VGICP_ERR_NUMERIC if the damped system
- * is not positive definite. */
+ * is not positive definite.  The factorisation uses AVX2/FMA where the host has
+ * them (VGICP_HOST_SIMD=0 in the environment selects portable loops; the two
+ * agree to rounding). */
 vgicp_status vgicp_solve_step(const int32_t *pairs, const double *H, const double *b, int64_t n_f, int64_t n_poses,
                               int32_t anchor, double lambda, double *delta, double *model_decrease);
 

@@ -6,7 +6,8 @@
 // Block-row order: for block row I and each block column J of its envelope,
 // the 36 dot products of I's rows with J's rows over their common columns
 // before J form one small product, computed with independent accumulators
-// (four doubles at a time on hosts with AVX2 and FMA, chosen at run time);
+// (four doubles at a time on hosts with AVX2 and FMA, chosen at run time;
+// VGICP_HOST_SIMD=0 in the environment selects the portable loops);
 // the few terms inside block J follow column by column (the six rows of a
 // column are independent), each scaled by its pivot's reciprocal.  Entry by entry, the same sums as the textbook row algorithm, in a
 // different order; the dependent chain of the row algorithm (each entry's
@@ -17,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 namespace vg {
 
@@ -119,8 +121,12 @@ bool factor_plain(double *a, const int64_t *first, const int64_t *off, int64_t n
     return factor_blocks<gram6_plain>(a, first, off, n);
 }
 
+// AVX2 and FMA present, and not switched off with VGICP_HOST_SIMD=0 in the
+// environment (read once).
 bool host_has_avx2_fma()
 {
+    const char *env = std::getenv("VGICP_HOST_SIMD");
+    if (env && env[0] == '0') return false;
     __builtin_cpu_init();
     return __builtin_cpu_supports("avx2") && __builtin_cpu_supports("fma");
 }

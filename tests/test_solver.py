@@ -2,6 +2,8 @@
 SE(3) retraction against the oracle's dense solve and closed-form exponential,
 and the oracle's own pins (scipy's matrix exponential, the normal equations'
 residual, a hand-solved case)."""
+import os
+
 import numpy as np
 import pytest
 import scipy.linalg
@@ -9,6 +11,8 @@ import scipy.linalg
 import datagen as dg
 import oracle
 import paper_2109_07073_b300 as vg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _twist_matrix(xi):
@@ -158,3 +162,49 @@ def test_loop_factor_matches_oracle(offset, width):
         assert cost[k] == pytest.approx(c_ref, rel=1e-9, abs=1e-12)
         assert np.allclose(H[k], H_ref, rtol=1e-4, atol=1e-6 * max(1.0, np.abs(H_ref).max()))
         assert np.allclose(b[k], b_ref, rtol=1e-4, atol=1e-6 * max(1.0, np.abs(b_ref).max()))
+
+
+def _loop_graph(rng, n_poses, reach=12):
+    """A pose graph shaped like the paper-scale loop: factors between poses up to
+    `reach` apart and between the two ends (loop closure), rank-6 factor blocks."""
+    pairs = [(i, j) for j in range(n_poses) for i in range(max(0, j - reach), j)]
+    pairs += [(i, j) for j in range(n_poses - reach, n_poses) for i in range(reach)]
+    H, b = [], []
+    for _ in pairs:
+        G = rng.normal(6 * 12).reshape(6, 12)
+        H.append(G.T @ G)
+        b.append(rng.normal(12))
+    return np.array(pairs), np.array(H), np.array(b)
+
+
+def test_solve_step_loop_graph_matches_oracle():
+    # 160 poses: envelope rows of ~150 columns, so the blocked factorisation runs its
+    # vector loops and their tails on every block pair
+    rng = dg.Stream(909)
+    pairs, H, b = _loop_graph(rng, 160)
+    got, gdec = vg.vgicp_solve_step(pairs, H, b, 160, 0, 1e-3)
+    ref, rdec = oracle.gn_step(pairs, H, b, 160, 0, 1e-3)
+    assert np.allclose(got, ref, rtol=1e-7, atol=1e-9 * np.abs(ref).max())
+    assert gdec == pytest.approx(rdec, rel=1e-7)
+
+
+def test_solve_step_portable_factorisation_agrees():
+    """The same solve with the host's vector instructions switched off (VGICP_HOST_SIMD=0,
+    read once per process, so in a child process) gives the same step to rounding."""
+    import json
+    import subprocess
+    import sys
+    rng = dg.Stream(910)
+    pairs, H, b = _loop_graph(rng, 60)
+    got, _ = vg.vgicp_solve_step(pairs, H, b, 60, 0, 1e-3)
+    code = ("import json, sys, numpy as np; sys.path.insert(0, %r); import paper_2109_07073_b300 as vg; "
+            "d = json.load(sys.stdin); "
+            "x, _ = vg.vgicp_solve_step(np.array(d['p']), np.array(d['H']), np.array(d['b']), 60, 0, 1e-3); "
+            "print(json.dumps(x.tolist()))") % ROOT
+    env = dict(os.environ, VGICP_HOST_SIMD="0")
+    res = subprocess.run([sys.executable, "-c", code], input=json.dumps({"p": pairs.tolist(), "H": H.tolist(),
+                                                                         "b": b.tolist()}),
+                         capture_output=True, text=True, env=env, timeout=300)
+    assert res.returncode == 0, res.stderr
+    plain = np.array(json.loads(res.stdout))
+    assert np.allclose(plain, got, rtol=1e-9, atol=1e-12 * np.abs(got).max())
