@@ -92,33 +92,90 @@ def load_frames(n_frames, n_points, seed):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """SM clocks and throttle reasons while running: nvidia-smi every 200 ms, and NVML
+    (read-only queries) every 2 ms; the NVML samples taken between mark_start() and
+    mark_end() (the timed region) give the median."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, device_index=0):
-        self.dev = str(device_index)
+        self.dev = device_index
         self.proc = None
         self.lines = []
+        self.nv = []            # (time, sm MHz, reason bits)
+        self.nv_max = None
+        self.window = [None, None]
+        self.stop = threading.Event()
+        self.ready = threading.Event()
+        self.poller = None
+        self.nv_err = None
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.dev, f"--query-gpu={self.Q}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
+        self.poller = threading.Thread(target=self._nvml_poll, daemon=True)
+        self.poller.start()
+        self.ready.wait(timeout=3.0)       # NVML initialised and sampling before the timed region
         return self
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    # NVML (the driver's management library), read-only queries through ctypes
+    NVML_CLOCK_SM = 1
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40}
+
+    def _nvml_poll(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit_v2 failed")
+            h = ctypes.c_void_p()
+            import torch
+            uuid = ("GPU-" + str(torch.cuda.get_device_properties(self.dev).uuid)).encode()
+            if lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(uuid), ctypes.byref(h)) != 0:
+                if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(int(self.dev)), ctypes.byref(h)) != 0:
+                    raise OSError("no NVML handle for the device")
+            clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+            if lib.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0:
+                self.nv_max = mx.value
+            reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            while not self.stop.is_set():
+                ok = lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(clk)) == 0
+                ok = ok and reasons(h, ctypes.byref(rs)) == 0
+                if ok:
+                    self.nv.append((time.perf_counter(), clk.value, rs.value))
+                self.ready.set()
+                self.stop.wait(0.002)
+            lib.nvmlShutdown()
+        except Exception as e:
+            self.nv_err = f"{type(e).__name__}: {e}"
+        finally:
+            self.ready.set()
+
+    def mark_start(self):
+        self.window[0] = time.perf_counter()
+
+    def mark_end(self):
+        self.window[1] = time.perf_counter()
+
     def __exit__(self, *a):
+        self.stop.set()
+        if self.poller:
+            self.poller.join(timeout=5)
         if self.proc:
             time.sleep(0.25)
             self.proc.terminate()
@@ -129,7 +186,6 @@ class ClockSampler:
 
     def summary(self):
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
@@ -139,13 +195,24 @@ class ClockSampler:
                 mx.append(float(f[2]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[4:8]):
+            for nm, v in zip(self.NAMES, f[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+        lo, hi = self.window
+        win = [x for x in self.nv if lo is not None and hi is not None and lo <= x[0] <= hi]
+        if win:
+            for _, _, r in win:
+                reasons.update(nm for nm, bit in self.REASON_BITS.items() if r & bit)
+            return {"sm_mhz": statistics.median(float(x[1]) for x in win),
+                    "sm_max_mhz": float(max([self.nv_max or 0] + mx)), "reasons": sorted(reasons),
+                    "samples": len(win), "sm_mhz_min": float(min(x[1] for x in win)),
+                    "source": "NVML every 2 ms inside the timed region; nvidia-smi every 200 ms around it",
+                    "nvidia_smi_samples": len(sm)}
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi every 200 ms",
+                "nvml": self.nv_err or f"{len(self.nv)} samples, none inside the timed region"}
 
 
 def dram_traffic(kernel):
@@ -247,12 +314,14 @@ def run_ours(a):
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier(world)
         torch.cuda.synchronize()
+        clk.mark_start()
         t0, t1 = ev(), ev()
         t0.record(stream)
         for _ in range(a.steps):
             step(phase_ev)
         t1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
         barrier(world)
     launches = ctx.kernel_launches() - launches0
     kernel_ms = {}
@@ -455,19 +524,31 @@ def run_ours(a):
 # oracle timing (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
+class _OracleJobs:
+    """Factors of the workload as oracle inputs, with the oracle's own covariances and
+    voxelmaps made once per frame (outside every timed region)."""
+
+    def __init__(self, pts, poses, tgt, src):
+        self.pts, self.poses, self.tgt, self.src = pts, poses, tgt, src
+        self.covs, self.vms = {}, {}
+
+    def jobs(self, pick):
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        pts = self.pts
+        frames = sorted((set(int(self.tgt[i]) for i in pick) | set(int(self.src[i]) for i in pick)) - set(self.covs))
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+            self.covs.update(zip(frames, ex.map(lambda f: oracle.covariances(pts[f]), frames)))
+            tset = sorted(set(int(self.tgt[i]) for i in pick) - set(self.vms))
+            self.vms.update(zip(tset, ex.map(lambda f: oracle.voxelmap(pts[f], self.covs[f], 1.0), tset)))
+        return [(self.vms[int(self.tgt[i])], pts[int(self.src[i])], self.covs[int(self.src[i])],
+                 oracle.relative_pose(self.poses[int(self.tgt[i])], self.poses[int(self.src[i])])) for i in pick]
+
+
 def _oracle_sample(pts, poses, tgt, src, n_factors, seed=7):
-    """n_factors factors of the workload, with the oracle's own covariances and voxelmaps."""
-    import oracle
-    from concurrent.futures import ThreadPoolExecutor
-    rng = dg.Stream(seed)
-    pick = rng.choose(len(tgt), min(n_factors, len(tgt)))
-    frames = sorted(set(int(tgt[i]) for i in pick) | set(int(src[i]) for i in pick))
-    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-        covs = dict(zip(frames, ex.map(lambda f: oracle.covariances(pts[f]), frames)))
-        tset = sorted(set(int(tgt[i]) for i in pick))
-        vms = dict(zip(tset, ex.map(lambda f: oracle.voxelmap(pts[f], covs[f], 1.0), tset)))
-    return [(vms[int(tgt[i])], pts[int(src[i])], covs[int(src[i])],
-             oracle.relative_pose(poses[int(tgt[i])], poses[int(src[i])])) for i in pick]
+    """n_factors factors of the workload drawn without replacement, as oracle inputs."""
+    pick = dg.Stream(seed).choose(len(tgt), min(n_factors, len(tgt)))
+    return _OracleJobs(pts, poses, tgt, src).jobs(pick)
 
 
 def _time_oracle(jobs, cores):
@@ -480,22 +561,49 @@ def _time_oracle(jobs, cores):
     return sum(j[1].shape[0] for j in jobs) / dt, dt
 
 
+def _time_oracle_bounded(jobs, cores, wall_seconds):
+    """Workers on all cores take factors from jobs in order until wall_seconds have
+    passed (a factor started before the deadline finishes) or the list ends."""
+    import oracle
+    lock = threading.Lock()
+    state = {"next": 0, "pts": 0, "done": 0}
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                k = state["next"]
+                if k >= len(jobs) or time.perf_counter() - t0 >= wall_seconds:
+                    return
+                state["next"] = k + 1
+            oracle.linearize(*jobs[k])
+            with lock:
+                state["pts"] += jobs[k][1].shape[0]
+                state["done"] += 1
+
+    threads = [threading.Thread(target=worker) for _ in range(cores)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    wall = time.perf_counter() - t0
+    return state["pts"] / wall, wall, state["done"]
+
+
 def cpu_baseline(pts, poses, tgt, src, cpu_seconds=20.0):
     """The FP64 oracle (single-threaded per factor, factors spread over all host cores)
-    on a sample of about cpu_seconds of CPU work, sized from a warm one-core probe."""
+    on the workload's factors in a seeded random order, for about cpu_seconds of core
+    time (wall x cores); a first untimed pass of 4 factors per core brings the cores
+    up to load."""
     cores = os.cpu_count() or 1
-    probe = _oracle_sample(pts, poses, tgt, src, 8, seed=11)
-    _time_oracle(probe[:1], 1)                          # warm: first-touch costs out of the probe
-    v1, _ = _time_oracle(probe, 1)
-    mean_n = float(np.mean([j[1].shape[0] for j in probe]))
-    n = int(max(cores, min(len(tgt), cpu_seconds * v1 / mean_n)))
-    jobs = _oracle_sample(pts, poses, tgt, src, n)
-    v, dt = _time_oracle(jobs, cores)
+    order = dg.Stream(7).choose(len(tgt), len(tgt))
+    jobs = _OracleJobs(pts, poses, tgt, src).jobs(order)
+    _time_oracle(jobs[-4 * cores:], cores)
+    v, wall, done = _time_oracle_bounded(jobs, cores, cpu_seconds / cores)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(jobs)} of the workload's factors (sized by a one-core probe of 8 factors to about "
-                      f"{cpu_seconds:.0f} s of one-core work; FP64 oracle linearisation, one factor per thread on "
-                      f"{cores} threads, {dt:.2f} s wall)",
-            "one_core_value": v1}
+            "sample": f"{done} of the workload's {len(tgt)} factors in seeded random order, taken by {cores} "
+                      f"threads (one factor each at a time) until about {cpu_seconds:.0f} s of core time; FP64 "
+                      f"oracle linearisation, {wall:.2f} s wall = {wall * cores:.1f} core-s"}
 
 
 def run_reference(a):
@@ -602,6 +710,8 @@ def run_uneven(a):
     res_t = {}
     ctx.kernel_timing_reset()          # the direct calls' kernel launches are timed (graph launches are not)
     with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        clk.mark_start()
         for name, fn in (("direct", lambda: ctx.linearize(factors, w.poses, out=out)),
                          ("graph", lambda: ctx.plan_linearize(plan, w.poses, out=out))):
             e0, e1 = ev(), ev()
@@ -611,6 +721,7 @@ def run_uneven(a):
             e1.record(stream)
             torch.cuda.synchronize()
             res_t[name] = e0.elapsed_time(e1) / a.steps
+        clk.mark_end()
     k_tot, k_n = ctx.kernel_timing(vg.VGICP_KERNEL_LINEARIZE)
     kernel_ms = k_tot / max(1, k_n)
     ctx.set_options(precision=vg.VGICP_PREC_F64)
