@@ -634,7 +634,7 @@ def run_reference(a):
     cores = os.cpu_count() or 1
     jobs = _oracle_sample(pts, poses, tgt, src, 8 * cores)
     for _ in range(a.warmup):
-        _time_oracle(jobs[:cores], cores)
+        _time_oracle(jobs, cores)
     vals = [_time_oracle(jobs, cores) for _ in range(a.steps)]
     v = float(np.mean([x[0] for x in vals]))
     dt = float(np.mean([x[1] for x in vals]))
