@@ -596,7 +596,7 @@ def cpu_baseline(pts, poses, tgt, src, cpu_seconds=20.0):
     time (wall x cores); a first untimed pass of 4 factors per core brings the cores
     up to load."""
     cores = os.cpu_count() or 1
-    order = dg.Stream(7).choose(len(tgt), len(tgt))
+    order = dg.Stream(7).permutation(len(tgt))
     jobs = _OracleJobs(pts, poses, tgt, src).jobs(order)
     _time_oracle(jobs[-4 * cores:], cores)
     v, wall, done = _time_oracle_bounded(jobs, cores, cpu_seconds / cores)

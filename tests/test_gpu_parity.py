@@ -300,6 +300,43 @@ def _oracle_factor(vm, pts, covs, TB, TA):
 
 
 @pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64, vg.VGICP_PREC_F32_COMP])
+def test_non_finite_source_points_are_skipped_and_counted(ctx, single, prec):
+    """Source points with a NaN or infinite coordinate find no voxel on either side:
+    the linearisation equals the oracle's, and the overlap counts them in N (Eq. 8)
+    but never as hits, for a pair and inside a matrix."""
+    w, cb, ca = single
+    src = w.points_source.copy()
+    n = src.shape[0]
+    idx = dg.Stream(41).permutation(n)[:60]
+    src[idx[:20], 0] = np.nan
+    src[idx[20:40], 1] = np.inf
+    src[idx[40:], 2] = -np.inf
+    ctx.set_options(precision=prec)
+    hm = ctx.build_voxelmap(w.points_target, cb, w.resolution)
+    hf = ctx.add_frame(src, ca)
+    poses = np.stack([w.T_target, w.T_source])
+    H, b, cost, inl = ctx.linearize(vg.make_factors([hm], [hf], [0], [1]), poses)
+    vm = oracle.voxelmap(w.points_target, cb, w.resolution)
+    L = _oracle_factor(vm, src, ca, w.T_target, w.T_source)
+    L_finite = _oracle_factor(vm, np.delete(src, idx, axis=0), np.delete(ca, idx, axis=0), w.T_target,
+                              w.T_source)
+    assert inl[0] == L.inliers == L_finite.inliers > 0
+    assert np.all(np.isfinite(H[0])) and np.all(np.isfinite(b[0])) and np.isfinite(cost[0])
+    assert err_metric(H[0], L.H, L.SH) <= TOL[prec]
+    assert err_metric(b[0], L.b, L.Sb) <= TOL[prec]
+    assert abs(cost[0] - L.cost) <= TOL[prec] * L.Scost
+    T = oracle.relative_pose(w.T_target, w.T_source)
+    ref = oracle.overlap_count(vm, src, T)
+    fr, cnt = ctx.overlap(hf, hm, T)
+    assert cnt == ref and fr == ref / n
+    counts = ctx.overlap_matrix([hf], [hm], poses[1:], poses[:1])
+    assert counts[0, 0] == ref
+    ctx.set_options(precision=vg.VGICP_PREC_F32)
+    ctx.release(hm)
+    ctx.release(hf)
+
+
+@pytest.mark.parametrize("prec", [vg.VGICP_PREC_F32, vg.VGICP_PREC_F64, vg.VGICP_PREC_F32_COMP])
 def test_linearize_single_factor(ctx, single, prec):
     w, cb, ca = single
     ctx.set_options(precision=prec)

@@ -55,6 +55,22 @@ def test_w1_single_point_single_voxel():
     np.testing.assert_allclose(L.b, np.array([0, 0, 0, *w, 0, 0, 0, *(-np.array(w))]), rtol=1e-14, atol=0)
 
 
+def test_w1_with_non_finite_source_points():
+    """W1 with three more source points, one NaN, one +inf and one -inf coordinate: they
+    find no voxel, so cost, H and b keep W1's closed form, one inlier, and the overlap
+    counts them in N (Eq. 8: 1 of 4)."""
+    vm = single_map([0.125, 0.25, 0.015625], diag6(1, 1, EPS), 1.0)
+    src = np.array([[np.nan, 0, 0], [0, 0, 0], [0, np.inf, 0], [0, 0, -np.inf]], np.float32)
+    L = oracle.linearize(vm, src, np.tile(np.array(diag6(1, 1, EPS), np.float32), (4, 1)), dg.identity_pose())
+    assert L.inliers == 1
+    assert abs(L.cost - (1 / 128 + 1 / 32 + 1 / 8)) < 1e-14
+    w = [0.0625, 0.125, 8.0]
+    np.testing.assert_allclose(L.b, np.array([0, 0, 0, *w, 0, 0, 0, *(-np.array(w))]), rtol=1e-14, atol=0)
+    assert np.all(np.isfinite(L.H)) and np.count_nonzero(L.H) == 12
+    assert oracle.overlap_count(vm, src, dg.identity_pose()) == 1
+    assert oracle.overlap(vm, src, dg.identity_pose()) == 0.25
+
+
 def test_w2_lever_arm():
     """Same with r = 2, p = (1, 1/2, 1/2), e = (1/8, 1/4, 1/64): w = Omega e = (1/16, 1/8, 8),
     b_B = [q x w ; w] = (63/16, -255/32, 3/32, 1/16, 1/8, 8) and b_A = -b_B (R = I, t = 0).
