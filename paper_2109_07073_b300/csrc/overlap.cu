@@ -122,10 +122,17 @@ __device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, ui
 // each) and of the large ones (one 1024-thread CTA per SM, 128 KB).
 constexpr int kSmallWords = 16384;
 
+// Live cull chunks of an item at or above which it counts as heavy: heavy
+// items are fetched first, so the last items to start are short ones and the
+// CTAs finish close together.
+constexpr int kHeavyChunks = 96;
+
 // List the (slice, target) items with at least one pair not culled, in two
 // lists by the target's presence structure: one that fits kSmallWords words
-// (list A: hdr[0] items, fetched through hdr[1]) or not (list B, from
-// list + total: hdr[2] items, fetched through hdr[3]); hdr zeroed first.
+// (list A, at list) or not (list B, at list + total).  In each list the heavy
+// items fill entries 0, 1, ... and the others entries total - 1, total - 2, ...;
+// list k's header hdr[3k .. 3k + 2] holds the heavy count, the other count and
+// the fetch counter (zeroed first).
 __global__ void k_overlap_items(const PoseParam *__restrict__ pairs, const MapDesc *__restrict__ maps, int n_src,
                                 int n_tgt, int32_t *__restrict__ list, int *__restrict__ hdr)
 {
@@ -133,24 +140,36 @@ __global__ void k_overlap_items(const PoseParam *__restrict__ pairs, const MapDe
     const int64_t total = (int64_t)n_slices * n_tgt;
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool live = false, small = false;
+    int chunks = 0;
     if (v < total) {
         const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
         const int s0 = sl * kSlice, s1 = min(n_src, s0 + kSlice);
-        for (int s = s0; s < s1 && !live; ++s) live = !__ldg(&pairs[(int64_t)s * n_tgt + t].cull);
+        for (int s = s0; s < s1; ++s) {
+            const PoseParam &P = pairs[(int64_t)s * n_tgt + t];
+            if (!__ldg(&P.cull)) {
+                live = true;
+                chunks += __popc(__ldg(&P.cmask));
+            }
+        }
         if (live) {
             const int32_t *cm = maps[__ldg(&pairs[(int64_t)s0 * n_tgt + t].map)].cmeta;
             small = (cm[2] && cm[3] <= kSmallWords) || (cm[1] && (1 << cm[0]) <= kSmallWords);
         }
     }
     const unsigned lane = threadIdx.x & 31;
+    const bool heavy = chunks >= kHeavyChunks;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const bool mine = live && (small == (k == 0));
-        const unsigned b = __ballot_sync(0xffffffffu, mine);
-        int base = 0;
-        if (lane == 0 && b) base = atomicAdd(hdr + 2 * k, __popc(b));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (mine) list[k * total + base + __popc(b & ((1u << lane) - 1u))] = (int32_t)v;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const bool mine = live && (small == (k == 0)) && (heavy == (h == 0));
+            const unsigned b = __ballot_sync(0xffffffffu, mine);
+            int base = 0;
+            if (lane == 0 && b) base = atomicAdd(hdr + 3 * k + h, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int64_t e = base + __popc(b & ((1u << lane) - 1u));
+            if (mine) list[k * total + (h == 0 ? e : total - 1 - e)] = (int32_t)v;
+        }
     }
 }
 
@@ -173,14 +192,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
     __shared__ unsigned char s_live[kSlice][kMaxCullChunks];   // live cull chunks of each source, in order
     __shared__ int s_q;
     const int lane = threadIdx.x & 31;
-    const int n_live = hdr[0];
+    const int n_heavy = hdr[0], n_live = hdr[0] + hdr[1];
+    const int64_t total = (int64_t)((n_src + kSlice - 1) / kSlice) * n_tgt;
     for (;;) {
         __syncthreads();                                // previous item's readers are done
-        if (threadIdx.x == 0) s_q = atomicAdd(hdr + 1, 1);
+        if (threadIdx.x == 0) s_q = atomicAdd(hdr + 2, 1);
         __syncthreads();
         const int q = s_q;
         if (q >= n_live) break;
-        const int64_t v = list[q];
+        const int64_t v = list[q < n_heavy ? (int64_t)q : total - 1 - (int64_t)(q - n_heavy)];
         const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
         const int s0 = sl * kSlice, ns = min(n_src, s0 + kSlice) - s0;
         // the slice's pair parameters (one warp per source) and the target's table
@@ -411,7 +431,7 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
 size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt)
 {
     const int64_t n_slices = (n_src + kSlice - 1) / kSlice;
-    return (size_t)(2 * n_slices * n_tgt + 4) * sizeof(int32_t);
+    return (size_t)(2 * n_slices * n_tgt + 8) * sizeof(int32_t);
 }
 
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
@@ -420,9 +440,9 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
 {
     if (n_src <= 0 || n_tgt <= 0) return;
     int *hdr = (int *)scratch;
-    int32_t *list = (int32_t *)scratch + 4;
+    int32_t *list = (int32_t *)scratch + 8;
     const int64_t total = (int64_t)((n_src + kSlice - 1) / kSlice) * n_tgt;
-    cudaMemsetAsync(hdr, 0, 4 * sizeof(int), st);
+    cudaMemsetAsync(hdr, 0, 8 * sizeof(int), st);
     k_overlap_items<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pairs, maps, n_src, n_tgt, list, hdr);
     // items whose target's table fits 64 KB: two 512-thread CTAs per SM, each
     // with its own item and staged table; the others one 1024-thread CTA per SM
@@ -437,7 +457,7 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
         const int words = 1 << kSmemLog2, smem = words * 4;
         cudaFuncSetAttribute(k_overlap_matrix<kOvBlock, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_overlap_matrix<kOvBlock, 1><<<num_sms, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt,
-                                                                     list + total, hdr + 2, words, counts);
+                                                                     list + total, hdr + 3, words, counts);
     }
 }
 
