@@ -91,11 +91,12 @@ __global__ void __launch_bounds__(256) k_overlap(const PoseParam *__restrict__ p
 // CTA stages the target's compact presence table (32-bit keys relative to its
 // voxel box, capacity ~2x its voxel count) in shared memory once, then streams
 // the slice's live sources through it, kPPT points per thread per step.  Only
-// items with a pair that survives culling are listed (k_overlap_items), in
-// slice-major order up to warp interleaving, and CTAs take them from that list
-// through a global counter, so the CTAs in flight share one slice of sources (a
-// few MB, L2-resident) while each holds a different target table, and no SM
-// sits idle while another works through a long static share.  Targets without a
+// items with a pair that survives culling are listed (k_overlap_items): the
+// heavy items, then the others, each group in slice-major order up to warp
+// interleaving.  CTAs take them from that list through a global counter, so
+// the CTAs in flight share one slice of sources (a few MB, L2-resident) while
+// each holds a different target table, no SM sits idle while another works
+// through a long static share, and the items that start last are short.  Targets without a
 // compact table that fits (very large or very wide maps) probe the main table
 // in global memory instead; undecided floors take the slower exact path.
 constexpr int kOvBlock = 1024, kPPT = 4, kSlice = 16;
