@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(256) k_overlap(const PoseParam *__restrict__ p
 // CTA stages the target's compact presence table (32-bit keys relative to its
 // voxel box, capacity ~2x its voxel count) in shared memory once, then streams
 // the slice's live sources through it, kPPT points per thread per step.  Only
-// items with a pair that survives culling are listed (k_overlap_items): the
-// heavy items, then the others, each group in slice-major order up to warp
+// items with a pair that survives culling are listed (k_overlap_items) in
+// tiers of decreasing size, each tier in slice-major order up to warp
 // interleaving.  CTAs take them from that list through a global counter, so
 // the CTAs in flight share one slice of sources (a few MB, L2-resident) while
 // each holds a different target table, no SM sits idle while another works
@@ -123,17 +123,18 @@ __device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, ui
 // each) and of the large ones (one 1024-thread CTA per SM, 128 KB).
 constexpr int kSmallWords = 16384;
 
-// Live cull chunks of an item at or above which it counts as heavy: heavy
-// items are fetched first, so the last items to start are short ones and the
-// CTAs finish close together.
-constexpr int kHeavyChunks = 96;
+// Items are fetched in tiers of decreasing size (live cull chunks of the
+// item: at least kTierChunks[0], then kTierChunks[1], ..., then the rest), so
+// the last items to start are short ones and the CTAs finish close together.
+constexpr int kTiers = 4;
+__device__ __constant__ int kTierChunks[kTiers - 1] = {192, 96, 48};
+constexpr int kHdrInts = 16;   // per list: kTiers counts and the fetch counter
 
 // List the (slice, target) items with at least one pair not culled, in two
 // lists by the target's presence structure: one that fits kSmallWords words
-// (list A, at list) or not (list B, at list + total).  In each list the heavy
-// items fill entries 0, 1, ... and the others entries total - 1, total - 2, ...;
-// list k's header hdr[3k .. 3k + 2] holds the heavy count, the other count and
-// the fetch counter (zeroed first).
+// (list A) or not (list B).  Tier t of list k occupies entries
+// list + (k kTiers + t) total ...; list k's header hdr[(kTiers + 1) k ..] holds
+// the tiers' counts and the fetch counter (zeroed first).
 __global__ void k_overlap_items(const PoseParam *__restrict__ pairs, const MapDesc *__restrict__ maps, int n_src,
                                 int n_tgt, int32_t *__restrict__ list, int *__restrict__ hdr)
 {
@@ -158,18 +159,20 @@ __global__ void k_overlap_items(const PoseParam *__restrict__ pairs, const MapDe
         }
     }
     const unsigned lane = threadIdx.x & 31;
-    const bool heavy = chunks >= kHeavyChunks;
+    int tier = kTiers - 1;
+#pragma unroll
+    for (int t = kTiers - 2; t >= 0; --t)
+        if (chunks >= kTierChunks[t]) tier = t;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const bool mine = live && (small == (k == 0)) && (heavy == (h == 0));
+        for (int t = 0; t < kTiers; ++t) {
+            const bool mine = live && (small == (k == 0)) && tier == t;
             const unsigned b = __ballot_sync(0xffffffffu, mine);
             int base = 0;
-            if (lane == 0 && b) base = atomicAdd(hdr + 3 * k + h, __popc(b));
+            if (lane == 0 && b) base = atomicAdd(hdr + (kTiers + 1) * k + t, __popc(b));
             base = __shfl_sync(0xffffffffu, base, 0);
-            const int64_t e = base + __popc(b & ((1u << lane) - 1u));
-            if (mine) list[k * total + (h == 0 ? e : total - 1 - e)] = (int32_t)v;
+            if (mine) list[(int64_t)(k * kTiers + t) * total + base + __popc(b & ((1u << lane) - 1u))] = (int32_t)v;
         }
     }
 }
@@ -193,15 +196,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
     __shared__ unsigned char s_live[kSlice][kMaxCullChunks];   // live cull chunks of each source, in order
     __shared__ int s_q;
     const int lane = threadIdx.x & 31;
-    const int n_heavy = hdr[0], n_live = hdr[0] + hdr[1];
+    int n_live = 0;
+#pragma unroll
+    for (int t = 0; t < kTiers; ++t) n_live += hdr[t];
     const int64_t total = (int64_t)((n_src + kSlice - 1) / kSlice) * n_tgt;
     for (;;) {
         __syncthreads();                                // previous item's readers are done
-        if (threadIdx.x == 0) s_q = atomicAdd(hdr + 2, 1);
+        if (threadIdx.x == 0) s_q = atomicAdd(hdr + kTiers, 1);
         __syncthreads();
-        const int q = s_q;
+        int q = s_q;
         if (q >= n_live) break;
-        const int64_t v = list[q < n_heavy ? (int64_t)q : total - 1 - (int64_t)(q - n_heavy)];
+        int tier = 0;
+        while (tier < kTiers - 1 && q >= hdr[tier]) q -= hdr[tier++];   // uniform across the block
+        const int64_t v = list[tier * total + q];
         const int sl = (int)(v / n_tgt), t = (int)(v - (int64_t)sl * n_tgt);
         const int s0 = sl * kSlice, ns = min(n_src, s0 + kSlice) - s0;
         // the slice's pair parameters (one warp per source) and the target's table
@@ -432,7 +439,7 @@ void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDes
 size_t overlap_matrix_scratch_bytes(int n_src, int n_tgt)
 {
     const int64_t n_slices = (n_src + kSlice - 1) / kSlice;
-    return (size_t)(2 * n_slices * n_tgt + 8) * sizeof(int32_t);
+    return (size_t)(2 * kTiers * n_slices * n_tgt + kHdrInts) * sizeof(int32_t);
 }
 
 void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const FrameDesc *frames, int n_src,
@@ -441,9 +448,9 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
 {
     if (n_src <= 0 || n_tgt <= 0) return;
     int *hdr = (int *)scratch;
-    int32_t *list = (int32_t *)scratch + 8;
+    int32_t *list = (int32_t *)scratch + kHdrInts;
     const int64_t total = (int64_t)((n_src + kSlice - 1) / kSlice) * n_tgt;
-    cudaMemsetAsync(hdr, 0, 8 * sizeof(int), st);
+    cudaMemsetAsync(hdr, 0, kHdrInts * sizeof(int), st);
     k_overlap_items<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pairs, maps, n_src, n_tgt, list, hdr);
     // items whose target's table fits 64 KB: two 512-thread CTAs per SM, each
     // with its own item and staged table; the others one 1024-thread CTA per SM
@@ -458,7 +465,8 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
         const int words = 1 << kSmemLog2, smem = words * 4;
         cudaFuncSetAttribute(k_overlap_matrix<kOvBlock, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_overlap_matrix<kOvBlock, 1><<<num_sms, kOvBlock, smem, st>>>(pairs, maps, frames, n_src, n_tgt,
-                                                                     list + total, hdr + 3, words, counts);
+                                                                     list + kTiers * total, hdr + kTiers + 1, words,
+                                                                     counts);
     }
 }
 
