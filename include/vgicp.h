@@ -211,6 +211,30 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
                              const double *poses, int64_t n_poses,
                              double *H, double *b, double *cost, int64_t *inliers, int out_kind);
 
+/* vgicp_linearize() with the correspondences it took recorded (Sec. III-A:
+ * each transformed source point is associated with the target voxel that
+ * contains it; parity checks of the linearisation's own voxel floor and hash
+ * probe).  The same launch configuration, precision, variant, chunks and
+ * culling as vgicp_linearize(); the kernels are the recording instantiations
+ * of the same code, so H, b, cost and inliers equal vgicp_linearize()'s.
+ * Point j of factor f's source is entry e = (sum of the source sizes of
+ * factors 0..f-1) + j of:
+ *   keys   3 int64 per entry: the voxel coordinate the kernel computed for the
+ *          point under T_target_source, INT64_MIN on every axis when it has
+ *          none (a coordinate outside [-2^20, 2^20 - 1] or not finite) or was
+ *          never visited;
+ *   state  int32 per entry: 1 when that voxel exists in the target map, 0 when
+ *          not, -1 when the point lies in a chunk the exact culling skipped
+ *          (provably no voxel); with neighbour association (options.neighbors
+ *          7 or 27), bit o set when the voxel at neighbour offset o exists.
+ * keys and state are host arrays sized for the sum of the factors' source
+ * sizes (required); H, b, cost, inliers are host arrays as for
+ * vgicp_linearize() and may all be NULL.  Errors as vgicp_linearize(). */
+vgicp_status vgicp_linearize_correspondences(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f,
+                                             const double *poses, int64_t n_poses,
+                                             double *H, double *b, double *cost, int64_t *inliers,
+                                             int64_t *keys, int32_t *state);
+
 /* Error evaluation (Sec. III-D: the optimiser evaluates the summed matching
  * cost of Eq. 1 to accept or reject a step): each factor's cost
  * sum e' Omega e and inlier count at the given poses, by the batched path with
@@ -280,10 +304,14 @@ vgicp_status vgicp_plan_destroy(vgicp_ctx *ctx, vgicp_plan *plan);
  * application whose own allocator owns all device memory.  They create the
  * context, frames and voxelmaps beforehand and pass their own outputs.
  *
- * Same results as vgicp_linearize() with the context's batched precision
- * (VGICP_PREC_F32, or VGICP_PREC_F32_COMP when set; VGICP_PREC_F64 runs as
- * VGICP_PREC_F32) and its
- * chunk_points / linearize_variant (the same kernels run over the same chunks).
+ * Results equal vgicp_linearize()'s bit for bit with the context's batched
+ * precision (VGICP_PREC_F32, or VGICP_PREC_F32_COMP when set; VGICP_PREC_F64
+ * runs as VGICP_PREC_F32), chunk_points and linearize_variant: each factor is
+ * cut into the same chunks, each chunk's sums are taken by one warp in the same
+ * point and lane order, and each factor's chunk sums are added in chunk order
+ * (only the order in which chunks are listed differs).  Variant 6 (the
+ * shared-memory map path) runs as the default variant, whose per-chunk
+ * arithmetic and lane order are the same.
  * factors and poses are host arrays copied on the context stream (a pinned
  * buffer must stay valid until the stream passes the copy); H (n_f x 144),
  * b (n_f x 12), cost (n_f) and inliers (n_f, nullable) are DEVICE memory,

@@ -39,7 +39,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_server_submit_batch", "vgicp_server_wait_batch", "vgicp_plan_create", "vgicp_plan_linearize",
            "vgicp_plan_info", "vgicp_plan_destroy", "vgicp_memory_estimate", "vgicp_evaluate", "vgicp_solve_step",
            "vgicp_se3_retract", "vgicp_optimize", "vgicp_add_frames", "vgicp_release_many", "vgicp_loop_linearize",
-           "vgicp_optimize_with_loops"]
+           "vgicp_optimize_with_loops", "vgicp_linearize_correspondences"]
 VGICP_REQ_LINEARIZE, VGICP_REQ_OVERLAP = 0, 1
 
 
@@ -147,6 +147,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_build_voxelmaps": [vp, vp, i64, f64, vp],
         "vgicp_voxelmap_size": [vp, i64, C.POINTER(i64)],
         "vgicp_linearize": [vp, vp, i64, vp, i64, vp, vp, vp, vp, C.c_int],
+        "vgicp_linearize_correspondences": [vp, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp],
         "vgicp_linearize_noalloc": [vp, vp, i64, vp, i64, vp, vp, vp, vp],
         "vgicp_autotune": [vp, vp, i64, vp, i64, i32, C.POINTER(Options), C.POINTER(f64)],
         "vgicp_overlap_matrix_work": [vp, C.POINTER(i64), C.POINTER(i64)],
@@ -359,6 +360,25 @@ def vgicp_linearize(ctx, factors, poses, out=None):
     return H, b, cost, inl
 
 
+def vgicp_linearize_correspondences(ctx, factors, poses):
+    """vgicp_linearize() with the correspondences its kernels took recorded.
+
+    Returns (H, b, cost, inliers, keys, state): keys (P, 3) int64 and state (P,)
+    int32 for the P = sum of the factors' source sizes points, factor by factor
+    in point order (INT64_MIN rows: no voxel coordinate or never visited; state
+    1 voxel found, 0 not found, -1 in a culled chunk)."""
+    f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
+    P = _pose12(poses)
+    nf = f.shape[0]
+    total = sum(vgicp_frame_size(ctx, int(h)) for h in f["source"])
+    H, b, cost, inl = np.zeros((nf, 12, 12)), np.zeros((nf, 12)), np.zeros(nf), np.zeros(nf, np.int64)
+    keys = np.zeros((max(total, 1), 3), np.int64)
+    state = np.zeros(max(total, 1), np.int32)
+    _check(ctx, load().vgicp_linearize_correspondences(ctx, _ptr(f), nf, _ptr(P), P.shape[0], _ptr(H), _ptr(b),
+                                                       _ptr(cost), _ptr(inl), _ptr(keys), _ptr(state)))
+    return H, b, cost, inl, keys[:total], state[:total]
+
+
 def vgicp_evaluate(ctx, factors, poses, out=None):
     """Each factor's cost (and inliers) at the poses, by the cost-only batched pass."""
     f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
@@ -459,15 +479,40 @@ def vgicp_plan_destroy(ctx, plan):
     _check(ctx, load().vgicp_plan_destroy(ctx, plan))
 
 
+def check_noalloc_outputs(n: int, out):
+    """Validate vgicp_linearize_noalloc's outputs before any device write: torch tensors,
+    contiguous, float64 H / b / cost and int64 inliers (or None) with room for n factors
+    (at least n*144, n*12, n and n elements), all CUDA tensors on one device."""
+    import torch
+    H, b, cost, inl = out
+    spec = [("H", H, torch.float64, 144), ("b", b, torch.float64, 12), ("cost", cost, torch.float64, 1)]
+    if inl is not None:
+        spec.append(("inliers", inl, torch.int64, 1))
+    for name, t, dt, per in spec:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"vgicp_linearize_noalloc: {name} must be a torch tensor")
+        if t.dtype != dt:
+            raise ValueError(f"vgicp_linearize_noalloc: {name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"vgicp_linearize_noalloc: {name} must be contiguous")
+        if t.numel() < n * per:
+            raise ValueError(f"vgicp_linearize_noalloc: {name} holds {t.numel()} elements, needs {n * per}")
+    for name, t, _, _ in spec:
+        if not t.is_cuda:
+            raise ValueError(f"vgicp_linearize_noalloc writes device outputs: {name} must be a CUDA tensor")
+    devs = {t.device.index for _, t, _, _ in spec}
+    if len(devs) != 1 or devs.pop() != torch.cuda.current_device():
+        raise ValueError("vgicp_linearize_noalloc: every output must be on the current (the context's) device")
+
+
 def vgicp_linearize_noalloc(ctx, factors, poses, out):
     """vgicp_linearize without allocating: out = (H, b, cost, inliers) torch CUDA tensors
-    (n,12,12) float64, (n,12) float64, (n,) float64, (n,) int64, written asynchronously on the
-    context stream.  For callers that must not allocate device memory at call time."""
+    (n,12,12) float64, (n,12) float64, (n,) float64, (n,) int64 or None, written asynchronously
+    on the context stream.  For callers that must not allocate device memory at call time."""
     f = np.ascontiguousarray(factors, dtype=FACTOR_DTYPE)
     P = _pose12(poses)
     H, b, cost, inl = out
-    if not all(_is_torch_cuda(x) for x in (H, b, cost)) or (inl is not None and not _is_torch_cuda(inl)):
-        raise ValueError("vgicp_linearize_noalloc writes device outputs: pass torch CUDA tensors")
+    check_noalloc_outputs(f.shape[0], out)
     _check(ctx, load().vgicp_linearize_noalloc(ctx, _ptr(f), f.shape[0], _ptr(P), P.shape[0], _ptr(H), _ptr(b),
                                                _ptr(cost), _ptr(inl)))
     return H, b, cost, inl

@@ -58,7 +58,7 @@ struct Lane {
     Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
     Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
     Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs, ws_tune, ws_knn;
-    Buf ws_fetch, ws_items, ws_img;
+    Buf ws_fetch, ws_items, ws_img, ws_rec;
     Plan plan;
     int64_t last_matrix_pairs = 0;   // pairs of the last overlap matrix (params kept in ws_pairs)
     // pinned staging for host -> device copies: two arenas used in turn, each
@@ -854,7 +854,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
                        &LN.ws_slot_of_vid, &LN.ws_img, &LN.ws_pairs, &LN.ws_fidx, &LN.ws_midx, &LN.ws_chunks,
                        &LN.ws_export_keys, &LN.ws_export_rec, &LN.ws_counter, &LN.ws_descs, &LN.ws_tune,
                        &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_range, &LN.plan.units, &LN.ws_fetch,
-                       &LN.ws_items};
+                       &LN.ws_items, &LN.ws_rec};
         for (Buf *b : bufs) free_buf(ctx, *b);
         const cudaError_t e2 = cudaStreamSynchronize(LN.stream);
         if (e == cudaSuccess) e = e2;
@@ -1103,20 +1103,48 @@ vgicp_status vgicp_voxelmap_size(vgicp_ctx *ctx, vgicp_map_t map, int64_t *n_vox
     return read_nvox(ctx, *o, n_voxels);
 }
 
-vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
-                             int64_t n_poses, double *H, double *b, double *cost, int64_t *inliers, int out_kind)
+}  // extern "C"
+
+namespace {
+
+// Host copy of a correspondence record (CorrRecord layout): voxel coordinates
+// unpacked to int64 triples (INT64_MIN on every axis where the point has none
+// or was never visited) and the states (-1 where never visited).
+struct HostRecord {
+    int64_t *keys;
+    int32_t *state;
+};
+
+// One linearisation of a factor set (the body of vgicp_linearize); with rec,
+// the recording instantiations of the same kernels also write each point's
+// correspondence, copied to rec's host arrays.
+vgicp_status linearize_run(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
+                           int64_t n_poses, double *H, double *b, double *cost, int64_t *inliers, int out_kind,
+                           const HostRecord *rec)
 {
-    if (!ctx) return VGICP_ERR_INVALID_ARG;
-    if (n_f < 0 || n_poses < 0 || (n_f > 0 && (!factors || !H || !b || !cost)) || (n_poses > 0 && !poses))
-        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: null pointer or negative size");
-    if (out_kind != VGICP_MEM_HOST && out_kind != VGICP_MEM_DEVICE)
-        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: bad out_kind %d", out_kind);
-    if (n_f == 0) return VGICP_OK;
     std::vector<int32_t> idx;
     TRY(factor_indices(ctx, factors, n_f, poses, n_poses, idx));
     TRY(upload(ctx, LN.ws_poses, poses, (size_t)n_poses * 12));
     TRY(get_plan(ctx, factors, n_f, idx));
     Plan &P = LN.plan;
+    CorrRecord crec{};
+    std::vector<int64_t> rbase;
+    int64_t rtotal = 0;
+    if (rec) {
+        rbase.resize((size_t)n_f);
+        for (int64_t i = 0; i < n_f; ++i) {
+            rbase[i] = rtotal;
+            rtotal += ctx->objs[idx[4 * i + 1]].n;
+        }
+        const size_t o_state = align256((size_t)rtotal * 8), o_base = o_state + align256((size_t)rtotal * 4);
+        TRY(ensure(ctx, LN.ws_rec, o_base + (size_t)n_f * 8));
+        char *base = (char *)LN.ws_rec.p;
+        crec.key = (uint64_t *)base;
+        crec.state = (int32_t *)(base + o_state);
+        crec.base = (const int64_t *)(base + o_base);
+        CU(cudaMemsetAsync(base, 0xff, o_base, LN.stream));   // kEmptyKey, state -1: not visited
+        CU(cudaMemcpyAsync(base + o_base, rbase.data(), (size_t)n_f * 8, cudaMemcpyHostToDevice, LN.stream));
+    }
     TRY(ensure(ctx, LN.ws_params, (size_t)n_f * sizeof(PoseParam)));
     PoseParam *d_params = (PoseParam *)LN.ws_params.p;
     launch_prepare_factors((const int32_t *)P.idx.p, (int)n_f, (const double *)LN.ws_poses.p, ctx->d_maps,
@@ -1146,7 +1174,8 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
             launch_linearize_f64(d_params + i, ctx->d_maps, ctx->d_frames, n, (double *)LN.ws_f64.p,
                                  (unsigned int *)LN.ws_ticket.p, dH + 144 * i, db + 12 * i, dc + i,
                                  di ? di + i : nullptr, grid, neighbor_count(ctx->opt), ctx->opt.count_weighted,
-                                 LN.stream);
+                                 LN.stream, rec ? crec.key + rbase[i] : nullptr,
+                                 rec ? crec.state + rbase[i] : nullptr);
         }
         ctx->launches += n_f;
         CHECK_LAUNCH();
@@ -1160,13 +1189,13 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
             launch_linearize_img(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p,
                                  (const int4 *)P.units.p, P.n_units, (double *)LN.ws_partials.p,
                                  (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p, ctx->num_sms,
-                                 ctx->opt.precision == VGICP_PREC_F32_COMP, LN.stream);
+                                 ctx->opt.precision == VGICP_PREC_F32_COMP, LN.stream, crec);
         else
             launch_linearize_f32(d_params, ctx->d_maps, ctx->d_frames, (const WorkItem *)P.items.p, P.n_items,
                                  (double *)LN.ws_partials.p, (int64_t *)LN.ws_inl.p, (int *)LN.ws_fetch.p,
                                  ctx->opt.linearize_variant, ctx->opt.blocks_per_sm, ctx->num_sms,
                                  ctx->opt.precision == VGICP_PREC_F32_COMP, neighbor_count(ctx->opt),
-                                 ctx->opt.count_weighted, LN.stream);
+                                 ctx->opt.count_weighted, LN.stream, crec);
         ktimer_end(ctx, VGICP_KERNEL_LINEARIZE, kt);
         launch_reduce_finalize(d_params, (const int32_t *)P.item_range.p, (int)n_f, (const double *)LN.ws_partials.p,
                                (const int64_t *)LN.ws_inl.p, dH, db, dc, di, LN.stream);
@@ -1178,7 +1207,51 @@ vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_
         const size_t nb[4] = {(size_t)n_f * 144 * 8, (size_t)n_f * 12 * 8, (size_t)n_f * 8, (size_t)n_f * 8};
         TRY(d2h_pieces(ctx, dH, dst, nb, 4));
     }
+    if (rec && rtotal > 0) {
+        std::vector<uint64_t> k((size_t)rtotal);
+        CU(cudaMemcpyAsync(k.data(), crec.key, (size_t)rtotal * 8, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaMemcpyAsync(rec->state, crec.state, (size_t)rtotal * 4, cudaMemcpyDeviceToHost, LN.stream));
+        CU(cudaStreamSynchronize(LN.stream));
+        for (int64_t j = 0; j < rtotal; ++j) {
+            const uint64_t key = k[j];
+            for (int a = 0; a < 3; ++a)
+                rec->keys[3 * j + a] =
+                    key == kEmptyKey ? INT64_MIN
+                                     : (int64_t)((key >> (42 - 21 * a)) & 0x1FFFFFull) - (int64_t)kKeyOffset;
+        }
+    }
     return VGICP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vgicp_status vgicp_linearize(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f, const double *poses,
+                             int64_t n_poses, double *H, double *b, double *cost, int64_t *inliers, int out_kind)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n_f < 0 || n_poses < 0 || (n_f > 0 && (!factors || !H || !b || !cost)) || (n_poses > 0 && !poses))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: null pointer or negative size");
+    if (out_kind != VGICP_MEM_HOST && out_kind != VGICP_MEM_DEVICE)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize: bad out_kind %d", out_kind);
+    if (n_f == 0) return VGICP_OK;
+    return linearize_run(ctx, factors, n_f, poses, n_poses, H, b, cost, inliers, out_kind, nullptr);
+}
+
+vgicp_status vgicp_linearize_correspondences(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t n_f,
+                                             const double *poses, int64_t n_poses, double *H, double *b,
+                                             double *cost, int64_t *inliers, int64_t *keys, int32_t *state)
+{
+    if (!ctx) return VGICP_ERR_INVALID_ARG;
+    if (n_f < 0 || n_poses < 0 || (n_f > 0 && (!factors || !keys || !state)) || (n_poses > 0 && !poses))
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_correspondences: null pointer or negative size");
+    if (n_f == 0) return VGICP_OK;
+    std::vector<double> tmp;
+    if (!H || !b || !cost) tmp.resize((size_t)n_f * 157);
+    double *h = H ? H : tmp.data(), *bb = b ? b : tmp.data() + n_f * 144, *c = cost ? cost : tmp.data() + n_f * 156;
+    const HostRecord rec{keys, state};
+    return linearize_run(ctx, factors, n_f, poses, n_poses, h, bb, c, inliers, VGICP_MEM_HOST, &rec);
 }
 
 }  // extern "C"

@@ -70,20 +70,37 @@ void launch_prepare_list(const double *T, const int32_t *map_idx, const int32_t 
 void launch_prepare_given(const double *T, int map, int frame, const MapDesc *maps, const FrameDesc *frames,
                           int cull, PoseParam *out, cudaStream_t st);
 
+// Per-point record of the correspondences one linearisation pass took (parity
+// checks of the hot path's own floor and probe).  For point i of factor f's
+// source, at j = base[f] + i: key[j] = the packed voxel coordinate the kernel
+// computed for the point (kEmptyKey when it has none: out of range, not
+// finite), state[j] = 1 when that voxel was found in the target map, 0 when not
+// (with neighbour association: bit o set when the voxel at neighbour offset o
+// was found).  Points the kernel never visits (culled chunks) keep whatever the
+// caller stored there.  A null key pointer turns recording off.
+struct CorrRecord {
+    uint64_t *key;
+    int32_t *state;
+    const int64_t *base;
+};
+
 // Batched float32 path: one persistent launch over all work items (one warp per
 // item at a time); each item writes 28 float64 partial sums and an inlier
 // count.  variant: 0 default, 1 and 2 alternatives (see linearize.cu);
 // grid_per_sm: blocks per SM of the persistent grid (0 = the variant's own).
+// rec: when rec.key is set, a recording instantiation of the same kernel also
+// writes every visited point's correspondence.
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
                           const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
                           int *next_item, int variant, int grid_per_sm, int num_sms, bool compensated, int nb,
-                          int weighted, cudaStream_t st);
+                          int weighted, cudaStream_t st, CorrRecord rec = CorrRecord{});
 
 // Per-factor fixed-order float64 reduction of the item partials and expansion
 // to the 12x12 H, b, cost.  item_begin has n_f + 1 entries.
 void launch_linearize_img(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
                           const WorkItem *items, const int4 *units, int n_units, double *partials,
-                          int64_t *inl_partials, int *next_unit, int num_sms, bool compensated, cudaStream_t st);
+                          int64_t *inl_partials, int *next_unit, int num_sms, bool compensated, cudaStream_t st,
+                          CorrRecord rec = CorrRecord{});
 void launch_cost_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                      int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
                      int grid_per_sm, int num_sms, bool compensated, int nb, int weighted, cudaStream_t st);
@@ -95,9 +112,12 @@ void launch_reduce_finalize(const PoseParam *params, const int32_t *item_range, 
 
 // Plain float64 path for one factor (literal Jacobians, 78 unique H entries).
 // scratch holds grid x 92 doubles; ticket is one zeroed int (reset by the kernel).
+// rec_key / rec_state (nullable): this factor's per-point record (CorrRecord
+// layout, already offset to the factor's first point).
 void launch_linearize_f64(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,
                           double *scratch, unsigned int *ticket, double *H, double *b, double *cost,
-                          int64_t *inliers, int grid, int nb, int weighted, cudaStream_t st);
+                          int64_t *inliers, int grid, int nb, int weighted, cudaStream_t st,
+                          uint64_t *rec_key = nullptr, int32_t *rec_state = nullptr);
 int linearize_f64_block();
 
 // ----------------------------------------------------------- overlap -----

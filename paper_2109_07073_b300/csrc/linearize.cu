@@ -356,6 +356,17 @@ __device__ __forceinline__ int resolve_slot(const MapDesc &m, const PointSlot &p
     return probe_from(m.keys, m.mask, ps.key, (ps.h + 1) & m.mask);
 }
 
+// Correspondence record of point j (CorrRecord layout); compiled in only for
+// the recording instantiations.
+template <bool REC>
+__device__ __forceinline__ void record_point(const CorrRecord &rc, int64_t j, bool ok, uint64_t key, int32_t state)
+{
+    if constexpr (REC) {
+        rc.key[j] = ok ? key : kEmptyKey;
+        rc.state[j] = state;
+    }
+}
+
 // The parts of a voxel record the linearisation reads (mean, covariance).
 __device__ __forceinline__ VoxelRec load_rec(const VoxelRec *r)
 {
@@ -503,10 +514,10 @@ __constant__ int8_t c_nb_off[27][3] = {
 // around the point's own voxel is a correspondence (e = mu_v - q, the point's
 // offset taken relative to that voxel's corner), optionally weighted by the
 // voxel's point count.  One point per lane per step, plain loads.
-template <int NT, bool FF>
+template <int NT, bool FF, bool REC>
 __device__ __forceinline__ void linearize_points_general(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
                                                          const WorkItem &w, int lane, float acc[NT], int &inl,
-                                                         int nb, int weighted)
+                                                         int nb, int weighted, const CorrRecord &rc, int64_t rbase)
 {
     const float4 *__restrict__ pa = F.pa + w.start;
     const float4 *__restrict__ pb = F.pb + w.start;
@@ -517,7 +528,11 @@ __device__ __forceinline__ void linearize_points_general(const PoseParam &P, con
         int k[3];
         float d[3], x[3];
         const bool ok = FF ? point_key_ff(P, m, A.x, A.y, A.z, k, d, x) : point_key_split(P, m, A.x, A.y, A.z, k, d, x);
-        if (!ok) continue;
+        if (!ok) {
+            record_point<REC>(rc, rbase + i, false, 0ull, 0);
+            continue;
+        }
+        int32_t found = 0;
         for (int j = 0; j < nb; ++j) {
             int kk[3];
             bool in = true;
@@ -532,10 +547,12 @@ __device__ __forceinline__ void linearize_points_general(const PoseParam &P, con
             if (!in) continue;
             const int slot = probe(m.keys, m.mask, m.log2cap, pack_key(kk[0], kk[1], kk[2]));
             if (slot < 0) continue;
+            found |= 1 << j;
             const VoxelRec v = m.rec[slot];
             const float wgt = weighted ? (float)__float_as_uint(v.c.y) : 1.f;
             inl += accumulate_weighted<NT>(acc, P.Rh, A, B, C, v, dj, x, wgt);
         }
+        record_point<REC>(rc, rbase + i, true, pack_key(k[0], k[1], k[2]), found);
     }
 }
 
@@ -552,9 +569,10 @@ __device__ __forceinline__ void linearize_points_general(const PoseParam &P, con
 //            before this step's key, probe and record chain;
 //   PTS = 2: two points per lane per step, both points' loads, keys and first
 //            probes issued before either record is needed.
-template <int PTS, bool FF, int NT>
+template <int PTS, bool FF, int NT, bool REC = false>
 __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
-                                                 const WorkItem &w, int lane, float acc[NT], int &inl)
+                                                 const WorkItem &w, int lane, float acc[NT], int &inl,
+                                                 const CorrRecord &rc = CorrRecord{}, int64_t rbase = 0)
 {
     const float4 *__restrict__ pa = F.pa + w.start;
     const float4 *__restrict__ pb = F.pb + w.start;
@@ -585,6 +603,7 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
                 v0 = load_rec(m.rec + s0.h);
             }
             const int slot0 = resolve_slot(m, s0, f0);
+            record_point<REC>(rc, rbase + i, s0.ok, s0.key, slot0 >= 0);
             if (slot0 < 0) continue;
             if (slot0 != (int)s0.h) v0 = load_rec(m.rec + slot0);
             inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
@@ -618,6 +637,8 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
             }
             const int slot0 = resolve_slot(m, s0, f0);
             const int slot1 = resolve_slot(m, s1, f1);
+            record_point<REC>(rc, rbase + i0, s0.ok, s0.key, slot0 >= 0);
+            if (h1) record_point<REC>(rc, rbase + i1, s1.ok, s1.key, slot1 >= 0);
             if (slot0 >= 0 && slot0 != (int)s0.h) v0 = load_rec(m.rec + slot0);
             if (slot1 >= 0 && slot1 != (int)s1.h) v1 = load_rec(m.rec + slot1);
             if (slot0 >= 0) inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
@@ -665,10 +686,10 @@ struct WarpStage {
 // probe (key and record together) is copied in, while step st's correspondence
 // is resolved and accumulated.  Each lane reads back only the slots it filled,
 // and refills a slot only after it consumed the slot's values.
-template <bool FF, int NT>
+template <bool FF, int NT, bool REC>
 __device__ __forceinline__ void linearize_points_staged(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
                                                         const WorkItem &w, int lane, float acc[NT], int &inl,
-                                                        WarpStage &S)
+                                                        WarpStage &S, const CorrRecord &rc, int64_t rbase)
 {
     const float4 *__restrict__ pa = F.pa + w.start;
     const float4 *__restrict__ pb = F.pb + w.start;
@@ -720,6 +741,10 @@ __device__ __forceinline__ void linearize_points_staged(const PoseParam &P, cons
             issue_probe(s1, (st + 1) & 1);
         }
         cp_async_commit();
+        if constexpr (REC) {
+            const int i = (st << 5) + lane;
+            if (i < n) record_point<REC>(rc, rbase + i, s.ok, s.key, s.ok && resolve_slot(m, s, S.key[st & 1][lane]) >= 0);
+        }
         if (s.ok) {
             const int b = st & 1;
             const int slot = resolve_slot(m, s, S.key[b][lane]);
@@ -748,21 +773,23 @@ __device__ __forceinline__ void linearize_points_staged(const PoseParam &P, cons
 
 // One work item: skipped when every cull chunk it spans is dead (no point of it
 // can find a voxel), otherwise all of its points.
-template <int PTS, bool FF, int NT>
+template <int PTS, bool FF, int NT, bool REC>
 __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
                                                     const WorkItem &w, int lane, float acc[NT], int &inl,
-                                                    WarpStage *S, int nb, int weighted)
+                                                    WarpStage *S, int nb, int weighted, const CorrRecord &rc)
 {
     if (w.count <= 0) return;
     const int c0 = (int)(w.start >> F.cshift), c1 = (int)((w.start + w.count - 1) >> F.cshift);
     const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
     if ((P.cmask & span) == 0u) return;
+    int64_t rbase = 0;
+    if constexpr (REC) rbase = rc.base[w.unit] + w.start;
     if (nb > 1 || weighted)
-        linearize_points_general<NT, FF>(P, m, F, w, lane, acc, inl, nb, weighted);
+        linearize_points_general<NT, FF, REC>(P, m, F, w, lane, acc, inl, nb, weighted, rc, rbase);
     else if constexpr (PTS == 0)
-        linearize_points_staged<FF, NT>(P, m, F, w, lane, acc, inl, *S);
+        linearize_points_staged<FF, NT, REC>(P, m, F, w, lane, acc, inl, *S, rc, rbase);
     else
-        linearize_points<PTS, FF, NT>(P, m, F, w, lane, acc, inl);
+        linearize_points<PTS, FF, NT, REC>(P, m, F, w, lane, acc, inl, rc, rbase);
 }
 
 // ------------------------------------------------ shared-memory map path --
@@ -775,10 +802,11 @@ __device__ __forceinline__ void linearize_warp_item(const PoseParam &P, const Ma
 // per-point arithmetic and the per-lane order are those of the global path.
 constexpr int kImgBlock = 512;
 
-template <bool FF>
+template <bool FF, bool REC>
 __device__ __forceinline__ void linearize_points_img(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
                                                      const WorkItem &w, int lane, float acc[kNT], int &inl,
-                                                     const uint32_t *__restrict__ hdr)
+                                                     const uint32_t *__restrict__ hdr, const CorrRecord &rc,
+                                                     int64_t rbase)
 {
     const uint32_t lg = hdr[1], mask = (1u << lg) - 1u;
     const uint32_t ex = hdr[3] & 0xffffu, ey = hdr[3] >> 16, ez = hdr[7];
@@ -809,9 +837,15 @@ __device__ __forceinline__ void linearize_points_img(const PoseParam &P, const M
         float d[3], x[3];
         const bool ok = FF ? point_key_ff(P, m, A0.x, A0.y, A0.z, k, d, x)
                            : point_key_split(P, m, A0.x, A0.y, A0.z, k, d, x);
-        if (!ok) continue;
+        if (!ok) {
+            record_point<REC>(rc, rbase + i, false, 0ull, 0);
+            continue;
+        }
         const uint32_t dx = (uint32_t)(k[0] - kb0), dy = (uint32_t)(k[1] - kb1), dz = (uint32_t)(k[2] - kb2);
-        if (dx > ex || dy > ey || dz > ez) continue;          // outside the voxel box: no voxel
+        if (dx > ex || dy > ey || dz > ez) {                  // outside the voxel box: no voxel
+            record_point<REC>(rc, rbase + i, true, pack_key(k[0], k[1], k[2]), 0);
+            continue;
+        }
         const uint32_t ck = pack_compact((int)dx, (int)dy, (int)dz);
         uint32_t h = hash_compact(ck, lg);
         int vid = -1;
@@ -824,6 +858,7 @@ __device__ __forceinline__ void linearize_points_img(const PoseParam &P, const M
             if (v == kEmptyCompact) break;
             h = (h + 1) & mask;
         }
+        record_point<REC>(rc, rbase + i, true, pack_key(k[0], k[1], k[2]), vid >= 0);
         if (vid < 0) continue;
         const float2 *r2 = (const float2 *)(recs + (size_t)vid * kImgRecFloats);
         const float2 q0 = r2[0], q1 = r2[1], q2 = r2[2], q3 = r2[3], q4 = r2[4];
@@ -835,7 +870,7 @@ __device__ __forceinline__ void linearize_points_img(const PoseParam &P, const M
     }
 }
 
-template <bool FF>
+template <bool FF, bool REC>
 __global__ void __launch_bounds__(kImgBlock, 1) k_linearize_img(const PoseParam *__restrict__ params,
                                                                 const MapDesc *__restrict__ maps,
                                                                 const FrameDesc *__restrict__ frames,
@@ -843,7 +878,7 @@ __global__ void __launch_bounds__(kImgBlock, 1) k_linearize_img(const PoseParam 
                                                                 const int4 *__restrict__ units, int n_units,
                                                                 double *__restrict__ partials,
                                                                 int64_t *__restrict__ inl_partials,
-                                                                int *__restrict__ next_unit)
+                                                                int *__restrict__ next_unit, CorrRecord rc)
 {
     extern __shared__ uint4 s_img4[];
     const uint32_t *s_img = (const uint32_t *)s_img4;
@@ -896,10 +931,12 @@ __global__ void __launch_bounds__(kImgBlock, 1) k_linearize_img(const PoseParam 
             const int c0 = (int)(w.start >> F.cshift), c1 = (int)((w.start + w.count - 1) >> F.cshift);
             const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
             if (w.count > 0 && (P.cmask & span) != 0u) {
+                int64_t rbase = 0;
+                if constexpr (REC) rbase = rc.base[w.unit] + w.start;
                 if (staged)
-                    linearize_points_img<FF>(P, m, F, w, lane, acc, inl, s_img);
+                    linearize_points_img<FF, REC>(P, m, F, w, lane, acc, inl, s_img, rc, rbase);
                 else
-                    linearize_points<1, FF, kNT>(P, m, F, w, lane, acc, inl);
+                    linearize_points<1, FF, kNT, REC>(P, m, F, w, lane, acc, inl, rc, rbase);
             }
             double mine = 0.0;
 #pragma unroll
@@ -917,14 +954,15 @@ __global__ void __launch_bounds__(kImgBlock, 1) k_linearize_img(const PoseParam 
     }
 }
 
-template <int BLOCK, int MINB, int PTS, bool FF, int NT = kNT>
+template <int BLOCK, int MINB, int PTS, bool FF, int NT = kNT, bool REC = false>
 __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *__restrict__ params,
                                                                const MapDesc *__restrict__ maps,
                                                                const FrameDesc *__restrict__ frames,
                                                                const WorkItem *__restrict__ items, int n_items,
                                                                double *__restrict__ partials,
                                                                int64_t *__restrict__ inl_partials,
-                                                               int *__restrict__ next_item, int nb, int weighted)
+                                                               int *__restrict__ next_item, int nb, int weighted,
+                                                               CorrRecord rc)
 {
     constexpr int NW = BLOCK / 32;
     constexpr int PW = (int)(sizeof(PoseParam) / 4);
@@ -954,7 +992,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
 #pragma unroll
         for (int j = 0; j < NT; ++j) acc[j] = 0.f;
         int inl = 0;
-        linearize_warp_item<PTS, FF, NT>(P, m, F, w, lane, acc, inl, sS + (PTS == 0 ? wib : 0), nb, weighted);
+        linearize_warp_item<PTS, FF, NT, REC>(P, m, F, w, lane, acc, inl, sS + (PTS == 0 ? wib : 0), nb, weighted,
+                                              rc);
         // butterfly: every lane ends with the warp's sums; lane j writes sum j
         // (a cost-only pass takes its sum from the lane that holds the cost in the
         // full pass, so both passes' costs agree bit for bit)
@@ -1089,7 +1128,8 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
                                                              double *__restrict__ scratch, unsigned int *ticket,
                                                              double *__restrict__ H, double *__restrict__ b,
                                                              double *__restrict__ cost, int64_t *__restrict__ inliers,
-                                                             int nb, int weighted)
+                                                             int nb, int weighted, uint64_t *__restrict__ rec_key,
+                                                             int32_t *__restrict__ rec_state)
 {
     __shared__ double sT[kF64Terms][kF64Block];
     __shared__ int sInl[kF64Block];
@@ -1110,6 +1150,7 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
             int k[3];
             double q[3];
             const bool valid = key_f64(P.T, A.x, A.y, A.z, m.inv_r, k, q);
+            int32_t found = 0;
             // correspondences: the containing voxel, or every voxel of the neighbour set
             for (int j = 0; valid && j < nb; ++j) {
                 int kk[3];
@@ -1122,6 +1163,7 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
                 if (!in) continue;
                 const int slot = probe(m.keys, m.mask, m.log2cap, pack_key(kk[0], kk[1], kk[2]));
                 if (slot < 0) continue;
+                found |= 1 << j;
                 const VoxelRec v = m.rec[slot];
                 double R[3][3], J[3][12], e[3], Om[3][3];
 #pragma unroll
@@ -1186,6 +1228,10 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
 #pragma unroll
                 for (int a = 0; a < 12; ++a) sT[78 + a][tid] += J[0][a] * Oe[0] + J[1][a] * Oe[1] + J[2][a] * Oe[2];
                 sT[90][tid] += e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];
+            }
+            if (rec_key) {
+                rec_key[i] = valid ? pack_key(k[0], k[1], k[2]) : kEmptyKey;
+                rec_state[i] = found;
             }
         }
         __syncthreads();
@@ -1269,46 +1315,46 @@ void launch_prepare_pairs(const double *poses_src, const double *poses_tgt, cons
 // Variants of the batched kernel: (points per lane per step, blocks per SM the
 // register budget is set for).  Work items are per warp, so the block size only
 // sets the occupancy granularity.
-template <bool FF, int NT>
+template <bool FF, int NT, bool REC = false>
 void launch_variant(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
                     int n_items, double *partials, int64_t *inl_partials, int *next_item, int variant,
-                    int grid_per_sm, int num_sms, int nb, int weighted, cudaStream_t st)
+                    int grid_per_sm, int num_sms, int nb, int weighted, cudaStream_t st, CorrRecord rc = CorrRecord{})
 {
     switch (variant) {
     case 1: {   // one point per step + prefetch, 128-thread blocks, 6 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
-        k_linearize_f32<128, 6, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item, nb, weighted);
+        k_linearize_f32<128, 6, 1, FF, NT, REC><<<g, 128, 0, st>>>(params, maps, frames, items, n_items,
+                                                                partials, inl_partials, next_item, nb, weighted, rc);
         break;
     }
     case 2: {   // two points per step, 128-thread blocks, 4 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
-        k_linearize_f32<128, 4, 2, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item, nb, weighted);
+        k_linearize_f32<128, 4, 2, FF, NT, REC><<<g, 128, 0, st>>>(params, maps, frames, items, n_items,
+                                                                partials, inl_partials, next_item, nb, weighted, rc);
         break;
     }
     case 3: {   // one point per step + prefetch, 128-thread blocks, 4 per SM (no register cap below 128)
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 4);
-        k_linearize_f32<128, 4, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item, nb, weighted);
+        k_linearize_f32<128, 4, 1, FF, NT, REC><<<g, 128, 0, st>>>(params, maps, frames, items, n_items,
+                                                                partials, inl_partials, next_item, nb, weighted, rc);
         break;
     }
     case 4: {   // cp.async pipeline (points two steps, probes one step ahead), 128-thread blocks, 5 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
-        k_linearize_f32<128, 5, 0, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item, nb, weighted);
+        k_linearize_f32<128, 5, 0, FF, NT, REC><<<g, 128, 0, st>>>(params, maps, frames, items, n_items,
+                                                                partials, inl_partials, next_item, nb, weighted, rc);
         break;
     }
     case 5: {   // cp.async pipeline, 128-thread blocks, 6 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 6);
-        k_linearize_f32<128, 6, 0, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item, nb, weighted);
+        k_linearize_f32<128, 6, 0, FF, NT, REC><<<g, 128, 0, st>>>(params, maps, frames, items, n_items,
+                                                                partials, inl_partials, next_item, nb, weighted, rc);
         break;
     }
     default: {  // one point per step + prefetch, 128-thread blocks, 5 per SM
         const int g = num_sms * (grid_per_sm > 0 ? grid_per_sm : 5);
-        k_linearize_f32<128, 5, 1, FF, NT><<<g, 128, 0, st>>>(params, maps, frames, items, n_items, partials,
-                                                           inl_partials, next_item, nb, weighted);
+        k_linearize_f32<128, 5, 1, FF, NT, REC><<<g, 128, 0, st>>>(params, maps, frames, items, n_items,
+                                                                partials, inl_partials, next_item, nb, weighted, rc);
         break;
     }
     }
@@ -1317,34 +1363,43 @@ void launch_variant(const PoseParam *params, const MapDesc *maps, const FrameDes
 void launch_linearize_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
                           const WorkItem *items, int n_items, double *partials, int64_t *inl_partials,
                           int *next_item, int variant, int grid_per_sm, int num_sms, bool compensated, int nb,
-                          int weighted, cudaStream_t st)
+                          int weighted, cudaStream_t st, CorrRecord rec)
 {
     if (n_items <= 0) return;
     cudaMemsetAsync(next_item, 0, sizeof(int), st);
-    if (compensated)
+    if (rec.key) {
+        if (compensated)
+            launch_variant<true, kNT, true>(params, maps, frames, items, n_items, partials, inl_partials, next_item,
+                                            variant, grid_per_sm, num_sms, nb, weighted, st, rec);
+        else
+            launch_variant<false, kNT, true>(params, maps, frames, items, n_items, partials, inl_partials, next_item,
+                                             variant, grid_per_sm, num_sms, nb, weighted, st, rec);
+    } else if (compensated) {
         launch_variant<true, kNT>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
                                   grid_per_sm, num_sms, nb, weighted, st);
-    else
+    } else {
         launch_variant<false, kNT>(params, maps, frames, items, n_items, partials, inl_partials, next_item, variant,
                                    grid_per_sm, num_sms, nb, weighted, st);
+    }
 }
 
 void launch_linearize_img(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames,
                           const WorkItem *items, const int4 *units, int n_units, double *partials,
-                          int64_t *inl_partials, int *next_unit, int num_sms, bool compensated, cudaStream_t st)
+                          int64_t *inl_partials, int *next_unit, int num_sms, bool compensated, cudaStream_t st,
+                          CorrRecord rec)
 {
     if (n_units <= 0) return;
     cudaMemsetAsync(next_unit, 0, sizeof(int), st);
     const int smem = (int)kImgMaxBytes;
-    if (compensated) {
-        cudaFuncSetAttribute(k_linearize_img<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_linearize_img<true><<<num_sms, kImgBlock, smem, st>>>(params, maps, frames, items, units, n_units, partials,
-                                                               inl_partials, next_unit);
-    } else {
-        cudaFuncSetAttribute(k_linearize_img<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_linearize_img<false><<<num_sms, kImgBlock, smem, st>>>(params, maps, frames, items, units, n_units,
-                                                                partials, inl_partials, next_unit);
-    }
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        kern<<<num_sms, kImgBlock, smem, st>>>(params, maps, frames, items, units, n_units, partials, inl_partials,
+                                               next_unit, rec);
+    };
+    if (rec.key)
+        compensated ? go(k_linearize_img<true, true>) : go(k_linearize_img<false, true>);
+    else
+        compensated ? go(k_linearize_img<true, false>) : go(k_linearize_img<false, false>);
 }
 
 void launch_cost_f32(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,
@@ -1381,10 +1436,11 @@ int linearize_f64_block() { return kF64Block; }
 
 void launch_linearize_f64(const PoseParam *param, const MapDesc *maps, const FrameDesc *frames, int64_t n,
                           double *scratch, unsigned int *ticket, double *H, double *b, double *cost,
-                          int64_t *inliers, int grid, int nb, int weighted, cudaStream_t st)
+                          int64_t *inliers, int grid, int nb, int weighted, cudaStream_t st, uint64_t *rec_key,
+                          int32_t *rec_state)
 {
     k_linearize_f64<<<grid, kF64Block, 0, st>>>(param, maps, frames, n, scratch, ticket, H, b, cost, inliers, nb,
-                                                weighted);
+                                                weighted, rec_key, rec_state);
 }
 
 }  // namespace vg

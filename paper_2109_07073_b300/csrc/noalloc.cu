@@ -119,7 +119,9 @@ extern "C" vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_fact
 {
     if (!ctx) return VGICP_ERR_INVALID_ARG;
     CtxView v;
-    ctx_view(ctx, &v);
+    if (!ctx_view(ctx, &v)) return ctx_fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_noalloc: context not usable");
+    // an error left by earlier, unrelated work on this thread is not this call's
+    (void)cudaGetLastError();
     if (n_f < 0 || n_poses < 0 || (n_f > 0 && (!factors || !H || !b || !cost)) || (n_poses > 0 && !poses))
         return ctx_fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_noalloc: null pointer or negative size");
     if (n_f > kMaxFactors || n_poses > kMaxPoses)
@@ -166,13 +168,28 @@ extern "C" vgicp_status vgicp_linearize_noalloc(vgicp_ctx *ctx, const vgicp_fact
     if (e != cudaSuccess) return ctx_fail(ctx, VGICP_ERR_CUDA, cudaGetErrorString(e));
     int threads = 32;
     while (threads < n_f) threads <<= 1;
+    // the shared-memory map variant (6) needs per-map images made on demand;
+    // here it runs as the default register variant, whose per-item arithmetic
+    // and lane order are the same, so the results are too
+    const int variant = v.variant == 6 ? 0 : v.variant;
     k_noalloc_plan<<<1, threads, 0, v.stream>>>(d_f, (int)n_f, v.d_frames, v.chunk, d_idx, d_begin, d_items);
-    launch_prepare_factors(d_idx, (int)n_f, d_poses, v.d_maps, v.d_frames, v.linearize_cull, d_params, v.stream);
-    launch_linearize_f32(d_params, v.d_maps, v.d_frames, d_items, (int)n_items, d_partials, d_inl, d_fetch, v.variant,
-                         v.blocks_per_sm, v.num_sms, v.compensated, v.neighbors, v.count_weighted, v.stream);
-    launch_reduce_finalize(d_params, d_begin, (int)n_f, d_partials, d_inl, H, b, cost, inliers, v.stream);
-    ctx_count_launches(ctx, 3 + (n_items > 0));
     e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        launch_prepare_factors(d_idx, (int)n_f, d_poses, v.d_maps, v.d_frames, v.linearize_cull, d_params,
+                               v.stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        launch_linearize_f32(d_params, v.d_maps, v.d_frames, d_items, (int)n_items, d_partials, d_inl, d_fetch,
+                             variant, v.blocks_per_sm, v.num_sms, v.compensated, v.neighbors, v.count_weighted,
+                             v.stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        launch_reduce_finalize(d_params, d_begin, (int)n_f, d_partials, d_inl, H, b, cost, inliers, v.stream);
+        e = cudaGetLastError();
+    }
+    ctx_count_launches(ctx, 3 + (n_items > 0));
     if (e != cudaSuccess) return ctx_fail(ctx, VGICP_ERR_CUDA, cudaGetErrorString(e));
     return VGICP_OK;
 }

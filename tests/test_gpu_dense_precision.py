@@ -5,7 +5,7 @@ batched float32 path (plain and compensated transform) and the plain float64 pat
 and recomputed one by one by the FP64 oracle (with the oracle's own kNN
 covariances).  Inlier counts are bit-exact; err(H), err(b), err(cost) stay within
 1e-4 (float32 paths) and 1e-5 (float64); max / p99 / median go to
-gpurun_out/precision_dense.json when that folder exists."""
+$VGICP_REPORT_DIR/precision_dense.json when that variable names a folder."""
 import json
 import os
 from concurrent.futures import ThreadPoolExecutor
@@ -71,7 +71,7 @@ def test_dense_frames_precision_split():
                 errs[nm].append(v)
         report[name] = {nm: {"max": float(np.max(v)), "p99": float(np.percentile(v, 99)),
                              "median": float(np.median(v))} for nm, v in errs.items()}
-    d = os.path.join(ROOT, "gpurun_out")
+    d = os.environ.get("VGICP_REPORT_DIR", "")
     if os.path.isdir(d):
         with open(os.path.join(d, "precision_dense.json"), "w") as fh:
             json.dump(report, fh, indent=1)

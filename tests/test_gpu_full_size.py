@@ -6,7 +6,7 @@ autotuned batched kernel; sampled outputs are recomputed one by one by the FP64
 oracle: overlap-matrix rows (bit-exact), the factor set they imply, and
 sampled factors' cost / H / b for both the batched float32 and the plain
 float64 path.  The per-factor errors of both paths (the precision split) are
-written to gpurun_out/precision_paper_scale.json when that folder exists.
+written to $VGICP_REPORT_DIR/precision_paper_scale.json when that variable names a folder.
 """
 import json
 import os
@@ -103,7 +103,7 @@ def test_paper_scale_graph_sampled_parity(graph):
                 v = np.array(report[path][name])
                 report[path][name] = {"max": float(v.max()), "p99": float(np.percentile(v, 99)),
                                       "median": float(np.median(v))}
-        out = os.path.join(ROOT, "gpurun_out")
+        out = os.environ.get("VGICP_REPORT_DIR", "")
         if os.path.isdir(out):
             with open(os.path.join(out, "precision_paper_scale.json"), "w") as fh:
                 json.dump(report, fh, indent=1)

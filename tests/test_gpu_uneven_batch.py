@@ -6,7 +6,7 @@ persistent launch (autotuned).  Sampled factors are recomputed one by one by
 the FP64 oracle (their frames' covariances computed by the oracle too), for
 the batched float32 path and the plain float64 path.  Throughput and the
 per-path error statistics (max / p99 / median of err(H), err(b), err(cost))
-go to gpurun_out/uneven_batch_report.json when that folder exists.
+go to $VGICP_REPORT_DIR/uneven_batch_report.json when that variable names a folder.
 """
 import json
 import os
@@ -125,7 +125,7 @@ def test_uneven_batch_sampled_parity():
                 v = np.array(report[path][nm])
                 report[path][nm] = {"max": float(v.max()), "p99": float(np.percentile(v, 99)),
                                     "median": float(np.median(v))}
-        d = os.path.join(ROOT, "gpurun_out")
+        d = os.environ.get("VGICP_REPORT_DIR", "")
         if os.path.isdir(d):
             with open(os.path.join(d, "uneven_batch_report.json"), "w") as fh:
                 json.dump(report, fh, indent=1)

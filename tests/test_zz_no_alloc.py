@@ -3,9 +3,13 @@
 Such callers (for example a mapping loop that fixes its device-memory footprint
 when it starts, or an application whose allocator owns all device memory) keep
 frames and voxelmaps in a context created up front and pass their own device
-outputs.  This file is collected last so that a run stopping at the first
-failure has already run every other test; it also passes when run alone in a
-fresh process, where its first call performs the entry point's one-time set-up.
+outputs.  The entry point's results must equal vgicp_linearize()'s bit for bit
+(same chunks, same per-chunk arithmetic, chunk sums added in chunk order) and
+the FP64 oracle's within the float32 path's err(X) <= 1e-4; a warm call must
+leave device memory exactly as it found it.  This file is collected last so
+that a run stopping at the first failure has already run every other test; it
+also passes when run alone in a fresh process, where its first call performs
+the entry point's one-time set-up.
 """
 import numpy as np
 import pytest
@@ -14,8 +18,6 @@ import datagen as dg
 import oracle
 import paper_2109_07073_b300 as vg
 from util import err_metric
-
-pytestmark = pytest.mark.gpu
 
 TOL = 1e-4   # the float32 path's tolerance used by every parity test
 
@@ -31,54 +33,120 @@ def _case(seed):
     return tg, tcov, src, scov, poses
 
 
+def _outputs(n):
+    import torch
+    return (torch.full((n, 12, 12), np.nan, dtype=torch.float64, device="cuda"),
+            torch.full((n, 12), np.nan, dtype=torch.float64, device="cuda"),
+            torch.full((n,), np.nan, dtype=torch.float64, device="cuda"),
+            torch.full((n,), -1, dtype=torch.int64, device="cuda"))
+
+
+@pytest.mark.gpu
 def test_noalloc_matches_linearize_on_two_calls_in_a_row():
     import torch
     tg, tcov, src, scov, poses = _case(77)
     with vg.Context() as ctx:
         hm = [ctx.build_voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
         hf = [ctx.add_frame(p, c) for p, c in zip(src, scov)]
-        n = len(src)
-        f = vg.make_factors([hm[i % 2] for i in range(n)], hf, [(i + 1) % 2 for i in range(n)],
-                            [2 + i for i in range(n)])
         vms = [oracle.voxelmap(p, c, 1.0) for p, c in zip(tg, tcov)]
-        for call in range(2):
-            # the second call moves the poses, so stale scratch contents would show
-            P = poses.copy()
-            if call == 1:
-                P[2:, :, 3] += 0.05
+        n = len(src)
+        # call 0: all five factors; call 1: three factors on other frames, targets and
+        # poses, so any stale scratch content of call 0 would show
+        sets = [(list(range(n)), [i % 2 for i in range(n)], poses),
+                ([4, 0, 2], [1, 1, 0], poses + np.concatenate([np.zeros((2, 3, 4)),
+                                                               np.full((n, 3, 4), 0.05) * [0, 0, 0, 1]]))]
+        for call, (srcs, tgts, P) in enumerate(sets):
+            m = len(srcs)
+            f = vg.make_factors([hm[t] for t in tgts], [hf[s] for s in srcs], [(t + 1) % 2 for t in tgts],
+                                [2 + s for s in srcs])
             H, b, cost, inl = ctx.linearize(f, P)          # the existing entry point
-            out = (torch.full((n, 12, 12), np.nan, dtype=torch.float64, device="cuda"),
-                   torch.full((n, 12), np.nan, dtype=torch.float64, device="cuda"),
-                   torch.full((n,), np.nan, dtype=torch.float64, device="cuda"),
-                   torch.full((n,), -1, dtype=torch.int64, device="cuda"))
+            out = _outputs(m)
+            torch.cuda.synchronize()
+            free0, _ = torch.cuda.mem_get_info()
+            alloc0 = torch.cuda.memory_allocated()
             vg.vgicp_linearize_noalloc(ctx.ctx, f, P, out)
             ctx.synchronize()
+            if call == 1:      # warm: the one-time set-up is done, nothing may be allocated
+                assert torch.cuda.mem_get_info()[0] == free0
+                assert torch.cuda.memory_allocated() == alloc0
             H2, b2, c2, i2 = (x.cpu().numpy() for x in out)
-            assert np.array_equal(i2, inl)
-            for k in range(n):
-                L = oracle.linearize(vms[k % 2], src[k], scov[k],
+            assert np.array_equal(i2, inl), call
+            assert np.array_equal(H2, H) and np.array_equal(b2, b) and np.array_equal(c2, cost), call
+            for k in range(m):
+                L = oracle.linearize(vms[tgts[k]], src[srcs[k]], scov[srcs[k]],
                                      oracle.relative_pose(P[f["target_pose"][k]], P[f["source_pose"][k]]))
-                scale_H = np.maximum(L.SH, np.abs(H[k]))
-                scale_b = np.maximum(L.Sb, np.abs(b[k]))
-                assert err_metric(H2[k], H[k], scale_H) <= TOL, (call, k)
-                assert err_metric(b2[k], b[k], scale_b) <= TOL, (call, k)
-                assert abs(c2[k] - cost[k]) <= TOL * max(L.Scost, abs(cost[k])), (call, k)
+                assert i2[k] == L.inliers, (call, k)
+                assert err_metric(H2[k], L.H, L.SH) <= TOL, (call, k)
+                assert err_metric(b2[k], L.b, L.Sb) <= TOL, (call, k)
+                assert err_metric([c2[k]], [L.cost], [L.Scost]) <= TOL, (call, k)
         for h in hm + hf:
             ctx.release(h)
 
 
-def test_noalloc_rejects_sizes_beyond_its_limit():
+@pytest.mark.gpu
+def test_noalloc_rejects_sizes_beyond_its_limit_and_bad_arguments():
     import torch
     with vg.Context() as ctx:
         w = dg.single_factor_workload()
         cov = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (w.points_target.shape[0], 1))
         hm = ctx.build_voxelmap(w.points_target, cov, 1.0)
         hf = ctx.add_frame(w.points_source, cov)
+        P2 = np.stack([w.T_target, w.T_source])
+
+        def call(f, P, n=None):
+            n = f.shape[0] if n is None else n
+            out = (torch.zeros((n, 12, 12), dtype=torch.float64, device="cuda"),
+                   torch.zeros((n, 12), dtype=torch.float64, device="cuda"),
+                   torch.zeros(n, dtype=torch.float64, device="cuda"), None)
+            with pytest.raises(vg.VgicpError) as e:
+                vg.vgicp_linearize_noalloc(ctx.ctx, f, P, out)
+            return e.value
+
         n = 1025   # one more than VGICP_NOALLOC_MAX_FACTORS
-        f = vg.make_factors([hm] * n, [hf] * n, [0] * n, [1] * n)
-        out = (torch.zeros((n, 12, 12), dtype=torch.float64, device="cuda"),
-               torch.zeros((n, 12), dtype=torch.float64, device="cuda"),
-               torch.zeros(n, dtype=torch.float64, device="cuda"), None)
-        with pytest.raises(vg.VgicpError) as e:
-            vg.vgicp_linearize_noalloc(ctx.ctx, f, np.stack([w.T_target, w.T_source]), out)
-        assert e.value.status == 1 and "NOALLOC_MAX_FACTORS" in str(e.value)
+        e = call(vg.make_factors([hm] * n, [hf] * n, [0] * n, [1] * n), P2)
+        assert e.status == 1 and "NOALLOC_MAX_FACTORS" in str(e)
+        # more chunks than VGICP_NOALLOC_MAX_ITEMS: 2,000-point sources in 64-point chunks
+        ctx.set_options(chunk_points=64)
+        m = 16384 // 32 + 1     # 32 chunks each
+        e = call(vg.make_factors([hm] * m, [hf] * m, [0] * m, [1] * m), P2)
+        assert e.status == 1 and "NOALLOC_MAX_ITEMS" in str(e)
+        ctx.set_options(chunk_points=0)
+        e = call(vg.make_factors([hm], [hf], [0], [2]), P2)          # pose index out of range
+        assert e.status == 1 and "pose index" in str(e)
+        Pn = P2.copy()
+        Pn[1, 0, 3] = np.nan
+        e = call(vg.make_factors([hm], [hf], [0], [1]), Pn)          # non-finite pose
+        assert e.status == 1 and "non-finite" in str(e)
+        e = call(vg.make_factors([hm], [hm], [0], [1]), P2)          # a map where a frame belongs
+        assert e.status == 3
+        # after the rejections the entry point still works
+        out = _outputs(1)
+        vg.vgicp_linearize_noalloc(ctx.ctx, vg.make_factors([hm], [hf], [0], [1]), P2, out)
+        H, b, cost, inl = ctx.linearize(vg.make_factors([hm], [hf], [0], [1]), P2)
+        ctx.synchronize()
+        assert np.array_equal(out[0].cpu().numpy(), H) and int(out[3].cpu()[0]) == inl[0]
+
+
+def test_noalloc_output_checks_on_the_host():
+    """Outputs are validated before the library is called: wrong dtype, too few
+    elements, non-contiguous views and host tensors are refused with ValueError."""
+    import torch
+    n = 3
+    good = (torch.zeros((n, 12, 12), dtype=torch.float64), torch.zeros((n, 12), dtype=torch.float64),
+            torch.zeros(n, dtype=torch.float64), torch.zeros(n, dtype=torch.int64))
+    bad = [
+        ((good[0].float(),) + good[1:], "float64"),
+        ((good[0], good[1], good[2].float(), good[3]), "float64"),
+        ((good[0], good[1], good[2], good[3].int()), "int64"),
+        ((good[0][:2],) + good[1:], "needs 432"),
+        ((good[0], good[1][:, :11].contiguous(), good[2], good[3]), "needs 36"),
+        ((good[0], good[1], good[2][:2], good[3]), "needs 3"),
+        ((good[0], good[1], good[2], good[3][:1]), "needs 3"),
+        ((good[0].transpose(1, 2),) + good[1:], "contiguous"),
+        ((good[0].numpy(),) + good[1:], "torch tensor"),
+        (good, "CUDA tensor"),
+        ((good[0], good[1], good[2], None), "CUDA tensor"),
+    ]
+    for out, msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            vg.check_noalloc_outputs(n, out)
