@@ -515,6 +515,10 @@ typedef struct {
     int32_t max_batch_requests;  /* requests per batch (0 = 4096) */
     int32_t lanes;               /* concurrent batches, 1..4 (0 = 2) */
     int64_t max_batch_points;    /* source points per batch (0 = 2^27); a larger single request still runs */
+    int32_t device_loop;         /* 1: device-resident request loop (below) instead of host-launched batches */
+    int32_t loop_slots;          /* device loop: requests in flight at most (0 = 256, at most 1024) */
+    double loop_idle_ms;         /* device loop: the loop kernel ends after this long without a request
+                                    (0 = 20 ms); the next request starts it again */
 } vgicp_server_options;
 
 enum { VGICP_REQ_LINEARIZE = 0, VGICP_REQ_OVERLAP = 1 };
@@ -597,6 +601,35 @@ vgicp_status vgicp_server_reset_stats(vgicp_server *server);
 
 /* Text of the server's last error ("" if none). */
 const char *vgicp_server_last_error(const vgicp_server *server);
+
+/* Device-resident request loop (options.device_loop = 1; Sec. III-D issues each
+ * factor's evaluation to the GPU on its own, Sec. IV's online mapper issues
+ * them as frames arrive).  Requests are not batched on the host: each admitted
+ * request is written into a ring of slots in page-locked host memory that the
+ * device reads directly, and one persistent kernel picks it up while earlier
+ * requests are still running -- a dispatcher warp splits it into chunks on a
+ * device work queue, every other warp of the grid takes chunks as they come,
+ * and the warp finishing a request's last chunk writes the result straight
+ * into the ring's result slot, which the server hands to the waiter.  A
+ * request's chunks, their per-chunk sums and the chunk-order reduction are
+ * those of vgicp_linearize(), so a result equals vgicp_linearize() of that
+ * factor (T_target = I, T_source = T_BA, same kernel options) bit for bit,
+ * alone or amid other requests; overlap counts are exact.  Residency, the
+ * budget and LRU eviction work as in batch mode; a request pins its map and
+ * frame until its result is read.  Every wait in the kernel is bounded: when
+ * no request arrives for loop_idle_ms the loop kernel ends with
+ * VGICP_ERR_TIMEOUT (not an error of any request) and the next request
+ * launches it again.  Requests need at most 128 chunks of the context's
+ * chunk_points (262,144 source points at the default); larger ones complete
+ * with VGICP_ERR_INVALID_ARG.  Needs the single-voxel, unweighted association
+ * (kernel_opt.neighbors <= 1, count_weighted 0).
+ *
+ * State of the loop kernel: *running 1 while it runs, *last_exit the status
+ * it ended with last time (VGICP_OK before the first end; VGICP_ERR_TIMEOUT
+ * after an idle end), *launches how often it was started (any may be NULL).
+ * VGICP_ERR_INVALID_ARG for a server without the device loop. */
+vgicp_status vgicp_server_loop_state(vgicp_server *server, int32_t *running, int32_t *last_exit,
+                                     int64_t *launches);
 
 #ifdef __cplusplus
 }

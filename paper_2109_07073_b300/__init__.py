@@ -39,7 +39,7 @@ EXPORTS = ["vgicp_options_default", "vgicp_create", "vgicp_destroy", "vgicp_set_
            "vgicp_server_reset_stats", "vgicp_server_last_error", "vgicp_server_submit_batch", "vgicp_server_wait_batch", "vgicp_plan_create", "vgicp_plan_linearize",
            "vgicp_plan_info", "vgicp_plan_destroy", "vgicp_memory_estimate", "vgicp_evaluate", "vgicp_solve_step",
            "vgicp_se3_retract", "vgicp_optimize", "vgicp_add_frames", "vgicp_release_many", "vgicp_loop_linearize",
-           "vgicp_optimize_with_loops", "vgicp_linearize_correspondences"]
+           "vgicp_optimize_with_loops", "vgicp_linearize_correspondences", "vgicp_server_loop_state"]
 VGICP_REQ_LINEARIZE, VGICP_REQ_OVERLAP = 0, 1
 
 
@@ -95,7 +95,8 @@ def make_loop_factors(pose_i, pose_j, T_ij, information, width, offset):
 
 class ServerOptions(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch_requests", C.c_int32), ("lanes", C.c_int32),
-                ("max_batch_points", C.c_int64)]
+                ("max_batch_points", C.c_int64), ("device_loop", C.c_int32), ("loop_slots", C.c_int32),
+                ("loop_idle_ms", C.c_double)]
 
 
 class Request(C.Structure):
@@ -183,6 +184,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "vgicp_server_wait": [vp, i64, f64, C.POINTER(Result)],
         "vgicp_server_stats": [vp, C.POINTER(ServerCounters)],
         "vgicp_server_reset_stats": [vp],
+        "vgicp_server_loop_state": [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -710,6 +712,13 @@ def vgicp_server_create(options: ServerOptions = None, kernel_options: Options =
     return s
 
 
+def vgicp_server_loop_state(server):
+    """(running, last exit status, launches) of a device-loop server's loop kernel."""
+    r, e, n = C.c_int32(), C.c_int32(), C.c_int64()
+    _scheck(server, load().vgicp_server_loop_state(server, C.byref(r), C.byref(e), C.byref(n)))
+    return bool(r.value), e.value, n.value
+
+
 def vgicp_server_destroy(server):
     _scheck(None, load().vgicp_server_destroy(server))
 
@@ -786,9 +795,11 @@ class Server:
     """A vgicp_server with the calls bound as methods (names without the vgicp_server_ prefix)."""
 
     def __init__(self, hbm_budget_bytes: int = 0, lanes: int = 2, max_batch_requests: int = 0,
-                 max_batch_points: int = 0, kernel_options: Options = None):
+                 max_batch_points: int = 0, kernel_options: Options = None, device_loop: bool = False,
+                 loop_slots: int = 0, loop_idle_ms: float = 0.0):
         self.server = vgicp_server_create(ServerOptions(hbm_budget_bytes, max_batch_requests, lanes,
-                                                        max_batch_points), kernel_options)
+                                                        max_batch_points, int(device_loop), loop_slots,
+                                                        loop_idle_ms), kernel_options)
 
     def close(self):
         if self.server:

@@ -2029,4 +2029,16 @@ vgicp_status ctx_fail(vgicp_ctx *ctx, vgicp_status s, const char *msg) { return 
 
 void ctx_count_launches(vgicp_ctx *ctx, int n) { ctx->launches += n; }
 
+bool ctx_descs(vgicp_ctx *ctx, int64_t map, int64_t frame, MapDesc *m, FrameDesc *f, int64_t *n_points)
+{
+    uint32_t mi, fi;
+    if (!lookup(ctx, map, Obj::MAP, &mi)) return false;
+    Obj *fo = lookup(ctx, frame, Obj::FRAME, &fi);
+    if (!fo) return false;
+    *m = ctx->h_maps[mi];
+    *f = ctx->h_frames[fi];
+    *n_points = fo->n;
+    return true;
+}
+
 }  // namespace vg

@@ -179,5 +179,88 @@ bool ctx_view(::vgicp_ctx *ctx, CtxView *v);
 bool ctx_is_map(::vgicp_ctx *ctx, int64_t handle);
 bool ctx_frame_size(::vgicp_ctx *ctx, int64_t handle, int64_t *n);
 void ctx_count_launches(::vgicp_ctx *ctx, int n);
+// Descriptors of a resident map and frame (copies of the host mirrors) and the
+// frame's point count; false for an unknown handle.
+bool ctx_descs(::vgicp_ctx *ctx, int64_t map, int64_t frame, MapDesc *m, FrameDesc *f, int64_t *n_points);
+
+}  // namespace vg
+
+namespace vg {
+
+// ------------------------------------------------ device request loop ----
+// A persistent kernel serving linearisation and overlap requests that the
+// host publishes, one at a time, into a ring of slots in page-locked host
+// memory mapped into the device's address space.  Request r lives in slot
+// r % slots; the host writes its fields, then its seq (= r + 1) with release
+// order.  One dispatcher warp waits for the next request, prepares its pose
+// parameters and appends its chunks to a device work queue; every other warp
+// takes chunks from the queue, computes them as the batched kernels do, and
+// the warp that finishes a request's last chunk adds the chunk sums in chunk
+// order into the request's result slot, then writes the result's done word
+// (= seq) with release order at system scope.  Every wait is bounded: the
+// dispatcher gives up when no request arrives for idle_ns (the loop then ends
+// with VGICP_ERR_TIMEOUT in LoopExit), a worker when the dispatcher has
+// signalled the end and no chunk is left, or after worker_ns without either.
+// The host can also end the loop through LoopExit::stop.
+constexpr int kLoopMaxItems = 128;      // chunks per request
+constexpr int kLoopBlock = 256;
+enum { kLoopLinearize = 0, kLoopOverlap = 1 };
+
+struct __align__(16) LoopRequest {      // host -> device, one per slot
+    MapDesc map;
+    FrameDesc frame;
+    double T[12];                       // T_target_source (T_BA)
+    int32_t kind;                       // kLoopLinearize or kLoopOverlap
+    int32_t n_items;                    // chunks (1 .. kLoopMaxItems)
+    int32_t chunk;                      // points per chunk (the last takes the rest)
+    int32_t cull;                       // exact culling of chunks (linearize_cull)
+    unsigned long long seq;             // r + 1, written last
+    unsigned long long pad;
+};
+
+struct __align__(16) LoopResult {       // device -> host, one per slot
+    double H[144], b[12], cost;
+    long long count;                    // inliers (linearise) or hits (overlap)
+    unsigned long long done;            // = seq once the fields above are complete
+    unsigned long long pad;
+};
+
+struct LoopControl {                    // device memory, written by the host before each launch
+    unsigned int item_head, item_tail, quit;
+    unsigned int status;                // VGICP_ERR_TIMEOUT when a worker's own limit ran out
+    unsigned long long next_req;        // first request the dispatcher waits for
+};
+
+struct LoopExit {                       // host-mapped
+    int status;                         // device, at the end: VGICP_OK when asked to stop,
+                                        // VGICP_ERR_TIMEOUT when the idle limit ran out
+    int stop;                           // host: 1 asks the dispatcher to end
+    unsigned long long next_req;        // device, at the end: first request not dispatched
+};
+
+struct __align__(16) LoopSlotState {    // device memory, one per slot
+    PoseParam P;
+    MapDesc map;
+    FrameDesc frame;
+    int32_t kind, n_items, chunk;
+    unsigned int done_items;
+    unsigned long long seq;
+};
+
+struct LoopArgs {
+    const LoopRequest *req;             // device view of the mapped request ring
+    LoopResult *res;                    // device view of the mapped result ring
+    LoopExit *exit;                     // device view of the mapped exit record
+    LoopControl *ctl;
+    LoopSlotState *state;
+    double *partials;                   // slots x kLoopMaxItems x 28
+    long long *counts;                  // slots x kLoopMaxItems
+    int2 *queue;                        // qcap entries (slot, chunk)
+    int slots;
+    unsigned int qcap;                  // power of two >= slots x kLoopMaxItems
+    unsigned long long idle_ns, worker_ns;
+};
+
+void launch_request_loop(const LoopArgs &a, int num_sms, cudaStream_t st);
 
 }  // namespace vg

@@ -22,6 +22,7 @@
 //   Literal 3x12 Jacobian J = [-[q]x, I | R[p]x, -R], all 78 unique entries of
 //   J' Omega J, 12 of J' Omega e and the cost, per point, in float64.
 #include "kernels.cuh"
+#include "vgicp.h"
 
 namespace vg {
 
@@ -349,11 +350,12 @@ __device__ __forceinline__ PointSlot point_hash(const PoseParam &P, const MapDes
     return r;
 }
 
+template <class L = LdNC>
 __device__ __forceinline__ int resolve_slot(const MapDesc &m, const PointSlot &ps, uint64_t first)
 {
     if (!ps.ok || first == kEmptyKey) return -1;
     if (first == ps.key) return (int)ps.h;
-    return probe_from(m.keys, m.mask, ps.key, (ps.h + 1) & m.mask);
+    return probe_from<L>(m.keys, m.mask, ps.key, (ps.h + 1) & m.mask);
 }
 
 // Correspondence record of point j (CorrRecord layout); compiled in only for
@@ -368,12 +370,13 @@ __device__ __forceinline__ void record_point(const CorrRecord &rc, int64_t j, bo
 }
 
 // The parts of a voxel record the linearisation reads (mean, covariance).
+template <class L = LdNC>
 __device__ __forceinline__ VoxelRec load_rec(const VoxelRec *r)
 {
     VoxelRec v;
-    v.a = __ldg(&r->a);
-    v.b = __ldg(&r->b);
-    v.c = make_float4(__ldg(&r->c.x), 0.f, 0.f, 0.f);
+    v.a = L::ld(&r->a);
+    v.b = L::ld(&r->b);
+    v.c = make_float4(L::ld(&r->c.x), 0.f, 0.f, 0.f);
     return v;
 }
 
@@ -569,7 +572,7 @@ __device__ __forceinline__ void linearize_points_general(const PoseParam &P, con
 //            before this step's key, probe and record chain;
 //   PTS = 2: two points per lane per step, both points' loads, keys and first
 //            probes issued before either record is needed.
-template <int PTS, bool FF, int NT, bool REC = false>
+template <int PTS, bool FF, int NT, bool REC = false, class L = LdNC>
 __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
                                                  const WorkItem &w, int lane, float acc[NT], int &inl,
                                                  const CorrRecord &rc = CorrRecord{}, int64_t rbase = 0)
@@ -582,44 +585,44 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
         float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
         float C = 0.f;
         if (lane < n) {
-            A = __ldg(pa + lane);
-            B = __ldg(pb + lane);
-            C = __ldg(pc + lane);
+            A = L::ld(pa + lane);
+            B = L::ld(pb + lane);
+            C = L::ld(pc + lane);
         }
         for (int i = lane; i < n; i += 32) {
             const float4 A0 = A, B0 = B;
             const float C0 = C;
             if (i + 32 < n) {
-                A = __ldg(pa + i + 32);
-                B = __ldg(pb + i + 32);
-                C = __ldg(pc + i + 32);
+                A = L::ld(pa + i + 32);
+                B = L::ld(pb + i + 32);
+                C = L::ld(pc + i + 32);
             }
             float d0[3], x0[3];
             const PointSlot s0 = point_hash<FF>(P, m, A0.x, A0.y, A0.z, d0, x0);
             uint64_t f0 = kEmptyKey;
             VoxelRec v0;
             if (s0.ok) {   // the record of the first slot probed travels with its key
-                f0 = __ldg(m.keys + s0.h);
-                v0 = load_rec(m.rec + s0.h);
+                f0 = L::ld(m.keys + s0.h);
+                v0 = load_rec<L>(m.rec + s0.h);
             }
-            const int slot0 = resolve_slot(m, s0, f0);
+            const int slot0 = resolve_slot<L>(m, s0, f0);
             record_point<REC>(rc, rbase + i, s0.ok, s0.key, slot0 >= 0);
             if (slot0 < 0) continue;
-            if (slot0 != (int)s0.h) v0 = load_rec(m.rec + slot0);
+            if (slot0 != (int)s0.h) v0 = load_rec<L>(m.rec + slot0);
             inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
         }
     } else {
         for (int i0 = lane; i0 < n; i0 += 64) {
             const int i1 = i0 + 32;
             const bool h1 = i1 < n;
-            const float4 A0 = __ldg(pa + i0), B0 = __ldg(pb + i0);
-            const float C0 = __ldg(pc + i0);
+            const float4 A0 = L::ld(pa + i0), B0 = L::ld(pb + i0);
+            const float C0 = L::ld(pc + i0);
             float4 A1 = make_float4(0.f, 0.f, 0.f, 0.f), B1 = A1;
             float C1 = 0.f;
             if (h1) {
-                A1 = __ldg(pa + i1);
-                B1 = __ldg(pb + i1);
-                C1 = __ldg(pc + i1);
+                A1 = L::ld(pa + i1);
+                B1 = L::ld(pb + i1);
+                C1 = L::ld(pc + i1);
             }
             float d0[3], x0[3], d1[3], x1[3];
             PointSlot s0 = point_hash<FF>(P, m, A0.x, A0.y, A0.z, d0, x0);
@@ -628,19 +631,19 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
             uint64_t f0 = kEmptyKey, f1 = kEmptyKey;
             VoxelRec v0, v1;
             if (s0.ok) {
-                f0 = __ldg(m.keys + s0.h);
-                v0 = load_rec(m.rec + s0.h);
+                f0 = L::ld(m.keys + s0.h);
+                v0 = load_rec<L>(m.rec + s0.h);
             }
             if (s1.ok) {
-                f1 = __ldg(m.keys + s1.h);
-                v1 = load_rec(m.rec + s1.h);
+                f1 = L::ld(m.keys + s1.h);
+                v1 = load_rec<L>(m.rec + s1.h);
             }
-            const int slot0 = resolve_slot(m, s0, f0);
-            const int slot1 = resolve_slot(m, s1, f1);
+            const int slot0 = resolve_slot<L>(m, s0, f0);
+            const int slot1 = resolve_slot<L>(m, s1, f1);
             record_point<REC>(rc, rbase + i0, s0.ok, s0.key, slot0 >= 0);
             if (h1) record_point<REC>(rc, rbase + i1, s1.ok, s1.key, slot1 >= 0);
-            if (slot0 >= 0 && slot0 != (int)s0.h) v0 = load_rec(m.rec + slot0);
-            if (slot1 >= 0 && slot1 != (int)s1.h) v1 = load_rec(m.rec + slot1);
+            if (slot0 >= 0 && slot0 != (int)s0.h) v0 = load_rec<L>(m.rec + slot0);
+            if (slot1 >= 0 && slot1 != (int)s1.h) v1 = load_rec<L>(m.rec + slot1);
             if (slot0 >= 0) inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
             if (slot1 >= 0) inl += accumulate<NT>(acc, P.Rh, A1, B1, C1, v1, d1, x1);
         }
@@ -1032,27 +1035,15 @@ __global__ void k_reduce_cost(const int32_t *__restrict__ item_range, int n_f, c
     if (inliers) inliers[f] = ni;
 }
 
-// One warp per factor: fixed-order float64 sum of the factor's item partials,
-// then H = L H^t L', b = L b^t with L = [S' ; -D'] (12 x 6).
-__global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const int32_t *__restrict__ item_range,
-                                  int n_f, const double *__restrict__ partials, const int64_t *__restrict__ inl_p,
-                                  double *__restrict__ H, double *__restrict__ b, double *__restrict__ cost,
-                                  int64_t *__restrict__ inliers)
+// One factor's 12x12 system from its summed adjoint-form terms, by one warp:
+// lane j < 28 holds sum j, lane 0 the inlier count; H = L H^t L', b = L b^t with
+// L = [S' ; -D'] (12 x 6) from the factor's T_BA.  Ht, bt, L, G are the warp's
+// scratch (36 + 6 + 72 + 72 doubles, shared memory).  inliers may be null.
+__device__ __forceinline__ void finalize_factor(double s, int64_t ni, const double *T, int lane, double *Ht,
+                                                double *bt, double *L, double *G, double *Hf, double *bf,
+                                                double *cost, int64_t *inliers)
 {
-    constexpr int WPB = 4;
-    __shared__ double sHt[WPB][36], sbt[WPB][6], sL[WPB][72], sG[WPB][72];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int f = blockIdx.x * WPB + warp;
-    if (f >= n_f) return;
-    const int i0 = item_range[2 * f], i1 = item_range[2 * f + 1];
-    double s = 0.0;
-    if (lane < kNT)
-        for (int i = i0; i < i1; ++i) s += partials[(int64_t)i * kNT + lane];
-    int64_t ni = 0;
-    if (lane == 0)
-        for (int i = i0; i < i1; ++i) ni += inl_p[i];
     // scatter the 28 sums into H^t (6x6) and b^t
-    double *Ht = sHt[warp], *bt = sbt[warp], *L = sL[warp], *G = sG[warp];
     if (lane < 6) {
         const int ww[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
         Ht[6 * ww[lane][0] + ww[lane][1]] = s;
@@ -1069,10 +1060,9 @@ __global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const in
     } else if (lane < 27) {
         bt[lane - 21] = s;
     } else if (lane == 27) {
-        cost[f] = s;
+        *cost = s;
     }
     // L rows 0..5 = S' = [[I, [t]x], [0, I]]; rows 6..11 = -D' = -blkdiag(R', R')
-    const double *T = params[f].T;
     for (int e = lane; e < 72; e += 32) {
         const int r = e / 6, c = e % 6;
         double v = 0.0;
@@ -1098,7 +1088,6 @@ __global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const in
         G[e] = x;
     }
     __syncwarp();
-    double *Hf = H + (int64_t)f * 144;
     for (int e = lane; e < 144; e += 32) {  // H = G L'
         const int r = e / 12, c = e % 12;
         if (c < r) continue;
@@ -1112,9 +1101,33 @@ __global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const in
         double x = 0.0;
 #pragma unroll
         for (int k = 0; k < 6; ++k) x += L[6 * lane + k] * bt[k];
-        b[(int64_t)f * 12 + lane] = x;
+        bf[lane] = x;
     }
-    if (lane == 0 && inliers) inliers[f] = ni;
+    if (lane == 0 && inliers) *inliers = ni;
+    __syncwarp();
+}
+
+// One warp per factor: fixed-order float64 sum of the factor's item partials,
+// then the 12x12 system (finalize_factor).
+__global__ void k_reduce_finalize(const PoseParam *__restrict__ params, const int32_t *__restrict__ item_range,
+                                  int n_f, const double *__restrict__ partials, const int64_t *__restrict__ inl_p,
+                                  double *__restrict__ H, double *__restrict__ b, double *__restrict__ cost,
+                                  int64_t *__restrict__ inliers)
+{
+    constexpr int WPB = 4;
+    __shared__ double sHt[WPB][36], sbt[WPB][6], sL[WPB][72], sG[WPB][72];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int f = blockIdx.x * WPB + warp;
+    if (f >= n_f) return;
+    const int i0 = item_range[2 * f], i1 = item_range[2 * f + 1];
+    double s = 0.0;
+    if (lane < kNT)
+        for (int i = i0; i < i1; ++i) s += partials[(int64_t)i * kNT + lane];
+    int64_t ni = 0;
+    if (lane == 0)
+        for (int i = i0; i < i1; ++i) ni += inl_p[i];
+    finalize_factor(s, ni, params[f].T, lane, sHt[warp], sbt[warp], sL[warp], sG[warp], H + (int64_t)f * 144,
+                    b + (int64_t)f * 12, cost + f, inliers ? inliers + f : nullptr);
 }
 
 // ------------------------------------------------------------------ f64 ----
@@ -1280,6 +1293,287 @@ __global__ void __launch_bounds__(kF64Block) k_linearize_f64(const PoseParam *__
     if (tid == 0) *ticket = 0u;
 }
 
+// ------------------------------------------------- device request loop ----
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_sys(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_sys32(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Copy n 32-bit words from global memory (L2, never a stale L1 line) to dst, by one warp.
+__device__ __forceinline__ void warp_copy_cg(uint32_t *dst, const uint32_t *src, int n, int lane)
+{
+    for (int j = lane; j < n; j += 32) dst[j] = __ldcg(src + j);
+}
+
+constexpr int kReqWords = (int)(sizeof(LoopRequest) / 8);
+static_assert(sizeof(LoopRequest) % 8 == 0, "request words");
+
+// The dispatcher (warp 0 of block 0): requests in order, each prepared and its
+// chunks appended to the work queue, until none arrives for idle_ns or the
+// host asks it to stop.  Lane 0 polls the ring (acquire loads at system scope)
+// and the warp reads a request only after lane 0 has seen it and the warp has
+// synchronised.
+__device__ void loop_dispatch(const LoopArgs &a, unsigned long long *sreq, int32_t *skbox, float *sstats,
+                              float *scbox)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long r = a.ctl->next_req;
+    unsigned int tail = a.ctl->item_tail;
+    unsigned long long t_last = globaltimer_ns();
+    int stop = 0;
+    for (;;) {
+        const int s = (int)(r % (unsigned long long)a.slots);
+        const LoopRequest *q = a.req + s;
+        // 0 wait, 1 request r is there, 2 it is there but already answered (a
+        // relaunch after an earlier loop ended), 3 idle limit, 4 stop
+        int what = 0;
+        if (lane == 0) {
+            unsigned int ns = 32;
+            while (what == 0) {
+                if (ld_acquire_sys(&q->seq) == r + 1)
+                    what = ld_relaxed_sys(&a.res[s].done) == r + 1 ? 2 : 1;
+                else if (ld_relaxed_sys32(&a.exit->stop) != 0)
+                    what = 4;
+                else if (globaltimer_ns() - t_last > a.idle_ns)
+                    what = 3;
+                else {
+                    __nanosleep(ns);
+                    if (ns < 512) ns <<= 1;
+                }
+            }
+        }
+        what = __shfl_sync(0xffffffffu, what, 0);
+        __syncwarp();
+        if (what >= 3) {
+            stop = what == 4;
+            break;
+        }
+        if (what == 2) {
+            ++r;
+            t_last = globaltimer_ns();
+            continue;
+        }
+        const unsigned long long *qw = (const unsigned long long *)q;
+        for (int j = lane; j < kReqWords; j += 32) sreq[j] = ld_relaxed_sys(qw + j);
+        __syncwarp();
+        const LoopRequest &R = *(const LoopRequest *)sreq;
+        // the map's voxel box and the frame's statistics and chunk boxes, read
+        // from L2 into shared memory for the pose parameters
+        warp_copy_cg((uint32_t *)skbox, (const uint32_t *)R.map.kbox, 6, lane);
+        warp_copy_cg((uint32_t *)sstats, (const uint32_t *)R.frame.stats, kStatCount, lane);
+        warp_copy_cg((uint32_t *)scbox, (const uint32_t *)R.frame.cbox, 6 * min(R.frame.nchunks, kMaxCullChunks),
+                     lane);
+        __syncwarp();
+        if (lane == 0) {
+            MapDesc m = R.map;
+            FrameDesc f = R.frame;
+            m.kbox = skbox;
+            f.stats = sstats;
+            f.cbox = scbox;
+            PoseParam P;
+#pragma unroll
+            for (int i = 0; i < 12; ++i) P.T[i] = R.T[i];
+            split_pose(P.T, P);
+            P.map = 0;
+            P.frame = 0;
+            finish_param(P, m, f, R.cull);
+            LoopSlotState &S = a.state[s];
+            S.P = P;
+            S.map = R.map;
+            S.frame = R.frame;
+            const int ni = min(max(R.n_items, 0), kLoopMaxItems);
+            S.kind = R.kind;
+            S.n_items = ni;
+            S.chunk = R.chunk;
+            S.done_items = 0u;
+            S.seq = r + 1;
+            for (int k = 0; k < ni; ++k) a.queue[(tail + (unsigned)k) & (a.qcap - 1u)] = make_int2(s, k);
+            tail += (unsigned)ni;
+            __threadfence();
+            st_release_gpu(&a.ctl->item_tail, tail);
+        }
+        __syncwarp();
+        ++r;
+        t_last = globaltimer_ns();
+    }
+    if (lane == 0) {
+        st_release_gpu(&a.ctl->quit, 1u);
+        a.exit->next_req = r;
+        a.exit->status = stop ? (int)VGICP_OK : (int)VGICP_ERR_TIMEOUT;
+        __threadfence_system();
+    }
+}
+
+// A worker warp: chunks from the queue until the dispatcher has ended and no
+// chunk is left (or worker_ns pass without either).
+__device__ void loop_work(const LoopArgs &a, PoseParam &sP, MapDesc &sM, FrameDesc &sF, double *fin)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned int i = 0;
+        if (lane == 0) i = atomicAdd(&a.ctl->item_head, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        int go = 0;
+        if (lane == 0) {
+            const unsigned long long t0 = globaltimer_ns();
+            unsigned int ns = 32;
+            for (;;) {
+                if ((int)(ld_acquire_gpu(&a.ctl->item_tail) - i) > 0) {
+                    go = 1;
+                    break;
+                }
+                if (ld_acquire_gpu(&a.ctl->quit)) {
+                    go = (int)(ld_acquire_gpu(&a.ctl->item_tail) - i) > 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > a.worker_ns) {
+                    atomicExch(&a.ctl->status, (unsigned int)VGICP_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
+            }
+        }
+        go = __shfl_sync(0xffffffffu, go, 0);
+        __syncwarp();
+        if (!go) return;
+        const int2 e = __ldcg(a.queue + (i & (a.qcap - 1u)));
+        LoopSlotState &S = a.state[e.x];
+        __syncwarp();
+        warp_copy_cg((uint32_t *)&sP, (const uint32_t *)&S.P, (int)(sizeof(PoseParam) / 4), lane);
+        warp_copy_cg((uint32_t *)&sM, (const uint32_t *)&S.map, (int)(sizeof(MapDesc) / 4), lane);
+        warp_copy_cg((uint32_t *)&sF, (const uint32_t *)&S.frame, (int)(sizeof(FrameDesc) / 4), lane);
+        const int kind = __ldcg(&S.kind), n_items = __ldcg(&S.n_items), chunk = __ldcg(&S.chunk);
+        const unsigned long long seq = __ldcg(&S.seq);
+        __syncwarp();
+        const PoseParam &P = sP;
+        const MapDesc &m = sM;
+        const FrameDesc &F = sF;
+        WorkItem w;
+        w.unit = e.x;
+        w.start = (int64_t)e.y * chunk;
+        w.count = (int32_t)min((int64_t)chunk, F.n - w.start);
+        const int c0 = (int)(w.start >> F.cshift), c1 = (int)((w.start + w.count - 1) >> F.cshift);
+        const uint32_t span = (c1 - c0 >= 31) ? 0xffffffffu : (((1u << (c1 - c0 + 1)) - 1u) << c0);
+        const bool live = w.count > 0 && (P.cmask & span) != 0u;
+        const int64_t slot_base = (int64_t)e.x * kLoopMaxItems;
+        if (kind == kLoopLinearize) {
+            float acc[kNT];
+#pragma unroll
+            for (int j = 0; j < kNT; ++j) acc[j] = 0.f;
+            int inl = 0;
+            if (live) linearize_points<1, false, kNT, false, LdCG>(P, m, F, w, lane, acc, inl);
+            double mine = 0.0;
+#pragma unroll
+            for (int j = 0; j < kNT; ++j) {
+                float x = acc[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == j) mine = (double)x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) inl += __shfl_xor_sync(0xffffffffu, inl, o);
+            if (lane < kNT) a.partials[(slot_base + e.y) * kNT + lane] = mine;
+            if (lane == kNT) a.counts[slot_base + e.y] = inl;
+        } else {
+            int hits = 0;
+            if (live) {
+                const float4 *__restrict__ pa = F.pa + w.start;
+                for (int j = lane; j < w.count; j += 32) {
+                    const float4 A = __ldcg(pa + j);
+                    int k[3];
+                    float d[3], x[3];
+                    if (point_key_split(P, m, A.x, A.y, A.z, k, d, x) &&
+                        probe<LdCG>(m.keys, m.mask, m.log2cap, pack_key(k[0], k[1], k[2])) >= 0)
+                        ++hits;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
+            if (lane == 0) a.counts[slot_base + e.y] = hits;
+        }
+        __threadfence();
+        unsigned int prev = 0;
+        if (lane == 0) prev = atomicAdd(&S.done_items, 1u);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev + 1u != (unsigned int)n_items) continue;
+        // the request's last chunk: its sums in chunk order, then the result
+        __threadfence();
+        LoopResult *res = a.res + e.x;
+        if (kind == kLoopLinearize) {
+            double s = 0.0;
+            if (lane < kNT)
+                for (int k = 0; k < n_items; ++k) s += __ldcg(a.partials + (slot_base + k) * kNT + lane);
+            int64_t ni = 0;
+            if (lane == 0)
+                for (int k = 0; k < n_items; ++k) ni += __ldcg(a.counts + slot_base + k);
+            finalize_factor(s, ni, P.T, lane, fin, fin + 36, fin + 42, fin + 114, res->H, res->b, &res->cost,
+                            (int64_t *)&res->count);
+        } else if (lane == 0) {
+            long long c = 0;
+            for (int k = 0; k < n_items; ++k) c += __ldcg(a.counts + slot_base + k);
+            res->count = c;
+        }
+        __threadfence_system();
+        __syncwarp();
+        if (lane == 0) st_release_sys(&res->done, seq);
+    }
+}
+
+__global__ void __launch_bounds__(kLoopBlock) k_request_loop(LoopArgs a)
+{
+    constexpr int NW = kLoopBlock / 32;
+    __shared__ PoseParam sP[NW];
+    __shared__ MapDesc sM[NW];
+    __shared__ FrameDesc sF[NW];
+    __shared__ double sFin[NW][186];
+    __shared__ __align__(16) unsigned long long sReq[kReqWords];
+    __shared__ int32_t sKbox[6];
+    __shared__ float sStats[kStatCount];
+    __shared__ float sCbox[6 * kMaxCullChunks];
+    const int wib = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && wib == 0) {
+        loop_dispatch(a, sReq, sKbox, sStats, sCbox);
+        return;
+    }
+    loop_work(a, sP[wib], sM[wib], sF[wib], sFin[wib]);
+}
+
 }  // namespace
 
 void launch_prepare_factors(const int32_t *factor_idx, int n_f, const double *poses, const MapDesc *maps,
@@ -1441,6 +1735,11 @@ void launch_linearize_f64(const PoseParam *param, const MapDesc *maps, const Fra
 {
     k_linearize_f64<<<grid, kF64Block, 0, st>>>(param, maps, frames, n, scratch, ticket, H, b, cost, inliers, nb,
                                                 weighted, rec_key, rec_state);
+}
+
+void launch_request_loop(const LoopArgs &a, int num_sms, cudaStream_t st)
+{
+    k_request_loop<<<num_sms, kLoopBlock, 0, st>>>(a);
 }
 
 }  // namespace vg

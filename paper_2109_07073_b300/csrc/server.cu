@@ -16,6 +16,14 @@
 //     copies each request's result out and wakes its waiter.
 // A request's result does not depend on the batch it ran in: a factor's sums
 // use fixed chunks and a fixed reduction order, and overlap counts are exact.
+//
+// Device-loop mode (options.device_loop): the scheduler thread admits each
+// request (residency as above), writes it into a ring of page-locked,
+// device-mapped request slots and keeps one persistent kernel running that
+// takes requests from the ring as they are published (see the request loop in
+// linearize.cu); finished results appear in the mapped result slots, where the
+// scheduler reads them.  The loop kernel ends on its own after loop_idle_ms
+// without a request and is launched again for the next one.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -31,6 +39,7 @@
 
 #include <cuda_runtime.h>
 
+#include "kernels.cuh"
 #include "vgicp.h"
 
 namespace {
@@ -98,6 +107,30 @@ struct vgicp_server {
     // that live as long as the server (re-admission copies them directly)
     std::vector<char *> slabs;
     size_t slab_cap = 0, slab_off = 0;
+    // device-loop mode
+    bool dloop = false;
+    int chunk = 2048, cull = 1, num_sms = 148;
+    int slots = 0;
+    unsigned int qcap = 0;
+    vg::LoopRequest *h_req = nullptr, *d_req = nullptr;      // mapped ring (host / device views)
+    vg::LoopResult *h_res = nullptr, *d_res = nullptr;
+    vg::LoopExit *h_exit = nullptr, *d_exit = nullptr;
+    vg::LoopControl *d_ctl = nullptr, *h_ctl = nullptr;      // h_ctl: pinned staging of the control words
+    vg::LoopSlotState *d_state = nullptr;
+    double *d_partials = nullptr;
+    long long *d_counts = nullptr;
+    int2 *d_queue = nullptr;
+    cudaStream_t loop_stream = nullptr;
+    cudaEvent_t loop_ev0 = nullptr, loop_ev1 = nullptr;
+    bool loop_running = false;
+    int loop_last_exit = VGICP_OK;
+    int64_t loop_launches = 0;
+    unsigned long long n_pub = 0;                            // requests published so far
+    double idle_ms = 20.0;
+    std::vector<int64_t> slot_ticket;                        // ticket in each slot, -1 when free
+    std::vector<unsigned long long> slot_seq;
+    std::vector<std::pair<int64_t, int64_t>> slot_keys;      // tagged keys the slot's request pins
+    std::vector<int> inflight;                               // slots with a request in flight
 };
 
 namespace {
@@ -420,6 +453,333 @@ void scheduler(vgicp_server *s)
     }
 }
 
+// ------------------------------------------------------- device loop --
+
+// Hand out every finished request of the ring (mutex held).
+bool harvest_slots(vgicp_server *s)
+{
+    bool any = false;
+    const auto now = Clock::now();
+    for (size_t q = 0; q < s->inflight.size();) {
+        const int slot = s->inflight[q];
+        const vg::LoopResult &R = s->h_res[slot];
+        if (__atomic_load_n(&R.done, __ATOMIC_ACQUIRE) != s->slot_seq[slot]) {
+            ++q;
+            continue;
+        }
+        Pending &p = s->reqs[s->slot_ticket[slot]];
+        p.res.status = VGICP_OK;
+        p.res.kind = p.req.kind;
+        if (p.req.kind == VGICP_REQ_LINEARIZE) {
+            std::memcpy(p.res.H, R.H, sizeof(p.res.H));
+            std::memcpy(p.res.b, R.b, sizeof(p.res.b));
+            p.res.cost = R.cost;
+            p.res.count = R.count;
+        } else {
+            const int64_t n = s->objs[tag(p.req.source, false)].n;
+            p.res.count = R.count;
+            p.res.fraction = (double)R.count / (double)n;
+        }
+        p.res.latency_ms = std::chrono::duration<double, std::milli>(now - p.t0).count();
+        p.done = true;
+        s->lat_ms.push_back(p.res.latency_ms);
+        s->objs[s->slot_keys[slot].first].pins--;
+        s->objs[s->slot_keys[slot].second].pins--;
+        s->slot_ticket[slot] = -1;
+        ++s->completed;
+        s->inflight[q] = s->inflight.back();
+        s->inflight.pop_back();
+        any = true;
+    }
+    return any;
+}
+
+// Launch the loop kernel, starting from the oldest request not yet answered (mutex held).
+vgicp_status launch_loop(vgicp_server *s)
+{
+    unsigned long long first = s->n_pub;
+    for (int slot : s->inflight) first = std::min(first, s->slot_seq[slot] - 1);
+    *s->h_ctl = vg::LoopControl{0u, 0u, 0u, 0u, first};
+    s->h_exit->status = VGICP_OK;
+    s->h_exit->next_req = first;
+    cudaEventRecord(s->loop_ev0, s->loop_stream);
+    cudaMemcpyAsync(s->d_ctl, s->h_ctl, sizeof(vg::LoopControl), cudaMemcpyHostToDevice, s->loop_stream);
+    vg::LoopArgs a{};
+    a.req = s->d_req;
+    a.res = s->d_res;
+    a.exit = s->d_exit;
+    a.ctl = s->d_ctl;
+    a.state = s->d_state;
+    a.partials = s->d_partials;
+    a.counts = s->d_counts;
+    a.queue = s->d_queue;
+    a.slots = s->slots;
+    a.qcap = s->qcap;
+    a.idle_ns = (unsigned long long)(s->idle_ms * 1e6);
+    a.worker_ns = a.idle_ns + 1000000000ull;       // the idle limit plus a second
+    vg::launch_request_loop(a, s->num_sms, s->loop_stream);
+    cudaEventRecord(s->loop_ev1, s->loop_stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        s->err = cudaGetErrorString(e);
+        return VGICP_ERR_CUDA;
+    }
+    s->loop_running = true;
+    ++s->loop_launches;
+    ++s->batches;
+    return VGICP_OK;
+}
+
+// Admit request t's objects and write it into the next ring slot (scheduler
+// thread, mutex not held).  VGICP_ERR_BUDGET: defer (nothing was published).
+vgicp_status publish(vgicp_server *s, int64_t t)
+{
+    vgicp_request r;
+    Resident *m, *f;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r = s->reqs[t].req;
+        m = &s->objs[tag(r.target, true)];
+        f = &s->objs[tag(r.source, false)];
+    }
+    const auto ta = Clock::now();
+    vgicp_status st = VGICP_OK;
+    const bool admitting = m->handle < 0 || f->handle < 0;
+    if (admitting) {
+        st = admit(s, *m);
+        if (st == VGICP_OK) {
+            { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
+            st = admit(s, *f);
+            std::lock_guard<std::mutex> lk(s->mu);
+            m->pins--;
+        }
+        // the loop reads the new objects: their copies and builds must be complete
+        if (st == VGICP_OK) st = vgicp_synchronize(s->ctx);
+    }
+    const double admit_ms = std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
+    if (st != VGICP_OK) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->host_admit_ms += admit_ms;
+        return st;
+    }
+    vg::MapDesc md;
+    vg::FrameDesc fd;
+    int64_t n = 0;
+    if (!vg::ctx_descs(s->ctx, m->handle, f->handle, &md, &fd, &n)) return VGICP_ERR_NOT_FOUND;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->host_admit_ms += admit_ms;
+    for (Resident *o : {m, f}) {
+        s->lru.erase({o->last_use, o->key});
+        o->last_use = ++s->clock;
+        s->lru.insert({o->last_use, o->key});
+    }
+    Pending &p = s->reqs[t];
+    if (n == 0) {                      // nothing to run: an empty sum, or Eq. 8 undefined
+        complete(s, t, r.kind == VGICP_REQ_OVERLAP ? VGICP_ERR_EMPTY : VGICP_OK);
+        s->lat_ms.push_back(p.res.latency_ms);
+        ++s->completed;
+        return VGICP_OK;
+    }
+    const int c = vg::item_chunk(n, s->chunk);
+    const int64_t items = (n + c - 1) / c;
+    if (items > vg::kLoopMaxItems) {
+        s->err = "request larger than 128 chunks";
+        complete(s, t, VGICP_ERR_INVALID_ARG);
+        ++s->completed;
+        return VGICP_OK;
+    }
+    const int slot = (int)(s->n_pub % (unsigned long long)s->slots);
+    const unsigned long long seq = ++s->n_pub;
+    vg::LoopRequest &q = s->h_req[slot];
+    q.map = md;
+    q.frame = fd;
+    std::memcpy(q.T, r.T_target_source, sizeof(q.T));
+    q.kind = r.kind == VGICP_REQ_LINEARIZE ? vg::kLoopLinearize : vg::kLoopOverlap;
+    q.n_items = (int32_t)items;
+    q.chunk = c;
+    q.cull = s->cull;
+    __atomic_store_n(&s->h_res[slot].done, 0ull, __ATOMIC_RELAXED);
+    __atomic_store_n(&q.seq, seq, __ATOMIC_RELEASE);      // the request is visible to the loop from here
+    m->pins++;
+    f->pins++;
+    s->slot_ticket[slot] = t;
+    s->slot_seq[slot] = seq;
+    s->slot_keys[slot] = {tag(r.target, true), tag(r.source, false)};
+    s->inflight.push_back(slot);
+    return VGICP_OK;
+}
+
+// Fail every request in flight (mutex held).
+void fail_inflight(vgicp_server *s, vgicp_status st)
+{
+    for (int slot : s->inflight) {
+        complete(s, s->slot_ticket[slot], st);
+        s->objs[s->slot_keys[slot].first].pins--;
+        s->objs[s->slot_keys[slot].second].pins--;
+        s->slot_ticket[slot] = -1;
+        ++s->completed;
+    }
+    s->inflight.clear();
+    s->cv_done.notify_all();
+}
+
+void scheduler_device(vgicp_server *s)
+{
+    std::unique_lock<std::mutex> lk(s->mu);
+    int idle_polls = 0, fruitless = 0;
+    int64_t completed_at_launch = 0;
+    for (;;) {
+        if (harvest_slots(s)) {
+            s->cv_done.notify_all();
+            idle_polls = 0;
+        }
+        if (s->loop_running && cudaStreamQuery(s->loop_stream) != cudaErrorNotReady) {
+            s->loop_running = false;
+            s->loop_last_exit = s->h_exit->status;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, s->loop_ev0, s->loop_ev1) == cudaSuccess) s->device_ms += ms;
+            vg::LoopControl c{};
+            if (cudaMemcpy(&c, s->d_ctl, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess && c.status)
+                s->err = "a worker of the request loop ran out of its wait limit";
+            harvest_slots(s);
+            // a loop that ended with requests in flight and answered none, several times
+            // in a row, will not answer them: fail them instead of relaunching forever
+            fruitless = (!s->inflight.empty() && s->completed == completed_at_launch) ? fruitless + 1 : 0;
+            if (fruitless >= 8) {
+                s->err = "the request loop ended repeatedly without answering the requests in flight";
+                fail_inflight(s, VGICP_ERR_CUDA);
+                fruitless = 0;
+            }
+            s->cv_done.notify_all();
+        }
+        if (s->stop) {
+            // drop what is pending, ask the loop to end, answer what it finished, fail the rest
+            for (int64_t t : s->pending) {
+                complete(s, t, VGICP_ERR_CUDA);
+                ++s->completed;
+            }
+            s->pending.clear();
+            if (s->loop_running) {
+                __atomic_store_n(&s->h_exit->stop, 1, __ATOMIC_RELEASE);
+                lk.unlock();
+                cudaStreamSynchronize(s->loop_stream);
+                lk.lock();
+                s->loop_running = false;
+            }
+            harvest_slots(s);
+            fail_inflight(s, VGICP_ERR_CUDA);
+            return;
+        }
+        // publish pending requests while the ring has room in order
+        const auto tl = Clock::now();
+        bool published = false;
+        while (!s->pending.empty() && s->slot_ticket[s->n_pub % (unsigned long long)s->slots] < 0) {
+            const int64_t t = s->pending.front();
+            s->pending.pop_front();
+            lk.unlock();
+            const vgicp_status st = publish(s, t);
+            lk.lock();
+            if (st == VGICP_ERR_BUDGET) {
+                if (s->inflight.empty()) {             // nothing to wait for: it can never fit
+                    complete(s, t, VGICP_ERR_BUDGET);
+                    ++s->completed;
+                    s->cv_done.notify_all();
+                    continue;
+                }
+                s->pending.push_front(t);              // retry when in-flight requests release objects
+                break;
+            }
+            if (st != VGICP_OK) {
+                complete(s, t, st);
+                ++s->completed;
+            }
+            published = true;
+            s->cv_done.notify_all();
+        }
+        if (published) {
+            s->host_launch_ms += std::chrono::duration<double, std::milli>(Clock::now() - tl).count();
+            int64_t bytes = 0;
+            vgicp_memory_in_use(s->ctx, &bytes);
+            s->resident_bytes = bytes;
+        }
+        if (!s->loop_running && !s->inflight.empty()) {
+            completed_at_launch = s->completed;
+            const vgicp_status st = launch_loop(s);
+            if (st != VGICP_OK) fail_inflight(s, st);  // rather than wait forever
+        }
+        if (!s->inflight.empty()) {
+            // results arrive in host memory: poll, yielding the core, then sleep a little
+            lk.unlock();
+            if (++idle_polls < 2000) std::this_thread::yield();
+            else std::this_thread::sleep_for(std::chrono::microseconds(50));
+            lk.lock();
+        } else {
+            idle_polls = 0;
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        }
+    }
+}
+
+vgicp_status loop_setup(vgicp_server *s, const vgicp_options &ko)
+{
+    s->dloop = true;
+    s->slots = s->opt.loop_slots > 0 ? s->opt.loop_slots : 256;
+    s->idle_ms = s->opt.loop_idle_ms > 0.0 ? s->opt.loop_idle_ms : 20.0;
+    s->chunk = ko.chunk_points > 0 ? ko.chunk_points : 2048;
+    s->cull = ko.linearize_cull;
+    unsigned int q = 1;
+    while (q < (unsigned int)s->slots * (unsigned int)vg::kLoopMaxItems) q <<= 1;
+    s->qcap = q;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t S = (size_t)s->slots;
+    if (cudaHostAlloc((void **)&s->h_req, S * sizeof(vg::LoopRequest), cudaHostAllocMapped) ||
+        cudaHostAlloc((void **)&s->h_res, S * sizeof(vg::LoopResult), cudaHostAllocMapped) ||
+        cudaHostAlloc((void **)&s->h_exit, sizeof(vg::LoopExit), cudaHostAllocMapped) ||
+        cudaHostAlloc((void **)&s->h_ctl, sizeof(vg::LoopControl), cudaHostAllocDefault) ||
+        cudaHostGetDevicePointer((void **)&s->d_req, s->h_req, 0) ||
+        cudaHostGetDevicePointer((void **)&s->d_res, s->h_res, 0) ||
+        cudaHostGetDevicePointer((void **)&s->d_exit, s->h_exit, 0) ||
+        cudaMalloc((void **)&s->d_ctl, sizeof(vg::LoopControl)) ||
+        cudaMalloc((void **)&s->d_state, S * sizeof(vg::LoopSlotState)) ||
+        cudaMalloc((void **)&s->d_partials, S * vg::kLoopMaxItems * 28 * sizeof(double)) ||
+        cudaMalloc((void **)&s->d_counts, S * vg::kLoopMaxItems * sizeof(long long)) ||
+        cudaMalloc((void **)&s->d_queue, (size_t)s->qcap * sizeof(int2)) ||
+        cudaStreamCreateWithFlags(&s->loop_stream, cudaStreamNonBlocking) ||
+        cudaEventCreate(&s->loop_ev0) || cudaEventCreate(&s->loop_ev1)) {
+        cudaGetLastError();
+        return VGICP_ERR_OOM;
+    }
+    std::memset(s->h_req, 0, S * sizeof(vg::LoopRequest));
+    std::memset(s->h_res, 0, S * sizeof(vg::LoopResult));
+    std::memset(s->h_exit, 0, sizeof(vg::LoopExit));
+    s->slot_ticket.assign(S, -1);
+    s->slot_seq.assign(S, 0ull);
+    s->slot_keys.assign(S, {0, 0});
+    return VGICP_OK;
+}
+
+void loop_free(vgicp_server *s)
+{
+    if (s->loop_stream) {
+        if (s->h_exit) __atomic_store_n(&s->h_exit->stop, 1, __ATOMIC_RELEASE);
+        cudaStreamSynchronize(s->loop_stream);
+        cudaStreamDestroy(s->loop_stream);
+    }
+    if (s->loop_ev0) cudaEventDestroy(s->loop_ev0);
+    if (s->loop_ev1) cudaEventDestroy(s->loop_ev1);
+    cudaFreeHost(s->h_req);
+    cudaFreeHost(s->h_res);
+    cudaFreeHost(s->h_exit);
+    cudaFreeHost(s->h_ctl);
+    cudaFree(s->d_ctl);
+    cudaFree(s->d_state);
+    cudaFree(s->d_partials);
+    cudaFree(s->d_counts);
+    cudaFree(s->d_queue);
+}
+
 // Room for `bytes` in the page-locked slabs, or null when no page-locked memory
 // can be had.  A new slab is pinned without the lock held (pinning 256 MB takes
 // tens of milliseconds, which the scheduler thread must not wait for).
@@ -498,7 +858,9 @@ vgicp_status vgicp_server_create(vgicp_server **out, const vgicp_server_options 
     if (s->opt.max_batch_requests <= 0) s->opt.max_batch_requests = 4096;
     if (s->opt.max_batch_points <= 0) s->opt.max_batch_points = (int64_t)1 << 27;
     if (s->opt.lanes <= 0) s->opt.lanes = 2;
-    if (s->opt.lanes > 4 || s->opt.hbm_budget_bytes < 0) {
+    if (s->opt.lanes > 4 || s->opt.hbm_budget_bytes < 0 || s->opt.device_loop < 0 || s->opt.device_loop > 1 ||
+        s->opt.loop_slots < 0 || s->opt.loop_slots > 1024 || !(s->opt.loop_idle_ms >= 0.0) ||
+        s->opt.loop_idle_ms > 60000.0) {
         delete s;
         return VGICP_ERR_INVALID_ARG;
     }
@@ -508,10 +870,26 @@ vgicp_status vgicp_server_create(vgicp_server **out, const vgicp_server_options 
     if (kopt) ko = *kopt;
     ko.precision = VGICP_PREC_F32;
     ko.hbm_budget_bytes = s->opt.hbm_budget_bytes;
+    if (s->opt.device_loop && (ko.neighbors > 1 || ko.count_weighted)) {
+        delete s;
+        return VGICP_ERR_INVALID_ARG;
+    }
     vgicp_status st = vgicp_create(&s->ctx, &ko, nullptr);
     if (st != VGICP_OK) {
         delete s;
         return st;
+    }
+    if (s->opt.device_loop) {
+        st = loop_setup(s, ko);
+        if (st != VGICP_OK) {
+            loop_free(s);
+            vgicp_destroy(s->ctx);
+            delete s;
+            return st;
+        }
+        s->thr = std::thread(scheduler_device, s);
+        *out = s;
+        return VGICP_OK;
     }
     for (int li = 0; li < s->nl; ++li) {
         s->lanes[li].cb = {s, li};
@@ -537,6 +915,13 @@ vgicp_status vgicp_server_destroy(vgicp_server *s)
     }
     s->cv_work.notify_all();
     s->thr.join();
+    if (s->dloop) {
+        loop_free(s);
+        vgicp_destroy(s->ctx);
+        for (char *p : s->slabs) cudaFreeHost(p);
+        delete s;
+        return VGICP_OK;
+    }
     for (int li = 0; li < s->nl; ++li) cudaStreamSynchronize(s->lanes[li].stream);
     vgicp_set_lane(s->ctx, 0, nullptr);
     vgicp_destroy(s->ctx);
@@ -703,5 +1088,21 @@ vgicp_status vgicp_server_reset_stats(vgicp_server *s)
 }
 
 const char *vgicp_server_last_error(const vgicp_server *s) { return s ? s->err.c_str() : "null server"; }
+
+vgicp_status vgicp_server_loop_state(vgicp_server *s, int32_t *running, int32_t *last_exit, int64_t *launches)
+{
+    if (!s || !s->dloop) return VGICP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    bool run = s->loop_running;
+    int last = s->loop_last_exit;
+    if (run && cudaStreamQuery(s->loop_stream) != cudaErrorNotReady) {   // ended since the scheduler looked
+        run = false;
+        last = s->h_exit->status;
+    }
+    if (running) *running = run ? 1 : 0;
+    if (last_exit) *last_exit = last;
+    if (launches) *launches = s->loop_launches;
+    return VGICP_OK;
+}
 
 }  // extern "C"

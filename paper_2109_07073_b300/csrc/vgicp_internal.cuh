@@ -175,6 +175,19 @@ __device__ __forceinline__ void unpack_key(uint64_t key, int &kx, int &ky, int &
     kz = (int)(key & 0x1FFFFF) - kKeyOffset;
 }
 
+// Load policies of the gather helpers: the read-only (non-coherent) data path
+// for kernels whose inputs cannot change while they run, and L2-only loads for
+// the persistent request loop, which reads objects made resident (by other
+// kernels, into memory other objects may have used before) after it started.
+struct LdNC {
+    template <class T>
+    __device__ __forceinline__ static T ld(const T *p) { return __ldg(p); }
+};
+struct LdCG {
+    template <class T>
+    __device__ __forceinline__ static T ld(const T *p) { return __ldcg(p); }
+};
+
 // Multiplicative (Fibonacci) hashing: top log2cap bits of key * 2^64/phi.
 __device__ __forceinline__ uint32_t hash_slot(uint64_t key, uint32_t log2cap)
 {
@@ -182,10 +195,11 @@ __device__ __forceinline__ uint32_t hash_slot(uint64_t key, uint32_t log2cap)
 }
 
 // Continue a probe for key from slot s (the caller has checked the slots before).
+template <class L = LdNC>
 __device__ __forceinline__ int probe_from(const uint64_t *__restrict__ keys, uint32_t mask, uint64_t key, uint32_t s)
 {
     for (uint32_t i = 0; i < mask; ++i) {
-        const uint64_t k = __ldg(keys + s);
+        const uint64_t k = L::ld(keys + s);
         if (k == key) return (int)s;
         if (k == kEmptyKey) return -1;
         s = (s + 1) & mask;
@@ -195,12 +209,13 @@ __device__ __forceinline__ int probe_from(const uint64_t *__restrict__ keys, uin
 
 // Slot of key in the map, or -1.  Linear probing; the table always holds an
 // empty slot (load <= 2/3), so the loop ends at the first empty slot.
+template <class L = LdNC>
 __device__ __forceinline__ int probe(const uint64_t *__restrict__ keys, uint32_t mask, uint32_t log2cap,
                                      uint64_t key)
 {
     uint32_t s = hash_slot(key, log2cap);
     for (uint32_t i = 0; i <= mask; ++i) {
-        const uint64_t k = __ldg(keys + s);
+        const uint64_t k = L::ld(keys + s);
         if (k == key) return (int)s;
         if (k == kEmptyKey) return -1;
         s = (s + 1) & mask;
