@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--f64-steps", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-legs", action="store_true",
+                   help="only the paper-scale step (no uneven-factor and serving legs)")
     p.add_argument("--profile-only", action="store_true", help="run warm-up and timed steps only (for ncu)")
     p.add_argument("--uneven", action="store_true",
                    help="the batched uneven-factor workload: one linearisation of 10,000 factors of 2,000-60,000 "
@@ -74,6 +76,12 @@ def parse():
     p.add_argument("--serving-requests", type=int, default=50000)
     p.add_argument("--serving-rates", default="2000,5000,10000,20000")
     p.add_argument("--serving-budgets-gb", default="40,2")
+    p.add_argument("--precision-split", action="store_true",
+                   help="the precision split: uneven factors plus 200 dense 120,000-point frames at 0.25 m, all "
+                        "three paths against the FP64 oracle; writes reports/precision_split.json")
+    p.add_argument("--dense-frames", type=int, default=200)
+    p.add_argument("--split-sample", type=int, default=200)
+    p.add_argument("--report-dir", default=os.path.join(ROOT, "reports"))
     return p.parse_args()
 
 
@@ -555,11 +563,42 @@ def run_ours(a):
         "clocks": clocks,
         "inliers_total": int(inl.sum()),
     }
+    ctx.close()
+    if rank == 0 and world == 1 and not a.no_legs:
+        # the other single-GPU workloads of the metric, each in its own short leg
+        w = uneven_data(a)
+        u = uneven_leg(a, w)
+        res["uneven"] = {k: u[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "direct_ms",
+                                           "graph_iteration_ms", "kernel_ms", "factors_per_s", "autotuned",
+                                           "plain_f64", "roofline", "clocks") if k in u}
+        covs = gpu_covariances(w)
+        n_req, rate = 10000, 10000.0
+        runs = []
+        for dl in (True, False):
+            runs += serving_runs(w, covs, 4000, n_req, [rate], [40.0], dl, closed=False)
+        res["serving"] = {"workload": f"{n_req} requests (90 % linearise, 10 % overlap) at Poisson {rate:.0f} req/s, "
+                                      f"{len(w.frames)} voxelmaps at 0.5/1/2 m, 4,000 distinct sources of "
+                                      "2,000-60,000 points, 40 GB budget (everything resident)",
+                          "runs": runs}
+    rp = os.path.join(ROOT, "reports", "precision_split.json")
+    if rank == 0 and os.path.exists(rp):
+        # the precision split runs on its own (python bench.py --precision-split: 200 dense frames and
+        # the oracle on hundreds of factors take minutes of host time); its committed report
+        with open(rp) as fh:
+            rep_ = json.load(fh)
+        res["precision_split"] = {
+            "report": "reports/precision_split.json", "made_by": "python bench.py --precision-split",
+            "errors_vs_oracle": {wl: {p_: {q: v[p_][q]["max"] for q in ("H", "b", "cost")} |
+                                      {"p99_H": v[p_]["H"]["p99"], "inlier_mismatches": v[p_]["inlier_mismatches"]}
+                                      for p_ in ("f32", "f32_comp", "f64")}
+                                 for wl, v in ((k, x["paths"]) for k, x in rep_["workloads"].items())},
+            "checked_factors": {k: x["checked_factors"] for k, x in rep_["workloads"].items()}}
     if rank == 0 and not a.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(pts, poses, tgt, src)
+        one = cpu_baseline(pts, poses, tgt, src, cpu_seconds=8.0, cores=1)
+        res["cpu_baseline"]["one_core"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
     if rank == 0:
         print(json.dumps(res), flush=True)
-    ctx.close()
 
 
 # ---------------------------------------------------------------------------
@@ -632,12 +671,12 @@ def _time_oracle_bounded(jobs, cores, wall_seconds):
     return state["pts"] / wall, wall, state["done"]
 
 
-def cpu_baseline(pts, poses, tgt, src, cpu_seconds=20.0):
-    """The FP64 oracle (single-threaded per factor, factors spread over all host cores)
-    on the workload's factors in a seeded random order, for about cpu_seconds of core
-    time (wall x cores); a first untimed pass of 4 factors per core brings the cores
-    up to load."""
-    cores = os.cpu_count() or 1
+def cpu_baseline(pts, poses, tgt, src, cpu_seconds=20.0, cores=None):
+    """The FP64 oracle (single-threaded per factor, factors spread over all host cores,
+    or over `cores` of them) on the workload's factors in a seeded random order, for
+    about cpu_seconds of core time (wall x cores); a first untimed pass of 4 factors
+    per core brings the cores up to load."""
+    cores = cores or os.cpu_count() or 1
     order = dg.Stream(7).permutation(len(tgt))
     jobs = _OracleJobs(pts, poses, tgt, src).jobs(order)
     _time_oracle(jobs[-4 * cores:], cores)
@@ -694,7 +733,19 @@ def run_reference(a):
 # batched uneven factors
 # ---------------------------------------------------------------------------
 
+def uneven_data(a):
+    return dg.uneven_workload(n_frames=a.uneven_frames, n_factors=a.uneven_factors,
+                              workers=min(16, os.cpu_count() or 1))
+
+
 def run_uneven(a):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    print(json.dumps(uneven_leg(a, uneven_data(a))), flush=True)
+
+
+def uneven_leg(a, w):
     """One Gauss-Newton iteration's linearisation of a batch of uneven factors:
     source sizes log-uniform in 2,000-60,000 points, targets from a pool of
     voxelmaps (20,000 points each) at 0.5, 1 or 2 m, each source a subsample of
@@ -703,11 +754,6 @@ def run_uneven(a):
     import torch
 
     import paper_2109_07073_b300 as vg
-    rank = int(os.environ.get("RANK", 0))
-    if rank != 0:
-        return
-    w = dg.uneven_workload(n_frames=a.uneven_frames, n_factors=a.uneven_factors,
-                           workers=min(16, os.cpu_count() or 1))
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = vg.Context(stream=stream)
@@ -748,7 +794,7 @@ def run_uneven(a):
             ctx.plan_linearize(plan, w.poses, out=out)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-        return
+        return {}
     res_t = {}
     ctx.kernel_timing_reset()          # the direct calls' kernel launches are timed (graph launches are not)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -800,9 +846,10 @@ def run_uneven(a):
                         "frac": ach / hbm, "traffic": None, "peak_source": peak_kind,
                         "algorithmic_bytes_per_launch": int(lin_bytes)},
            "clocks": clk.summary()}
-    print(json.dumps(res), flush=True)
     ctx.plan_destroy(plan)
     ctx.close()
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -869,41 +916,35 @@ def run_optimize(a):
 # serving loop
 # ---------------------------------------------------------------------------
 
-def run_serving(a):
+def serving_runs(w, covs, n_sources, n_req, rates, budgets_gb, device_loop, seed=5050, closed=True):
     """Poisson streams of linearise (90 %) and overlap (10 %) requests of uneven
-    size through the serving loop, at each rate and device-memory budget.
-    Targets: a pool of raycast frames subsampled to 20,000 points at 0.5, 1 or
-    2 m; sources: distinct subsamples (log-uniform 2,000-60,000 points) of frames
-    within 10 m of their target.  Requests draw (target, source) pairs of that
-    set uniformly; latency is submit-to-completion on the host clock."""
-    import torch
-
+    size through the server, at each rate and device-memory budget.  Targets:
+    the workload's pool of raycast frames subsampled to 20,000 points at 0.5, 1
+    or 2 m; sources: its first n_sources distinct subsamples (log-uniform
+    2,000-60,000 points) of frames within 10 m of their target.  Requests draw
+    sources uniformly; latency is submit-to-completion on the host clock.
+    device_loop: the device-resident request loop, else host-launched batches."""
     import paper_2109_07073_b300 as vg
-    rank = int(os.environ.get("RANK", 0))
-    if rank != 0:
-        return
-    w = dg.uneven_workload(n_frames=a.serving_maps, n_factors=a.serving_sources,
-                           workers=min(16, os.cpu_count() or 1))
-    with vg.Context() as ctx:                           # per-point covariances (GPU kNN) of every frame
-        covs = [ctx.estimate_covariances(torch.from_numpy(f).cuda(), 10, 1e-3).cpu().numpy() for f in w.frames]
-    n_src_pts = np.array([len(i) for i in w.factor_idx])
-    rng = dg.Stream(5050)
-    n_req = a.serving_requests
-    pick = np.floor(rng.uniform(n_req, 0, a.serving_sources)).astype(np.int64)
+    n_src_pts = np.array([len(i) for i in w.factor_idx[:n_sources]])
+    rng = dg.Stream(seed)
+    pick = np.floor(rng.uniform(n_req, 0, n_sources)).astype(np.int64)
     kinds = np.where(rng.uniform(n_req) < 0.9, vg.VGICP_REQ_LINEARIZE, vg.VGICP_REQ_OVERLAP)
-    T = [None] * a.serving_sources
-    for f in range(a.serving_sources):
+    T = [None] * n_sources
+    for f in range(n_sources):
         t, j = int(w.factor_target[f]), int(w.factor_frame[f])
         Ti = np.linalg.inv(np.vstack([w.poses[t], [0, 0, 0, 1]]))
         T[f] = (Ti @ np.vstack([w.poses[j], [0, 0, 0, 1]]))[:3]
     T_all = np.stack(T)
+    n_lin = int((kinds == vg.VGICP_REQ_LINEARIZE).sum())
+    pts = int(n_src_pts[pick].sum())
+    mode = "device loop" if device_loop else "host batches"
     runs = []
-    for budget_gb in [float(x) for x in a.serving_budgets_gb.split(",")]:
-        with vg.Server(hbm_budget_bytes=int(budget_gb * 2**30), lanes=2) as srv:
+    for budget_gb in budgets_gb:
+        with vg.Server(hbm_budget_bytes=int(budget_gb * 2**30), lanes=2, device_loop=device_loop) as srv:
             for t in range(len(w.frames)):
                 ix = w.target_idx[t]
                 srv.put_map(t, w.frames[t][ix], covs[t][ix], float(w.target_res[t]))
-            for f in range(a.serving_sources):
+            for f in range(n_sources):
                 j, ix = int(w.factor_frame[f]), w.factor_idx[f]
                 srv.put_frame(f, w.frames[j][ix], covs[j][ix])
 
@@ -911,27 +952,26 @@ def run_serving(a):
                 f = int(pick[k])
                 return srv.submit(int(kinds[k]), int(w.factor_target[f]), f, T[f])
 
-            # warm: every source once (admits what the budget holds), then peak throughput:
-            # all requests submitted at once
-            for tk in [submit(k) for k in range(min(n_req, a.serving_sources))]:
+            # warm: every source once (admits what the budget holds)
+            for tk in [submit(k) for k in range(min(n_req, n_sources))]:
                 srv.wait(tk, 600.0)
-            srv.reset_stats()
-            t0 = time.perf_counter()
-            tks = srv.submit_batch(kinds, w.factor_target[pick], pick, T_all[pick])
-            srv.wait_batch(tks, 600.0)
-            wall = time.perf_counter() - t0
-            st = srv.stats()
-            n_lin = int((kinds == vg.VGICP_REQ_LINEARIZE).sum())
-            pts = int(n_src_pts[pick].sum())
-            runs.append({"budget_gb": budget_gb, "rate": "closed (all submitted in one batch)",
-                         "requests_per_s": n_req / wall, "factors_per_s": n_lin / wall,
-                         "point_correspondences_per_s": pts / wall, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-                         "max_ms": st.max_ms, "mean_batch_requests": st.mean_batch_requests,
-                         "evictions": st.evictions, "admissions": st.admissions,
-                         "resident_gb": st.resident_bytes / 2**30, "host_launch_ms": st.host_launch_ms,
-                         "host_finish_ms": st.host_finish_ms, "device_ms": st.device_ms, "wall_ms": wall * 1e3,
-                         "host_admit_ms": st.host_admit_ms, "host_enqueue_ms": st.host_enqueue_ms})
-            for rate in [float(x) for x in a.serving_rates.split(",")]:
+            if closed:      # peak throughput: all requests submitted at once
+                srv.reset_stats()
+                t0 = time.perf_counter()
+                tks = srv.submit_batch(kinds, w.factor_target[pick], pick, T_all[pick])
+                srv.wait_batch(tks, 600.0)
+                wall = time.perf_counter() - t0
+                st = srv.stats()
+                runs.append({"mode": mode, "budget_gb": budget_gb, "rate": "closed (all submitted in one batch)",
+                             "requests": n_req, "requests_per_s": n_req / wall, "factors_per_s": n_lin / wall,
+                             "point_correspondences_per_s": pts / wall, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                             "max_ms": st.max_ms, "mean_batch_requests": st.mean_batch_requests,
+                             "evictions": st.evictions, "admissions": st.admissions,
+                             "resident_gb": st.resident_bytes / 2**30, "host_launch_ms": st.host_launch_ms,
+                             "host_finish_ms": st.host_finish_ms, "device_ms": st.device_ms,
+                             "wall_ms": wall * 1e3, "host_admit_ms": st.host_admit_ms,
+                             "host_enqueue_ms": st.host_enqueue_ms})
+            for rate in rates:
                 gaps = -np.log(1.0 - rng.uniform(n_req)) / rate      # exponential inter-arrival times
                 arrive = np.cumsum(gaps)
                 srv.reset_stats()
@@ -950,22 +990,188 @@ def run_serving(a):
                 srv.wait_batch(tks, 600.0)
                 wall = time.perf_counter() - t0
                 st = srv.stats()
-                runs.append({"budget_gb": budget_gb, "rate": rate, "requests_per_s": n_req / wall,
-                             "factors_per_s": n_lin / wall, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-                             "max_ms": st.max_ms, "mean_batch_requests": st.mean_batch_requests,
-                             "evictions": st.evictions, "admissions": st.admissions,
-                             "resident_gb": st.resident_bytes / 2**30,
+                runs.append({"mode": mode, "budget_gb": budget_gb, "rate": rate, "requests": n_req,
+                             "requests_per_s": n_req / wall, "factors_per_s": n_lin / wall,
+                             "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": st.max_ms,
+                             "mean_batch_requests": st.mean_batch_requests, "evictions": st.evictions,
+                             "admissions": st.admissions, "resident_gb": st.resident_bytes / 2**30,
                              "submit_lag_p99_ms": float(np.percentile(lag, 99) * 1e3)})
+    return runs
+
+
+def gpu_covariances(w):
+    """Per-point covariances of every frame of the workload (GPU kNN, k = 10)."""
+    import torch
+
+    import paper_2109_07073_b300 as vg
+    with vg.Context() as ctx:
+        return [ctx.estimate_covariances(torch.from_numpy(f).cuda(), 10, 1e-3).cpu().numpy() for f in w.frames]
+
+
+def run_serving(a):
+    """The serving workload at every rate and budget, in both server modes."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    w = dg.uneven_workload(n_frames=a.serving_maps, n_factors=a.serving_sources,
+                           workers=min(16, os.cpu_count() or 1))
+    covs = gpu_covariances(w)
+    rates = [float(x) for x in a.serving_rates.split(",")]
+    budgets = [float(x) for x in a.serving_budgets_gb.split(",")]
+    runs = []
+    for dl in (True, False):
+        runs += serving_runs(w, covs, a.serving_sources, a.serving_requests, rates, budgets, dl)
     peak = runs[0]
     res = {"metric": "factors/s (serving loop, closed)", "value": peak["factors_per_s"], "unit": "factors/s",
            "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded urban-loop LiDAR raycasts)",
-           "config": {"workload": f"serving loop: {n_req} requests (90 % linearise, 10 % overlap), "
+           "config": {"workload": f"serving loop: {a.serving_requests} requests (90 % linearise, 10 % overlap), "
                                   f"{a.serving_maps} voxelmaps, {a.serving_sources} distinct sources of "
                                   "2,000-60,000 points, Poisson arrivals",
-                      "maps": a.serving_maps, "sources": a.serving_sources, "requests": n_req},
+                      "maps": a.serving_maps, "sources": a.serving_sources, "requests": a.serving_requests},
            "latency_ms": {"p50": peak["p50_ms"], "p99": peak["p99_ms"]}, "runs": runs}
     print(json.dumps(res), flush=True)
+
+
+def err_metric(X, Xref, S):
+    """max_i |X_i - Xref_i| / S_i with S_i the sum of |per-point contributions| of
+    entry i (entries with S_i = 0 must match exactly, else the error is infinite)."""
+    X, Xref, S = (np.asarray(v, dtype=np.float64).ravel() for v in (X, Xref, S))
+    d = np.abs(X - Xref)
+    z = S == 0
+    if np.any(d[z] != 0):
+        return float("inf")
+    return float(np.max(d[~z] / S[~z])) if np.any(~z) else 0.0
+
+
+def run_precision_split(a):
+    """The precision split: the 10,000 uneven factors plus 200 dense frames (a
+    128-ring x 1,024-column LiDAR, 120,000 points, 0.25 m voxels) with factors
+    (i, i+1) and (i, i+2).  Every factor is linearised by the batched float32 path
+    (plain and float32-pair transform) and the plain float64 path; every dense
+    factor and a seeded sample of uneven factors are recomputed by the FP64 oracle.
+    Per workload and path: err(H), err(b), err(cost) (max, p99, median over the
+    checked factors), inlier mismatches, and the time of each path on the whole
+    batch.  Covariances come from the oracle (k = 10) and are the shared input of
+    both sides.  The report goes to reports/precision_split.json."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    import paper_2109_07073_b300 as vg
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t_start = time.perf_counter()
+    dense = dg.graph_workload(seed=dg.config_seed(4), n_frames=a.dense_frames, spacing=4.0, n_points=120000,
+                              lidar=dg.Lidar(rings=128), resolution=0.25, workers=min(cores, 32))
+    w = uneven_data(a)
+    t_gen = time.perf_counter() - t_start
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        dcov = list(ex.map(oracle.covariances, dense.points))
+        ucov = list(ex.map(oracle.covariances, w.frames))
+    t_cov = time.perf_counter() - t_start - t_gen
+    nd = len(dense.points)
+    pairs = [(i, i + 1) for i in range(nd - 1)] + [(i, i + 2) for i in range(nd - 2)]
+    report = {"workloads": {}, "host_cores": cores, "generation_s": t_gen, "oracle_covariances_s": t_cov}
+    ctx = vg.Context()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def run_paths(factors, poses, n_pts):
+        out, times = {}, {}
+        for name, prec in (("f32", vg.VGICP_PREC_F32), ("f32_comp", vg.VGICP_PREC_F32_COMP),
+                           ("f64", vg.VGICP_PREC_F64)):
+            ctx.set_options(precision=prec)
+            res = ctx.linearize(factors, poses)          # warm-up, then one timed pass
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record()
+            res = ctx.linearize(factors, poses)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name] = res
+            times[name] = {"ms": ms, "factors_per_s": len(factors) / (ms / 1e3),
+                           "point_correspondences_per_s": n_pts / (ms / 1e3)}
+        ctx.set_options(precision=vg.VGICP_PREC_F32)
+        return out, times
+
+    def summarise(out, refs, idx):
+        tol = {"f32": 1e-4, "f32_comp": 1e-4, "f64": 1e-5}
+        summ = {}
+        for name, (H, b, cost, inl) in out.items():
+            e = {"H": [], "b": [], "cost": []}
+            bad = 0
+            for k, L in zip(idx, refs):
+                bad += int(inl[k] != L.inliers)
+                e["H"].append(err_metric(H[k], L.H, L.SH))
+                e["b"].append(err_metric(b[k], L.b, L.Sb))
+                e["cost"].append(abs(cost[k] - L.cost) / L.Scost if L.Scost > 0 else abs(cost[k] - L.cost))
+            summ[name] = {nm: {"max": float(np.max(v)), "p99": float(np.percentile(v, 99)),
+                               "median": float(np.median(v))} for nm, v in e.items()}
+            summ[name]["inlier_mismatches"] = bad
+            summ[name]["within_tolerance"] = bool(max(max(v) for v in e.values()) <= tol[name] and bad == 0)
+            summ[name]["tolerance"] = tol[name]
+        return summ
+
+    # dense frames
+    fr = np.array([ctx.add_frame(p, c) for p, c in zip(dense.points, dcov)], np.int64)
+    maps = ctx.build_voxelmaps(fr, 0.25)
+    tgt = np.array([t for t, _ in pairs])
+    src = np.array([s_ for _, s_ in pairs])
+    f = vg.make_factors(maps[tgt], fr[src], tgt, src)
+    n_pts = int(sum(dense.points[s_].shape[0] for s_ in src))
+    out, times = run_paths(f, dense.poses, n_pts)
+    ctx.release_many(np.concatenate([fr, maps]))
+
+    def dref(k):
+        t, s_ = pairs[k]
+        vm = oracle.voxelmap(dense.points[t], dcov[t], 0.25)
+        return oracle.linearize(vm, dense.points[s_], dcov[s_], oracle.relative_pose(dense.poses[t], dense.poses[s_]))
+
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        refs = list(ex.map(dref, range(len(pairs))))
+    report["workloads"]["dense"] = {
+        "frames": nd, "points_per_frame_min": int(min(p.shape[0] for p in dense.points)),
+        "resolution_m": 0.25, "factors": len(pairs), "checked_factors": len(pairs), "paths": summarise(out, refs, range(len(pairs))),
+        "time": times}
+    # uneven factors
+    maps = np.full(len(w.frames), -1, np.int64)
+    for r in sorted(set(w.target_res.tolist())):
+        ts = np.nonzero(w.target_res == r)[0]
+        tf = [ctx.add_frame(w.frames[t][w.target_idx[t]], ucov[t][w.target_idx[t]]) for t in ts]
+        maps[ts] = ctx.build_voxelmaps(tf, float(r))
+        ctx.release_many(tf)
+    srcs = [ctx.add_frame(w.frames[int(w.factor_frame[q])][w.factor_idx[q]],
+                          ucov[int(w.factor_frame[q])][w.factor_idx[q]]) for q in range(len(w.factor_idx))]
+    f = vg.make_factors(maps[w.factor_target], srcs, w.factor_target, w.factor_frame)
+    n_pts = int(sum(len(i) for i in w.factor_idx))
+    out, times = run_paths(f, w.poses, n_pts)
+    ctx.close()
+    pick = np.sort(dg.Stream(404).choose(len(f), min(a.split_sample, len(f))))
+
+    def uref(q):
+        t, j = int(w.factor_target[q]), int(w.factor_frame[q])
+        vm = oracle.voxelmap(w.frames[t][w.target_idx[t]], ucov[t][w.target_idx[t]], float(w.target_res[t]))
+        return oracle.linearize(vm, w.frames[j][w.factor_idx[q]], ucov[j][w.factor_idx[q]],
+                                oracle.relative_pose(w.poses[t], w.poses[j]))
+
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        refs = list(ex.map(uref, pick))
+    report["workloads"]["uneven"] = {"factors": len(f), "points": n_pts, "checked_factors": len(pick),
+                                     "paths": summarise(out, refs, pick), "time": times}
+    report["wall_s"] = time.perf_counter() - t_start
+    os.makedirs(a.report_dir, exist_ok=True)
+    with open(os.path.join(a.report_dir, "precision_split.json"), "w") as fh:
+        json.dump(report, fh, indent=1)
+    line = {"metric": "relative error vs the FP64 oracle (precision split)", "value": max(
+        report["workloads"][k]["paths"]["f32"]["H"]["max"] for k in ("dense", "uneven")), "unit": "err(H) max, f32",
+        "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic (seeded urban-loop LiDAR raycasts)",
+        "config": {"workload": f"precision split: {len(f)} uneven factors + {nd} dense frames of 120,000 points at "
+                               "0.25 m"}, "report": report}
+    print(json.dumps(line), flush=True)
 
 
 def run_single(a):
@@ -1042,6 +1248,8 @@ def main():
         run_uneven(a)
     elif a.optimize:
         run_optimize(a)
+    elif a.precision_split:
+        run_precision_split(a)
     else:
         run_ours(a)
 
