@@ -507,14 +507,21 @@ def run_ours(a):
     roof_lin = {"bound": "hbm", "kernel": "linearize_f32", "achieved": lin_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": lin_gbs / hbm, "traffic": dram_traffic("linearize_f32"), "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(lin_bytes)}
+    # overlap matrix: 12 B of source coordinates per point lookup performed (points of the live
+    # chunks of the pairs not culled); the floor's 21 flops per lookup give the ALU view
+    ov_bytes = 12 * lookups_live
+    ov_gbs = ov_bytes / (kernel_ms["overlap_matrix"] / 1e3) / 1e9
+    roof_ov = {"bound": "hbm", "kernel": "overlap_matrix", "achieved": ov_gbs, "peak": hbm, "unit": "GB/s",
+               "frac": ov_gbs / hbm, "traffic": dram_traffic("overlap_matrix"), "peak_source": peak_kind,
+               "algorithmic_bytes_per_launch": int(ov_bytes), "lookups_per_launch": int(lookups_live)}
+    flops = 21.0 * lookups_live
+    ach_f = flops / (kernel_ms["overlap_matrix"] / 1e3) / 1e12
+    roof_ov_alu = {"bound": "alu", "kernel": "overlap_matrix", "achieved": ach_f, "peak": fp32_peak,
+                   "unit": "TFLOP/s", "frac": ach_f / fp32_peak,
+                   "peak_source": "FP32 lanes x 2 x max SM clock (SMs x 128 x 2 x %.0f MHz)" % sm_max,
+                   "algorithmic_flops_per_launch": flops}
     if dom == 1:
-        # the floor of Eq. 8's lookup, x = R p + t and x / r per axis: 21 flops per performed lookup
-        flops = 21.0 * lookups_live
-        ach = flops / (kernel_ms["overlap_matrix"] / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": "overlap_matrix", "achieved": ach, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": dram_traffic("overlap_matrix"),
-                    "peak_source": "FP32 lanes x 2 x max SM clock (SMs x 128 x 2 x %.0f MHz)" % sm_max,
-                    "algorithmic_flops_per_launch": flops, "lookups_per_launch": int(lookups_live)}
+        roofline = dict(roof_ov)
     elif dom == 2:
         roofline = dict(roof_lin)
     else:
@@ -559,6 +566,8 @@ def run_ours(a):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "roofline_linearize": roof_lin,
+        "roofline_overlap": roof_ov,
+        "roofline_overlap_alu": roof_ov_alu,
         "overlap_work": {"live_pairs": ctx.overlap_matrix_work()[0], "lookups": int(lookups_live)},
         "clocks": clocks,
         "inliers_total": int(inl.sum()),

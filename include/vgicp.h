@@ -136,6 +136,16 @@ typedef struct {
     /* 1: each correspondence weighted by its voxel's point count (Omega scaled
      * by it); 0 (default): unweighted, as Eq. 2, 5, 6. */
     int32_t count_weighted;
+    /* Storage order of the points of frames registered from now on: 1 (default)
+     * spatial -- the points sorted by the Morton (z-order) code of their cell
+     * in a 256^3 grid over the frame's bounding box, points of one cell in the
+     * given order, non-finite points last -- so that the lanes of a warp look
+     * up the same few voxels; 0: the given order.  Results differ only by the
+     * float32 summation order (overlap counts, inliers and voxelmaps are the
+     * same); per-point outputs (vgicp_debug_correspondences,
+     * vgicp_linearize_correspondences) are always in the given order.  A
+     * spatially ordered frame holds 4 more bytes per point. */
+    int32_t frame_order;
 } vgicp_options;
 
 /* Fill *opt with the defaults above. */

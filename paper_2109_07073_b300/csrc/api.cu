@@ -58,7 +58,7 @@ struct Lane {
     Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
     Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
     Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs, ws_tune, ws_knn;
-    Buf ws_fetch, ws_items, ws_img, ws_rec;
+    Buf ws_fetch, ws_items, ws_img, ws_rec, ws_order;
     Plan plan;
     int64_t last_matrix_pairs = 0;   // pairs of the last overlap matrix (params kept in ws_pairs)
     // pinned staging for host -> device copies: two arenas used in turn, each
@@ -420,18 +420,22 @@ vgicp_status put_frame_desc(vgicp_ctx *ctx, uint32_t idx)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Device bytes of a frame of n points: pa, pb, pc, statistics, chunk boxes.
-size_t frame_bytes(int64_t n)
+// Device bytes of a frame of n points: pa, pb, pc, statistics, chunk boxes,
+// and the storage permutation of a spatially ordered frame.
+size_t frame_bytes(int64_t n, bool ordered)
 {
-    return align256((size_t)n * 16) * 2 + align256((size_t)n * 4) + 256 + 1024;
+    return align256((size_t)n * 16) * 2 + align256((size_t)n * 4) + 256 + 1024 +
+           (ordered ? align256((size_t)n * 4) : 0);
 }
 
 // Allocate a frame handle of n points and fill its host descriptor (the
 // device copy of the descriptor and the data are the caller's business).
 vgicp_status alloc_frame(vgicp_ctx *ctx, int64_t n, uint32_t *out_idx)
 {
+    const bool ordered = ctx->opt.frame_order == 1 && n > 1;
     const size_t o_pb = align256((size_t)n * 16), o_pc = o_pb + align256((size_t)n * 16);
-    const size_t o_st = o_pc + align256((size_t)n * 4), o_cb = o_st + 256, bytes = o_cb + 1024;
+    const size_t o_st = o_pc + align256((size_t)n * 4), o_cb = o_st + 256, o_pm = o_cb + 1024;
+    const size_t bytes = o_pm + (ordered ? align256((size_t)n * 4) : 0);
     TRY(budget_check(ctx, (int64_t)bytes));
     uint32_t idx;
     TRY(new_obj(ctx, Obj::FRAME, &idx));
@@ -453,31 +457,11 @@ vgicp_status alloc_frame(vgicp_ctx *ctx, int64_t n, uint32_t *out_idx)
     f.pc = (const float *)(base + o_pc);
     f.stats = (const float *)(base + o_st);
     f.cbox = (const float *)(base + o_cb);
+    f.perm = ordered ? (const int32_t *)(base + o_pm) : nullptr;
     f.n = n;
     f.cshift = 10;
     while (((int64_t)kMaxCullChunks << f.cshift) < n) ++f.cshift;
     f.nchunks = (int32_t)((n + ((int64_t)1 << f.cshift) - 1) >> f.cshift);
-    *out_idx = idx;
-    return VGICP_OK;
-}
-
-// Allocate and fill a frame from device-resident points / covariances.
-vgicp_status make_frame(vgicp_ctx *ctx, const float *d_pts, const float *d_cov, int64_t n, uint32_t *out_idx)
-{
-    uint32_t idx;
-    TRY(alloc_frame(ctx, n, &idx));
-    char *base = (char *)ctx->objs[idx].frame_mem;
-    FrameDesc &f = ctx->h_frames[idx];
-    const size_t o_st = (size_t)((const char *)f.stats - base);
-    // statistics start at: zero maxima of |c| and |p|, +inf minima, -inf maxima
-    static const uint32_t init[kStatCount] = {0, 0, 0, 0, kOrderedPosInf, kOrderedPosInf, kOrderedPosInf,
-                                              kOrderedNegInf, kOrderedNegInf, kOrderedNegInf};
-    TRY(h2d(ctx, base + o_st, init, sizeof(init)));
-    launch_frame_pack(d_pts, d_cov, n, (float4 *)f.pa, (float4 *)f.pb, (float *)f.pc, (float *)f.stats, LN.stream);
-    launch_chunk_boxes(f.pa, n, f.cshift, f.nchunks, (float *)f.cbox, LN.stream);
-    ctx->launches += n > 0 ? 2 : 0;
-    CHECK_LAUNCH();
-    TRY(put_frame_desc(ctx, idx));
     *out_idx = idx;
     return VGICP_OK;
 }
@@ -779,6 +763,7 @@ vgicp_status vgicp_options_default(vgicp_options *opt)
     opt->hbm_budget_bytes = 0;
     opt->overlap_cull = 1;
     opt->linearize_cull = 1;
+    opt->frame_order = 1;
     return VGICP_OK;
 }
 
@@ -798,6 +783,8 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
     if (o->overlap_cull != 0 && o->overlap_cull != 1)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_cull must be 0 or 1");
+    if (o->frame_order != 0 && o->frame_order != 1)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "frame_order must be 0 or 1");
     if (o->linearize_cull != 0 && o->linearize_cull != 1)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_cull must be 0 or 1");
     return VGICP_OK;
@@ -854,7 +841,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
                        &LN.ws_slot_of_vid, &LN.ws_img, &LN.ws_pairs, &LN.ws_fidx, &LN.ws_midx, &LN.ws_chunks,
                        &LN.ws_export_keys, &LN.ws_export_rec, &LN.ws_counter, &LN.ws_descs, &LN.ws_tune,
                        &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_range, &LN.plan.units, &LN.ws_fetch,
-                       &LN.ws_items, &LN.ws_rec};
+                       &LN.ws_items, &LN.ws_rec, &LN.ws_order};
         for (Buf *b : bufs) free_buf(ctx, *b);
         const cudaError_t e2 = cudaStreamSynchronize(LN.stream);
         if (e == cudaSuccess) e = e2;
@@ -942,12 +929,7 @@ vgicp_status vgicp_add_frame(vgicp_ctx *ctx, const float *points, const float *c
     if (mem_kind != VGICP_MEM_HOST && mem_kind != VGICP_MEM_DEVICE)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frame: bad mem_kind %d", mem_kind);
     if (n > ((int64_t)1 << 31) - 1) return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frame: n >= 2^31");
-    const float *dp, *dc;
-    TRY(stage_inputs(ctx, points, covs, n, mem_kind, &dp, &dc));
-    uint32_t idx;
-    TRY(make_frame(ctx, dp, dc, n, &idx));
-    *out = make_handle(idx, ctx->objs[idx].gen);
-    return VGICP_OK;
+    return vgicp_add_frames(ctx, points, covs, &n, 1, mem_kind, out);
 }
 
 vgicp_status vgicp_add_frames(vgicp_ctx *ctx, const float *points, const float *covs, const int64_t *n, int64_t m,
@@ -1016,11 +998,15 @@ vgicp_status vgicp_add_frames(vgicp_ctx *ctx, const float *points, const float *
     if (!chunks.empty()) std::memcpy(host.data() + o_c, chunks.data(), chunks.size() * sizeof(WorkItem));
     TRY(upload(ctx, LN.ws_descs, host.data(), host.size()));
     char *d = (char *)LN.ws_descs.p;
+    bool ordered = false;
+    for (int64_t u = 0; u < m; ++u) ordered = ordered || descs[u].perm != nullptr;
+    if (ordered) TRY(ensure(ctx, LN.ws_order, (size_t)total * 16));
     launch_frames_register(dp, dc, (const int64_t *)d, (const int32_t *)(d + o_f), (int)m,
                            (const WorkItem *)(d + o_i), (int)items.size(), (const WorkItem *)(d + o_c),
                            (int)chunks.size(), (const uint32_t *)(d + o_f), (const FrameDesc *)(d + o_d),
-                           ctx->d_frames, LN.stream);
-    ctx->launches += 2 + !items.empty() + !chunks.empty();
+                           ctx->d_frames, ordered ? (uint32_t *)LN.ws_order.p : nullptr, total, ctx->num_sms,
+                           LN.stream);
+    ctx->launches += 2 + (!items.empty()) * (ordered ? 3 : 1) + !chunks.empty();
     CHECK_LAUNCH();
     for (int64_t u = 0; u < m; ++u) out[u] = make_handle(idx[u], ctx->objs[idx[u]].gen);
     return VGICP_OK;
@@ -1106,6 +1092,29 @@ vgicp_status vgicp_voxelmap_size(vgicp_ctx *ctx, vgicp_map_t map, int64_t *n_vox
 }  // extern "C"
 
 namespace {
+
+// Host copy of a spatially ordered frame's storage permutation (empty for a
+// frame kept in the given order).
+vgicp_status frame_perm(vgicp_ctx *ctx, uint32_t fi, std::vector<int32_t> &perm)
+{
+    perm.clear();
+    const FrameDesc &f = ctx->h_frames[fi];
+    if (!f.perm || f.n == 0) return VGICP_OK;
+    perm.resize((size_t)f.n);
+    CU(cudaMemcpyAsync(perm.data(), f.perm, (size_t)f.n * 4, cudaMemcpyDeviceToHost, LN.stream));
+    CU(cudaStreamSynchronize(LN.stream));
+    return VGICP_OK;
+}
+
+// Per-point rows (w values each) from storage order back to the given order.
+template <class T>
+void unpermute(T *data, int64_t n, int w, const std::vector<int32_t> &perm)
+{
+    if (perm.empty() || n == 0) return;
+    std::vector<T> tmp(data, data + n * w);
+    for (int64_t j = 0; j < n; ++j)
+        for (int c = 0; c < w; ++c) data[(int64_t)perm[j] * w + c] = tmp[j * w + c];
+}
 
 // Host copy of a correspondence record (CorrRecord layout): voxel coordinates
 // unpacked to int64 triples (INT64_MIN on every axis where the point has none
@@ -1218,6 +1227,19 @@ vgicp_status linearize_run(vgicp_ctx *ctx, const vgicp_factor *factors, int64_t 
                 rec->keys[3 * j + a] =
                     key == kEmptyKey ? INT64_MIN
                                      : (int64_t)((key >> (42 - 21 * a)) & 0x1FFFFFull) - (int64_t)kKeyOffset;
+        }
+        // each factor's points back in its source's given order
+        std::vector<int32_t> perm;
+        int32_t have = -1;
+        for (int64_t i = 0; i < n_f; ++i) {
+            const uint32_t fi = (uint32_t)idx[4 * i + 1];
+            if ((int32_t)fi != have) {
+                TRY(frame_perm(ctx, fi, perm));
+                have = (int32_t)fi;
+            }
+            const int64_t n = ctx->objs[fi].n;
+            unpermute(rec->keys + 3 * rbase[i], n, 3, perm);
+            unpermute(rec->state + rbase[i], n, 1, perm);
         }
     }
     return VGICP_OK;
@@ -1806,6 +1828,10 @@ vgicp_status vgicp_debug_correspondences(vgicp_ctx *ctx, vgicp_frame_t source, v
     if (keys) CU(cudaMemcpyAsync(keys, dk, (size_t)n * 24, cudaMemcpyDeviceToHost, LN.stream));
     if (hit) CU(cudaMemcpyAsync(hit, dh, (size_t)n * 4, cudaMemcpyDeviceToHost, LN.stream));
     CU(cudaStreamSynchronize(LN.stream));
+    std::vector<int32_t> perm;
+    TRY(frame_perm(ctx, fi, perm));
+    if (keys) unpermute(keys, n, 3, perm);
+    if (hit) unpermute(hit, n, 1, perm);
     return VGICP_OK;
 }
 
@@ -1928,7 +1954,8 @@ vgicp_status vgicp_memory_estimate(vgicp_ctx *ctx, int64_t n, int32_t is_map, in
 {
     if (!ctx) return VGICP_ERR_INVALID_ARG;
     if (!bytes || n < 0) return fail(ctx, VGICP_ERR_INVALID_ARG, "memory_estimate: bad arguments");
-    *bytes = is_map ? (int64_t)map_bytes(map_capacity(n)) : (int64_t)frame_bytes(n);
+    *bytes = is_map ? (int64_t)map_bytes(map_capacity(n))
+                    : (int64_t)frame_bytes(n, ctx->opt.frame_order == 1 && n > 1);
     return VGICP_OK;
 }
 

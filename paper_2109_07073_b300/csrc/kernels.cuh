@@ -22,10 +22,15 @@ struct __align__(16) WorkItem {
 void launch_frame_pack(const float *points, const float *covs, int64_t n, float4 *pa, float4 *pb, float *pc,
                        float *stats, cudaStream_t st);
 
-// Bounding boxes of a frame's cull chunks (2^shift points each).
+// Register m frames from staged points / covariances (frame u's at src_off[u]):
+// descriptors into the table, statistics, the streams and the cull-chunk
+// bounding boxes (2^shift points each).  Frames whose descriptor has a perm
+// array are stored in spatial order (order_scratch: 4 x total uint32, required
+// when any frame has one).
 void launch_frames_register(const float *pts, const float *cov, const int64_t *src_off, const int32_t *fidx, int m,
                             const WorkItem *items, int n_items, const WorkItem *chunks, int n_chunks,
-                            const uint32_t *desc_idx, const FrameDesc *descs, FrameDesc *table, cudaStream_t st);
+                            const uint32_t *desc_idx, const FrameDesc *descs, FrameDesc *table, uint32_t *order_scratch,
+                            int64_t total, int num_sms, cudaStream_t st);
 void launch_chunk_boxes(const float4 *pa, int64_t n, int shift, int nchunks, float *cbox, cudaStream_t st);
 
 // Write n map descriptors into the device table: table[idx[i]] = src[i].

@@ -79,6 +79,7 @@ struct FrameDesc {
     const float *cbox;   // device: per cull chunk min xyz, max xyz (6 floats; at most kMaxCullChunks)
     int32_t cshift;      // cull chunk = 2^cshift consecutive points (>= 10, so <= 32 chunks)
     int32_t nchunks;
+    const int32_t *perm; // device: given index of the point stored at each position (null: given order)
 };
 
 constexpr int kMaxCullChunks = 32;

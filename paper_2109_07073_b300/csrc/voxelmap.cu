@@ -86,23 +86,39 @@ __global__ void k_frames_init(const int32_t *__restrict__ fidx, int m, const Fra
     }
 }
 
+// mode 0: write the streams in the given order and gather the statistics;
+// mode 1: statistics only; mode 2: write the streams in the frame's stored
+// point order (stream position i takes given point perm[i]), no statistics.
 __global__ void k_frames_pack(const float *__restrict__ pts, const float *__restrict__ cov,
                               const int64_t *__restrict__ src_off, const int32_t *__restrict__ fidx,
-                              const WorkItem *__restrict__ items, int n_items, const FrameDesc *__restrict__ frames)
+                              const WorkItem *__restrict__ items, int n_items, const FrameDesc *__restrict__ frames,
+                              int mode)
 {
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
         const FrameDesc F = frames[fidx[w.unit]];
         const float *p0 = pts + 3 * src_off[w.unit], *c0 = cov + 6 * src_off[w.unit];
+        if (mode == 2) {
+            for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+                const int64_t i = w.start + k, j = F.perm[i];
+                const float *p = p0 + 3 * j, *c = c0 + 6 * j;
+                ((float4 *)F.pa)[i] = make_float4(p[0], p[1], p[2], c[0]);
+                ((float4 *)F.pb)[i] = make_float4(c[1], c[2], c[3], c[4]);
+                ((float *)F.pc)[i] = c[5];
+            }
+            continue;
+        }
         float m = 0.f, am[3] = {0.f, 0.f, 0.f};
         uint32_t mn[3] = {kOrderedPosInf, kOrderedPosInf, kOrderedPosInf};
         uint32_t mx[3] = {kOrderedNegInf, kOrderedNegInf, kOrderedNegInf};
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const int64_t i = w.start + k;
             const float *p = p0 + 3 * i, *c = c0 + 6 * i;
-            ((float4 *)F.pa)[i] = make_float4(p[0], p[1], p[2], c[0]);
-            ((float4 *)F.pb)[i] = make_float4(c[1], c[2], c[3], c[4]);
-            ((float *)F.pc)[i] = c[5];
+            if (mode == 0) {
+                ((float4 *)F.pa)[i] = make_float4(p[0], p[1], p[2], c[0]);
+                ((float4 *)F.pb)[i] = make_float4(c[1], c[2], c[3], c[4]);
+                ((float *)F.pc)[i] = c[5];
+            }
 #pragma unroll
             for (int j = 0; j < 6; ++j) m = fmaxf(m, fabsf(c[j]));
             if (isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2])) {
@@ -134,6 +150,132 @@ __global__ void k_frames_pack(const float *__restrict__ pts, const float *__rest
                 atomicMax(st + kStatMax + j, mx[j]);
             }
         }
+    }
+}
+
+// Spatial point order of frames (one block per frame at a time): each finite
+// point's cell in a grid of 256^3 cubic cells spanning the frame's bounding
+// box (cell edge = the largest box extent / 256), the cells in Morton order
+// (z-order: bits of x, y, z interleaved), points of one cell in their given
+// order, points that are not finite last.  A stable LSD radix sort of the
+// 24-bit codes, 8 bits per pass: per pass a digit histogram and its prefix,
+// then tiles of kSortBlock points in index order, each point's rank among the
+// tile's points of its digit from the warps' __match_any_sync groups and the
+// per-warp counts.  The result is a permutation (perm[i] = given index of the
+// point stored at i): deterministic, so a cloud registered twice is stored
+// the same way.  Scratch: 4 arrays of total-points uint32 (keys and indices,
+// two buffers), frame u's points at src_off[u].
+constexpr int kSortBlock = 1024, kSortBins = 256, kSortWarps = kSortBlock / 32;
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v)
+{
+    // bit b of v to bit 3 b (v < 256)
+    v &= 0xffu;
+    v = (v | (v << 8)) & 0x0000f00fu;
+    v = (v | (v << 4)) & 0x000c30c3u;
+    v = (v | (v << 2)) & 0x00249249u;
+    return v;
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_frames_order(const float *__restrict__ pts,
+                                                             const int64_t *__restrict__ src_off,
+                                                             const int32_t *__restrict__ fidx, int m,
+                                                             const FrameDesc *__restrict__ frames,
+                                                             uint32_t *__restrict__ scratch, int64_t total)
+{
+    __shared__ uint32_t s_cnt[kSortWarps][kSortBins];
+    __shared__ uint32_t s_base[kSortBins], s_tot[kSortBins];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int u = blockIdx.x; u < m; u += gridDim.x) {
+        const FrameDesc F = frames[fidx[u]];
+        const int64_t n = F.n, off = src_off[u];
+        if (!F.perm || n == 0) continue;
+        uint32_t *keyA = scratch + off, *idxA = scratch + total + off;
+        uint32_t *keyB = scratch + 2 * total + off, *idxB = scratch + 3 * total + off;
+        float lo[3], ext = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = from_ordered_bits(((const uint32_t *)F.stats)[kStatMin + a]);
+            const float hi = from_ordered_bits(((const uint32_t *)F.stats)[kStatMax + a]);
+            ext = fmaxf(ext, hi - lo[a]);
+        }
+        const float inv = ext > 0.f ? 256.f / ext : 0.f;
+        const float *p0 = pts + 3 * off;
+        for (int64_t i = t; i < n; i += kSortBlock) {
+            const float *p = p0 + 3 * i;
+            uint32_t code = 0xffffffu;
+            if (isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2])) {
+                uint32_t q[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float c = fmaxf(0.f, (p[a] - lo[a]) * inv);
+                    q[a] = c < 255.f ? (uint32_t)c : 255u;
+                }
+                code = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+            }
+            keyA[i] = code;
+            idxA[i] = (uint32_t)i;
+        }
+        __syncthreads();
+        for (int pass = 0; pass < 3; ++pass) {
+            const int sh = 8 * pass;
+            const uint32_t *sk = pass == 1 ? keyB : keyA, *si = pass == 1 ? idxB : idxA;
+            uint32_t *dk = pass == 1 ? keyA : keyB, *di = pass == 1 ? idxA : idxB;
+            // digit histogram and its exclusive prefix
+            if (t < kSortBins) s_tot[t] = 0u;
+            for (int j = t; j < kSortWarps * kSortBins; j += kSortBlock) (&s_cnt[0][0])[j] = 0u;
+            __syncthreads();
+            for (int64_t i = t; i < n; i += kSortBlock) atomicAdd(&s_tot[(sk[i] >> sh) & 0xffu], 1u);
+            __syncthreads();
+            if (t < 32) {
+                uint32_t run = 0;
+                for (int q = 0; q < kSortBins / 32; ++q) {
+                    const uint32_t v = s_tot[q * 32 + t];
+                    uint32_t x = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    s_base[q * 32 + t] = run + x - v;
+                    run += __shfl_sync(0xffffffffu, x, 31);
+                }
+            }
+            __syncthreads();
+            for (int64_t b = 0; b < n; b += kSortBlock) {
+                const int64_t i = b + t;
+                const bool ok = i < n;
+                const uint32_t key = ok ? sk[i] : 0u, id = ok ? si[i] : 0u;
+                const uint32_t d = ok ? ((key >> sh) & 0xffu) : 0x100u;   // 0x100: past the end
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t rank = __popc(peers & lt);
+                if (ok && rank == 0) s_cnt[w][d] = (uint32_t)__popc(peers);
+                __syncthreads();
+                if (t < kSortBins) {            // per digit: exclusive prefix over the warps
+                    uint32_t run = 0;
+                    for (int q = 0; q < kSortWarps; ++q) {
+                        const uint32_t c = s_cnt[q][t];
+                        s_cnt[q][t] = run;
+                        run += c;
+                    }
+                    s_tot[t] = run;
+                }
+                __syncthreads();
+                if (ok) {
+                    const uint32_t pos = s_base[d] + s_cnt[w][d] + rank;
+                    dk[pos] = key;
+                    di[pos] = id;
+                }
+                __syncthreads();
+                if (t < kSortBins) s_base[t] += s_tot[t];
+                for (int j = t; j < kSortWarps * kSortBins; j += kSortBlock) (&s_cnt[0][0])[j] = 0u;
+                __syncthreads();
+            }
+        }
+        // three passes: A -> B -> A -> B
+        for (int64_t i = t; i < n; i += kSortBlock) ((int32_t *)F.perm)[i] = (int32_t)idxB[i];
+        __syncthreads();
     }
 }
 
@@ -603,13 +745,22 @@ void launch_frame_pack(const float *points, const float *covs, int64_t n, float4
 
 void launch_frames_register(const float *pts, const float *cov, const int64_t *src_off, const int32_t *fidx, int m,
                             const WorkItem *items, int n_items, const WorkItem *chunks, int n_chunks,
-                            const uint32_t *desc_idx, const FrameDesc *descs, FrameDesc *table, cudaStream_t st)
+                            const uint32_t *desc_idx, const FrameDesc *descs, FrameDesc *table, uint32_t *order_scratch,
+                            int64_t total, int num_sms, cudaStream_t st)
 {
     if (m <= 0) return;
     k_scatter_frame_descs<<<(m + 127) / 128, 128, 0, st>>>(desc_idx, descs, m, table);
     k_frames_init<<<(m + 127) / 128, 128, 0, st>>>(fidx, m, table);
-    if (n_items > 0)
-        k_frames_pack<<<std::min(n_items, 148 * 16), 256, 0, st>>>(pts, cov, src_off, fidx, items, n_items, table);
+    const int pg = std::min(n_items, 148 * 16);
+    if (n_items > 0 && order_scratch) {
+        // statistics (the bounding box), the spatial order, then the streams in that order
+        k_frames_pack<<<pg, 256, 0, st>>>(pts, cov, src_off, fidx, items, n_items, table, 1);
+        k_frames_order<<<std::min(m, num_sms), kSortBlock, 0, st>>>(pts, src_off, fidx, m, table, order_scratch,
+                                                                    total);
+        k_frames_pack<<<pg, 256, 0, st>>>(pts, cov, src_off, fidx, items, n_items, table, 2);
+    } else if (n_items > 0) {
+        k_frames_pack<<<pg, 256, 0, st>>>(pts, cov, src_off, fidx, items, n_items, table, 0);
+    }
     if (n_chunks > 0)
         k_frames_chunk_boxes<<<std::min(n_chunks, 148 * 16), 256, 0, st>>>(fidx, chunks, n_chunks, table);
 }
