@@ -118,12 +118,14 @@ typedef struct {
     /* 1 (default): overlap pairs whose source bounding box, moved by the pair's
      * pose and grown by a margin far above float64 rounding, misses the target's
      * voxel bounding box are answered 0 without visiting their points (exact:
-     * such a pair has no correspondence), and chunks of consecutive points whose
-     * box misses it are skipped.  0: every point is looked up. */
+     * such a pair has no correspondence), chunks of consecutive points whose
+     * box misses it are skipped, and so are groups of 32 consecutive stored
+     * points whose moved box reaches no occupied cell of the target's coarse
+     * occupancy grid (cells of 4^3 voxels or more).  0: every point is looked up. */
     int32_t overlap_cull;
-    /* 1 (default): the same exact test per chunk of consecutive source points
-     * (chunk boxes kept per frame) lets the linearisation skip work items whose
-     * chunks all miss the target's voxels; results are unchanged. */
+    /* 1 (default): the same exact tests per chunk and per group of 32 source
+     * points (boxes kept per frame) let the linearisation skip work items and
+     * groups that provably find no voxel; results are unchanged. */
     int32_t linearize_cull;
     /* Correspondences of a source point (linearisation and evaluation; the
      * overlap of Eq. 8 always uses the containing voxel): 1 (default) the voxel
@@ -136,16 +138,24 @@ typedef struct {
     /* 1: each correspondence weighted by its voxel's point count (Omega scaled
      * by it); 0 (default): unweighted, as Eq. 2, 5, 6. */
     int32_t count_weighted;
-    /* Storage order of the points of frames registered from now on: 1 (default)
-     * spatial -- the points sorted by the Morton (z-order) code of their cell
-     * in a 256^3 grid over the frame's bounding box, points of one cell in the
-     * given order, non-finite points last -- so that the lanes of a warp look
-     * up the same few voxels; 0: the given order.  Results differ only by the
+    /* Storage order of the points of frames registered from now on: 2 (default)
+     * spatial within tiles -- each run of 4,096 given points sorted on its own by
+     * the Morton (z-order) code of the points' cells in a 256^3 grid over the
+     * frame's bounding box, ties in the given order, non-finite points last --
+     * so that the lanes of a warp look up the same few voxels; a frame of any
+     * size is ordered by as many blocks as it has tiles, so one frame registers
+     * quickly; 1: the same order over the whole frame (one block per frame; as
+     * fast for batches of hundreds of frames, slow for one large frame); 0: the
+     * given order.  Results differ only by the
      * float32 summation order (overlap counts, inliers and voxelmaps are the
      * same); per-point outputs (vgicp_debug_correspondences,
      * vgicp_linearize_correspondences) are always in the given order.  A
      * spatially ordered frame holds 4 more bytes per point. */
     int32_t frame_order;
+    /* 1 (default): with overlap_cull / linearize_cull, the exact tests also
+     * skip groups of 32 consecutive stored points (see those options); 0: cull
+     * chunks and pairs only.  Results are the same either way. */
+    int32_t group_cull;
 } vgicp_options;
 
 /* Fill *opt with the defaults above. */
@@ -362,7 +372,8 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
 
 /* Work of the last vgicp_overlap_matrix() call on this context: the number of
  * pairs not culled and the number of point lookups performed (the points of
- * their live chunks).  Synchronises the context stream. */
+ * the groups of 32 stored points that the exact culling could not rule out).
+ * Synchronises the context stream. */
 vgicp_status vgicp_overlap_matrix_work(vgicp_ctx *ctx, int64_t *live_pairs, int64_t *lookups);
 
 /* Per-point voxel association of a source against a target (debug / parity):

@@ -53,7 +53,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("chunk_points", C.c_int32), ("linearize_variant", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("overlap_cull", C.c_int32),
                 ("linearize_cull", C.c_int32), ("neighbors", C.c_int32), ("count_weighted", C.c_int32),
-                ("frame_order", C.c_int32)]
+                ("frame_order", C.c_int32), ("group_cull", C.c_int32)]
 
 
 class Factor(C.Structure):

@@ -413,18 +413,14 @@ vgicp_status budget_check(vgicp_ctx *ctx, int64_t extra)
     return VGICP_OK;
 }
 
-vgicp_status put_frame_desc(vgicp_ctx *ctx, uint32_t idx)
-{
-    return h2d(ctx, ctx->d_frames + idx, &ctx->h_frames[idx], sizeof(FrameDesc));
-}
-
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Device bytes of a frame of n points: pa, pb, pc, statistics, chunk boxes,
-// and the storage permutation of a spatially ordered frame.
+// group boxes, and the storage permutation of a spatially ordered frame.
+size_t group_box_bytes(int64_t n) { return align256((size_t)((n + kGroup - 1) / kGroup) * 24); }
 size_t frame_bytes(int64_t n, bool ordered)
 {
-    return align256((size_t)n * 16) * 2 + align256((size_t)n * 4) + 256 + 1024 +
+    return align256((size_t)n * 16) * 2 + align256((size_t)n * 4) + 256 + 1024 + group_box_bytes(n) +
            (ordered ? align256((size_t)n * 4) : 0);
 }
 
@@ -432,9 +428,10 @@ size_t frame_bytes(int64_t n, bool ordered)
 // device copy of the descriptor and the data are the caller's business).
 vgicp_status alloc_frame(vgicp_ctx *ctx, int64_t n, uint32_t *out_idx)
 {
-    const bool ordered = ctx->opt.frame_order == 1 && n > 1;
+    const bool ordered = ctx->opt.frame_order != 0 && n > 1;
     const size_t o_pb = align256((size_t)n * 16), o_pc = o_pb + align256((size_t)n * 16);
-    const size_t o_st = o_pc + align256((size_t)n * 4), o_cb = o_st + 256, o_pm = o_cb + 1024;
+    const size_t o_st = o_pc + align256((size_t)n * 4), o_cb = o_st + 256, o_gb = o_cb + 1024;
+    const size_t o_pm = o_gb + group_box_bytes(n);
     const size_t bytes = o_pm + (ordered ? align256((size_t)n * 4) : 0);
     TRY(budget_check(ctx, (int64_t)bytes));
     uint32_t idx;
@@ -458,6 +455,7 @@ vgicp_status alloc_frame(vgicp_ctx *ctx, int64_t n, uint32_t *out_idx)
     f.stats = (const float *)(base + o_st);
     f.cbox = (const float *)(base + o_cb);
     f.perm = ordered ? (const int32_t *)(base + o_pm) : nullptr;
+    f.gbox = (const float *)(base + o_gb);
     f.n = n;
     f.cshift = 10;
     while (((int64_t)kMaxCullChunks << f.cshift) < n) ++f.cshift;
@@ -489,6 +487,7 @@ void fill_map_desc(MapDesc &m, char *base, uint32_t cap, double r)
     m.ckeys = (uint32_t *)(base + align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)));
     m.img = (unsigned char *)(base + align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)) +
                               align256((size_t)cap * 4));
+    m.coarse = (uint32_t *)(base + map_bytes(cap) - 256 - align256(kCoarseWords * 4));
     m.kbox = (int32_t *)(base + map_bytes(cap) - 256 + 16);
     m.cmeta = (int32_t *)(base + map_bytes(cap) - 256 + 48);
     m.mask = cap - 1;
@@ -506,7 +505,7 @@ void fill_map_desc(MapDesc &m, char *base, uint32_t cap, double r)
 size_t map_bytes(uint32_t cap)
 {
     return align256((size_t)cap * 8) + align256((size_t)cap * sizeof(VoxelRec)) + align256((size_t)cap * 4) +
-           align256(kImgMaxBytes) + 256;
+           align256(kImgMaxBytes) + align256(kCoarseWords * 4) + 256;
 }
 
 uint32_t *map_nvox_ptr(const Obj &o) { return (uint32_t *)((char *)o.map_mem + o.map_bytes - 256); }
@@ -611,7 +610,11 @@ vgicp_status read_nvox(vgicp_ctx *ctx, const Obj &o, int64_t *n)
 int default_chunk(const vgicp_options &o) { return o.chunk_points > 0 ? o.chunk_points : 2048; }
 int neighbor_count(const vgicp_options &o) { return o.neighbors > 1 ? o.neighbors : 1; }
 // chunk culling tests the target's voxel box, so it holds for the containing voxel only
-int lin_cull(const vgicp_options &o) { return neighbor_count(o) == 1 ? o.linearize_cull : 0; }
+// Culling level handed to the pair preparation: 0 none, 1 pairs and cull
+// chunks, 2 also groups of kGroup points against the coarse occupancy.
+int cull_level(int on, const vgicp_options &o) { return on ? (o.group_cull ? 2 : 1) : 0; }
+int lin_cull(const vgicp_options &o) { return neighbor_count(o) == 1 ? cull_level(o.linearize_cull, o) : 0; }
+int ov_cull(const vgicp_options &o) { return cull_level(o.overlap_cull, o); }
 // variant 6: the shared-memory map path (single-voxel, unweighted association)
 bool uses_img(const vgicp_options &o) { return o.linearize_variant == 6 && neighbor_count(o) == 1 && !o.count_weighted; }
 
@@ -762,8 +765,9 @@ vgicp_status vgicp_options_default(vgicp_options *opt)
     opt->blocks_per_sm = 0;
     opt->hbm_budget_bytes = 0;
     opt->overlap_cull = 1;
+    opt->group_cull = 1;
     opt->linearize_cull = 1;
-    opt->frame_order = 1;
+    opt->frame_order = 2;
     return VGICP_OK;
 }
 
@@ -783,8 +787,10 @@ static vgicp_status check_options(vgicp_ctx *ctx, const vgicp_options *o)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "blocks_per_sm and hbm_budget_bytes must be >= 0");
     if (o->overlap_cull != 0 && o->overlap_cull != 1)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "overlap_cull must be 0 or 1");
-    if (o->frame_order != 0 && o->frame_order != 1)
-        return fail(ctx, VGICP_ERR_INVALID_ARG, "frame_order must be 0 or 1");
+    if (o->group_cull != 0 && o->group_cull != 1)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "group_cull must be 0 or 1");
+    if (o->frame_order < 0 || o->frame_order > 2)
+        return fail(ctx, VGICP_ERR_INVALID_ARG, "frame_order must be 0, 1 or 2");
     if (o->linearize_cull != 0 && o->linearize_cull != 1)
         return fail(ctx, VGICP_ERR_INVALID_ARG, "linearize_cull must be 0 or 1");
     return VGICP_OK;
@@ -1000,12 +1006,13 @@ vgicp_status vgicp_add_frames(vgicp_ctx *ctx, const float *points, const float *
     char *d = (char *)LN.ws_descs.p;
     bool ordered = false;
     for (int64_t u = 0; u < m; ++u) ordered = ordered || descs[u].perm != nullptr;
-    if (ordered) TRY(ensure(ctx, LN.ws_order, (size_t)total * 16));
+    const bool tiles_only = ctx->opt.frame_order == 2;
+    if (ordered && !tiles_only) TRY(ensure(ctx, LN.ws_order, (size_t)total * 16));
     launch_frames_register(dp, dc, (const int64_t *)d, (const int32_t *)(d + o_f), (int)m,
                            (const WorkItem *)(d + o_i), (int)items.size(), (const WorkItem *)(d + o_c),
                            (int)chunks.size(), (const uint32_t *)(d + o_f), (const FrameDesc *)(d + o_d),
-                           ctx->d_frames, ordered ? (uint32_t *)LN.ws_order.p : nullptr, total, ctx->num_sms,
-                           LN.stream);
+                           ctx->d_frames, ordered && !tiles_only ? (uint32_t *)LN.ws_order.p : nullptr, total,
+                           ctx->num_sms, ordered ? (tiles_only ? 2 : 1) : 0, LN.stream);
     ctx->launches += 2 + (!items.empty()) * (ordered ? 3 : 1) + !chunks.empty();
     CHECK_LAUNCH();
     for (int64_t u = 0; u < m; ++u) out[u] = make_handle(idx[u], ctx->objs[idx[u]].gen);
@@ -1640,7 +1647,7 @@ vgicp_status vgicp_overlap(vgicp_ctx *ctx, vgicp_frame_t source, vgicp_map_t tar
     TRY(ensure(ctx, LN.ws_pairs, sizeof(PoseParam)));
     LN.last_matrix_pairs = 0;
     launch_prepare_given((const double *)LN.ws_poses.p, (int)mi, (int)fi, ctx->d_maps, ctx->d_frames,
-                         ctx->opt.overlap_cull, (PoseParam *)LN.ws_pairs.p, LN.stream);
+                         ov_cull(ctx->opt), (PoseParam *)LN.ws_pairs.p, LN.stream);
     ctx->launches += 1;
     TRY(upload(ctx, LN.ws_chunks, items.data(), items.size()));
     TRY(ensure(ctx, LN.ws_counts, 8));
@@ -1697,7 +1704,7 @@ vgicp_status vgicp_overlap_pairs(vgicp_ctx *ctx, const vgicp_frame_t *sources, c
     LN.last_matrix_pairs = 0;
     const int32_t *d_idx = (const int32_t *)LN.ws_fidx.p;
     launch_prepare_list((const double *)LN.ws_poses.p, d_idx, d_idx + n, (int)n, ctx->d_maps, ctx->d_frames,
-                        ctx->opt.overlap_cull, (PoseParam *)LN.ws_pairs.p, LN.stream);
+                        ov_cull(ctx->opt), (PoseParam *)LN.ws_pairs.p, LN.stream);
     unsigned long long *dc = (unsigned long long *)counts;
     if (out_kind == VGICP_MEM_HOST) {
         TRY(ensure(ctx, LN.ws_counts, (size_t)n * 8));
@@ -1757,7 +1764,7 @@ vgicp_status vgicp_overlap_matrix(vgicp_ctx *ctx, const vgicp_frame_t *sources, 
     TRY(ensure(ctx, LN.ws_pairs, (size_t)n_pairs * sizeof(PoseParam)));
     launch_prepare_pairs((const double *)LN.ws_poses.p, (const double *)LN.ws_stage.p,
                          (const int32_t *)LN.ws_fidx.p, (const int32_t *)LN.ws_midx.p, (int)n_src, (int)n_tgt,
-                         ctx->d_maps, ctx->d_frames, ctx->opt.overlap_cull, (PoseParam *)LN.ws_pairs.p,
+                         ctx->d_maps, ctx->d_frames, ov_cull(ctx->opt), (PoseParam *)LN.ws_pairs.p,
                          LN.stream);
     LN.last_matrix_pairs = n_pairs;
     unsigned long long *dcounts = (unsigned long long *)counts;
@@ -1789,7 +1796,7 @@ vgicp_status vgicp_overlap_matrix_work(vgicp_ctx *ctx, int64_t *live_pairs, int6
     if (LN.last_matrix_pairs <= 0) return VGICP_OK;
     TRY(ensure(ctx, LN.ws_counter, 16));
     CU(cudaMemsetAsync(LN.ws_counter.p, 0, 16, LN.stream));
-    launch_count_live((const PoseParam *)LN.ws_pairs.p, LN.last_matrix_pairs, ctx->d_frames,
+    launch_count_live((const PoseParam *)LN.ws_pairs.p, LN.last_matrix_pairs, ctx->d_frames, ctx->d_maps,
                       (unsigned long long *)LN.ws_counter.p, LN.stream);
     ctx->launches += 1;
     CHECK_LAUNCH();
@@ -1955,7 +1962,7 @@ vgicp_status vgicp_memory_estimate(vgicp_ctx *ctx, int64_t n, int32_t is_map, in
     if (!ctx) return VGICP_ERR_INVALID_ARG;
     if (!bytes || n < 0) return fail(ctx, VGICP_ERR_INVALID_ARG, "memory_estimate: bad arguments");
     *bytes = is_map ? (int64_t)map_bytes(map_capacity(n))
-                    : (int64_t)frame_bytes(n, ctx->opt.frame_order == 1 && n > 1);
+                    : (int64_t)frame_bytes(n, ctx->opt.frame_order != 0 && n > 1);
     return VGICP_OK;
 }
 

@@ -26,11 +26,13 @@ void launch_frame_pack(const float *points, const float *covs, int64_t n, float4
 // descriptors into the table, statistics, the streams and the cull-chunk
 // bounding boxes (2^shift points each).  Frames whose descriptor has a perm
 // array are stored in spatial order (order_scratch: 4 x total uint32, required
-// when any frame has one).
+// when order_mode is 1).  order_mode: 0 the given order; 1 spatial order of
+// each whole frame; 2 spatial order within each 4,096-point registration item
+// (points stay in their tile; no scratch).  Every frame then has a perm array.
 void launch_frames_register(const float *pts, const float *cov, const int64_t *src_off, const int32_t *fidx, int m,
                             const WorkItem *items, int n_items, const WorkItem *chunks, int n_chunks,
                             const uint32_t *desc_idx, const FrameDesc *descs, FrameDesc *table, uint32_t *order_scratch,
-                            int64_t total, int num_sms, cudaStream_t st);
+                            int64_t total, int num_sms, int order_mode, cudaStream_t st);
 void launch_chunk_boxes(const float4 *pa, int64_t n, int shift, int nchunks, float *cbox, cudaStream_t st);
 
 // Write n map descriptors into the device table: table[idx[i]] = src[i].
@@ -139,9 +141,10 @@ void launch_overlap_matrix(const PoseParam *pairs, const MapDesc *maps, const Fr
                            int n_tgt, unsigned long long *counts, void *scratch, int num_sms,
                            cudaStream_t st);
 
-// out[0] += pairs not culled, out[1] += their source sizes (out zeroed).
-void launch_count_live(const PoseParam *pairs, int64_t n_pairs, const FrameDesc *frames, unsigned long long *out,
-                       cudaStream_t st);
+// out[0] += pairs not culled, out[1] += the points the matrix kernel visits for
+// them (points of live groups in live cull chunks) (out zeroed).
+void launch_count_live(const PoseParam *pairs, int64_t n_pairs, const FrameDesc *frames, const MapDesc *maps,
+                       unsigned long long *out, cudaStream_t st);
 
 // Pair parameters of an overlap matrix: pair (s, t) -> T_t^-1 T_s; with cull set,
 // pairs whose source bounding box cannot meet the target's voxels are flagged.
@@ -218,7 +221,7 @@ struct __align__(16) LoopRequest {      // host -> device, one per slot
     int32_t kind;                       // kLoopLinearize or kLoopOverlap
     int32_t n_items;                    // chunks (1 .. kLoopMaxItems)
     int32_t chunk;                      // points per chunk (the last takes the rest)
-    int32_t cull;                       // exact culling of chunks (linearize_cull)
+    int32_t cull;                       // exact culling: 0 none, 1 chunks, 2 chunks and groups
     unsigned long long seq;             // r + 1, written last
     unsigned long long pad;
 };

@@ -134,10 +134,21 @@ __device__ void finish_param(PoseParam &p, const MapDesc &m, const FrameDesc &f,
     }
     p.cull = 0;
     p.cmask = f.nchunks >= 32 ? 0xffffffffu : ((1u << f.nchunks) - 1u);
+    bool koff_ok = true;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const long long off = (long long)m.kbox[i] - (long long)p.k0[i];
+        koff_ok = koff_ok && !(off > INT32_MAX / 2 || off < INT32_MIN / 2);
         p.koff[i] = (off > INT32_MAX / 2 || off < INT32_MIN / 2) ? INT32_MAX / 2 : (int32_t)off;
+    }
+    // group culling against the target's coarse occupancy (exact culling only)
+    const int cs = m.cmeta[4];
+    const bool coarse_ok = cull >= 2 && koff_ok && m.kbox[0] <= m.kbox[3] && cs >= 2 && cs < 31;
+    p.cs = coarse_ok ? cs : -1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p.bext[i] = coarse_ok ? m.kbox[3 + i] - m.kbox[i] : 0;
+        p.cext[i] = coarse_ok ? m.cmeta[5 + i] : 0;
     }
     if (!cull) return;
     // A source without a finite point or a map without a voxel: nothing can hit.
@@ -241,6 +252,7 @@ __global__ void k_prepare_pairs(const double *__restrict__ ps, const double *__r
         q.map = midx[t];
         q.frame = fidx[s];
         q.cull = 1;
+        q.cs = -1;
         out[g] = q;
         return;
     }
@@ -563,11 +575,24 @@ __device__ __forceinline__ void linearize_points_general(const PoseParam &P, con
 // its own shared-memory slot, runs over the item's points, reduces its 28 sums
 // by shuffles and writes them as float64 -- no block barriers anywhere.  Warps
 // take items in list order from a global counter.
-//   PTS = 1: one point per lane per step, the next step's point loads issued
-//            before this step's key, probe and record chain;
-//   PTS = 2: two points per lane per step, both points' loads, keys and first
-//            probes issued before either record is needed.
-// Points of one work item, 32 per warp step.
+// Live groups (kGroup consecutive points) gw .. gw + 31 of a work item, one bit
+// each: every group in range when the pair has no group test, else those whose
+// box may reach a voxel of the target (group_live; a dead group provably has no
+// correspondence).  The item starts on a group boundary.
+template <class L>
+__device__ __forceinline__ uint32_t live_groups(const PoseParam &P, const MapDesc &m, const FrameDesc &F,
+                                                const WorkItem &w, int gw, int ng, int lane)
+{
+    if (P.cs < 0) return (ng - gw >= 32) ? 0xffffffffu : ((1u << (ng - gw)) - 1u);
+    const bool l = gw + lane < ng &&
+                   group_live<L>(P, F.gbox + 6 * ((w.start >> 5) + gw + lane), m.r_h, m.inv_rf, m.coarse);
+    return __ballot_sync(0xffffffffu, l);
+}
+
+// Points of one work item, one lane per point.  The item's groups are taken in
+// runs of consecutive live groups (all of them when the pair has no group
+// test); dead groups are never visited.  Each lane adds its points in index
+// order whether or not dead groups are skipped, so the sums do not change.
 //   PTS = 1: one point per lane per step, the next step's point loads issued
 //            before this step's key, probe and record chain;
 //   PTS = 2: two points per lane per step, both points' loads, keys and first
@@ -580,72 +605,84 @@ __device__ __forceinline__ void linearize_points(const PoseParam &P, const MapDe
     const float4 *__restrict__ pa = F.pa + w.start;
     const float4 *__restrict__ pb = F.pb + w.start;
     const float *__restrict__ pc = F.pc + w.start;
-    const int n = w.count;
-    if (PTS == 1) {
-        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
-        float C = 0.f;
-        if (lane < n) {
-            A = L::ld(pa + lane);
-            B = L::ld(pb + lane);
-            C = L::ld(pc + lane);
-        }
-        for (int i = lane; i < n; i += 32) {
-            const float4 A0 = A, B0 = B;
-            const float C0 = C;
-            if (i + 32 < n) {
-                A = L::ld(pa + i + 32);
-                B = L::ld(pb + i + 32);
-                C = L::ld(pc + i + 32);
+    const int n_all = w.count, ng = (n_all + kGroup - 1) / kGroup;
+    for (int gw = 0; gw < ng; gw += 32) {
+        uint32_t live = live_groups<L>(P, m, F, w, gw, ng, lane);
+        while (live) {
+            // the next run of consecutive live groups: points [i_begin, n)
+            const int a = __ffs(live) - 1;
+            const uint32_t rest = ~(live >> a);
+            const int len = rest ? __ffs(rest) - 1 : 32 - a;
+            live = (a + len >= 32) ? 0u : (live & (~0u << (a + len)));
+            const int i_begin = (gw + a) * kGroup;
+            const int n = min(n_all, (gw + a + len) * kGroup);
+            if (PTS == 1) {
+                float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
+                float C = 0.f;
+                if (i_begin + lane < n) {
+                    A = L::ld(pa + i_begin + lane);
+                    B = L::ld(pb + i_begin + lane);
+                    C = L::ld(pc + i_begin + lane);
+                }
+                for (int i = i_begin + lane; i < n; i += 32) {
+                    const float4 A0 = A, B0 = B;
+                    const float C0 = C;
+                    if (i + 32 < n) {
+                        A = L::ld(pa + i + 32);
+                        B = L::ld(pb + i + 32);
+                        C = L::ld(pc + i + 32);
+                    }
+                    float d0[3], x0[3];
+                    const PointSlot s0 = point_hash<FF>(P, m, A0.x, A0.y, A0.z, d0, x0);
+                    uint64_t f0 = kEmptyKey;
+                    VoxelRec v0;
+                    if (s0.ok) {   // the record of the first slot probed travels with its key
+                        f0 = L::ld(m.keys + s0.h);
+                        v0 = load_rec<L>(m.rec + s0.h);
+                    }
+                    const int slot0 = resolve_slot<L>(m, s0, f0);
+                    record_point<REC>(rc, rbase + i, s0.ok, s0.key, slot0 >= 0);
+                    if (slot0 < 0) continue;
+                    if (slot0 != (int)s0.h) v0 = load_rec<L>(m.rec + slot0);
+                    inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
+                }
+            } else {
+                for (int i0 = i_begin + lane; i0 < n; i0 += 64) {
+                    const int i1 = i0 + 32;
+                    const bool h1 = i1 < n;
+                    const float4 A0 = L::ld(pa + i0), B0 = L::ld(pb + i0);
+                    const float C0 = L::ld(pc + i0);
+                    float4 A1 = make_float4(0.f, 0.f, 0.f, 0.f), B1 = A1;
+                    float C1 = 0.f;
+                    if (h1) {
+                        A1 = L::ld(pa + i1);
+                        B1 = L::ld(pb + i1);
+                        C1 = L::ld(pc + i1);
+                    }
+                    float d0[3], x0[3], d1[3], x1[3];
+                    PointSlot s0 = point_hash<FF>(P, m, A0.x, A0.y, A0.z, d0, x0);
+                    PointSlot s1 = point_hash<FF>(P, m, A1.x, A1.y, A1.z, d1, x1);
+                    s1.ok = s1.ok && h1;
+                    uint64_t f0 = kEmptyKey, f1 = kEmptyKey;
+                    VoxelRec v0, v1;
+                    if (s0.ok) {
+                        f0 = L::ld(m.keys + s0.h);
+                        v0 = load_rec<L>(m.rec + s0.h);
+                    }
+                    if (s1.ok) {
+                        f1 = L::ld(m.keys + s1.h);
+                        v1 = load_rec<L>(m.rec + s1.h);
+                    }
+                    const int slot0 = resolve_slot<L>(m, s0, f0);
+                    const int slot1 = resolve_slot<L>(m, s1, f1);
+                    record_point<REC>(rc, rbase + i0, s0.ok, s0.key, slot0 >= 0);
+                    if (h1) record_point<REC>(rc, rbase + i1, s1.ok, s1.key, slot1 >= 0);
+                    if (slot0 >= 0 && slot0 != (int)s0.h) v0 = load_rec<L>(m.rec + slot0);
+                    if (slot1 >= 0 && slot1 != (int)s1.h) v1 = load_rec<L>(m.rec + slot1);
+                    if (slot0 >= 0) inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
+                    if (slot1 >= 0) inl += accumulate<NT>(acc, P.Rh, A1, B1, C1, v1, d1, x1);
+                }
             }
-            float d0[3], x0[3];
-            const PointSlot s0 = point_hash<FF>(P, m, A0.x, A0.y, A0.z, d0, x0);
-            uint64_t f0 = kEmptyKey;
-            VoxelRec v0;
-            if (s0.ok) {   // the record of the first slot probed travels with its key
-                f0 = L::ld(m.keys + s0.h);
-                v0 = load_rec<L>(m.rec + s0.h);
-            }
-            const int slot0 = resolve_slot<L>(m, s0, f0);
-            record_point<REC>(rc, rbase + i, s0.ok, s0.key, slot0 >= 0);
-            if (slot0 < 0) continue;
-            if (slot0 != (int)s0.h) v0 = load_rec<L>(m.rec + slot0);
-            inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
-        }
-    } else {
-        for (int i0 = lane; i0 < n; i0 += 64) {
-            const int i1 = i0 + 32;
-            const bool h1 = i1 < n;
-            const float4 A0 = L::ld(pa + i0), B0 = L::ld(pb + i0);
-            const float C0 = L::ld(pc + i0);
-            float4 A1 = make_float4(0.f, 0.f, 0.f, 0.f), B1 = A1;
-            float C1 = 0.f;
-            if (h1) {
-                A1 = L::ld(pa + i1);
-                B1 = L::ld(pb + i1);
-                C1 = L::ld(pc + i1);
-            }
-            float d0[3], x0[3], d1[3], x1[3];
-            PointSlot s0 = point_hash<FF>(P, m, A0.x, A0.y, A0.z, d0, x0);
-            PointSlot s1 = point_hash<FF>(P, m, A1.x, A1.y, A1.z, d1, x1);
-            s1.ok = s1.ok && h1;
-            uint64_t f0 = kEmptyKey, f1 = kEmptyKey;
-            VoxelRec v0, v1;
-            if (s0.ok) {
-                f0 = L::ld(m.keys + s0.h);
-                v0 = load_rec<L>(m.rec + s0.h);
-            }
-            if (s1.ok) {
-                f1 = L::ld(m.keys + s1.h);
-                v1 = load_rec<L>(m.rec + s1.h);
-            }
-            const int slot0 = resolve_slot<L>(m, s0, f0);
-            const int slot1 = resolve_slot<L>(m, s1, f1);
-            record_point<REC>(rc, rbase + i0, s0.ok, s0.key, slot0 >= 0);
-            if (h1) record_point<REC>(rc, rbase + i1, s1.ok, s1.key, slot1 >= 0);
-            if (slot0 >= 0 && slot0 != (int)s0.h) v0 = load_rec<L>(m.rec + slot0);
-            if (slot1 >= 0 && slot1 != (int)s1.h) v1 = load_rec<L>(m.rec + slot1);
-            if (slot0 >= 0) inl += accumulate<NT>(acc, P.Rh, A0, B0, C0, v0, d0, x0);
-            if (slot1 >= 0) inl += accumulate<NT>(acc, P.Rh, A1, B1, C1, v1, d1, x1);
         }
     }
 }
@@ -1395,6 +1432,7 @@ __device__ void loop_dispatch(const LoopArgs &a, unsigned long long *sreq, int32
         // the map's voxel box and the frame's statistics and chunk boxes, read
         // from L2 into shared memory for the pose parameters
         warp_copy_cg((uint32_t *)skbox, (const uint32_t *)R.map.kbox, 6, lane);
+        warp_copy_cg((uint32_t *)(skbox + 8), (const uint32_t *)R.map.cmeta, 8, lane);
         warp_copy_cg((uint32_t *)sstats, (const uint32_t *)R.frame.stats, kStatCount, lane);
         warp_copy_cg((uint32_t *)scbox, (const uint32_t *)R.frame.cbox, 6 * min(R.frame.nchunks, kMaxCullChunks),
                      lane);
@@ -1403,6 +1441,7 @@ __device__ void loop_dispatch(const LoopArgs &a, unsigned long long *sreq, int32
             MapDesc m = R.map;
             FrameDesc f = R.frame;
             m.kbox = skbox;
+            m.cmeta = skbox + 8;
             f.stats = sstats;
             f.cbox = scbox;
             PoseParam P;
@@ -1563,7 +1602,7 @@ __global__ void __launch_bounds__(kLoopBlock) k_request_loop(LoopArgs a)
     __shared__ FrameDesc sF[NW];
     __shared__ double sFin[NW][186];
     __shared__ __align__(16) unsigned long long sReq[kReqWords];
-    __shared__ int32_t sKbox[6];
+    __shared__ int32_t sKbox[16];        // voxel box (6), then the map's metadata words (8)
     __shared__ float sStats[kStatCount];
     __shared__ float sCbox[6 * kMaxCullChunks];
     const int wib = threadIdx.x >> 5;

@@ -102,26 +102,10 @@ __global__ void __launch_bounds__(256) k_overlap(const PoseParam *__restrict__ p
 constexpr int kOvBlock = 1024, kPPT = 4, kSlice = 16;
 constexpr int kSmemLog2 = 15;   // 32,768 compact keys = 128 KB of shared memory
 
-// Presence of the voxel at box-relative coordinate (dx, dy, dz) in a compact
-// table (ext = box extents); anything outside the box is absent.
-__device__ __forceinline__ bool compact_hit(const uint32_t *__restrict__ tab, uint32_t lg, int ex, int ey, int ez,
-                                            int dx, int dy, int dz)
-{
-    if ((unsigned)dx > (unsigned)ex || (unsigned)dy > (unsigned)ey || (unsigned)dz > (unsigned)ez) return false;
-    const uint32_t ck = pack_compact(dx, dy, dz), mask = (1u << lg) - 1u;
-    uint32_t s = hash_compact(ck, lg);
-    for (uint32_t i = 0; i <= mask; ++i) {
-        const uint32_t v = tab[s];
-        if (v == ck) return true;
-        if (v == kEmptyCompact) return false;
-        s = (s + 1) & mask;
-    }
-    return false;
-}
-
 // Shared-memory words of the small CTAs (two 512-thread CTAs per SM, 64 KB
 // each) and of the large ones (one 1024-thread CTA per SM, 128 KB).
 constexpr int kSmallWords = 16384;
+
 
 // Items are fetched in tiers of decreasing size (live cull chunks of the
 // item: at least kTierChunks[0], then kTierChunks[1], ..., then the rest), so
@@ -192,8 +176,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
     __shared__ MapDesc sM;
     __shared__ int s_kb[6], s_lg, s_smem, s_words;   // voxel box, compact table size, staged: 1 table, 2 bitmap
     __shared__ const float4 *s_pa[kSlice];
-    __shared__ int s_n[kSlice], s_csh[kSlice], s_nlive[kSlice];
-    __shared__ unsigned char s_live[kSlice][kMaxCullChunks];   // live cull chunks of each source, in order
+    __shared__ const float *s_gb[kSlice];
+    __shared__ int s_n[kSlice], s_csh[kSlice];
     __shared__ int s_q;
     const int lane = threadIdx.x & 31;
     int n_live = 0;
@@ -219,13 +203,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
                 for (int j = lane; j < PW; j += 32) dst[j] = __ldg(src + j);
                 const PoseParam &Pg = pairs[(int64_t)(s0 + wib) * n_tgt + t];
                 const FrameDesc &F = frames[__ldg((const int *)&Pg.frame)];
-                const uint32_t cm = __ldg((const unsigned int *)&Pg.cmask);
-                if ((cm >> lane) & 1u) s_live[wib][__popc(cm & ((1u << lane) - 1u))] = (unsigned char)lane;
                 if (lane == 0) {
                     s_pa[wib] = F.pa;
+                    s_gb[wib] = F.gbox;
                     s_n[wib] = (int)F.n;
                     s_csh[wib] = F.cshift;
-                    s_nlive[wib] = __popc(cm);
                 }
             }
         }
@@ -253,17 +235,29 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
             const PoseParam &P = sP[si];
             if (P.cull) continue;                       // uniform across the block
             const float4 *__restrict__ pa = s_pa[si];
-            const int n = s_n[si], csh = s_csh[si];
-            const int nv = s_nlive[si] << csh;          // points of the live chunks, end to end
-            const unsigned char *live = s_live[si];
+            const int n = s_n[si], csh = s_csh[si], ng = (n + kGroup - 1) / kGroup;
+            constexpr int NW = BLOCK / 32;
+            const int wid = (int)(threadIdx.x >> 5);
             unsigned int hits = 0;
-            for (int base = 0; base < nv; base += BLOCK * kPPT) {
+            // warp wid takes groups wid, wid + NW, ...: 32 candidates per round, one
+            // per lane, kept when in a live cull chunk and (with a group test) when
+            // reaching an occupied coarse cell of the target; then the live ones,
+            // kPPT groups per step, one lane per point.  No block barrier.
+            for (int gr = wid; gr < ng; gr += NW * 32) {
+                const int gc = gr + NW * lane;
+                bool l = gc < ng && ((P.cmask >> (((int64_t)gc * kGroup) >> csh)) & 1u);
+                if (l && P.cs >= 0) l = group_live(P, s_gb[si] + 6 * (int64_t)gc, m.r_h, m.inv_rf, m.coarse);
+                uint32_t livem = __ballot_sync(0xffffffffu, l);
+            while (livem) {
                 float px[kPPT], py[kPPT], pz[kPPT];
                 bool have[kPPT];
 #pragma unroll
                 for (int j = 0; j < kPPT; ++j) {
-                    const int vi = base + j * BLOCK + threadIdx.x;
-                    const int i = vi < nv ? ((int)live[vi >> csh] << csh) + (vi & ((1 << csh) - 1)) : n;
+                    int i = n;
+                    if (livem) {
+                        i = (gr + NW * (__ffs(livem) - 1)) * kGroup + lane;
+                        livem &= livem - 1u;
+                    }
                     have[j] = i < n;
                     const float4 A = have[j] ? __ldg(pa + i) : make_float4(0.f, 0.f, 0.f, 0.f);
                     px[j] = A.x; py[j] = A.y; pz[j] = A.z;
@@ -354,6 +348,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
                     }
                 }
             }
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
             if (lane == 0 && hits)
@@ -394,27 +389,35 @@ __global__ void k_correspondences(const PoseParam *__restrict__ prm, const MapDe
     }
 }
 
+// out[0] += pairs not culled, out[1] += the points the matrix kernel visits for
+// them (points of the live groups of live chunks); one warp per pair.
 __global__ void k_count_live(const PoseParam *__restrict__ pairs, int64_t n_pairs,
-                             const FrameDesc *__restrict__ frames, unsigned long long *out)
+                             const FrameDesc *__restrict__ frames, const MapDesc *__restrict__ maps,
+                             unsigned long long *out)
 {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long live = 0, pts = 0;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_pairs; g += (int64_t)gridDim.x * blockDim.x)
-        if (!pairs[g].cull) {
-            ++live;
-            const FrameDesc &F = frames[pairs[g].frame];
-            const uint32_t cm = pairs[g].cmask;
-            for (int c = 0; c < F.nchunks; ++c)
-                if ((cm >> c) & 1u) {
-                    const int64_t b = (int64_t)c << F.cshift, e = min(F.n, b + ((int64_t)1 << F.cshift));
-                    pts += (unsigned long long)(e - b);
-                }
+    for (int64_t g = w0; g < n_pairs; g += nw) {
+        const PoseParam &P = pairs[g];
+        if (P.cull) continue;
+        live += lane == 0;
+        const FrameDesc &F = frames[P.frame];
+        const MapDesc &m = maps[P.map];
+        const int64_t ng = (F.n + kGroup - 1) / kGroup;
+        for (int64_t q = lane; q < ng; q += 32) {
+            bool l = (P.cmask >> ((q * kGroup) >> F.cshift)) & 1u;
+            if (l && P.cs >= 0) l = group_live(P, F.gbox + 6 * q, m.r_h, m.inv_rf, m.coarse);
+            if (l) pts += (unsigned long long)min((int64_t)kGroup, F.n - q * kGroup);
         }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         live += __shfl_xor_sync(0xffffffffu, live, o);
         pts += __shfl_xor_sync(0xffffffffu, pts, o);
     }
-    if ((threadIdx.x & 31) == 0 && live) {
+    if (lane == 0 && (live || pts)) {
         atomicAdd(out, live);
         atomicAdd(out + 1, pts);
     }
@@ -422,11 +425,11 @@ __global__ void k_count_live(const PoseParam *__restrict__ pairs, int64_t n_pair
 
 }  // namespace
 
-void launch_count_live(const PoseParam *pairs, int64_t n_pairs, const FrameDesc *frames, unsigned long long *out,
-                       cudaStream_t st)
+void launch_count_live(const PoseParam *pairs, int64_t n_pairs, const FrameDesc *frames, const MapDesc *maps,
+                       unsigned long long *out, cudaStream_t st)
 {
     if (n_pairs <= 0) return;
-    k_count_live<<<148 * 4, 256, 0, st>>>(pairs, n_pairs, frames, out);
+    k_count_live<<<148 * 8, 256, 0, st>>>(pairs, n_pairs, frames, maps, out);
 }
 
 void launch_overlap(const PoseParam *params, const MapDesc *maps, const FrameDesc *frames, const WorkItem *items,

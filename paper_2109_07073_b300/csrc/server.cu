@@ -56,6 +56,8 @@ struct Resident {
     uint64_t last_use = 0;
     int64_t key = 0;                // tagged key (position in the LRU order: (last_use, key))
     int pins = 0;                   // batches in flight that use it
+    cudaEvent_t ready = nullptr;    // device loop: recorded after the object's admission
+    bool ready_done = true;         // ... and seen complete
 };
 
 struct Pending {
@@ -131,6 +133,8 @@ struct vgicp_server {
     std::vector<unsigned long long> slot_seq;
     std::vector<std::pair<int64_t, int64_t>> slot_keys;      // tagged keys the slot's request pins
     std::vector<int> inflight;                               // slots with a request in flight
+    std::vector<int64_t> waiting;                            // admitted, objects' copies / builds in flight
+    std::deque<int64_t> ready_q;                             // objects ready, waiting for a ring slot
 };
 
 namespace {
@@ -530,9 +534,12 @@ vgicp_status launch_loop(vgicp_server *s)
     return VGICP_OK;
 }
 
-// Admit request t's objects and write it into the next ring slot (scheduler
-// thread, mutex not held).  VGICP_ERR_BUDGET: defer (nothing was published).
-vgicp_status publish(vgicp_server *s, int64_t t)
+// Make request t's objects resident without waiting for their copies and
+// builds (scheduler thread, mutex not held): an admitted object records an
+// event on the context stream that says when it is ready; the request pins
+// both objects from here until its result is read.  VGICP_ERR_BUDGET: defer
+// (nothing pinned).
+vgicp_status prepare(vgicp_server *s, int64_t t)
 {
     vgicp_request r;
     Resident *m, *f;
@@ -544,49 +551,87 @@ vgicp_status publish(vgicp_server *s, int64_t t)
     }
     const auto ta = Clock::now();
     vgicp_status st = VGICP_OK;
-    const bool admitting = m->handle < 0 || f->handle < 0;
-    if (admitting) {
-        st = admit(s, *m);
+    if (m->handle < 0 || f->handle < 0) {
+        vg::CtxView v;
+        vg::ctx_view(s->ctx, &v);
+        auto admit_ready = [&](Resident &o) {
+            if (o.handle >= 0) return VGICP_OK;
+            const vgicp_status a = admit(s, o);
+            if (a != VGICP_OK) return a;
+            if (!o.ready && cudaEventCreateWithFlags(&o.ready, cudaEventDisableTiming) != cudaSuccess)
+                return VGICP_ERR_CUDA;
+            if (cudaEventRecord(o.ready, v.stream) != cudaSuccess) return VGICP_ERR_CUDA;
+            o.ready_done = false;
+            return VGICP_OK;
+        };
+        st = admit_ready(*m);
         if (st == VGICP_OK) {
             { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
-            st = admit(s, *f);
+            st = admit_ready(*f);
             std::lock_guard<std::mutex> lk(s->mu);
             m->pins--;
         }
-        // the loop reads the new objects: their copies and builds must be complete
-        if (st == VGICP_OK) st = vgicp_synchronize(s->ctx);
     }
     const double admit_ms = std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
-    if (st != VGICP_OK) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->host_admit_ms += admit_ms;
-        return st;
-    }
-    vg::MapDesc md;
-    vg::FrameDesc fd;
-    int64_t n = 0;
-    if (!vg::ctx_descs(s->ctx, m->handle, f->handle, &md, &fd, &n)) return VGICP_ERR_NOT_FOUND;
     std::lock_guard<std::mutex> lk(s->mu);
     s->host_admit_ms += admit_ms;
+    if (st != VGICP_OK) return st;
+    m->pins++;
+    f->pins++;
     for (Resident *o : {m, f}) {
         s->lru.erase({o->last_use, o->key});
         o->last_use = ++s->clock;
         s->lru.insert({o->last_use, o->key});
     }
+    return VGICP_OK;
+}
+
+// Whether an object's admission has completed on the device (mutex held).
+bool object_ready(Resident &o)
+{
+    if (!o.ready_done && cudaEventQuery(o.ready) == cudaSuccess) o.ready_done = true;
+    return o.ready_done;
+}
+
+// Unpin a prepared request's objects (mutex held).
+void unpin(vgicp_server *s, int64_t t)
+{
+    const vgicp_request &r = s->reqs[t].req;
+    s->objs[tag(r.target, true)].pins--;
+    s->objs[tag(r.source, false)].pins--;
+}
+
+// Write prepared request t, whose objects are ready, into the next ring slot
+// (mutex held; the slot is free).
+void publish_slot(vgicp_server *s, int64_t t)
+{
+    const vgicp_request r = s->reqs[t].req;
+    Resident &m = s->objs[tag(r.target, true)], &f = s->objs[tag(r.source, false)];
+    vg::MapDesc md;
+    vg::FrameDesc fd;
+    int64_t n = 0;
     Pending &p = s->reqs[t];
+    if (!vg::ctx_descs(s->ctx, m.handle, f.handle, &md, &fd, &n)) {
+        unpin(s, t);
+        complete(s, t, VGICP_ERR_NOT_FOUND);
+        ++s->completed;
+        return;
+    }
     if (n == 0) {                      // nothing to run: an empty sum, or Eq. 8 undefined
+        unpin(s, t);
         complete(s, t, r.kind == VGICP_REQ_OVERLAP ? VGICP_ERR_EMPTY : VGICP_OK);
         s->lat_ms.push_back(p.res.latency_ms);
         ++s->completed;
-        return VGICP_OK;
+        return;
     }
     const int c = vg::item_chunk(n, s->chunk);
     const int64_t items = (n + c - 1) / c;
     if (items > vg::kLoopMaxItems) {
+        unpin(s, t);
         s->err = "request larger than 128 chunks";
         complete(s, t, VGICP_ERR_INVALID_ARG);
         ++s->completed;
-        return VGICP_OK;
+        return;
     }
     const int slot = (int)(s->n_pub % (unsigned long long)s->slots);
     const unsigned long long seq = ++s->n_pub;
@@ -600,13 +645,10 @@ vgicp_status publish(vgicp_server *s, int64_t t)
     q.cull = s->cull;
     __atomic_store_n(&s->h_res[slot].done, 0ull, __ATOMIC_RELAXED);
     __atomic_store_n(&q.seq, seq, __ATOMIC_RELEASE);      // the request is visible to the loop from here
-    m->pins++;
-    f->pins++;
     s->slot_ticket[slot] = t;
     s->slot_seq[slot] = seq;
     s->slot_keys[slot] = {tag(r.target, true), tag(r.source, false)};
     s->inflight.push_back(slot);
-    return VGICP_OK;
 }
 
 // Fail every request in flight (mutex held).
@@ -668,35 +710,66 @@ void scheduler_device(vgicp_server *s)
             }
             harvest_slots(s);
             fail_inflight(s, VGICP_ERR_CUDA);
+            for (int64_t t : s->waiting) {
+                unpin(s, t);
+                complete(s, t, VGICP_ERR_CUDA);
+                ++s->completed;
+            }
+            for (int64_t t : s->ready_q) {
+                unpin(s, t);
+                complete(s, t, VGICP_ERR_CUDA);
+                ++s->completed;
+            }
+            s->waiting.clear();
+            s->ready_q.clear();
+            s->cv_done.notify_all();
             return;
         }
-        // publish pending requests while the ring has room in order
         const auto tl = Clock::now();
         bool published = false;
-        while (!s->pending.empty() && s->slot_ticket[s->n_pub % (unsigned long long)s->slots] < 0) {
+        // admit pending requests (asynchronously), at most a ring's worth ahead of publishing
+        while (!s->pending.empty() && s->waiting.size() + s->ready_q.size() < (size_t)s->slots) {
             const int64_t t = s->pending.front();
             s->pending.pop_front();
             lk.unlock();
-            const vgicp_status st = publish(s, t);
+            const vgicp_status st = prepare(s, t);
             lk.lock();
             if (st == VGICP_ERR_BUDGET) {
-                if (s->inflight.empty()) {             // nothing to wait for: it can never fit
-                    complete(s, t, VGICP_ERR_BUDGET);
+                if (s->inflight.empty() && s->waiting.empty() && s->ready_q.empty()) {
+                    complete(s, t, VGICP_ERR_BUDGET);   // nothing to wait for: it can never fit
                     ++s->completed;
                     s->cv_done.notify_all();
                     continue;
                 }
-                s->pending.push_front(t);              // retry when in-flight requests release objects
+                s->pending.push_front(t);              // retry when other requests release objects
                 break;
             }
             if (st != VGICP_OK) {
                 complete(s, t, st);
                 ++s->completed;
+                s->cv_done.notify_all();
+                continue;
             }
+            s->waiting.push_back(t);
+        }
+        // requests whose objects' copies and builds are complete, in order
+        for (size_t q = 0; q < s->waiting.size();) {
+            const vgicp_request &r = s->reqs[s->waiting[q]].req;
+            if (object_ready(s->objs[tag(r.target, true)]) && object_ready(s->objs[tag(r.source, false)])) {
+                s->ready_q.push_back(s->waiting[q]);
+                s->waiting.erase(s->waiting.begin() + (ptrdiff_t)q);
+            } else {
+                ++q;
+            }
+        }
+        // into the ring while it has room in order
+        while (!s->ready_q.empty() && s->slot_ticket[s->n_pub % (unsigned long long)s->slots] < 0) {
+            publish_slot(s, s->ready_q.front());
+            s->ready_q.pop_front();
             published = true;
-            s->cv_done.notify_all();
         }
         if (published) {
+            s->cv_done.notify_all();
             s->host_launch_ms += std::chrono::duration<double, std::milli>(Clock::now() - tl).count();
             int64_t bytes = 0;
             vgicp_memory_in_use(s->ctx, &bytes);
@@ -707,8 +780,9 @@ void scheduler_device(vgicp_server *s)
             const vgicp_status st = launch_loop(s);
             if (st != VGICP_OK) fail_inflight(s, st);  // rather than wait forever
         }
-        if (!s->inflight.empty()) {
-            // results arrive in host memory: poll, yielding the core, then sleep a little
+        if (!s->inflight.empty() || !s->waiting.empty() || !s->ready_q.empty()) {
+            // results arrive in host memory, admissions complete on the device: poll,
+            // yielding the core, then sleep a little
             lk.unlock();
             if (++idle_polls < 2000) std::this_thread::yield();
             else std::this_thread::sleep_for(std::chrono::microseconds(50));
@@ -726,7 +800,7 @@ vgicp_status loop_setup(vgicp_server *s, const vgicp_options &ko)
     s->slots = s->opt.loop_slots > 0 ? s->opt.loop_slots : 256;
     s->idle_ms = s->opt.loop_idle_ms > 0.0 ? s->opt.loop_idle_ms : 20.0;
     s->chunk = ko.chunk_points > 0 ? ko.chunk_points : 2048;
-    s->cull = ko.linearize_cull;
+    s->cull = ko.linearize_cull ? (ko.group_cull ? 2 : 1) : 0;   // culling level (chunks, groups)
     unsigned int q = 1;
     while (q < (unsigned int)s->slots * (unsigned int)vg::kLoopMaxItems) q <<= 1;
     s->qcap = q;
@@ -917,6 +991,8 @@ vgicp_status vgicp_server_destroy(vgicp_server *s)
     s->thr.join();
     if (s->dloop) {
         loop_free(s);
+        for (auto &kv : s->objs)
+            if (kv.second.ready) cudaEventDestroy(kv.second.ready);
         vgicp_destroy(s->ctx);
         for (char *p : s->slabs) cudaFreeHost(p);
         delete s;

@@ -84,7 +84,6 @@ struct Skyline {
     std::vector<int64_t> first, off;
     std::vector<double> a;
     double &at(int64_t r, int64_t c) { return a[off[r] + (c - first[r])]; }
-    bool inside(int64_t r, int64_t c) const { return c >= first[r] && c <= r; }
 };
 
 // The global system's product H x from the factor blocks (x, y: 6 per pose).

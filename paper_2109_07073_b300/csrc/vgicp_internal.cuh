@@ -62,6 +62,8 @@ struct MapDesc {
     int32_t *kbox;       // device: min voxel coordinate (3), max voxel coordinate (3)
     uint32_t *ckeys;     // compact presence table (capacity cap; the first 2^cmeta[0] entries used)
     int32_t *cmeta;      // device: log2 of the compact table's used capacity, 1 if the map has one
+                         // (cmeta[4] coarse shift or -1, cmeta[5..7] coarse grid extents)
+    uint32_t *coarse;    // coarse occupancy bitmap over the voxel box (kCoarseWords words)
     uint32_t mask;       // cap - 1
     uint32_t log2cap;    // >= 4
     double r, inv_r;     // resolution and fl64(1 / r)
@@ -80,7 +82,18 @@ struct FrameDesc {
     int32_t cshift;      // cull chunk = 2^cshift consecutive points (>= 10, so <= 32 chunks)
     int32_t nchunks;
     const int32_t *perm; // device: given index of the point stored at each position (null: given order)
+    const float *gbox;   // device: per group of kGroup consecutive points min xyz, max xyz (finite points)
 };
+
+// Groups of consecutive stored points with a bounding box each (exact culling
+// below the cull chunks: with the points in spatial order a group is compact).
+constexpr int kGroup = 32;
+// Coarse occupancy of a voxelmap: one bit per cell of 2^shift x 2^shift x 2^shift
+// voxels over its voxel box (shift >= 2, the smallest that fits kCoarseWords
+// words), set when the cell holds a voxel.  A group test spanning more than
+// kCoarseMaxCells cells takes the group as live without looking.
+constexpr int kCoarseWords = 1024;
+constexpr int kCoarseMaxCells = 16;
 
 constexpr int kMaxCullChunks = 32;
 
@@ -138,6 +151,9 @@ struct __align__(16) PoseParam {
     int32_t koff[3];     // target voxel-box minimum minus k0: compact coordinate = floor(x'/r) - koff
     uint32_t cmask;      // bit c: cull chunk c of the source may have correspondences
     float hm[3];         // overlap floor decided when |frac(x / r) - 1/2| <= hm (see axis_box)
+    int32_t cs;          // group culling: the target's coarse shift, or -1 (no group test)
+    int32_t cext[3];     // coarse grid extents of the target (cells per axis)
+    int32_t bext[3];     // voxel box extents of the target minus one (voxels per axis - 1)
 };
 
 // ---------------------------------------------------------------- keys ----
@@ -355,6 +371,57 @@ __device__ __forceinline__ bool axis_key_f32(const float *Rh, float th, float px
     }
     k = (int)kf;
     return true;
+}
+
+// Whether a group of source points may have a voxel in the target map under the
+// pair's pose; false is exact (no point of the group has one).  gb: the group's
+// box (min xyz, max xyz of its finite points; min > max when it has none).  The
+// box moves by the float32 pose on the split translation -- centre Rh c + tfh,
+// half extent |Rh| h -- grown by 2^-18 of the magnitudes involved plus 1e-6 r:
+// 16 times the float32 error of that evaluation and of Rh, tfh against the
+// float64 pose, and far above the float64 reference's own rounding.  Divided by
+// r with a further 2^-20 relative margin, it gives per axis a range of voxel
+// coordinates (relative to the target's voxel box through koff) that holds
+// every point's reference coordinate; the coarse cells it spans are looked up in
+// the target's coarse occupancy bitmap.  A range outside the box on any axis is
+// dead; one spanning more than kCoarseMaxCells cells, or not finite, is live.
+template <class L = LdNC>
+__device__ __forceinline__ bool group_live(const PoseParam &P, const float *__restrict__ gb, float r_h,
+                                          float inv_rf, const uint32_t *__restrict__ coarse)
+{
+    float b[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) b[j] = L::ld(gb + j);
+    if (!(b[0] <= b[3] && b[1] <= b[4] && b[2] <= b[5])) return false;   // no finite point
+    int lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float *R = P.Rh + 3 * a;
+        float c = P.tfh[a], e = 0.f, mag = fabsf(P.tfh[a]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float cc = 0.5f * (b[j] + b[3 + j]), hh = 0.5f * (b[3 + j] - b[j]);
+            c = fmaf(R[j], cc, c);
+            e = fmaf(fabsf(R[j]), hh, e);
+            mag = fmaf(fabsf(R[j]), fabsf(cc) + hh, mag);
+        }
+        const float mu = mag * 0x1p-18f + 1e-6f * r_h + 1e-30f;
+        float ylo = (c - e - mu) * inv_rf, yhi = (c + e + mu) * inv_rf;
+        const float dy = (fabsf(ylo) + fabsf(yhi)) * 0x1p-20f + 0x1p-20f;
+        ylo = floorf(ylo - dy) - (float)P.koff[a];
+        yhi = floorf(yhi + dy) - (float)P.koff[a];
+        if (yhi < 0.f || ylo > (float)P.bext[a]) return false;       // misses the voxel box
+        lo[a] = (int)fmaxf(ylo, 0.f) >> P.cs;                         // (not finite: the whole box)
+        hi[a] = (int)fminf(yhi, (float)P.bext[a]) >> P.cs;
+    }
+    if ((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) > kCoarseMaxCells) return true;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+                const uint32_t bit = (uint32_t)x + (uint32_t)P.cext[0] * ((uint32_t)y + (uint32_t)P.cext[1] * (uint32_t)z);
+                if ((L::ld(coarse + (bit >> 5)) >> (bit & 31)) & 1u) return true;
+            }
+    return false;
 }
 
 }  // namespace vg

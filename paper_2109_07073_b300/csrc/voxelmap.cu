@@ -88,7 +88,8 @@ __global__ void k_frames_init(const int32_t *__restrict__ fidx, int m, const Fra
 
 // mode 0: write the streams in the given order and gather the statistics;
 // mode 1: statistics only; mode 2: write the streams in the frame's stored
-// point order (stream position i takes given point perm[i]), no statistics.
+// point order (stream position i takes given point perm[i]; a frame without a
+// perm array, one of at most one point, in the given order), no statistics.
 __global__ void k_frames_pack(const float *__restrict__ pts, const float *__restrict__ cov,
                               const int64_t *__restrict__ src_off, const int32_t *__restrict__ fidx,
                               const WorkItem *__restrict__ items, int n_items, const FrameDesc *__restrict__ frames,
@@ -100,7 +101,7 @@ __global__ void k_frames_pack(const float *__restrict__ pts, const float *__rest
         const float *p0 = pts + 3 * src_off[w.unit], *c0 = cov + 6 * src_off[w.unit];
         if (mode == 2) {
             for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
-                const int64_t i = w.start + k, j = F.perm[i];
+                const int64_t i = w.start + k, j = F.perm ? (int64_t)F.perm[i] : i;   // one-point frames: no perm
                 const float *p = p0 + 3 * j, *c = c0 + 6 * j;
                 ((float4 *)F.pa)[i] = make_float4(p[0], p[1], p[2], c[0]);
                 ((float4 *)F.pb)[i] = make_float4(c[1], c[2], c[3], c[4]);
@@ -165,7 +166,7 @@ __global__ void k_frames_pack(const float *__restrict__ pts, const float *__rest
 // point stored at i): deterministic, so a cloud registered twice is stored
 // the same way.  Scratch: 4 arrays of total-points uint32 (keys and indices,
 // two buffers), frame u's points at src_off[u].
-constexpr int kSortBlock = 1024, kSortBins = 256, kSortWarps = kSortBlock / 32;
+constexpr int kSortBlock = 256, kSortBins = 256, kSortWarps = kSortBlock / 32;
 
 __device__ __forceinline__ uint32_t spread3(uint32_t v)
 {
@@ -279,6 +280,112 @@ __global__ void __launch_bounds__(kSortBlock) k_frames_order(const float *__rest
     }
 }
 
+// Spatial point order within tiles: every registration item (4,096 consecutive
+// given points of one frame, one block) sorted on its own by the same 24-bit
+// Morton cell codes as k_frames_order (cells over the whole frame's box),
+// ties by given index: a bitonic sort of 4,096 unique 64-bit keys (code,
+// index) in shared memory.  Points stay within their tile, so a frame of any
+// size is ordered by as many blocks as it has tiles.
+constexpr int kTileSort = 4096, kTileBlock = 1024;
+
+__global__ void __launch_bounds__(kTileBlock) k_frames_order_tiles(const float *__restrict__ pts,
+                                                                   const int64_t *__restrict__ src_off,
+                                                                   const int32_t *__restrict__ fidx,
+                                                                   const WorkItem *__restrict__ items, int n_items,
+                                                                   const FrameDesc *__restrict__ frames)
+{
+    __shared__ unsigned long long s_key[kTileSort];
+    const int t = threadIdx.x;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const FrameDesc F = frames[fidx[w.unit]];
+        if (!F.perm) continue;                          // uniform: the whole block
+        float lo[3], ext = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = from_ordered_bits(((const uint32_t *)F.stats)[kStatMin + a]);
+            const float hi = from_ordered_bits(((const uint32_t *)F.stats)[kStatMax + a]);
+            ext = fmaxf(ext, hi - lo[a]);
+        }
+        const float inv = ext > 0.f ? 256.f / ext : 0.f;
+        const float *p0 = pts + 3 * (src_off[w.unit] + w.start);
+        __syncthreads();                                // the previous item's readers are done
+        for (int j = t; j < kTileSort; j += kTileBlock) {
+            unsigned long long key = ~0ull;             // padding sorts last
+            if (j < w.count) {
+                const float *p = p0 + 3 * j;
+                uint32_t code = 0xffffffu;
+                if (isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2])) {
+                    uint32_t q[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float c = fmaxf(0.f, (p[a] - lo[a]) * inv);
+                        q[a] = c < 255.f ? (uint32_t)c : 255u;
+                    }
+                    code = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+                }
+                key = ((unsigned long long)code << 32) | (unsigned long long)j;
+            }
+            s_key[j] = key;
+        }
+        __syncthreads();
+        for (int k = 2; k <= kTileSort; k <<= 1)
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = t; i < kTileSort; i += kTileBlock) {
+                    const int l = i ^ jj;
+                    if (l > i) {
+                        const unsigned long long a = s_key[i], b = s_key[l];
+                        const bool up = (i & k) == 0;
+                        if ((a > b) == up) {
+                            s_key[i] = b;
+                            s_key[l] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int j = t; j < w.count; j += kTileBlock)
+            ((int32_t *)F.perm)[w.start + j] = (int32_t)(w.start + (int64_t)(s_key[j] & 0xffffffffull));
+    }
+}
+
+// Group boxes of many frames (after the streams are written): for every group of
+// kGroup consecutive stored points the box of its finite points (min > max when
+// it has none), one warp per group, over the point items (their starts are
+// multiples of kGroup).
+__global__ void k_frames_group_boxes(const int32_t *__restrict__ fidx, const WorkItem *__restrict__ items,
+                                     int n_items, const FrameDesc *__restrict__ frames)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const FrameDesc F = frames[fidx[w.unit]];
+        for (int g = wib; g * kGroup < w.count; g += nw) {
+            const int64_t i = w.start + (int64_t)g * kGroup + lane;
+            float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+            if (i < w.start + w.count) {
+                const float4 p = F.pa[i];
+                if (isfinite(p.x) && isfinite(p.y) && isfinite(p.z)) {
+                    mn[0] = mx[0] = p.x;
+                    mn[1] = mx[1] = p.y;
+                    mn[2] = mx[2] = p.z;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    mn[j] = fminf(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
+                    mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
+                }
+            if (lane < 6) {
+                const int64_t grp = (w.start >> 5) + g;
+                ((float *)F.gbox)[6 * grp + lane] = lane < 3 ? mn[lane] : mx[lane - 3];
+            }
+        }
+    }
+}
+
 // Chunk boxes of many frames: item (frame, chunk) per block, as k_chunk_boxes.
 __global__ void k_frames_chunk_boxes(const int32_t *__restrict__ fidx, const WorkItem *__restrict__ chunks,
                                      int n_chunks, const FrameDesc *__restrict__ frames)
@@ -380,6 +487,7 @@ __global__ void k_build_clear(const MapDesc *__restrict__ maps, const BuildUnit 
             ck[v] = ones;                                                       // kEmptyCompact = all ones
             vos[v] = ones;                                                      // -1
         }
+        for (int v = threadIdx.x; v < kCoarseWords; v += blockDim.x) m.coarse[v] = 0u;
         if (threadIdx.x == 0) {
             *U.n_voxels = 0;
             m.kbox[0] = m.kbox[1] = m.kbox[2] = INT32_MAX;
@@ -604,11 +712,36 @@ __global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUni
                        Z = nv > 0 ? (uint64_t)(kb[5] - kb[2] + 1) : 0;
         const uint64_t words = (X * Y * Z + 31) / 32;
         const bool bitmap = ok && words <= (uint64_t)(m.mask + 1) && words <= kBitmapMaxWords;
+        // coarse occupancy: the smallest shift >= 2 whose grid fits kCoarseWords words
+        int cs = 2;
+        uint64_t cx = 0, cy = 0, cz = 0;
+        if (nv > 0) {
+            for (;; ++cs) {
+                cx = (uint64_t)((kb[3] - kb[0]) >> cs) + 1;
+                cy = (uint64_t)((kb[4] - kb[1]) >> cs) + 1;
+                cz = (uint64_t)((kb[5] - kb[2]) >> cs) + 1;
+                if (cx * cy * cz <= (uint64_t)kCoarseWords * 32) break;
+            }
+        }
         if (w.start == 0 && threadIdx.x == 0) {
             m.cmeta[0] = (int32_t)lg;
             m.cmeta[1] = (ok && !bitmap) ? 1 : 0;
             m.cmeta[2] = bitmap ? 1 : 0;
             m.cmeta[3] = bitmap ? (int32_t)words : 0;
+            m.cmeta[4] = nv > 0 ? cs : -1;
+            m.cmeta[5] = (int32_t)cx;
+            m.cmeta[6] = (int32_t)cy;
+            m.cmeta[7] = (int32_t)cz;
+        }
+        if (nv > 0) {
+            for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
+                if (v >= (int64_t)nv) break;
+                int kx, ky, kz;
+                unpack_key(m.keys[scr.slot_of_vid[u.point_base + v]], kx, ky, kz);
+                const uint64_t bit = (uint64_t)((kx - kb[0]) >> cs) +
+                                     cx * ((uint64_t)((ky - kb[1]) >> cs) + cy * (uint64_t)((kz - kb[2]) >> cs));
+                atomicOr(m.coarse + (bit >> 5), 1u << (bit & 31));
+            }
         }
         if (!ok) continue;
         if (bitmap) {
@@ -746,21 +879,26 @@ void launch_frame_pack(const float *points, const float *covs, int64_t n, float4
 void launch_frames_register(const float *pts, const float *cov, const int64_t *src_off, const int32_t *fidx, int m,
                             const WorkItem *items, int n_items, const WorkItem *chunks, int n_chunks,
                             const uint32_t *desc_idx, const FrameDesc *descs, FrameDesc *table, uint32_t *order_scratch,
-                            int64_t total, int num_sms, cudaStream_t st)
+                            int64_t total, int num_sms, int order_mode, cudaStream_t st)
 {
     if (m <= 0) return;
     k_scatter_frame_descs<<<(m + 127) / 128, 128, 0, st>>>(desc_idx, descs, m, table);
     k_frames_init<<<(m + 127) / 128, 128, 0, st>>>(fidx, m, table);
     const int pg = std::min(n_items, 148 * 16);
-    if (n_items > 0 && order_scratch) {
+    if (n_items > 0 && order_mode != 0) {
         // statistics (the bounding box), the spatial order, then the streams in that order
         k_frames_pack<<<pg, 256, 0, st>>>(pts, cov, src_off, fidx, items, n_items, table, 1);
-        k_frames_order<<<std::min(m, num_sms), kSortBlock, 0, st>>>(pts, src_off, fidx, m, table, order_scratch,
-                                                                    total);
+        if (order_mode == 2)
+            k_frames_order_tiles<<<std::min(n_items, num_sms * 2), kTileBlock, 0, st>>>(pts, src_off, fidx, items,
+                                                                                     n_items, table);
+        else
+            k_frames_order<<<std::min(m, num_sms * 4), kSortBlock, 0, st>>>(pts, src_off, fidx, m, table,
+                                                                            order_scratch, total);
         k_frames_pack<<<pg, 256, 0, st>>>(pts, cov, src_off, fidx, items, n_items, table, 2);
     } else if (n_items > 0) {
         k_frames_pack<<<pg, 256, 0, st>>>(pts, cov, src_off, fidx, items, n_items, table, 0);
     }
+    if (n_items > 0) k_frames_group_boxes<<<pg, 256, 0, st>>>(fidx, items, n_items, table);
     if (n_chunks > 0)
         k_frames_chunk_boxes<<<std::min(n_chunks, 148 * 16), 256, 0, st>>>(fidx, chunks, n_chunks, table);
 }
