@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
     __shared__ int s_kb[6], s_lg, s_smem, s_words;   // voxel box, compact table size, staged: 1 table, 2 bitmap
     __shared__ const float4 *s_pa[kSlice];
     __shared__ const float *s_gb[kSlice];
-    __shared__ int s_n[kSlice], s_csh[kSlice];
+    __shared__ int s_n[kSlice], s_csh[kSlice], s_next[kSlice];   // s_next: next round of each source
     __shared__ int s_q;
     const int lane = threadIdx.x & 31;
     int n_live = 0;
@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
                 const PoseParam &Pg = pairs[(int64_t)(s0 + wib) * n_tgt + t];
                 const FrameDesc &F = frames[__ldg((const int *)&Pg.frame)];
                 if (lane == 0) {
+                    s_next[wib] = 0;
                     s_pa[wib] = F.pa;
                     s_gb[wib] = F.gbox;
                     s_n[wib] = (int)F.n;
@@ -236,15 +237,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
             if (P.cull) continue;                       // uniform across the block
             const float4 *__restrict__ pa = s_pa[si];
             const int n = s_n[si], csh = s_csh[si], ng = (n + kGroup - 1) / kGroup;
-            constexpr int NW = BLOCK / 32;
-            const int wid = (int)(threadIdx.x >> 5);
             unsigned int hits = 0;
-            // warp wid takes groups wid, wid + NW, ...: 32 candidates per round, one
-            // per lane, kept when in a live cull chunk and (with a group test) when
-            // reaching an occupied coarse cell of the target; then the live ones,
-            // kPPT groups per step, one lane per point.  No block barrier.
-            for (int gr = wid; gr < ng; gr += NW * 32) {
-                const int gc = gr + NW * lane;
+            // rounds of 32 consecutive candidate groups, taken by the warps from a
+            // per-source counter (no block barrier, no fixed shares): a candidate is
+            // kept when in a live cull chunk and (with a group test) when reaching an
+            // occupied coarse cell of the target; then the live ones, kPPT groups
+            // per step, one lane per point
+            for (;;) {
+                int rnd = 0;
+                if (lane == 0) rnd = atomicAdd(&s_next[si], 1);
+                const int gr = __shfl_sync(0xffffffffu, rnd, 0) * 32;
+                if (gr >= ng) break;
+                const int gc = gr + lane;
                 bool l = gc < ng && ((P.cmask >> (((int64_t)gc * kGroup) >> csh)) & 1u);
                 if (l && P.cs >= 0) l = group_live(P, s_gb[si] + 6 * (int64_t)gc, m.r_h, m.inv_rf, m.coarse);
                 uint32_t livem = __ballot_sync(0xffffffffu, l);
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
                 for (int j = 0; j < kPPT; ++j) {
                     int i = n;
                     if (livem) {
-                        i = (gr + NW * (__ffs(livem) - 1)) * kGroup + lane;
+                        i = (gr + __ffs(livem) - 1) * kGroup + lane;
                         livem &= livem - 1u;
                     }
                     have[j] = i < n;
