@@ -68,6 +68,14 @@ typedef enum {
     VGICP_ERR_NUMERIC = 8       /* a linear system is not positive definite */
 } vgicp_status;
 
+/* Where an input or output array lives: host memory (pageable or pinned) or
+ * device memory of the context's GPU.  Inputs are always copied: the kernels
+ * read frames in their own padded, per-point 36 B layout (x, y, z and the six
+ * covariance entries in two 16 B vectors and one float, optionally stored in
+ * spatial order) with per-frame statistics and group boxes next to it, so a
+ * caller's n x 3 and n x 6 arrays cannot be borrowed in place.  From device
+ * memory the copy is one pass of the packing kernel (about 72 B of traffic
+ * per point). */
 enum { VGICP_MEM_HOST = 0, VGICP_MEM_DEVICE = 1 };
 
 /* Linearisation precision (vgicp_options.precision). */
