@@ -937,6 +937,16 @@ def run_optimize(a):
 # serving loop
 # ---------------------------------------------------------------------------
 
+def served(srv, results, what):
+    """Raise unless every request of a serving run succeeded; log the run's end."""
+    import paper_2109_07073_b300 as vg
+    bad = [r.status for r in results if vg.STATUS.get(r.status) not in ("VGICP_OK", "VGICP_ERR_EMPTY")]
+    print(f"[serving] {what}: {len(results)} requests, {len(bad)} failed", file=sys.stderr, flush=True)
+    if bad:
+        raise RuntimeError(f"serving ({what}): {len(bad)} of {len(results)} requests failed "
+                           f"(first status {bad[0]}): {srv.last_error()}")
+
+
 def serving_runs(w, covs, n_sources, n_req, rates, budgets_gb, device_loop, seed=5050, closed=True):
     """Poisson streams of linearise (90 %) and overlap (10 %) requests of uneven
     size through the server, at each rate and device-memory budget.  Targets:
@@ -976,13 +986,12 @@ def serving_runs(w, covs, n_sources, n_req, rates, budgets_gb, device_loop, seed
             # warm: every source once with its own target (admits every object the
             # budget holds, so a budget above the working set leaves nothing to admit)
             warm = [srv.submit(vg.VGICP_REQ_LINEARIZE, int(w.factor_target[f]), f, T[f]) for f in range(n_sources)]
-            for tk in warm:
-                srv.wait(tk, 600.0)
+            served(srv, [srv.wait(tk, 120.0) for tk in warm], f"{mode}, {budget_gb} GB: warm-up")
             if closed:      # peak throughput: all requests submitted at once
                 srv.reset_stats()
                 t0 = time.perf_counter()
                 tks = srv.submit_batch(kinds, w.factor_target[pick], pick, T_all[pick])
-                srv.wait_batch(tks, 600.0)
+                served(srv, srv.wait_batch(tks, 120.0), f"{mode}, {budget_gb} GB: closed")
                 wall = time.perf_counter() - t0
                 st = srv.stats()
                 runs.append({"mode": mode, "budget_gb": budget_gb, "rate": "closed (all submitted in one batch)",
@@ -1010,7 +1019,7 @@ def serving_runs(w, covs, n_sources, n_req, rates, budgets_gb, device_loop, seed
                             time.sleep(dt - 1e-4)
                     tks.append(submit(k))
                     lag[k] = time.perf_counter() - t0 - arrive[k]
-                srv.wait_batch(tks, 600.0)
+                served(srv, srv.wait_batch(tks, 120.0), f"{mode}, {budget_gb} GB: {rate:.0f} req/s")
                 wall = time.perf_counter() - t0
                 st = srv.stats()
                 runs.append({"mode": mode, "budget_gb": budget_gb, "rate": rate, "requests": n_req,

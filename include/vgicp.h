@@ -188,7 +188,11 @@ vgicp_status vgicp_set_stream(vgicp_ctx *ctx, void *cuda_stream);
  * its own scratch buffers, so calls on different lanes may be in flight at
  * the same time; handles and their device data are shared by all lanes.  The
  * caller must not release or rebuild a handle that another lane's enqueued
- * work still reads.  Lane 0 is the context's initial stream. */
+ * work still reads, and must order work that uses a handle after the work that
+ * created or rebuilt it when that ran on another lane (vgicp_synchronize on
+ * that lane, or a CUDA event recorded there and waited for on this lane's
+ * stream): a handle's descriptor and data are written on the creating lane's
+ * stream.  Lane 0 is the context's initial stream. */
 vgicp_status vgicp_set_lane(vgicp_ctx *ctx, int32_t lane, void *cuda_stream);
 
 /* Block until all work enqueued on the context's current lane has finished. */

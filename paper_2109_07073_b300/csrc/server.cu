@@ -56,7 +56,7 @@ struct Resident {
     uint64_t last_use = 0;
     int64_t key = 0;                // tagged key (position in the LRU order: (last_use, key))
     int pins = 0;                   // batches in flight that use it
-    cudaEvent_t ready = nullptr;    // device loop: recorded after the object's admission
+    cudaEvent_t ready = nullptr;    // recorded after the object's admission (on the admitting stream)
     bool ready_done = true;         // ... and seen complete
 };
 
@@ -152,6 +152,37 @@ void CUDART_CB lane_done(void *p)
     s->cv_work.notify_all();
 }
 
+// An object's admission (copy, build, descriptor update) is enqueued on the
+// context's current stream; its ready event marks where that work ends
+// (scheduler thread).
+vgicp_status mark_admitted(vgicp_server *s, Resident &o)
+{
+    vg::CtxView v;
+    vg::ctx_view(s->ctx, &v);
+    if (!o.ready && cudaEventCreateWithFlags(&o.ready, cudaEventDisableTiming) != cudaSuccess) return VGICP_ERR_CUDA;
+    if (cudaEventRecord(o.ready, v.stream) != cudaSuccess) return VGICP_ERR_CUDA;
+    o.ready_done = false;
+    return VGICP_OK;
+}
+
+// Order the context's current stream after object o's admission, which may
+// have been enqueued on another lane's stream: work that reads the object, or
+// frees its memory and reuses its descriptor slot, must not overtake it
+// (scheduler thread; nothing to do once the admission is seen complete).
+vgicp_status after_admission(vgicp_server *s, Resident &o)
+{
+    if (o.ready_done || !o.ready) return VGICP_OK;
+    const cudaError_t q = cudaEventQuery(o.ready);
+    if (q == cudaSuccess) {
+        o.ready_done = true;
+        return VGICP_OK;
+    }
+    if (q != cudaErrorNotReady) return VGICP_ERR_CUDA;
+    vg::CtxView v;
+    vg::ctx_view(s->ctx, &v);
+    return cudaStreamWaitEvent(v.stream, o.ready, 0) == cudaSuccess ? VGICP_OK : VGICP_ERR_CUDA;
+}
+
 // Release the least recently used idle resident object (scheduler thread).
 bool evict_one(vgicp_server *s)
 {
@@ -168,6 +199,13 @@ bool evict_one(vgicp_server *s)
         }
         if (!best) return false;
         ++s->evictions;
+    }
+    // the free and the reuse of the object's descriptor slot come after its admission
+    if (after_admission(s, *best) != VGICP_OK) {
+        vg::CtxView v;
+        vg::ctx_view(s->ctx, &v);
+        cudaStreamSynchronize(v.stream);
+        if (best->ready) cudaEventSynchronize(best->ready);
     }
     vgicp_release(s->ctx, best->handle);
     best->handle = -1;
@@ -205,11 +243,12 @@ vgicp_status admit(vgicp_server *s, Resident &o)
         }
         if (st == VGICP_OK) {
             o.handle = h;
+            const vgicp_status ev = mark_admitted(s, o);
             std::lock_guard<std::mutex> lk(s->mu);
             o.last_use = ++s->clock;
             s->lru.insert({o.last_use, o.key});
             ++s->admissions;
-            return VGICP_OK;
+            return ev;
         }
         if (st != VGICP_ERR_BUDGET) return st;
         if (!evict_one(s)) return VGICP_ERR_BUDGET;
@@ -288,6 +327,10 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
             }
             admit_ms += std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
         }
+        // objects admitted by a batch on another lane may still be in transit:
+        // this lane's work waits for their admission
+        if (st == VGICP_OK) st = after_admission(s, *m);
+        if (st == VGICP_OK) st = after_admission(s, *f);
         std::lock_guard<std::mutex> lk(s->mu);
         if (st == VGICP_ERR_BUDGET) {
             deferred.push_back(t);
@@ -401,6 +444,19 @@ void scheduler(vgicp_server *s)
 {
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
+        // a failed context runs no host callbacks: a lane whose stream reports an
+        // error is finished, with that status, so no waiter (nor the server's
+        // destruction) waits for it forever
+        for (int li = 0; li < s->nl; ++li) {
+            LaneState &L = s->lanes[li];
+            if (!L.busy || L.finished.load()) continue;
+            const cudaError_t q = cudaStreamQuery(L.stream);
+            if (q != cudaSuccess && q != cudaErrorNotReady) {
+                s->err = cudaGetErrorString(q);
+                L.status = VGICP_ERR_CUDA;
+                L.finished.store(true);
+            }
+        }
         bool harvested = false;
         for (int li = 0; li < s->nl; ++li)
             if (s->lanes[li].busy && s->lanes[li].finished.load()) {
@@ -521,9 +577,13 @@ vgicp_status launch_loop(vgicp_server *s)
     a.qcap = s->qcap;
     a.idle_ns = (unsigned long long)(s->idle_ms * 1e6);
     a.worker_ns = a.idle_ns + 1000000000ull;       // the idle limit plus a second
+    // an error left by an earlier call of this thread must not be taken for a
+    // failed launch: the requests would be answered and their objects unpinned
+    // while the kernel reads them
+    cudaGetLastError();
     vg::launch_request_loop(a, s->num_sms, s->loop_stream);
-    cudaEventRecord(s->loop_ev1, s->loop_stream);
     const cudaError_t e = cudaGetLastError();
+    cudaEventRecord(s->loop_ev1, s->loop_stream);
     if (e != cudaSuccess) {
         s->err = cudaGetErrorString(e);
         return VGICP_ERR_CUDA;
@@ -552,22 +612,11 @@ vgicp_status prepare(vgicp_server *s, int64_t t)
     const auto ta = Clock::now();
     vgicp_status st = VGICP_OK;
     if (m->handle < 0 || f->handle < 0) {
-        vg::CtxView v;
-        vg::ctx_view(s->ctx, &v);
-        auto admit_ready = [&](Resident &o) {
-            if (o.handle >= 0) return VGICP_OK;
-            const vgicp_status a = admit(s, o);
-            if (a != VGICP_OK) return a;
-            if (!o.ready && cudaEventCreateWithFlags(&o.ready, cudaEventDisableTiming) != cudaSuccess)
-                return VGICP_ERR_CUDA;
-            if (cudaEventRecord(o.ready, v.stream) != cudaSuccess) return VGICP_ERR_CUDA;
-            o.ready_done = false;
-            return VGICP_OK;
-        };
-        st = admit_ready(*m);
+        // admit() records each admitted object's ready event
+        st = admit(s, *m);
         if (st == VGICP_OK) {
             { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
-            st = admit_ready(*f);
+            st = admit(s, *f);
             std::lock_guard<std::mutex> lk(s->mu);
             m->pins--;
         }
@@ -589,7 +638,8 @@ vgicp_status prepare(vgicp_server *s, int64_t t)
 // Whether an object's admission has completed on the device (mutex held).
 bool object_ready(Resident &o)
 {
-    if (!o.ready_done && cudaEventQuery(o.ready) == cudaSuccess) o.ready_done = true;
+    // an error (a failed context) counts as done: the loop launch then reports it
+    if (!o.ready_done && cudaEventQuery(o.ready) != cudaErrorNotReady) o.ready_done = true;
     return o.ready_done;
 }
 
@@ -1000,6 +1050,8 @@ vgicp_status vgicp_server_destroy(vgicp_server *s)
     }
     for (int li = 0; li < s->nl; ++li) cudaStreamSynchronize(s->lanes[li].stream);
     vgicp_set_lane(s->ctx, 0, nullptr);
+    for (auto &kv : s->objs)
+        if (kv.second.ready) cudaEventDestroy(kv.second.ready);
     vgicp_destroy(s->ctx);
     for (int li = 0; li < s->nl; ++li) {
         LaneState &L = s->lanes[li];

@@ -68,6 +68,38 @@ def test_voxelmap_faces_negative_and_out_of_range(ctx):
     ctx.release(h)
 
 
+def _run_pattern_clouds(r):
+    """Storage orders that shape the build's runs of equal voxels within a warp:
+    one voxel for every point (one claim, every other warp adds later), two
+    voxels alternating (runs of one point), blocks of 33 points per voxel (runs
+    across warp boundaries), and a real cloud in random order."""
+    rng = dg.Stream(23)
+    one = (0.25 + 0.5 * rng.uniform(3 * 5000, 0, 1)).reshape(-1, 3) * r
+    two = np.concatenate([one[:2000], one[:2000] + np.array([r, 0, 0])], 1).reshape(-1, 3)
+    cells = np.repeat(np.round(rng.uniform(3 * 150, -20, 20)).reshape(-1, 3), 33, axis=0)
+    blocks = (cells + 0.1 + 0.8 * rng.uniform(cells.size, 0, 1).reshape(-1, 3)) * r
+    w = dg.single_factor_workload()
+    perm = np.argsort(rng.uniform(w.points_target.shape[0], 0, 1))
+    shuffled = w.points_target[perm]
+    return [c.astype(np.float32) for c in (one, two, blocks, shuffled)]
+
+
+@pytest.mark.parametrize("r", [1.0, 0.3])
+def test_voxelmap_build_run_patterns(r):
+    """Every run pattern builds the oracle's voxelmap (keys and counts exact), in
+    the given storage order and in the spatial order, with identical exports."""
+    rng = dg.Stream(24)
+    with vg.Context(frame_order=0) as given, vg.Context(frame_order=2) as spatial:
+        for pts in _run_pattern_clouds(r):
+            cov = rng.uniform(pts.shape[0] * 6, -1, 1).astype(np.float32).reshape(-1, 6)
+            hg, hs = given.build_voxelmap(pts, cov, r), spatial.build_voxelmap(pts, cov, r)
+            check_voxelmap(given, hg, pts, cov, r)
+            for x, y in zip(given.export_voxelmap(hg), spatial.export_voxelmap(hs)):
+                assert np.array_equal(x, y)
+            given.release(hg)
+            spatial.release(hs)
+
+
 def test_batched_build_equals_single_builds(ctx, single):
     w, cb, ca = single
     fr = [ctx.add_frame(w.points_target, cb), ctx.add_frame(w.points_source, ca),

@@ -119,6 +119,24 @@ def test_server_budget_evicts_and_matches(data):
     assert st.evictions > 0 and st.resident_bytes <= int(full * 0.4)
 
 
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_server_small_batches_across_lanes_under_eviction(data, lanes):
+    """Batches of at most two requests on two or four lanes under a budget of a
+    third of the working set: an object admitted (copied, built, its descriptor
+    written) by one lane's batch is used, or evicted, by the next batch on
+    another lane while that admission may still be in flight.  Every result
+    equals the request run alone, bit for bit."""
+    maps, frames, reqs = data
+    reqs = reqs * 3
+    ref = alone(maps, frames, reqs)
+    _, st = serve(maps, frames, reqs[:len(reqs) // 3], clients=1)
+    full = st.resident_bytes
+    res, st = serve(maps, frames, reqs, clients=4, hbm_budget_bytes=int(full * 0.34), lanes=lanes,
+                    max_batch_requests=2)
+    check_identical(reqs, res, ref)
+    assert st.evictions > 0 and st.batches >= len(reqs) // 2
+
+
 def test_server_vs_oracle(data):
     maps, frames, reqs = data
     kind, t, s, T = next(r for r in reqs if r[0] == vg.VGICP_REQ_LINEARIZE)
