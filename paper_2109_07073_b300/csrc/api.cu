@@ -56,7 +56,7 @@ struct Lane {
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
     Buf ws_poses, ws_params, ws_partials, ws_inl, ws_out, ws_f64, ws_ticket, ws_counts, ws_stage;
-    Buf ws_bunits, ws_bitems, ws_bprefix, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
+    Buf ws_bunits, ws_bitems, ws_slot_of_point, ws_acc, ws_vid_of_slot, ws_slot_of_vid;
     Buf ws_pairs, ws_fidx, ws_midx, ws_chunks, ws_export_keys, ws_export_rec, ws_counter, ws_descs, ws_tune, ws_knn;
     Buf ws_fetch, ws_items, ws_img, ws_rec, ws_order;
     Plan plan;
@@ -539,7 +539,6 @@ vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const 
         pts += fo.n;
     }
     TRY(upload(ctx, LN.ws_bunits, units.data(), units.size()));
-    TRY(upload(ctx, LN.ws_bprefix, prefix.data(), prefix.size()));
     TRY(upload(ctx, LN.ws_bitems, items.data(), items.size()));
     TRY(ensure(ctx, LN.ws_slot_of_point, (size_t)pts * 4));
     TRY(ensure(ctx, LN.ws_acc, (size_t)pts * 80));
@@ -553,10 +552,10 @@ vgicp_status run_build(vgicp_ctx *ctx, const std::vector<uint32_t> &fidx, const 
     const int grid = std::max(1, std::min<int>((int)items.size(), ctx->num_sms * 8));
     const int kt = ktimer_begin(ctx, VGICP_KERNEL_VOXELMAP_BUILD);
     launch_voxelmap_build(ctx->d_maps, ctx->d_frames, (const BuildUnit *)LN.ws_bunits.p, nu,
-                          (const WorkItem *)LN.ws_bitems.p, (int)items.size(), (const int64_t *)LN.ws_bprefix.p,
+                          (const WorkItem *)LN.ws_bitems.p, (int)items.size(),
                           scr, grid, LN.stream);
     ktimer_end(ctx, VGICP_KERNEL_VOXELMAP_BUILD, kt);
-    ctx->launches += 1 + (items.empty() ? 0 : 4);
+    ctx->launches += 1 + (items.empty() ? 0 : 3);
     CHECK_LAUNCH();
     return VGICP_OK;
 }
@@ -843,7 +842,7 @@ vgicp_status vgicp_destroy(vgicp_ctx *ctx)
         if (!LN.stream) continue;
         Buf *bufs[] = {&LN.ws_poses, &LN.ws_params, &LN.ws_partials, &LN.ws_inl, &LN.ws_out, &LN.ws_f64,
                        &LN.ws_ticket, &LN.ws_counts, &LN.ws_stage, &LN.ws_bunits, &LN.ws_bitems,
-                       &LN.ws_bprefix, &LN.ws_slot_of_point, &LN.ws_acc, &LN.ws_vid_of_slot,
+                       &LN.ws_slot_of_point, &LN.ws_acc, &LN.ws_vid_of_slot,
                        &LN.ws_slot_of_vid, &LN.ws_img, &LN.ws_pairs, &LN.ws_fidx, &LN.ws_midx, &LN.ws_chunks,
                        &LN.ws_export_keys, &LN.ws_export_rec, &LN.ws_counter, &LN.ws_descs, &LN.ws_tune,
                        &LN.ws_knn, &LN.plan.idx, &LN.plan.items, &LN.plan.item_range, &LN.plan.units, &LN.ws_fetch,

@@ -58,8 +58,7 @@ struct BuildUnit {
 };
 
 void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const BuildUnit *units, int n_units,
-                           const WorkItem *items, int n_items, const int64_t *slot_items /* n_units+1 prefix */,
-                           BuildScratch scr, int grid, cudaStream_t st);
+                           const WorkItem *items, int n_items, BuildScratch scr, int grid, cudaStream_t st);
 // Shared-memory images of the maps idx[0..n) (table indices), made on demand.
 void launch_map_images(const MapDesc *maps, const int32_t *idx, int n, int num_sms, cudaStream_t st);
 

@@ -2,18 +2,18 @@
 // distribution aggregates the distributions of the points that fall in it:
 // mean of the point means and mean of the point covariances).
 //
-// Build of all maps of a batch in five launches:
-//   clear      keys <- EMPTY, voxel counters <- 0
+// Build of all maps of a batch in four launches:
+//   clear      keys <- EMPTY, voxel counters <- 0, presence words reset
 //   insert     per point: voxel key, atomicCAS into the map's open-addressing
 //              table; the thread that claims a slot takes a dense voxel id and
 //              zeroes that voxel's accumulators
 //   accumulate per point: exact fixed-point sums (int64 atomics, so the result
 //              does not depend on the order the GPU runs the points in)
 //   finalize   per voxel: mean relative to the voxel's lower corner, mean
-//              covariance, count -> the slot's 48 B record
-//   compact    per voxel: its 32-bit key relative to the map's voxel box into a
-//              presence table sized by the voxel count (overlap queries stage
-//              it in shared memory)
+//              covariance, count -> the slot's 48 B record; its 32-bit key
+//              relative to the map's voxel box into a presence table sized by
+//              the voxel count (overlap queries stage it in shared memory) and
+//              its bit in the coarse occupancy bitmap
 #include <algorithm>
 #include "kernels.cuh"
 
@@ -470,23 +470,21 @@ __global__ void k_chunk_boxes(const float4 *__restrict__ pa, int64_t n, int shif
     }
 }
 
-// Empty tables, one block per map: keys, compact presence entries and slot ->
-// voxel ids in 16-byte stores (capacities are powers of two >= 16, so every
-// array holds a whole number of vectors), the voxel count and the box.
-__global__ void k_build_clear(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units, int n_units,
-                              const int64_t *__restrict__ slot_prefix, int32_t *__restrict__ vid_of_slot)
+// Empty tables, one block per map: keys and compact presence entries in
+// 16-byte stores (capacities are powers of two >= 16, so every array holds a
+// whole number of vectors), the coarse occupancy words, the voxel count and
+// the box.  The slot -> voxel id array needs no clearing: only slots claimed
+// in this build are ever read from it.
+__global__ void k_build_clear(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units, int n_units)
 {
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const BuildUnit U = units[u];
         const MapDesc &m = maps[U.map];
-        const int64_t base = slot_prefix[u], cap = slot_prefix[u + 1] - base;
-        uint4 *keys = (uint4 *)m.keys, *ck = (uint4 *)m.ckeys, *vos = (uint4 *)(vid_of_slot + base);
+        const int64_t cap = (int64_t)m.mask + 1;
+        uint4 *keys = (uint4 *)m.keys, *ck = (uint4 *)m.ckeys;
         const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
         for (int64_t v = threadIdx.x; v < cap / 2; v += blockDim.x) keys[v] = ones;   // kEmptyKey = all ones
-        for (int64_t v = threadIdx.x; v < cap / 4; v += blockDim.x) {
-            ck[v] = ones;                                                       // kEmptyCompact = all ones
-            vos[v] = ones;                                                      // -1
-        }
+        for (int64_t v = threadIdx.x; v < cap / 4; v += blockDim.x) ck[v] = ones;     // kEmptyCompact = all ones
         for (int v = threadIdx.x; v < kCoarseWords; v += blockDim.x) m.coarse[v] = 0u;
         if (threadIdx.x == 0) {
             *U.n_voxels = 0;
@@ -662,6 +660,15 @@ __global__ void k_build_accumulate(const MapDesc *__restrict__ maps, const Frame
     }
 }
 
+// Per voxel: the 48 B record of its slot (mean relative to the voxel's lower
+// corner, mean covariance, count) and its entries in the presence structures.
+// The map's header (cmeta) describes them: a bitmap over the voxel box when
+// the box needs at most min(capacity, kBitmapMaxWords) words (cmeta[2] = 1,
+// cmeta[3] = words); otherwise the compact presence table, the compact key of
+// every voxel inserted into the first 2^lg entries (lg = log2 of the smallest
+// power of two >= 4 V, at most the main capacity: load <= 1/4, short probe
+// chains), when the voxel box extent allows it (cmeta[1] = 1); and always the
+// coarse occupancy bitmap (cmeta[4..7]: shift and extents).
 __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
                                  const BuildUnit *__restrict__ units, const WorkItem *__restrict__ items,
                                  int n_items, BuildScratch scr)
@@ -671,37 +678,6 @@ __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDe
         const BuildUnit u = units[w.unit];
         const MapDesc m = maps[u.map];
         const FrameDesc f = frames[u.frame];
-        const uint32_t nv = *u.n_voxels;
-        const float isc = 1.f / cov_scale(f.stats), ism = 1.f / mean_scale(m);
-        for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
-            if (v >= (int64_t)nv) break;
-            const int64_t *acc = scr.acc + (u.point_base + v) * kAcc;
-            const int32_t slot = scr.slot_of_vid[u.point_base + v];
-            const float n = (float)acc[0], in = 1.f / n;
-            VoxelRec r;
-            r.a = make_float4(__ll2float_rn(acc[1]) * ism * in, __ll2float_rn(acc[2]) * ism * in,
-                              __ll2float_rn(acc[3]) * ism * in, __ll2float_rn(acc[4]) * isc * in);
-            r.b = make_float4(__ll2float_rn(acc[5]) * isc * in, __ll2float_rn(acc[6]) * isc * in,
-                              __ll2float_rn(acc[7]) * isc * in, __ll2float_rn(acc[8]) * isc * in);
-            r.c = make_float4(__ll2float_rn(acc[9]) * isc * in, __uint_as_float((uint32_t)acc[0]), 0.f, 0.f);
-            m.rec[slot] = r;
-        }
-    }
-}
-
-// Presence structure of each map in its ckeys words: a bitmap over the voxel
-// box when the box needs at most min(capacity, kBitmapMaxWords) words
-// (cmeta[2] = 1, cmeta[3] = words); otherwise the compact presence table, the
-// compact key of every voxel inserted into the first 2^lg entries (lg = log2 of
-// the smallest power of two >= 4 V, at most the main capacity: load <= 1/4,
-// short probe chains), when the voxel box extent allows it (cmeta[1] = 1).
-__global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUnit *__restrict__ units,
-                                const WorkItem *__restrict__ items, int n_items, BuildScratch scr)
-{
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const WorkItem w = items[it];
-        const BuildUnit u = units[w.unit];
-        const MapDesc m = maps[u.map];
         const uint32_t nv = *u.n_voxels;
         const int *kb = m.kbox;
         const bool ok = nv > 0 && kb[3] - kb[0] <= kCompactMaxX && kb[4] - kb[1] <= kCompactMaxX &&
@@ -733,32 +709,32 @@ __global__ void k_build_compact(const MapDesc *__restrict__ maps, const BuildUni
             m.cmeta[6] = (int32_t)cy;
             m.cmeta[7] = (int32_t)cz;
         }
-        if (nv > 0) {
-            for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
-                if (v >= (int64_t)nv) break;
-                int kx, ky, kz;
-                unpack_key(m.keys[scr.slot_of_vid[u.point_base + v]], kx, ky, kz);
-                const uint64_t bit = (uint64_t)((kx - kb[0]) >> cs) +
-                                     cx * ((uint64_t)((ky - kb[1]) >> cs) + cy * (uint64_t)((kz - kb[2]) >> cs));
-                atomicOr(m.coarse + (bit >> 5), 1u << (bit & 31));
-            }
-        }
-        if (!ok) continue;
-        if (bitmap) {
-            for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
-                if (v >= (int64_t)nv) break;
-                int kx, ky, kz;
-                unpack_key(m.keys[scr.slot_of_vid[u.point_base + v]], kx, ky, kz);
-                const uint64_t bit = (uint64_t)(kx - kb[0]) + X * ((uint64_t)(ky - kb[1]) + Y * (uint64_t)(kz - kb[2]));
-                atomicAnd(m.ckeys + (bit >> 5), ~(1u << (bit & 31)));
-            }
-            continue;
-        }
+        const float isc = 1.f / cov_scale(f.stats), ism = 1.f / mean_scale(m);
         const uint32_t cmask = (1u << lg) - 1u;
         for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
             if (v >= (int64_t)nv) break;
+            const int64_t *acc = scr.acc + (u.point_base + v) * kAcc;
+            const int32_t slot = scr.slot_of_vid[u.point_base + v];
+            const float n = (float)acc[0], in = 1.f / n;
+            VoxelRec r;
+            r.a = make_float4(__ll2float_rn(acc[1]) * ism * in, __ll2float_rn(acc[2]) * ism * in,
+                              __ll2float_rn(acc[3]) * ism * in, __ll2float_rn(acc[4]) * isc * in);
+            r.b = make_float4(__ll2float_rn(acc[5]) * isc * in, __ll2float_rn(acc[6]) * isc * in,
+                              __ll2float_rn(acc[7]) * isc * in, __ll2float_rn(acc[8]) * isc * in);
+            r.c = make_float4(__ll2float_rn(acc[9]) * isc * in, __uint_as_float((uint32_t)acc[0]), 0.f, 0.f);
+            m.rec[slot] = r;
             int kx, ky, kz;
-            unpack_key(m.keys[scr.slot_of_vid[u.point_base + v]], kx, ky, kz);
+            unpack_key(m.keys[slot], kx, ky, kz);
+            const uint64_t cbit = (uint64_t)((kx - kb[0]) >> cs) +
+                                  cx * ((uint64_t)((ky - kb[1]) >> cs) + cy * (uint64_t)((kz - kb[2]) >> cs));
+            atomicOr(m.coarse + (cbit >> 5), 1u << (cbit & 31));
+            if (!ok) continue;
+            if (bitmap) {
+                const uint64_t bit =
+                    (uint64_t)(kx - kb[0]) + X * ((uint64_t)(ky - kb[1]) + Y * (uint64_t)(kz - kb[2]));
+                atomicAnd(m.ckeys + (bit >> 5), ~(1u << (bit & 31)));
+                continue;
+            }
             const uint32_t ck = pack_compact(kx - kb[0], ky - kb[1], kz - kb[2]);
             uint32_t s = hash_compact(ck, lg);
             for (uint32_t t = 0; t <= cmask; ++t) {
@@ -910,16 +886,14 @@ void launch_chunk_boxes(const float4 *pa, int64_t n, int shift, int nchunks, flo
 }
 
 void launch_voxelmap_build(const MapDesc *maps, const FrameDesc *frames, const BuildUnit *units, int n_units,
-                           const WorkItem *items, int n_items, const int64_t *slot_prefix, BuildScratch scr,
-                           int grid, cudaStream_t st)
+                           const WorkItem *items, int n_items, BuildScratch scr, int grid, cudaStream_t st)
 {
     if (n_units <= 0) return;
-    k_build_clear<<<std::min(n_units, 148 * 8), 512, 0, st>>>(maps, units, n_units, slot_prefix, scr.vid_of_slot);
+    k_build_clear<<<std::min(n_units, 148 * 8), 512, 0, st>>>(maps, units, n_units);
     if (n_items > 0) {
         k_build_insert<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
         k_build_accumulate<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
         k_build_finalize<<<grid, 256, 0, st>>>(maps, frames, units, items, n_items, scr);
-        k_build_compact<<<grid, 256, 0, st>>>(maps, units, items, n_items, scr);
     }
 }
 
