@@ -581,10 +581,14 @@ __device__ __forceinline__ float cov_scale(const float *stats)
 
 __device__ __forceinline__ float mean_scale(const MapDesc &m) { return m.inv_rf * 0x1p32f; }
 
-__global__ void k_build_accumulate(const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
-                                   const BuildUnit *__restrict__ units, const WorkItem *__restrict__ items,
-                                   int n_items, BuildScratch scr)
+__global__ void __launch_bounds__(256) k_build_accumulate(const MapDesc *__restrict__ maps,
+                                                          const FrameDesc *__restrict__ frames,
+                                                          const BuildUnit *__restrict__ units,
+                                                          const WorkItem *__restrict__ items, int n_items,
+                                                          BuildScratch scr)
 {
+    __shared__ long long s_stage[8][kAcc - 1][32];    // per warp of the 256-thread block
+    long long(*stage)[32] = s_stage[threadIdx.x >> 5];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
         const BuildUnit u = units[w.unit];
@@ -592,7 +596,7 @@ __global__ void k_build_accumulate(const MapDesc *__restrict__ maps, const Frame
         const FrameDesc f = frames[u.frame];
         const float sc = cov_scale(f.stats), sm = mean_scale(m);
         const unsigned lane = threadIdx.x & 31;
-        // whole warps step together (the run reduction below shuffles across lanes)
+        // whole warps step together (lanes of one voxel are grouped below)
         for (int64_t i0 = w.start + (threadIdx.x & ~31u); i0 < w.start + w.count; i0 += blockDim.x) {
             const int64_t i = i0 + lane;
             int32_t vid = -1;
@@ -634,41 +638,31 @@ __global__ void k_build_accumulate(const MapDesc *__restrict__ maps, const Frame
                     v[9] = __float2ll_rn(c22 * sc);
                 }
             }
-            // consecutive points (firing order) often share a voxel: a segmented
-            // inclusive scan over runs of equal voxel ids, then one atomic per run
-            // and sum from the run's last lane.  Integer sums: the result does not
-            // depend on the grouping.
-            const int32_t prev = __shfl_up_sync(0xffffffffu, vid, 1);
-            bool seg = lane == 0 || prev != vid;       // a run starts here
+            // the lanes of one voxel (a spatially ordered frame keeps them close):
+            // the lowest adds up their sums from shared memory and makes the one
+            // set of int64 atomics.  Integer sums: the result does not depend on
+            // the grouping or on the order the atomics land in.
+            const unsigned peers = __match_any_sync(0xffffffffu, vid);
+            const int leader = __ffs(peers) - 1;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const bool up_seg = __shfl_up_sync(0xffffffffu, seg, d);
+            for (int j = 1; j < kAcc; ++j) stage[j - 1][lane] = v[j];
+            __syncwarp();
+            if ((int)lane == leader && vid >= 0) {
+                for (unsigned rest = peers & (peers - 1u); rest; rest &= rest - 1u) {
+                    const int b = __ffs(rest) - 1;
 #pragma unroll
-                for (int j = 0; j < kAcc; ++j) {
-                    const long long x = __shfl_up_sync(0xffffffffu, v[j], d);
-                    if (lane >= (unsigned)d && !seg) v[j] += x;
+                    for (int j = 1; j < kAcc; ++j) v[j] += stage[j - 1][b];
                 }
-                if (lane >= (unsigned)d) seg = seg || up_seg;
-            }
-            const int32_t next = __shfl_down_sync(0xffffffffu, vid, 1);
-            if (vid >= 0 && (lane == 31 || next != vid)) {
+                v[0] = __popc(peers);
                 unsigned long long *acc = (unsigned long long *)(scr.acc + (u.point_base + vid) * kAcc);
 #pragma unroll
                 for (int j = 0; j < kAcc; ++j) atomicAdd(acc + j, (unsigned long long)v[j]);
             }
+            __syncwarp();
         }
     }
 }
 
-// Per voxel: the 48 B record of its slot (mean relative to the voxel's lower
-// corner, mean covariance, count) and its entries in the presence structures.
-// The map's header (cmeta) describes them: a bitmap over the voxel box when
-// the box needs at most min(capacity, kBitmapMaxWords) words (cmeta[2] = 1,
-// cmeta[3] = words); otherwise the compact presence table, the compact key of
-// every voxel inserted into the first 2^lg entries (lg = log2 of the smallest
-// power of two >= 4 V, at most the main capacity: load <= 1/4, short probe
-// chains), when the voxel box extent allows it (cmeta[1] = 1); and always the
-// coarse occupancy bitmap (cmeta[4..7]: shift and extents).
 __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDesc *__restrict__ frames,
                                  const BuildUnit *__restrict__ units, const WorkItem *__restrict__ items,
                                  int n_items, BuildScratch scr)
