@@ -76,6 +76,8 @@ def parse():
     p.add_argument("--serving-requests", type=int, default=50000)
     p.add_argument("--serving-rates", default="2000,5000,10000,20000")
     p.add_argument("--serving-budgets-gb", default="40,2")
+    p.add_argument("--serving-modes", default="device,host",
+                   help="server modes of --serving: device (request loop) and/or host (host-launched batches)")
     p.add_argument("--precision-split", action="store_true",
                    help="the precision split: uneven factors plus 200 dense 120,000-point frames at 0.25 m, all "
                         "three paths against the FP64 oracle; writes reports/precision_split.json")
@@ -1049,7 +1051,10 @@ def run_serving(a):
     rates = [float(x) for x in a.serving_rates.split(",")]
     budgets = [float(x) for x in a.serving_budgets_gb.split(",")]
     runs = []
-    for dl in (True, False):
+    modes = [x.strip() for x in a.serving_modes.split(",") if x.strip()]
+    if not modes or any(x not in ("device", "host") for x in modes):
+        raise SystemExit("--serving-modes takes device and/or host")
+    for dl in [x == "device" for x in modes]:
         runs += serving_runs(w, covs, a.serving_sources, a.serving_requests, rates, budgets, dl)
     peak = runs[0]
     res = {"metric": "factors/s (serving loop, closed)", "value": peak["factors_per_s"], "unit": "factors/s",
