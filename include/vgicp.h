@@ -29,9 +29,11 @@
  *     (c00, c01, c02, c11, c12, c22), symmetric positive definite.
  *
  * Memory: mem_kind / out_kind say where a caller pointer lives.  HOST
- * pointers may be pageable; DEVICE pointers are read on the context stream and
- * copied into library-owned device memory before the call returns control of
- * the stream.  HOST inputs in pageable memory (and any below 64 KB) are staged
+ * pointers may be pageable; DEVICE inputs are read by work enqueued on the
+ * context's current lane (copied into library-owned device memory there), so
+ * they must stay valid and unchanged until that lane has been synchronised
+ * (vgicp_synchronize, or any later call with HOST outputs on the same lane).
+ * HOST inputs in pageable memory (and any below 64 KB) are staged
  * before the call returns, so the caller may reuse them at once; HOST inputs in
  * page-locked memory of 64 KB or more are copied by the device in stream order,
  * like cudaMemcpyAsync: leave them unchanged until the lane has been
@@ -75,7 +77,8 @@ typedef enum {
  * spatial order) with per-frame statistics and group boxes next to it, so a
  * caller's n x 3 and n x 6 arrays cannot be borrowed in place.  From device
  * memory the copy is one pass of the packing kernel (about 72 B of traffic
- * per point). */
+ * per point), enqueued on the context's current lane (see "Memory" above for
+ * how long the caller's arrays must stay unchanged). */
 enum { VGICP_MEM_HOST = 0, VGICP_MEM_DEVICE = 1 };
 
 /* Linearisation precision (vgicp_options.precision). */

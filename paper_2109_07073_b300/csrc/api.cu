@@ -91,6 +91,11 @@ struct vgicp_ctx {
     std::string err;
     std::vector<Obj> objs;
     std::vector<uint32_t> free_idx;
+    // per descriptor index: an event recorded on the lane that released the
+    // index (after the work that lane had enqueued, which may still read the
+    // index's descriptor), waited for by the lane that takes the index again
+    std::vector<cudaEvent_t> idx_ev;
+    std::vector<uint8_t> idx_ev_set;
     int64_t bytes_in_use = 0;
     int64_t launches = 0;
     // descriptor tables (device) and host mirrors
@@ -393,6 +398,12 @@ vgicp_status new_obj(vgicp_ctx *ctx, Obj::Kind kind, uint32_t *idx)
     if (!ctx->free_idx.empty()) {
         i = ctx->free_idx.back();
         ctx->free_idx.pop_back();
+        // the lane that released i may still have work queued that reads the
+        // descriptor at i: this lane's writes to it come after that work
+        if (i < ctx->idx_ev_set.size() && ctx->idx_ev_set[i]) {
+            ctx->idx_ev_set[i] = 0;
+            CU(cudaStreamWaitEvent(LN.stream, ctx->idx_ev[i], 0));
+        }
     } else {
         i = (uint32_t)ctx->objs.size();
         ctx->objs.emplace_back();
@@ -829,6 +840,11 @@ vgicp_status vgicp_create(vgicp_ctx **out, const vgicp_options *opt, void *cuda_
 vgicp_status vgicp_destroy(vgicp_ctx *ctx)
 {
     if (!ctx) return VGICP_ERR_INVALID_ARG;
+    // every lane's work ends before the memory it may read is freed
+    for (int l = 0; l < kMaxLanes; ++l)
+        if (ctx->lanes[l].stream) cudaStreamSynchronize(ctx->lanes[l].stream);
+    for (cudaEvent_t ev : ctx->idx_ev)
+        if (ev) cudaEventDestroy(ev);
     ctx->lane = 0;
     for (Obj &o : ctx->objs) {
         if (o.frame_mem) cudaFreeAsync(o.frame_mem, LN.stream);
@@ -1937,6 +1953,13 @@ vgicp_status vgicp_release(vgicp_ctx *ctx, int64_t handle)
     const uint32_t gen = o->gen;
     *o = Obj();
     o->gen = gen;
+    if (ctx->idx_ev.size() <= idx) {
+        ctx->idx_ev.resize(idx + 1, nullptr);
+        ctx->idx_ev_set.resize(idx + 1, 0);
+    }
+    if (!ctx->idx_ev[idx]) CU(cudaEventCreateWithFlags(&ctx->idx_ev[idx], cudaEventDisableTiming));
+    CU(cudaEventRecord(ctx->idx_ev[idx], LN.stream));
+    ctx->idx_ev_set[idx] = 1;
     ctx->free_idx.push_back(idx);
     LN.plan.key.clear();   // a cached work list may name this handle
     return VGICP_OK;

@@ -77,3 +77,55 @@ def test_pipelined_lanes_match_one_lane(batch):
         ctx.release_many(np.concatenate([nxt, np.array(extra, np.int64)]))
         ctx.synchronize()
         ctx.set_lane(0)
+
+
+def test_released_index_reused_on_another_lane(batch):
+    """A frame registered, built into a voxelmap and released on lane 1 while
+    lane 1 is still busy with a long linearisation; lane 2 then registers a
+    larger frame, which takes the released descriptor index at once, and builds
+    its voxelmap.  Lane 2's writes to that index wait for lane 1's queued work,
+    so both voxelmaps (and the larger frame's overlap) equal those made on one
+    lane, bit for bit."""
+    poses, pts, covs = batch
+    small_p, small_c = pts[0][:5000], covs[0][:5000]
+    big_p, big_c = pts[1], covs[1]
+    with vg.Context() as ref:
+        want_a = ref.export_voxelmap(ref.build_voxelmap(small_p, small_c, 1.0))
+        hb = ref.add_frame(big_p, big_c)
+        want_b = ref.export_voxelmap(ref.build_voxelmaps([hb], 1.0)[0])
+        want_ov = ref.overlap_matrix([hb], ref.build_voxelmaps([ref.add_frame(pts[2], covs[2])], 1.0),
+                                     poses[1:2], poses[2:3])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    # device inputs are read by the lane's queued work: they stay alive until it is done
+    d_small, d_big = (dev(small_p), dev(small_c)), (dev(big_p), dev(big_c))
+    with vg.Context() as ctx:
+        fr = ctx.add_frames(np.concatenate(pts), np.concatenate(covs), np.array([p.shape[0] for p in pts]))
+        mp = ctx.build_voxelmaps(fr, 1.0)
+        m2 = ctx.build_voxelmaps([ctx.add_frame(pts[2], covs[2])], 1.0)
+        pairs = [(i, j) for j in range(len(pts)) for i in range(len(pts)) if i != j] * 100
+        f = vg.make_factors(mp[[i for i, _ in pairs]], fr[[j for _, j in pairs]], [i for i, _ in pairs],
+                            [j for _, j in pairs])
+        nf = f.shape[0]
+        out = (torch.empty((nf, 12, 12), dtype=torch.float64, device="cuda"),
+               torch.empty((nf, 12), dtype=torch.float64, device="cuda"),
+               torch.empty(nf, dtype=torch.float64, device="cuda"), torch.empty(nf, dtype=torch.int64, device="cuda"))
+        torch.cuda.synchronize()
+        for _ in range(3):
+            ctx.set_lane(1)
+            ctx.linearize(f, poses, out=out)                   # long work queued on lane 1
+            ha = ctx.add_frame(*d_small)
+            ma = ctx.build_voxelmaps([ha], 1.0)[0]
+            ctx.release(ha)                                    # its index is free on the host at once
+            ctx.set_lane(2)
+            hb = ctx.add_frame(*d_big)                         # takes that index
+            mb = ctx.build_voxelmaps([hb], 1.0)[0]
+            ctx.synchronize()
+            ctx.set_lane(1)
+            ctx.synchronize()
+            ctx.set_lane(0)
+            for x, y in zip(ctx.export_voxelmap(int(ma)), want_a):
+                assert np.array_equal(x, y)
+            for x, y in zip(ctx.export_voxelmap(int(mb)), want_b):
+                assert np.array_equal(x, y)
+            assert np.array_equal(ctx.overlap_matrix([hb], m2, poses[1:2], poses[2:3]), want_ov)
+            ctx.release_many([int(ma), int(mb), hb])
