@@ -923,6 +923,11 @@ vgicp_status vgicp_synchronize(vgicp_ctx *ctx)
 }
 
 // Stage host or device points / covariances in device memory (covs nullable).
+namespace {
+vgicp_status add_frames_staged(vgicp_ctx *ctx, const float *dp, const float *dc, const int64_t *n, int64_t m,
+                               int64_t total, vgicp_frame_t *out);
+}
+
 static vgicp_status stage_inputs(vgicp_ctx *ctx, const float *points, const float *covs, int64_t n, int mem_kind,
                                  const float **d_pts, const float **d_cov)
 {
@@ -971,7 +976,19 @@ vgicp_status vgicp_add_frames(vgicp_ctx *ctx, const float *points, const float *
     if (m == 0) return VGICP_OK;
     const float *dp = nullptr, *dc = nullptr;
     TRY(stage_inputs(ctx, points, covs, total, mem_kind, &dp, &dc));
-    // handles first (all or none), then one descriptor scatter and the batched kernels
+    return add_frames_staged(ctx, dp, dc, n, m, total, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Register m frames whose points (total x 3) and covariances (total x 6) are in
+// device memory, one frame after another: handles first (all or none), then
+// one descriptor scatter and the batched kernels.
+vgicp_status add_frames_staged(vgicp_ctx *ctx, const float *dp, const float *dc, const int64_t *n, int64_t m,
+                               int64_t total, vgicp_frame_t *out)
+{
     std::vector<uint32_t> idx((size_t)m);
     for (int64_t u = 0; u < m; ++u) {
         const vgicp_status st = alloc_frame(ctx, n[u], &idx[u]);
@@ -1033,6 +1050,10 @@ vgicp_status vgicp_add_frames(vgicp_ctx *ctx, const float *points, const float *
     for (int64_t u = 0; u < m; ++u) out[u] = make_handle(idx[u], ctx->objs[idx[u]].gen);
     return VGICP_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 vgicp_status vgicp_frame_size(vgicp_ctx *ctx, vgicp_frame_t frame, int64_t *n)
 {
@@ -2084,6 +2105,29 @@ bool ctx_frame_size(vgicp_ctx *ctx, int64_t handle, int64_t *n)
 vgicp_status ctx_fail(vgicp_ctx *ctx, vgicp_status s, const char *msg) { return fail(ctx, s, "%s", msg); }
 
 void ctx_count_launches(vgicp_ctx *ctx, int n) { ctx->launches += n; }
+
+int ctx_add_frames_gather(vgicp_ctx *ctx, const float *const *points, const float *const *covs,
+                                   const int64_t *n, int64_t m, int64_t *out)
+{
+    if (m <= 0) return VGICP_OK;
+    int64_t total = 0;
+    for (int64_t u = 0; u < m; ++u) {
+        if (n[u] < 0 || n[u] > ((int64_t)1 << 31) - 1 || (n[u] > 0 && (!points[u] || !covs[u])))
+            return fail(ctx, VGICP_ERR_INVALID_ARG, "add_frames: frame %lld: bad size or pointer", (long long)u);
+        total += n[u];
+    }
+    // each frame's arrays copied to its place in the lane's staging buffer
+    const size_t pb = align256((size_t)total * 12);
+    TRY(ensure(ctx, LN.ws_stage, pb + (size_t)total * 24));
+    char *base = (char *)LN.ws_stage.p;
+    int64_t o = 0;
+    for (int64_t u = 0; u < m; ++u) {
+        TRY(h2d(ctx, base + 12 * o, points[u], (size_t)n[u] * 12));
+        TRY(h2d(ctx, base + pb + 24 * o, covs[u], (size_t)n[u] * 24));
+        o += n[u];
+    }
+    return add_frames_staged(ctx, (const float *)base, (const float *)(base + pb), n, m, total, out);
+}
 
 bool ctx_descs(vgicp_ctx *ctx, int64_t map, int64_t frame, MapDesc *m, FrameDesc *f, int64_t *n_points)
 {

@@ -189,6 +189,12 @@ void ctx_count_launches(::vgicp_ctx *ctx, int n);
 // Descriptors of a resident map and frame (copies of the host mirrors) and the
 // frame's point count; false for an unknown handle.
 bool ctx_descs(::vgicp_ctx *ctx, int64_t map, int64_t frame, MapDesc *m, FrameDesc *f, int64_t *n_points);
+// vgicp_add_frames for m frames whose host arrays lie apart: frame u's points
+// (n[u] x 3) and covariances (n[u] x 6) at points[u] and covs[u], each copied
+// into the current lane's staging buffer, then registered in one batched pass.
+// Returns a vgicp_status.
+int ctx_add_frames_gather(::vgicp_ctx *ctx, const float *const *points, const float *const *covs, const int64_t *n,
+                          int64_t m, int64_t *out);
 
 }  // namespace vg
 

@@ -35,6 +35,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -56,6 +57,7 @@ struct Resident {
     uint64_t last_use = 0;
     int64_t key = 0;                // tagged key (position in the LRU order: (last_use, key))
     int pins = 0;                   // batches in flight that use it
+    int64_t bytes = 0;              // device bytes it holds while resident
     cudaEvent_t ready = nullptr;    // recorded after the object's admission (on the admitting stream)
     bool ready_done = true;         // ... and seen complete
 };
@@ -212,47 +214,183 @@ bool evict_one(vgicp_server *s)
     return true;
 }
 
-// Make an object resident (scheduler thread).  VGICP_ERR_BUDGET when it cannot
-// fit even with every idle object released.
-vgicp_status admit(vgicp_server *s, Resident &o)
+// Device bytes an object holds once resident; for a map with the temporary
+// frame it is built from, which is held until the build is queued.
+int64_t object_bytes(vgicp_server *s, const Resident &o)
 {
-    if (o.handle >= 0) return VGICP_OK;
-    if (s->opt.hbm_budget_bytes > 0) {
-        // make room for the estimate first, so a failed attempt (and its copy) is rare
-        int64_t need = 0, used = 0, fb = 0;
-        vgicp_memory_estimate(s->ctx, o.n, o.is_map ? 1 : 0, &need);
-        if (o.is_map) vgicp_memory_estimate(s->ctx, o.n, 0, &fb);
-        vgicp_memory_in_use(s->ctx, &used);
-        while (used + need + fb > s->opt.hbm_budget_bytes && evict_one(s)) vgicp_memory_in_use(s->ctx, &used);
-        // nothing left to evict (the rest is pinned by batches in flight): defer
-        // without staging the object's data for an allocation that would fail
-        if (used + need + fb > s->opt.hbm_budget_bytes) return VGICP_ERR_BUDGET;
+    int64_t b = 0, fb = 0;
+    vgicp_memory_estimate(s->ctx, o.n, o.is_map ? 1 : 0, &b);
+    if (o.is_map) vgicp_memory_estimate(s->ctx, o.n, 0, &fb);
+    return b + fb;
+}
+
+// Make the distinct, non-resident objects `miss` resident in one batched pass
+// on the context's current stream (scheduler thread; the caller has made room
+// for them): one registration of every missing frame and of a temporary frame
+// per missing map, one voxelmap build per resolution, the temporary frames
+// released once their builds are queued, and each object's ready event
+// recorded after all of it.  All or nothing.
+vgicp_status admit_many(vgicp_server *s, const std::vector<Resident *> &miss)
+{
+    const size_t k = miss.size();
+    if (k == 0) return VGICP_OK;
+    std::vector<const float *> P(k), C(k);
+    std::vector<int64_t> N(k), H(k, -1), MH(k, -1);
+    for (size_t i = 0; i < k; ++i) {
+        P[i] = miss[i]->pts;
+        C[i] = miss[i]->covs;
+        N[i] = miss[i]->n;
     }
-    for (;;) {
-        vgicp_status st;
-        int64_t h = -1;
-        if (o.is_map) {
-            vgicp_frame_t fr;
-            st = vgicp_add_frame(s->ctx, o.pts, o.covs, o.n, VGICP_MEM_HOST, &fr);
-            if (st == VGICP_OK) {
-                st = vgicp_build_voxelmaps(s->ctx, &fr, 1, o.r, &h);
-                vgicp_release(s->ctx, fr);
+    vgicp_status st = (vgicp_status)vg::ctx_add_frames_gather(s->ctx, P.data(), C.data(), N.data(), (int64_t)k,
+                                                              H.data());
+    if (st != VGICP_OK) return st;
+    std::vector<size_t> maps;
+    for (size_t i = 0; i < k; ++i)
+        if (miss[i]->is_map) maps.push_back(i);
+    std::vector<char> built(maps.size(), 0);
+    for (size_t a = 0; a < maps.size() && st == VGICP_OK; ++a) {
+        if (built[a]) continue;
+        const double r = miss[maps[a]]->r;
+        std::vector<int64_t> fr, out;
+        std::vector<size_t> who;
+        for (size_t b = a; b < maps.size(); ++b)
+            if (!built[b] && miss[maps[b]]->r == r) {
+                built[b] = 1;
+                fr.push_back(H[maps[b]]);
+                who.push_back(maps[b]);
             }
-        } else {
-            st = vgicp_add_frame(s->ctx, o.pts, o.covs, o.n, VGICP_MEM_HOST, &h);
-        }
-        if (st == VGICP_OK) {
-            o.handle = h;
-            const vgicp_status ev = mark_admitted(s, o);
-            std::lock_guard<std::mutex> lk(s->mu);
-            o.last_use = ++s->clock;
-            s->lru.insert({o.last_use, o.key});
-            ++s->admissions;
-            return ev;
-        }
-        if (st != VGICP_ERR_BUDGET) return st;
-        if (!evict_one(s)) return VGICP_ERR_BUDGET;
+        out.assign(fr.size(), -1);
+        st = vgicp_build_voxelmaps(s->ctx, fr.data(), (int64_t)fr.size(), r, out.data());
+        if (st == VGICP_OK)
+            for (size_t j = 0; j < who.size(); ++j) MH[who[j]] = out[j];
     }
+    for (size_t i : maps) vgicp_release(s->ctx, H[i]);
+    if (st != VGICP_OK) {
+        for (size_t i = 0; i < k; ++i) {
+            if (!miss[i]->is_map) vgicp_release(s->ctx, H[i]);
+            else if (MH[i] >= 0) vgicp_release(s->ctx, MH[i]);
+        }
+        return st;
+    }
+    for (size_t i = 0; i < k; ++i) {
+        Resident &o = *miss[i];
+        o.handle = o.is_map ? MH[i] : H[i];
+        vgicp_memory_estimate(s->ctx, o.n, o.is_map ? 1 : 0, &o.bytes);
+        const vgicp_status ev = mark_admitted(s, o);
+        std::lock_guard<std::mutex> lk(s->mu);
+        o.last_use = ++s->clock;
+        s->lru.insert({o.last_use, o.key});
+        ++s->admissions;
+        if (ev != VGICP_OK) st = ev;
+    }
+    return st;
+}
+
+// Requests admitted together at most (their missing objects in one pass).
+constexpr size_t kAdmitGroup = 64;
+
+// Make the objects of requests ts resident (scheduler thread, mutex not held).
+// From the front, as many requests are taken as the budget can hold once the
+// idle resident objects that those requests do not use are counted as free;
+// least recently used idle objects are evicted to make exactly that room, the
+// taken requests' missing objects are admitted together, and both objects of
+// each taken request stay pinned until its result is read: those requests go
+// to ok.  The rest go to deferred with nothing pinned (all of them when even
+// the first does not fit).  When the admission fails other than for the
+// budget, the taken requests go to failed and fail_status says why.
+void prepare_group(vgicp_server *s, const std::vector<int64_t> &ts, std::vector<int64_t> &ok,
+                   std::vector<int64_t> &deferred, std::vector<int64_t> &failed, vgicp_status &fail_status)
+{
+    const size_t nt = ts.size();
+    std::vector<Resident *> m(nt), f(nt);
+    // need[k]: bytes the missing objects of the first k requests take (each
+    // once); kept[k]: bytes of the idle resident objects those requests use,
+    // which cannot be evicted for them
+    std::vector<int64_t> need(nt + 1, 0), kept(nt + 1, 0);
+    std::vector<Resident *> order;                     // missing objects in first-use order
+    std::vector<size_t> first_req;                     // the request that needs each first
+    int64_t idle = 0;                                  // bytes held by evictable objects
+    size_t take = nt;
+    const auto ta = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        std::unordered_set<Resident *> seen;
+        for (size_t i = 0; i < nt; ++i) {
+            const vgicp_request &r = s->reqs[ts[i]].req;
+            m[i] = &s->objs[tag(r.target, true)];
+            f[i] = &s->objs[tag(r.source, false)];
+            need[i + 1] = need[i];
+            kept[i + 1] = kept[i];
+            for (Resident *o : {m[i], f[i]}) {
+                if (!seen.insert(o).second) continue;
+                if (o->handle < 0) {
+                    order.push_back(o);
+                    first_req.push_back(i);
+                    need[i + 1] += object_bytes(s, *o);
+                } else if (o->pins == 0) {
+                    kept[i + 1] += o->bytes;
+                }
+            }
+        }
+        if (s->opt.hbm_budget_bytes > 0) {
+            for (const auto &e : s->lru) {
+                const Resident &o = s->objs[e.second];
+                if (o.pins == 0) idle += o.bytes;
+            }
+            int64_t used = 0;
+            vgicp_memory_in_use(s->ctx, &used);
+            const int64_t room = s->opt.hbm_budget_bytes - (used - idle);
+            while (take > 0 && need[take] + kept[take] > room) --take;
+        }
+        for (size_t i = 0; i < take; ++i) {
+            m[i]->pins++;
+            f[i]->pins++;
+        }
+    }
+    if (s->opt.hbm_budget_bytes > 0 && take > 0) {
+        int64_t used = 0;
+        vgicp_memory_in_use(s->ctx, &used);
+        while (used + need[take] > s->opt.hbm_budget_bytes && evict_one(s)) vgicp_memory_in_use(s->ctx, &used);
+        // an estimate that fell short: fewer requests, down to none
+        size_t k = take;
+        while (k > 0 && used + need[k] > s->opt.hbm_budget_bytes) --k;
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t i = k; i < take; ++i) {
+            m[i]->pins--;
+            f[i]->pins--;
+        }
+        take = k;
+    }
+    std::vector<Resident *> miss;
+    for (size_t j = 0; j < order.size() && first_req[j] < take; ++j) miss.push_back(order[j]);
+    vgicp_status st = take ? admit_many(s, miss) : VGICP_OK;
+    const double admit_ms = std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->host_admit_ms += admit_ms;
+    if (st == VGICP_ERR_BUDGET) {                        // the allocation itself did not fit: later
+        for (size_t i = 0; i < take; ++i) {
+            m[i]->pins--;
+            f[i]->pins--;
+        }
+        take = 0;
+        st = VGICP_OK;
+    }
+    for (size_t i = 0; i < take; ++i) {
+        if (st != VGICP_OK) {
+            m[i]->pins--;
+            f[i]->pins--;
+            failed.push_back(ts[i]);
+            continue;
+        }
+        for (Resident *o : {m[i], f[i]}) {
+            s->lru.erase({o->last_use, o->key});
+            o->last_use = ++s->clock;
+            s->lru.insert({o->last_use, o->key});
+        }
+        ok.push_back(ts[i]);
+    }
+    fail_status = st;
+    for (size_t i = take; i < nt; ++i) deferred.push_back(ts[i]);
 }
 
 vgicp_status ensure_lane_buffers(LaneState &L, int64_t n)
@@ -310,44 +448,44 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
     }
     fac.reserve(tickets.size());
     poses.reserve(12 * (tickets.size() + 1));
-    double admit_ms = 0.0;
+    // admission in groups; once a group leaves requests out for lack of room,
+    // the rest of the batch waits with them (arrival order is kept)
+    std::vector<char> admitted(tickets.size(), 0);
+    size_t next = 0;
+    while (next < tickets.size()) {
+        const size_t end = std::min(tickets.size(), next + kAdmitGroup);
+        const std::vector<int64_t> grp(tickets.begin() + (ptrdiff_t)next, tickets.begin() + (ptrdiff_t)end);
+        std::vector<int64_t> ok, def, failed;
+        vgicp_status fst = VGICP_OK;
+        prepare_group(s, grp, ok, def, failed, fst);
+        for (size_t k = next; k < next + ok.size(); ++k) admitted[k] = 1;   // ok is the group's front
+        if (!failed.empty()) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (int64_t t : failed) complete(s, t, fst);
+        }
+        if (!def.empty()) {
+            deferred.assign(tickets.begin() + (ptrdiff_t)(next + ok.size() + failed.size()), tickets.end());
+            break;
+        }
+        next = end;
+    }
     for (size_t k = 0; k < tickets.size(); ++k) {
+        if (!admitted[k]) continue;
         const int64_t t = tickets[k];
         const vgicp_request &r = rq[k];
         Resident *m = om[k], *f = of[k];
-        vgicp_status st = VGICP_OK;
-        if (m->handle < 0 || f->handle < 0) {      // admission (scheduler thread owns the handles)
-            const auto ta = Clock::now();
-            st = admit(s, *m);
-            if (st == VGICP_OK) {
-                { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
-                st = admit(s, *f);
-                std::lock_guard<std::mutex> lk(s->mu);
-                m->pins--;
-            }
-            admit_ms += std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
-        }
         // objects admitted by a batch on another lane may still be in transit:
         // this lane's work waits for their admission
-        if (st == VGICP_OK) st = after_admission(s, *m);
+        vgicp_status st = after_admission(s, *m);
         if (st == VGICP_OK) st = after_admission(s, *f);
         std::lock_guard<std::mutex> lk(s->mu);
-        if (st == VGICP_ERR_BUDGET) {
-            deferred.push_back(t);
-            continue;
-        }
         if (st != VGICP_OK) {
+            m->pins--;
+            f->pins--;
             complete(s, t, st);
             continue;
         }
-        m->pins++;
-        f->pins++;
-        for (Resident *o : {m, f}) {
-            s->lru.erase({o->last_use, o->key});
-            o->last_use = ++s->clock;
-            s->lru.insert({o->last_use, o->key});
-        }
-        L.pinned.push_back(tag(r.target, true));
+        L.pinned.push_back(tag(r.target, true));           // pinned by the admission until finish
         L.pinned.push_back(tag(r.source, false));
         if (r.kind == VGICP_REQ_LINEARIZE) {
             vgicp_factor x;
@@ -394,7 +532,6 @@ std::vector<int64_t> launch_batch(vgicp_server *s, int li, const std::vector<int
     vgicp_memory_in_use(s->ctx, &bytes);
     std::lock_guard<std::mutex> lk(s->mu);
     s->resident_bytes = bytes;
-    s->host_admit_ms += admit_ms;
     s->host_enqueue_ms += enq_ms;
     return deferred;
 }
@@ -594,47 +731,6 @@ vgicp_status launch_loop(vgicp_server *s)
     return VGICP_OK;
 }
 
-// Make request t's objects resident without waiting for their copies and
-// builds (scheduler thread, mutex not held): an admitted object records an
-// event on the context stream that says when it is ready; the request pins
-// both objects from here until its result is read.  VGICP_ERR_BUDGET: defer
-// (nothing pinned).
-vgicp_status prepare(vgicp_server *s, int64_t t)
-{
-    vgicp_request r;
-    Resident *m, *f;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        r = s->reqs[t].req;
-        m = &s->objs[tag(r.target, true)];
-        f = &s->objs[tag(r.source, false)];
-    }
-    const auto ta = Clock::now();
-    vgicp_status st = VGICP_OK;
-    if (m->handle < 0 || f->handle < 0) {
-        // admit() records each admitted object's ready event
-        st = admit(s, *m);
-        if (st == VGICP_OK) {
-            { std::lock_guard<std::mutex> lk(s->mu); m->pins++; }
-            st = admit(s, *f);
-            std::lock_guard<std::mutex> lk(s->mu);
-            m->pins--;
-        }
-    }
-    const double admit_ms = std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->host_admit_ms += admit_ms;
-    if (st != VGICP_OK) return st;
-    m->pins++;
-    f->pins++;
-    for (Resident *o : {m, f}) {
-        s->lru.erase({o->last_use, o->key});
-        o->last_use = ++s->clock;
-        s->lru.insert({o->last_use, o->key});
-    }
-    return VGICP_OK;
-}
-
 // Whether an object's admission has completed on the device (mutex held).
 bool object_ready(Resident &o)
 {
@@ -777,30 +873,37 @@ void scheduler_device(vgicp_server *s)
         }
         const auto tl = Clock::now();
         bool published = false;
-        // admit pending requests (asynchronously), at most a ring's worth ahead of publishing
+        // admit pending requests (asynchronously) in groups, at most a ring's worth
+        // ahead of publishing
         while (!s->pending.empty() && s->waiting.size() + s->ready_q.size() < (size_t)s->slots) {
-            const int64_t t = s->pending.front();
-            s->pending.pop_front();
-            lk.unlock();
-            const vgicp_status st = prepare(s, t);
-            lk.lock();
-            if (st == VGICP_ERR_BUDGET) {
-                if (s->inflight.empty() && s->waiting.empty() && s->ready_q.empty()) {
-                    complete(s, t, VGICP_ERR_BUDGET);   // nothing to wait for: it can never fit
-                    ++s->completed;
-                    s->cv_done.notify_all();
-                    continue;
-                }
-                s->pending.push_front(t);              // retry when other requests release objects
-                break;
+            const size_t room = (size_t)s->slots - s->waiting.size() - s->ready_q.size();
+            std::vector<int64_t> grp;
+            while (!s->pending.empty() && grp.size() < std::min(room, kAdmitGroup)) {
+                grp.push_back(s->pending.front());
+                s->pending.pop_front();
             }
-            if (st != VGICP_OK) {
-                complete(s, t, st);
+            std::vector<int64_t> ok, def, failed;
+            vgicp_status fst = VGICP_OK;
+            lk.unlock();
+            prepare_group(s, grp, ok, def, failed, fst);
+            lk.lock();
+            for (int64_t t : failed) {
+                complete(s, t, fst);
+                ++s->completed;
+            }
+            if (!failed.empty()) s->cv_done.notify_all();
+            for (int64_t t : ok) s->waiting.push_back(t);
+            if (def.empty()) continue;
+            size_t d0 = 0;
+            if (s->inflight.empty() && s->waiting.empty() && s->ready_q.empty()) {
+                complete(s, def[0], VGICP_ERR_BUDGET);   // nothing to wait for: it can never fit
                 ++s->completed;
                 s->cv_done.notify_all();
-                continue;
+                d0 = 1;
             }
-            s->waiting.push_back(t);
+            // the rest waits, in order, until other requests release objects
+            for (size_t i = def.size(); i > d0; --i) s->pending.push_front(def[i - 1]);
+            if (d0 == 0) break;
         }
         // requests whose objects' copies and builds are complete, in order
         for (size_t q = 0; q < s->waiting.size();) {
