@@ -540,7 +540,10 @@ const char *vgicp_status_string(vgicp_status s);
  * are registered once under caller keys; the server keeps host copies and
  * makes them resident on demand (targets as voxelmaps), releasing the least
  * recently used idle ones when the device-memory budget would be exceeded.
- * A request's result is bit-identical to the same request run alone: the
+ * Admission works on up to 64 pending requests at a time: as many of them,
+ * from the front, as the budget can hold have their missing objects made
+ * resident together (one registration of all their frames, one voxelmap build
+ * per resolution); the rest wait in arrival order.  A request's result is bit-identical to the same request run alone: the
  * batched float32 linearisation sums fixed chunks in a fixed order and
  * overlap counts are exact.
  * ---------------------------------------------------------------------- */
