@@ -332,13 +332,14 @@ void prepare_group(vgicp_server *s, const std::vector<int64_t> &ts, std::vector<
                 }
             }
         }
-        if (s->opt.hbm_budget_bytes > 0) {
+        int64_t used = 0;
+        if (s->opt.hbm_budget_bytes > 0 && need[nt] > 0) vgicp_memory_in_use(s->ctx, &used);
+        // only a group that does not fit as things stand walks the resident objects
+        if (s->opt.hbm_budget_bytes > 0 && need[nt] > 0 && used + need[nt] > s->opt.hbm_budget_bytes) {
             for (const auto &e : s->lru) {
                 const Resident &o = s->objs[e.second];
                 if (o.pins == 0) idle += o.bytes;
             }
-            int64_t used = 0;
-            vgicp_memory_in_use(s->ctx, &used);
             const int64_t room = s->opt.hbm_budget_bytes - (used - idle);
             while (take > 0 && need[take] + kept[take] > room) --take;
         }
@@ -347,7 +348,7 @@ void prepare_group(vgicp_server *s, const std::vector<int64_t> &ts, std::vector<
             f[i]->pins++;
         }
     }
-    if (s->opt.hbm_budget_bytes > 0 && take > 0) {
+    if (s->opt.hbm_budget_bytes > 0 && take > 0 && need[take] > 0) {
         int64_t used = 0;
         vgicp_memory_in_use(s->ctx, &used);
         while (used + need[take] > s->opt.hbm_budget_bytes && evict_one(s)) vgicp_memory_in_use(s->ctx, &used);
