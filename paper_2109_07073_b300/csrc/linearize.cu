@@ -1026,7 +1026,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_linearize_f32(const PoseParam *
         if (lane == 0) sM[wib] = maps[sP[wib].map];
         __syncwarp();
         const PoseParam &P = sP[wib];
-        const MapDesc m = sM[wib];
+        const MapDesc &m = sM[wib];
         const FrameDesc F = frames[P.frame];
         float acc[NT];
 #pragma unroll
