@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_overlap_matrix(const PoseParam 
             for (int i = threadIdx.x; i < n4; i += BLOCK) s_tab4[i] = __ldg(src + i);
         }
         __syncthreads();
-        const MapDesc m = sM;
+        const MapDesc &m = sM;
         const int smem = s_smem;
         const uint32_t lg = (uint32_t)s_lg;
         const int ex = s_kb[3] - s_kb[0], ey = s_kb[4] - s_kb[1], ez = s_kb[5] - s_kb[2];
