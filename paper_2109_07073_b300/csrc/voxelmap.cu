@@ -705,8 +705,13 @@ __global__ void k_build_finalize(const MapDesc *__restrict__ maps, const FrameDe
         }
         const float isc = 1.f / cov_scale(f.stats), ism = 1.f / mean_scale(m);
         const uint32_t cmask = (1u << lg) - 1u;
-        for (int64_t v = w.start + threadIdx.x; v < w.start + w.count; v += blockDim.x) {
-            if (v >= (int64_t)nv) break;
+        // the item's share of the map's voxels: the same fraction of [0, nv) as
+        // its points are of the frame (the items tile the points, so the shares
+        // tile the voxels; nv <= f.n), so every item of the map finalizes about
+        // the same number of voxels
+        const int64_t v0 = f.n > 0 ? w.start * (int64_t)nv / f.n : 0;
+        const int64_t v1 = f.n > 0 ? (w.start + w.count) * (int64_t)nv / f.n : 0;
+        for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
             const int64_t *acc = scr.acc + (u.point_base + v) * kAcc;
             const int32_t slot = scr.slot_of_vid[u.point_base + v];
             const float n = (float)acc[0], in = 1.f / n;
